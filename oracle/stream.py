@@ -1,0 +1,121 @@
+"""The five per-stream calls over host memory, in FP64 (the CUDA library's
+``sw_create_stream`` / ``sw_set_model`` / ``sw_upload_depth`` /
+``sw_solve_frame`` / ``sw_fuse_frame`` / ``sw_read_nodes`` counterparts).
+
+Per frame (Sec. 4): the warp field starts from the previous frame's, is
+re-estimated against the new depth image (Sec. 7), then the depth surfels are
+fused into the live surfels (Sec. 6.1) and the fused surfels are warped back to
+the reference frame (Eq. 3).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import dq as DQ
+from . import depth as DEPTH
+from . import skinning as SKIN
+from . import solver as SOLVER
+from . import fusion as FUSION
+
+
+@dataclass
+class Params:
+    """Table 1 values, plus the readings for what the paper leaves open."""
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    lam: float = 5.0               # λ, Table 1
+    fuse_dist: float = 1e-3        # δ_distance, Table 1
+    fuse_normal: float = 0.85      # δ_normal, Table 1
+    corr_dist: float = 0.05        # association distance (reading)
+    corr_normal: float = 0.7       # association normal dot (reading)
+    stable_conf: float = 10.0      # δ_stable, Table 1
+    recent_frames: int = 2         # δ_recent, Table 1
+
+    @property
+    def cam(self):
+        return (self.fx, self.fy, self.cx, self.cy, self.width, self.height)
+
+
+class OracleStream:
+    def __init__(self, params: Params):
+        self.p = params
+        self.maps = None
+        self.t_now = 0
+
+    # -- model ---------------------------------------------------------------
+    def set_model(self, v, n, r, c, t, node_p, node_sigma):
+        """Reference surfels and nodes; node transforms start at identity;
+        skinning (4-NN) and the 8-NN node graph are computed (Sec. 6.5)."""
+        self.v_ref = np.asarray(v, dtype=np.float64).copy()
+        self.n_ref = np.asarray(n, dtype=np.float64).copy()
+        self.radius = np.asarray(r, dtype=np.float64).copy()
+        self.conf = np.asarray(c, dtype=np.float64).copy()
+        t = np.asarray(t)
+        self.t_init = t[:, 0].astype(np.int64).copy()
+        self.t_obs = t[:, 1].astype(np.int64).copy()
+        self.node_p = np.asarray(node_p, dtype=np.float64).copy()
+        self.node_sigma = np.asarray(node_sigma, dtype=np.float64).copy()
+        self.knn = SKIN.knn_fp32(np.asarray(v, dtype=np.float32),
+                                 np.asarray(node_p, dtype=np.float32), SKIN.K_SKIN)
+        self.w = SKIN.skin_weights(v, node_p, node_sigma, self.knn)
+        self.graph = SKIN.node_graph(np.asarray(node_p, dtype=np.float32))
+        self.node_dq = DQ.dq_identity(len(node_p))
+        self.pattern = SOLVER.BlockMatrix.pattern(len(node_p), self.knn, self.graph).keys
+
+    # -- per frame -----------------------------------------------------------
+    def upload_depth(self, depth, frame_id):
+        p = self.p
+        self.depth = np.asarray(depth, dtype=np.float32)
+        self.maps = DEPTH.depth_maps(self.depth, p.fx, p.fy, p.cx, p.cy)
+        self.V32 = self.maps["V"].astype(np.float32)
+        self.N32 = self.maps["N"].astype(np.float32)
+        self.t_now = frame_id
+
+    def associate(self, v_live, n_live):
+        p = self.p
+        sel = SOLVER.select_surfels(self.conf, self.t_obs, self.t_now,
+                                    p.stable_conf, p.recent_frames)
+        ok, pix = SOLVER.associate(v_live, n_live, sel, self.V32, self.N32,
+                                   self.maps["valid"], p.cam, p.corr_dist, p.corr_normal)
+        tv = np.zeros_like(v_live)
+        tn = np.zeros_like(v_live)
+        tv[ok] = self.maps["V"].reshape(-1, 3)[pix[ok]]
+        tn[ok] = self.maps["N"].reshape(-1, 3)[pix[ok]]
+        return ok, tv, tn
+
+    def solve_frame(self, gn_iters, pcg_iters, keep_masks=False):
+        self.node_dq, stats = SOLVER.gauss_newton(
+            self.v_ref, self.n_ref, self.knn, self.w, self.node_p, self.node_dq,
+            self.graph, self.pattern, self.p.lam, gn_iters, pcg_iters,
+            associate_fn=self.associate, keep_masks=keep_masks)
+        return stats
+
+    def fuse_frame(self):
+        p = self.p
+        b, v_live, n_live = SOLVER.warp_surfels(self.v_ref, self.n_ref, self.knn,
+                                                self.w, self.node_dq)
+        imap = FUSION.index_map(v_live, p.cam)
+        target = FUSION.select_fusion_targets(imap, v_live, n_live, self.conf,
+                                              self.V32, self.N32, self.maps["valid"],
+                                              p.fuse_dist, p.fuse_normal)
+        v_live, n_live, self.radius, self.conf, self.t_obs, fused = FUSION.fuse(
+            v_live, n_live, self.radius, self.conf, self.t_obs, self.maps, target, self.t_now)
+        vr, nr = FUSION.inverse_warp(b[fused], v_live[fused], n_live[fused])
+        self.v_ref[fused] = vr
+        self.n_ref[fused] = nr
+        self.last_target = target
+        self.last_index_map = imap
+        return int(fused.sum())
+
+    # -- read-back -----------------------------------------------------------
+    def read_nodes(self):
+        """(node positions (Nn,3), node dual quaternions (Nn,8))."""
+        return self.node_p.copy(), self.node_dq.copy()
+
+    def warped_nodes(self):
+        """T_j p_j: where every node's own transform takes it."""
+        return SOLVER.node_transform(self.node_dq, self.node_p)

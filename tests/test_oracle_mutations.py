@@ -1,0 +1,130 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in the oracle (on the CPU, through monkeypatch)
+-- a flipped sign, a dropped term, a transposed operand, a wrong tie order --
+and checks that at least one pin then fails.
+"""
+import numpy as np
+import pytest
+
+from oracle import dq as DQ
+from oracle import depth as DEPTH
+from oracle import skinning as SKIN
+from oracle import solver as S
+from oracle import fusion as FU
+
+import test_oracle_depth_dq as T_DQ
+import test_oracle_skin_solver as T_SOLVE
+import test_oracle_fusion as T_FU
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_flipped_sign_in_dq_translation(monkeypatch):
+    def bad(c0, ce):
+        w0, a0 = c0[..., :1], c0[..., 1:]
+        we, ae = ce[..., :1], ce[..., 1:]
+        return 2.0 * (w0 * ae + we * a0 + np.cross(a0, ae))
+    monkeypatch.setattr(DQ, "dq_translation", bad)
+    _fails(T_DQ.test_dq_rigid_transform_and_composition_match_matrices)
+
+
+def test_dropped_normalisation_term_in_jacobian(monkeypatch):
+    orig = S.transform_jacobian
+
+    def bad(b, p):
+        out = orig(b, p)
+        W, A = b[:, 0], b[:, 1:4]
+        We, Ae = b[:, 4], b[:, 5:8]
+        n2 = W * W + np.sum(A * A, axis=1)
+        Axp = np.cross(A, p)
+        h = np.cross(A, Axp) + W[:, None] * Axp + W[:, None] * Ae - We[:, None] * A + np.cross(A, Ae)
+        out[:, :, 0:4] += (4.0 / n2 ** 2)[:, None, None] * h[:, :, None] * b[:, None, 0:4]
+        return out
+    monkeypatch.setattr(S, "transform_jacobian", bad)
+    _fails(T_SOLVE.test_data_jacobian_matches_finite_differences)
+
+
+def test_transposed_operand_in_increment_jacobian(monkeypatch):
+    def bad(q):
+        L0 = DQ.left_mult_matrix(q[..., :4])
+        Le = DQ.left_mult_matrix(q[..., 4:])
+        out = np.zeros(q.shape[:-1] + (8, 6))
+        out[..., 0:4, 0:3] = 0.5 * L0
+        out[..., 4:8, 0:3] = 0.5 * L0          # should be Le
+        out[..., 4:8, 3:6] = 0.5 * Le          # should be L0
+        return out
+    monkeypatch.setattr(S, "node_increment_jacobian", bad)
+    _fails(T_SOLVE.test_data_jacobian_matches_finite_differences)
+
+
+def test_swapped_cross_product_in_normals(monkeypatch):
+    orig = np.cross
+
+    def swapped(a, b, *args, **kw):
+        return orig(b, a, *args, **kw)
+    monkeypatch.setattr(DEPTH.np, "cross", swapped)
+    try:
+        _fails(T_DQ.test_plane_normals_radius_confidence)
+    finally:
+        monkeypatch.undo()
+
+
+def test_wrong_reg_jacobian_sign(monkeypatch):
+    orig = S.reg_terms
+
+    def bad(node_p, node_dq, graph, lam):
+        j, i, r, Jj, Ji = orig(node_p, node_dq, graph, lam)
+        return j, i, r, Jj, -Ji
+    monkeypatch.setattr(S, "reg_terms", bad)
+    _fails(T_SOLVE.test_reg_jacobian_matches_finite_differences_and_rigid_zero)
+
+
+def test_wrong_beta_in_pcg(monkeypatch, tiny_scene):
+    def bad_pcg(A, b, Minv, iters):
+        n = A.n
+        As = A.to_scipy()
+
+        def pre(v):
+            return np.einsum('nij,nj->ni', Minv, v.reshape(n, 6)).reshape(-1)
+        x = np.zeros(6 * n)
+        r = b.copy()
+        z = pre(r)
+        p = z.copy()
+        rz = r @ z
+        for _ in range(iters):
+            q = As @ p
+            pq = p @ q
+            alpha = rz / pq
+            x += alpha * p
+            r -= alpha * q
+            z = pre(r)
+            rz_new = r @ z
+            p = z + (rz_new / pq) * p      # wrong denominator
+            rz = rz_new
+        return x, rz, iters
+    monkeypatch.setattr(S, "pcg", bad_pcg)
+    _fails(T_SOLVE.test_pcg_iterate_is_krylov_minimiser, tiny_scene)
+
+
+def test_wrong_knn_tie_order(monkeypatch):
+    orig = SKIN.knn_fp32
+
+    def bad(q, nodes, k, exclude_self=False, chunk=4096):
+        nn = len(nodes)
+        rev = orig(q, np.asarray(nodes)[::-1], k, exclude_self, chunk)
+        return nn - 1 - rev                 # ties now go to the higher id
+    monkeypatch.setattr(SKIN, "knn_fp32", bad)
+    _fails(T_SOLVE.test_knn_brute_force_fp32_with_ties)
+
+
+def test_wrong_fusion_preference(monkeypatch):
+    orig = FU.select_fusion_targets
+
+    def bad(imap, v, n, conf, *a):
+        return orig(imap, v, n, -np.asarray(conf), *a)   # lowest confidence wins
+    monkeypatch.setattr(FU, "select_fusion_targets", bad)
+    _fails(T_FU.test_window_search_brute_force_and_update)
