@@ -1,0 +1,197 @@
+/*
+ * surfelwarp.h -- C ABI of the GB300 (sm_103a) SurfelWarp per-frame hot path.
+ *
+ * SurfelWarp (Gao & Tedrake 2019) reconstructs a deforming surface from a depth
+ * stream.  Per frame it (Sec. 4) re-estimates a node-graph deformation field
+ * against the new depth image (Sec. 7-8), fuses the depth surfels into the
+ * warped ("live") surfels (Sec. 6.1) and warps the fused surfels back to the
+ * reference frame (Sec. 4, Eq. 3).  This library runs that path on one GPU.
+ *
+ * Conventions (all calls):
+ *  - Every call returns an sw_status and never aborts the process.  On an
+ *    error the human-readable reason is available from sw_last_error(h).
+ *  - The library owns all device state of a stream.  Buffers passed in are
+ *    owned by the caller; the library copies what it keeps.
+ *  - "host" pointers point to CPU memory; "device" pointers to memory of the
+ *    current CUDA device.  Arrays are C-contiguous, row-major, float32 or
+ *    int32, indexed by the caller's surfel / node / pixel indices.
+ *  - Work is enqueued on the CUDA stream given at creation.  Calls that
+ *    return data to the host synchronise that stream; the others return
+ *    without waiting for the GPU.
+ *  - A stream handle may be used by one host thread at a time.
+ *  - Units: metres; pixel (x, y) has its centre at integer coordinates.
+ */
+#ifndef SURFELWARP_H
+#define SURFELWARP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_MAX_GN_ITERS 16     /* Sec. 8 caps Gauss-Newton at 10 iterations */
+#define SW_MAX_PCG_ITERS 128
+#define SW_MAX_NODES 65535     /* node ids are packed in 16 bits */
+#define SW_K_SKIN 4            /* nearest nodes per surfel (Eq. 1) */
+#define SW_K_GRAPH 8           /* graph neighbours per node (Eq. 11) */
+
+typedef struct sw_stream* sw_handle;
+
+typedef enum {
+  SW_OK = 0,
+  SW_ERR_INVALID_ARG = 1,       /* a null pointer, a size out of range */
+  SW_ERR_NO_MEMORY = 2,         /* the device-memory budget refused the stream */
+  SW_ERR_NOT_INITIALIZED = 3,   /* no model (sw_set_model) or no depth frame yet */
+  SW_ERR_SOLVER_BREAKDOWN = 4,  /* a 6x6 diagonal block is not positive definite, or pᵀAp <= 0 */
+  SW_ERR_TIMEOUT = 5,           /* a bounded device-side wait gave up */
+  SW_ERR_CUDA = 6               /* a CUDA runtime error; see sw_last_error */
+} sw_status;
+
+/* Parameters of one stream.  Table 1 fixes lambda, fuse_dist, fuse_normal,
+ * stable_conf and recent_frames; corr_dist and corr_normal (the solver's
+ * projective-association thresholds) are not given by the paper. */
+typedef struct {
+  int width, height;            /* depth image size in pixels */
+  float fx, fy, cx, cy;         /* pinhole intrinsics K */
+  int max_surfels, max_nodes;   /* capacity; device memory is sized from these */
+  float lambda;                 /* λ of Eq. 9 (Table 1: 5) */
+  float fuse_dist;              /* δ_distance, metres (Table 1: 1 mm) */
+  float fuse_normal;            /* δ_normal (Table 1: 0.85) */
+  float corr_dist;              /* association distance, metres (0.05) */
+  float corr_normal;            /* association normal dot (0.7) */
+  float stable_conf;            /* δ_stable (Table 1: 10) */
+  int recent_frames;            /* δ_recent (Table 1: 2) */
+  int precision;                /* 0: FP32 residuals/Jacobians/JᵀJ, FP64 PCG dots and 6x6 inversions */
+} sw_params;
+
+/* Per-call statistics of sw_solve_frame; entry i describes Gauss-Newton
+ * iteration i at its linearisation point (before its update). */
+typedef struct {
+  int gn_iters;                         /* iterations run */
+  double e_depth[SW_MAX_GN_ITERS];      /* E_depth of Eq. 10 */
+  double e_reg[SW_MAX_GN_ITERS];        /* λ E_regulation of Eq. 11 */
+  int n_corr[SW_MAX_GN_ITERS];          /* associated (surfel, pixel) pairs */
+  double pcg_rz[SW_MAX_GN_ITERS];       /* final rᵀ M⁻¹ r of the linear solve */
+} sw_solve_stats;
+
+/* Fill *p with Table 1 values and the association defaults for a camera.
+ * Returns SW_ERR_INVALID_ARG for a null p or non-positive sizes. */
+sw_status sw_params_default(sw_params* p, int width, int height, float fx, float fy,
+                            float cx, float cy, int max_surfels, int max_nodes);
+
+/* Create a stream: validate *p, reserve its device memory under the
+ * process-wide budget (SW_ERR_NO_MEMORY if it does not fit) and bind it to
+ * cuda_stream (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the handle; it stays valid until sw_destroy_stream. */
+sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out);
+
+/* Release every device allocation of the stream (synchronises it). */
+sw_status sw_destroy_stream(sw_handle h);
+
+/* Set the process-wide device-memory budget in bytes for sw_create_stream
+ * (0 = unlimited) and read the bytes currently held by all streams. */
+sw_status sw_set_memory_budget(size_t bytes);
+size_t sw_memory_in_use(void);
+
+/* Load the reference surfel model S_ref (= S_live) and the warp-field nodes
+ * (Sec. 3), then initialise as Sec. 6.5 does: node transforms to identity,
+ * 4-NN skinning of every surfel with weights exp(−‖v − p_k‖² / (2 σ_k²))
+ * (Eq. 1), the 8-NN node graph, and the block-sparse pattern of JᵀJ.
+ * Host arrays, caller's order:
+ *   surfel_v4 [n_surfels][4]: x, y, z, radius
+ *   surfel_n4 [n_surfels][4]: nx, ny, nz, confidence
+ *   surfel_t2 [n_surfels][2]: t_init, t_observed (int32; NULL = all 0)
+ *   node4     [n_nodes][4]  : x, y, z, σ
+ * Requires 0 <= n_surfels <= max_surfels and 9 <= n_nodes <= max_nodes.
+ * Synchronous. */
+sw_status sw_set_model(sw_handle h, const float* surfel_v4, const float* surfel_n4,
+                       const int* surfel_t2, int n_surfels, const float* node4, int n_nodes);
+
+/* Upload depth frame `frame_id` (metres, 0 = invalid; [height][width] float32,
+ * host or device memory as on_device says) and compute the depth surfels of
+ * Sec. 5: vertex map V = D K⁻¹ (u, 1), normal map by central differences,
+ * confidence exp(−γ²/(2·0.6²)) and radius √2 d / (f |n_z|) (Eq. 4, |n_z|
+ * clamped at cos 75°).  The frame id becomes t_now. */
+sw_status sw_upload_depth(sw_handle h, const float* depth, int on_device, int frame_id);
+
+/* Estimate the node transforms for the current frame (Sec. 7-8), starting
+ * from the previous frame's: gn_iters Gauss-Newton iterations (1..16), each
+ * re-associating the selected surfels (stable c > δ_stable or recent
+ * t_now − t_obs <= δ_recent) to the depth map, assembling JᵀJ and Jᵀe of
+ * E_depth + λ E_regulation (Eq. 9-11) in a block-sparse 6x6 layout, and
+ * solving JᵀJ Δ = −Jᵀe by pcg_iters (1..128) block-Jacobi PCG iterations.
+ * stats (host, nullable): when given, the call synchronises and fills it.
+ * Returns SW_ERR_SOLVER_BREAKDOWN if a diagonal block was not positive
+ * definite (reported when stats is given or at the next synchronising call). */
+sw_status sw_solve_frame(sw_handle h, int gn_iters, int pcg_iters, sw_solve_stats* stats);
+
+/* Fuse the current depth frame into the model (Sec. 6.1, Eq. 5-6): forward
+ * warp S_ref with the solved field (Eq. 2), render the 4x super-sampled index
+ * map of unsized points, pick per depth pixel the corresponding surfel in its
+ * 4x4 sub-pixel window (δ_distance, δ_normal; highest confidence, then
+ * closest), average it with the depth surfel, and warp the fused surfels back
+ * to the reference frame (Eq. 3). */
+sw_status sw_fuse_frame(sw_handle h);
+
+/* Copy the node state to the host: pos4 [n][4] = x, y, z, σ and dq8 [n][8] =
+ * the dual quaternion (real w x y z, dual w x y z) of each node transform T_j.
+ * cap is the capacity of both arrays in nodes; *n_out receives n_nodes.
+ * Either array may be NULL.  Synchronous. */
+sw_status sw_read_nodes(sw_handle h, float* pos4, float* dq8, int cap, int* n_out);
+
+/* ---------------------------------------------------------------------------
+ * Inspection and test hooks (additions to the paper's interface).  All host
+ * memory, caller's order, synchronous.
+ * ------------------------------------------------------------------------- */
+
+/* Reference surfels: v4 (x y z r), n4 (nx ny nz c), t2 (t_init, t_obs). */
+sw_status sw_read_surfels(sw_handle h, float* v4, float* n4, int* t2, int cap, int* n_out);
+/* Live surfels of the last forward warp (solve or fuse): v4, n4 as above. */
+sw_status sw_read_live_surfels(sw_handle h, float* v4, float* n4, int cap, int* n_out);
+/* Skinning: knn4 [n][4] node ids nearest first (ties: lower id), w4 weights. */
+sw_status sw_read_skinning(sw_handle h, int* knn4, float* w4, int cap, int* n_out);
+/* Node graph: graph8 [n_nodes][8] neighbour ids, nearest first. */
+sw_status sw_read_graph(sw_handle h, int* graph8, int cap);
+/* Depth surfels of the current frame: V4 [H][W][4] = x y z confidence
+ * (confidence 0 = not a usable depth surfel), N4 [H][W][4] = nx ny nz radius. */
+sw_status sw_read_maps(sw_handle h, float* V4, float* N4);
+/* Replace the current frame's depth surfels by the given maps (same layout as
+ * sw_read_maps), so that stages can be checked on fixed FP32 inputs. */
+sw_status sw_debug_set_maps(sw_handle h, const float* V4, const float* N4);
+/* Set every node's dual quaternion (dq8 [n_nodes][8], not re-normalised). */
+sw_status sw_set_node_dq(sw_handle h, const float* dq8, int n_nodes);
+/* Association of the last Gauss-Newton iteration: pixel index y*W+x per
+ * surfel, or -1. */
+sw_status sw_read_correspondence(sw_handle h, int* pix, int cap, int* n_out);
+/* Replace the live surfels (v4: x y z r, n4: nx ny nz c; only xyz are used). */
+sw_status sw_debug_set_live(sw_handle h, const float* v4, const float* n4, int n);
+/* Run projective association on the current live surfels (no warp); the
+ * result is read with sw_read_correspondence. */
+sw_status sw_debug_associate(sw_handle h);
+/* Render the index map of the current live surfels and select each depth
+ * pixel's fusion target without updating anything: target [H*W] caller's
+ * surfel index or -1; imap [4H][4W] caller's surfel index or -1 (nullable). */
+sw_status sw_debug_fusion_targets(sw_handle h, int* target, int* imap);
+/* Assemble JᵀJ and Jᵀe at the current node transforms and maps (one
+ * Gauss-Newton linearisation, no solve).  Sizes: *nnzb_out upper blocks. */
+sw_status sw_debug_assemble(sw_handle h, int* nnzb_out, int* n_corr_out);
+/* Read the last assembled system: rows/cols [nnzb] block coordinates
+ * (row <= col), vals [nnzb][36] row-major 6x6, g [6 n_nodes]. */
+sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, float* g, int cap_blocks);
+
+/* Whole-stream state to and from host memory (checkpoint / resume):
+ * sw_export_state with buf NULL reports the size in *bytes. */
+sw_status sw_export_state(sw_handle h, void* buf, size_t* bytes);
+sw_status sw_import_state(sw_handle h, const void* buf, size_t bytes);
+
+/* Reason of the last error on this handle ("" if none); NULL handle: the last
+ * process-wide error (e.g. of sw_create_stream). */
+const char* sw_last_error(sw_handle h);
+const char* sw_status_string(sw_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SURFELWARP_H */

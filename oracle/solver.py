@@ -290,15 +290,19 @@ def assemble(pattern_keys, n, knn_t, J, r, reg, absolute=False):
     """JᵀJ and Jᵀe of the data terms (rows of ``knn_t``/``J``/``r``) and the
     regulariser terms ``reg`` = (j, i, r, Jj, Ji), accumulated in term order.
 
-    With ``absolute`` the same sums of |J_a|ᵀ|J_b| are returned as well; they
-    are the natural scale of the rounding error of any summation order.
+    With ``absolute`` the sums of |J_a|ᵀ|J_b| and |J_a| |r| are returned as
+    well; they are the natural scale of the rounding error of any summation
+    order.
     """
     A = BlockMatrix(n, pattern_keys)
     S = BlockMatrix(n, pattern_keys) if absolute else None
     g = np.zeros((n, 6))
+    gS = np.zeros((n, 6))
     k = knn_t.shape[1]
     for a in range(k):
         np.add.at(g, knn_t[:, a], J[:, a] * r[:, None])
+        if absolute:
+            np.add.at(gS, knn_t[:, a], np.abs(J[:, a] * r[:, None]))
         for b in range(k):
             blk = J[:, a, :, None] * J[:, b, None, :]
             A.add(knn_t[:, a], knn_t[:, b], blk)
@@ -313,7 +317,11 @@ def assemble(pattern_keys, n, knn_t, J, r, reg, absolute=False):
             S.add(ra, rb, np.einsum('eri,erj->eij', np.abs(Ja), np.abs(Jb)))
     np.add.at(g, j, np.einsum('eri,er->ei', Jj, rr))
     np.add.at(g, i, np.einsum('eri,er->ei', Ji, rr))
-    return (A, g, S) if absolute else (A, g)
+    if absolute:
+        np.add.at(gS, j, np.einsum('eri,er->ei', np.abs(Jj), np.abs(rr)))
+        np.add.at(gS, i, np.einsum('eri,er->ei', np.abs(Ji), np.abs(rr)))
+        return A, g, S, gS
+    return A, g
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,348 @@
+"""Python binding of the SurfelWarp GB300 library (``include/surfelwarp.h``).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, converts numpy arrays / torch tensors to pointers, and raises
+``SwError`` with the library's message when a call returns an error.  All
+computation runs in the CUDA library; if it cannot be loaded, every call
+fails loudly (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsurfelwarp.so")
+
+SW_MAX_GN_ITERS = 16
+SW_MAX_PCG_ITERS = 128
+
+STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_NO_MEMORY", 3: "SW_ERR_NOT_INITIALIZED",
+          4: "SW_ERR_SOLVER_BREAKDOWN", 5: "SW_ERR_TIMEOUT", 6: "SW_ERR_CUDA"}
+
+
+class SwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sw_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("max_surfels", ctypes.c_int), ("max_nodes", ctypes.c_int),
+                ("lambda_", ctypes.c_float), ("fuse_dist", ctypes.c_float), ("fuse_normal", ctypes.c_float),
+                ("corr_dist", ctypes.c_float), ("corr_normal", ctypes.c_float), ("stable_conf", ctypes.c_float),
+                ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class sw_solve_stats(ctypes.Structure):
+    _fields_ = [("gn_iters", ctypes.c_int),
+                ("e_depth", ctypes.c_double * SW_MAX_GN_ITERS),
+                ("e_reg", ctypes.c_double * SW_MAX_GN_ITERS),
+                ("n_corr", ctypes.c_int * SW_MAX_GN_ITERS),
+                ("pcg_rz", ctypes.c_double * SW_MAX_GN_ITERS)]
+
+    def as_dict(self):
+        n = self.gn_iters
+        return {"gn_iters": n, "e_depth": list(self.e_depth[:n]), "e_reg": list(self.e_reg[:n]),
+                "n_corr": list(self.n_corr[:n]), "pcg_rz": list(self.pcg_rz[:n])}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "sw_params_default": [ctypes.POINTER(sw_params), _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, _I, _I],
+    "sw_create_stream": [ctypes.POINTER(sw_params), _P, ctypes.POINTER(_P)],
+    "sw_destroy_stream": [_P],
+    "sw_set_memory_budget": [ctypes.c_size_t],
+    "sw_set_model": [_P, _P, _P, _P, _I, _P, _I],
+    "sw_upload_depth": [_P, _P, _I, _I],
+    "sw_solve_frame": [_P, _I, _I, ctypes.POINTER(sw_solve_stats)],
+    "sw_fuse_frame": [_P],
+    "sw_read_nodes": [_P, _P, _P, _I, ctypes.POINTER(_I)],
+    "sw_read_surfels": [_P, _P, _P, _P, _I, ctypes.POINTER(_I)],
+    "sw_read_live_surfels": [_P, _P, _P, _I, ctypes.POINTER(_I)],
+    "sw_read_skinning": [_P, _P, _P, _I, ctypes.POINTER(_I)],
+    "sw_read_graph": [_P, _P, _I],
+    "sw_read_maps": [_P, _P, _P],
+    "sw_debug_set_maps": [_P, _P, _P],
+    "sw_set_node_dq": [_P, _P, _I],
+    "sw_read_correspondence": [_P, _P, _I, ctypes.POINTER(_I)],
+    "sw_debug_set_live": [_P, _P, _P, _I],
+    "sw_debug_associate": [_P],
+    "sw_debug_fusion_targets": [_P, _P, _P],
+    "sw_debug_assemble": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "sw_debug_read_jtj": [_P, _P, _P, _P, _P, _I],
+    "sw_export_state": [_P, _P, ctypes.POINTER(ctypes.c_size_t)],
+    "sw_import_state": [_P, _P, ctypes.c_size_t],
+}
+
+
+def exported_symbols():
+    """Names of every entry point declared in include/surfelwarp.h."""
+    return sorted(list(_SIGS) + ["sw_memory_in_use", "sw_last_error", "sw_status_string"])
+
+
+def lib():
+    """Load the in-tree CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1904_13073_gb300.build.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sw_memory_in_use.argtypes = []
+        L.sw_memory_in_use.restype = ctypes.c_size_t
+        L.sw_last_error.argtypes = [_P]
+        L.sw_last_error.restype = ctypes.c_char_p
+        L.sw_status_string.argtypes = [_I]
+        L.sw_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().sw_last_error(handle)
+        raise SwError(status, msg.decode() if msg else "")
+
+
+def _ptr(a, dtype=None, shape_last=None):
+    """Pointer of a C-contiguous numpy array (copied to ``dtype`` if needed),
+    or of a torch tensor (data_ptr); None stays None."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if shape_last is not None and arr.shape[-1] != shape_last:
+        raise ValueError(f"expected last dimension {shape_last}, got {arr.shape}")
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+def _pad4(a, w):
+    a = np.asarray(a, dtype=np.float32)
+    if a.ndim == 1:
+        a = a[:, None]
+    out = np.empty((a.shape[0], 4), dtype=np.float32)
+    out[:, :3] = a[:, :3]
+    out[:, 3] = w
+    return out
+
+
+# --------------------------------------------------------------------------- calls
+
+def sw_params_default(width, height, fx, fy, cx, cy, max_surfels, max_nodes):
+    p = sw_params()
+    _check(lib().sw_params_default(ctypes.byref(p), width, height, fx, fy, cx, cy, max_surfels, max_nodes))
+    return p
+
+
+def sw_set_memory_budget(nbytes):
+    _check(lib().sw_set_memory_budget(nbytes))
+
+
+def sw_memory_in_use():
+    return int(lib().sw_memory_in_use())
+
+
+def sw_create_stream(params, cuda_stream=None):
+    """Returns an opaque handle (int).  ``cuda_stream``: a raw cudaStream_t
+    (int), a torch.cuda.Stream, or None for a library-owned stream."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib().sw_create_stream(ctypes.byref(params), ctypes.c_void_p(cuda_stream or 0), ctypes.byref(h)))
+    return h.value
+
+
+def sw_destroy_stream(h):
+    _check(lib().sw_destroy_stream(h), h)
+
+
+def sw_set_model(h, v4, n4, t2, node4):
+    """v4 [n,4] x y z r; n4 [n,4] nx ny nz c; t2 [n,2] int32 or None; node4 [m,4] x y z σ."""
+    pv, v4a = _ptr(v4, np.float32, 4)
+    pn, n4a = _ptr(n4, np.float32, 4)
+    pt, t2a = _ptr(t2, np.int32, 2)
+    pnode, nodea = _ptr(node4, np.float32, 4)
+    n = 0 if v4a is None else v4a.shape[0]
+    _check(lib().sw_set_model(h, pv, pn, pt, n, pnode, nodea.shape[0]), h)
+
+
+def sw_upload_depth(h, depth, frame_id):
+    """depth: numpy (host) or a CUDA torch tensor (device), [H, W] float32."""
+    on_device = hasattr(depth, "is_cuda") and depth.is_cuda
+    if hasattr(depth, "data_ptr") and not on_device:
+        depth = depth.numpy()
+    p, keep = _ptr(depth, np.float32)
+    _check(lib().sw_upload_depth(h, p, int(on_device), int(frame_id)), h)
+    return keep
+
+
+def sw_solve_frame(h, gn_iters, pcg_iters, want_stats=True):
+    st = sw_solve_stats() if want_stats else None
+    _check(lib().sw_solve_frame(h, gn_iters, pcg_iters, ctypes.byref(st) if st is not None else None), h)
+    return st.as_dict() if st is not None else None
+
+
+def sw_fuse_frame(h):
+    _check(lib().sw_fuse_frame(h), h)
+
+
+def _count_nodes(h):
+    n = ctypes.c_int()
+    _check(lib().sw_read_nodes(h, None, None, 0, ctypes.byref(n)), h)
+    return n.value
+
+
+def sw_read_nodes(h):
+    """(pos4 [n,4], dq8 [n,8]) float32."""
+    n = _count_nodes(h)
+    pos = np.empty((n, 4), np.float32)
+    dq = np.empty((n, 8), np.float32)
+    cnt = ctypes.c_int()
+    _check(lib().sw_read_nodes(h, pos.ctypes.data_as(_P), dq.ctypes.data_as(_P), n, ctypes.byref(cnt)), h)
+    return pos, dq
+
+
+def _count_surfels(h):
+    n = ctypes.c_int()
+    _check(lib().sw_read_surfels(h, None, None, None, 1 << 30, ctypes.byref(n)), h)
+    return n.value
+
+
+def sw_read_surfels(h):
+    n = _count_surfels(h)
+    v = np.empty((n, 4), np.float32)
+    nn = np.empty((n, 4), np.float32)
+    t = np.empty((n, 2), np.int32)
+    _check(lib().sw_read_surfels(h, v.ctypes.data_as(_P), nn.ctypes.data_as(_P), t.ctypes.data_as(_P), n, None), h)
+    return v, nn, t
+
+
+def sw_read_live_surfels(h):
+    n = _count_surfels(h)
+    v = np.empty((n, 4), np.float32)
+    nn = np.empty((n, 4), np.float32)
+    _check(lib().sw_read_live_surfels(h, v.ctypes.data_as(_P), nn.ctypes.data_as(_P), n, None), h)
+    return v, nn
+
+
+def sw_read_skinning(h):
+    n = _count_surfels(h)
+    k = np.empty((n, 4), np.int32)
+    w = np.empty((n, 4), np.float32)
+    _check(lib().sw_read_skinning(h, k.ctypes.data_as(_P), w.ctypes.data_as(_P), n, None), h)
+    return k, w
+
+
+def sw_read_graph(h):
+    m = _count_nodes(h)
+    g = np.empty((m, 8), np.int32)
+    _check(lib().sw_read_graph(h, g.ctypes.data_as(_P), m), h)
+    return g
+
+
+def sw_read_maps(h, height, width):
+    V = np.empty((height, width, 4), np.float32)
+    N = np.empty((height, width, 4), np.float32)
+    _check(lib().sw_read_maps(h, V.ctypes.data_as(_P), N.ctypes.data_as(_P)), h)
+    return V, N
+
+
+def sw_debug_set_maps(h, V4, N4):
+    pV, a = _ptr(V4, np.float32)
+    pN, b = _ptr(N4, np.float32)
+    _check(lib().sw_debug_set_maps(h, pV, pN), h)
+
+
+def sw_set_node_dq(h, dq8):
+    p, a = _ptr(dq8, np.float32, 8)
+    _check(lib().sw_set_node_dq(h, p, a.shape[0]), h)
+
+
+def sw_read_correspondence(h):
+    n = _count_surfels(h)
+    pix = np.empty(n, np.int32)
+    _check(lib().sw_read_correspondence(h, pix.ctypes.data_as(_P), n, None), h)
+    return pix
+
+
+def sw_debug_set_live(h, v, n):
+    pv, a = _ptr(_pad4(v, 0.0))
+    pn, b = _ptr(_pad4(n, 0.0))
+    _check(lib().sw_debug_set_live(h, pv, pn, a.shape[0]), h)
+
+
+def sw_debug_associate(h):
+    _check(lib().sw_debug_associate(h), h)
+
+
+def sw_debug_fusion_targets(h, height, width):
+    t = np.empty(height * width, np.int32)
+    im = np.empty((4 * height, 4 * width), np.int32)
+    _check(lib().sw_debug_fusion_targets(h, t.ctypes.data_as(_P), im.ctypes.data_as(_P)), h)
+    return t, im
+
+
+def sw_debug_assemble(h):
+    nb, nc = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sw_debug_assemble(h, ctypes.byref(nb), ctypes.byref(nc)), h)
+    return nb.value, nc.value
+
+
+def sw_debug_read_jtj(h, nnzb, n_nodes):
+    rows = np.empty(nnzb, np.int32)
+    cols = np.empty(nnzb, np.int32)
+    vals = np.empty((nnzb, 6, 6), np.float32)
+    g = np.empty(6 * n_nodes, np.float32)
+    _check(lib().sw_debug_read_jtj(h, rows.ctypes.data_as(_P), cols.ctypes.data_as(_P), vals.ctypes.data_as(_P),
+                                   g.ctypes.data_as(_P), nnzb), h)
+    return rows, cols, vals, g
+
+
+def sw_export_state(h):
+    n = ctypes.c_size_t()
+    _check(lib().sw_export_state(h, None, ctypes.byref(n)), h)
+    buf = np.empty(n.value, np.uint8)
+    _check(lib().sw_export_state(h, buf.ctypes.data_as(_P), ctypes.byref(n)), h)
+    return buf
+
+
+def sw_import_state(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().sw_import_state(h, buf.ctypes.data_as(_P), buf.size), h)
+
+
+def sw_last_error(h=None):
+    m = lib().sw_last_error(h)
+    return m.decode() if m else ""
+
+
+def sw_status_string(status):
+    return lib().sw_status_string(status).decode()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def params_for(cam, n_surfels, n_nodes, **over):
+    """sw_params for a synth.Camera-like object with Table 1 defaults."""
+    p = sw_params_default(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, max(1, n_surfels), n_nodes)
+    for k, v in over.items():
+        setattr(p, "lambda_" if k == "lam" else k, v)
+    return p
+
+
+def model_arrays(scene):
+    """(v4, n4, t2, node4) of a synth.Scene in the library's layout."""
+    return (_pad4(scene.surfel_v, scene.surfel_r), _pad4(scene.surfel_n, scene.surfel_c),
+            np.ascontiguousarray(scene.surfel_t, dtype=np.int32), _pad4(scene.node_p, scene.node_sigma))

@@ -1,0 +1,906 @@
+// C ABI of the SurfelWarp hot path: stream lifecycle, device memory under a
+// process-wide budget, model set-up (skinning, node graph, the block-sparse
+// pattern of JᵀJ), the per-frame calls and the inspection hooks.
+//
+// Model set-up sorts the surfels by their 4-node set on the GPU (CUB radix
+// sort), so that surfels that contribute to the same ten JᵀJ blocks are
+// adjacent; the node-level structure (pattern of 6x6 blocks, graph in-edges,
+// the transposed-block lists of the SpMV) is O(nodes + node sets) and is
+// built on the host once per model.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sw_internal.h"
+
+using namespace sw;
+
+// ------------------------------------------------------------------ errors / memory
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_last_error;
+std::atomic<size_t> g_budget{0};
+std::atomic<size_t> g_in_use{0};
+
+void set_global_error(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_last_error = s;
+}
+
+}  // namespace
+
+struct sw_stream {
+  sw_params p{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  bool has_model = false;
+  bool has_depth = false;
+  std::string err;
+  // device memory
+  std::vector<std::pair<void*, size_t>> allocs;   // fixed arena pieces
+  std::vector<std::pair<void*, size_t>> model_allocs;
+  SwDev h{};            // host mirror of the descriptor
+  SwDev* dev = nullptr; // device copy
+  int* tile_dev = nullptr;   // kTileKinds x 2 ints
+  int4* knn_dist = nullptr;  // skinning in distance order, caller's order (inspection, checkpoint)
+  float4* w_dist = nullptr;
+  BatchHost bh{};
+  std::map<std::pair<int, int>, cudaGraphExec_t> solve_graphs;
+  cudaGraph_t fuse_graph_dummy = nullptr;
+};
+
+namespace {
+
+sw_status fail(sw_stream* s, sw_status code, const std::string& msg) {
+  if (s) s->err = msg; else set_global_error(msg);
+  return code;
+}
+
+#define SW_CUDA(s, call)                                                          \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail((s), SW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool reserve(size_t bytes) {
+  const size_t budget = g_budget.load();
+  size_t cur = g_in_use.load();
+  do {
+    if (budget && cur + bytes > budget) return false;
+  } while (!g_in_use.compare_exchange_weak(cur, cur + bytes));
+  return true;
+}
+
+sw_status dalloc(sw_stream* s, std::vector<std::pair<void*, size_t>>& list, void** out, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  if (!reserve(bytes)) return fail(s, SW_ERR_NO_MEMORY, "device memory budget exceeded");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    g_in_use -= bytes;
+    return fail(s, e == cudaErrorMemoryAllocation ? SW_ERR_NO_MEMORY : SW_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  list.emplace_back(p, bytes);
+  *out = p;
+  return SW_OK;
+}
+
+void free_list(std::vector<std::pair<void*, size_t>>& list) {
+  for (auto& a : list) {
+    cudaFree(a.first);
+    g_in_use -= a.second;
+  }
+  list.clear();
+}
+
+template <typename T>
+sw_status A(sw_stream* s, T** out, size_t count, bool model = false) {
+  return dalloc(s, model ? s->model_allocs : s->allocs, reinterpret_cast<void**>(out), count * sizeof(T));
+}
+
+#define SW_TRY(expr)                    \
+  do {                                  \
+    sw_status st_ = (expr);             \
+    if (st_ != SW_OK) return st_;       \
+  } while (0)
+
+void drop_graphs(sw_stream* s) {
+  for (auto& kv : s->solve_graphs) cudaGraphExecDestroy(kv.second);
+  s->solve_graphs.clear();
+}
+
+// Push the host descriptor and the one-stream tile tables to the device.
+sw_status sync_desc(sw_stream* s) {
+  int tiles[kTileKinds * 2];
+  for (int k = 0; k < kTileKinds; ++k) {
+    tiles[2 * k] = 0;
+    tiles[2 * k + 1] = tiles_for(k, s->h);
+    s->bh.total_tiles[k] = tiles[2 * k + 1];
+    s->bh.tile_base_dev[k] = s->tile_dev + 2 * k;
+  }
+  SW_CUDA(s, cudaMemcpyAsync(s->tile_dev, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaMemcpyAsync(s->dev, &s->h, sizeof(SwDev), cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  s->bh.bt.devs = s->dev;
+  s->bh.bt.n_streams = 1;
+  drop_graphs(s);
+  return SW_OK;
+}
+
+bool params_ok(const sw_params* p, std::string& why) {
+  if (!p) { why = "null params"; return false; }
+  if (p->width < 3 || p->height < 3 || p->width > 16384 || p->height > 16384) { why = "image size out of range"; return false; }
+  if (!(p->fx > 0 && p->fy > 0)) { why = "focal lengths must be positive"; return false; }
+  if (p->max_surfels < 0 || p->max_surfels > (1 << 28)) { why = "max_surfels out of range"; return false; }
+  if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
+  if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
+  if (p->precision != 0) { why = "only precision 0 (FP32 assembly, FP64 PCG reductions) is built"; return false; }
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ set-up kernels
+
+namespace {
+
+__global__ void k_set_keys(const int4* __restrict__ knn, int n, unsigned long long* keys, int* vals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 k = knn[i];
+  int a[4] = {k.x, k.y, k.z, k.w};
+  // sort 4 ids ascending
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3 - x; ++y)
+      if (a[y] > a[y + 1]) { const int t = a[y]; a[y] = a[y + 1]; a[y + 1] = t; }
+  keys[i] = ((unsigned long long)a[0] << 48) | ((unsigned long long)a[1] << 32) |
+            ((unsigned long long)a[2] << 16) | (unsigned long long)a[3];
+  vals[i] = i;
+}
+
+__global__ void k_gather_model(SwDev d, const unsigned long long* __restrict__ keys, const int* __restrict__ perm,
+                               const float4* __restrict__ tv, const float4* __restrict__ tn,
+                               const int2* __restrict__ tt, const int4* __restrict__ tknn,
+                               const float4* __restrict__ tw, int* __restrict__ head) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_s) return;
+  const int o = perm[i];
+  d.v_ref[i] = tv[o];
+  d.n_ref[i] = tn[o];
+  d.tt[i] = tt[o];
+  d.orig_id[i] = o;
+  d.inv_perm[o] = i;
+  const int4 k = tknn[o];
+  const float4 w = tw[o];
+  int id[4] = {k.x, k.y, k.z, k.w};
+  float ww[4] = {w.x, w.y, w.z, w.w};
+  int slot0 = 0;   // tracks where the nearest node (distance slot 0) goes
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3 - x; ++y)
+      if (id[y] > id[y + 1]) {
+        const int t = id[y]; id[y] = id[y + 1]; id[y + 1] = t;
+        const float u = ww[y]; ww[y] = ww[y + 1]; ww[y + 1] = u;
+        if (slot0 == y) slot0 = y + 1; else if (slot0 == y + 1) slot0 = y;
+      }
+  d.knn[i] = make_int4(id[0], id[1], id[2], id[3]);
+  d.w[i] = make_float4(ww[0], ww[1], ww[2], ww[3]);
+  d.ref_slot[i] = slot0;
+  head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_set_nodes(SwDev d, const int* __restrict__ head, int4* __restrict__ set_nodes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_s) return;
+  if (head[i]) set_nodes[d.set_id[i]] = d.knn[i];
+}
+
+__global__ void k_minus_one(int* a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] -= 1;
+}
+
+__global__ void k_identity_dq(float4* dq, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  dq[2 * j] = make_float4(1.f, 0.f, 0.f, 0.f);
+  dq[2 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_set_frame(SwDev* dev, int t) { dev->t_now = t; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ public API
+
+// Definitions take C linkage from their declarations in surfelwarp.h.
+
+sw_status sw_params_default(sw_params* p, int width, int height, float fx, float fy, float cx, float cy,
+                            int max_surfels, int max_nodes) {
+  if (!p || width <= 0 || height <= 0) return fail(nullptr, SW_ERR_INVALID_ARG, "bad sw_params_default arguments");
+  std::memset(p, 0, sizeof(*p));
+  p->width = width; p->height = height;
+  p->fx = fx; p->fy = fy; p->cx = cx; p->cy = cy;
+  p->max_surfels = max_surfels; p->max_nodes = max_nodes;
+  p->lambda = 5.f;          // Table 1
+  p->fuse_dist = 1e-3f;     // Table 1
+  p->fuse_normal = 0.85f;   // Table 1
+  p->corr_dist = 0.05f;
+  p->corr_normal = 0.7f;
+  p->stable_conf = 10.f;    // Table 1
+  p->recent_frames = 2;     // Table 1
+  p->precision = 0;
+  return SW_OK;
+}
+
+sw_status sw_set_memory_budget(size_t bytes) {
+  g_budget = bytes;
+  return SW_OK;
+}
+
+size_t sw_memory_in_use(void) { return g_in_use.load(); }
+
+sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out) {
+  std::string why;
+  if (!out) return fail(nullptr, SW_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  if (!params_ok(p, why)) return fail(nullptr, SW_ERR_INVALID_ARG, why);
+  sw_stream* s = new sw_stream();
+  s->p = *p;
+  auto cleanup = [&](sw_status code) {
+    const std::string msg = s->err;
+    free_list(s->allocs);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+    set_global_error(msg);
+    return code;
+  };
+  if (cuda_stream) {
+    s->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      s->err = "cudaStreamCreate failed";
+      return cleanup(SW_ERR_CUDA);
+    }
+    s->own_stream = true;
+  }
+  SwDev& h = s->h;
+  h.W = p->width; h.H = p->height;
+  h.fx = p->fx; h.fy = p->fy; h.cx = p->cx; h.cy = p->cy;
+  h.sqrt_lambda = std::sqrt(p->lambda);
+  h.corr_dist = p->corr_dist; h.corr_normal = p->corr_normal;
+  h.fuse_dist = p->fuse_dist; h.fuse_normal = p->fuse_normal;
+  h.stable_conf = p->stable_conf; h.recent_frames = p->recent_frames;
+  const size_t ns = std::max(1, p->max_surfels), nn = p->max_nodes, np = (size_t)p->width * p->height;
+  sw_status st = SW_OK;
+#define ALLOC(ptr, count) if (st == SW_OK) st = A(s, &(ptr), (count))
+  ALLOC(h.v_ref, ns); ALLOC(h.n_ref, ns); ALLOC(h.tt, ns); ALLOC(h.knn, ns); ALLOC(h.w, ns);
+  ALLOC(h.ref_slot, ns); ALLOC(h.set_id, ns); ALLOC(h.orig_id, ns); ALLOC(h.inv_perm, ns);
+  ALLOC(h.v_live, ns); ALLOC(h.n_live, ns); ALLOC(h.corr_pix, ns);
+  ALLOC(h.node_p, nn); ALLOC(h.dq, 2 * nn); ALLOC(h.graph, SW_K_GRAPH * nn);
+  ALLOC(h.in_ptr, nn + 1); ALLOC(h.in_src, SW_K_GRAPH * nn);
+  ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
+  ALLOC(h.row_ptr, nn + 1); ALLOC(h.low_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Minv, 36 * nn);
+  ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
+  ALLOC(h.q, 6 * nn); ALLOC(h.red, kRedSlots);
+  ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
+  ALLOC(h.status, 1);
+  ALLOC(s->dev, 1); ALLOC(s->tile_dev, 2 * kTileKinds);
+#undef ALLOC
+  if (st != SW_OK) return cleanup(st);
+  if (cudaMemsetAsync(h.status, 0, sizeof(int), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.vmap, 0, np * sizeof(float4), s->st) != cudaSuccess) {
+    s->err = "cudaMemset failed";
+    return cleanup(SW_ERR_CUDA);
+  }
+  if (sync_desc(s) != SW_OK) return cleanup(SW_ERR_CUDA);
+  *out = s;
+  return SW_OK;
+}
+
+sw_status sw_destroy_stream(sw_handle s) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  cudaStreamSynchronize(s->st);
+  drop_graphs(s);
+  free_list(s->model_allocs);
+  free_list(s->allocs);
+  if (s->own_stream) cudaStreamDestroy(s->st);
+  delete s;
+  return SW_OK;
+}
+
+namespace {
+
+// temporary device buffer freed at scope exit (set-up only)
+struct Tmp {
+  void* p = nullptr;
+  explicit Tmp(size_t bytes) { if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) p = nullptr; }
+  ~Tmp() { if (p) cudaFree(p); }
+  template <typename T> T* as() { return reinterpret_cast<T*>(p); }
+};
+
+struct Pattern {
+  std::vector<int> row_ptr, col, blk_row, blk_edge, low_ptr, low_blk, in_ptr, in_src, set_slots;
+};
+
+// Block-sparse pattern of JᵀJ: upper blocks (a <= b) of every node pair that
+// shares a surfel's 4-node set, every graph edge and every diagonal block.
+bool build_pattern(int n_n, const std::vector<int4>& sets, const std::vector<int>& graph, Pattern& P,
+                   std::string& why) {
+  std::vector<uint32_t> keys;
+  keys.reserve(sets.size() * 10 + (size_t)n_n * 9);
+  for (int j = 0; j < n_n; ++j) keys.push_back(((uint32_t)j << 16) | (uint32_t)j);
+  for (const int4& s : sets) {
+    const int id[4] = {s.x, s.y, s.z, s.w};
+    for (int a = 0; a < 4; ++a)
+      for (int b = a; b < 4; ++b) keys.push_back(((uint32_t)id[a] << 16) | (uint32_t)id[b]);
+  }
+  for (int j = 0; j < n_n; ++j)
+    for (int e = 0; e < SW_K_GRAPH; ++e) {
+      const int i = graph[(size_t)j * SW_K_GRAPH + e];
+      if (i < 0 || i >= n_n) { why = "node graph index out of range"; return false; }
+      const int a = std::min(i, j), b = std::max(i, j);
+      keys.push_back(((uint32_t)a << 16) | (uint32_t)b);
+    }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  const int nb = (int)keys.size();
+  P.col.resize(nb); P.blk_row.resize(nb); P.blk_edge.assign(nb, 0);
+  P.row_ptr.assign(n_n + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    P.blk_row[b] = (int)(keys[b] >> 16);
+    P.col[b] = (int)(keys[b] & 0xffff);
+    P.row_ptr[P.blk_row[b] + 1]++;
+  }
+  for (int j = 0; j < n_n; ++j) P.row_ptr[j + 1] += P.row_ptr[j];
+  auto find = [&](int a, int b) {
+    const uint32_t key = ((uint32_t)a << 16) | (uint32_t)b;
+    return (int)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+  };
+  // graph edges: flags on off-diagonal blocks; in-edge lists sorted by source
+  std::vector<std::vector<int>> in(n_n);
+  for (int j = 0; j < n_n; ++j)
+    for (int e = 0; e < SW_K_GRAPH; ++e) {
+      const int i = graph[(size_t)j * SW_K_GRAPH + e];
+      in[i].push_back(j);
+      if (i == j) continue;
+      const int b = find(std::min(i, j), std::max(i, j));
+      P.blk_edge[b] |= (j < i) ? 1 : 2;   // bit0: edge row->col
+    }
+  P.in_ptr.assign(n_n + 1, 0);
+  P.in_src.clear();
+  for (int j = 0; j < n_n; ++j) {
+    std::sort(in[j].begin(), in[j].end());
+    P.in_src.insert(P.in_src.end(), in[j].begin(), in[j].end());
+    P.in_ptr[j + 1] = (int)P.in_src.size();
+  }
+  // transposed-block lists: for row i the blocks (j, i) with j < i
+  std::vector<std::vector<int>> low(n_n);
+  for (int b = 0; b < nb; ++b)
+    if (P.blk_row[b] != P.col[b]) low[P.col[b]].push_back(b);
+  P.low_ptr.assign(n_n + 1, 0);
+  P.low_blk.clear();
+  for (int i = 0; i < n_n; ++i) {
+    P.low_blk.insert(P.low_blk.end(), low[i].begin(), low[i].end());
+    P.low_ptr[i + 1] = (int)P.low_blk.size();
+  }
+  // per set: 10 upper blocks in (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3) order + 4 node ids
+  P.set_slots.resize(sets.size() * 14);
+  for (size_t s = 0; s < sets.size(); ++s) {
+    const int id[4] = {sets[s].x, sets[s].y, sets[s].z, sets[s].w};
+    int k = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a; b < 4; ++b) P.set_slots[s * 14 + k++] = find(id[a], id[b]);
+    for (int a = 0; a < 4; ++a) P.set_slots[s * 14 + 10 + a] = id[a];
+  }
+  return true;
+}
+
+template <typename T>
+sw_status upload_vec(sw_stream* s, T** dst, const std::vector<T>& v) {
+  SW_TRY(A(s, dst, std::max<size_t>(1, v.size()), true));
+  if (!v.empty()) SW_CUDA(s, cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s->st));
+  return SW_OK;
+}
+
+}  // namespace
+
+namespace {
+sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const int* t2, int n_s, const float* node4,
+                         int n_n, const int* knn_in, const float* w_in) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (n_s < 0 || n_s > s->p.max_surfels) return fail(s, SW_ERR_INVALID_ARG, "n_surfels out of range");
+  if (n_n < SW_K_GRAPH + 1 || n_n > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "n_nodes out of range");
+  if ((n_s > 0 && (!v4 || !n4)) || !node4) return fail(s, SW_ERR_INVALID_ARG, "null model array");
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  drop_graphs(s);
+  free_list(s->model_allocs);
+  SwDev& h = s->h;
+  h.n_s = n_s; h.n_n = n_n;
+  cudaStream_t st = s->st;
+  // nodes, identity transforms, graph
+  SW_CUDA(s, cudaMemcpyAsync(h.node_p, node4, (size_t)n_n * sizeof(float4), cudaMemcpyHostToDevice, st));
+  k_identity_dq<<<(n_n + 127) / 128, 128, 0, st>>>(h.dq, n_n);
+  launch_node_graph(h, st);
+  std::vector<int> graph((size_t)n_n * SW_K_GRAPH);
+  SW_CUDA(s, cudaMemcpyAsync(graph.data(), h.graph, graph.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+
+  std::vector<int4> sets;
+  if (n_s > 0) {
+    const size_t n = n_s;
+    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(n * 16), d2(n * 16), keys(n * 8),
+        keys2(n * 8), vals(n * 4), perm(n * 4), head(n * 4);
+    if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p || !keys.p || !keys2.p || !vals.p ||
+        !perm.p || !head.p)
+      return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
+    SW_CUDA(s, cudaMemcpyAsync(tv.p, v4, n * 16, cudaMemcpyHostToDevice, st));
+    SW_CUDA(s, cudaMemcpyAsync(tn.p, n4, n * 16, cudaMemcpyHostToDevice, st));
+    if (t2) SW_CUDA(s, cudaMemcpyAsync(tt.p, t2, n * 8, cudaMemcpyHostToDevice, st));
+    else SW_CUDA(s, cudaMemsetAsync(tt.p, 0, n * 8, st));
+    if (knn_in) {
+      SW_CUDA(s, cudaMemcpyAsync(tknn.p, knn_in, n * 16, cudaMemcpyHostToDevice, st));
+      SW_CUDA(s, cudaMemcpyAsync(tw.p, w_in, n * 16, cudaMemcpyHostToDevice, st));
+    } else {
+      launch_knn_skin(h, tv.as<float4>(), n_s, ids.as<int>(), d2.as<float>(), tknn.as<int4>(), tw.as<float4>(), st);
+    }
+    SW_TRY(A(s, &s->knn_dist, n, true));
+    SW_TRY(A(s, &s->w_dist, n, true));
+    SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn.p, n * 16, cudaMemcpyDeviceToDevice, st));
+    SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw.p, n * 16, cudaMemcpyDeviceToDevice, st));
+    k_set_keys<<<(n_s + 255) / 256, 256, 0, st>>>(tknn.as<int4>(), n_s, keys.as<unsigned long long>(), vals.as<int>());
+    size_t tmp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(),
+                                    keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
+    {
+      Tmp cubtmp(tmp_bytes);
+      if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
+      SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, tmp_bytes, keys.as<unsigned long long>(),
+                                                 keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(),
+                                                 n_s, 0, 64, st));
+      k_gather_model<<<(n_s + 255) / 256, 256, 0, st>>>(h, keys2.as<unsigned long long>(), perm.as<int>(),
+                                                        tv.as<float4>(), tn.as<float4>(), tt.as<int2>(),
+                                                        tknn.as<int4>(), tw.as<float4>(), head.as<int>());
+      size_t scan_bytes = 0;
+      cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
+      Tmp scantmp(scan_bytes);
+      if (!scantmp.p) return fail(s, SW_ERR_NO_MEMORY, "scan scratch allocation failed");
+      SW_CUDA(s, cub::DeviceScan::InclusiveSum(scantmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
+      k_minus_one<<<(n_s + 255) / 256, 256, 0, st>>>(h.set_id, n_s);
+      int last = 0;
+      SW_CUDA(s, cudaMemcpyAsync(&last, h.set_id + n_s - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(s, cudaStreamSynchronize(st));
+      const int n_sets = last + 1;
+      Tmp setn((size_t)n_sets * 16);
+      if (!setn.p) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
+      k_set_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(h, head.as<int>(), setn.as<int4>());
+      sets.resize(n_sets);
+      SW_CUDA(s, cudaMemcpyAsync(sets.data(), setn.p, (size_t)n_sets * 16, cudaMemcpyDeviceToHost, st));
+      SW_CUDA(s, cudaStreamSynchronize(st));
+    }
+  } else {
+    SW_CUDA(s, cudaStreamSynchronize(st));
+  }
+  Pattern P;
+  std::string why;
+  if (!build_pattern(n_n, sets, graph, P, why)) return fail(s, SW_ERR_INVALID_ARG, why);
+  h.n_sets = (int)sets.size();
+  h.nnzb = (int)P.col.size();
+  SW_CUDA(s, cudaMemcpyAsync(h.row_ptr, P.row_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  SW_CUDA(s, cudaMemcpyAsync(h.low_ptr, P.low_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  SW_CUDA(s, cudaMemcpyAsync(h.in_ptr, P.in_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  SW_CUDA(s, cudaMemcpyAsync(h.in_src, P.in_src.data(), P.in_src.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  SW_TRY(upload_vec(s, &h.col, P.col));
+  SW_TRY(upload_vec(s, &h.blk_row, P.blk_row));
+  SW_TRY(upload_vec(s, &h.blk_edge, P.blk_edge));
+  SW_TRY(upload_vec(s, &h.low_blk, P.low_blk));
+  SW_TRY(upload_vec(s, &h.set_slots, P.set_slots));
+  SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
+  SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
+  SW_CUDA(s, cudaMemsetAsync(h.g, 0, (size_t)n_n * 6 * sizeof(float), st));
+  SW_CUDA(s, cudaMemsetAsync(h.corr_pix, 0xff, (size_t)std::max(1, n_s) * sizeof(int), st));
+  SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
+  SW_TRY(sync_desc(s));
+  launch_warp_live(s->bh, st);
+  SW_CUDA(s, cudaGetLastError());
+  SW_CUDA(s, cudaStreamSynchronize(st));
+  s->has_model = true;
+  return SW_OK;
+}
+}  // namespace
+
+sw_status sw_set_model(sw_handle s, const float* v4, const float* n4, const int* t2, int n_s, const float* node4,
+                       int n_n) {
+  return set_model_impl(s, v4, n4, t2, n_s, node4, n_n, nullptr, nullptr);
+}
+
+sw_status sw_upload_depth(sw_handle s, const float* depth, int on_device, int frame_id) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!depth) return fail(s, SW_ERR_INVALID_ARG, "null depth");
+  const size_t bytes = (size_t)s->h.W * s->h.H * sizeof(float);
+  if (on_device && s->own_stream) SW_CUDA(s, cudaStreamSynchronize(0));   // order after the caller's default-stream work
+  SW_CUDA(s, cudaMemcpyAsync(s->h.depth, depth, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             s->st));
+  s->h.t_now = frame_id;
+  k_set_frame<<<1, 1, 0, s->st>>>(s->dev, frame_id);
+  launch_depth_maps(s->bh, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  s->has_depth = true;
+  return SW_OK;
+}
+
+namespace {
+
+sw_status enqueue_solve(sw_stream* s, int gn, int pcg) {
+  cudaStream_t st = s->st;
+  const SwDev& h = s->h;
+  SW_CUDA(s, cudaMemsetAsync(h.e_depth, 0, kMaxGn * sizeof(double), st));
+  SW_CUDA(s, cudaMemsetAsync(h.e_reg, 0, kMaxGn * sizeof(double), st));
+  SW_CUDA(s, cudaMemsetAsync(h.n_corr, 0, kMaxGn * sizeof(int), st));
+  SW_CUDA(s, cudaMemsetAsync(h.pcg_rz, 0, kMaxGn * sizeof(double), st));
+  SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
+  for (int it = 0; it < gn; ++it) {
+    launch_reg_assemble(s->bh, it, st);
+    launch_data_assemble(s->bh, it, st);
+    launch_pcg_init(s->bh, st);
+    for (int k = 0; k < pcg; ++k) {
+      launch_pcg_spmv(s->bh, k, st);
+      launch_pcg_update(s->bh, k, st);
+    }
+    launch_apply_update(s->bh, it, pcg, st);
+  }
+  SW_CUDA(s, cudaGetLastError());
+  return SW_OK;
+}
+
+sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
+  int status = 0;
+  SW_CUDA(s, cudaMemcpyAsync(&status, s->h.status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->gn_iters = gn;
+    SW_CUDA(s, cudaMemcpyAsync(out->e_depth, s->h.e_depth, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaMemcpyAsync(out->e_reg, s->h.e_reg, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaMemcpyAsync(out->n_corr, s->h.n_corr, kMaxGn * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaMemcpyAsync(out->pcg_rz, s->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  }
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (status & kStatusBreakdown) return fail(s, SW_ERR_SOLVER_BREAKDOWN, "a diagonal block is not positive definite or pᵀAp <= 0");
+  return SW_OK;
+}
+
+}  // namespace
+
+sw_status sw_solve_frame(sw_handle s, int gn_iters, int pcg_iters, sw_solve_stats* stats) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "solve needs a model and a depth frame");
+  if (gn_iters < 1 || gn_iters > kMaxGn || pcg_iters < 1 || pcg_iters > kMaxPcg)
+    return fail(s, SW_ERR_INVALID_ARG, "iteration counts out of range");
+  const auto key = std::make_pair(gn_iters, pcg_iters);
+  auto itg = s->solve_graphs.find(key);
+  if (itg == s->solve_graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    SW_CUDA(s, cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    const sw_status e = enqueue_solve(s, gn_iters, pcg_iters);
+    const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    if (e != SW_OK) { if (graph) cudaGraphDestroy(graph); return e; }
+    if (ce != cudaSuccess) return fail(s, SW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(s, SW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    itg = s->solve_graphs.emplace(key, exec).first;
+  }
+  SW_CUDA(s, cudaGraphLaunch(itg->second, s->st));
+  if (stats) return read_stats(s, gn_iters, stats);
+  return SW_OK;
+}
+
+sw_status sw_fuse_frame(sw_handle s) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "fusion needs a model and a depth frame");
+  cudaStream_t st = s->st;
+  launch_warp_live(s->bh, st);
+  SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, (size_t)16 * s->h.W * s->h.H * sizeof(unsigned long long), st));
+  launch_index_map(s->bh, st);
+  launch_fuse(s->bh, 0, st);
+  SW_CUDA(s, cudaGetLastError());
+  return SW_OK;
+}
+
+sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_out) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  const int n = s->h.n_n;
+  if (n_out) *n_out = n;
+  if ((pos4 || dq8) && cap < n) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
+  if (pos4) SW_CUDA(s, cudaMemcpyAsync(pos4, s->h.node_p, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st));
+  if (dq8) SW_CUDA(s, cudaMemcpyAsync(dq8, s->h.dq, (size_t)n * 32, cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  int status = 0;
+  SW_CUDA(s, cudaMemcpy(&status, s->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status & kStatusBreakdown) return fail(s, SW_ERR_SOLVER_BREAKDOWN, "the last solve broke down");
+  return SW_OK;
+}
+
+// ------------------------------------------------------------------ inspection hooks
+
+namespace {
+
+template <typename T>
+sw_status d2h_perm(sw_stream* s, const T* dev, T* host, int per, bool permute) {
+  const int n = s->h.n_s;
+  std::vector<T> buf((size_t)n * per);
+  if (n) SW_CUDA(s, cudaMemcpyAsync(buf.data(), dev, buf.size() * sizeof(T), cudaMemcpyDeviceToHost, s->st));
+  std::vector<int> orig(n);
+  if (n && permute) SW_CUDA(s, cudaMemcpyAsync(orig.data(), s->h.orig_id, n * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  for (int i = 0; i < n; ++i) {
+    const int o = permute ? orig[i] : i;
+    std::memcpy(host + (size_t)o * per, buf.data() + (size_t)i * per, per * sizeof(T));
+  }
+  return SW_OK;
+}
+
+template <typename T>
+sw_status h2d_perm(sw_stream* s, const T* host, T* dev, int per) {
+  const int n = s->h.n_s;
+  std::vector<int> orig(n);
+  if (n) SW_CUDA(s, cudaMemcpy(orig.data(), s->h.orig_id, n * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<T> buf((size_t)n * per);
+  for (int i = 0; i < n; ++i) std::memcpy(buf.data() + (size_t)i * per, host + (size_t)orig[i] * per, per * sizeof(T));
+  if (n) SW_CUDA(s, cudaMemcpyAsync(dev, buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status need_model(sw_stream* s, int cap) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  if (cap < s->h.n_s) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
+  return SW_OK;
+}
+
+}  // namespace
+
+sw_status sw_read_surfels(sw_handle s, float* v4, float* n4, int* t2, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  if (n_out) *n_out = s->h.n_s;
+  if (v4) SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.v_ref), v4, 4, true));
+  if (n4) SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.n_ref), n4, 4, true));
+  if (t2) SW_TRY(d2h_perm(s, reinterpret_cast<const int*>(s->h.tt), t2, 2, true));
+  return SW_OK;
+}
+
+sw_status sw_read_live_surfels(sw_handle s, float* v4, float* n4, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  if (n_out) *n_out = s->h.n_s;
+  if (v4) SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.v_live), v4, 4, true));
+  if (n4) SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.n_live), n4, 4, true));
+  return SW_OK;
+}
+
+sw_status sw_read_skinning(sw_handle s, int* knn4, float* w4, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  const int n = s->h.n_s;
+  if (n_out) *n_out = n;
+  if (knn4 && n) SW_CUDA(s, cudaMemcpyAsync(knn4, s->knn_dist, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st));
+  if (w4 && n) SW_CUDA(s, cudaMemcpyAsync(w4, s->w_dist, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_read_graph(sw_handle s, int* graph8, int cap) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  if (!graph8 || cap < s->h.n_n) return fail(s, SW_ERR_INVALID_ARG, "bad graph buffer");
+  SW_CUDA(s, cudaMemcpyAsync(graph8, s->h.graph, (size_t)s->h.n_n * SW_K_GRAPH * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_read_maps(sw_handle s, float* V4, float* N4) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
+  const size_t np = (size_t)s->h.W * s->h.H;
+  if (V4) SW_CUDA(s, cudaMemcpyAsync(V4, s->h.vmap, np * 16, cudaMemcpyDeviceToHost, s->st));
+  if (N4) SW_CUDA(s, cudaMemcpyAsync(N4, s->h.nmap, np * 16, cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_debug_set_maps(sw_handle s, const float* V4, const float* N4) {
+  if (!s || !V4 || !N4) return fail(s, SW_ERR_INVALID_ARG, "null argument");
+  const size_t np = (size_t)s->h.W * s->h.H;
+  SW_CUDA(s, cudaMemcpyAsync(s->h.vmap, V4, np * 16, cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaMemcpyAsync(s->h.nmap, N4, np * 16, cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  s->has_depth = true;
+  return SW_OK;
+}
+
+sw_status sw_set_node_dq(sw_handle s, const float* dq8, int n) {
+  if (!s || !dq8) return fail(s, SW_ERR_INVALID_ARG, "null argument");
+  if (!s->has_model || n != s->h.n_n) return fail(s, SW_ERR_INVALID_ARG, "node count mismatch");
+  SW_CUDA(s, cudaMemcpyAsync(s->h.dq, dq8, (size_t)n * 32, cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_read_correspondence(sw_handle s, int* pix, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  if (n_out) *n_out = s->h.n_s;
+  if (pix) SW_TRY(d2h_perm(s, s->h.corr_pix, pix, 1, true));
+  return SW_OK;
+}
+
+sw_status sw_debug_set_live(sw_handle s, const float* v4, const float* n4, int n) {
+  SW_TRY(need_model(s, n));
+  if (n != s->h.n_s || !v4 || !n4) return fail(s, SW_ERR_INVALID_ARG, "surfel count mismatch");
+  // keep each surfel's radius / confidence in .w
+  std::vector<float> v((size_t)n * 4), nn((size_t)n * 4), vr((size_t)n * 4), nr((size_t)n * 4);
+  SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.v_ref), vr.data(), 4, true));
+  SW_TRY(d2h_perm(s, reinterpret_cast<const float*>(s->h.n_ref), nr.data(), 4, true));
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k) { v[4 * i + k] = v4[4 * i + k]; nn[4 * i + k] = n4[4 * i + k]; }
+    v[4 * i + 3] = vr[4 * i + 3];
+    nn[4 * i + 3] = nr[4 * i + 3];
+  }
+  SW_TRY(h2d_perm(s, v.data(), reinterpret_cast<float*>(s->h.v_live), 4));
+  SW_TRY(h2d_perm(s, nn.data(), reinterpret_cast<float*>(s->h.n_live), 4));
+  return SW_OK;
+}
+
+sw_status sw_debug_associate(sw_handle s) {
+  SW_TRY(need_model(s, s ? s->h.n_s : 0));
+  if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
+  launch_associate_only(s->bh, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_debug_fusion_targets(sw_handle s, int* target, int* imap) {
+  SW_TRY(need_model(s, s ? s->h.n_s : 0));
+  if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
+  const size_t np = (size_t)s->h.W * s->h.H;
+  SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st));
+  launch_index_map(s->bh, s->st);
+  launch_fuse(s->bh, 1, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  std::vector<int> t(np), orig(std::max(1, s->h.n_s));
+  SW_CUDA(s, cudaMemcpyAsync(t.data(), s->h.fuse_target, np * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (s->h.n_s) SW_CUDA(s, cudaMemcpyAsync(orig.data(), s->h.orig_id, s->h.n_s * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  std::vector<unsigned long long> im;
+  if (imap) {
+    im.resize(16 * np);
+    SW_CUDA(s, cudaMemcpyAsync(im.data(), s->h.imap, im.size() * 8, cudaMemcpyDeviceToHost, s->st));
+  }
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (target)
+    for (size_t p = 0; p < np; ++p) target[p] = t[p] < 0 ? -1 : orig[t[p]];
+  if (imap)
+    for (size_t p = 0; p < im.size(); ++p) imap[p] = im[p] == ~0ull ? -1 : (int)(im[p] & 0xffffffffu);
+  return SW_OK;
+}
+
+sw_status sw_debug_assemble(sw_handle s, int* nnzb_out, int* n_corr_out) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "needs a model and a depth frame");
+  SW_CUDA(s, cudaMemsetAsync(s->h.e_depth, 0, kMaxGn * sizeof(double), s->st));
+  SW_CUDA(s, cudaMemsetAsync(s->h.e_reg, 0, kMaxGn * sizeof(double), s->st));
+  SW_CUDA(s, cudaMemsetAsync(s->h.n_corr, 0, kMaxGn * sizeof(int), s->st));
+  launch_reg_assemble(s->bh, 0, s->st);
+  launch_data_assemble(s->bh, 0, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  int nc = 0;
+  SW_CUDA(s, cudaMemcpyAsync(&nc, s->h.n_corr, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (nnzb_out) *nnzb_out = s->h.nnzb;
+  if (n_corr_out) *n_corr_out = nc;
+  return SW_OK;
+}
+
+sw_status sw_debug_read_jtj(sw_handle s, int* rows, int* cols, float* vals, float* g, int cap_blocks) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  const int nb = s->h.nnzb;
+  if (cap_blocks < nb) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
+  if (rows) SW_CUDA(s, cudaMemcpyAsync(rows, s->h.blk_row, nb * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (cols) SW_CUDA(s, cudaMemcpyAsync(cols, s->h.col, nb * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (vals) SW_CUDA(s, cudaMemcpyAsync(vals, s->h.A, (size_t)nb * 36 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+  if (g) SW_CUDA(s, cudaMemcpyAsync(g, s->h.g, (size_t)s->h.n_n * 6 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+
+namespace {
+constexpr uint32_t kStateMagic = 0x53574731u;   // "SWG1"
+struct StateHeader {
+  uint32_t magic;
+  int n_s, n_n, W, H, t_now;
+};
+}  // namespace
+
+sw_status sw_export_state(sw_handle s, void* buf, size_t* bytes) {
+  if (!s || !bytes) return fail(s, SW_ERR_INVALID_ARG, "null argument");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  const int n = s->h.n_s, m = s->h.n_n;
+  const size_t need = sizeof(StateHeader) + (size_t)n * (16 + 16 + 8 + 16 + 16) + (size_t)m * (16 + 32);
+  if (!buf) { *bytes = need; return SW_OK; }
+  if (*bytes < need) return fail(s, SW_ERR_INVALID_ARG, "state buffer too small");
+  char* p = static_cast<char*>(buf);
+  StateHeader hd{kStateMagic, n, m, s->h.W, s->h.H, s->h.t_now};
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  SW_TRY(sw_read_surfels(s, reinterpret_cast<float*>(p), reinterpret_cast<float*>(p + (size_t)n * 16),
+                         reinterpret_cast<int*>(p + (size_t)n * 32), n, nullptr));
+  p += (size_t)n * 40;
+  SW_TRY(sw_read_skinning(s, reinterpret_cast<int*>(p), reinterpret_cast<float*>(p + (size_t)n * 16), n, nullptr));
+  p += (size_t)n * 32;
+  SW_TRY(sw_read_nodes(s, reinterpret_cast<float*>(p), reinterpret_cast<float*>(p + (size_t)m * 16), m, nullptr));
+  *bytes = need;
+  return SW_OK;
+}
+
+sw_status sw_import_state(sw_handle s, const void* buf, size_t bytes) {
+  if (!s || !buf || bytes < sizeof(StateHeader)) return fail(s, SW_ERR_INVALID_ARG, "bad state buffer");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.W != s->h.W || hd.H != s->h.H) return fail(s, SW_ERR_INVALID_ARG, "state does not match the stream");
+  const int n = hd.n_s, m = hd.n_n;
+  if (bytes < sizeof(StateHeader) + (size_t)n * 72 + (size_t)m * 48) return fail(s, SW_ERR_INVALID_ARG, "state truncated");
+  if (n > s->p.max_surfels || m > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "state exceeds the stream capacity");
+  const char* p = static_cast<const char*>(buf) + sizeof(StateHeader);
+  const float* v4 = reinterpret_cast<const float*>(p);
+  const float* n4 = reinterpret_cast<const float*>(p + (size_t)n * 16);
+  const int* t2 = reinterpret_cast<const int*>(p + (size_t)n * 32);
+  const int* knn = reinterpret_cast<const int*>(p + (size_t)n * 40);
+  const float* w = reinterpret_cast<const float*>(p + (size_t)n * 56);
+  const float* node4 = reinterpret_cast<const float*>(p + (size_t)n * 72);
+  const float* dq8 = node4 + (size_t)m * 4;
+  s->h.t_now = hd.t_now;
+  SW_TRY(set_model_impl(s, v4, n4, t2, n, node4, m, knn, w));
+  SW_TRY(sw_set_node_dq(s, dq8, m));
+  return SW_OK;
+}
+
+const char* sw_last_error(sw_handle s) {
+  if (s) return s->err.c_str();
+  static thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  copy = g_last_error;
+  return copy.c_str();
+}
+
+const char* sw_status_string(sw_status s) {
+  switch (s) {
+    case SW_OK: return "ok";
+    case SW_ERR_INVALID_ARG: return "invalid argument";
+    case SW_ERR_NO_MEMORY: return "out of device memory budget";
+    case SW_ERR_NOT_INITIALIZED: return "not initialized";
+    case SW_ERR_SOLVER_BREAKDOWN: return "solver breakdown";
+    case SW_ERR_TIMEOUT: return "device wait timed out";
+    case SW_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+

@@ -1,0 +1,191 @@
+"""End-to-end parity of the CUDA solve and fusion with the FP64 oracle, plus
+edge cases, error paths and checkpoint / resume.
+
+Tolerances for the solved warp field: node rotations within 1e-4 rad and
+node translations within 1e-5 m of the oracle's.  Translation is measured at
+the node (T_j p_j), where it is a physical displacement; the translation part
+of T_j alone mixes in rotation error times the node's distance from the
+camera origin."""
+import numpy as np
+import pytest
+
+import synth
+import paper_1904_13073_gb300 as sw
+from oracle import solver as OS
+
+from gpu_helpers import Pair, ensure_built, rotation_angle_between
+
+pytestmark = pytest.mark.gpu
+ROT_TOL = 1e-4
+TRANS_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+def _compare_nodes(p):
+    _, dq = sw.sw_read_nodes(p.h)
+    dq = dq.astype(np.float64)
+    rot = rotation_angle_between(dq, p.o.node_dq)
+    got = OS.node_transform(dq, p.o.node_p)
+    trans = np.linalg.norm(got - p.o.warped_nodes(), axis=1)
+    return float(rot.max()), float(trans.max())
+
+
+def test_plain_tiny_solve_matches_oracle():
+    """160x120 wavy surface, 64 nodes, 5 GN x 10 PCG."""
+    scene = synth.plain_tiny(seed=0)
+    p = Pair(scene)
+    try:
+        p.upload(1)
+        st = sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
+        ost = p.o.solve_frame(scene.gn_iters, scene.pcg_iters)
+        for k in range(scene.gn_iters):
+            assert abs(st["n_corr"][k] - ost[k].n_corr) <= 2
+            assert st["e_depth"][k] == pytest.approx(ost[k].e_depth, rel=1e-3)
+            assert st["e_reg"][k] == pytest.approx(ost[k].e_reg, rel=1e-3, abs=1e-9)
+        rot, trans = _compare_nodes(p)
+        assert rot <= ROT_TOL and trans <= TRANS_TOL, (rot, trans)
+        # the solve reduced the data energy to the noise floor (1 mm noise)
+        assert st["e_depth"][-1] < 0.25 * st["e_depth"][0]
+    finally:
+        p.close()
+
+
+def test_small_sequence_solve_and_fuse_matches_oracle():
+    """Bending sphere with outliers over three frames of solve + fusion."""
+    scene = synth.random_scene(seed=3, n_surfels=6000, n_nodes=48, outliers=0.01)
+    p = Pair(scene)
+    try:
+        for t in (1, 2, 3):
+            p.upload(t)
+            sw.sw_solve_frame(p.h, 3, 10)
+            p.o.solve_frame(3, 10)
+            rot, trans = _compare_nodes(p)
+            assert rot <= ROT_TOL and trans <= TRANS_TOL, (t, rot, trans)
+            sw.sw_fuse_frame(p.h)
+            n_fused = p.o.fuse_frame()
+            v, n, tt = sw.sw_read_surfels(p.h)
+            fused_gpu = tt[:, 1] == t
+            fused_ora = p.o.t_obs == t
+            # a few fusion decisions may flip on 1-ulp differences of the warps
+            assert np.sum(fused_gpu != fused_ora) <= max(3, n_fused // 200)
+            both = fused_gpu & fused_ora
+            assert np.max(np.abs(v[both, :3] - p.o.v_ref[both])) < 2e-5
+            assert np.max(np.abs(n[both, 3] - p.o.conf[both])) < 1e-4
+    finally:
+        p.close()
+
+
+def test_identity_zero_residual_gives_identity_update():
+    """Live depth equals the reference depth, surfels back-projected from it,
+    identity warp: every term has a zero residual, so the nodes stay put."""
+    scene = synth.plain_tiny(seed=0, noise=0.0)
+    c = scene.cam
+    d = scene.frame(0)
+    p = sw.params_for(c, c.width * c.height, len(scene.node_p))
+    h = sw.sw_create_stream(p)
+    try:
+        # surfels = the GPU's own depth surfels of this frame
+        tmp = sw.sw_create_stream(sw.params_for(c, 1, len(scene.node_p)))
+        sw.sw_set_model(tmp, np.zeros((0, 4), np.float32), np.zeros((0, 4), np.float32), None,
+                        sw.model_arrays(scene)[3])
+        sw.sw_upload_depth(tmp, d, 0)
+        V, N = sw.sw_read_maps(tmp, c.height, c.width)
+        sw.sw_destroy_stream(tmp)
+        ok = V[..., 3].reshape(-1) > 0
+        v4 = V.reshape(-1, 4)[ok].copy()
+        n4 = N.reshape(-1, 4)[ok].copy()
+        n4[:, 3] = 1.0
+        sw.sw_set_model(h, v4, n4, None, sw.model_arrays(scene)[3])
+        sw.sw_upload_depth(h, d, 1)
+        st = sw.sw_solve_frame(h, 2, 10)
+        assert st["n_corr"][0] == ok.sum()
+        assert st["e_depth"][0] == 0.0 and st["e_reg"][0] == 0.0
+        _, dq = sw.sw_read_nodes(h)
+        np.testing.assert_array_equal(dq, np.tile(np.array([1, 0, 0, 0, 0, 0, 0, 0], np.float32), (len(dq), 1)))
+    finally:
+        sw.sw_destroy_stream(h)
+
+
+def test_edge_cases_and_errors():
+    scene = synth.random_scene(seed=4, n_surfels=500, n_nodes=9)
+    c = scene.cam
+    v4, n4, t2, node4 = sw.model_arrays(scene)
+    h = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4)))
+    try:
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_solve_frame(h, 1, 1)
+        assert e.value.status == 3                       # no model yet
+        # minimum node count, ragged surfel count
+        sw.sw_set_model(h, v4[:333], n4[:333], t2[:333], node4)
+        sw.sw_upload_depth(h, scene.frame(1), 1)
+        st = sw.sw_solve_frame(h, 1, 1)
+        assert st["gn_iters"] == 1
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_solve_frame(h, 0, 5)
+        assert e.value.status == 1
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_solve_frame(h, 17, 5)
+        assert e.value.status == 1
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_set_model(h, v4, n4, t2, node4[:8])   # fewer than 9 nodes
+        assert e.value.status == 1
+        # an empty depth frame: no correspondences, regulariser only
+        sw.sw_set_model(h, v4, n4, t2, node4)
+        sw.sw_upload_depth(h, np.zeros((c.height, c.width), np.float32), 2)
+        st = sw.sw_solve_frame(h, 2, 4)
+        assert st["n_corr"] == [0, 0] and st["e_depth"] == [0.0, 0.0]
+        sw.sw_fuse_frame(h)
+        # no surfels at all
+        sw.sw_set_model(h, np.zeros((0, 4), np.float32), np.zeros((0, 4), np.float32), None, node4)
+        sw.sw_upload_depth(h, scene.frame(1), 1)
+        st = sw.sw_solve_frame(h, 1, 3)
+        assert st["n_corr"] == [0]
+        sw.sw_fuse_frame(h)
+    finally:
+        sw.sw_destroy_stream(h)
+
+
+def test_memory_budget_refuses_a_stream():
+    scene = synth.random_scene(seed=4, n_surfels=500, n_nodes=12)
+    base = sw.sw_memory_in_use()
+    try:
+        sw.sw_set_memory_budget(base + (1 << 20))
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_create_stream(sw.params_for(scene.cam, 10_000_000, 4096))
+        assert e.value.status == 2
+        assert sw.sw_memory_in_use() == base
+    finally:
+        sw.sw_set_memory_budget(0)
+
+
+def test_checkpoint_resume_gives_identical_next_frame():
+    scene = synth.random_scene(seed=6, n_surfels=4000, n_nodes=40)
+    c = scene.cam
+    v4, n4, t2, node4 = sw.model_arrays(scene)
+    a = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4)))
+    b = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4)))
+    try:
+        sw.sw_set_model(a, v4, n4, t2, node4)
+        sw.sw_upload_depth(a, scene.frame(1), 1)
+        sw.sw_solve_frame(a, 3, 8)
+        sw.sw_fuse_frame(a)
+        state = sw.sw_export_state(a)
+        sw.sw_import_state(b, state)
+        for h in (a, b):
+            sw.sw_upload_depth(h, scene.frame(2), 2)
+            sw.sw_solve_frame(h, 3, 8)
+            sw.sw_fuse_frame(h)
+        va, na, ta = sw.sw_read_surfels(a)
+        vb, nb, tb = sw.sw_read_surfels(b)
+        _, qa = sw.sw_read_nodes(a)
+        _, qb = sw.sw_read_nodes(b)
+        np.testing.assert_allclose(qa, qb, atol=2e-6)
+        np.testing.assert_allclose(va, vb, atol=2e-6)
+        assert np.sum(ta != tb) <= 2
+    finally:
+        sw.sw_destroy_stream(a)
+        sw.sw_destroy_stream(b)
