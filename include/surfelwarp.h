@@ -186,6 +186,45 @@ sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, floa
 sw_status sw_export_state(sw_handle h, void* buf, size_t* bytes);
 sw_status sw_import_state(sw_handle h, const void* buf, size_t bytes);
 
+/* ---------------------------------------------------------------------------
+ * Fusion-target selection without any device allocation.
+ *
+ * The paper has no counterpart to this call; it is an addition for callers
+ * that may not call cudaMalloc: code that runs while someone else is
+ * capturing its CUDA stream into a graph, real-time loops in which an
+ * allocation would stall every stream of the device, and host frameworks
+ * that hand out all device memory from their own pool.  It computes what
+ * sw_debug_fusion_targets computes (the 4x super-sampled index map of the
+ * live surfels, then each depth pixel's fusion target, Sec. 6.1) but takes
+ * every input and output as caller-owned device memory and keeps its only
+ * scratch buffer, the index map, in a fixed array compiled into the
+ * library.
+ *
+ * Scratch: 16 * SW_STATIC_MAX_PIXELS 64-bit entries (9.8 MB).  Every GPU
+ * that loads the library holds this array until the process exits.  The
+ * first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device uses the same array and overwrites
+ * it (the call clears it first), so calls whose work overlaps on the GPU --
+ * on different streams, or from different host threads -- race and give
+ * wrong results; serialise them.
+ *
+ * Arguments (all device pointers, caller's surfel order):
+ *   v_live4 [n_surfels][4] x y z (.w unused), n_live4 [n_surfels][4]
+ *   nx ny nz confidence; vmap4 / nmap4 [height][width][4] as sw_read_maps
+ *   returns them (confidence 0 = not a usable depth surfel); target
+ *   [height*width] receives the chosen surfel index or -1.
+ * The work is enqueued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without waiting.  Returns SW_ERR_INVALID_ARG (with a message
+ * in sw_last_error(NULL)) for null pointers, non-positive sizes or
+ * width * height > SW_STATIC_MAX_PIXELS, and SW_ERR_CUDA if a launch fails.
+ * ------------------------------------------------------------------------- */
+#define SW_STATIC_MAX_PIXELS 76800   /* 320 x 240 */
+sw_status sw_fusion_targets_static(const float* v_live4, const float* n_live4, int n_surfels,
+                                   const float* vmap4, const float* nmap4, int width, int height,
+                                   float fx, float fy, float cx, float cy, float fuse_dist,
+                                   float fuse_normal, int* target, void* cuda_stream);
+
 /* Reason of the last error on this handle ("" if none); NULL handle: the last
  * process-wide error (e.g. of sw_create_stream). */
 const char* sw_last_error(sw_handle h);

@@ -79,6 +79,8 @@ _SIGS = {
     "sw_debug_read_jtj": [_P, _P, _P, _P, _P, _I],
     "sw_export_state": [_P, _P, ctypes.POINTER(ctypes.c_size_t)],
     "sw_import_state": [_P, _P, ctypes.c_size_t],
+    "sw_fusion_targets_static": [_P, _P, _I, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P],
 }
 
 
@@ -321,6 +323,20 @@ def sw_export_state(h):
 def sw_import_state(h, buf):
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     _check(lib().sw_import_state(h, buf.ctypes.data_as(_P), buf.size), h)
+
+
+def sw_fusion_targets_static(v_live4, n_live4, vmap4, nmap4, width, height, fx, fy, cx, cy,
+                             fuse_dist, fuse_normal, target, cuda_stream=None):
+    """Fusion targets with no device allocation (all arguments CUDA tensors
+    the caller owns; see include/surfelwarp.h for the size limit and the rule
+    that overlapping calls race).  Enqueued on ``cuda_stream``; no wait."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    n = 0 if v_live4 is None else int(v_live4.shape[0])
+    ptr = (lambda t: None if t is None else ctypes.c_void_p(t.data_ptr()))
+    _check(lib().sw_fusion_targets_static(ptr(v_live4), ptr(n_live4), n, ptr(vmap4), ptr(nmap4), width, height,
+                                          fx, fy, cx, cy, fuse_dist, fuse_normal, ptr(target),
+                                          ctypes.c_void_p(cuda_stream or 0)))
 
 
 def sw_last_error(h=None):

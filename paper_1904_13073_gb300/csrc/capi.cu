@@ -39,6 +39,11 @@ void set_global_error(const std::string& s) {
 
 }  // namespace
 
+namespace sw {
+// process-wide error text for calls that take no stream handle
+void set_process_error(const std::string& msg) { set_global_error(msg); }
+}  // namespace sw
+
 struct sw_stream {
   sw_params p{};
   cudaStream_t st = nullptr;
