@@ -18,10 +18,12 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
-import threading
 import time
 
-import numpy as np
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -89,50 +91,115 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline_sample(scene, frame, gn, pcg):
-    """Time the FP64 oracle on a bounded sample: one frame, 2 GN x pcg, fusion;
-    scaled to frames/s of the full 10-GN frame by the GN fraction."""
+def measured_hbm_peak():
+    """Measured copy bandwidth of this machine's GB300 (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
+    """Algorithmic bytes per launch of each stage (what the stage must move at
+    least, per unit of work):
+      depth      4 B depth read + 32 B of V/N maps written per pixel
+      reg        144 B per 6x6 block written + 80 B of node data per node
+      data       64 B per surfel (v_ref, n_ref, 4-NN ids, weights)
+                 + 32 B per association (V, N gathered) + 32 B per node (DQ)
+                 + 144 B per block and 24 B per node of JᵀJ / Jᵀe written
+      pcg        per iteration 144 B per block (A read) + 192 B per node
+                 (8 FP32 6-vectors), plus 252 B per node for the set-up
+      fusion     96 B per surfel (warp: 64 read + 32 written) + 24 B per
+                 surfel (index map) + 160 B per pixel (16 map entries + maps)
+    """
+    return {
+        "depth": 36.0 * n_pix,
+        "reg_assembly": 144.0 * nnzb + 80.0 * n_n,
+        "data_assembly": 64.0 * n_s + 32.0 * n_corr + 32.0 * n_n + 144.0 * nnzb + 24.0 * n_n,
+        "pcg": pcg_iters * (144.0 * nnzb + 192.0 * n_n) + 252.0 * n_n,
+        "fusion": 120.0 * n_s + 160.0 * n_pix,
+    }
+
+
+def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
+    peak, src = measured_hbm_peak()
+    nbytes = stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters)
+    stages = {}
+    for k, b in nbytes.items():
+        if stage_n[k] == 0:
+            continue
+        per_launch_s = stage_ms[k] / stage_n[k] / 1000.0
+        gbs = b / per_launch_s / 1e9
+        stages[k] = {"achieved": gbs, "frac": gbs / peak, "us_per_launch": per_launch_s * 1e6,
+                     "bytes_per_launch": b}
+    dom = max(stages, key=lambda k: stage_ms[k])
+    d = stages[dom]
+    return {"stages": stages,
+            "dominant": {"kernel": dom, "bound": "hbm", "achieved": d["achieved"], "peak": peak,
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+                         "unit": "GB/s", "frac": d["frac"], "traffic": None,
+                         "bytes_per_launch": d["bytes_per_launch"], "us_per_launch": d["us_per_launch"]}}
+
+
+def oracle_stream(scene):
     import oracle
     c = scene.cam
     st = oracle.OracleStream(oracle.Params(c.width, c.height, c.fx, c.fy, c.cx, c.cy))
     st.set_model(scene.surfel_v, scene.surfel_n, scene.surfel_r, scene.surfel_c, scene.surfel_t,
                  scene.node_p, scene.node_sigma)
+    return st
+
+
+def oracle_frame_seconds(st, frame, t, gn, pcg, gn_sample=1):
+    """Seconds of one oracle frame: depth processing and fusion timed whole,
+    ``gn_sample`` of the ``gn`` Gauss-Newton iterations timed and scaled."""
     t0 = time.perf_counter()
-    st.upload_depth(frame, 1)
+    st.upload_depth(frame, t)
     t1 = time.perf_counter()
-    gs = 2
-    st.solve_frame(gs, pcg)
+    st.solve_frame(gn_sample, pcg)
     t2 = time.perf_counter()
     st.fuse_frame()
     t3 = time.perf_counter()
-    per_frame = (t1 - t0) + (t2 - t1) * gn / gs + (t3 - t2)
-    return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 frame, {gs} of {gn} GN iterations x {pcg} PCG timed, solve scaled by {gn}/{gs}, "
-                      "depth processing and fusion timed whole; numpy FP64, single-threaded BLAS"}
+    return (t1 - t0) + (t2 - t1) * gn / gn_sample + (t3 - t2)
+
+
+def oracle_sample_text(gn, pcg):
+    return (f"per frame: depth processing and fusion timed whole, 1 of {gn} Gauss-Newton iterations "
+            f"(x {pcg} PCG) timed and scaled by {gn}; numpy FP64 oracle, 1 thread")
+
+
+def cpu_baseline_sample(scene, frame, gn, pcg):
+    """The FP64 oracle on a bounded sample of the same workload (one frame)."""
+    st = oracle_stream(scene)
+    sec = oracle_frame_seconds(st, frame, 1, gn, pcg)
+    return {"value": 1.0 / sec, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": oracle_sample_text(gn, pcg)}
 
 
 def run_reference(args):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import synth
     scene = synth.plain_full(seed=0)
-    frames = render_frames(0, [1, 2], 2)
-    import oracle  # noqa: F401
+    n = args.warmup + args.steps
+    ts = [1 + (k % (scene.n_frames - 1)) for k in range(n)]
+    frames = dict(zip(sorted(set(ts)), render_frames(0, sorted(set(ts)), os.cpu_count() or 4)))
+    st = oracle_stream(scene)
     times = []
-    for k in range(args.warmup + args.steps):
-        b = cpu_baseline_sample(scene, frames[k % 2], scene.gn_iters, scene.pcg_iters)
+    for k in range(n):
+        sec = oracle_frame_seconds(st, frames[ts[k]], ts[k], scene.gn_iters, scene.pcg_iters)
         if k >= args.warmup:
-            times.append(1.0 / b["value"])
+            times.append(sec)
     ms = 1000.0 * float(np.mean(times))
+    sample = oracle_sample_text(scene.gn_iters, scene.pcg_iters)
     line = {"impl": "reference", "metric": METRIC, "value": 1000.0 / ms, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": b["sample"]},
+            "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": 1000.0 / ms, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": b["sample"]},
+                             "sample": sample},
             "e2e": {"value": 1000.0 / ms, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -214,6 +281,26 @@ def main():
         ms = float(t.item())
     clocks = clk.summary()
 
+    # stage timing, live: CUDA events recorded inside the captured solve graph
+    # on the library's stream, over a second timed region of the same steps
+    sw.sw_set_profiling(h, True)
+    prof_steps = min(args.steps, 8)
+    stage_ms = {k: 0.0 for k in sw.PROFILE_STAGES}
+    stage_n = {k: 0 for k in sw.PROFILE_STAGES}
+    for k in range(prof_steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xff)
+        step(ts[args.warmup + k], False)
+        pr = sw.sw_read_profile(h)
+        for name, (t_ms, n_l) in pr.items():
+            stage_ms[name] += t_ms
+            stage_n[name] += n_l
+    sw.sw_set_profiling(h, False)
+    stats = sw.sw_solve_frame(h, gn, pcg)   # the association count of a representative frame
+    n_corr = int(np.mean(stats["n_corr"]))
+    nnzb = sw.sw_debug_assemble(h)[0]
+    roof = roofline(stage_ms, stage_n, len(v4), len(node4), nnzb, n_corr, c.width * c.height, pcg)
+
     # end to end through the C ABI: host depth in, node state out, every step
     pos = np.empty((len(node4), 4), np.float32)
     torch.cuda.synchronize()
@@ -243,7 +330,12 @@ def main():
                 "h2d_bytes_per_step": c.width * c.height * 4, "d2h_bytes_per_step": len(node4) * 48,
                 "p50_ms": 1000.0 * float(np.percentile(e_lat, 50)), "p99_ms": 1000.0 * float(np.percentile(e_lat, 99))},
         "clocks": clocks,
-        "gpu_launches": None,
+        # kernels of this library per step: depth (frame id + maps), solve
+        # (stats reset + 3 per Gauss-Newton iteration), fusion (3)
+        "gpu_launches": args.steps * (2 + 1 + 3 * gn + 3),
+        "roofline": roof["dominant"],
+        "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
+        "stage_roofline": roof["stages"],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(scene, frame_of[ts[0]], gn, pcg)

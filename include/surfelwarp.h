@@ -181,6 +181,63 @@ sw_status sw_debug_assemble(sw_handle h, int* nnzb_out, int* n_corr_out);
  * (row <= col), vals [nnzb][36] row-major 6x6, g [6 n_nodes]. */
 sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, float* g, int cap_blocks);
 
+/* ---------------------------------------------------------------------------
+ * Batches: several streams of uneven size advanced together, each stage one
+ * launch over all of them (additions to the paper's interface, which runs
+ * one stream; Sec. 8 names stream-level parallelism as future work).
+ *
+ * A batch keeps per-stream state where it is (every member stays resident)
+ * and runs on its own CUDA stream.  Each Gauss-Newton iteration is three
+ * launches for the whole batch -- regulariser assembly, data-term assembly,
+ * and one persistent cooperative kernel that runs the block-Jacobi PCG and
+ * the update -- replayed from a captured CUDA graph.  Members whose active
+ * flag is 0 are skipped by every launch (their state is untouched).
+ * Results equal those of running each member alone up to floating-point
+ * summation order.  Work that a member's own calls enqueued is ordered before
+ * the next batch call, and batch work before the member's next own call.
+ * A batch becomes invalid when a member's model is replaced (sw_set_model /
+ * sw_import_state): batch calls then return SW_ERR_INVALID_ARG.  Errors of
+ * batch calls are reported by sw_last_error(NULL).
+ * ------------------------------------------------------------------------- */
+typedef struct sw_batch* sw_batch_handle;
+
+/* streams: n (1..4096) distinct handles with a model; cuda_stream as in
+ * sw_create_stream.  All members start active. */
+sw_status sw_batch_create(const sw_handle* streams, int n, void* cuda_stream, sw_batch_handle* out);
+sw_status sw_batch_destroy(sw_batch_handle b);
+/* active: host [n] ints, nonzero = the member takes part in the next calls. */
+sw_status sw_batch_set_active(sw_batch_handle b, const int* active);
+/* depths: host array of n pointers to [H_i][W_i] float32 depth images (host
+ * or device memory as on_device says; NULL entries and inactive members are
+ * skipped); frame_ids: host [n].  Computes every active member's depth
+ * surfels (Sec. 5) in one launch. */
+sw_status sw_batch_upload_depth(sw_batch_handle b, const float* const* depths, int on_device, const int* frame_ids);
+/* sw_solve_frame for every active member; stats: host [n] or NULL. */
+sw_status sw_batch_solve(sw_batch_handle b, int gn_iters, int pcg_iters, sw_solve_stats* stats);
+/* sw_fuse_frame for every active member. */
+sw_status sw_batch_fuse(sw_batch_handle b);
+
+/* ---------------------------------------------------------------------------
+ * Stage timing (CUDA events recorded on the launching stream, inside the
+ * captured solve graph).  Stages: 0 depth processing, 1 regulariser
+ * assembly, 2 data-term assembly, 3 PCG + update, 4 fusion.  Enabling or
+ * disabling re-captures the solve graph.  sw_read_profile synchronises and
+ * returns, per stage, the summed milliseconds and the number of launches of
+ * the last upload, solve and fusion.
+ * ------------------------------------------------------------------------- */
+#define SW_PROFILE_STAGES 5
+sw_status sw_set_profiling(sw_handle h, int enable);
+sw_status sw_read_profile(sw_handle h, double* ms, int* launches);
+sw_status sw_batch_set_profiling(sw_batch_handle b, int enable);
+sw_status sw_batch_read_profile(sw_batch_handle b, double* ms, int* launches);
+
+/* Test hook for failure detection: a cooperative launch whose grid barrier
+ * expects one more CTA than it has, so that every wait runs out after
+ * spin_limit polls.  Returns SW_ERR_TIMEOUT with *status_out holding the
+ * device status bits when the bounded waits ended as they must; the CUDA
+ * context stays usable. */
+sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out);
+
 /* Whole-stream state to and from host memory (checkpoint / resume):
  * sw_export_state with buf NULL reports the size in *bytes. */
 sw_status sw_export_state(sw_handle h, void* buf, size_t* bytes);

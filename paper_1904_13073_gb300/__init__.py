@@ -81,7 +81,20 @@ _SIGS = {
     "sw_import_state": [_P, _P, ctypes.c_size_t],
     "sw_fusion_targets_static": [_P, _P, _I, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P],
+    "sw_batch_create": [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(_P)],
+    "sw_batch_destroy": [_P],
+    "sw_batch_set_active": [_P, ctypes.POINTER(_I)],
+    "sw_batch_upload_depth": [_P, ctypes.POINTER(_P), _I, ctypes.POINTER(_I)],
+    "sw_batch_solve": [_P, _I, _I, ctypes.POINTER(sw_solve_stats)],
+    "sw_batch_fuse": [_P],
+    "sw_set_profiling": [_P, _I],
+    "sw_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
+    "sw_batch_set_profiling": [_P, _I],
+    "sw_batch_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
+    "sw_debug_barrier_timeout": [_I, ctypes.POINTER(_I)],
 }
+
+PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion")
 
 
 def exported_symbols():
@@ -337,6 +350,89 @@ def sw_fusion_targets_static(v_live4, n_live4, vmap4, nmap4, width, height, fx, 
     _check(lib().sw_fusion_targets_static(ptr(v_live4), ptr(n_live4), n, ptr(vmap4), ptr(nmap4), width, height,
                                           fx, fy, cx, cy, fuse_dist, fuse_normal, ptr(target),
                                           ctypes.c_void_p(cuda_stream or 0)))
+
+
+_batch_sizes = {}
+
+
+def sw_batch_create(handles, cuda_stream=None):
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    arr = (_P * len(handles))(*handles)
+    b = ctypes.c_void_p()
+    _check(lib().sw_batch_create(arr, len(handles), ctypes.c_void_p(cuda_stream or 0), ctypes.byref(b)))
+    _batch_sizes[b.value] = len(handles)
+    return b.value
+
+
+def sw_batch_destroy(b):
+    _check(lib().sw_batch_destroy(b))
+    _batch_sizes.pop(b, None)
+
+
+def sw_batch_set_active(b, active):
+    arr = (_I * len(active))(*[int(bool(a)) for a in active])
+    _check(lib().sw_batch_set_active(b, arr))
+
+
+def sw_batch_upload_depth(b, depths, frame_ids):
+    """depths: list of numpy arrays (host), CUDA tensors (device) or None."""
+    on_device = any(hasattr(d, "is_cuda") and d.is_cuda for d in depths if d is not None)
+    keep, ptrs = [], []
+    for d in depths:
+        if d is None:
+            ptrs.append(None)
+            continue
+        if hasattr(d, "data_ptr") and not on_device:
+            d = d.numpy()
+        p, k = _ptr(d, np.float32)
+        keep.append(k)
+        ptrs.append(p.value if p is not None else None)
+    arr = (_P * len(depths))(*ptrs)
+    ids = (_I * len(frame_ids))(*[int(f) for f in frame_ids])
+    _check(lib().sw_batch_upload_depth(b, arr, int(on_device), ids))
+    return keep
+
+
+def sw_batch_solve(b, gn_iters, pcg_iters, want_stats=True):
+    st = (sw_solve_stats * _batch_sizes[b])() if want_stats else None
+    _check(lib().sw_batch_solve(b, gn_iters, pcg_iters, st))
+    return [x.as_dict() for x in st] if st is not None else None
+
+
+def sw_batch_fuse(b):
+    _check(lib().sw_batch_fuse(b))
+
+
+def sw_set_profiling(h, enable):
+    _check(lib().sw_set_profiling(h, int(bool(enable))), h)
+
+
+def _profile(fn, h, handle_for_error):
+    ms = (ctypes.c_double * len(PROFILE_STAGES))()
+    n = (_I * len(PROFILE_STAGES))()
+    _check(fn(h, ms, n), handle_for_error)
+    return {k: (ms[i], n[i]) for i, k in enumerate(PROFILE_STAGES)}
+
+
+def sw_read_profile(h):
+    """{stage: (milliseconds, launches)} of the last upload, solve and fusion."""
+    return _profile(lib().sw_read_profile, h, h)
+
+
+def sw_batch_set_profiling(b, enable):
+    _check(lib().sw_batch_set_profiling(b, int(bool(enable))))
+
+
+def sw_batch_read_profile(b):
+    return _profile(lib().sw_batch_read_profile, b, None)
+
+
+def sw_debug_barrier_timeout(spin_limit):
+    """Returns (status code, device status bits) of a barrier that cannot complete."""
+    st = _I()
+    code = lib().sw_debug_barrier_timeout(spin_limit, ctypes.byref(st))
+    return code, st.value
 
 
 def sw_last_error(h=None):

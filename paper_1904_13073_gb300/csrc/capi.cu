@@ -44,27 +44,71 @@ namespace sw {
 void set_process_error(const std::string& msg) { set_global_error(msg); }
 }  // namespace sw
 
+// A Runner launches the per-frame kernels over one stream or over a batch of
+// streams: it owns the device tile tables, the descriptor array, the active
+// mask, the grid barrier of the persistent PCG, the captured solve graphs and
+// the profiling events.
+enum ProfStage { kProfDepth = 0, kProfReg, kProfData, kProfPcg, kProfFuse, kProfStages };
+
+struct ProfEvent {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+struct Runner {
+  std::vector<sw_stream*> members;
+  std::vector<uint64_t> versions;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  BatchHost bh{};
+  std::vector<std::pair<void*, size_t>> allocs;
+  int* active_host = nullptr;    // current active flags (host copy)
+  int* frames_dev = nullptr;
+  // pinned staging slots for small host->device copies, reused round-robin;
+  // each slot's event tells when its previous copy has been consumed
+  static constexpr int kRing = 8;
+  static constexpr int kSlotInts = 4096;
+  int* ring = nullptr;
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_pos = 0;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  std::map<std::pair<int, int>, std::vector<ProfEvent>> graph_prof;
+  std::pair<int, int> last_key{0, 0};
+  bool profiling = false;
+  std::vector<ProfEvent> eager_prof;   // events of the last upload / fusion
+  std::vector<cudaEvent_t> event_pool;
+  std::string err;
+};
+
 struct sw_stream {
   sw_params p{};
   cudaStream_t st = nullptr;
   bool own_stream = false;
   bool has_model = false;
   bool has_depth = false;
+  uint64_t version = 0;      // bumped whenever the device layout of the model changes
   std::string err;
   // device memory
   std::vector<std::pair<void*, size_t>> allocs;   // fixed arena pieces
   std::vector<std::pair<void*, size_t>> model_allocs;
-  SwDev h{};            // host mirror of the descriptor
-  SwDev* dev = nullptr; // device copy
-  int* tile_dev = nullptr;   // kTileKinds x 2 ints
+  SwDev h{};                 // host mirror of the descriptor
   int4* knn_dist = nullptr;  // skinning in distance order, caller's order (inspection, checkpoint)
   float4* w_dist = nullptr;
-  BatchHost bh{};
-  std::map<std::pair<int, int>, cudaGraphExec_t> solve_graphs;
-  cudaGraph_t fuse_graph_dummy = nullptr;
+  Runner* run = nullptr;     // the stream's own one-stream runner
+  // ordering against batches this stream belongs to
+  cudaEvent_t batch_done = nullptr;   // recorded by the last batch call (owned by the batch)
+  cudaEvent_t own_ev = nullptr;       // recorded before a batch call when own work is pending
+  bool own_pending = false;
+};
+
+struct sw_batch {
+  Runner run;
+  cudaEvent_t done = nullptr;
 };
 
 namespace {
+
+constexpr int kPcgMaxCtas = 64;   // persistent-PCG CTAs one stream may own
 
 sw_status fail(sw_stream* s, sw_status code, const std::string& msg) {
   if (s) s->err = msg; else set_global_error(msg);
@@ -122,27 +166,242 @@ sw_status A(sw_stream* s, T** out, size_t count, bool model = false) {
     if (st_ != SW_OK) return st_;       \
   } while (0)
 
-void drop_graphs(sw_stream* s) {
-  for (auto& kv : s->solve_graphs) cudaGraphExecDestroy(kv.second);
-  s->solve_graphs.clear();
+// Order a stream's own call after the batch work that touched it.
+void enter(sw_stream* s) {
+  if (s->batch_done) cudaStreamWaitEvent(s->st, s->batch_done, 0);
+  s->own_pending = true;
 }
 
-// Push the host descriptor and the one-stream tile tables to the device.
-sw_status sync_desc(sw_stream* s) {
-  int tiles[kTileKinds * 2];
+void drop_graphs(Runner* r) {
+  for (auto& kv : r->graphs) cudaGraphExecDestroy(kv.second);
+  r->graphs.clear();
+  for (auto& kv : r->graph_prof)
+    for (auto& e : kv.second) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  r->graph_prof.clear();
+}
+
+void destroy_runner(Runner* r) {
+  if (!r) return;
+  if (r->st) cudaStreamSynchronize(r->st);
+  drop_graphs(r);
+  for (auto& e : r->eager_prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  r->eager_prof.clear();
+  free_list(r->allocs);
+  if (r->ring) cudaFreeHost(r->ring);
+  for (auto& e : r->ring_ev) if (e) { cudaEventDestroy(e); e = nullptr; }
+  delete[] r->active_host;
+  if (r->own_stream && r->st) cudaStreamDestroy(r->st);
+  r->active_host = nullptr;
+  r->ring = nullptr;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// (Re)build the device tables of a runner for its members.
+sw_status build_runner(Runner* r, sw_stream* err_to) {
+  drop_graphs(r);
+  free_list(r->allocs);
+  const int n = (int)r->members.size();
+  r->versions.clear();
+  for (auto* m : r->members) r->versions.push_back(m->version);
+  std::vector<SwDev> devs(n);
+  for (int i = 0; i < n; ++i) devs[i] = r->members[i]->h;
+  std::vector<int> tiles((size_t)kTileKinds * (n + 1), 0);
   for (int k = 0; k < kTileKinds; ++k) {
-    tiles[2 * k] = 0;
-    tiles[2 * k + 1] = tiles_for(k, s->h);
-    s->bh.total_tiles[k] = tiles[2 * k + 1];
-    s->bh.tile_base_dev[k] = s->tile_dev + 2 * k;
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+      tiles[(size_t)k * (n + 1) + i] = acc;
+      acc += tiles_for(k, devs[i]);
+    }
+    tiles[(size_t)k * (n + 1) + n] = acc;
+    r->bh.total_tiles[k] = acc;
   }
-  SW_CUDA(s, cudaMemcpyAsync(s->tile_dev, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s->st));
-  SW_CUDA(s, cudaMemcpyAsync(s->dev, &s->h, sizeof(SwDev), cudaMemcpyHostToDevice, s->st));
-  SW_CUDA(s, cudaStreamSynchronize(s->st));
-  s->bh.bt.devs = s->dev;
-  s->bh.bt.n_streams = 1;
-  drop_graphs(s);
+  // PCG: one cooperative grid (every CTA resident); each stream gets its own
+  // CTAs, about one warp per block row and at most kPcgMaxCtas, scaled down
+  // in proportion when the batch asks for more CTAs than the GPU holds
+  {
+    const int per_sm = std::max(1, pcg_blocks_per_sm());
+    const int cap = sm_count() * per_sm;
+    if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
+    const int warps = pcg_threads() / 32;
+    std::vector<int> want(n);
+    long long total_want = 0;
+    for (int i = 0; i < n; ++i) {
+      want[i] = std::max(1, std::min(kPcgMaxCtas, (devs[i].n_n + warps - 1) / warps));
+      total_want += want[i];
+    }
+    if (total_want > cap) {
+      const int left = cap - n;
+      const long long rest = total_want - n;
+      for (int i = 0; i < n; ++i)
+        want[i] = 1 + (rest > 0 ? (int)((long long)(want[i] - 1) * left / rest) : 0);
+    }
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+      tiles[(size_t)kTilePcg * (n + 1) + i] = acc;
+      acc += want[i];
+    }
+    tiles[(size_t)kTilePcg * (n + 1) + n] = acc;
+    r->bh.total_tiles[kTilePcg] = acc;
+  }
+  SwDev* devs_dev = nullptr;
+  int* tile_dev = nullptr;
+  int* active_dev = nullptr;
+  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&devs_dev), sizeof(SwDev) * std::max(1, n)));
+  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&tile_dev), sizeof(int) * tiles.size()));
+  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&active_dev), sizeof(int) * std::max(1, n)));
+  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&r->frames_dev), sizeof(int) * std::max(1, n)));
+  if (!r->ring) {
+    if (cudaMallocHost(&r->ring, sizeof(int) * Runner::kRing * Runner::kSlotInts) != cudaSuccess)
+      return fail(err_to, SW_ERR_NO_MEMORY, "pinned host allocation failed");
+    for (auto& e : r->ring_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    r->active_host = new int[Runner::kSlotInts];
+  }
+  for (int i = 0; i < n; ++i) r->active_host[i] = 1;
+  std::vector<int> ones(std::max(1, n), 1);
+  SW_CUDA(err_to, cudaMemcpyAsync(devs_dev, devs.data(), sizeof(SwDev) * n, cudaMemcpyHostToDevice, r->st));
+  SW_CUDA(err_to, cudaMemcpyAsync(tile_dev, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, r->st));
+  SW_CUDA(err_to, cudaMemcpyAsync(active_dev, ones.data(), sizeof(int) * n, cudaMemcpyHostToDevice, r->st));
+  SW_CUDA(err_to, cudaStreamSynchronize(r->st));
+  r->bh.bt.devs = devs_dev;
+  r->bh.bt.active = active_dev;
+  r->bh.bt.n_streams = n;
+  for (int k = 0; k < kTileKinds; ++k) r->bh.tile_base_dev[k] = tile_dev + (size_t)k * (n + 1);
+  r->bh.spin_limit = 1 << 22;   // bounded polls (well under a second), then a timeout status
   return SW_OK;
+}
+
+// Copy n ints to device memory on the runner's stream through a pinned slot,
+// without waiting for earlier work on the stream.
+cudaError_t ring_copy(Runner* r, int* dst, const int* src, int n) {
+  const int k = r->ring_pos;
+  r->ring_pos = (k + 1) % Runner::kRing;
+  cudaError_t e = cudaEventSynchronize(r->ring_ev[k]);   // the slot's last copy has run
+  if (e != cudaSuccess) return e;
+  int* slot = r->ring + (size_t)k * Runner::kSlotInts;
+  std::memcpy(slot, src, sizeof(int) * n);
+  e = cudaMemcpyAsync(dst, slot, sizeof(int) * n, cudaMemcpyHostToDevice, r->st);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(r->ring_ev[k], r->st);
+}
+
+bool runner_stale(const Runner* r) {
+  for (size_t i = 0; i < r->members.size(); ++i)
+    if (r->members[i]->version != r->versions[i]) return true;
+  return false;
+}
+
+cudaEvent_t take_event(Runner* r) {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records a stage boundary.  During capture the record becomes a graph node.
+void prof_mark(Runner* r, std::vector<ProfEvent>* list, int stage, bool begin, bool capturing) {
+  if (!list) return;
+  if (begin) {
+    ProfEvent pe{stage, take_event(r), take_event(r)};
+    list->push_back(pe);
+    if (capturing) cudaEventRecordWithFlags(pe.a, r->st, cudaEventRecordExternal);
+    else cudaEventRecord(pe.a, r->st);
+  } else {
+    const ProfEvent& pe = list->back();
+    if (capturing) cudaEventRecordWithFlags(pe.b, r->st, cudaEventRecordExternal);
+    else cudaEventRecord(pe.b, r->st);
+  }
+}
+
+sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vector<ProfEvent>* prof) {
+  cudaStream_t st = r->st;
+  launch_solve_begin(r->bh, st);
+  for (int it = 0; it < gn; ++it) {
+    prof_mark(r, prof, kProfReg, true, true);
+    launch_reg_assemble(r->bh, it, st);
+    prof_mark(r, prof, kProfReg, false, true);
+    prof_mark(r, prof, kProfData, true, true);
+    launch_data_assemble(r->bh, it, st);
+    prof_mark(r, prof, kProfData, false, true);
+    prof_mark(r, prof, kProfPcg, true, true);
+    SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
+    prof_mark(r, prof, kProfPcg, false, true);
+  }
+  SW_CUDA(err_to, cudaGetLastError());
+  return SW_OK;
+}
+
+sw_status runner_solve(Runner* r, sw_stream* err_to, int gn, int pcg) {
+  const auto key = std::make_pair(gn, pcg);
+  auto itg = r->graphs.find(key);
+  if (itg == r->graphs.end()) {
+    std::vector<ProfEvent> prof;
+    cudaGraph_t graph = nullptr;
+    SW_CUDA(err_to, cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal));
+    const sw_status e = enqueue_solve(r, err_to, gn, pcg, r->profiling ? &prof : nullptr);
+    const cudaError_t ce = cudaStreamEndCapture(r->st, &graph);
+    if (e != SW_OK) { if (graph) cudaGraphDestroy(graph); return e; }
+    if (ce != cudaSuccess) return fail(err_to, SW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(err_to, SW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    itg = r->graphs.emplace(key, exec).first;
+    r->graph_prof[key] = prof;
+  }
+  r->last_key = key;
+  SW_CUDA(err_to, cudaGraphLaunch(itg->second, r->st));
+  return SW_OK;
+}
+
+void reset_eager_prof(Runner* r) {
+  for (auto& e : r->eager_prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  r->eager_prof.clear();
+}
+
+sw_status runner_fuse(Runner* r, sw_stream* err_to) {
+  cudaStream_t st = r->st;
+  std::vector<ProfEvent>* prof = r->profiling ? &r->eager_prof : nullptr;
+  prof_mark(r, prof, kProfFuse, true, false);
+  launch_warp_live(r->bh, st);
+  launch_index_map(r->bh, st);
+  launch_fuse(r->bh, 0, st);
+  prof_mark(r, prof, kProfFuse, false, false);
+  SW_CUDA(err_to, cudaGetLastError());
+  return SW_OK;
+}
+
+sw_status runner_profile(Runner* r, sw_stream* err_to, double* ms, int* launches) {
+  SW_CUDA(err_to, cudaStreamSynchronize(r->st));
+  for (int k = 0; k < kProfStages; ++k) { if (ms) ms[k] = 0.0; if (launches) launches[k] = 0; }
+  auto add = [&](const std::vector<ProfEvent>& v) -> sw_status {
+    for (const auto& e : v) {
+      float t = 0.f;
+      const cudaError_t ce = cudaEventElapsedTime(&t, e.a, e.b);
+      if (ce != cudaSuccess) return fail(err_to, SW_ERR_CUDA, std::string("profile events: ") + cudaGetErrorString(ce));
+      if (ms) ms[e.stage] += t;
+      if (launches) launches[e.stage] += 1;
+    }
+    return SW_OK;
+  };
+  auto it = r->graph_prof.find(r->last_key);
+  if (it != r->graph_prof.end()) SW_TRY(add(it->second));
+  SW_TRY(add(r->eager_prof));
+  return SW_OK;
+}
+
+// Push the host descriptor of a stream to its own runner.
+sw_status sync_desc(sw_stream* s) {
+  if (!s->run) {
+    s->run = new Runner();
+    s->run->st = s->st;
+  }
+  s->run->members.assign(1, s);
+  return build_runner(s->run, s);
 }
 
 bool params_ok(const sw_params* p, std::string& why) {
@@ -228,7 +487,12 @@ __global__ void k_identity_dq(float4* dq, int n) {
   dq[2 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void k_set_frame(SwDev* dev, int t) { dev->t_now = t; }
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+__global__ void k_set_frames(Batch bt, const int* __restrict__ frames) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < bt.n_streams && stream_active(bt, s)) *bt.devs[s].t_now = frames[s];
+}
 
 }  // namespace
 
@@ -270,6 +534,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   s->p = *p;
   auto cleanup = [&](sw_status code) {
     const std::string msg = s->err;
+    if (s->run) { destroy_runner(s->run); delete s->run; }
     free_list(s->allocs);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -301,20 +566,27 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.node_p, nn); ALLOC(h.dq, 2 * nn); ALLOC(h.graph, SW_K_GRAPH * nn);
   ALLOC(h.in_ptr, nn + 1); ALLOC(h.in_src, SW_K_GRAPH * nn);
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
-  ALLOC(h.row_ptr, nn + 1); ALLOC(h.low_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Minv, 36 * nn);
+  ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Li, 21 * nn);
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
-  ALLOC(h.q, 6 * nn); ALLOC(h.red, kRedSlots);
+  ALLOC(h.q, 6 * nn); ALLOC(h.part, 2 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
   ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
-  ALLOC(h.status, 1);
-  ALLOC(s->dev, 1); ALLOC(s->tile_dev, 2 * kTileKinds);
+  ALLOC(h.status, 1); ALLOC(h.t_now, 1);
 #undef ALLOC
   if (st != SW_OK) return cleanup(st);
+  // the index map is cleared here once; fusion leaves it empty after every frame
   if (cudaMemsetAsync(h.status, 0, sizeof(int), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.t_now, 0, sizeof(int), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.part, 0, 2 * kMaxCtaPerStream * sizeof(PartSlot), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.pcg_epoch, 0, sizeof(unsigned long long), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.vmap, 0, np * sizeof(float4), s->st) != cudaSuccess) {
     s->err = "cudaMemset failed";
     return cleanup(SW_ERR_CUDA);
   }
-  if (sync_desc(s) != SW_OK) return cleanup(SW_ERR_CUDA);
+  {
+    const sw_status e = sync_desc(s);
+    if (e != SW_OK) return cleanup(e);
+  }
   *out = s;
   return SW_OK;
 }
@@ -322,7 +594,8 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
 sw_status sw_destroy_stream(sw_handle s) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   cudaStreamSynchronize(s->st);
-  drop_graphs(s);
+  if (s->run) { destroy_runner(s->run); delete s->run; s->run = nullptr; }
+  if (s->own_ev) cudaEventDestroy(s->own_ev);
   free_list(s->model_allocs);
   free_list(s->allocs);
   if (s->own_stream) cudaStreamDestroy(s->st);
@@ -341,7 +614,8 @@ struct Tmp {
 };
 
 struct Pattern {
-  std::vector<int> row_ptr, col, blk_row, blk_edge, low_ptr, low_blk, in_ptr, in_src, set_slots;
+  std::vector<int> row_ptr, col, blk_row, blk_edge, rl_ptr, in_ptr, in_src, set_slots;
+  std::vector<int2> rl_ent;
 };
 
 // Block-sparse pattern of JᵀJ: upper blocks (a <= b) of every node pair that
@@ -395,15 +669,18 @@ bool build_pattern(int n_n, const std::vector<int4>& sets, const std::vector<int
     P.in_src.insert(P.in_src.end(), in[j].begin(), in[j].end());
     P.in_ptr[j + 1] = (int)P.in_src.size();
   }
-  // transposed-block lists: for row i the blocks (j, i) with j < i
-  std::vector<std::vector<int>> low(n_n);
-  for (int b = 0; b < nb; ++b)
-    if (P.blk_row[b] != P.col[b]) low[P.col[b]].push_back(b);
-  P.low_ptr.assign(n_n + 1, 0);
-  P.low_blk.clear();
+  // per block row i, every block that multiplies into it: its own upper
+  // blocks (i, j) and, transposed, the upper blocks (j, i) with j < i
+  std::vector<std::vector<int2>> rows(n_n);
+  for (int b = 0; b < nb; ++b) {
+    rows[P.blk_row[b]].push_back(make_int2(b, P.col[b]));
+    if (P.blk_row[b] != P.col[b]) rows[P.col[b]].push_back(make_int2(b | int(0x80000000u), P.blk_row[b]));
+  }
+  P.rl_ptr.assign(n_n + 1, 0);
+  P.rl_ent.clear();
   for (int i = 0; i < n_n; ++i) {
-    P.low_blk.insert(P.low_blk.end(), low[i].begin(), low[i].end());
-    P.low_ptr[i + 1] = (int)P.low_blk.size();
+    P.rl_ent.insert(P.rl_ent.end(), rows[i].begin(), rows[i].end());
+    P.rl_ptr[i + 1] = (int)P.rl_ent.size();
   }
   // per set: 10 upper blocks in (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3) order + 4 node ids
   P.set_slots.resize(sets.size() * 14);
@@ -433,9 +710,11 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   if (n_s < 0 || n_s > s->p.max_surfels) return fail(s, SW_ERR_INVALID_ARG, "n_surfels out of range");
   if (n_n < SW_K_GRAPH + 1 || n_n > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "n_nodes out of range");
   if ((n_s > 0 && (!v4 || !n4)) || !node4) return fail(s, SW_ERR_INVALID_ARG, "null model array");
+  enter(s);
   SW_CUDA(s, cudaStreamSynchronize(s->st));
-  drop_graphs(s);
+  if (s->run) drop_graphs(s->run);
   free_list(s->model_allocs);
+  s->version++;
   SwDev& h = s->h;
   h.n_s = n_s; h.n_n = n_n;
   cudaStream_t st = s->st;
@@ -507,13 +786,13 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   h.n_sets = (int)sets.size();
   h.nnzb = (int)P.col.size();
   SW_CUDA(s, cudaMemcpyAsync(h.row_ptr, P.row_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  SW_CUDA(s, cudaMemcpyAsync(h.low_ptr, P.low_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  SW_CUDA(s, cudaMemcpyAsync(h.rl_ptr, P.rl_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   SW_CUDA(s, cudaMemcpyAsync(h.in_ptr, P.in_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
   SW_CUDA(s, cudaMemcpyAsync(h.in_src, P.in_src.data(), P.in_src.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   SW_TRY(upload_vec(s, &h.col, P.col));
   SW_TRY(upload_vec(s, &h.blk_row, P.blk_row));
   SW_TRY(upload_vec(s, &h.blk_edge, P.blk_edge));
-  SW_TRY(upload_vec(s, &h.low_blk, P.low_blk));
+  SW_TRY(upload_vec(s, &h.rl_ent, P.rl_ent));
   SW_TRY(upload_vec(s, &h.set_slots, P.set_slots));
   SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
   SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
@@ -521,7 +800,7 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   SW_CUDA(s, cudaMemsetAsync(h.corr_pix, 0xff, (size_t)std::max(1, n_s) * sizeof(int), st));
   SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
   SW_TRY(sync_desc(s));
-  launch_warp_live(s->bh, st);
+  launch_warp_live(s->run->bh, st);
   SW_CUDA(s, cudaGetLastError());
   SW_CUDA(s, cudaStreamSynchronize(st));
   s->has_model = true;
@@ -538,40 +817,23 @@ sw_status sw_upload_depth(sw_handle s, const float* depth, int on_device, int fr
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!depth) return fail(s, SW_ERR_INVALID_ARG, "null depth");
   const size_t bytes = (size_t)s->h.W * s->h.H * sizeof(float);
+  enter(s);
   if (on_device && s->own_stream) SW_CUDA(s, cudaStreamSynchronize(0));   // order after the caller's default-stream work
   SW_CUDA(s, cudaMemcpyAsync(s->h.depth, depth, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              s->st));
-  s->h.t_now = frame_id;
-  k_set_frame<<<1, 1, 0, s->st>>>(s->dev, frame_id);
-  launch_depth_maps(s->bh, s->st);
+  Runner* r = s->run;
+  std::vector<ProfEvent>* prof = nullptr;
+  if (r->profiling) { reset_eager_prof(r); prof = &r->eager_prof; }
+  k_set_int<<<1, 1, 0, s->st>>>(s->h.t_now, frame_id);
+  prof_mark(r, prof, kProfDepth, true, false);
+  launch_depth_maps(r->bh, s->st);
+  prof_mark(r, prof, kProfDepth, false, false);
   SW_CUDA(s, cudaGetLastError());
   s->has_depth = true;
   return SW_OK;
 }
 
 namespace {
-
-sw_status enqueue_solve(sw_stream* s, int gn, int pcg) {
-  cudaStream_t st = s->st;
-  const SwDev& h = s->h;
-  SW_CUDA(s, cudaMemsetAsync(h.e_depth, 0, kMaxGn * sizeof(double), st));
-  SW_CUDA(s, cudaMemsetAsync(h.e_reg, 0, kMaxGn * sizeof(double), st));
-  SW_CUDA(s, cudaMemsetAsync(h.n_corr, 0, kMaxGn * sizeof(int), st));
-  SW_CUDA(s, cudaMemsetAsync(h.pcg_rz, 0, kMaxGn * sizeof(double), st));
-  SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
-  for (int it = 0; it < gn; ++it) {
-    launch_reg_assemble(s->bh, it, st);
-    launch_data_assemble(s->bh, it, st);
-    launch_pcg_init(s->bh, st);
-    for (int k = 0; k < pcg; ++k) {
-      launch_pcg_spmv(s->bh, k, st);
-      launch_pcg_update(s->bh, k, st);
-    }
-    launch_apply_update(s->bh, it, pcg, st);
-  }
-  SW_CUDA(s, cudaGetLastError());
-  return SW_OK;
-}
 
 sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
   int status = 0;
@@ -585,6 +847,7 @@ sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
     SW_CUDA(s, cudaMemcpyAsync(out->pcg_rz, s->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
   }
   SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (status & kStatusTimeout) return fail(s, SW_ERR_TIMEOUT, "a bounded grid-barrier wait of the PCG gave up");
   if (status & kStatusBreakdown) return fail(s, SW_ERR_SOLVER_BREAKDOWN, "a diagonal block is not positive definite or pᵀAp <= 0");
   return SW_OK;
 }
@@ -596,22 +859,8 @@ sw_status sw_solve_frame(sw_handle s, int gn_iters, int pcg_iters, sw_solve_stat
   if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "solve needs a model and a depth frame");
   if (gn_iters < 1 || gn_iters > kMaxGn || pcg_iters < 1 || pcg_iters > kMaxPcg)
     return fail(s, SW_ERR_INVALID_ARG, "iteration counts out of range");
-  const auto key = std::make_pair(gn_iters, pcg_iters);
-  auto itg = s->solve_graphs.find(key);
-  if (itg == s->solve_graphs.end()) {
-    cudaGraph_t graph = nullptr;
-    SW_CUDA(s, cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    const sw_status e = enqueue_solve(s, gn_iters, pcg_iters);
-    const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
-    if (e != SW_OK) { if (graph) cudaGraphDestroy(graph); return e; }
-    if (ce != cudaSuccess) return fail(s, SW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    cudaGraphExec_t exec = nullptr;
-    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) return fail(s, SW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
-    itg = s->solve_graphs.emplace(key, exec).first;
-  }
-  SW_CUDA(s, cudaGraphLaunch(itg->second, s->st));
+  enter(s);
+  SW_TRY(runner_solve(s->run, s, gn_iters, pcg_iters));
   if (stats) return read_stats(s, gn_iters, stats);
   return SW_OK;
 }
@@ -619,13 +868,8 @@ sw_status sw_solve_frame(sw_handle s, int gn_iters, int pcg_iters, sw_solve_stat
 sw_status sw_fuse_frame(sw_handle s) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "fusion needs a model and a depth frame");
-  cudaStream_t st = s->st;
-  launch_warp_live(s->bh, st);
-  SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, (size_t)16 * s->h.W * s->h.H * sizeof(unsigned long long), st));
-  launch_index_map(s->bh, st);
-  launch_fuse(s->bh, 0, st);
-  SW_CUDA(s, cudaGetLastError());
-  return SW_OK;
+  enter(s);
+  return runner_fuse(s->run, s);
 }
 
 sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_out) {
@@ -633,6 +877,7 @@ sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_ou
   if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
   const int n = s->h.n_n;
   if (n_out) *n_out = n;
+  enter(s);
   if ((pos4 || dq8) && cap < n) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
   if (pos4) SW_CUDA(s, cudaMemcpyAsync(pos4, s->h.node_p, (size_t)n * 16, cudaMemcpyDeviceToHost, s->st));
   if (dq8) SW_CUDA(s, cudaMemcpyAsync(dq8, s->h.dq, (size_t)n * 32, cudaMemcpyDeviceToHost, s->st));
@@ -677,6 +922,7 @@ sw_status h2d_perm(sw_stream* s, const T* host, T* dev, int per) {
 sw_status need_model(sw_stream* s, int cap) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  enter(s);
   if (cap < s->h.n_s) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
   return SW_OK;
 }
@@ -722,6 +968,7 @@ sw_status sw_read_graph(sw_handle s, int* graph8, int cap) {
 sw_status sw_read_maps(sw_handle s, float* V4, float* N4) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
+  enter(s);
   const size_t np = (size_t)s->h.W * s->h.H;
   if (V4) SW_CUDA(s, cudaMemcpyAsync(V4, s->h.vmap, np * 16, cudaMemcpyDeviceToHost, s->st));
   if (N4) SW_CUDA(s, cudaMemcpyAsync(N4, s->h.nmap, np * 16, cudaMemcpyDeviceToHost, s->st));
@@ -774,7 +1021,7 @@ sw_status sw_debug_set_live(sw_handle s, const float* v4, const float* n4, int n
 sw_status sw_debug_associate(sw_handle s) {
   SW_TRY(need_model(s, s ? s->h.n_s : 0));
   if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
-  launch_associate_only(s->bh, s->st);
+  launch_associate_only(s->run->bh, s->st);
   SW_CUDA(s, cudaGetLastError());
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   return SW_OK;
@@ -785,8 +1032,8 @@ sw_status sw_debug_fusion_targets(sw_handle s, int* target, int* imap) {
   if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
   const size_t np = (size_t)s->h.W * s->h.H;
   SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st));
-  launch_index_map(s->bh, s->st);
-  launch_fuse(s->bh, 1, s->st);
+  launch_index_map(s->run->bh, s->st);
+  launch_fuse(s->run->bh, 1, s->st);
   SW_CUDA(s, cudaGetLastError());
   std::vector<int> t(np), orig(std::max(1, s->h.n_s));
   SW_CUDA(s, cudaMemcpyAsync(t.data(), s->h.fuse_target, np * sizeof(int), cudaMemcpyDeviceToHost, s->st));
@@ -796,6 +1043,7 @@ sw_status sw_debug_fusion_targets(sw_handle s, int* target, int* imap) {
     im.resize(16 * np);
     SW_CUDA(s, cudaMemcpyAsync(im.data(), s->h.imap, im.size() * 8, cudaMemcpyDeviceToHost, s->st));
   }
+  SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   if (target)
     for (size_t p = 0; p < np; ++p) target[p] = t[p] < 0 ? -1 : orig[t[p]];
@@ -807,11 +1055,9 @@ sw_status sw_debug_fusion_targets(sw_handle s, int* target, int* imap) {
 sw_status sw_debug_assemble(sw_handle s, int* nnzb_out, int* n_corr_out) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "needs a model and a depth frame");
-  SW_CUDA(s, cudaMemsetAsync(s->h.e_depth, 0, kMaxGn * sizeof(double), s->st));
-  SW_CUDA(s, cudaMemsetAsync(s->h.e_reg, 0, kMaxGn * sizeof(double), s->st));
-  SW_CUDA(s, cudaMemsetAsync(s->h.n_corr, 0, kMaxGn * sizeof(int), s->st));
-  launch_reg_assemble(s->bh, 0, s->st);
-  launch_data_assemble(s->bh, 0, s->st);
+  launch_solve_begin(s->run->bh, s->st);
+  launch_reg_assemble(s->run->bh, 0, s->st);
+  launch_data_assemble(s->run->bh, 0, s->st);
   SW_CUDA(s, cudaGetLastError());
   int nc = 0;
   SW_CUDA(s, cudaMemcpyAsync(&nc, s->h.n_corr, sizeof(int), cudaMemcpyDeviceToHost, s->st));
@@ -852,7 +1098,9 @@ sw_status sw_export_state(sw_handle s, void* buf, size_t* bytes) {
   if (!buf) { *bytes = need; return SW_OK; }
   if (*bytes < need) return fail(s, SW_ERR_INVALID_ARG, "state buffer too small");
   char* p = static_cast<char*>(buf);
-  StateHeader hd{kStateMagic, n, m, s->h.W, s->h.H, s->h.t_now};
+  int t_now = 0;
+  SW_CUDA(s, cudaMemcpy(&t_now, s->h.t_now, sizeof(int), cudaMemcpyDeviceToHost));
+  StateHeader hd{kStateMagic, n, m, s->h.W, s->h.H, t_now};
   std::memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
   SW_TRY(sw_read_surfels(s, reinterpret_cast<float*>(p), reinterpret_cast<float*>(p + (size_t)n * 16),
@@ -881,8 +1129,8 @@ sw_status sw_import_state(sw_handle s, const void* buf, size_t bytes) {
   const float* w = reinterpret_cast<const float*>(p + (size_t)n * 56);
   const float* node4 = reinterpret_cast<const float*>(p + (size_t)n * 72);
   const float* dq8 = node4 + (size_t)m * 4;
-  s->h.t_now = hd.t_now;
   SW_TRY(set_model_impl(s, v4, n4, t2, n, node4, m, knn, w));
+  k_set_int<<<1, 1, 0, s->st>>>(s->h.t_now, hd.t_now);
   SW_TRY(sw_set_node_dq(s, dq8, m));
   return SW_OK;
 }
@@ -909,3 +1157,207 @@ const char* sw_status_string(sw_status s) {
 }
 
 
+
+// ------------------------------------------------------------------ batches
+
+namespace {
+
+sw_status batch_check(sw_batch* b) {
+  if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
+  if (runner_stale(&b->run)) return fail(nullptr, SW_ERR_INVALID_ARG, "a member's model changed; re-create the batch");
+  return SW_OK;
+}
+
+// The batch stream waits for work that members enqueued on their own streams.
+void batch_enter(sw_batch* b) {
+  for (sw_stream* m : b->run.members) {
+    if (!m->own_pending) continue;
+    if (!m->own_ev) cudaEventCreateWithFlags(&m->own_ev, cudaEventDisableTiming);
+    cudaEventRecord(m->own_ev, m->st);
+    cudaStreamWaitEvent(b->run.st, m->own_ev, 0);
+    m->own_pending = false;
+  }
+}
+
+// Members' own streams will wait for this batch call's work.
+void batch_leave(sw_batch* b) {
+  cudaEventRecord(b->done, b->run.st);
+  for (sw_stream* m : b->run.members) m->batch_done = b->done;
+}
+
+}  // namespace
+
+sw_status sw_batch_create(const sw_handle* streams, int n, void* cuda_stream, sw_batch_handle* out) {
+  if (!out || !streams || n < 1 || n > 4096) return fail(nullptr, SW_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  std::vector<sw_stream*> mem(streams, streams + n);
+  for (int i = 0; i < n; ++i) {
+    if (!mem[i] || !mem[i]->has_model) return fail(nullptr, SW_ERR_INVALID_ARG, "batch member without a model");
+    for (int j = 0; j < i; ++j)
+      if (mem[j] == mem[i]) return fail(nullptr, SW_ERR_INVALID_ARG, "a stream appears twice in a batch");
+  }
+  sw_batch* b = new sw_batch();
+  Runner* r = &b->run;
+  if (cuda_stream) {
+    r->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) == cudaSuccess) {
+    r->own_stream = true;
+  } else {
+    delete b;
+    return fail(nullptr, SW_ERR_CUDA, "cudaStreamCreate failed");
+  }
+  cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  r->members = mem;
+  for (sw_stream* m : mem) {   // the members' pending work comes first
+    if (!m->own_ev) cudaEventCreateWithFlags(&m->own_ev, cudaEventDisableTiming);
+    cudaEventRecord(m->own_ev, m->st);
+    cudaStreamWaitEvent(r->st, m->own_ev, 0);
+    m->own_pending = false;
+  }
+  const sw_status e = build_runner(r, nullptr);
+  if (e != SW_OK) {
+    destroy_runner(r);
+    cudaEventDestroy(b->done);
+    delete b;
+    return e;
+  }
+  *out = b;
+  return SW_OK;
+}
+
+sw_status sw_batch_destroy(sw_batch_handle b) {
+  if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
+  cudaStreamSynchronize(b->run.st);
+  for (sw_stream* m : b->run.members)
+    if (m->batch_done == b->done) m->batch_done = nullptr;
+  destroy_runner(&b->run);
+  cudaEventDestroy(b->done);
+  delete b;
+  return SW_OK;
+}
+
+sw_status sw_batch_set_active(sw_batch_handle b, const int* active) {
+  SW_TRY(batch_check(b));
+  if (!active) return fail(nullptr, SW_ERR_INVALID_ARG, "null active array");
+  Runner* r = &b->run;
+  const int n = (int)r->members.size();
+  for (int i = 0; i < n; ++i) r->active_host[i] = active[i] ? 1 : 0;
+  SW_CUDA(nullptr, ring_copy(r, const_cast<int*>(r->bh.bt.active), r->active_host, n));
+  return SW_OK;
+}
+
+sw_status sw_batch_upload_depth(sw_batch_handle b, const float* const* depths, int on_device, const int* frame_ids) {
+  SW_TRY(batch_check(b));
+  if (!depths || !frame_ids) return fail(nullptr, SW_ERR_INVALID_ARG, "null argument");
+  Runner* r = &b->run;
+  const int n = (int)r->members.size();
+  batch_enter(b);
+  if (on_device) SW_CUDA(nullptr, cudaStreamSynchronize(0));
+  for (int i = 0; i < n; ++i) {
+    sw_stream* m = r->members[i];
+    if (!r->active_host[i] || !depths[i]) continue;
+    const size_t bytes = (size_t)m->h.W * m->h.H * sizeof(float);
+    SW_CUDA(nullptr, cudaMemcpyAsync(m->h.depth, depths[i], bytes,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, r->st));
+    m->has_depth = true;
+  }
+  SW_CUDA(nullptr, ring_copy(r, r->frames_dev, frame_ids, n));
+  k_set_frames<<<(n + 127) / 128, 128, 0, r->st>>>(r->bh.bt, r->frames_dev);
+  std::vector<ProfEvent>* prof = nullptr;
+  if (r->profiling) { reset_eager_prof(r); prof = &r->eager_prof; }
+  prof_mark(r, prof, kProfDepth, true, false);
+  launch_depth_maps(r->bh, r->st);
+  prof_mark(r, prof, kProfDepth, false, false);
+  SW_CUDA(nullptr, cudaGetLastError());
+  batch_leave(b);
+  return SW_OK;
+}
+
+sw_status sw_batch_solve(sw_batch_handle b, int gn_iters, int pcg_iters, sw_solve_stats* stats) {
+  SW_TRY(batch_check(b));
+  if (gn_iters < 1 || gn_iters > kMaxGn || pcg_iters < 1 || pcg_iters > kMaxPcg)
+    return fail(nullptr, SW_ERR_INVALID_ARG, "iteration counts out of range");
+  Runner* r = &b->run;
+  for (int i = 0; i < (int)r->members.size(); ++i)
+    if (r->active_host[i] && !r->members[i]->has_depth)
+      return fail(nullptr, SW_ERR_NOT_INITIALIZED, "an active member has no depth frame");
+  batch_enter(b);
+  SW_TRY(runner_solve(r, nullptr, gn_iters, pcg_iters));
+  batch_leave(b);
+  if (!stats) return SW_OK;
+  sw_status worst = SW_OK;
+  for (int i = 0; i < (int)r->members.size(); ++i) {
+    sw_stream* m = r->members[i];
+    std::memset(&stats[i], 0, sizeof(sw_solve_stats));
+    if (!r->active_host[i]) continue;
+    int status = 0;
+    stats[i].gn_iters = gn_iters;
+    SW_CUDA(nullptr, cudaMemcpyAsync(&status, m->h.status, sizeof(int), cudaMemcpyDeviceToHost, r->st));
+    SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].e_depth, m->h.e_depth, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, r->st));
+    SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].e_reg, m->h.e_reg, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, r->st));
+    SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].n_corr, m->h.n_corr, kMaxGn * sizeof(int), cudaMemcpyDeviceToHost, r->st));
+    SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].pcg_rz, m->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, r->st));
+    SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
+    if (status & kStatusTimeout) worst = SW_ERR_TIMEOUT;
+    else if ((status & kStatusBreakdown) && worst == SW_OK) worst = SW_ERR_SOLVER_BREAKDOWN;
+  }
+  if (worst != SW_OK) return fail(nullptr, worst, "a member's solve broke down or timed out (see its stats)");
+  return SW_OK;
+}
+
+sw_status sw_batch_fuse(sw_batch_handle b) {
+  SW_TRY(batch_check(b));
+  batch_enter(b);
+  SW_TRY(runner_fuse(&b->run, nullptr));
+  batch_leave(b);
+  return SW_OK;
+}
+
+sw_status sw_set_profiling(sw_handle s, int enable) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  s->run->profiling = enable != 0;
+  drop_graphs(s->run);
+  reset_eager_prof(s->run);
+  return SW_OK;
+}
+
+sw_status sw_read_profile(sw_handle s, double* ms, int* launches) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  return runner_profile(s->run, s, ms, launches);
+}
+
+sw_status sw_batch_set_profiling(sw_batch_handle b, int enable) {
+  if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
+  SW_CUDA(nullptr, cudaStreamSynchronize(b->run.st));
+  b->run.profiling = enable != 0;
+  drop_graphs(&b->run);
+  reset_eager_prof(&b->run);
+  return SW_OK;
+}
+
+sw_status sw_batch_read_profile(sw_batch_handle b, double* ms, int* launches) {
+  if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
+  return runner_profile(&b->run, nullptr, ms, launches);
+}
+
+sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out) {
+  if (spin_limit < 1 || spin_limit > (1 << 24)) return fail(nullptr, SW_ERR_INVALID_ARG, "spin_limit out of range");
+  GridBarrier* gb = nullptr;
+  int* status = nullptr;
+  SW_CUDA(nullptr, cudaMalloc(&gb, sizeof(GridBarrier)));
+  if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) { cudaFree(gb); return fail(nullptr, SW_ERR_CUDA, "cudaMalloc failed"); }
+  cudaMemset(gb, 0, sizeof(GridBarrier));
+  cudaMemset(status, 0, sizeof(int));
+  // two CTAs run, the barrier waits for three: no wait can complete
+  cudaError_t e = launch_barrier_probe(gb, 2, 3, spin_limit, status, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(gb);
+  cudaFree(status);
+  if (e != cudaSuccess) return fail(nullptr, SW_ERR_CUDA, std::string("barrier probe: ") + cudaGetErrorString(e));
+  if (status_out) *status_out = st;
+  if (st & kStatusTimeout) return fail(nullptr, SW_ERR_TIMEOUT, "bounded grid-barrier wait ran out (expected)");
+  return SW_OK;
+}

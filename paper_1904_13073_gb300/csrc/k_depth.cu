@@ -18,7 +18,8 @@ constexpr int TX = 32, TY = 8;
 
 __global__ void __launch_bounds__(TX * TY) k_depth_maps(Batch bt) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int tile = blockIdx.x - __ldg(bt.tile_base + s);
   const int tiles_x = (d.W + TX - 1) / TX;
   const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;

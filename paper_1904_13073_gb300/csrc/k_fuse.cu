@@ -36,7 +36,8 @@ __device__ __forceinline__ DQ surfel_blend(const SwDev& d, int i, float& inv_n2)
 
 __global__ void __launch_bounds__(kSurfTile) k_warp_live(Batch bt) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int i = (blockIdx.x - __ldg(bt.tile_base + s)) * kSurfTile + threadIdx.x;
   if (i >= d.n_s) return;
   float inv;
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(kSurfTile) k_warp_live(Batch bt) {
 
 __global__ void __launch_bounds__(kSurfTile) k_index_map(Batch bt) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int i = (blockIdx.x - __ldg(bt.tile_base + s)) * kSurfTile + threadIdx.x;
   if (i >= d.n_s) return;
   const float4 v = d.v_live[i];
@@ -66,7 +68,8 @@ __global__ void __launch_bounds__(kSurfTile) k_index_map(Batch bt) {
 
 __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int tile = blockIdx.x - __ldg(bt.tile_base + s);
   const int tiles_x = (d.W + 31) / 32;
   const int x = (tile % tiles_x) * 32 + (threadIdx.x & 31);
@@ -75,17 +78,27 @@ __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
   const int pix = y * d.W + x;
   const float4 V = d.vmap[pix];
   int best = -1;
+  // This pixel owns its 16 sub-pixels.  In full mode it also leaves them empty
+  // for the next frame, so the map is cleared once at creation and never again.
+  unsigned long long* row0 = d.imap + (size_t)(4 * y) * (4 * d.W) + 4 * x;
+  unsigned long long keys[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) keys[k] = row0[(size_t)(k >> 2) * (4 * d.W) + (k & 3)];
+  if (!select_only) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (keys[k] != kEmpty) row0[(size_t)(k >> 2) * (4 * d.W) + (k & 3)] = kEmpty;
+  }
   if (V.w > 0.f) {
     const float4 N = d.nmap[pix];
     const float fd2 = __fmul_rn(d.fuse_dist, d.fuse_dist);
     float bc = -__int_as_float(0x7f800000), bd = __int_as_float(0x7f800000);
     unsigned bo = 0xffffffffu;
-    const unsigned long long* row0 = d.imap + (size_t)(4 * y) * (4 * d.W) + 4 * x;
 #pragma unroll
     for (int sy = 0; sy < 4; ++sy) {
 #pragma unroll
       for (int sx = 0; sx < 4; ++sx) {
-        const unsigned long long key = row0[(size_t)sy * (4 * d.W) + sx];
+        const unsigned long long key = keys[sy * 4 + sx];
         if (key == kEmpty) continue;
         const unsigned o = (unsigned)(key & 0xffffffffu);
         const int si = d.inv_perm[o];
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
       const float3 nr = dq_inv_rotate(b, inv, n);
       d.v_ref[best] = make_float4(vr.x, vr.y, vr.z, r);
       d.n_ref[best] = make_float4(nr.x, nr.y, nr.z, c_new);
-      d.tt[best].y = d.t_now;
+      d.tt[best].y = *d.t_now;
     }
   }
   d.fuse_target[pix] = best;

@@ -12,10 +12,14 @@
 //                       stored sorted by that set) and adds each run's ten
 //                       6x6 blocks and four 6-vectors to the system with
 //                       atomics.
-//   K7 k_pcg_*          block-Jacobi PCG on JᵀJ Δ = −Jᵀe: FP64 Cholesky
-//                       inverses of the diagonal blocks, FP32 block SpMV and
-//                       vector updates, FP64 dot-product reductions.
-//   K8 k_apply_update   T_j ← Δ_j T_j and re-normalisation.
+//   K7+K8 k_pcg         one persistent cooperative launch per Gauss-Newton
+//                       iteration runs the whole block-Jacobi PCG on
+//                       JᵀJ Δ = −Jᵀe and applies T_j ← Δ_j T_j: FP64 Cholesky
+//                       of the diagonal blocks, FP32 block SpMV (a warp per
+//                       block row) and vector updates, FP64 dot products
+//                       summed from published per-CTA partials in a fixed
+//                       order; each reduction is a bounded wait among the
+//                       CTAs of one stream.
 #include "sw_internal.h"
 #include "sw_math.cuh"
 
@@ -23,8 +27,8 @@ namespace sw {
 
 // ------------------------------------------------------------------ helpers
 
-__device__ __forceinline__ bool surfel_selected(const SwDev& d, float conf, int t_obs) {
-  return conf > d.stable_conf || (d.t_now - t_obs) <= d.recent_frames;
+__device__ __forceinline__ bool surfel_selected(const SwDev& d, int t_now, float conf, int t_obs) {
+  return conf > d.stable_conf || (t_now - t_obs) <= d.recent_frames;
 }
 
 // Projective association of one warped surfel (Sec. 7); -1 if rejected.
@@ -101,13 +105,23 @@ __device__ __forceinline__ float3 node_apply(const SwDev& d, int j, float3 p) {
 
 namespace {
 
+__global__ void k_solve_begin(Batch bt) {
+  const int s = blockIdx.x;
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  for (int k = threadIdx.x; k < kMaxGn; k += blockDim.x) {
+    d.e_depth[k] = 0.0; d.e_reg[k] = 0.0; d.n_corr[k] = 0; d.pcg_rz[k] = 0.0;
+  }
+  if (threadIdx.x == 0) *d.status = 0;
+}
+
 __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
-  if (b == 0) {
-    for (int k = 0; k < kRedSlots; ++k) d.red[k] = 0.0;
-  }
+  // a new epoch for the generation stamps of the PCG launch that follows
+  if (b == 0) *d.pcg_epoch += 1;
   float ereg = 0.f;
   if (b < d.nnzb) {
     const int i = d.blk_row[b], j = d.col[b];
@@ -165,7 +179,9 @@ constexpr int kJS = 25;   // 24 Jacobian entries + residual per term
 
 __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it, int write_live) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int t_now = *d.t_now;
   const int tid = threadIdx.x;
   const int i = (blockIdx.x - __ldg(bt.tile_base + s)) * kAsmTile + tid;
 
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
       inv = 1.f / n2;
       vl = dq_transform(b, inv, f3(v4));
       nl = dq_rotate(b, inv, f3(n4));
-      if (surfel_selected(d, n4.w, d.tt[i].y)) pix = associate_one(d, vl, nl);
+      if (surfel_selected(d, t_now, n4.w, d.tt[i].y)) pix = associate_one(d, vl, nl);
     }
     d.corr_pix[i] = pix;
     if (write_live) {
@@ -300,180 +316,314 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
 // association alone, on the stored live surfels (stage checks)
 __global__ void k_associate_only(Batch bt) {
   const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
   const int i = (blockIdx.x - __ldg(bt.tile_base + s)) * kSurfTile + threadIdx.x;
   if (i >= d.n_s) return;
   const float4 vl = d.v_live[i], nl = d.n_live[i];
   int pix = -1;
-  if (surfel_selected(d, d.n_ref[i].w, d.tt[i].y)) pix = associate_one(d, f3(vl), f3(nl));
+  if (surfel_selected(d, *d.t_now, d.n_ref[i].w, d.tt[i].y)) pix = associate_one(d, f3(vl), f3(nl));
   d.corr_pix[i] = pix;
 }
 
-// ------------------------------------------------------------------ K7: PCG
+// ------------------------------------------------------------------ K7+K8: PCG
 
-// 6x6 SPD inverse by Cholesky in FP64; false if not positive definite.
-__device__ bool spd_inverse6(const float* a, double* inv) {
-  double L[36];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) L[k] = 0.0;
+// Counter barrier over all CTAs of a cooperative launch, with a bounded wait
+// (used by the timeout probe).
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, int spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    const unsigned g = *vgen;
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      int spins = 0;
+      while (*vgen == g) {
+        if (++spins > spin_limit) { ok = 0; break; }
+        if (spins > 64) __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Packed lower-triangular index (r >= c).
+__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// Inverse Cholesky factor Li = L⁻¹ of a 6x6 SPD block, in FP64, stored packed
+// as FP32; false if the block is not positive definite.
+__device__ bool chol_inverse_factor(const float* a, float* li) {
+  double L[21], dinv[6];
   for (int c = 0; c < 6; ++c) {
     double s = (double)a[c * 6 + c];
-    for (int k = 0; k < c; ++k) s -= L[c * 6 + k] * L[c * 6 + k];
+    for (int k = 0; k < c; ++k) s -= L[tri(c, k)] * L[tri(c, k)];
     if (!(s > 0.0)) return false;
     const double lcc = sqrt(s);
-    L[c * 6 + c] = lcc;
+    L[tri(c, c)] = lcc;
+    dinv[c] = 1.0 / lcc;
     for (int r = c + 1; r < 6; ++r) {
       double t = 0.5 * ((double)a[r * 6 + c] + (double)a[c * 6 + r]);
-      for (int k = 0; k < c; ++k) t -= L[r * 6 + k] * L[c * 6 + k];
-      L[r * 6 + c] = t / lcc;
+      for (int k = 0; k < c; ++k) t -= L[tri(r, k)] * L[tri(c, k)];
+      L[tri(r, c)] = t * dinv[c];
     }
   }
-  // Li = L⁻¹ (lower), inv = Liᵀ Li
-  double Li[36];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) Li[k] = 0.0;
   for (int c = 0; c < 6; ++c) {
-    Li[c * 6 + c] = 1.0 / L[c * 6 + c];
+    li[tri(c, c)] = (float)dinv[c];
+    double col[6];
+    col[c] = dinv[c];
     for (int r = c + 1; r < 6; ++r) {
       double t = 0.0;
-      for (int k = c; k < r; ++k) t -= L[r * 6 + k] * Li[k * 6 + c];
-      Li[r * 6 + c] = t / L[r * 6 + r];
+      for (int k = c; k < r; ++k) t += L[tri(r, k)] * col[k];
+      col[r] = -t * dinv[r];
+      li[tri(r, c)] = (float)col[r];
     }
   }
-  for (int r = 0; r < 6; ++r)
-    for (int c = 0; c < 6; ++c) {
-      double t = 0.0;
-      for (int k = (r > c ? r : c); k < 6; ++k) t += Li[k * 6 + r] * Li[k * 6 + c];
-      inv[r * 6 + c] = t;
-    }
   return true;
 }
 
-__global__ void __launch_bounds__(kNodeTile) k_pcg_init(Batch bt) {
-  const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
-  const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kNodeTile + threadIdx.x;
-  double rz = 0.0;
-  if (j < d.n_n) {
-    const float* Ajj = d.A + (size_t)d.row_ptr[j] * 36;    // diagonal block leads its row
-    double inv[36];
-    float* M = d.Minv + (size_t)j * 36;
-    if (spd_inverse6(Ajj, inv)) {
+// z = M⁻¹ r = Liᵀ (Li r)
+__device__ __forceinline__ void apply_precond(const float* __restrict__ li, const float* r, float* z) {
+  float y[6];
 #pragma unroll
-      for (int k = 0; k < 36; ++k) M[k] = (float)inv[k];
-    } else {
+  for (int a = 0; a < 6; ++a) {
+    float t = 0.f;
+#pragma unroll
+    for (int c = 0; c <= a; ++c) t += li[tri(a, c)] * r[c];
+    y[a] = t;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float t = 0.f;
+#pragma unroll
+    for (int a = c; a < 6; ++a) t += li[tri(a, c)] * y[a];
+    z[c] = t;
+  }
+}
+
+// p_j = z_j (+ β p_old,j) for one neighbour node (6 values, 8-byte aligned)
+__device__ __forceinline__ void load_p(const float* __restrict__ z, const float* __restrict__ pold, int j, float beta,
+                                       bool first, float* p) {
+  const float2* z2 = reinterpret_cast<const float2*>(z + 6 * j);
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const float2 a = __ldcg(z2 + h);
+    p[2 * h] = a.x; p[2 * h + 1] = a.y;
+  }
+  if (!first) {
+    const float2* o2 = reinterpret_cast<const float2*>(pold + 6 * j);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const float2 b = __ldcg(o2 + h);
+      p[2 * h] += beta * b.x; p[2 * h + 1] += beta * b.y;
+    }
+  }
+}
+
+// One reduction among the CTAs of one stream, which is also their only
+// synchronisation.  Every CTA publishes its block sum in its slot with
+// generation `gen` (value, fence, stamp), then one warp polls the stream's
+// slots (plain volatile loads, bounded), fences, and sums the values in a
+// fixed order, so the total is deterministic for a given number of CTAs.
+// The CTA's global-memory writes before the call are visible to every CTA
+// that returns from the same reduction.  Returns false if the wait ran out.
+__device__ __forceinline__ bool stream_reduce(double v, PartSlot* part, int t, int gs, unsigned long long gen,
+                                              int spin_limit, double* total) {
+  __shared__ double s_w[32];
+  __shared__ double s_tot;
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  PartSlot* buf = part + (gen & 1ull) * kMaxCtaPerStream;
+  if (wid == 0) {
+    double b = lane < nw ? s_w[lane] : 0.0;
+    b = warp_sum(b);
+    if (lane == 0) {
+      __threadfence();                       // the CTA's data writes, then the value, then the stamp
+      buf[t].val = b;
+      __threadfence();
+      *reinterpret_cast<volatile unsigned long long*>(&buf[t].gen) = gen;
+    }
+    int ok = 1;
+    for (int k = lane; k < gs; k += 32) {
+      int spins = 0;
+      while (*reinterpret_cast<volatile unsigned long long*>(&buf[k].gen) < gen) {
+        if (++spins > spin_limit) { ok = 0; break; }
+      }
+      if (!ok) break;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __threadfence();
+    double acc = 0.0;
+    for (int k = lane; k < gs; k += 32) acc += __ldcg(&buf[k].val);
+    acc = warp_sum(acc);
+    if (lane == 0) { s_tot = acc; s_ok = ok; }
+  }
+  __syncthreads();
+  *total = s_tot;
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
+}
+
+// One persistent launch runs the PCG of every active stream of the batch and
+// applies the increments.  Stream s owns the CTAs [tile_base[s],
+// tile_base[s+1]) (all co-resident: cooperative launch); its block rows are
+// dealt round-robin over those CTAs (row i -> CTA i mod G_s, one warp per
+// row), its nodes likewise (node j -> CTA j mod G_s, one thread per node).
+// The two reductions of every iteration (pᵀq, rᵀz) are also the only
+// synchronisation, and they are per stream, so streams never wait for one
+// another (stream_reduce).  Per iteration:
+//   SpMV    a warp per block row, a lane per 6x6 block of the row: the block
+//           times the neighbour's p = z + β p_old (formed on the fly), then a
+//           warp sum of the six outputs;
+//   update  x += α p, r −= α q, z = M⁻¹ r per node.
+// All dot products are accumulated in FP64; the 6x6 factorisations are FP64.
+constexpr int kPcgThreads = 1024;
+constexpr int kPcgWarps = kPcgThreads / 32;
+
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_it, int spin_limit) {
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int t = blockIdx.x - __ldg(bt.tile_base + s);
+  const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = d.n_n;
+  const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
+  const int node_step = Gs * kPcgThreads, row_step = Gs * kPcgWarps;
+  const int node0 = t + Gs * tid, row0 = t + Gs * warp;
+
+  // ---- set-up: preconditioner, r = −g, z = M⁻¹ r, x = 0
+  double acc = 0.0;
+  for (int j = node0; j < n; j += node_step) {
+    float* li = d.Li + (size_t)j * 21;
+    if (!chol_inverse_factor(d.A + (size_t)d.row_ptr[j] * 36, li)) {
       atomicOr(d.status, kStatusBreakdown);
 #pragma unroll
-      for (int k = 0; k < 36; ++k) { M[k] = 0.f; inv[k] = 0.0; }
+      for (int k = 0; k < 21; ++k) li[k] = 0.f;
     }
-    float r[6];
+    float r[6], z[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) { r[k] = -d.g[6 * j + k]; d.r[6 * j + k] = r[k]; d.x[6 * j + k] = 0.f; }
+    for (int c = 0; c < 6; ++c) { r[c] = -d.g[6 * j + c]; d.r[6 * j + c] = r[c]; d.x[6 * j + c] = 0.f; }
+    apply_precond(li, r, z);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) {
-      float zp = 0.f;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) zp += M[p * 6 + q] * r[q];
-      d.z[6 * j + p] = zp;
-      rz += (double)r[p] * (double)zp;
-    }
+    for (int c = 0; c < 6; ++c) { d.z[6 * j + c] = z[c]; acc += (double)r[c] * (double)z[c]; }
   }
-  block_atomic_sum<double>(rz, d.red + 0);
-}
+  double rz, rz_prev = 1.0;
+  if (!stream_reduce(acc, d.part, t, Gs, base + 1, spin_limit, &rz)) { atomicOr(d.status, kStatusTimeout); return; }
+  bool bad = (__ldcg(d.status) & kStatusBreakdown) != 0;
 
-// red layout: rz_0 = red[0]; iteration k: pq_k = red[2k+1], rz_{k+1} = red[2k+2]
-__global__ void __launch_bounds__(kRowTile) k_pcg_spmv(Batch bt, int k) {
-  const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
-  const double rzk = *(volatile const double*)(d.red + 2 * k);
-  if (rzk == 0.0) return;                      // exact zero residual: the solve is done
-  const float beta = k == 0 ? 0.f : (float)(rzk / d.red[2 * k - 2]);
-  const float* __restrict__ z = d.z;
-  const float* __restrict__ pold = (k & 1) ? d.p0 : d.p1;
-  float* __restrict__ pnew = (k & 1) ? d.p1 : d.p0;
-  const int t = (blockIdx.x - __ldg(bt.tile_base + s)) * kRowTile + threadIdx.x;
-  double pq = 0.0;
-  if (t < 6 * d.n_n) {
-    const int i = t / 6, c = t - 6 * i;
-    float acc = 0.f;
-    for (int bk = d.row_ptr[i]; bk < d.row_ptr[i + 1]; ++bk) {
-      const int j = d.col[bk];
-      const float* B = d.A + (size_t)bk * 36 + c * 6;
+  for (int k = 0; k < K; ++k) {
+    const bool work = !bad && rz != 0.0;
+    const float beta = (k == 0 || !work) ? 0.f : (float)(rz / rz_prev);
+    const float* __restrict__ pold = (k & 1) ? d.p0 : d.p1;
+    float* __restrict__ pnew = (k & 1) ? d.p1 : d.p0;
+    acc = 0.0;
+    if (work) {
+      for (int i = row0; i < n; i += row_step) {
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int e1 = d.rl_ptr[i + 1];
+        for (int e = d.rl_ptr[i] + lane; e < e1; e += 32) {
+          const int2 ent = d.rl_ent[e];
+          const float2* B2 = reinterpret_cast<const float2*>(d.A + (size_t)(ent.x & 0x7fffffff) * 36);
+          float p[6];
+          load_p(d.z, pold, ent.y, beta, k == 0, p);
+          const bool tr = ent.x < 0;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const float pj = k == 0 ? z[6 * j + q] : z[6 * j + q] + beta * pold[6 * j + q];
-        acc += B[q] * pj;
+          for (int a = 0; a < 6; ++a) {
+            const float2 b0 = __ldg(B2 + 3 * a), b1 = __ldg(B2 + 3 * a + 1), b2 = __ldg(B2 + 3 * a + 2);
+            const float row[6] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y};
+            if (!tr) {
+              float u = 0.f;
+#pragma unroll
+              for (int q = 0; q < 6; ++q) u += row[q] * p[q];
+              v[a] += u;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) v[q] += p[a] * row[q];
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = warp_sum(v[c]);
+        if (lane < 6) {
+          float vc = v[0];
+#pragma unroll
+          for (int c = 1; c < 6; ++c) if (lane == c) vc = v[c];
+          float pi = __ldcg(d.z + 6 * i + lane);
+          if (k > 0) pi += beta * __ldcg(pold + 6 * i + lane);
+          pnew[6 * i + lane] = pi;
+          d.q[6 * i + lane] = vc;
+          acc += (double)pi * (double)vc;
+        }
       }
     }
-    for (int e = d.low_ptr[i]; e < d.low_ptr[i + 1]; ++e) {
-      const int bk = d.low_blk[e];
-      const int j = d.blk_row[bk];
-      const float* B = d.A + (size_t)bk * 36 + c;
+    double pq;
+    if (!stream_reduce(acc, d.part, t, Gs, base + 2 + 2 * k, spin_limit, &pq)) {
+      atomicOr(d.status, kStatusTimeout);
+      return;
+    }
+    acc = 0.0;
+    if (work) {
+      if (!(pq > 0.0)) {
+        bad = true;
+        if (t == 0 && tid == 0) atomicOr(d.status, kStatusBreakdown);
+      } else {
+        const float alpha = (float)(rz / pq);
+        for (int j = node0; j < n; j += node_step) {
+          float r[6], z[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const float pj = k == 0 ? z[6 * j + q] : z[6 * j + q] + beta * pold[6 * j + q];
-        acc += B[q * 6] * pj;
+          for (int c = 0; c < 6; ++c) {
+            const int ix = 6 * j + c;
+            d.x[ix] += alpha * __ldcg(pnew + ix);
+            r[c] = d.r[ix] - alpha * __ldcg(d.q + ix);
+            d.r[ix] = r[c];
+          }
+          apply_precond(d.Li + (size_t)j * 21, r, z);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) { d.z[6 * j + c] = z[c]; acc += (double)r[c] * (double)z[c]; }
+        }
       }
     }
-    const float pi = k == 0 ? z[t] : z[t] + beta * pold[t];
-    pnew[t] = pi;
-    d.q[t] = acc;
-    pq = (double)pi * (double)acc;
+    double rz_new;
+    if (!stream_reduce(acc, d.part, t, Gs, base + 3 + 2 * k, spin_limit, &rz_new)) {
+      atomicOr(d.status, kStatusTimeout);
+      return;
+    }
+    if (work && !bad) { rz_prev = rz; rz = rz_new; }
   }
-  block_atomic_sum<double>(pq, d.red + 2 * k + 1);
+  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = rz;
+  // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
+  if (bad || (__ldcg(d.status) & kStatusBreakdown)) return;
+  for (int j = node0; j < n; j += node_step) {
+    float xi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) xi[c] = d.x[6 * j + c];
+    float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
+    apply_increment(q0, qe, xi);
+    d.dq[2 * j] = q0;
+    d.dq[2 * j + 1] = qe;
+  }
 }
 
-__global__ void __launch_bounds__(kNodeTile) k_pcg_update(Batch bt, int k) {
-  const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
-  const double rzk = d.red[2 * k];
-  if (rzk == 0.0) return;
-  const double pqk = d.red[2 * k + 1];
-  const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kNodeTile + threadIdx.x;
-  if (!(pqk > 0.0)) {
-    if (j == 0) atomicOr(d.status, kStatusBreakdown);
-    return;
+// A grid barrier that never completes when fewer CTAs run than it expects:
+// used to check that a wait which cannot finish ends by its bound and reports
+// a status the host can read.
+__global__ void k_barrier_probe(GridBarrier* gb, unsigned expected, int spin_limit, int* status) {
+  if (!grid_sync(gb, expected, spin_limit)) {
+    if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   }
-  const float alpha = (float)(rzk / pqk);
-  const float* __restrict__ p = (k & 1) ? d.p1 : d.p0;
-  double rz = 0.0;
-  if (j < d.n_n) {
-    float r[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const int t = 6 * j + c;
-      d.x[t] += alpha * p[t];
-      r[c] = d.r[t] - alpha * d.q[t];
-      d.r[t] = r[c];
-    }
-    const float* M = d.Minv + (size_t)j * 36;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      float zp = 0.f;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) zp += M[a * 6 + c] * r[c];
-      d.z[6 * j + a] = zp;
-      rz += (double)r[a] * (double)zp;
-    }
-  }
-  block_atomic_sum<double>(rz, d.red + 2 * k + 2);
-}
-
-// ------------------------------------------------------------------ K8: update
-
-__global__ void __launch_bounds__(kNodeTile) k_apply_update(Batch bt, int gn_it, int pcg_iters) {
-  const int s = find_stream(bt, blockIdx.x);
-  const SwDev& d = bt.devs[s];
-  const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kNodeTile + threadIdx.x;
-  if (j == 0) d.pcg_rz[gn_it] = d.red[2 * pcg_iters];
-  if (j >= d.n_n || (*d.status & kStatusBreakdown)) return;
-  float xi[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) xi[c] = d.x[6 * j + c];
-  float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
-  apply_increment(q0, qe, xi);
-  d.dq[2 * j] = q0;
-  d.dq[2 * j + 1] = qe;
 }
 
 inline Batch with_kind(const BatchHost& b, int kind) {
@@ -484,28 +634,61 @@ inline Batch with_kind(const BatchHost& b, int kind) {
 
 }  // namespace
 
+void launch_solve_begin(const BatchHost& b, cudaStream_t st) {
+  if (b.bt.n_streams) k_solve_begin<<<b.bt.n_streams, 32, 0, st>>>(b.bt);
+}
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileBlocks]) k_reg_assemble<<<b.total_tiles[kTileBlocks], kBlkTile, 0, st>>>(with_kind(b, kTileBlocks), gn_it);
 }
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileSurfelsAssembly])
-    k_data_assemble<<<b.total_tiles[kTileSurfelsAssembly], kAsmTile, 0, st>>>(with_kind(b, kTileSurfelsAssembly), gn_it, 1);
+    k_data_assemble<<<b.total_tiles[kTileSurfelsAssembly], kAsmTile, 0, st>>>(with_kind(b, kTileSurfelsAssembly), gn_it, 0);
 }
 void launch_associate_only(const BatchHost& b, cudaStream_t st) {
   if (b.total_tiles[kTileSurfels]) k_associate_only<<<b.total_tiles[kTileSurfels], kSurfTile, 0, st>>>(with_kind(b, kTileSurfels));
 }
-void launch_pcg_init(const BatchHost& b, cudaStream_t st) {
-  if (b.total_tiles[kTileNodes]) k_pcg_init<<<b.total_tiles[kTileNodes], kNodeTile, 0, st>>>(with_kind(b, kTileNodes));
-}
-void launch_pcg_spmv(const BatchHost& b, int k, cudaStream_t st) {
-  if (b.total_tiles[kTileRows6]) k_pcg_spmv<<<b.total_tiles[kTileRows6], kRowTile, 0, st>>>(with_kind(b, kTileRows6), k);
-}
-void launch_pcg_update(const BatchHost& b, int k, cudaStream_t st) {
-  if (b.total_tiles[kTileNodes]) k_pcg_update<<<b.total_tiles[kTileNodes], kNodeTile, 0, st>>>(with_kind(b, kTileNodes), k);
-}
-void launch_apply_update(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st) {
-  if (b.total_tiles[kTileNodes])
-    k_apply_update<<<b.total_tiles[kTileNodes], kNodeTile, 0, st>>>(with_kind(b, kTileNodes), gn_it, pcg_iters);
+
+int pcg_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pcg, kPcgThreads, 0) != cudaSuccess) return 0;
+  return n;
 }
 
+int pcg_threads() { return kPcgThreads; }
+
+// One cooperative launch: every CTA is resident, so the waits of
+// stream_reduce always end (and are bounded regardless).
+cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st) {
+  const int nb = b.total_tiles[kTilePcg];
+  if (nb == 0) return cudaSuccess;
+  Batch bt = with_kind(b, kTilePcg);
+  int spin = b.spin_limit;
+  void* args[] = {&bt, &pcg_iters, &gn_it, &spin};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(k_pcg), args);
+}
+
+cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
+                                 int* status, cudaStream_t st) {
+  unsigned expected = (unsigned)nblocks_expected;
+  void* args[] = {&gb, &expected, &spin_limit, &status};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks_launched);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(k_barrier_probe), args);
+}
 }  // namespace sw

@@ -1,15 +1,14 @@
 // Internal declarations shared by the kernel translation units and the C-ABI.
 //
 // Per-stream device state is described by SwDev, a plain struct of device
-// pointers and sizes.  Kernels take a pointer to an array of SwDev in device
-// memory plus a tile table, so one launch can serve one stream or a batch of
-// streams of uneven size (blockIdx.x -> (stream, tile) through a prefix sum
-// of tiles per stream).
+// pointers and immutable sizes; everything that changes per frame lives behind
+// a pointer, so a stream's descriptor can be copied into any number of batch
+// tables.  Kernels take a Batch: an array of SwDev in device memory plus a tile
+// table, so one launch serves one stream or many streams of uneven size
+// (blockIdx.x -> (stream, tile) through a prefix sum of tiles per stream).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <string>
-#include <vector>
 
 #include "../../include/surfelwarp.h"
 
@@ -17,11 +16,20 @@ namespace sw {
 
 constexpr int kMaxGn = SW_MAX_GN_ITERS;
 constexpr int kMaxPcg = SW_MAX_PCG_ITERS;
-constexpr int kRedSlots = 2 * kMaxPcg + 2;   // rz0, then (pq_k, rz_k+1) per PCG iteration
+constexpr int kMaxCtaPerStream = 1024;   // CTAs of the persistent PCG that one stream may own
 
 // status bits written by kernels
-constexpr int kStatusBreakdown = 1;          // a diagonal block is not positive definite, or pᵀAp <= 0
-constexpr int kStatusBadIndex = 2;           // a gather index failed its range check
+constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive definite, or pᵀAp <= 0
+constexpr int kStatusBadIndex = 2;       // a gather index failed its range check
+constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
+
+// A CTA's partial of one reduction, published with a generation stamp
+// (release store of `gen` after `val`); slots are double-buffered by the
+// parity of the reduction's index.
+struct PartSlot {
+  double val;
+  unsigned long long gen;
+};
 
 struct SwDev {
   // camera and parameters
@@ -29,9 +37,9 @@ struct SwDev {
   float fx, fy, cx, cy;
   float sqrt_lambda, corr_dist, corr_normal, fuse_dist, fuse_normal, stable_conf;
   int recent_frames;
-  int t_now;
   // sizes
   int n_s, n_n, n_sets, nnzb;
+  int* t_now;         // current frame id (device scalar)
   // surfels, internal order (sorted by their 4-node set)
   float4* v_ref;      // x y z radius
   float4* n_ref;      // nx ny nz confidence
@@ -58,19 +66,20 @@ struct SwDev {
   unsigned long long* imap;  // 4W x 4H: (z bits << 32) | caller's surfel index
   int* fuse_target;   // per pixel: internal surfel index or -1
   // block-sparse JᵀJ (upper triangle incl. diagonal, 6x6 blocks, row-major)
-  int* row_ptr;       // n_n + 1
+  int* row_ptr;       // n_n + 1; the diagonal block leads its row
   int* col;           // nnzb
   int* blk_row;       // nnzb
   int* blk_edge;      // bit0: graph edge row->col, bit1: col->row
-  int* low_ptr;       // per row i: blocks (j, i) with j < i
-  int* low_blk;
+  int* rl_ptr;        // n_n + 1: per block row, every block that multiplies into it
+  int2* rl_ent;       //   (block | transposed << 31, neighbour node)
   int* set_slots;     // 14 per set: 10 upper blocks of (a<=b), then 4 node ids
   float* A;           // nnzb * 36
   float* g;           // 6 n_n
   // PCG
-  float* Minv;        // n_n * 36
+  float* Li;          // n_n * 21: inverse Cholesky factor of each diagonal block, packed lower
   float* x; float* r; float* z; float* p0; float* p1; float* q;
-  double* red;        // kRedSlots
+  struct PartSlot* part;   // 2 * kMaxCtaPerStream published per-CTA partial dot products
+  unsigned long long* pcg_epoch;   // launches of the persistent PCG so far
   // per-GN-iteration statistics
   double* e_depth;    // kMaxGn
   double* e_reg;      // kMaxGn
@@ -79,11 +88,13 @@ struct SwDev {
   int* status;
 };
 
-// tile table for batched launches: block b serves stream s with
-// tile_base[s] <= b < tile_base[s+1]
+// A launch over several streams: block b serves stream s with
+// tile_base[s] <= b < tile_base[s+1]; streams whose active flag is 0 skip
+// their tiles (the persistent PCG still takes part in its barriers).
 struct Batch {
   const SwDev* devs;      // device array
   const int* tile_base;   // device array, n_streams + 1
+  const int* active;      // device array or null (all active)
   int n_streams;
 };
 
@@ -96,49 +107,53 @@ __device__ __forceinline__ int find_stream(const Batch& bt, int b) {
   return lo;
 }
 
-// ------------------------------------------------------------------ launchers
-// Each launcher covers every stream of the batch; `tiles[s]` is the number of
-// CTAs stream s needs and is turned into the device tile table by the caller.
+__device__ __forceinline__ bool stream_active(const Batch& bt, int s) { return !bt.active || __ldg(bt.active + s); }
 
-enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileNodes, kTileBlocks, kTileRows6,
-                kTileKinds };
+struct GridBarrier {   // counter barrier used by the timeout probe
+  unsigned int count;
+  unsigned int gen;
+};
+
+// ------------------------------------------------------------------ launchers
+
+enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileKinds };
 
 struct BatchHost {
   Batch bt;
   int total_tiles[kTileKinds];
   int* tile_base_dev[kTileKinds];   // device, per kind
+  int spin_limit;                   // bounded wait of the PCG's reductions (polls)
 };
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st);
 void launch_knn_skin(const SwDev& d, const float4* v_orig, int n_s, int* ids_tmp, float* d2_tmp, int4* knn_out,
                      float4* w_out, cudaStream_t st);
 void launch_node_graph(const SwDev& d, cudaStream_t st);
+void launch_solve_begin(const BatchHost& b, cudaStream_t st);
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
-void launch_pcg_init(const BatchHost& b, cudaStream_t st);
-void launch_pcg_spmv(const BatchHost& b, int k, cudaStream_t st);
-void launch_pcg_update(const BatchHost& b, int k, cudaStream_t st);
-void launch_apply_update(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
+cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
 void launch_warp_live(const BatchHost& b, cudaStream_t st);
 void launch_index_map(const BatchHost& b, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
+int pcg_blocks_per_sm();
+int pcg_threads();
+cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
+                                 int* status, cudaStream_t st);
 
 // tile sizes
 constexpr int kSurfTile = 256;
 constexpr int kAsmTile = 256;
-constexpr int kNodeTile = 128;
 constexpr int kBlkTile = 128;
-constexpr int kRowTile = 192;   // 32 rows x 6 components
 
 inline int tiles_for(int kind, const SwDev& d) {
   switch (kind) {
     case kTilePixels: return ((d.W + 31) / 32) * ((d.H + 7) / 8);   // 32x8 pixel tiles
     case kTileSurfels: return (d.n_s + kSurfTile - 1) / kSurfTile;
     case kTileSurfelsAssembly: return (d.n_s + kAsmTile - 1) / kAsmTile;
-    case kTileNodes: return (d.n_n + kNodeTile - 1) / kNodeTile;
     case kTileBlocks: return (d.nnzb + kBlkTile - 1) / kBlkTile;
-    case kTileRows6: return (6 * d.n_n + kRowTile - 1) / kRowTile;
+    case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
   }
   return 0;
 }
