@@ -204,6 +204,118 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _batch_member_data(args):
+    """Build member k of the uneven multi-stream workload in a worker process."""
+    k, frame_ids, scale = args
+    import synth
+    from paper_1904_13073_gb300 import model_arrays
+    s = synth.batch_member(k, scale=scale)
+    c = s.cam
+    return k, {"name": s.name, "cam": (c.width, c.height, c.fx, c.fy, c.cx, c.cy),
+               "arrays": model_arrays(s), "frames": [s.frame(t) for t in frame_ids],
+               "gn": s.gn_iters, "pcg": s.pcg_iters}
+
+
+def batch_workload(n_streams, frame_ids, scale=1.0):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=max(1, min(os.cpu_count() or 4, n_streams))) as pool:
+        out = dict(pool.map(_batch_member_data, [(k, frame_ids, scale) for k in range(n_streams)]))
+    return [out[k] for k in range(n_streams)]
+
+
+def run_batched(sw, torch, members, rounds, warmup, flush, stream):
+    """The uneven streams advanced one frame per round, first one stream at a
+    time (every call serialised on one CUDA stream: the plain solve), then as
+    one batch (one launch per stage for all streams).  Device time per round
+    by CUDA events; L2 flushed between rounds outside the events."""
+    from types import SimpleNamespace
+    handles, dev_frames, nnzb, n_s, n_n, n_pix = [], [], [], [], [], []
+    for m in members:
+        w, h_, fx, fy, cx, cy = m["cam"]
+        cam = SimpleNamespace(width=w, height=h_, fx=fx, fy=fy, cx=cx, cy=cy)
+        v4, n4, t2, node4 = m["arrays"]
+        hd = sw.sw_create_stream(sw.params_for(cam, len(v4), len(node4)), stream)
+        sw.sw_set_model(hd, v4, n4, t2, node4)
+        handles.append(hd)
+        dev_frames.append([torch.from_numpy(f).cuda() for f in m["frames"]])
+        n_s.append(len(v4))
+        n_n.append(len(node4))
+        n_pix.append(w * h_)
+    gn, pcg = members[0]["gn"], members[0]["pcg"]
+    nf = len(members[0]["frames"])
+    S = len(members)
+    for hd, fr in zip(handles, dev_frames):       # structure sizes and a first frame
+        sw.sw_upload_depth(hd, fr[0], 1)
+        nnzb.append(sw.sw_debug_assemble(hd)[0])
+    torch.cuda.synchronize()
+
+    def timed(fn, n_rounds, n_warm):
+        lat = []
+        for r in range(n_warm + n_rounds):
+            with torch.cuda.stream(stream):
+                flush.fill_(r & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(r)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r >= n_warm:
+                lat.append(a.elapsed_time(b))
+        return np.array(lat)
+
+    def plain_round(r):
+        t = 2 + (r % nf)
+        for hd, fr in zip(handles, dev_frames):
+            sw.sw_upload_depth(hd, fr[r % nf], t)
+            sw.sw_solve_frame(hd, gn, pcg, want_stats=False)
+            sw.sw_fuse_frame(hd)
+
+    lat_plain = timed(plain_round, rounds, warmup)
+    b = sw.sw_batch_create(handles, stream)
+
+    def batch_round(r):
+        t = 2 + (r % nf)
+        sw.sw_batch_upload_depth(b, [fr[r % nf] for fr in dev_frames], [t] * S)
+        sw.sw_batch_solve(b, gn, pcg, want_stats=False)
+        sw.sw_batch_fuse(b)
+
+    lat_batch = timed(batch_round, rounds, warmup)
+    # live stage times of one profiled batched round, and its associations
+    sw.sw_batch_set_profiling(b, True)
+    prof = {}
+    for r in range(2):
+        batch_round(r)
+        prof = sw.sw_batch_read_profile(b)
+    sw.sw_batch_set_profiling(b, False)
+    stats = sw.sw_batch_solve(b, gn, pcg)
+    n_corr = [int(np.mean(st["n_corr"])) for st in stats]
+    sw.sw_batch_destroy(b)
+    for hd in handles:
+        sw.sw_destroy_stream(hd)
+    data_bytes = sum(stage_bytes(n_s[k], n_n[k], nnzb[k], n_corr[k], n_pix[k], pcg)["data_assembly"] for k in range(S))
+    peak, src = measured_hbm_peak()
+    t_data = prof["data_assembly"][0] / prof["data_assembly"][1] / 1000.0
+    return {
+        "workload": f"{S} streams of uneven size (depth 320x240..640x480, 40k-400k surfels, 256-4096 nodes, "
+                    f"log-uniform; sphere / torus / wavy plane), {gn} GN x {pcg} PCG + fusion per frame",
+        "streams": [m["name"] for m in members],
+        "plain": {"frames_per_s": S * 1000.0 / float(lat_plain.mean()),
+                  "round_ms_p50": float(np.percentile(lat_plain, 50)),
+                  "round_ms_p99": float(np.percentile(lat_plain, 99))},
+        "batched": {"frames_per_s": S * 1000.0 / float(lat_batch.mean()),
+                    "round_ms_p50": float(np.percentile(lat_batch, 50)),
+                    "round_ms_p99": float(np.percentile(lat_batch, 99))},
+        "speedup": float(lat_plain.mean() / lat_batch.mean()),
+        "stages_ms_per_round": {k: v[0] for k, v in prof.items()},
+        "data_assembly_roofline": {"bound": "hbm", "achieved": data_bytes / t_data / 1e9, "peak": peak,
+                                   "unit": "GB/s", "frac": data_bytes / t_data / 1e9 / peak,
+                                   "bytes_per_launch": data_bytes, "us_per_launch": t_data * 1e6,
+                                   "peak_source": src},
+        "l2": "flushed between rounds (512 MiB write outside the events)",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +323,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-streams", type=int, default=16, help="streams of the uneven batched workload (0: skip)")
+    ap.add_argument("--batch-rounds", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -223,6 +337,7 @@ def main():
     ts = [1 + (k % (scene.n_frames - 1)) for k in range(n_frames)]
     frames = render_frames(0, sorted(set(ts)), os.cpu_count() or 4)
     frame_of = dict(zip(sorted(set(ts)), frames))
+    members = batch_workload(args.batch_streams, [2, 3, 4], 1.0) if args.batch_streams > 0 and rank == 0 else []
 
     import torch
     import paper_1904_13073_gb300 as sw
@@ -314,6 +429,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
     sw.sw_destroy_stream(h)
+    batched = run_batched(sw, torch, members, args.batch_rounds, 2, flush, stream) if members else None
 
     if rank != 0:
         return
@@ -337,6 +453,8 @@ def main():
         "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
         "stage_roofline": roof["stages"],
     }
+    if batched:
+        line["multi_stream"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(scene, frame_of[ts[0]], gn, pcg)
     print(json.dumps(line))

@@ -241,13 +241,20 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
       for (int i = 0; i < n; ++i)
         want[i] = 1 + (rest > 0 ? (int)((long long)(want[i] - 1) * left / rest) : 0);
     }
-    int acc = 0;
+    int acc = 0, rows_cap = 1;
     for (int i = 0; i < n; ++i) {
       tiles[(size_t)kTilePcg * (n + 1) + i] = acc;
       acc += want[i];
+      rows_cap = std::max(rows_cap, (devs[i].n_n + want[i] - 1) / want[i]);
     }
     tiles[(size_t)kTilePcg * (n + 1) + n] = acc;
     r->bh.total_tiles[kTilePcg] = acc;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (pcg_smem_bytes(rows_cap) > (size_t)optin)
+      return fail(err_to, SW_ERR_INVALID_ARG, "a stream has too many nodes for the PCG's on-chip state");
+    r->bh.pcg_rows_cap = rows_cap;
   }
   SwDev* devs_dev = nullptr;
   int* tile_dev = nullptr;

@@ -356,6 +356,15 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, int
   return s_ok != 0;
 }
 
+// a / b for positive FP64 dot products, rounded to FP32: the exponents are
+// split off exactly (frexp) and only the mantissa ratio is divided, in FP32
+// (an FP64 division is ~550 cycles on this part; the ratio is used in FP32).
+__device__ __forceinline__ float ratio_f32(double a, double b) {
+  int ea, eb;
+  const double ma = frexp(a, &ea), mb = frexp(b, &eb);
+  return ldexpf(__fdiv_rn((float)ma, (float)mb), ea - eb);
+}
+
 // Packed lower-triangular index (r >= c).
 __device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
@@ -478,21 +487,25 @@ __device__ __forceinline__ bool stream_reduce(double v, PartSlot* part, int t, i
 
 // One persistent launch runs the PCG of every active stream of the batch and
 // applies the increments.  Stream s owns the CTAs [tile_base[s],
-// tile_base[s+1]) (all co-resident: cooperative launch); its block rows are
-// dealt round-robin over those CTAs (row i -> CTA i mod G_s, one warp per
-// row), its nodes likewise (node j -> CTA j mod G_s, one thread per node).
-// The two reductions of every iteration (pᵀq, rᵀz) are also the only
+// tile_base[s+1]) (all co-resident: cooperative launch).  CTA t of a stream
+// with G CTAs owns the nodes and block rows i = t + G a (a = 0, 1, ...) and
+// keeps everything about them in shared memory for the whole solve: the
+// inverse Cholesky factors of their diagonal blocks and their x, r, z, q and
+// p.  Global memory carries only what other CTAs read: z and p of every node.
+// The two reductions of an iteration (pᵀq, rᵀz) are also its only
 // synchronisation, and they are per stream, so streams never wait for one
 // another (stream_reduce).  Per iteration:
-//   SpMV    a warp per block row, a lane per 6x6 block of the row: the block
-//           times the neighbour's p = z + β p_old (formed on the fly), then a
-//           warp sum of the six outputs;
-//   update  x += α p, r −= α q, z = M⁻¹ r per node.
+//   SpMV    a warp per own block row, a lane per 6x6 block of the row: the
+//           block times the neighbour's p = z + β p_old (formed on the fly
+//           from global memory), a warp sum of the six outputs;
+//   update  x += α p, r −= α q, z = M⁻¹ r per own node, in shared memory.
 // All dot products are accumulated in FP64; the 6x6 factorisations are FP64.
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgWarps = kPcgThreads / 32;
+constexpr int kPcgRowFloats = 21 + 5 * 6;   // Li, then x, r, z, q, p
 
-__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_it, int spin_limit) {
+__global__ void __launch_bounds__(kPcgThreads, 1)
+k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap) {
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -500,14 +513,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
   const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d.n_n;
+  const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
   const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
-  const int node_step = Gs * kPcgThreads, row_step = Gs * kPcgWarps;
-  const int node0 = t + Gs * tid, row0 = t + Gs * warp;
+  extern __shared__ float smem_f[];
+  float* sli = smem_f;
+  float* sx = sli + 21 * rows_cap;
+  float* sr = sx + 6 * rows_cap;
+  float* sz = sr + 6 * rows_cap;
+  float* sq = sz + 6 * rows_cap;
+  float* sp = sq + 6 * rows_cap;
 
   // ---- set-up: preconditioner, r = −g, z = M⁻¹ r, x = 0
   double acc = 0.0;
-  for (int j = node0; j < n; j += node_step) {
-    float* li = d.Li + (size_t)j * 21;
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
+    float* li = sli + 21 * a;
     if (!chol_inverse_factor(d.A + (size_t)d.row_ptr[j] * 36, li)) {
       atomicOr(d.status, kStatusBreakdown);
 #pragma unroll
@@ -515,10 +535,14 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
     }
     float r[6], z[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) { r[c] = -d.g[6 * j + c]; d.r[6 * j + c] = r[c]; d.x[6 * j + c] = 0.f; }
+    for (int c = 0; c < 6; ++c) { r[c] = -d.g[6 * j + c]; sr[6 * a + c] = r[c]; sx[6 * a + c] = 0.f; }
     apply_precond(li, r, z);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) { d.z[6 * j + c] = z[c]; acc += (double)r[c] * (double)z[c]; }
+    for (int c = 0; c < 6; ++c) {
+      sz[6 * a + c] = z[c];
+      d.z[6 * j + c] = z[c];
+      acc += (double)r[c] * (double)z[c];
+    }
   }
   double rz, rz_prev = 1.0;
   if (!stream_reduce(acc, d.part, t, Gs, base + 1, spin_limit, &rz)) { atomicOr(d.status, kStatusTimeout); return; }
@@ -526,12 +550,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
 
   for (int k = 0; k < K; ++k) {
     const bool work = !bad && rz != 0.0;
-    const float beta = (k == 0 || !work) ? 0.f : (float)(rz / rz_prev);
+    const float beta = (k == 0 || !work) ? 0.f : ratio_f32(rz, rz_prev);
     const float* __restrict__ pold = (k & 1) ? d.p0 : d.p1;
     float* __restrict__ pnew = (k & 1) ? d.p1 : d.p0;
     acc = 0.0;
     if (work) {
-      for (int i = row0; i < n; i += row_step) {
+      for (int a = warp; a < nr; a += kPcgWarps) {
+        const int i = t + Gs * a;
         float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int e1 = d.rl_ptr[i + 1];
         for (int e = d.rl_ptr[i] + lane; e < e1; e += 32) {
@@ -541,17 +566,17 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
           load_p(d.z, pold, ent.y, beta, k == 0, p);
           const bool tr = ent.x < 0;
 #pragma unroll
-          for (int a = 0; a < 6; ++a) {
-            const float2 b0 = __ldg(B2 + 3 * a), b1 = __ldg(B2 + 3 * a + 1), b2 = __ldg(B2 + 3 * a + 2);
+          for (int b = 0; b < 6; ++b) {
+            const float2 b0 = __ldg(B2 + 3 * b), b1 = __ldg(B2 + 3 * b + 1), b2 = __ldg(B2 + 3 * b + 2);
             const float row[6] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y};
             if (!tr) {
               float u = 0.f;
 #pragma unroll
               for (int q = 0; q < 6; ++q) u += row[q] * p[q];
-              v[a] += u;
+              v[b] += u;
             } else {
 #pragma unroll
-              for (int q = 0; q < 6; ++q) v[q] += p[a] * row[q];
+              for (int q = 0; q < 6; ++q) v[q] += p[b] * row[q];
             }
           }
         }
@@ -561,10 +586,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
           float vc = v[0];
 #pragma unroll
           for (int c = 1; c < 6; ++c) if (lane == c) vc = v[c];
-          float pi = __ldcg(d.z + 6 * i + lane);
-          if (k > 0) pi += beta * __ldcg(pold + 6 * i + lane);
+          const float pi = k == 0 ? sz[6 * a + lane] : sz[6 * a + lane] + beta * sp[6 * a + lane];
+          sp[6 * a + lane] = pi;
+          sq[6 * a + lane] = vc;
           pnew[6 * i + lane] = pi;
-          d.q[6 * i + lane] = vc;
           acc += (double)pi * (double)vc;
         }
       }
@@ -580,19 +605,23 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
         bad = true;
         if (t == 0 && tid == 0) atomicOr(d.status, kStatusBreakdown);
       } else {
-        const float alpha = (float)(rz / pq);
-        for (int j = node0; j < n; j += node_step) {
+        const float alpha = ratio_f32(rz, pq);
+        for (int a = tid; a < nr; a += kPcgThreads) {
           float r[6], z[6];
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
-            const int ix = 6 * j + c;
-            d.x[ix] += alpha * __ldcg(pnew + ix);
-            r[c] = d.r[ix] - alpha * __ldcg(d.q + ix);
-            d.r[ix] = r[c];
+            sx[6 * a + c] += alpha * sp[6 * a + c];
+            r[c] = sr[6 * a + c] - alpha * sq[6 * a + c];
+            sr[6 * a + c] = r[c];
           }
-          apply_precond(d.Li + (size_t)j * 21, r, z);
+          apply_precond(sli + 21 * a, r, z);
+          const int j = t + Gs * a;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) { d.z[6 * j + c] = z[c]; acc += (double)r[c] * (double)z[c]; }
+          for (int c = 0; c < 6; ++c) {
+            sz[6 * a + c] = z[c];
+            d.z[6 * j + c] = z[c];
+            acc += (double)r[c] * (double)z[c];
+          }
         }
       }
     }
@@ -606,10 +635,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg(Batch bt, int K, int gn_
   if (t == 0 && tid == 0) d.pcg_rz[gn_it] = rz;
   // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
   if (bad || (__ldcg(d.status) & kStatusBreakdown)) return;
-  for (int j = node0; j < n; j += node_step) {
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
     float xi[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) xi[c] = d.x[6 * j + c];
+    for (int c = 0; c < 6; ++c) xi[c] = sx[6 * a + c];
     float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
     apply_increment(q0, qe, xi);
     d.dq[2 * j] = q0;
@@ -656,6 +686,8 @@ int pcg_blocks_per_sm() {
 
 int pcg_threads() { return kPcgThreads; }
 
+size_t pcg_smem_bytes(int rows_cap) { return sizeof(float) * (size_t)kPcgRowFloats * rows_cap; }
+
 // One cooperative launch: every CTA is resident, so the waits of
 // stream_reduce always end (and are bounded regardless).
 cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st) {
@@ -663,10 +695,19 @@ cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_
   if (nb == 0) return cudaSuccess;
   Batch bt = with_kind(b, kTilePcg);
   int spin = b.spin_limit;
-  void* args[] = {&bt, &pcg_iters, &gn_it, &spin};
+  int rows_cap = b.pcg_rows_cap;
+  const size_t smem = pcg_smem_bytes(rows_cap);
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
+    const cudaError_t e = cudaFuncSetAttribute(k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  void* args[] = {&bt, &pcg_iters, &gn_it, &spin, &rows_cap};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nb);
   cfg.blockDim = dim3(kPcgThreads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -123,6 +123,7 @@ struct BatchHost {
   int total_tiles[kTileKinds];
   int* tile_base_dev[kTileKinds];   // device, per kind
   int spin_limit;                   // bounded wait of the PCG's reductions (polls)
+  int pcg_rows_cap;                 // most rows one PCG CTA owns in the batch
 };
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st);
@@ -139,6 +140,7 @@ void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
 int pcg_blocks_per_sm();
 int pcg_threads();
+size_t pcg_smem_bytes(int rows_cap);
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
                                  int* status, cudaStream_t st);
 

@@ -451,23 +451,144 @@ def random_rigid_dq_inputs(seed: int, n: int, max_angle_deg: float = 10.0,
     return axis, ang, tr
 
 
-def batch_scenes(n_streams: int = 16, seed: int = 0, scale: float = 1.0):
-    """Streams of uneven size for multi-stream batching.
+def _render_param(cam, surf, u0, deform, noise, outlier_frac, rng):
+    """Depth of a deformed parametric surface x = deform(surf(u)), u in R^2.
 
-    Depth 320x240..640x480, surfels 40k..400k and nodes 256..4096, sizes drawn
-    log-uniformly; each stream is a bending sphere with its own seed.
-    ``scale`` shrinks surfel and node counts for quick tests.
+    The undeformed surface is sampled at ``u0`` (n, 2) and splatted into a
+    per-pixel z-buffer to pick each pixel's starting parameter; Newton then
+    puts the deformed point exactly on the pixel's ray.  Pixels whose
+    surface faces away or whose solve does not converge stay invalid.
     """
+    a, b = cam.rays()
+    x0 = deform(surf(u0))
+    z0 = x0[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        px = np.floor(cam.fx * x0[:, 0] / z0 + cam.cx + 0.5)
+        py = np.floor(cam.fy * x0[:, 1] / z0 + cam.cy + 0.5)
+    ok = (z0 > 0) & (px >= 0) & (px < cam.width) & (py >= 0) & (py < cam.height)
+    lin = (py[ok] * cam.width + px[ok]).astype(np.int64)
+    order = np.lexsort((z0[ok], lin))
+    first = np.ones(len(order), dtype=bool)
+    first[1:] = lin[order][1:] != lin[order][:-1]
+    pix = lin[order][first]
+    start = u0[ok][order][first]
+    aa, bb = a.ravel()[pix], b.ravel()[pix]
+
+    def fun(p):
+        w = deform(surf(p))
+        return np.stack([w[:, 0] - aa * w[:, 2], w[:, 1] - bb * w[:, 2]], -1)
+
+    p, conv = _newton2(fun, start)
+    w = deform(surf(p))
+    h = 1e-6
+    tu = deform(surf(p + np.array([h, 0.0]))) - deform(surf(p - np.array([h, 0.0])))
+    tv = deform(surf(p + np.array([0.0, h]))) - deform(surf(p - np.array([0.0, h])))
+    nrm = np.cross(tu, tv)
+    ray = np.stack([aa, bb, np.ones_like(aa)], axis=-1)
+    facing = np.abs(np.sum(nrm * ray, axis=1)) > 1e-3 * np.linalg.norm(nrm, axis=1) * np.linalg.norm(ray, axis=1)
+    good = conv & facing & (w[:, 2] > 0)
+    depth = np.zeros(cam.width * cam.height)
+    depth[pix[good]] = w[good, 2]
+    valid = depth > 0
+    depth = depth + rng.normal(0.0, noise, depth.shape) * valid
+    if outlier_frac > 0:
+        n_out = int(round(outlier_frac * depth.size))
+        pos = rng.choice(depth.size, n_out, replace=False)
+        depth[pos] = rng.uniform(0.5, 2.0, n_out)
+    return depth.reshape(cam.height, cam.width)
+
+
+def _param_scene(name, cam, surf, u_model, u_render, seed, n_nodes, noise, outliers, n_frames,
+                 conf=15.0):
+    """Reference surfels at surf(u_model) with normals from the parameter
+    derivatives (oriented towards the camera), voxel-subsampled nodes, and
+    frames of the surface bent by three sinusoidal fields."""
     rng = np.random.default_rng(seed)
-    scenes = []
-    for s in range(n_streams):
-        w = int(rng.choice([320, 480, 640]))
-        h = w * 3 // 4
-        ns = int(np.exp(rng.uniform(np.log(40_000), np.log(400_000))) * scale)
-        nn = int(np.exp(rng.uniform(np.log(256), np.log(4096))) * min(1.0, scale * 4))
-        nn = max(nn, 16)
-        ns = max(ns, 20 * nn)
-        scenes.append(plain_full(seed=100 + s, n_surfels=ns, n_nodes=nn,
-                                 width=w, height=h, f=570.0 * w / 640.0,
-                                 n_frames=100))
-    return scenes
+    v = surf(u_model)
+    h = 1e-6
+    tu = surf(u_model + np.array([h, 0.0])) - surf(u_model - np.array([h, 0.0]))
+    tv = surf(u_model + np.array([0.0, h])) - surf(u_model - np.array([0.0, h]))
+    n = _unit(np.cross(tu, tv))
+    n = np.where((np.sum(n * v, axis=1) > 0)[:, None], -n, n)
+    node_p, vox = _voxel_nodes(v, n_nodes)
+    bend = _Bending(rng)
+    spacing = np.sqrt(np.linalg.norm(np.cross(tu, tv), axis=1) / (4 * h * h)
+                      * (np.ptp(u_model[:, 0]) * np.ptp(u_model[:, 1]) / len(u_model)))
+
+    def frame(t):
+        fr = np.random.default_rng([seed, 4000 + t])
+        return _render_param(cam, surf, u_render, lambda x: bend(x, t), noise, outliers, fr)
+
+    ns = len(v)
+    return Scene(name=name, cam=cam, surfel_v=_f32(v), surfel_n=_f32(n),
+                 surfel_r=_f32(np.maximum(spacing, 1e-4)), surfel_c=np.full(ns, conf, dtype=np.float32),
+                 surfel_t=np.zeros((ns, 2), dtype=np.int32), node_p=_f32(node_p),
+                 node_sigma=np.full(len(node_p), vox, dtype=np.float32), n_frames=n_frames,
+                 gn_iters=10, pcg_iters=20, _frame_fn=frame, truth={"bend": bend})
+
+
+def wavy_plane(seed: int = 0, n_surfels: int = 100_000, n_nodes: int = 1024, width: int = 640,
+               height: int = 480, f: float = 570.0, noise: float = 1.5e-3, outliers: float = 0.01,
+               n_frames: int = 100) -> Scene:
+    """A bending wavy sheet z = 1.1 + 0.04 sin(7x) cos(5y) facing the camera."""
+    cam = Camera(width, height, f, f, width / 2.0, height / 2.0)
+    hx, hy = 0.5 * width / f * 1.1, 0.5 * height / f * 1.1
+
+    def surf(u):
+        x, y = u[:, 0] * hx, u[:, 1] * hy
+        return np.stack([x, y, 1.1 + 0.04 * np.sin(7 * x) * np.cos(5 * y)], axis=-1)
+
+    m = int(np.sqrt(n_surfels * hx / hy))
+    k = max(2, n_surfels // max(m, 1))
+    gu, gv = np.meshgrid(np.linspace(-1, 1, m), np.linspace(-1, 1, k))
+    u_model = np.stack([gu.ravel(), gv.ravel()], -1)[:n_surfels]
+    ru, rv = np.meshgrid(np.linspace(-1, 1, 3 * width), np.linspace(-1, 1, 3 * height))
+    return _param_scene(f"wavy_{width}x{height}_{len(u_model)}s_{n_nodes}n", cam, surf, u_model,
+                        np.stack([ru.ravel(), rv.ravel()], -1), seed, n_nodes, noise, outliers, n_frames)
+
+
+def torus(seed: int = 0, n_surfels: int = 200_000, n_nodes: int = 2048, width: int = 640, height: int = 480,
+          f: float = 570.0, noise: float = 1.5e-3, outliers: float = 0.01, n_frames: int = 100) -> Scene:
+    """A bending torus (R = 0.25 m, r = 0.08 m) at 1.2 m, tilted 40 degrees."""
+    cam = Camera(width, height, f, f, width / 2.0, height / 2.0)
+    R, r = 0.25, 0.08
+    tilt = _rot_axis_angle(np.array([[1.0, 0.0, 0.0]]), np.array([np.deg2rad(40.0)]))[0]
+    center = np.array([0.0, 0.0, 1.2])
+
+    def surf(u):
+        a, b = np.pi * u[:, 0], np.pi * u[:, 1]
+        p = np.stack([(R + r * np.cos(b)) * np.cos(a), (R + r * np.cos(b)) * np.sin(a), r * np.sin(b)], -1)
+        return p @ tilt.T + center
+
+    m = int(np.sqrt(n_surfels * R / r))
+    k = max(2, n_surfels // max(m, 1))
+    gu, gv = np.meshgrid(np.linspace(-1, 1, m, endpoint=False), np.linspace(-1, 1, k, endpoint=False))
+    u_model = np.stack([gu.ravel(), gv.ravel()], -1)[:n_surfels]
+    ru, rv = np.meshgrid(np.linspace(-1, 1, 2000, endpoint=False), np.linspace(-1, 1, 700, endpoint=False))
+    return _param_scene(f"torus_{width}x{height}_{len(u_model)}s_{n_nodes}n", cam, surf, u_model,
+                        np.stack([ru.ravel(), rv.ravel()], -1), seed, n_nodes, noise, outliers, n_frames)
+
+
+def batch_member(k: int, seed: int = 0, scale: float = 1.0) -> Scene:
+    """Member k of the uneven multi-stream workload: depth 320x240..640x480,
+    surfels 40k..400k and nodes 256..4096 drawn log-uniformly (seeded by k),
+    shapes cycling sphere, torus, wavy plane."""
+    rng = np.random.default_rng([seed, k])
+    w = int(rng.choice([320, 480, 640]))
+    h = w * 3 // 4
+    ns = int(np.exp(rng.uniform(np.log(40_000), np.log(400_000))) * scale)
+    nn = int(np.exp(rng.uniform(np.log(256), np.log(4096))) * min(1.0, scale * 4))
+    nn = max(nn, 16)
+    ns = max(ns, 20 * nn)
+    f = 570.0 * w / 640.0
+    shape = k % 3
+    if shape == 0:
+        return plain_full(seed=100 + k, n_surfels=ns, n_nodes=nn, width=w, height=h, f=f)
+    if shape == 1:
+        return torus(seed=100 + k, n_surfels=ns, n_nodes=nn, width=w, height=h, f=f)
+    return wavy_plane(seed=100 + k, n_surfels=ns, n_nodes=nn, width=w, height=h, f=f)
+
+
+def batch_scenes(n_streams: int = 16, seed: int = 0, scale: float = 1.0):
+    """The uneven multi-stream workload (see ``batch_member``)."""
+    return [batch_member(k, seed, scale) for k in range(n_streams)]
