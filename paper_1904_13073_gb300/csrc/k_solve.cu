@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
 // ------------------------------------------------------------------ K4+K5: data term
 
 constexpr int kJS = 25;   // 24 Jacobian entries + residual per term
+constexpr int kAsmChunks = kAsmTile / 14;                        // 18 chunks x 14 outputs = 252 threads
 
-__global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it, int write_live) {
+__global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_it, int write_live) {
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -187,11 +188,9 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
 
   __shared__ float sJ[kAsmTile * kJS];
   __shared__ int sset[kAsmTile];
-  __shared__ int sseg_start[kAsmTile + 1];
-  __shared__ int sseg_active[kAsmTile];
-  __shared__ int swarp_cnt[kAsmTile / 32];
+  __shared__ int swarp[kAsmTile / 32];
 
-  float* myJ = sJ + tid * kJS;
+  float Jr[24];
   int set = -1;
   bool valid = false;
   float res = 0.f;
@@ -230,53 +229,55 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
       for (int k = 0; k < 4; ++k) {
         const float4 q0 = __ldg(d.dq + 2 * id[k]), qe = __ldg(d.dq + 2 * id[k] + 1);
         const float ws = qdot(q0, qref) >= 0.f ? wk[k] : -wk[k];
-        node_jacobian(gr, q0, qe, ws, myJ + 6 * k);
+        node_jacobian(gr, q0, qe, ws, Jr + 6 * k);
       }
-      myJ[24] = res;
     }
   }
-  if (!valid) {
-#pragma unroll
-    for (int k = 0; k < kJS; ++k) myJ[k] = 0.f;
-  }
-  sset[tid] = set;
 
-  // statistics
-  block_atomic_sum<double>((double)(res * res), d.e_depth + gn_it);
-  {
-    const int c = __syncthreads_count(valid);
-    if (tid == 0 && c) atomicAdd(d.n_corr + gn_it, c);
-  }
-
-  // segments: maximal runs of equal set id within the tile
-  const bool head = (tid == 0) || (sset[tid] != sset[tid - 1]);
-  const unsigned hb = __ballot_sync(0xffffffffu, head);
+  // statistics: E_depth is a diagnostic (FP32 warp sums, one FP64 atomic per warp)
   const int lane = tid & 31, wid = tid >> 5;
-  if (lane == 0) swarp_cnt[wid] = __popc(hb);
+  {
+    const float e = warp_sum(res * res);
+    if (lane == 0 && e != 0.f) atomicAdd(d.e_depth + gn_it, (double)e);
+  }
+
+  // compact the tile's associated terms, in order, into shared memory
+  const unsigned vb = __ballot_sync(0xffffffffu, valid);
+  if (lane == 0) swarp[wid] = __popc(vb);
   __syncthreads();
-  int before = 0, nseg = 0;
+  int pos = __popc(vb & ((1u << lane) - 1u)), nvalid = 0;
 #pragma unroll
   for (int k = 0; k < kAsmTile / 32; ++k) {
-    const int c = swarp_cnt[k];
-    if (k < wid) before += c;
-    nseg += c;
+    const int c = swarp[k];
+    if (k < wid) pos += c;
+    nvalid += c;
   }
-  const int seg = before + __popc(hb & ((2u << lane) - 1u)) - 1;
-  if (head) { sseg_start[seg] = tid; sseg_active[seg] = 0; }
-  if (tid == 0) sseg_start[nseg] = kAsmTile;
+  if (valid) {
+    float* dst = sJ + pos * kJS;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) dst[k] = Jr[k];
+    dst[24] = res;
+    sset[pos] = set;
+  }
+  if (tid == 0 && nvalid) atomicAdd(d.n_corr + gn_it, nvalid);
   __syncthreads();
-  if (valid) sseg_active[seg] = 1;
-  __syncthreads();
+  if (nvalid == 0) return;
 
-  // work items: (segment, item) with items 0..9 = upper blocks (a<=b), 10..13 = Jᵀe of node a
-  const int nitems = nseg * 14;
-  for (int it = tid; it < nitems; it += kAsmTile) {
-    const int sg = it / 14, item = it - sg * 14;
-    if (!sseg_active[sg]) continue;
-    const int t0 = sseg_start[sg], t1 = sseg_start[sg + 1];
-    const int st_ = sset[t0];
-    if (st_ < 0) continue;
-    const int* slots = d.set_slots + (size_t)st_ * 14;
+  // JᵀJ and Jᵀe of the tile's terms, balanced over the threads: thread
+  // (item, chunk) owns one of the 14 outputs of a node set -- items 0..9 the
+  // upper blocks (a <= b) of its 4 nodes, 10..13 the Jᵀe segments -- over one
+  // chunk of consecutive terms.  It accumulates while the set id stays the
+  // same and adds the sum to the system (16-byte vector atomics) whenever the
+  // set changes or the chunk ends, so node sets of any size cost every thread
+  // about the same.
+  // item-major: a warp's lanes take the same item on neighbouring chunks (no
+  // divergence between block and Jᵀe items); an odd chunk length keeps the
+  // lanes' shared-memory rows in different banks
+  const int item = tid / kAsmChunks, chunk = tid - item * kAsmChunks;
+  const int len = ((nvalid + kAsmChunks - 1) / kAsmChunks) | 1;
+  if (item < 14) {
+    const int t0 = min(nvalid, chunk * len), t1 = min(nvalid, t0 + len);
+    if (t0 >= t1) return;
     if (item < 10) {
       // pair index -> (a, b): (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3)
       const int a = item < 4 ? 0 : item < 7 ? 1 : item < 9 ? 2 : 3;
@@ -284,7 +285,21 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
       float acc[36];
 #pragma unroll
       for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-      for (int t = t0; t < t1; ++t) {
+      int cur = sset[t0];
+      int slot = __ldg(d.set_slots + (size_t)cur * 14 + item);
+      for (int t = t0; t <= t1; ++t) {
+        const int st_ = t < t1 ? sset[t] : -1;
+        if (st_ != cur) {
+          float4* dst = reinterpret_cast<float4*>(d.A + (size_t)slot * 36);
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            atomicAdd(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
+          if (t == t1) break;
+#pragma unroll
+          for (int k = 0; k < 36; ++k) acc[k] = 0.f;
+          cur = st_;
+          slot = __ldg(d.set_slots + (size_t)cur * 14 + item);
+        }
         const float* Jt = sJ + t * kJS;
         float ja[6], jb[6];
 #pragma unroll
@@ -294,21 +309,28 @@ __global__ void __launch_bounds__(kAsmTile) k_data_assemble(Batch bt, int gn_it,
 #pragma unroll
           for (int q = 0; q < 6; ++q) acc[p * 6 + q] += ja[p] * jb[q];
       }
-      float* dst = d.A + (size_t)__ldg(slots + item) * 36;
-#pragma unroll
-      for (int k = 0; k < 36; ++k) atomicAdd(dst + k, acc[k]);
     } else {
       const int a = item - 10;
       float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int t = t0; t < t1; ++t) {
+      int cur = sset[t0];
+      int node = __ldg(d.set_slots + (size_t)cur * 14 + 10 + a);
+      for (int t = t0; t <= t1; ++t) {
+        const int st_ = t < t1 ? sset[t] : -1;
+        if (st_ != cur) {
+          float2* dst = reinterpret_cast<float2*>(d.g + (size_t)node * 6);   // 8-byte aligned
+#pragma unroll
+          for (int k = 0; k < 3; ++k) atomicAdd(dst + k, make_float2(acc[2 * k], acc[2 * k + 1]));
+          if (t == t1) break;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) acc[k] = 0.f;
+          cur = st_;
+          node = __ldg(d.set_slots + (size_t)cur * 14 + 10 + a);
+        }
         const float* Jt = sJ + t * kJS;
         const float rr = Jt[24];
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc[k] += Jt[6 * a + k] * rr;
       }
-      float* dst = d.g + (size_t)__ldg(slots + 10 + a) * 6;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) atomicAdd(dst + k, acc[k]);
     }
   }
 }
