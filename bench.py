@@ -16,6 +16,7 @@ import argparse
 import json
 import multiprocessing as mp
 import os
+import tempfile
 import subprocess
 import sys
 import time
@@ -325,6 +326,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-streams", type=int, default=16, help="streams of the uneven batched workload (0: skip)")
     ap.add_argument("--batch-rounds", type=int, default=5)
+    ap.add_argument("--clocks-csv", default="", help="keep the nvidia-smi clock samples here ({rank} is replaced)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -377,8 +379,9 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/sw_clocks.csv") as clk:
+    clocks_csv = args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else os.path.join(
+        tempfile.gettempdir(), f"sw_clocks_rank{rank}.csv")
+    with Clocks(clocks_csv) as clk:
         for k in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xff)

@@ -22,8 +22,8 @@ decides an integer (k-NN selection, projective association, index-map
 sub-pixel and depth key, fusion candidate tests): those decisions are taken in
 FP32 with a fixed operation order, the precision the CUDA kernels take them in.
 
-Readings of passages the paper leaves open are listed in the design doc and are
-restated next to the code that implements them.  Parity unpinned: the
+Readings of passages the paper leaves open are restated next to the code
+that implements them.  Parity unpinned: the
 paper-faithfulness of those readings (thresholds, node radius, association
 method, parameterisation); they are decisions, not facts the paper fixes.
 """

@@ -12,7 +12,7 @@ The problem is solved by Gauss-Newton (Sec. 7-8): at each iteration form JᵀJ
 and Jᵀe explicitly and solve JᵀJ Δ = −Jᵀe; here the linear solve is block-
 Jacobi preconditioned conjugate gradients with a fixed iteration count.
 
-Readings of what the paper leaves open (all stated in the design doc):
+Readings of what the paper leaves open:
 
 * association (the paper defers to another work): each selected surfel is
   warped, projected with the pinhole model to the pixel

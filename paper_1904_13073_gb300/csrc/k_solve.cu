@@ -378,14 +378,63 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, int
   return s_ok != 0;
 }
 
-// a / b for positive FP64 dot products, rounded to FP32: the exponents are
-// split off exactly (frexp) and only the mantissa ratio is divided, in FP32
-// (an FP64 division is ~550 cycles on this part; the ratio is used in FP32).
-__device__ __forceinline__ float ratio_f32(double a, double b) {
-  int ea, eb;
-  const double ma = frexp(a, &ea), mb = frexp(b, &eb);
-  return ldexpf(__fdiv_rn((float)ma, (float)mb), ea - eb);
+// Double-float accumulation of the PCG's dot products: a value is the
+// unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, which
+// carries about 48 significant bits.  Products come from the error-free
+// TwoProduct (one FMA recovers the rounding error of a*b, Dekker 1971);
+// sums use Knuth's TwoSum on the high and the low parts followed by two
+// renormalisations (the "accurate" pair addition analysed by Joldes, Muller
+// and Popescu, ACM TOMS 2017: relative error below 3 * 2^-48).  Only FP32
+// operations are involved: an FP64 instruction occupies this part's FP64
+// pipe for tens of cycles, and the reductions sit on the PCG's critical path.
+// The _rn intrinsics are never contracted or reassociated by the compiler.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
 }
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b| or a == 0
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e, t, f;
+  two_sum(a.hi, b.hi, s, e);
+  two_sum(a.lo, b.lo, t, f);
+  e = __fadd_rn(e, t);
+  fast_two_sum(s, e, s, e);
+  e = __fadd_rn(e, f);
+  fast_two_sum(s, e, s, e);
+  return DF{s, e};
+}
+
+// TwoSum's error term is exact, so df_add(a, b) == df_add(b, a) bit for bit
+// and every lane of the butterfly ends with the same pair.
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// a / b of two positive pair totals, rounded to FP32 (the PCG uses its step
+// lengths in FP32; dividing the high parts costs at most one more ulp).
+__device__ __forceinline__ float df_ratio(DF a, DF b) { return __fdiv_rn(a.hi, b.hi); }
 
 // Packed lower-triangular index (r >= c).
 __device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
@@ -466,22 +515,22 @@ __device__ __forceinline__ void load_p(const float* __restrict__ z, const float*
 // fixed order, so the total is deterministic for a given number of CTAs.
 // The CTA's global-memory writes before the call are visible to every CTA
 // that returns from the same reduction.  Returns false if the wait ran out.
-__device__ __forceinline__ bool stream_reduce(double v, PartSlot* part, int t, int gs, unsigned long long gen,
-                                              int spin_limit, double* total) {
-  __shared__ double s_w[32];
-  __shared__ double s_tot;
+__device__ __forceinline__ bool stream_reduce(DF v, PartSlot* part, int t, int gs, unsigned long long gen,
+                                              int spin_limit, DF* total) {
+  __shared__ DF s_w[32];
+  __shared__ DF s_tot;
   __shared__ int s_ok;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
+  v = warp_sum_df(v);
   if (lane == 0) s_w[wid] = v;
   __syncthreads();
   PartSlot* buf = part + (gen & 1ull) * kMaxCtaPerStream;
   if (wid == 0) {
-    double b = lane < nw ? s_w[lane] : 0.0;
-    b = warp_sum(b);
+    DF b = lane < nw ? s_w[lane] : DF{0.f, 0.f};
+    b = warp_sum_df(b);
     if (lane == 0) {
       __threadfence();                       // the CTA's data writes, then the value, then the stamp
-      buf[t].val = b;
+      *reinterpret_cast<float2*>(&buf[t].hi) = make_float2(b.hi, b.lo);
       __threadfence();
       *reinterpret_cast<volatile unsigned long long*>(&buf[t].gen) = gen;
     }
@@ -495,9 +544,12 @@ __device__ __forceinline__ bool stream_reduce(double v, PartSlot* part, int t, i
     }
     ok = __all_sync(0xffffffffu, ok);
     __threadfence();
-    double acc = 0.0;
-    for (int k = lane; k < gs; k += 32) acc += __ldcg(&buf[k].val);
-    acc = warp_sum(acc);
+    DF acc{0.f, 0.f};
+    for (int k = lane; k < gs; k += 32) {
+      const float2 pv = __ldcg(reinterpret_cast<const float2*>(&buf[k].hi));
+      acc = df_add(acc, DF{pv.x, pv.y});
+    }
+    acc = warp_sum_df(acc);
     if (lane == 0) { s_tot = acc; s_ok = ok; }
   }
   __syncthreads();
@@ -521,7 +573,8 @@ __device__ __forceinline__ bool stream_reduce(double v, PartSlot* part, int t, i
 //           block times the neighbour's p = z + β p_old (formed on the fly
 //           from global memory), a warp sum of the six outputs;
 //   update  x += α p, r −= α q, z = M⁻¹ r per own node, in shared memory.
-// All dot products are accumulated in FP64; the 6x6 factorisations are FP64.
+// Dot products are accumulated in double-float pairs (about 48 bits, see DF);
+// the 6x6 factorisations are FP64.
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgWarps = kPcgThreads / 32;
 constexpr int kPcgRowFloats = 21 + 5 * 6;   // Li, then x, r, z, q, p
@@ -546,7 +599,7 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap) {
   float* sp = sq + 6 * rows_cap;
 
   // ---- set-up: preconditioner, r = −g, z = M⁻¹ r, x = 0
-  double acc = 0.0;
+  DF acc{0.f, 0.f};
   for (int a = tid; a < nr; a += kPcgThreads) {
     const int j = t + Gs * a;
     float* li = sli + 21 * a;
@@ -563,19 +616,19 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap) {
     for (int c = 0; c < 6; ++c) {
       sz[6 * a + c] = z[c];
       d.z[6 * j + c] = z[c];
-      acc += (double)r[c] * (double)z[c];
+      acc = df_add(acc, df_prod(r[c], z[c]));
     }
   }
-  double rz, rz_prev = 1.0;
+  DF rz, rz_prev{1.f, 0.f};
   if (!stream_reduce(acc, d.part, t, Gs, base + 1, spin_limit, &rz)) { atomicOr(d.status, kStatusTimeout); return; }
   bool bad = (__ldcg(d.status) & kStatusBreakdown) != 0;
 
   for (int k = 0; k < K; ++k) {
-    const bool work = !bad && rz != 0.0;
-    const float beta = (k == 0 || !work) ? 0.f : ratio_f32(rz, rz_prev);
+    const bool work = !bad && rz.hi != 0.f;
+    const float beta = (k == 0 || !work) ? 0.f : df_ratio(rz, rz_prev);
     const float* __restrict__ pold = (k & 1) ? d.p0 : d.p1;
     float* __restrict__ pnew = (k & 1) ? d.p1 : d.p0;
-    acc = 0.0;
+    acc = DF{0.f, 0.f};
     if (work) {
       for (int a = warp; a < nr; a += kPcgWarps) {
         const int i = t + Gs * a;
@@ -612,22 +665,22 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap) {
           sp[6 * a + lane] = pi;
           sq[6 * a + lane] = vc;
           pnew[6 * i + lane] = pi;
-          acc += (double)pi * (double)vc;
+          acc = df_add(acc, df_prod(pi, vc));
         }
       }
     }
-    double pq;
+    DF pq;
     if (!stream_reduce(acc, d.part, t, Gs, base + 2 + 2 * k, spin_limit, &pq)) {
       atomicOr(d.status, kStatusTimeout);
       return;
     }
-    acc = 0.0;
+    acc = DF{0.f, 0.f};
     if (work) {
-      if (!(pq > 0.0)) {
+      if (!(pq.hi > 0.f)) {
         bad = true;
         if (t == 0 && tid == 0) atomicOr(d.status, kStatusBreakdown);
       } else {
-        const float alpha = ratio_f32(rz, pq);
+        const float alpha = df_ratio(rz, pq);
         for (int a = tid; a < nr; a += kPcgThreads) {
           float r[6], z[6];
 #pragma unroll
@@ -642,19 +695,19 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap) {
           for (int c = 0; c < 6; ++c) {
             sz[6 * a + c] = z[c];
             d.z[6 * j + c] = z[c];
-            acc += (double)r[c] * (double)z[c];
+            acc = df_add(acc, df_prod(r[c], z[c]));
           }
         }
       }
     }
-    double rz_new;
+    DF rz_new;
     if (!stream_reduce(acc, d.part, t, Gs, base + 3 + 2 * k, spin_limit, &rz_new)) {
       atomicOr(d.status, kStatusTimeout);
       return;
     }
     if (work && !bad) { rz_prev = rz; rz = rz_new; }
   }
-  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = rz;
+  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = (double)rz.hi + (double)rz.lo;
   // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
   if (bad || (__ldcg(d.status) & kStatusBreakdown)) return;
   for (int a = tid; a < nr; a += kPcgThreads) {

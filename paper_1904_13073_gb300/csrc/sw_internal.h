@@ -23,11 +23,11 @@ constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive def
 constexpr int kStatusBadIndex = 2;       // a gather index failed its range check
 constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
 
-// A CTA's partial of one reduction, published with a generation stamp
-// (release store of `gen` after `val`); slots are double-buffered by the
-// parity of the reduction's index.
+// A CTA's partial of one reduction (a double-float pair hi + lo), published
+// with a generation stamp (release store of `gen` after the pair); slots are
+// double-buffered by the parity of the reduction's index.
 struct PartSlot {
-  double val;
+  float hi, lo;
   unsigned long long gen;
 };
 
