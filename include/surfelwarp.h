@@ -37,6 +37,22 @@ extern "C" {
 #define SW_K_SKIN 4            /* nearest nodes per surfel (Eq. 1) */
 #define SW_K_GRAPH 8           /* graph neighbours per node (Eq. 11) */
 
+/* Arithmetic of the solve (sw_params.precision).  Depth processing, the
+ * association decisions, fusion and the stored surfels are FP32 in every mode.
+ *   SW_PRECISION_MIXED         residuals, Jacobians, JᵀJ, SpMV and vectors in
+ *                              FP32; PCG inner products accumulated in
+ *                              double-float pairs (about 48 significant bits);
+ *                              6x6 block inverses by FP64 Cholesky.
+ *   SW_PRECISION_FP64          the whole solve in FP64: node transforms, warp,
+ *                              residuals, Jacobians, JᵀJ, PCG (the association
+ *                              still decided in FP32 from the FP64 warp).
+ *   SW_PRECISION_MIXED_F64DOTS as MIXED, with the inner products accumulated
+ *                              in FP64.
+ * Every member of one batch must use the same mode. */
+#define SW_PRECISION_MIXED 0
+#define SW_PRECISION_FP64 1
+#define SW_PRECISION_MIXED_F64DOTS 2
+
 typedef struct sw_stream* sw_handle;
 
 typedef enum {
@@ -63,7 +79,7 @@ typedef struct {
   float corr_normal;            /* association normal dot (0.7) */
   float stable_conf;            /* δ_stable (Table 1: 10) */
   int recent_frames;            /* δ_recent (Table 1: 2) */
-  int precision;                /* 0: FP32 residuals/Jacobians/JᵀJ, FP64 PCG dots and 6x6 inversions */
+  int precision;                /* SW_PRECISION_* (default SW_PRECISION_MIXED) */
 } sw_params;
 
 /* Per-call statistics of sw_solve_frame; entry i describes Gauss-Newton

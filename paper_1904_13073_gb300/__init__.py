@@ -16,6 +16,9 @@ LIB_PATH = os.path.join(HERE, "libsurfelwarp.so")
 
 SW_MAX_GN_ITERS = 16
 SW_MAX_PCG_ITERS = 128
+SW_PRECISION_MIXED = 0           # FP32 solve, double-float PCG inner products, FP64 6x6 inverses
+SW_PRECISION_FP64 = 1            # the whole solve in FP64
+SW_PRECISION_MIXED_F64DOTS = 2   # FP32 solve, FP64 PCG inner products, FP64 6x6 inverses
 
 STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_NO_MEMORY", 3: "SW_ERR_NOT_INITIALIZED",
           4: "SW_ERR_SOLVER_BREAKDOWN", 5: "SW_ERR_TIMEOUT", 6: "SW_ERR_CUDA"}

@@ -95,6 +95,7 @@ struct sw_stream {
   int4* knn_dist = nullptr;  // skinning in distance order, caller's order (inspection, checkpoint)
   float4* w_dist = nullptr;
   Runner* run = nullptr;     // the stream's own one-stream runner
+  std::vector<int> rl_ptr_host;   // per block row, the start of its SpMV entries (PCG work sizing)
   // ordering against batches this stream belongs to
   cudaEvent_t batch_done = nullptr;   // recorded by the last batch call (owned by the batch)
   cudaEvent_t own_ev = nullptr;       // recorded before a batch call when own work is pending
@@ -225,7 +226,11 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
   // CTAs, about one warp per block row and at most kPcgMaxCtas, scaled down
   // in proportion when the batch asks for more CTAs than the GPU holds
   {
-    const int per_sm = std::max(1, pcg_blocks_per_sm());
+    const int prec = n ? devs[0].precision : SW_PRECISION_MIXED;
+    for (int i = 1; i < n; ++i)
+      if (devs[i].precision != prec) return fail(err_to, SW_ERR_INVALID_ARG, "batch members differ in precision");
+    r->bh.precision = prec;
+    const int per_sm = std::max(1, pcg_blocks_per_sm(prec));
     const int cap = sm_count() * per_sm;
     if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
     const int warps = pcg_threads() / 32;
@@ -249,12 +254,30 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     }
     tiles[(size_t)kTilePcg * (n + 1) + n] = acc;
     r->bh.total_tiles[kTilePcg] = acc;
+    // the most SpMV entries one CTA owns (its rows are i = t + G a)
+    int ent_cap = 1;
+    for (int i = 0; i < n; ++i) {
+      const std::vector<int>& rp = r->members[i]->rl_ptr_host;
+      const int G = want[i], nn = devs[i].n_n;
+      if (nn == 0) continue;   // a stream without a model yet
+      if ((int)rp.size() != nn + 1) return fail(err_to, SW_ERR_INVALID_ARG, "batch member without a JᵀJ pattern");
+      for (int t = 0; t < G; ++t) {
+        int e = 0;
+        for (int j = t; j < nn; j += G) e += rp[j + 1] - rp[j];
+        ent_cap = std::max(ent_cap, e);
+      }
+    }
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (pcg_smem_bytes(rows_cap) > (size_t)optin)
-      return fail(err_to, SW_ERR_INVALID_ARG, "a stream has too many nodes for the PCG's on-chip state");
+    // the SpMV stages as much in shared memory as fits: the rows' blocks and
+    // the entries' outputs (2), the outputs only (1), or nothing (0)
+    int mode = 2;
+    while (mode >= 0 && pcg_smem_bytes(rows_cap, ent_cap, prec, mode) > (size_t)optin) --mode;
+    if (mode < 0) return fail(err_to, SW_ERR_INVALID_ARG, "a stream has too many nodes for the PCG's on-chip state");
     r->bh.pcg_rows_cap = rows_cap;
+    r->bh.pcg_ent_cap = ent_cap;
+    r->bh.pcg_mode = mode;
   }
   SwDev* devs_dev = nullptr;
   int* tile_dev = nullptr;
@@ -418,7 +441,10 @@ bool params_ok(const sw_params* p, std::string& why) {
   if (p->max_surfels < 0 || p->max_surfels > (1 << 28)) { why = "max_surfels out of range"; return false; }
   if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
   if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
-  if (p->precision != 0) { why = "only precision 0 (FP32 assembly, FP64 PCG reductions) is built"; return false; }
+  if (p->precision != SW_PRECISION_MIXED && p->precision != SW_PRECISION_MIXED_F64DOTS) {
+    why = "precision must be SW_PRECISION_MIXED or SW_PRECISION_MIXED_F64DOTS";
+    return false;
+  }
   return true;
 }
 
@@ -521,7 +547,7 @@ sw_status sw_params_default(sw_params* p, int width, int height, float fx, float
   p->corr_normal = 0.7f;
   p->stable_conf = 10.f;    // Table 1
   p->recent_frames = 2;     // Table 1
-  p->precision = 0;
+  p->precision = SW_PRECISION_MIXED;
   return SW_OK;
 }
 
@@ -561,6 +587,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   h.W = p->width; h.H = p->height;
   h.fx = p->fx; h.fy = p->fy; h.cx = p->cx; h.cy = p->cy;
   h.sqrt_lambda = std::sqrt(p->lambda);
+  h.precision = p->precision;
   h.corr_dist = p->corr_dist; h.corr_normal = p->corr_normal;
   h.fuse_dist = p->fuse_dist; h.fuse_normal = p->fuse_normal;
   h.stable_conf = p->stable_conf; h.recent_frames = p->recent_frames;
@@ -575,7 +602,8 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
   ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Li, 21 * nn);
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
-  ALLOC(h.q, 6 * nn); ALLOC(h.part, 2 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
+  ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
+  ALLOC(h.xz, 6 * nn); ALLOC(h.xp, 12 * nn);
   ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
   ALLOC(h.status, 1); ALLOC(h.t_now, 1);
 #undef ALLOC
@@ -583,7 +611,9 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   // the index map is cleared here once; fusion leaves it empty after every frame
   if (cudaMemsetAsync(h.status, 0, sizeof(int), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.t_now, 0, sizeof(int), s->st) != cudaSuccess ||
-      cudaMemsetAsync(h.part, 0, 2 * kMaxCtaPerStream * sizeof(PartSlot), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.part, 0, 4 * kMaxCtaPerStream * sizeof(PartSlot), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.xz, 0, 6 * nn * sizeof(unsigned long long), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.xp, 0, 12 * nn * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.pcg_epoch, 0, sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.vmap, 0, np * sizeof(float4), s->st) != cudaSuccess) {
@@ -790,6 +820,7 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   Pattern P;
   std::string why;
   if (!build_pattern(n_n, sets, graph, P, why)) return fail(s, SW_ERR_INVALID_ARG, why);
+  s->rl_ptr_host = P.rl_ptr;
   h.n_sets = (int)sets.size();
   h.nnzb = (int)P.col.size();
   SW_CUDA(s, cudaMemcpyAsync(h.row_ptr, P.row_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));

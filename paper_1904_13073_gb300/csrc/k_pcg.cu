@@ -1,0 +1,1303 @@
+// K7+K8: block-Jacobi preconditioned conjugate gradients on JᵀJ Δ = −Jᵀe
+// and the node update T_j ← Δ_j T_j (Sec. 7), one persistent cooperative
+// launch per Gauss-Newton iteration for every stream of a batch.
+//
+// Recurrences: standard PCG, x₀ = 0, exactly K iterations, stopping early
+// only when rᵀz is exactly zero; pᵀAp <= 0 is a breakdown.
+//   z = M⁻¹ r, p = z + β p, q = A p, α = rᵀz / pᵀq, x += α p, r −= α q.
+// (Pipelined variants that fuse the two reductions of an iteration into one
+// lose orders of magnitude of accuracy in FP32 on ill-conditioned systems of
+// this solve, so the two reductions stay.)
+//
+// Work split.  Stream s owns the CTAs [tile_base[s], tile_base[s+1]), all
+// co-resident.  CTA t of a stream with G CTAs owns the block rows and nodes
+// i = t + G a (a = 0, 1, ...) and keeps everything about them in shared
+// memory for the whole solve: the 6x6 block of M⁻¹ and x, r, z, p, q.
+// Global memory carries only what other CTAs read: z, and p double-buffered
+// by iteration parity.  A warp takes one own row at a time: a lane per 6x6
+// block of the row for (A p)_i, with the neighbour's p = z + β p_old formed
+// on the fly, a warp sum of the six outputs; lanes 0-5 then hold the row's
+// six components for the vector updates.  The two reductions of an
+// iteration (pᵀq, rᵀz) are also its only synchronisation, and they are per
+// stream, so streams never wait for one another.
+//
+// Precision (template parameters).  Real is the type of the matrix, the
+// vectors and the step lengths; Acc the type the inner products are
+// accumulated in: float + DF (double-float pairs, the default), float +
+// double, or double + double (the all-FP64 variant).  M⁻¹ is formed in FP64
+// by Cholesky in every case.
+#include <type_traits>
+
+#include "sw_internal.h"
+#include "sw_math.cuh"
+#include "sw_math64.cuh"
+
+namespace sw {
+namespace {
+
+// ------------------------------------------------------------------ accumulators
+
+// Double-float accumulation: a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits.  Products
+// come from the error-free TwoProduct (one FMA recovers the rounding error of
+// a*b, Dekker 1971); sums use Knuth's TwoSum on the high and the low parts
+// followed by two renormalisations (the "accurate" pair addition analysed by
+// Joldes, Muller and Popescu, ACM TOMS 2017: relative error below 3 * 2^-48).
+// Only FP32 operations are involved: an FP64 instruction occupies this part's
+// FP64 pipe for tens of cycles, and the reductions sit on the critical path.
+// The _rn intrinsics are never contracted or reassociated by the compiler.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b| or a == 0
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e, t, f;
+  two_sum(a.hi, b.hi, s, e);
+  two_sum(a.lo, b.lo, t, f);
+  e = __fadd_rn(e, t);
+  fast_two_sum(s, e, s, e);
+  e = __fadd_rn(e, f);
+  fast_two_sum(s, e, s, e);
+  return DF{s, e};
+}
+
+// Operations the PCG needs from an accumulator type.  TwoSum's error term is
+// exact, so df_add(a, b) == df_add(b, a) bit for bit and every lane of a
+// butterfly ends with the same value; the same holds for FP64 addition.
+template <typename Acc>
+struct AccOps;
+
+template <>
+struct AccOps<DF> {
+  static __device__ __forceinline__ DF zero() { return DF{0.f, 0.f}; }
+  static __device__ __forceinline__ DF prod(float a, float b) { return df_prod(a, b); }
+  static __device__ __forceinline__ DF add(DF a, DF b) { return df_add(a, b); }
+  static __device__ __forceinline__ DF shfl_xor(DF v, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+  }
+  static __device__ __forceinline__ unsigned long long bits(DF v) {
+    return (unsigned long long)__float_as_uint(v.hi) | ((unsigned long long)__float_as_uint(v.lo) << 32);
+  }
+  static __device__ __forceinline__ DF from_bits(unsigned long long b) {
+    return DF{__uint_as_float((unsigned)(b & 0xffffffffu)), __uint_as_float((unsigned)(b >> 32))};
+  }
+  static __device__ __forceinline__ bool nonzero(DF v) { return v.hi != 0.f; }
+  static __device__ __forceinline__ double value(DF v) { return (double)v.hi + (double)v.lo; }
+};
+
+template <>
+struct AccOps<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double prod(float a, float b) { return (double)a * (double)b; }   // exact
+  static __device__ __forceinline__ double prod(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  static __device__ __forceinline__ unsigned long long bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+  static __device__ __forceinline__ double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
+  static __device__ __forceinline__ bool nonzero(double v) { return v != 0.0; }
+  static __device__ __forceinline__ double value(double v) { return v; }
+};
+
+template <typename Acc>
+__device__ __forceinline__ Acc warp_sum_acc(Acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = AccOps<Acc>::add(v, AccOps<Acc>::shfl_xor(v, o));
+  return v;
+}
+
+// a / b for positive FP64 values, rounded to FP32: the exponents are split
+// off exactly (frexp) and only the mantissa ratio is divided, in FP32 (an
+// FP64 division is several hundred cycles on this part).
+__device__ __forceinline__ float ratio_f32(double a, double b) {
+  int ea, eb;
+  const double ma = frexp(a, &ea), mb = frexp(b, &eb);
+  return ldexpf(__fdiv_rn((float)ma, (float)mb), ea - eb);
+}
+
+// ------------------------------------------------------------------ 6x6 blocks
+
+__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }   // packed, r >= c
+__device__ __forceinline__ int sym(int r, int c) { return r >= c ? tri(r, c) : tri(c, r); }
+
+// M⁻¹ of one diagonal block (symmetric, packed lower) by Cholesky A = L Lᵀ in
+// FP64: M⁻¹ = L⁻ᵀ L⁻¹.  The block's two triangles are averaged first.  False
+// if the block is not positive definite.
+template <typename Real>
+__device__ bool block_inverse(const Real* a, Real* out) {
+  double L[21], Li[21];
+  for (int c = 0; c < 6; ++c) {
+    double s = (double)a[c * 6 + c];
+    for (int k = 0; k < c; ++k) s -= L[tri(c, k)] * L[tri(c, k)];
+    if (!(s > 0.0)) return false;
+    const double lcc = sqrt(s), inv = 1.0 / lcc;
+    L[tri(c, c)] = lcc;
+    Li[tri(c, c)] = inv;
+    for (int r = c + 1; r < 6; ++r) {
+      double t = 0.5 * ((double)a[r * 6 + c] + (double)a[c * 6 + r]);
+      for (int k = 0; k < c; ++k) t -= L[tri(r, k)] * L[tri(c, k)];
+      L[tri(r, c)] = t * inv;
+    }
+  }
+  for (int c = 0; c < 6; ++c) {   // Li = L⁻¹ by forward substitution, column by column
+    for (int r = c + 1; r < 6; ++r) {
+      double t = 0.0;
+      for (int k = c; k < r; ++k) t += L[tri(r, k)] * Li[tri(k, c)];
+      Li[tri(r, c)] = -t * Li[tri(r, r)];
+    }
+  }
+  for (int r = 0; r < 6; ++r) {   // (L⁻ᵀ L⁻¹)_rc = Σ_{k >= r} Li_kr Li_kc, r >= c
+    for (int c = 0; c <= r; ++c) {
+      double t = 0.0;
+      for (int k = r; k < 6; ++k) t += Li[tri(k, r)] * Li[tri(k, c)];
+      out[tri(r, c)] = (Real)t;
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ exchange
+
+// What other CTAs read during the solve, z and p (p double-buffered by
+// iteration parity), and the reductions' slots.
+//
+// FP32 (the default): every value travels as one 8-byte word {FP32 bits,
+// 32-bit generation tag}, written and read with single 8-byte accesses, so a
+// reader that sees the expected tag also sees the value written with it, and
+// no fence is needed anywhere (the writer never waits for its stores to
+// reach L2).  A reader that finds an older tag reads again (bounded).  The
+// owner of a row forms its p = z + β p_old as soon as β is known and
+// publishes p alone; readers wait for its tag.
+// FP64: plain values, published with a release pattern (value, acq_rel fence,
+// stamp) and read after acquire loads of the stamps; z and p_old are
+// published before the reduction that precedes their use, and readers form
+// p = z + β p_old themselves.
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void st_relaxed_gpu(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a, unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ ulonglong2 ld_relaxed_v2(const unsigned long long* p) {
+  ulonglong2 v;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long tagged(unsigned bits, unsigned tag) {
+  return (unsigned long long)bits | ((unsigned long long)tag << 32);
+}
+__device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
+
+template <typename Real>
+struct Xchg;
+
+template <>
+struct Xchg<float> {
+  unsigned long long* z;    // unused: the owner of a row publishes its p
+  unsigned long long* p0;   // p, even iterations (6 n_n tagged words)
+  unsigned long long* p1;   // p, odd iterations
+  __device__ __forceinline__ static void put(unsigned long long* buf, size_t i, float v, unsigned tag) {
+    st_relaxed_u64(buf + i, tagged(__float_as_uint(v), tag));
+  }
+  // the 6 values of node j carrying the given tag; false if they did not
+  // arrive within `spins` further reads
+  __device__ __forceinline__ static bool get6(const unsigned long long* buf, int j, unsigned tag, float* v, int spins) {
+    const unsigned long long* src = buf + 6 * (size_t)j;
+    for (int n = 0;; ++n) {
+      ulonglong2 a[3];
+#pragma unroll
+      for (int h = 0; h < 3; ++h) a[h] = ld_relaxed_v2(src + 2 * h);
+      unsigned bad = 0;
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        bad |= (tag_of(a[h].x) ^ tag) | (tag_of(a[h].y) ^ tag);
+        v[2 * h] = __uint_as_float((unsigned)a[h].x);
+        v[2 * h + 1] = __uint_as_float((unsigned)a[h].y);
+      }
+      if (bad == 0) return true;
+      if (n >= spins) return false;
+    }
+  }
+};
+
+template <>
+struct Xchg<double> {
+  double* z;
+  double* p0;
+  double* p1;
+  __device__ __forceinline__ static void put(double* buf, size_t i, double v, unsigned) { buf[i] = v; }
+  __device__ __forceinline__ static bool get_p(const double* z, unsigned, const double* po, unsigned, bool with_old,
+                                               double beta, int j, double* p, int) {
+    const double2* z2 = reinterpret_cast<const double2*>(z + 6 * (size_t)j);
+    const double2* o2 = reinterpret_cast<const double2*>(po + 6 * (size_t)j);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const double2 a = __ldcg(z2 + h);
+      p[2 * h] = a.x; p[2 * h + 1] = a.y;
+    }
+    if (with_old) {
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        const double2 o = __ldcg(o2 + h);
+        p[2 * h] += beta * o.x; p[2 * h + 1] += beta * o.y;
+      }
+    }
+    return true;
+  }
+};
+
+template <typename Real>
+struct PcgData {
+  const Real* A;   // nnzb x 36
+  const Real* g;   // 6 n_n
+  Xchg<Real> X;
+};
+
+__device__ __forceinline__ PcgData<float> pcg_data(const SwDev& d, float) {
+  const size_t n6 = 6 * (size_t)d.n_n;
+  return {d.A, d.g, {d.xz, d.xp, d.xp + n6}};
+}
+__device__ __forceinline__ PcgData<double> pcg_data(const SwDev& d, double) {
+  const size_t n6 = 6 * (size_t)d.n_n;
+  return {d.A64, d.g64, {d.v64, d.v64 + n6, d.v64 + 2 * n6}};
+}
+
+// one row of a 6x6 block of the matrix (read-only for the whole launch)
+__device__ __forceinline__ void load6_ro(const float* p, float* v) {
+  const float2* p2 = reinterpret_cast<const float2*>(p);
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const float2 a = __ldg(p2 + h);
+    v[2 * h] = a.x; v[2 * h + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void load6_ro(const double* p, double* v) {
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const double2 a = __ldg(p2 + h);
+    v[2 * h] = a.x; v[2 * h + 1] = a.y;
+  }
+}
+
+template <typename Real>
+__device__ __forceinline__ Real warp_sum_r(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ reduction
+
+// One reduction among the CTAs of one stream, which is also their only
+// synchronisation.  Precondition: within each warp only lanes below `lanes`
+// (a power of two) hold nonzero values.  Every CTA publishes its block sum
+// in its slot for generation `gen` (slots double-buffered by its parity);
+// one warp polls the stream's slots (bounded) and sums them in a fixed
+// order, so the total is deterministic for a given number of CTAs.
+// `on_total(total)` runs on one thread before the CTA continues (the
+// step-length arithmetic, done once).  Returns false if the wait ran out.
+// kTagged: the slot is two tagged words holding the value's two 32-bit
+// halves; otherwise the release / acquire pattern on a stamp.
+template <bool kTagged, typename Acc, typename F>
+__device__ __forceinline__ bool stream_reduce(Acc v, int lanes, PartSlot* part, int t, int gs,
+                                              unsigned long long gen, int spin_limit, F&& on_total) {
+  using O = AccOps<Acc>;
+  __shared__ Acc s_w[32];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = lanes >> 1; o > 0; o >>= 1) v = O::add(v, O::shfl_xor(v, o));
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  PartSlot* buf = part + (gen & 1ull) * kMaxCtaPerStream;
+  const unsigned tag = (unsigned)gen;
+  if (wid == 0) {
+    Acc b = lane < nw ? s_w[lane] : O::zero();
+    b = warp_sum_acc(b);
+    int ok = 1;
+    Acc c = O::zero();
+    if constexpr (kTagged) {
+      if (lane == 0) {
+        const unsigned long long bits = O::bits(b);
+        st_relaxed_v2(&buf[t].v, tagged((unsigned)bits, tag), tagged((unsigned)(bits >> 32), tag));
+      }
+      for (int k = lane; k < gs; k += 64) {   // a lane waits for two slots at once
+        const bool two = k + 32 < gs;
+        ulonglong2 w0, w1 = make_ulonglong2(tagged(0u, tag), tagged(0u, tag));
+        int spins = 0;
+        for (;;) {
+          w0 = ld_relaxed_v2(&buf[k].v);
+          if (two) w1 = ld_relaxed_v2(&buf[k + 32].v);
+          if (((tag_of(w0.x) ^ tag) | (tag_of(w0.y) ^ tag) | (tag_of(w1.x) ^ tag) | (tag_of(w1.y) ^ tag)) == 0) break;
+          if (++spins > spin_limit) { ok = 0; break; }
+        }
+        if (!ok) break;
+        c = O::add(c, O::from_bits((w0.x & 0xffffffffull) | (w0.y << 32)));
+        if (two) c = O::add(c, O::from_bits((w1.x & 0xffffffffull) | (w1.y << 32)));
+      }
+      ok = __all_sync(0xffffffffu, ok);
+    } else {
+      if (lane == 0) {
+        buf[t].v = O::bits(b);
+        fence_acq_rel_gpu();
+        st_relaxed_gpu(&buf[t].gen, gen);
+      }
+      for (int k = lane; k < gs; k += 32) {
+        int spins = 0;
+        while (ld_acquire_gpu(&buf[k].gen) < gen) {
+          if (++spins > spin_limit) { ok = 0; break; }
+        }
+        if (!ok) break;
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      for (int k = lane; k < gs; k += 32) c = O::add(c, O::from_bits(__ldcg(&buf[k].v)));
+    }
+    c = warp_sum_acc(c);
+    if (lane == 0) {
+      s_ok = ok;
+      on_total(c);
+    }
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Two values in one tagged reduction: CTA t publishes both in the slots
+// 2t and 2t+1 of the generation's half of `part` (2 kMaxCtaPerStream slots
+// per parity), and the pollers check all four tags of a CTA at once.
+template <typename Acc, typename F>
+__device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, PartSlot* part, int t, int gs,
+                                                   unsigned long long gen, int spin_limit, F&& on_total) {
+  using O = AccOps<Acc>;
+  __shared__ Acc s_w[2][32];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = lanes >> 1; o > 0; o >>= 1) {
+    va = O::add(va, O::shfl_xor(va, o));
+    vb = O::add(vb, O::shfl_xor(vb, o));
+  }
+  if (lane == 0) { s_w[0][wid] = va; s_w[1][wid] = vb; }
+  __syncthreads();
+  PartSlot* buf = part + (gen & 1ull) * 2 * kMaxCtaPerStream;
+  const unsigned tag = (unsigned)gen;
+  if (wid == 0) {
+    Acc a = lane < nw ? s_w[0][lane] : O::zero();
+    Acc b = lane < nw ? s_w[1][lane] : O::zero();
+    a = warp_sum_acc(a);
+    b = warp_sum_acc(b);
+    if (lane == 0) {
+      const unsigned long long ba = O::bits(a), bb = O::bits(b);
+      st_relaxed_v2(&buf[2 * t].v, tagged((unsigned)ba, tag), tagged((unsigned)(ba >> 32), tag));
+      st_relaxed_v2(&buf[2 * t + 1].v, tagged((unsigned)bb, tag), tagged((unsigned)(bb >> 32), tag));
+    }
+    int ok = 1;
+    Acc ca = O::zero(), cb = O::zero();
+    for (int k = lane; k < gs; k += 32) {
+      ulonglong2 wa, wb;
+      int spins = 0;
+      for (;;) {
+        wa = ld_relaxed_v2(&buf[2 * k].v);
+        wb = ld_relaxed_v2(&buf[2 * k + 1].v);
+        if (((tag_of(wa.x) ^ tag) | (tag_of(wa.y) ^ tag) | (tag_of(wb.x) ^ tag) | (tag_of(wb.y) ^ tag)) == 0) break;
+        if (++spins > spin_limit) { ok = 0; break; }
+      }
+      if (!ok) break;
+      ca = O::add(ca, O::from_bits((wa.x & 0xffffffffull) | (wa.y << 32)));
+      cb = O::add(cb, O::from_bits((wb.x & 0xffffffffull) | (wb.y << 32)));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    ca = warp_sum_acc(ca);
+    cb = warp_sum_acc(cb);
+    if (lane == 0) {
+      s_ok = ok;
+      on_total(ca, cb);
+    }
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ the solver
+
+constexpr int kPcgThreads = 1024;
+constexpr int kPcgWarps = kPcgThreads / 32;
+enum { kX = 0, kR, kZ, kP, kQ, kRowVecs };
+constexpr int kRowReals = 21 + 6 * kRowVecs;   // M⁻¹ packed, then the five vectors
+
+template <typename Real, typename Acc>
+struct Scalars {
+  Real alpha, beta;
+  Acc rz;      // current rᵀz
+  int work;    // rᵀz != 0 and no breakdown
+  int bad;     // breakdown seen
+};
+
+// a / b of two positive accumulated values, in Real
+template <typename Real, typename Acc>
+__device__ __forceinline__ Real acc_ratio(Acc a, Acc b) {
+  if constexpr (std::is_same<Acc, DF>::value) {
+    return __fdiv_rn(a.hi, b.hi);
+  } else if constexpr (std::is_same<Real, float>::value) {
+    return ratio_f32(a, b);
+  } else {
+    return a / b;
+  }
+}
+
+template <typename Acc>
+__device__ __forceinline__ bool acc_positive(Acc a) {
+  if constexpr (std::is_same<Acc, DF>::value) return a.hi > 0.f;
+  else return a > 0.0;
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc acc_nan() {
+  if constexpr (std::is_same<Acc, DF>::value) return DF{__int_as_float(0x7fffffff), 0.f};
+  else return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+template <typename Acc>
+__device__ __forceinline__ bool acc_is_nan(Acc a) {
+  if constexpr (std::is_same<Acc, DF>::value) return a.hi != a.hi;
+  else return a != a;
+}
+
+// How the SpMV reaches the matrix (chosen per batch by what fits in shared
+// memory):
+//   kSpmvSmemA   the CTA copies its rows' blocks into shared memory at set-up;
+//   kSpmvSmemOut the blocks are read from global memory each iteration;
+// both take one thread per matrix entry of the CTA's rows (all of them in
+// flight at once) with six outputs per entry in shared memory, then a warp
+// per row sums its entries;
+//   kSpmvRows    a warp per row, a lane per entry, nothing staged.
+enum SpmvMode { kSpmvRows = 0, kSpmvSmemOut = 1, kSpmvSmemA = 2 };
+
+// Shared memory of one CTA: per own row M⁻¹ (21) and x r z p q (30); in the
+// staged modes the six outputs of every entry and, with kSpmvSmemA, the
+// entries' blocks (36 values each), both stored entry-minor (value q of entry
+// e at q * ent_cap + e, so threads on consecutive entries hit consecutive
+// banks) with every block already turned to multiply the neighbour's vector
+// directly; then the rows' entry offsets and per entry its neighbour
+// (kSpmvSmemA) or its block and neighbour (kSpmvSmemOut).
+// Byte offsets of the sections, each rounded up to 16 bytes.
+struct SmemLayout {
+  size_t mi, vec, a, out, ent, off, total;
+};
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <typename Real>
+__host__ __device__ constexpr SmemLayout pcg_layout(int rows_cap, int ent_cap, int mode, int row_vecs) {
+  SmemLayout L{};
+  const size_t R = sizeof(Real), rc = (size_t)rows_cap, ec = (size_t)ent_cap;
+  L.mi = 0;
+  L.vec = align16(L.mi + R * 21 * rc);
+  L.a = align16(L.vec + R * 6 * (size_t)row_vecs * rc);
+  L.out = align16(L.a + (mode == kSpmvSmemA ? R * 36 * ec : 0));
+  L.ent = align16(L.out + (mode != kSpmvRows ? R * 6 * ec : 0));
+  L.off = align16(L.ent + (mode == kSpmvSmemA ? sizeof(int) * ec : mode == kSpmvSmemOut ? sizeof(int2) * ec : 0));
+  L.total = align16(L.off + sizeof(int) * (rc + 1));
+  return L;
+}
+
+// p of neighbour j for this iteration's SpMV: the published p (tagged
+// exchange) or z + β p_old formed here (FP64 exchange)
+__device__ __forceinline__ bool fetch_p(const Xchg<float>&, const unsigned long long* pcur, const unsigned long long*,
+                                        unsigned tag, bool, float, int j, float* p, int spins) {
+  return Xchg<float>::get6(pcur, j, tag, p, spins);
+}
+__device__ __forceinline__ bool fetch_p(const Xchg<double>& X, const double*, const double* pold, unsigned, bool with_old,
+                                        double beta, int j, double* p, int) {
+  return Xchg<double>::get_p(X.z, 0u, pold, 0u, with_old, beta, j, p, 0);
+}
+
+template <typename Real, typename Acc, int kMode>
+__global__ void __launch_bounds__(kPcgThreads, 1)
+k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+  using O = AccOps<Acc>;
+  constexpr bool kTagged = std::is_same<Real, float>::value;
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int t = blockIdx.x - __ldg(bt.tile_base + s);
+  const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = d.n_n;
+  const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
+  const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
+  const PcgData<Real> P = pcg_data(d, Real(0));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kStaged = kMode != kSpmvRows;
+  const SmemLayout L = pcg_layout<Real>(rows_cap, ent_cap, kMode, kRowVecs);
+  Real* sMi = reinterpret_cast<Real*>(smem_raw + L.mi);
+  Real* svec = reinterpret_cast<Real*>(smem_raw + L.vec);
+  Real* sA = reinterpret_cast<Real*>(smem_raw + L.a);
+  Real* sOut = reinterpret_cast<Real*>(smem_raw + L.out);
+  int* sj = reinterpret_cast<int*>(smem_raw + L.ent);       // kSpmvSmemA: neighbour per entry
+  int2* sent = reinterpret_cast<int2*>(smem_raw + L.ent);   // kSpmvSmemOut: (block | turned << 31, neighbour)
+  int* soff = reinterpret_cast<int*>(smem_raw + L.off);
+  auto V = [&](int v, int a) { return svec + ((size_t)v * rows_cap + a) * 6; };
+  __shared__ Scalars<Real, Acc> sc;
+  __shared__ int s_late;   // a tagged value that never arrived
+
+  // ---- set-up, a thread per own row: M⁻¹, r = −g, z = M⁻¹ r, x = p = 0
+  if (tid == 0) s_late = 0;
+  Acc pa = O::zero();
+  bool broken = false;
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
+    Real* mi = sMi + 21 * a;
+    if (!block_inverse(P.A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
+      atomicOr(d.status, kStatusBreakdown);
+      broken = true;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) mi[k] = 0;
+    }
+    Real r[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) r[c] = -P.g[6 * j + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      Real z = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) z += mi[sym(c, k)] * r[k];
+      V(kR, a)[c] = r[c];
+      V(kZ, a)[c] = z;
+      V(kX, a)[c] = 0;
+      V(kP, a)[c] = kTagged ? z : 0;
+      if constexpr (kTagged) P.X.put(P.X.p0, 6 * (size_t)j + c, z, (unsigned)(base + 1));   // p₀ = z₀
+      else P.X.put(P.X.z, 6 * (size_t)j + c, z, 0u);
+      pa = O::add(pa, O::prod(r[c], z));
+    }
+  }
+  if (broken) pa = acc_nan<Acc>();   // a diagonal block that is not positive definite reaches every CTA
+  if constexpr (kStaged) {
+    // the rows' entry offsets (warp 0, an exclusive scan of the row lengths) ...
+    if (warp == 0) {
+      int run = 0;
+      for (int a0 = 0; a0 < nr; a0 += 32) {
+        const int a = a0 + lane;
+        const int i = t + Gs * a;
+        const int len = a < nr ? __ldg(d.rl_ptr + i + 1) - __ldg(d.rl_ptr + i) : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += u;
+        }
+        if (a < nr) soff[a + 1] = run + incl;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) soff[0] = 0;
+    }
+    __syncthreads();
+    // ... then every entry: its block (turned to multiply the neighbour's
+    // vector) and neighbour, or where to find them
+    for (int a = warp; a < nr; a += kPcgWarps) {
+      const int i = t + Gs * a;
+      const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
+      for (int k = lane; k < len; k += 32) {
+        const int2 ent = __ldg(d.rl_ent + r0 + k);
+        const int e = e0 + k;
+        if constexpr (kMode == kSpmvSmemA) {
+          const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
+          const bool tr = ent.x < 0;
+          sj[e] = ent.y;
+#pragma unroll
+          for (int q = 0; q < 36; ++q) {
+            const int dst = tr ? (q % 6) * 6 + q / 6 : q;
+            sA[(size_t)dst * ent_cap + e] = __ldg(B + q);
+          }
+        } else {
+          sent[e] = ent;
+        }
+      }
+    }
+  }
+  if (!stream_reduce<kTagged>(pa, 32, d.part, t, Gs, base + 1, spin_limit, [&](Acc rz) {
+        sc.rz = rz;
+        sc.bad = acc_is_nan(rz);
+        sc.work = !sc.bad && O::nonzero(rz);
+        sc.alpha = 0;
+        sc.beta = 0;
+      })) {
+    atomicOr(d.status, kStatusTimeout);
+    return;
+  }
+
+  for (int k = 0; k < K; ++k) {
+    const bool work = sc.work;
+    const Real beta = sc.beta;
+    const auto* pold = (k & 1) ? P.X.p0 : P.X.p1;
+    auto* pnew = (k & 1) ? P.X.p1 : P.X.p0;
+    const unsigned tp = (unsigned)(base + 1 + 2 * k);      // p of this iteration (tagged exchange)
+    const auto* pcur = (k & 1) ? P.X.p1 : P.X.p0;
+    // a tagged value is written before its writer publishes the reduction
+    // that this CTA has already seen, so it arrives within the L2 latency
+    const int data_spins = spin_limit >> 6;
+    bool late = false;
+    // ---- q = A p with p = z + β p_old, and the shares of pᵀq (lanes 0-5)
+    pa = O::zero();
+    if (work) {
+      if constexpr (kStaged) {
+        // a thread per entry of the CTA's rows: its 6x6 block times the
+        // neighbour's p, six outputs to shared memory ...
+        const int ne = soff[nr];
+        for (int e = tid; e < ne; e += kPcgThreads) {
+          Real p[6];
+          if constexpr (kMode == kSpmvSmemA) {
+            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, sj[e], p, data_spins);
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+              Real u = 0;
+#pragma unroll
+              for (int q = 0; q < 6; ++q) u += sA[(size_t)(6 * b + q) * ent_cap + e] * p[q];
+              sOut[(size_t)b * ent_cap + e] = u;
+            }
+          } else {
+            const int2 ent = sent[e];
+            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, ent.y, p, data_spins);
+            const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
+            Real out[6] = {0, 0, 0, 0, 0, 0};
+            const bool tr = ent.x < 0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+              Real row[6];
+              load6_ro(B + 6 * b, row);
+              if (!tr) {
+                Real u = 0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) u += row[q] * p[q];
+                out[b] = u;
+              } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) out[q] += p[b] * row[q];
+              }
+            }
+#pragma unroll
+            for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
+          }
+        }
+        __syncthreads();
+      }
+      // ... then a warp per row sums its entries
+      for (int a = warp; a < nr; a += kPcgWarps) {
+        const int i = t + Gs * a;
+        Real acc[6] = {0, 0, 0, 0, 0, 0};
+        if constexpr (kStaged) {
+          const int e1 = soff[a + 1];
+          for (int e = soff[a] + lane; e < e1; e += 32) {
+#pragma unroll
+            for (int b = 0; b < 6; ++b) acc[b] += sOut[(size_t)b * ent_cap + e];
+          }
+        } else {
+          const int e1 = __ldg(d.rl_ptr + i + 1);
+          for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
+            const int2 ent = __ldg(d.rl_ent + e);
+            const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
+            Real p[6];
+            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, ent.y, p, data_spins);
+            const bool tr = ent.x < 0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+              Real row[6];
+              load6_ro(B + 6 * b, row);
+              if (!tr) {
+                Real u = 0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) u += row[q] * p[q];
+                acc[b] += u;
+              } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[q] += p[b] * row[q];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] = warp_sum_r(acc[c]);
+        if (lane < 6) {
+          Real qc = acc[0];
+#pragma unroll
+          for (int c = 1; c < 6; ++c)
+            if (lane == c) qc = acc[c];
+          Real pc;
+          if constexpr (kTagged) {   // formed and published after the last reduction
+            pc = V(kP, a)[lane];
+          } else {
+            pc = k == 0 ? V(kZ, a)[lane] : V(kZ, a)[lane] + beta * V(kP, a)[lane];
+            V(kP, a)[lane] = pc;
+            P.X.put(pnew, 6 * (size_t)i + lane, pc, 0u);
+          }
+          V(kQ, a)[lane] = qc;
+          pa = O::add(pa, O::prod(pc, qc));
+        }
+      }
+    }
+    if (late) {   // every CTA stops iterating; the host gets a timeout
+      s_late = 1;
+      pa = acc_nan<Acc>();
+    }
+    if (!stream_reduce<kTagged>(pa, 8, d.part, t, Gs, base + 2 + 2 * k, spin_limit, [&](Acc pq) {
+          if (!sc.work) return;
+          if (!acc_positive(pq)) {   // pᵀAp <= 0: nothing moves from here on
+            sc.bad = 1;
+            sc.work = 0;
+            atomicOr(d.status, kStatusBreakdown);
+            return;
+          }
+          sc.alpha = acc_ratio<Real, Acc>(sc.rz, pq);
+        })) {
+      atomicOr(d.status, kStatusTimeout);
+      return;
+    }
+    // ---- x += α p, r −= α q, z = M⁻¹ r, and the shares of rᵀz (lanes 0-5)
+    pa = O::zero();
+    if (sc.work) {
+      const Real alpha = sc.alpha;
+      for (int a = warp; a < nr; a += kPcgWarps) {
+        if (lane < 6) {
+          V(kX, a)[lane] += alpha * V(kP, a)[lane];
+          V(kR, a)[lane] -= alpha * V(kQ, a)[lane];
+        }
+        __syncwarp();
+        if (lane < 6) {
+          const Real* mi = sMi + 21 * a;
+          const Real* r = V(kR, a);
+          Real z = 0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) z += mi[sym(lane, c)] * r[c];
+          V(kZ, a)[lane] = z;
+          if constexpr (!kTagged) P.X.put(P.X.z, 6 * (size_t)(t + Gs * a) + lane, z, 0u);
+          pa = O::add(pa, O::prod(r[lane], z));
+        }
+      }
+    }
+    if (!stream_reduce<kTagged>(pa, 8, d.part, t, Gs, base + 3 + 2 * k, spin_limit, [&](Acc rz) {
+          if (!sc.work) return;
+          sc.beta = acc_ratio<Real, Acc>(rz, sc.rz);
+          sc.rz = rz;
+          sc.work = O::nonzero(rz);
+        })) {
+      atomicOr(d.status, kStatusTimeout);
+      return;
+    }
+    if constexpr (kTagged) {   // p of the next iteration, published for the rows' readers
+      if (sc.work && k + 1 < K) {
+        const Real beta_n = sc.beta;
+        const unsigned tag = (unsigned)(base + 3 + 2 * k);
+        auto* pnext = (k & 1) ? P.X.p0 : P.X.p1;
+        for (int a = warp; a < nr; a += kPcgWarps)
+          if (lane < 6) {
+            const Real pc = V(kZ, a)[lane] + beta_n * V(kP, a)[lane];
+            V(kP, a)[lane] = pc;
+            P.X.put(pnext, 6 * (size_t)(t + Gs * a) + lane, pc, tag);
+          }
+      }
+    }
+  }
+  if (tid == 0 && s_late) atomicOr(d.status, kStatusTimeout);
+  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = O::value(sc.rz);
+
+  // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
+  if (sc.bad) return;
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
+    const Real* x = V(kX, a);
+    if constexpr (std::is_same<Real, float>::value) {
+      float xi[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) xi[c] = x[c];
+      float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
+      apply_increment(q0, qe, xi);
+      d.dq[2 * j] = q0;
+      d.dq[2 * j + 1] = qe;
+    } else {
+      double xi[6], q[8];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) xi[c] = x[c];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) q[c] = d.dq64[8 * j + c];
+      apply_increment64(q, xi);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) d.dq64[8 * j + c] = q[c];
+      d.dq[2 * j] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+      d.dq[2 * j + 1] = make_float4((float)q[4], (float)q[5], (float)q[6], (float)q[7]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP32 solver, one reduction per iteration
+
+// The FP32 modes run PCG in the Chronopoulos-Gear arrangement (Chronopoulos
+// & Gear, J. Comput. Appl. Math. 27, 1989): u = M⁻¹ r and w = A u are formed
+// explicitly every iteration, both inner products γ = (r, u) and δ = (w, u)
+// come from ONE reduction, and p, s = A p follow by recurrence:
+//   β = γ / γ_prev,  α = γ / (δ − β γ / α_prev)   (first: β = 0, α = γ / δ)
+//   p = u + β p,  s = w + β s,  x += α p,  r −= α s.
+// The iterates are those of standard PCG in exact arithmetic; with w
+// computed, not recurred, FP32 accuracy stays close to the standard
+// recurrences (unlike the pipelined variants).  The denominator is pᵀAp; a
+// value <= 0 is a breakdown.  A row's owner publishes its u (tagged words)
+// as soon as it is formed; the SpMV waits for its neighbours' tags, so the
+// exchange of u needs no barrier and an iteration has one synchronisation.
+enum { kGx = 0, kGr, kGu, kGw, kGp, kGs, kGearVecs };
+
+template <typename Acc, int kMode>
+__global__ void __launch_bounds__(kPcgThreads, 1)
+k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+  using O = AccOps<Acc>;
+  using Real = float;
+  constexpr bool kStaged = kMode != kSpmvRows;
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int t = blockIdx.x - __ldg(bt.tile_base + s);
+  const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = d.n_n;
+  const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
+  const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
+  const float* __restrict__ A = d.A;
+  unsigned long long* const ub[2] = {d.xp, d.xp + 6 * (size_t)n};   // u by iteration parity
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SmemLayout L = pcg_layout<Real>(rows_cap, ent_cap, kMode, kGearVecs);
+  Real* sMi = reinterpret_cast<Real*>(smem_raw + L.mi);
+  Real* svec = reinterpret_cast<Real*>(smem_raw + L.vec);
+  Real* sA = reinterpret_cast<Real*>(smem_raw + L.a);
+  Real* sOut = reinterpret_cast<Real*>(smem_raw + L.out);
+  int* sj = reinterpret_cast<int*>(smem_raw + L.ent);
+  int2* sent = reinterpret_cast<int2*>(smem_raw + L.ent);
+  int* soff = reinterpret_cast<int*>(smem_raw + L.off);
+  auto V = [&](int v, int a) { return svec + ((size_t)v * rows_cap + a) * 6; };
+  __shared__ Scalars<Real, Acc> sc;
+  __shared__ Acc s_gprev;
+  __shared__ Real s_aprev;
+  __shared__ int s_late;
+  const int data_spins = spin_limit >> 6;
+
+  // ---- set-up, a thread per own row: M⁻¹, r = −g, u = M⁻¹ r (published), x = p = s = 0
+  if (tid == 0) s_late = 0;
+  bool broken = false;
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
+    Real* mi = sMi + 21 * a;
+    if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
+      atomicOr(d.status, kStatusBreakdown);
+      broken = true;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) mi[k] = 0;
+    }
+    Real r[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) r[c] = -d.g[6 * j + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      Real u = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) u += mi[sym(c, k)] * r[k];
+      V(kGr, a)[c] = r[c];
+      V(kGu, a)[c] = u;
+      V(kGx, a)[c] = 0;
+      V(kGp, a)[c] = 0;
+      V(kGs, a)[c] = 0;
+      Xchg<float>::put(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
+    }
+  }
+  if constexpr (kStaged) {
+    if (warp == 0) {   // the rows' entry offsets: an exclusive scan of the row lengths
+      int run = 0;
+      for (int a0 = 0; a0 < nr; a0 += 32) {
+        const int a = a0 + lane;
+        const int i = t + Gs * a;
+        const int len = a < nr ? __ldg(d.rl_ptr + i + 1) - __ldg(d.rl_ptr + i) : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += u;
+        }
+        if (a < nr) soff[a + 1] = run + incl;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) soff[0] = 0;
+    }
+    __syncthreads();
+    for (int a = warp; a < nr; a += kPcgWarps) {   // every entry's block (turned) and neighbour
+      const int i = t + Gs * a;
+      const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
+      for (int k = lane; k < len; k += 32) {
+        const int2 ent = __ldg(d.rl_ent + r0 + k);
+        const int e = e0 + k;
+        if constexpr (kMode == kSpmvSmemA) {
+          const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
+          const bool tr = ent.x < 0;
+          sj[e] = ent.y;
+#pragma unroll
+          for (int q = 0; q < 36; ++q) {
+            const int dst = tr ? (q % 6) * 6 + q / 6 : q;
+            sA[(size_t)dst * ent_cap + e] = __ldg(B + q);
+          }
+        } else {
+          sent[e] = ent;
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    sc.alpha = 0; sc.beta = 0; sc.rz = O::zero(); sc.bad = 0; sc.work = 1;
+    s_gprev = O::zero(); s_aprev = 1.f;
+  }
+  __syncthreads();
+  // a broken diagonal block reaches every CTA through the first reduction
+  Acc carry = broken ? acc_nan<Acc>() : O::zero();
+  __syncthreads();
+
+  for (int k = 0; k <= K; ++k) {
+    // ---- w = A u (u of iteration k, from the rows' owners) and the shares of γ = (r, u), δ = (w, u)
+    const bool last = k == K;   // the final reduction only measures γ for the statistics
+    const unsigned tu = (unsigned)(base + 1 + k);
+    const unsigned long long* ucur = ub[k & 1];
+    Acc pg = carry, pd = O::zero();
+    carry = O::zero();
+    bool late = false;
+    const bool spmv = sc.work && !last;
+    if (spmv && kStaged) {
+      const int ne = soff[nr];
+      for (int e = tid; e < ne; e += kPcgThreads) {
+        Real p[6];
+        if constexpr (kMode == kSpmvSmemA) {
+          late |= !Xchg<float>::get6(ucur, sj[e], tu, p, data_spins);
+#pragma unroll
+          for (int b = 0; b < 6; ++b) {
+            Real v = 0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v += sA[(size_t)(6 * b + q) * ent_cap + e] * p[q];
+            sOut[(size_t)b * ent_cap + e] = v;
+          }
+        } else {
+          const int2 ent = sent[e];
+          late |= !Xchg<float>::get6(ucur, ent.y, tu, p, data_spins);
+          const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
+          Real out[6] = {0, 0, 0, 0, 0, 0};
+          const bool tr = ent.x < 0;
+#pragma unroll
+          for (int b = 0; b < 6; ++b) {
+            Real row[6];
+            load6_ro(B + 6 * b, row);
+            if (!tr) {
+              Real v = 0;
+#pragma unroll
+              for (int q = 0; q < 6; ++q) v += row[q] * p[q];
+              out[b] = v;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) out[q] += p[b] * row[q];
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
+        }
+      }
+      __syncthreads();
+    }
+    for (int a = warp; a < nr; a += kPcgWarps) {
+      const int i = t + Gs * a;
+      Real acc[6] = {0, 0, 0, 0, 0, 0};
+      if (spmv) {
+        if constexpr (kStaged) {
+          const int e1 = soff[a + 1];
+          for (int e = soff[a] + lane; e < e1; e += 32) {
+#pragma unroll
+            for (int b = 0; b < 6; ++b) acc[b] += sOut[(size_t)b * ent_cap + e];
+          }
+        } else {
+          const int e1 = __ldg(d.rl_ptr + i + 1);
+          for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
+            const int2 ent = __ldg(d.rl_ent + e);
+            const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
+            Real p[6];
+            late |= !Xchg<float>::get6(ucur, ent.y, tu, p, data_spins);
+            const bool tr = ent.x < 0;
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+              Real row[6];
+              load6_ro(B + 6 * b, row);
+              if (!tr) {
+                Real v = 0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) v += row[q] * p[q];
+                acc[b] += v;
+              } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[q] += p[b] * row[q];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] = warp_sum_r(acc[c]);
+      }
+      if (lane < 6) {
+        Real wc = acc[0];
+#pragma unroll
+        for (int c = 1; c < 6; ++c)
+          if (lane == c) wc = acc[c];
+        const Real uc = V(kGu, a)[lane];
+        pg = O::add(pg, O::prod(V(kGr, a)[lane], uc));
+        if (spmv) {
+          V(kGw, a)[lane] = wc;
+          pd = O::add(pd, O::prod(wc, uc));
+        }
+      }
+    }
+    if (late) {   // every CTA stops iterating; the host gets a timeout
+      s_late = 1;
+      pg = acc_nan<Acc>();
+    }
+    // ---- one reduction: γ and δ together
+    if (!stream_reduce_pair(pg, pd, k == 0 ? 32 : 8, d.part, t, Gs, base + 1 + k, spin_limit, [&](Acc g, Acc dl) {
+          if (last) {
+            if (t == 0) d.pcg_rz[gn_it] = O::value(g);
+            return;
+          }
+          if (!sc.work) return;
+          if (acc_is_nan(g) || acc_is_nan(dl)) {
+            sc.bad = 1; sc.work = 0;
+            atomicOr(d.status, kStatusBreakdown);
+            return;
+          }
+          sc.rz = g;
+          if (!O::nonzero(g)) { sc.work = 0; return; }   // r = 0: converged exactly
+          Real beta = 0;
+          bool pos;
+          Real alpha;
+          if constexpr (std::is_same<Acc, DF>::value) {
+            float den = dl.hi;
+            if (k > 0) {
+              beta = __fdiv_rn(g.hi, s_gprev.hi);
+              const float tt = __fmul_rn(beta, __fdiv_rn(g.hi, s_aprev));
+              den = df_add(dl, DF{-tt, 0.f}).hi;
+            }
+            pos = den > 0.f;
+            alpha = pos ? __fdiv_rn(g.hi, den) : 0.f;
+          } else {
+            double den = dl;
+            if (k > 0) {
+              beta = ratio_f32(g, s_gprev);
+              den = dl - (double)beta * (double)ratio_f32(g, (double)s_aprev);
+            }
+            pos = den > 0.0;
+            alpha = pos ? ratio_f32(g, den) : 0.f;
+          }
+          if (!pos) {   // pᵀAp <= 0: nothing moves from here on
+            sc.bad = 1; sc.work = 0;
+            atomicOr(d.status, kStatusBreakdown);
+            return;
+          }
+          sc.alpha = alpha;
+          sc.beta = beta;
+          s_aprev = alpha;
+          s_gprev = g;
+        })) {
+      atomicOr(d.status, kStatusTimeout);
+      return;
+    }
+    if (last) break;
+    // ---- p = u + β p, s = w + β s, x += α p, r −= α s, then u = M⁻¹ r (published)
+    if (sc.work) {
+      const Real alpha = sc.alpha, beta = sc.beta;
+      const unsigned tn = (unsigned)(base + 2 + k);
+      unsigned long long* unext = ub[(k + 1) & 1];
+      for (int a = warp; a < nr; a += kPcgWarps) {
+        if (lane < 6) {
+          const Real pc = V(kGu, a)[lane] + beta * V(kGp, a)[lane];
+          const Real sc_ = V(kGw, a)[lane] + beta * V(kGs, a)[lane];
+          V(kGp, a)[lane] = pc;
+          V(kGs, a)[lane] = sc_;
+          V(kGx, a)[lane] += alpha * pc;
+          V(kGr, a)[lane] -= alpha * sc_;
+        }
+        __syncwarp();
+        if (lane < 6) {
+          const Real* mi = sMi + 21 * a;
+          const Real* r = V(kGr, a);
+          Real u = 0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) u += mi[sym(lane, c)] * r[c];
+          V(kGu, a)[lane] = u;
+          Xchg<float>::put(unext, 6 * (size_t)(t + Gs * a) + lane, u, tn);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (tid == 0 && s_late) atomicOr(d.status, kStatusTimeout);
+
+  // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
+  if (sc.bad) return;
+  for (int a = tid; a < nr; a += kPcgThreads) {
+    const int j = t + Gs * a;
+    float xi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) xi[c] = V(kGx, a)[c];
+    float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
+    apply_increment(q0, qe, xi);
+    d.dq[2 * j] = q0;
+    d.dq[2 * j + 1] = qe;
+  }
+}
+
+// ------------------------------------------------------------------ timeout probe
+
+// Counter barrier over all CTAs of a cooperative launch, with a bounded wait.
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, int spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    const unsigned g = *vgen;
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      int spins = 0;
+      while (*vgen == g) {
+        if (++spins > spin_limit) { ok = 0; break; }
+        if (spins > 64) __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// A grid barrier that never completes when fewer CTAs run than it expects:
+// used to check that a wait which cannot finish ends by its bound and reports
+// a status the host can read.
+__global__ void k_barrier_probe(GridBarrier* gb, unsigned expected, int spin_limit, int* status) {
+  if (!grid_sync(gb, expected, spin_limit)) {
+    if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+  }
+}
+
+template <typename Acc>
+const void* pcg_gear_fn(int mode) {
+  switch (mode) {
+    case kSpmvSmemA: return reinterpret_cast<const void*>(k_pcg_gear<Acc, kSpmvSmemA>);
+    case kSpmvSmemOut: return reinterpret_cast<const void*>(k_pcg_gear<Acc, kSpmvSmemOut>);
+    default: return reinterpret_cast<const void*>(k_pcg_gear<Acc, kSpmvRows>);
+  }
+}
+
+const void* pcg_kernel(int precision, int mode) {
+  switch (precision) {
+    case SW_PRECISION_FP64:
+      switch (mode) {
+        case kSpmvSmemA: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvSmemA>);
+        case kSpmvSmemOut: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvSmemOut>);
+        default: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvRows>);
+      }
+    case SW_PRECISION_MIXED_F64DOTS: return pcg_gear_fn<double>(mode);
+    default: return pcg_gear_fn<DF>(mode);
+  }
+}
+
+}  // namespace
+
+int pcg_blocks_per_sm(int precision) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pcg_kernel(precision, kSpmvRows), kPcgThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+int pcg_threads() { return kPcgThreads; }
+
+size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode) {
+  return precision == SW_PRECISION_FP64 ? pcg_layout<double>(rows_cap, ent_cap, mode, kRowVecs).total
+                                        : pcg_layout<float>(rows_cap, ent_cap, mode, kGearVecs).total;
+}
+
+// One cooperative launch: every CTA is resident, so the waits of
+// stream_reduce always end (and are bounded regardless).
+cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st) {
+  const int nb = b.total_tiles[kTilePcg];
+  if (nb == 0) return cudaSuccess;
+  Batch bt = b.bt;
+  bt.tile_base = b.tile_base_dev[kTilePcg];
+  int spin = b.spin_limit;
+  int rows_cap = b.pcg_rows_cap;
+  int ent_cap = b.pcg_ent_cap;
+  const int prec = b.precision;
+  const int mode = b.pcg_mode;
+  const void* fn = pcg_kernel(prec, mode);
+  const size_t smem = pcg_smem_bytes(rows_cap, ent_cap, prec, mode);
+  static size_t configured[3][3] = {};
+  const int slot = prec < 0 || prec > 2 ? 0 : prec;
+  if (smem > 48 * 1024 && smem > configured[slot][mode]) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[slot][mode] = smem;
+  }
+  void* args[] = {&bt, &pcg_iters, &gn_it, &spin, &rows_cap, &ent_cap};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
+                                 int* status, cudaStream_t st) {
+  unsigned expected = (unsigned)nblocks_expected;
+  void* args[] = {&gb, &expected, &spin_limit, &status};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks_launched);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(k_barrier_probe), args);
+}
+
+}  // namespace sw

@@ -23,11 +23,12 @@ constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive def
 constexpr int kStatusBadIndex = 2;       // a gather index failed its range check
 constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
 
-// A CTA's partial of one reduction (a double-float pair hi + lo), published
-// with a generation stamp (release store of `gen` after the pair); slots are
-// double-buffered by the parity of the reduction's index.
-struct PartSlot {
-  float hi, lo;
+// A CTA's partial of one reduction (the accumulator's bit pattern),
+// published with a generation stamp (release pattern: the value, a fence,
+// then `gen`); slots are double-buffered by the parity of the reduction's
+// index.
+struct __align__(16) PartSlot {
+  unsigned long long v;
   unsigned long long gen;
 };
 
@@ -37,6 +38,7 @@ struct SwDev {
   float fx, fy, cx, cy;
   float sqrt_lambda, corr_dist, corr_normal, fuse_dist, fuse_normal, stable_conf;
   int recent_frames;
+  int precision;      // SW_PRECISION_*
   // sizes
   int n_s, n_n, n_sets, nnzb;
   int* t_now;         // current frame id (device scalar)
@@ -78,8 +80,16 @@ struct SwDev {
   // PCG
   float* Li;          // n_n * 21: inverse Cholesky factor of each diagonal block, packed lower
   float* x; float* r; float* z; float* p0; float* p1; float* q;
-  struct PartSlot* part;   // 2 * kMaxCtaPerStream published per-CTA partial dot products
+  struct PartSlot* part;   // 4 * kMaxCtaPerStream slots for the per-CTA partials of the PCG's reductions
+  unsigned long long* xz;  // 6 n_n tagged words: z as other CTAs of the PCG read it
+  unsigned long long* xp;  // 12 n_n tagged words: p, by iteration parity
   unsigned long long* pcg_epoch;   // launches of the persistent PCG so far
+  // all-FP64 variant only (null otherwise): the system, the PCG's shared
+  // vectors (u, m even, m odd) and the authoritative node transforms
+  double* A64;        // nnzb * 36
+  double* g64;        // 6 n_n
+  double* v64;        // 3 * 6 n_n
+  double* dq64;       // 8 per node
   // per-GN-iteration statistics
   double* e_depth;    // kMaxGn
   double* e_reg;      // kMaxGn
@@ -124,6 +134,9 @@ struct BatchHost {
   int* tile_base_dev[kTileKinds];   // device, per kind
   int spin_limit;                   // bounded wait of the PCG's reductions (polls)
   int pcg_rows_cap;                 // most rows one PCG CTA owns in the batch
+  int precision;                    // SW_PRECISION_* shared by every member
+  int pcg_ent_cap;                  // most matrix entries (block-row terms) one PCG CTA owns
+  int pcg_mode;                     // how the PCG's SpMV reaches the matrix (k_pcg.cu: SpmvMode)
 };
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st);
@@ -138,9 +151,9 @@ void launch_warp_live(const BatchHost& b, cudaStream_t st);
 void launch_index_map(const BatchHost& b, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
-int pcg_blocks_per_sm();
+int pcg_blocks_per_sm(int precision);
 int pcg_threads();
-size_t pcg_smem_bytes(int rows_cap);
+size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
                                  int* status, cudaStream_t st);
 

@@ -17,13 +17,16 @@ def ensure_built():
 class Pair:
     """A library stream and an oracle stream over one scene."""
 
-    def __init__(self, scene, **params):
+    def __init__(self, scene, precision=None, **params):
         self.scene = scene
         c = scene.cam
         self.cam = c
         self.params = params
         v4, n4, t2, node4 = sw.model_arrays(scene)
-        self.h = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4), **params))
+        lib_params = dict(params)
+        if precision is not None:
+            lib_params["precision"] = precision
+        self.h = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4), **lib_params))
         sw.sw_set_model(self.h, v4, n4, t2, node4)
         op = oracle.Params(c.width, c.height, c.fx, c.fy, c.cx, c.cy,
                            **{k: v for k, v in params.items()})

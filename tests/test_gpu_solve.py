@@ -34,10 +34,11 @@ def _compare_nodes(p):
     return float(rot.max()), float(trans.max())
 
 
-def test_plain_tiny_solve_matches_oracle():
-    """160x120 wavy surface, 64 nodes, 5 GN x 10 PCG."""
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_MIXED_F64DOTS])
+def test_plain_tiny_solve_matches_oracle(precision):
+    """160x120 wavy surface, 64 nodes, 5 GN x 10 PCG, in each solve precision."""
     scene = synth.plain_tiny(seed=0)
-    p = Pair(scene)
+    p = Pair(scene, precision=precision)
     try:
         p.upload(1)
         st = sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
