@@ -351,11 +351,14 @@ sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vect
   cudaStream_t st = r->st;
   launch_solve_begin(r->bh, st);
   for (int it = 0; it < gn; ++it) {
+    const bool f64 = r->bh.precision == SW_PRECISION_FP64;
     prof_mark(r, prof, kProfReg, true, true);
-    launch_reg_assemble(r->bh, it, st);
+    if (f64) launch_reg_assemble64(r->bh, it, st);
+    else launch_reg_assemble(r->bh, it, st);
     prof_mark(r, prof, kProfReg, false, true);
     prof_mark(r, prof, kProfData, true, true);
-    launch_data_assemble(r->bh, it, st);
+    if (f64) launch_data_assemble64(r->bh, it, st);
+    else launch_data_assemble(r->bh, it, st);
     prof_mark(r, prof, kProfData, false, true);
     prof_mark(r, prof, kProfPcg, true, true);
     SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
@@ -441,8 +444,9 @@ bool params_ok(const sw_params* p, std::string& why) {
   if (p->max_surfels < 0 || p->max_surfels > (1 << 28)) { why = "max_surfels out of range"; return false; }
   if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
   if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
-  if (p->precision != SW_PRECISION_MIXED && p->precision != SW_PRECISION_MIXED_F64DOTS) {
-    why = "precision must be SW_PRECISION_MIXED or SW_PRECISION_MIXED_F64DOTS";
+  if (p->precision != SW_PRECISION_MIXED && p->precision != SW_PRECISION_FP64 &&
+      p->precision != SW_PRECISION_MIXED_F64DOTS) {
+    why = "precision must be one of SW_PRECISION_MIXED, SW_PRECISION_FP64, SW_PRECISION_MIXED_F64DOTS";
     return false;
   }
   return true;
@@ -604,6 +608,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
   ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
   ALLOC(h.xz, 6 * nn); ALLOC(h.xp, 12 * nn);
+  if (p->precision == SW_PRECISION_FP64) { ALLOC(h.g64, 6 * nn); ALLOC(h.v64, 18 * nn); ALLOC(h.dq64, 8 * nn); }
   ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
   ALLOC(h.status, 1); ALLOC(h.t_now, 1);
 #undef ALLOC
@@ -758,6 +763,7 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   // nodes, identity transforms, graph
   SW_CUDA(s, cudaMemcpyAsync(h.node_p, node4, (size_t)n_n * sizeof(float4), cudaMemcpyHostToDevice, st));
   k_identity_dq<<<(n_n + 127) / 128, 128, 0, st>>>(h.dq, n_n);
+  launch_dq_widen(h, st);
   launch_node_graph(h, st);
   std::vector<int> graph((size_t)n_n * SW_K_GRAPH);
   SW_CUDA(s, cudaMemcpyAsync(graph.data(), h.graph, graph.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -834,6 +840,10 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   SW_TRY(upload_vec(s, &h.set_slots, P.set_slots));
   SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
   SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
+  if (h.precision == SW_PRECISION_FP64) {
+    SW_TRY(A(s, &h.A64, (size_t)h.nnzb * 36, true));
+    SW_CUDA(s, cudaMemsetAsync(h.A64, 0, (size_t)h.nnzb * 36 * sizeof(double), st));
+  }
   SW_CUDA(s, cudaMemsetAsync(h.g, 0, (size_t)n_n * 6 * sizeof(float), st));
   SW_CUDA(s, cudaMemsetAsync(h.corr_pix, 0xff, (size_t)std::max(1, n_s) * sizeof(int), st));
   SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
@@ -1028,6 +1038,8 @@ sw_status sw_set_node_dq(sw_handle s, const float* dq8, int n) {
   if (!s || !dq8) return fail(s, SW_ERR_INVALID_ARG, "null argument");
   if (!s->has_model || n != s->h.n_n) return fail(s, SW_ERR_INVALID_ARG, "node count mismatch");
   SW_CUDA(s, cudaMemcpyAsync(s->h.dq, dq8, (size_t)n * 32, cudaMemcpyHostToDevice, s->st));
+  launch_dq_widen(s->h, s->st);
+  SW_CUDA(s, cudaGetLastError());
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   return SW_OK;
 }
@@ -1094,8 +1106,13 @@ sw_status sw_debug_assemble(sw_handle s, int* nnzb_out, int* n_corr_out) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "needs a model and a depth frame");
   launch_solve_begin(s->run->bh, s->st);
-  launch_reg_assemble(s->run->bh, 0, s->st);
-  launch_data_assemble(s->run->bh, 0, s->st);
+  if (s->h.precision == SW_PRECISION_FP64) {
+    launch_reg_assemble64(s->run->bh, 0, s->st);
+    launch_data_assemble64(s->run->bh, 0, s->st);
+  } else {
+    launch_reg_assemble(s->run->bh, 0, s->st);
+    launch_data_assemble(s->run->bh, 0, s->st);
+  }
   SW_CUDA(s, cudaGetLastError());
   int nc = 0;
   SW_CUDA(s, cudaMemcpyAsync(&nc, s->h.n_corr, sizeof(int), cudaMemcpyDeviceToHost, s->st));
@@ -1112,6 +1129,15 @@ sw_status sw_debug_read_jtj(sw_handle s, int* rows, int* cols, float* vals, floa
   if (cap_blocks < nb) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
   if (rows) SW_CUDA(s, cudaMemcpyAsync(rows, s->h.blk_row, nb * sizeof(int), cudaMemcpyDeviceToHost, s->st));
   if (cols) SW_CUDA(s, cudaMemcpyAsync(cols, s->h.col, nb * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (s->h.precision == SW_PRECISION_FP64) {   // the FP64 system, rounded for the caller
+    std::vector<double> va(vals ? (size_t)nb * 36 : 0), vg(g ? (size_t)s->h.n_n * 6 : 0);
+    if (vals) SW_CUDA(s, cudaMemcpyAsync(va.data(), s->h.A64, va.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    if (g) SW_CUDA(s, cudaMemcpyAsync(vg.data(), s->h.g64, vg.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaStreamSynchronize(s->st));
+    for (size_t k = 0; k < va.size(); ++k) vals[k] = (float)va[k];
+    for (size_t k = 0; k < vg.size(); ++k) g[k] = (float)vg[k];
+    return SW_OK;
+  }
   if (vals) SW_CUDA(s, cudaMemcpyAsync(vals, s->h.A, (size_t)nb * 36 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
   if (g) SW_CUDA(s, cudaMemcpyAsync(g, s->h.g, (size_t)s->h.n_n * 6 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));

@@ -2,30 +2,28 @@
 // and the node update T_j ← Δ_j T_j (Sec. 7), one persistent cooperative
 // launch per Gauss-Newton iteration for every stream of a batch.
 //
-// Recurrences: standard PCG, x₀ = 0, exactly K iterations, stopping early
-// only when rᵀz is exactly zero; pᵀAp <= 0 is a breakdown.
-//   z = M⁻¹ r, p = z + β p, q = A p, α = rᵀz / pᵀq, x += α p, r −= α q.
-// (Pipelined variants that fuse the two reductions of an iteration into one
-// lose orders of magnitude of accuracy in FP32 on ill-conditioned systems of
-// this solve, so the two reductions stay.)
+// Both kernels run x₀ = 0 and exactly K iterations, stopping early only when
+// rᵀM⁻¹r is exactly zero; pᵀAp <= 0 (or a diagonal block that is not
+// positive definite) is a breakdown and leaves the node transforms as they
+// were.
 //
 // Work split.  Stream s owns the CTAs [tile_base[s], tile_base[s+1]), all
 // co-resident.  CTA t of a stream with G CTAs owns the block rows and nodes
 // i = t + G a (a = 0, 1, ...) and keeps everything about them in shared
-// memory for the whole solve: the 6x6 block of M⁻¹ and x, r, z, p, q.
-// Global memory carries only what other CTAs read: z, and p double-buffered
-// by iteration parity.  A warp takes one own row at a time: a lane per 6x6
-// block of the row for (A p)_i, with the neighbour's p = z + β p_old formed
-// on the fly, a warp sum of the six outputs; lanes 0-5 then hold the row's
-// six components for the vector updates.  The two reductions of an
-// iteration (pᵀq, rᵀz) are also its only synchronisation, and they are per
-// stream, so streams never wait for one another.
+// memory for the whole solve: the 6x6 block of M⁻¹ (FP64 Cholesky) and the
+// rows' vectors.  Global memory carries only the vector other CTAs read for
+// the SpMV.  The reductions are per stream, so streams never wait for one
+// another.
 //
-// Precision (template parameters).  Real is the type of the matrix, the
-// vectors and the step lengths; Acc the type the inner products are
-// accumulated in: float + DF (double-float pairs, the default), float +
-// double, or double + double (the all-FP64 variant).  M⁻¹ is formed in FP64
-// by Cholesky in every case.
+//   k_pcg_gear (FP32 modes)  Chronopoulos-Gear arrangement: one reduction
+//       per iteration; the SpMV's input is exchanged as tagged words that
+//       the readers wait for, with no fences and no barrier.
+//   k_pcg_f64 (SW_PRECISION_FP64)  the standard recurrences, two reductions
+//       per iteration with a release / acquire protocol; readers form the
+//       neighbour's p = z + β p_old from published z and p_old.
+//
+// Inner products accumulate in the Acc type: DF (double-float pairs, the
+// default) or FP64.
 #include <type_traits>
 
 #include "sw_internal.h"
@@ -173,32 +171,23 @@ __device__ bool block_inverse(const Real* a, Real* out) {
 
 // ------------------------------------------------------------------ exchange
 
-// What other CTAs read during the solve, z and p (p double-buffered by
-// iteration parity), and the reductions' slots.
-//
-// FP32 (the default): every value travels as one 8-byte word {FP32 bits,
+// FP32 kernel: every shared value travels as one 8-byte word {FP32 bits,
 // 32-bit generation tag}, written and read with single 8-byte accesses, so a
-// reader that sees the expected tag also sees the value written with it, and
-// no fence is needed anywhere (the writer never waits for its stores to
-// reach L2).  A reader that finds an older tag reads again (bounded).  The
-// owner of a row forms its p = z + β p_old as soon as β is known and
-// publishes p alone; readers wait for its tag.
-// FP64: plain values, published with a release pattern (value, acq_rel fence,
-// stamp) and read after acquire loads of the stamps; z and p_old are
-// published before the reduction that precedes their use, and readers form
-// p = z + β p_old themselves.
+// reader that sees the expected tag also sees the value written with it and
+// no fence is needed (the writer never waits for its stores to reach L2).  A
+// reader that finds an older tag reads again, a bounded number of times.
+// FP64 kernel: plain values, published with a release pattern (values, one
+// acq_rel fence, a relaxed store of a stamp) and read after acquire loads of
+// the stamps.
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-__device__ __forceinline__ void st_relaxed_gpu(unsigned long long* p, unsigned long long v) {
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a, unsigned long long b) {
   asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
@@ -214,78 +203,47 @@ __device__ __forceinline__ unsigned long long tagged(unsigned bits, unsigned tag
 }
 __device__ __forceinline__ unsigned tag_of(unsigned long long w) { return (unsigned)(w >> 32); }
 
-template <typename Real>
-struct Xchg;
+__device__ __forceinline__ void put_tagged(unsigned long long* buf, size_t i, float v, unsigned tag) {
+  st_relaxed_u64(buf + i, tagged(__float_as_uint(v), tag));
+}
 
-template <>
-struct Xchg<float> {
-  unsigned long long* z;    // unused: the owner of a row publishes its p
-  unsigned long long* p0;   // p, even iterations (6 n_n tagged words)
-  unsigned long long* p1;   // p, odd iterations
-  __device__ __forceinline__ static void put(unsigned long long* buf, size_t i, float v, unsigned tag) {
-    st_relaxed_u64(buf + i, tagged(__float_as_uint(v), tag));
-  }
-  // the 6 values of node j carrying the given tag; false if they did not
-  // arrive within `spins` further reads
-  __device__ __forceinline__ static bool get6(const unsigned long long* buf, int j, unsigned tag, float* v, int spins) {
-    const unsigned long long* src = buf + 6 * (size_t)j;
-    for (int n = 0;; ++n) {
-      ulonglong2 a[3];
+// the 6 values of node j carrying the given tag; false if they did not
+// arrive within `spins` further reads
+__device__ __forceinline__ bool get6_tagged(const unsigned long long* buf, int j, unsigned tag, float* v, int spins) {
+  const unsigned long long* src = buf + 6 * (size_t)j;
+  for (int n = 0;; ++n) {
+    ulonglong2 a[3];
 #pragma unroll
-      for (int h = 0; h < 3; ++h) a[h] = ld_relaxed_v2(src + 2 * h);
-      unsigned bad = 0;
-#pragma unroll
-      for (int h = 0; h < 3; ++h) {
-        bad |= (tag_of(a[h].x) ^ tag) | (tag_of(a[h].y) ^ tag);
-        v[2 * h] = __uint_as_float((unsigned)a[h].x);
-        v[2 * h + 1] = __uint_as_float((unsigned)a[h].y);
-      }
-      if (bad == 0) return true;
-      if (n >= spins) return false;
-    }
-  }
-};
-
-template <>
-struct Xchg<double> {
-  double* z;
-  double* p0;
-  double* p1;
-  __device__ __forceinline__ static void put(double* buf, size_t i, double v, unsigned) { buf[i] = v; }
-  __device__ __forceinline__ static bool get_p(const double* z, unsigned, const double* po, unsigned, bool with_old,
-                                               double beta, int j, double* p, int) {
-    const double2* z2 = reinterpret_cast<const double2*>(z + 6 * (size_t)j);
-    const double2* o2 = reinterpret_cast<const double2*>(po + 6 * (size_t)j);
+    for (int h = 0; h < 3; ++h) a[h] = ld_relaxed_v2(src + 2 * h);
+    unsigned bad = 0;
 #pragma unroll
     for (int h = 0; h < 3; ++h) {
-      const double2 a = __ldcg(z2 + h);
-      p[2 * h] = a.x; p[2 * h + 1] = a.y;
+      bad |= (tag_of(a[h].x) ^ tag) | (tag_of(a[h].y) ^ tag);
+      v[2 * h] = __uint_as_float((unsigned)a[h].x);
+      v[2 * h + 1] = __uint_as_float((unsigned)a[h].y);
     }
-    if (with_old) {
-#pragma unroll
-      for (int h = 0; h < 3; ++h) {
-        const double2 o = __ldcg(o2 + h);
-        p[2 * h] += beta * o.x; p[2 * h + 1] += beta * o.y;
-      }
-    }
-    return true;
+    if (bad == 0) return true;
+    if (n >= spins) return false;
   }
-};
-
-template <typename Real>
-struct PcgData {
-  const Real* A;   // nnzb x 36
-  const Real* g;   // 6 n_n
-  Xchg<Real> X;
-};
-
-__device__ __forceinline__ PcgData<float> pcg_data(const SwDev& d, float) {
-  const size_t n6 = 6 * (size_t)d.n_n;
-  return {d.A, d.g, {d.xz, d.xp, d.xp + n6}};
 }
-__device__ __forceinline__ PcgData<double> pcg_data(const SwDev& d, double) {
-  const size_t n6 = 6 * (size_t)d.n_n;
-  return {d.A64, d.g64, {d.v64, d.v64 + n6, d.v64 + 2 * n6}};
+
+// p_j = z_j (+ β p_old,j) from two FP64 vectors published before the last reduction
+__device__ __forceinline__ void get_p64(const double* z, const double* po, bool with_old, double beta, int j,
+                                        double* p) {
+  const double2* z2 = reinterpret_cast<const double2*>(z + 6 * (size_t)j);
+  const double2* o2 = reinterpret_cast<const double2*>(po + 6 * (size_t)j);
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const double2 a = __ldcg(z2 + h);
+    p[2 * h] = a.x; p[2 * h + 1] = a.y;
+  }
+  if (with_old) {
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const double2 o = __ldcg(o2 + h);
+      p[2 * h] += beta * o.x; p[2 * h + 1] += beta * o.y;
+    }
+  }
 }
 
 // one row of a 6x6 block of the matrix (read-only for the whole launch)
@@ -313,84 +271,20 @@ __device__ __forceinline__ Real warp_sum_r(Real v) {
   return v;
 }
 
-// ------------------------------------------------------------------ reduction
+// ------------------------------------------------------------------ reductions
 
-// One reduction among the CTAs of one stream, which is also their only
-// synchronisation.  Precondition: within each warp only lanes below `lanes`
-// (a power of two) hold nonzero values.  Every CTA publishes its block sum
-// in its slot for generation `gen` (slots double-buffered by its parity);
-// one warp polls the stream's slots (bounded) and sums them in a fixed
-// order, so the total is deterministic for a given number of CTAs.
-// `on_total(total)` runs on one thread before the CTA continues (the
-// step-length arithmetic, done once).  Returns false if the wait ran out.
-// kTagged: the slot is two tagged words holding the value's two 32-bit
-// halves; otherwise the release / acquire pattern on a stamp.
-template <bool kTagged, typename Acc, typename F>
-__device__ __forceinline__ bool stream_reduce(Acc v, int lanes, PartSlot* part, int t, int gs,
-                                              unsigned long long gen, int spin_limit, F&& on_total) {
-  using O = AccOps<Acc>;
-  __shared__ Acc s_w[32];
-  __shared__ int s_ok;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = lanes >> 1; o > 0; o >>= 1) v = O::add(v, O::shfl_xor(v, o));
-  if (lane == 0) s_w[wid] = v;
-  __syncthreads();
-  PartSlot* buf = part + (gen & 1ull) * kMaxCtaPerStream;
-  const unsigned tag = (unsigned)gen;
-  if (wid == 0) {
-    Acc b = lane < nw ? s_w[lane] : O::zero();
-    b = warp_sum_acc(b);
-    int ok = 1;
-    Acc c = O::zero();
-    if constexpr (kTagged) {
-      if (lane == 0) {
-        const unsigned long long bits = O::bits(b);
-        st_relaxed_v2(&buf[t].v, tagged((unsigned)bits, tag), tagged((unsigned)(bits >> 32), tag));
-      }
-      for (int k = lane; k < gs; k += 64) {   // a lane waits for two slots at once
-        const bool two = k + 32 < gs;
-        ulonglong2 w0, w1 = make_ulonglong2(tagged(0u, tag), tagged(0u, tag));
-        int spins = 0;
-        for (;;) {
-          w0 = ld_relaxed_v2(&buf[k].v);
-          if (two) w1 = ld_relaxed_v2(&buf[k + 32].v);
-          if (((tag_of(w0.x) ^ tag) | (tag_of(w0.y) ^ tag) | (tag_of(w1.x) ^ tag) | (tag_of(w1.y) ^ tag)) == 0) break;
-          if (++spins > spin_limit) { ok = 0; break; }
-        }
-        if (!ok) break;
-        c = O::add(c, O::from_bits((w0.x & 0xffffffffull) | (w0.y << 32)));
-        if (two) c = O::add(c, O::from_bits((w1.x & 0xffffffffull) | (w1.y << 32)));
-      }
-      ok = __all_sync(0xffffffffu, ok);
-    } else {
-      if (lane == 0) {
-        buf[t].v = O::bits(b);
-        fence_acq_rel_gpu();
-        st_relaxed_gpu(&buf[t].gen, gen);
-      }
-      for (int k = lane; k < gs; k += 32) {
-        int spins = 0;
-        while (ld_acquire_gpu(&buf[k].gen) < gen) {
-          if (++spins > spin_limit) { ok = 0; break; }
-        }
-        if (!ok) break;
-      }
-      ok = __all_sync(0xffffffffu, ok);
-      for (int k = lane; k < gs; k += 32) c = O::add(c, O::from_bits(__ldcg(&buf[k].v)));
-    }
-    c = warp_sum_acc(c);
-    if (lane == 0) {
-      s_ok = ok;
-      on_total(c);
-    }
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
+// A reduction among the CTAs of one stream is also their synchronisation.
+// Precondition: within each warp only lanes below `lanes` (a power of two)
+// hold nonzero values.  Every CTA publishes its block sums for generation
+// `gen` (slots double-buffered by its parity); one warp polls the stream's
+// slots (bounded) and sums them in a fixed order, so the totals are
+// deterministic for a given number of CTAs.  `on_total` runs on one thread
+// before the CTA continues (the step-length arithmetic, done once).  Both
+// return false if the wait ran out.
 
-// Two values in one tagged reduction: CTA t publishes both in the slots
-// 2t and 2t+1 of the generation's half of `part` (2 kMaxCtaPerStream slots
-// per parity), and the pollers check all four tags of a CTA at once.
+// Two values, tagged: CTA t writes each value's two 32-bit halves as tagged
+// words into slots 2t and 2t+1 of the generation's half of `part`
+// (2 kMaxCtaPerStream slots per parity); pollers check all four tags at once.
 template <typename Acc, typename F>
 __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, PartSlot* part, int t, int gs,
                                                    unsigned long long gen, int spin_limit, F&& on_total) {
@@ -443,38 +337,61 @@ __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, Pa
   return s_ok != 0;
 }
 
-// ------------------------------------------------------------------ the solver
+// One value, release / acquire: the value, one acq_rel fence and a relaxed
+// store of the stamp, so the CTA's global writes before the call go with it;
+// pollers take acquire loads of the stamps.
+template <typename Acc, typename F>
+__device__ __forceinline__ bool stream_reduce_fenced(Acc v, int lanes, PartSlot* part, int t, int gs,
+                                                     unsigned long long gen, int spin_limit, F&& on_total) {
+  using O = AccOps<Acc>;
+  __shared__ Acc s_w[32];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = lanes >> 1; o > 0; o >>= 1) v = O::add(v, O::shfl_xor(v, o));
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  PartSlot* buf = part + (gen & 1ull) * kMaxCtaPerStream;
+  if (wid == 0) {
+    Acc b = lane < nw ? s_w[lane] : O::zero();
+    b = warp_sum_acc(b);
+    if (lane == 0) {
+      buf[t].v = O::bits(b);
+      fence_acq_rel_gpu();
+      st_relaxed_u64(&buf[t].gen, gen);
+    }
+    int ok = 1;
+    for (int k = lane; k < gs; k += 32) {
+      int spins = 0;
+      while (ld_acquire_u64(&buf[k].gen) < gen) {
+        if (++spins > spin_limit) { ok = 0; break; }
+      }
+      if (!ok) break;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    Acc c = O::zero();
+    for (int k = lane; k < gs; k += 32) c = O::add(c, O::from_bits(__ldcg(&buf[k].v)));
+    c = warp_sum_acc(c);
+    if (lane == 0) {
+      s_ok = ok;
+      on_total(c);
+    }
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ shared pieces of the two kernels
 
 constexpr int kPcgThreads = 1024;
 constexpr int kPcgWarps = kPcgThreads / 32;
-enum { kX = 0, kR, kZ, kP, kQ, kRowVecs };
-constexpr int kRowReals = 21 + 6 * kRowVecs;   // M⁻¹ packed, then the five vectors
 
 template <typename Real, typename Acc>
 struct Scalars {
   Real alpha, beta;
-  Acc rz;      // current rᵀz
-  int work;    // rᵀz != 0 and no breakdown
+  Acc rz;      // current rᵀM⁻¹r
+  int work;    // rᵀM⁻¹r != 0 and no breakdown
   int bad;     // breakdown seen
 };
-
-// a / b of two positive accumulated values, in Real
-template <typename Real, typename Acc>
-__device__ __forceinline__ Real acc_ratio(Acc a, Acc b) {
-  if constexpr (std::is_same<Acc, DF>::value) {
-    return __fdiv_rn(a.hi, b.hi);
-  } else if constexpr (std::is_same<Real, float>::value) {
-    return ratio_f32(a, b);
-  } else {
-    return a / b;
-  }
-}
-
-template <typename Acc>
-__device__ __forceinline__ bool acc_positive(Acc a) {
-  if constexpr (std::is_same<Acc, DF>::value) return a.hi > 0.f;
-  else return a > 0.0;
-}
 
 template <typename Acc>
 __device__ __forceinline__ Acc acc_nan() {
@@ -498,13 +415,13 @@ __device__ __forceinline__ bool acc_is_nan(Acc a) {
 //   kSpmvRows    a warp per row, a lane per entry, nothing staged.
 enum SpmvMode { kSpmvRows = 0, kSpmvSmemOut = 1, kSpmvSmemA = 2 };
 
-// Shared memory of one CTA: per own row M⁻¹ (21) and x r z p q (30); in the
-// staged modes the six outputs of every entry and, with kSpmvSmemA, the
-// entries' blocks (36 values each), both stored entry-minor (value q of entry
-// e at q * ent_cap + e, so threads on consecutive entries hit consecutive
-// banks) with every block already turned to multiply the neighbour's vector
-// directly; then the rows' entry offsets and per entry its neighbour
-// (kSpmvSmemA) or its block and neighbour (kSpmvSmemOut).
+// Shared memory of one CTA: per own row M⁻¹ (21) and `row_vecs` 6-vectors;
+// in the staged modes the six outputs of every entry and, with kSpmvSmemA,
+// the entries' blocks (36 values each), both stored entry-minor (value q of
+// entry e at q * ent_cap + e, so threads on consecutive entries hit
+// consecutive banks) with every block already turned to multiply the
+// neighbour's vector directly; then per entry its neighbour (kSpmvSmemA) or
+// its block and neighbour (kSpmvSmemOut); then the rows' entry offsets.
 // Byte offsets of the sections, each rounded up to 16 bytes.
 struct SmemLayout {
   size_t mi, vec, a, out, ent, off, total;
@@ -524,22 +441,97 @@ __host__ __device__ constexpr SmemLayout pcg_layout(int rows_cap, int ent_cap, i
   return L;
 }
 
-// p of neighbour j for this iteration's SpMV: the published p (tagged
-// exchange) or z + β p_old formed here (FP64 exchange)
-__device__ __forceinline__ bool fetch_p(const Xchg<float>&, const unsigned long long* pcur, const unsigned long long*,
-                                        unsigned tag, bool, float, int j, float* p, int spins) {
-  return Xchg<float>::get6(pcur, j, tag, p, spins);
-}
-__device__ __forceinline__ bool fetch_p(const Xchg<double>& X, const double*, const double* pold, unsigned, bool with_old,
-                                        double beta, int j, double* p, int) {
-  return Xchg<double>::get_p(X.z, 0u, pold, 0u, with_old, beta, j, p, 0);
+// Staged modes, at set-up: the rows' entry offsets (warp 0, an exclusive
+// scan of the row lengths), then per entry its block turned to multiply the
+// neighbour's vector (kSpmvSmemA) or where to find it (kSpmvSmemOut).
+template <int kMode, typename Real>
+__device__ __forceinline__ void stage_entries(const SwDev& d, const Real* A, int t, int Gs, int nr, int ent_cap,
+                                              Real* sA, int* sj, int2* sent, int* soff) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    int run = 0;
+    for (int a0 = 0; a0 < nr; a0 += 32) {
+      const int a = a0 + lane;
+      const int i = t + Gs * a;
+      const int len = a < nr ? __ldg(d.rl_ptr + i + 1) - __ldg(d.rl_ptr + i) : 0;
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (a < nr) soff[a + 1] = run + incl;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) soff[0] = 0;
+  }
+  __syncthreads();
+  for (int a = warp; a < nr; a += kPcgWarps) {
+    const int i = t + Gs * a;
+    const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
+    for (int k = lane; k < len; k += 32) {
+      const int2 ent = __ldg(d.rl_ent + r0 + k);
+      const int e = e0 + k;
+      if constexpr (kMode == kSpmvSmemA) {
+        const Real* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
+        const bool tr = ent.x < 0;
+        sj[e] = ent.y;
+#pragma unroll
+        for (int q = 0; q < 36; ++q) {
+          const int dst = tr ? (q % 6) * 6 + q / 6 : q;
+          sA[(size_t)dst * ent_cap + e] = __ldg(B + q);
+        }
+      } else {
+        sent[e] = ent;
+      }
+    }
+  }
 }
 
-template <typename Real, typename Acc, int kMode>
+// One entry's product: the block of entry `ent` (or entry e of sA) times p, six outputs.
+template <int kMode, typename Real>
+__device__ __forceinline__ void entry_product(const Real* A, const Real* sA, int ent_cap, int e, int2 ent,
+                                              const Real* p, Real* out) {
+  if constexpr (kMode == kSpmvSmemA) {
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      Real v = 0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += sA[(size_t)(6 * b + q) * ent_cap + e] * p[q];
+      out[b] = v;
+    }
+  } else {
+    const Real* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
+    const bool tr = ent.x < 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) out[b] = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      Real row[6];
+      load6_ro(B + 6 * b, row);
+      if (!tr) {
+        Real v = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += row[q] * p[q];
+        out[b] += v;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out[q] += p[b] * row[q];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP64 solver, standard recurrences
+
+enum { kX = 0, kR, kZ, kP, kQ, kRowVecs };
+
+template <int kMode>
 __global__ void __launch_bounds__(kPcgThreads, 1)
-k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+  using Acc = double;
   using O = AccOps<Acc>;
-  constexpr bool kTagged = std::is_same<Real, float>::value;
+  constexpr bool kStaged = kMode != kSpmvRows;
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -549,96 +541,53 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
   const int n = d.n_n;
   const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
   const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
-  const PcgData<Real> P = pcg_data(d, Real(0));
+  const double* __restrict__ A = d.A64;
+  const size_t n6 = 6 * (size_t)n;
+  double* const gz = d.v64;                                   // z of every node
+  double* const pbuf[2] = {d.v64 + n6, d.v64 + 2 * n6};       // p by iteration parity
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool kStaged = kMode != kSpmvRows;
-  const SmemLayout L = pcg_layout<Real>(rows_cap, ent_cap, kMode, kRowVecs);
-  Real* sMi = reinterpret_cast<Real*>(smem_raw + L.mi);
-  Real* svec = reinterpret_cast<Real*>(smem_raw + L.vec);
-  Real* sA = reinterpret_cast<Real*>(smem_raw + L.a);
-  Real* sOut = reinterpret_cast<Real*>(smem_raw + L.out);
-  int* sj = reinterpret_cast<int*>(smem_raw + L.ent);       // kSpmvSmemA: neighbour per entry
-  int2* sent = reinterpret_cast<int2*>(smem_raw + L.ent);   // kSpmvSmemOut: (block | turned << 31, neighbour)
+  const SmemLayout L = pcg_layout<double>(rows_cap, ent_cap, kMode, kRowVecs);
+  double* sMi = reinterpret_cast<double*>(smem_raw + L.mi);
+  double* svec = reinterpret_cast<double*>(smem_raw + L.vec);
+  double* sA = reinterpret_cast<double*>(smem_raw + L.a);
+  double* sOut = reinterpret_cast<double*>(smem_raw + L.out);
+  int* sj = reinterpret_cast<int*>(smem_raw + L.ent);
+  int2* sent = reinterpret_cast<int2*>(smem_raw + L.ent);
   int* soff = reinterpret_cast<int*>(smem_raw + L.off);
   auto V = [&](int v, int a) { return svec + ((size_t)v * rows_cap + a) * 6; };
-  __shared__ Scalars<Real, Acc> sc;
-  __shared__ int s_late;   // a tagged value that never arrived
+  __shared__ Scalars<double, Acc> sc;
 
-  // ---- set-up, a thread per own row: M⁻¹, r = −g, z = M⁻¹ r, x = p = 0
-  if (tid == 0) s_late = 0;
+  // ---- set-up, a thread per own row: M⁻¹, r = −g, z = M⁻¹ r (published), x = p = 0
   Acc pa = O::zero();
   bool broken = false;
   for (int a = tid; a < nr; a += kPcgThreads) {
     const int j = t + Gs * a;
-    Real* mi = sMi + 21 * a;
-    if (!block_inverse(P.A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
+    double* mi = sMi + 21 * a;
+    if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
       atomicOr(d.status, kStatusBreakdown);
       broken = true;
 #pragma unroll
       for (int k = 0; k < 21; ++k) mi[k] = 0;
     }
-    Real r[6];
+    double r[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) r[c] = -P.g[6 * j + c];
+    for (int c = 0; c < 6; ++c) r[c] = -d.g64[6 * j + c];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      Real z = 0;
+      double z = 0;
 #pragma unroll
       for (int k = 0; k < 6; ++k) z += mi[sym(c, k)] * r[k];
       V(kR, a)[c] = r[c];
       V(kZ, a)[c] = z;
       V(kX, a)[c] = 0;
-      V(kP, a)[c] = kTagged ? z : 0;
-      if constexpr (kTagged) P.X.put(P.X.p0, 6 * (size_t)j + c, z, (unsigned)(base + 1));   // p₀ = z₀
-      else P.X.put(P.X.z, 6 * (size_t)j + c, z, 0u);
+      V(kP, a)[c] = 0;
+      gz[6 * (size_t)j + c] = z;
       pa = O::add(pa, O::prod(r[c], z));
     }
   }
-  if (broken) pa = acc_nan<Acc>();   // a diagonal block that is not positive definite reaches every CTA
-  if constexpr (kStaged) {
-    // the rows' entry offsets (warp 0, an exclusive scan of the row lengths) ...
-    if (warp == 0) {
-      int run = 0;
-      for (int a0 = 0; a0 < nr; a0 += 32) {
-        const int a = a0 + lane;
-        const int i = t + Gs * a;
-        const int len = a < nr ? __ldg(d.rl_ptr + i + 1) - __ldg(d.rl_ptr + i) : 0;
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += u;
-        }
-        if (a < nr) soff[a + 1] = run + incl;
-        run += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      if (lane == 0) soff[0] = 0;
-    }
-    __syncthreads();
-    // ... then every entry: its block (turned to multiply the neighbour's
-    // vector) and neighbour, or where to find them
-    for (int a = warp; a < nr; a += kPcgWarps) {
-      const int i = t + Gs * a;
-      const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
-      for (int k = lane; k < len; k += 32) {
-        const int2 ent = __ldg(d.rl_ent + r0 + k);
-        const int e = e0 + k;
-        if constexpr (kMode == kSpmvSmemA) {
-          const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
-          const bool tr = ent.x < 0;
-          sj[e] = ent.y;
-#pragma unroll
-          for (int q = 0; q < 36; ++q) {
-            const int dst = tr ? (q % 6) * 6 + q / 6 : q;
-            sA[(size_t)dst * ent_cap + e] = __ldg(B + q);
-          }
-        } else {
-          sent[e] = ent;
-        }
-      }
-    }
-  }
-  if (!stream_reduce<kTagged>(pa, 32, d.part, t, Gs, base + 1, spin_limit, [&](Acc rz) {
+  if (broken) pa = acc_nan<Acc>();   // reaches every CTA through the first reduction
+  if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff);
+  if (!stream_reduce_fenced(pa, 32, d.part, t, Gs, base + 1, spin_limit, [&](Acc rz) {
         sc.rz = rz;
         sc.bad = acc_is_nan(rz);
         sc.work = !sc.bad && O::nonzero(rz);
@@ -651,63 +600,27 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
 
   for (int k = 0; k < K; ++k) {
     const bool work = sc.work;
-    const Real beta = sc.beta;
-    const auto* pold = (k & 1) ? P.X.p0 : P.X.p1;
-    auto* pnew = (k & 1) ? P.X.p1 : P.X.p0;
-    const unsigned tp = (unsigned)(base + 1 + 2 * k);      // p of this iteration (tagged exchange)
-    const auto* pcur = (k & 1) ? P.X.p1 : P.X.p0;
-    // a tagged value is written before its writer publishes the reduction
-    // that this CTA has already seen, so it arrives within the L2 latency
-    const int data_spins = spin_limit >> 6;
-    bool late = false;
-    // ---- q = A p with p = z + β p_old, and the shares of pᵀq (lanes 0-5)
+    const double beta = sc.beta;
+    const double* __restrict__ pold = pbuf[(k + 1) & 1];
+    double* __restrict__ pnew = pbuf[k & 1];
+    // ---- q = A p with the neighbour's p = z + β p_old, and the shares of pᵀq (lanes 0-5)
     pa = O::zero();
     if (work) {
       if constexpr (kStaged) {
-        // a thread per entry of the CTA's rows: its 6x6 block times the
-        // neighbour's p, six outputs to shared memory ...
         const int ne = soff[nr];
         for (int e = tid; e < ne; e += kPcgThreads) {
-          Real p[6];
-          if constexpr (kMode == kSpmvSmemA) {
-            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, sj[e], p, data_spins);
+          const int2 ent = kMode == kSpmvSmemA ? make_int2(0, sj[e]) : sent[e];
+          double p[6], out[6];
+          get_p64(gz, pold, k > 0, beta, ent.y, p);
+          entry_product<kMode>(A, sA, ent_cap, e, ent, p, out);
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-              Real u = 0;
-#pragma unroll
-              for (int q = 0; q < 6; ++q) u += sA[(size_t)(6 * b + q) * ent_cap + e] * p[q];
-              sOut[(size_t)b * ent_cap + e] = u;
-            }
-          } else {
-            const int2 ent = sent[e];
-            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, ent.y, p, data_spins);
-            const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
-            Real out[6] = {0, 0, 0, 0, 0, 0};
-            const bool tr = ent.x < 0;
-#pragma unroll
-            for (int b = 0; b < 6; ++b) {
-              Real row[6];
-              load6_ro(B + 6 * b, row);
-              if (!tr) {
-                Real u = 0;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) u += row[q] * p[q];
-                out[b] = u;
-              } else {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) out[q] += p[b] * row[q];
-              }
-            }
-#pragma unroll
-            for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
-          }
+          for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
         }
         __syncthreads();
       }
-      // ... then a warp per row sums its entries
       for (int a = warp; a < nr; a += kPcgWarps) {
         const int i = t + Gs * a;
-        Real acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc[6] = {0, 0, 0, 0, 0, 0};
         if constexpr (kStaged) {
           const int e1 = soff[a + 1];
           for (int e = soff[a] + lane; e < e1; e += 32) {
@@ -718,67 +631,45 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
           const int e1 = __ldg(d.rl_ptr + i + 1);
           for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
             const int2 ent = __ldg(d.rl_ent + e);
-            const Real* B = P.A + (size_t)(ent.x & 0x7fffffff) * 36;
-            Real p[6];
-            late |= !fetch_p(P.X, pcur, pold, tp, k > 0, beta, ent.y, p, data_spins);
-            const bool tr = ent.x < 0;
+            double p[6], out[6];
+            get_p64(gz, pold, k > 0, beta, ent.y, p);
+            entry_product<kSpmvRows>(A, sA, ent_cap, e, ent, p, out);
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-              Real row[6];
-              load6_ro(B + 6 * b, row);
-              if (!tr) {
-                Real u = 0;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) u += row[q] * p[q];
-                acc[b] += u;
-              } else {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) acc[q] += p[b] * row[q];
-              }
-            }
+            for (int b = 0; b < 6; ++b) acc[b] += out[b];
           }
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[c] = warp_sum_r(acc[c]);
         if (lane < 6) {
-          Real qc = acc[0];
+          double qc = acc[0];
 #pragma unroll
           for (int c = 1; c < 6; ++c)
             if (lane == c) qc = acc[c];
-          Real pc;
-          if constexpr (kTagged) {   // formed and published after the last reduction
-            pc = V(kP, a)[lane];
-          } else {
-            pc = k == 0 ? V(kZ, a)[lane] : V(kZ, a)[lane] + beta * V(kP, a)[lane];
-            V(kP, a)[lane] = pc;
-            P.X.put(pnew, 6 * (size_t)i + lane, pc, 0u);
-          }
+          const double pc = k == 0 ? V(kZ, a)[lane] : V(kZ, a)[lane] + beta * V(kP, a)[lane];
+          V(kP, a)[lane] = pc;
           V(kQ, a)[lane] = qc;
+          pnew[6 * (size_t)i + lane] = pc;
           pa = O::add(pa, O::prod(pc, qc));
         }
       }
     }
-    if (late) {   // every CTA stops iterating; the host gets a timeout
-      s_late = 1;
-      pa = acc_nan<Acc>();
-    }
-    if (!stream_reduce<kTagged>(pa, 8, d.part, t, Gs, base + 2 + 2 * k, spin_limit, [&](Acc pq) {
+    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 2 + 2 * k, spin_limit, [&](Acc pq) {
           if (!sc.work) return;
-          if (!acc_positive(pq)) {   // pᵀAp <= 0: nothing moves from here on
+          if (!(pq > 0.0)) {   // pᵀAp <= 0: nothing moves from here on
             sc.bad = 1;
             sc.work = 0;
             atomicOr(d.status, kStatusBreakdown);
             return;
           }
-          sc.alpha = acc_ratio<Real, Acc>(sc.rz, pq);
+          sc.alpha = sc.rz / pq;
         })) {
       atomicOr(d.status, kStatusTimeout);
       return;
     }
-    // ---- x += α p, r −= α q, z = M⁻¹ r, and the shares of rᵀz (lanes 0-5)
+    // ---- x += α p, r −= α q, z = M⁻¹ r (published), and the shares of rᵀz (lanes 0-5)
     pa = O::zero();
     if (sc.work) {
-      const Real alpha = sc.alpha;
+      const double alpha = sc.alpha;
       for (int a = warp; a < nr; a += kPcgWarps) {
         if (lane < 6) {
           V(kX, a)[lane] += alpha * V(kP, a)[lane];
@@ -786,68 +677,44 @@ k_pcg(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
         }
         __syncwarp();
         if (lane < 6) {
-          const Real* mi = sMi + 21 * a;
-          const Real* r = V(kR, a);
-          Real z = 0;
+          const double* mi = sMi + 21 * a;
+          const double* r = V(kR, a);
+          double z = 0;
 #pragma unroll
           for (int c = 0; c < 6; ++c) z += mi[sym(lane, c)] * r[c];
           V(kZ, a)[lane] = z;
-          if constexpr (!kTagged) P.X.put(P.X.z, 6 * (size_t)(t + Gs * a) + lane, z, 0u);
+          gz[6 * (size_t)(t + Gs * a) + lane] = z;
           pa = O::add(pa, O::prod(r[lane], z));
         }
+        __syncwarp();
       }
     }
-    if (!stream_reduce<kTagged>(pa, 8, d.part, t, Gs, base + 3 + 2 * k, spin_limit, [&](Acc rz) {
+    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 3 + 2 * k, spin_limit, [&](Acc rz) {
           if (!sc.work) return;
-          sc.beta = acc_ratio<Real, Acc>(rz, sc.rz);
+          sc.beta = rz / sc.rz;
           sc.rz = rz;
           sc.work = O::nonzero(rz);
         })) {
       atomicOr(d.status, kStatusTimeout);
       return;
     }
-    if constexpr (kTagged) {   // p of the next iteration, published for the rows' readers
-      if (sc.work && k + 1 < K) {
-        const Real beta_n = sc.beta;
-        const unsigned tag = (unsigned)(base + 3 + 2 * k);
-        auto* pnext = (k & 1) ? P.X.p0 : P.X.p1;
-        for (int a = warp; a < nr; a += kPcgWarps)
-          if (lane < 6) {
-            const Real pc = V(kZ, a)[lane] + beta_n * V(kP, a)[lane];
-            V(kP, a)[lane] = pc;
-            P.X.put(pnext, 6 * (size_t)(t + Gs * a) + lane, pc, tag);
-          }
-      }
-    }
   }
-  if (tid == 0 && s_late) atomicOr(d.status, kStatusTimeout);
-  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = O::value(sc.rz);
+  if (t == 0 && tid == 0) d.pcg_rz[gn_it] = sc.rz;
 
-  // ---- T_j ← Δ_j T_j (nothing moves after a breakdown)
+  // ---- T_j ← Δ_j T_j in FP64 (nothing moves after a breakdown); the FP32 copy follows
   if (sc.bad) return;
   for (int a = tid; a < nr; a += kPcgThreads) {
     const int j = t + Gs * a;
-    const Real* x = V(kX, a);
-    if constexpr (std::is_same<Real, float>::value) {
-      float xi[6];
+    double xi[6], q[8];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) xi[c] = x[c];
-      float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
-      apply_increment(q0, qe, xi);
-      d.dq[2 * j] = q0;
-      d.dq[2 * j + 1] = qe;
-    } else {
-      double xi[6], q[8];
+    for (int c = 0; c < 6; ++c) xi[c] = V(kX, a)[c];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) xi[c] = x[c];
+    for (int c = 0; c < 8; ++c) q[c] = d.dq64[8 * j + c];
+    apply_increment64(q, xi);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) q[c] = d.dq64[8 * j + c];
-      apply_increment64(q, xi);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) d.dq64[8 * j + c] = q[c];
-      d.dq[2 * j] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-      d.dq[2 * j + 1] = make_float4((float)q[4], (float)q[5], (float)q[6], (float)q[7]);
-    }
+    for (int c = 0; c < 8; ++c) d.dq64[8 * j + c] = q[c];
+    d.dq[2 * j] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+    d.dq[2 * j + 1] = make_float4((float)q[4], (float)q[5], (float)q[6], (float)q[7]);
   }
 }
 
@@ -925,49 +792,10 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
       V(kGx, a)[c] = 0;
       V(kGp, a)[c] = 0;
       V(kGs, a)[c] = 0;
-      Xchg<float>::put(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
+      put_tagged(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
     }
   }
-  if constexpr (kStaged) {
-    if (warp == 0) {   // the rows' entry offsets: an exclusive scan of the row lengths
-      int run = 0;
-      for (int a0 = 0; a0 < nr; a0 += 32) {
-        const int a = a0 + lane;
-        const int i = t + Gs * a;
-        const int len = a < nr ? __ldg(d.rl_ptr + i + 1) - __ldg(d.rl_ptr + i) : 0;
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += u;
-        }
-        if (a < nr) soff[a + 1] = run + incl;
-        run += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      if (lane == 0) soff[0] = 0;
-    }
-    __syncthreads();
-    for (int a = warp; a < nr; a += kPcgWarps) {   // every entry's block (turned) and neighbour
-      const int i = t + Gs * a;
-      const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
-      for (int k = lane; k < len; k += 32) {
-        const int2 ent = __ldg(d.rl_ent + r0 + k);
-        const int e = e0 + k;
-        if constexpr (kMode == kSpmvSmemA) {
-          const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
-          const bool tr = ent.x < 0;
-          sj[e] = ent.y;
-#pragma unroll
-          for (int q = 0; q < 36; ++q) {
-            const int dst = tr ? (q % 6) * 6 + q / 6 : q;
-            sA[(size_t)dst * ent_cap + e] = __ldg(B + q);
-          }
-        } else {
-          sent[e] = ent;
-        }
-      }
-    }
-  }
+  if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff);
   if (tid == 0) {
     sc.alpha = 0; sc.beta = 0; sc.rz = O::zero(); sc.bad = 0; sc.work = 1;
     s_gprev = O::zero(); s_aprev = 1.f;
@@ -989,39 +817,12 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
     if (spmv && kStaged) {
       const int ne = soff[nr];
       for (int e = tid; e < ne; e += kPcgThreads) {
-        Real p[6];
-        if constexpr (kMode == kSpmvSmemA) {
-          late |= !Xchg<float>::get6(ucur, sj[e], tu, p, data_spins);
+        const int2 ent = kMode == kSpmvSmemA ? make_int2(0, sj[e]) : sent[e];
+        Real p[6], out[6];
+        late |= !get6_tagged(ucur, ent.y, tu, p, data_spins);
+        entry_product<kMode>(A, sA, ent_cap, e, ent, p, out);
 #pragma unroll
-          for (int b = 0; b < 6; ++b) {
-            Real v = 0;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v += sA[(size_t)(6 * b + q) * ent_cap + e] * p[q];
-            sOut[(size_t)b * ent_cap + e] = v;
-          }
-        } else {
-          const int2 ent = sent[e];
-          late |= !Xchg<float>::get6(ucur, ent.y, tu, p, data_spins);
-          const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
-          Real out[6] = {0, 0, 0, 0, 0, 0};
-          const bool tr = ent.x < 0;
-#pragma unroll
-          for (int b = 0; b < 6; ++b) {
-            Real row[6];
-            load6_ro(B + 6 * b, row);
-            if (!tr) {
-              Real v = 0;
-#pragma unroll
-              for (int q = 0; q < 6; ++q) v += row[q] * p[q];
-              out[b] = v;
-            } else {
-#pragma unroll
-              for (int q = 0; q < 6; ++q) out[q] += p[b] * row[q];
-            }
-          }
-#pragma unroll
-          for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
-        }
+        for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
       }
       __syncthreads();
     }
@@ -1039,24 +840,11 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
           const int e1 = __ldg(d.rl_ptr + i + 1);
           for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
             const int2 ent = __ldg(d.rl_ent + e);
-            const float* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
-            Real p[6];
-            late |= !Xchg<float>::get6(ucur, ent.y, tu, p, data_spins);
-            const bool tr = ent.x < 0;
+            Real p[6], out[6];
+            late |= !get6_tagged(ucur, ent.y, tu, p, data_spins);
+            entry_product<kSpmvRows>(A, sA, ent_cap, e, ent, p, out);
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-              Real row[6];
-              load6_ro(B + 6 * b, row);
-              if (!tr) {
-                Real v = 0;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) v += row[q] * p[q];
-                acc[b] += v;
-              } else {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) acc[q] += p[b] * row[q];
-              }
-            }
+            for (int b = 0; b < 6; ++b) acc[b] += out[b];
           }
         }
 #pragma unroll
@@ -1150,7 +938,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
 #pragma unroll
           for (int c = 0; c < 6; ++c) u += mi[sym(lane, c)] * r[c];
           V(kGu, a)[lane] = u;
-          Xchg<float>::put(unext, 6 * (size_t)(t + Gs * a) + lane, u, tn);
+          put_tagged(unext, 6 * (size_t)(t + Gs * a) + lane, u, tn);
         }
         __syncwarp();
       }
@@ -1223,9 +1011,9 @@ const void* pcg_kernel(int precision, int mode) {
   switch (precision) {
     case SW_PRECISION_FP64:
       switch (mode) {
-        case kSpmvSmemA: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvSmemA>);
-        case kSpmvSmemOut: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvSmemOut>);
-        default: return reinterpret_cast<const void*>(k_pcg<double, double, kSpmvRows>);
+        case kSpmvSmemA: return reinterpret_cast<const void*>(k_pcg_f64<kSpmvSmemA>);
+        case kSpmvSmemOut: return reinterpret_cast<const void*>(k_pcg_f64<kSpmvSmemOut>);
+        default: return reinterpret_cast<const void*>(k_pcg_f64<kSpmvRows>);
       }
     case SW_PRECISION_MIXED_F64DOTS: return pcg_gear_fn<double>(mode);
     default: return pcg_gear_fn<DF>(mode);

@@ -16,32 +16,11 @@
 //   (K7+K8, the PCG and the node update, are in k_pcg.cu.)
 #include "sw_internal.h"
 #include "sw_math.cuh"
+#include "sw_assoc.cuh"
 
 namespace sw {
 
 // ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ bool surfel_selected(const SwDev& d, int t_now, float conf, int t_obs) {
-  return conf > d.stable_conf || (t_now - t_obs) <= d.recent_frames;
-}
-
-// Projective association of one warped surfel (Sec. 7); -1 if rejected.
-// Every test is an exact-order FP32 expression (see sw_math.cuh).
-__device__ __forceinline__ int associate_one(const SwDev& d, float3 vl, float3 nl) {
-  if (!(vl.z > 0.f)) return -1;
-  const float u = project_rn(d.fx, vl.x, vl.z, d.cx);
-  const float v = project_rn(d.fy, vl.y, vl.z, d.cy);
-  const float px = floorf(__fadd_rn(u, 0.5f)), py = floorf(__fadd_rn(v, 0.5f));
-  if (!(px >= 0.f && px < (float)d.W && py >= 0.f && py < (float)d.H)) return -1;
-  const int pix = (int)py * d.W + (int)px;
-  const float4 V = d.vmap[pix];
-  if (!(V.w > 0.f)) return -1;
-  const float4 N = d.nmap[pix];
-  const float d2 = dist2_rn(vl.x, vl.y, vl.z, V.x, V.y, V.z);
-  if (!(d2 < __fmul_rn(d.corr_dist, d.corr_dist))) return -1;
-  if (!(dot_rn(nl, f3(N)) > d.corr_normal)) return -1;
-  return pix;
-}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

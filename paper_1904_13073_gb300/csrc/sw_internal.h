@@ -147,6 +147,9 @@ void launch_solve_begin(const BatchHost& b, cudaStream_t st);
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
 cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
+void launch_reg_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
+void launch_data_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
+void launch_dq_widen(const SwDev& d, cudaStream_t st);
 void launch_warp_live(const BatchHost& b, cudaStream_t st);
 void launch_index_map(const BatchHost& b, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);

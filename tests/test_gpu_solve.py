@@ -34,7 +34,7 @@ def _compare_nodes(p):
     return float(rot.max()), float(trans.max())
 
 
-@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_MIXED_F64DOTS])
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_MIXED_F64DOTS, sw.SW_PRECISION_FP64])
 def test_plain_tiny_solve_matches_oracle(precision):
     """160x120 wavy surface, 64 nodes, 5 GN x 10 PCG, in each solve precision."""
     scene = synth.plain_tiny(seed=0)
@@ -53,6 +53,30 @@ def test_plain_tiny_solve_matches_oracle(precision):
         assert st["e_depth"][-1] < 0.25 * st["e_depth"][0]
     finally:
         p.close()
+
+
+def test_fp64_variant_matches_oracle_closely():
+    """The all-FP64 solve against the FP64 oracle on identical FP32 depth
+    maps: what remains is the FP32 storage of the surfels, the skinning
+    weights and the maps, so the agreement is far inside the FP32 modes'
+    1e-4 rad / 1e-5 m."""
+    scene = synth.plain_tiny(seed=0)
+    errs = {}
+    for prec in (sw.SW_PRECISION_MIXED, sw.SW_PRECISION_FP64):
+        p = Pair(scene, precision=prec)
+        try:
+            p.upload(1)
+            p.set_maps_from_oracle()
+            st = sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
+            ost = p.o.solve_frame(scene.gn_iters, scene.pcg_iters)
+            assert [st["n_corr"][k] for k in range(scene.gn_iters)] == [o.n_corr for o in ost]
+            errs[prec] = _compare_nodes(p)
+        finally:
+            p.close()
+    rot64, trans64 = errs[sw.SW_PRECISION_FP64]
+    assert rot64 <= 1e-6 and trans64 <= 1e-7, errs
+    rot32, trans32 = errs[sw.SW_PRECISION_MIXED]
+    assert rot64 <= rot32 and trans64 <= trans32, errs
 
 
 def test_small_sequence_solve_and_fuse_matches_oracle():
