@@ -298,6 +298,77 @@ sw_status sw_fusion_targets_static(const float* v_live4, const float* n_live4, i
                                    float fx, float fy, float cx, float cy, float fuse_dist,
                                    float fuse_normal, int* target, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over many independent streams with continuous
+ * batching.  Addition with no counterpart in the paper (one camera there).
+ *
+ * One worker thread per server owns the GPU.  Streams are opened with their
+ * parameters and model and wait for admission until their device state fits
+ * the memory budget (sw_server_create sets the process-wide budget of
+ * sw_set_memory_budget); admitted streams keep their surfels, node graph and
+ * warp field resident on the device.  Each worker step takes the oldest
+ * queued frame of every admitted stream that has one and runs depth
+ * processing, the Gauss-Newton solve (gn_iters x pcg_iters) and fusion for
+ * all of them in one batch; frames submitted while a step runs join the next.
+ * Streams leave with sw_server_close once their queued frames are done.
+ * The server's streams are used only through these calls.
+ * ------------------------------------------------------------------------- */
+typedef struct sw_server* sw_server_handle;
+
+/* One completed frame.  Times are milliseconds on the server's host clock
+ * (steady, from sw_server_create). */
+typedef struct {
+  int stream;          /* id from sw_server_open */
+  int frame_id;
+  int status;          /* sw_status of the frame's work */
+  int batch_size;      /* frames processed in the same step */
+  double submit_ms;    /* sw_server_submit took the frame */
+  double start_ms;     /* its step began */
+  double done_ms;      /* its fusion had finished on the device */
+} sw_frame_result;
+
+typedef struct {
+  int admitted;             /* streams on the device */
+  int waiting;              /* opened, waiting for memory */
+  long long steps;          /* worker steps with at least one frame */
+  long long frames;         /* frames completed */
+  double busy_ms;           /* time spent in steps */
+  size_t memory_in_use;     /* bytes held by all streams */
+} sw_server_stats;
+
+/* Start a server.  memory_budget: bytes for all streams (0 = unlimited);
+ * queue_depth: frames a stream may have queued (1..64), each in a pinned
+ * host slot.  SW_ERR_INVALID_ARG for out-of-range counts. */
+sw_status sw_server_create(size_t memory_budget, int gn_iters, int pcg_iters, int queue_depth,
+                           sw_server_handle* out);
+/* Stop the worker (after its current step) and release every stream. */
+sw_status sw_server_destroy(sw_server_handle s);
+/* Open a stream: p and the model as for sw_create_stream / sw_set_model
+ * (copied; t2 may be NULL = all zero).  *stream_id is valid at once; frames
+ * can be submitted once sw_server_is_admitted reports 1. */
+sw_status sw_server_open(sw_server_handle s, const sw_params* p, const float* v4, const float* n4, const int* t2,
+                         int n_s, const float* node4, int n_n, int* stream_id);
+/* Close a stream: it leaves after its queued frames (or at once if waiting). */
+sw_status sw_server_close(sw_server_handle s, int stream_id);
+/* 1 in *admitted once the stream's state is on the device. */
+sw_status sw_server_is_admitted(sw_server_handle s, int stream_id, int* admitted);
+/* Queue one depth frame (host memory, width*height floats, copied before the
+ * call returns).  SW_ERR_NOT_INITIALIZED while the stream waits for
+ * admission, SW_ERR_NO_MEMORY when its queue is full, SW_ERR_INVALID_ARG for
+ * an unknown or closing stream. */
+sw_status sw_server_submit(sw_server_handle s, int stream_id, const float* depth, int frame_id);
+/* Move up to cap completed frames (oldest first) into out; *n_out = count. */
+sw_status sw_server_poll(sw_server_handle s, sw_frame_result* out, int cap, int* n_out);
+/* Wait until every submitted frame has completed (SW_ERR_TIMEOUT after timeout_ms). */
+sw_status sw_server_wait(sw_server_handle s, int timeout_ms);
+/* A stream's node positions and transforms, as sw_read_nodes. */
+sw_status sw_server_read_nodes(sw_server_handle s, int stream_id, float* pos4, float* dq8, int cap, int* n_out);
+/* Batching window: a step with frames of only some admitted streams waits up
+ * to window_ms (0..1000) after its oldest frame arrived for the others'
+ * frames (0 = start at once, the default). */
+sw_status sw_server_set_batch_window(sw_server_handle s, double window_ms);
+sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
+
 /* Reason of the last error on this handle ("" if none); NULL handle: the last
  * process-wide error (e.g. of sw_create_stream). */
 const char* sw_last_error(sw_handle h);

@@ -52,6 +52,23 @@ class sw_solve_stats(ctypes.Structure):
                 "n_corr": list(self.n_corr[:n]), "pcg_rz": list(self.pcg_rz[:n])}
 
 
+class sw_frame_result(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_int), ("frame_id", ctypes.c_int), ("status", ctypes.c_int),
+                ("batch_size", ctypes.c_int), ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class sw_server_stats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int), ("waiting", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("frames", ctypes.c_longlong), ("busy_ms", ctypes.c_double), ("memory_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -95,6 +112,17 @@ _SIGS = {
     "sw_batch_set_profiling": [_P, _I],
     "sw_batch_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "sw_debug_barrier_timeout": [_I, ctypes.POINTER(_I)],
+    "sw_server_create": [ctypes.c_size_t, _I, _I, _I, ctypes.POINTER(_P)],
+    "sw_server_destroy": [_P],
+    "sw_server_open": [_P, ctypes.POINTER(sw_params), _P, _P, _P, _I, _P, _I, ctypes.POINTER(_I)],
+    "sw_server_close": [_P, _I],
+    "sw_server_is_admitted": [_P, _I, ctypes.POINTER(_I)],
+    "sw_server_submit": [_P, _I, _P, _I],
+    "sw_server_poll": [_P, ctypes.POINTER(sw_frame_result), _I, ctypes.POINTER(_I)],
+    "sw_server_wait": [_P, _I],
+    "sw_server_read_nodes": [_P, _I, _P, _P, _I, ctypes.POINTER(_I)],
+    "sw_server_read_stats": [_P, ctypes.POINTER(sw_server_stats)],
+    "sw_server_set_batch_window": [_P, ctypes.c_double],
 }
 
 PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion")
@@ -461,3 +489,80 @@ def model_arrays(scene):
     """(v4, n4, t2, node4) of a synth.Scene in the library's layout."""
     return (_pad4(scene.surfel_v, scene.surfel_r), _pad4(scene.surfel_n, scene.surfel_c),
             np.ascontiguousarray(scene.surfel_t, dtype=np.int32), _pad4(scene.node_p, scene.node_sigma))
+
+
+# ---------------------------------------------------------------- serving
+
+def sw_server_create(memory_budget, gn_iters, pcg_iters, queue_depth=4):
+    out = ctypes.c_void_p()
+    _check(lib().sw_server_create(int(memory_budget), gn_iters, pcg_iters, queue_depth, ctypes.byref(out)))
+    return out.value
+
+
+def sw_server_destroy(srv):
+    _check(lib().sw_server_destroy(srv))
+
+
+def sw_server_open(srv, params, v4, n4, t2, node4):
+    """Open a stream on the server; returns its id (admission happens later)."""
+    v4 = np.ascontiguousarray(v4, np.float32)
+    n4 = np.ascontiguousarray(n4, np.float32)
+    node4 = np.ascontiguousarray(node4, np.float32)
+    t2p = None
+    if t2 is not None:
+        t2 = np.ascontiguousarray(t2, np.int32)
+        t2p = t2.ctypes.data_as(_P)
+    sid = ctypes.c_int()
+    _check(lib().sw_server_open(srv, ctypes.byref(params), v4.ctypes.data_as(_P), n4.ctypes.data_as(_P), t2p,
+                                len(v4), node4.ctypes.data_as(_P), len(node4), ctypes.byref(sid)))
+    return sid.value
+
+
+def sw_server_close(srv, stream_id):
+    _check(lib().sw_server_close(srv, stream_id))
+
+
+def sw_server_is_admitted(srv, stream_id):
+    a = ctypes.c_int()
+    _check(lib().sw_server_is_admitted(srv, stream_id, ctypes.byref(a)))
+    return bool(a.value)
+
+
+def sw_server_submit(srv, stream_id, depth, frame_id):
+    """Queue a frame; returns the sw_status (0 = queued, 2 = queue full,
+    3 = not admitted yet) instead of raising for those two."""
+    d = np.ascontiguousarray(depth, np.float32)
+    st = lib().sw_server_submit(srv, stream_id, d.ctypes.data_as(_P), frame_id)
+    if st not in (0, 2, 3):
+        _check(st)
+    return st
+
+
+def sw_server_poll(srv, cap=4096):
+    buf = (sw_frame_result * cap)()
+    n = ctypes.c_int()
+    _check(lib().sw_server_poll(srv, buf, cap, ctypes.byref(n)))
+    return [buf[k].as_dict() for k in range(n.value)]
+
+
+def sw_server_wait(srv, timeout_ms):
+    return lib().sw_server_wait(srv, int(timeout_ms)) == 0
+
+
+def sw_server_read_nodes(srv, stream_id, n_nodes):
+    pos = np.empty((n_nodes, 4), np.float32)
+    dq = np.empty((n_nodes, 8), np.float32)
+    cnt = ctypes.c_int()
+    _check(lib().sw_server_read_nodes(srv, stream_id, pos.ctypes.data_as(_P), dq.ctypes.data_as(_P), n_nodes,
+                                      ctypes.byref(cnt)))
+    return pos[:cnt.value], dq[:cnt.value]
+
+
+def sw_server_set_batch_window(srv, window_ms):
+    _check(lib().sw_server_set_batch_window(srv, float(window_ms)))
+
+
+def sw_server_read_stats(srv):
+    st = sw_server_stats()
+    _check(lib().sw_server_read_stats(srv, ctypes.byref(st)))
+    return st.as_dict()

@@ -1377,6 +1377,22 @@ sw_status sw_batch_fuse(sw_batch_handle b) {
   return SW_OK;
 }
 
+namespace sw {
+sw_status batch_member_status(sw_batch_handle b, int* status) {
+  if (!b || !status) return SW_ERR_INVALID_ARG;
+  Runner* r = &b->run;
+  const int n = (int)r->members.size();
+  std::vector<int> raw(n, 0);
+  for (int i = 0; i < n; ++i)
+    if (r->active_host[i])
+      SW_CUDA(nullptr, cudaMemcpyAsync(&raw[i], r->members[i]->h.status, sizeof(int), cudaMemcpyDeviceToHost, r->st));
+  SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
+  for (int i = 0; i < n; ++i)
+    status[i] = (raw[i] & kStatusTimeout) ? SW_ERR_TIMEOUT : (raw[i] & kStatusBreakdown) ? SW_ERR_SOLVER_BREAKDOWN : SW_OK;
+  return SW_OK;
+}
+}  // namespace sw
+
 sw_status sw_set_profiling(sw_handle s, int enable) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   SW_CUDA(s, cudaStreamSynchronize(s->st));

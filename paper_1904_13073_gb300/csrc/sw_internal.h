@@ -157,6 +157,9 @@ void launch_associate_only(const BatchHost& b, cudaStream_t st);
 int pcg_blocks_per_sm(int precision);
 int pcg_threads();
 size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
+// Wait for a batch's work and turn each member's device status word into
+// its sw_status (SW_OK for inactive members); `status` has one entry per member.
+sw_status batch_member_status(sw_batch_handle b, int* status);
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
                                  int* status, cudaStream_t st);
 

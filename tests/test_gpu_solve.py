@@ -214,3 +214,42 @@ def test_checkpoint_resume_gives_identical_next_frame():
     finally:
         sw.sw_destroy_stream(a)
         sw.sw_destroy_stream(b)
+
+
+def test_precision_report():
+    """The precision configuration: the 160x120 frame solved in each mode
+    against the FP64 oracle (max node rotation / translation error, and the
+    point-to-plane RMS at the last Gauss-Newton linearisation).  Writes
+    precision_report.json to $SW_REPORT_DIR when that is set."""
+    import json
+    import os
+    scene = synth.plain_tiny(seed=0)
+    names = {sw.SW_PRECISION_MIXED: "fp32_assembly_doublefloat_dots",
+             sw.SW_PRECISION_MIXED_F64DOTS: "fp32_assembly_fp64_dots",
+             sw.SW_PRECISION_FP64: "fp64"}
+    report, oracle_rms = {}, None
+    for prec, name in names.items():
+        p = Pair(scene, precision=prec)
+        try:
+            p.upload(1)
+            st = sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
+            if oracle_rms is None:
+                ost = p.o.solve_frame(scene.gn_iters, scene.pcg_iters)
+                oracle_rms = float(np.sqrt(ost[-1].e_depth / ost[-1].n_corr))
+                ora_dq = p.o.node_dq.copy()
+            else:
+                p.o.node_dq = ora_dq.copy()
+            rot, trans = _compare_nodes(p)
+            last = scene.gn_iters - 1
+            report[name] = {"max_rot_err_rad": rot, "max_trans_err_m": trans,
+                            "rms_last_gn_m": float(np.sqrt(st["e_depth"][last] / st["n_corr"][last]))}
+            assert rot <= ROT_TOL and trans <= TRANS_TOL, (name, rot, trans)
+        finally:
+            p.close()
+    report["oracle_rms_last_gn_m"] = oracle_rms
+    out = os.environ.get("SW_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_report.json"), "w") as f:
+            json.dump(report, f, indent=1)
+    assert report["fp64"]["max_rot_err_rad"] <= report["fp32_assembly_doublefloat_dots"]["max_rot_err_rad"]
