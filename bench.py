@@ -217,6 +217,121 @@ def _batch_member_data(args):
                "gn": s.gn_iters, "pcg": s.pcg_iters}
 
 
+def _large_member_data(args):
+    """A large stream of the serving workload: 640x480 sphere, 4096 nodes."""
+    seed, frame_ids = args
+    import synth
+    from paper_1904_13073_gb300 import model_arrays
+    s = synth.plain_full(seed=100 + seed, n_nodes=4096)
+    c = s.cam
+    return seed, {"name": f"sphere_640x480_{len(s.surfel_v)}s_{len(s.node_p)}n_large",
+                  "cam": (c.width, c.height, c.fx, c.fy, c.cx, c.cy),
+                  "arrays": model_arrays(s), "frames": [s.frame(t) for t in frame_ids],
+                  "gn": s.gn_iters, "pcg": s.pcg_iters}
+
+
+def large_workload(n_models, frame_ids):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=max(1, min(os.cpu_count() or 4, n_models))) as pool:
+        out = dict(pool.map(_large_member_data, [(k, frame_ids) for k in range(n_models)]))
+    return [out[k] for k in range(n_models)]
+
+
+def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_gb, gn, pcg, seed=0):
+    """The serving workload: n_regular streams of the uneven sizes (models
+    reused from the uneven batch) plus n_large large ones, each submitting
+    depth frames as a Poisson process of rate_hz; an eighth of the regular
+    streams joins a third into the run and another eighth leaves at two
+    thirds.  Frames go through the library's server (admission against the
+    budget, continuous batching); latency is completion minus submission on
+    the server's clock.  A frame refused because its stream's queue is full
+    (or not admitted yet) is counted as dropped."""
+    import heapq
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    specs = [members[k % len(members)] for k in range(n_regular)] + [large[k % len(large)] for k in range(n_large)]
+    n = len(specs)
+    late = set(range(n_regular - n_regular // 8, n_regular))
+    leaving = set(range(n_regular // 8))
+    srv = sw.sw_server_create(int(budget_gb * (1 << 30)), gn, pcg, queue_depth=4)
+    ids = {}
+
+    def open_stream(k):
+        m = specs[k]
+        w, h_, fx, fy, cx, cy = m["cam"]
+        cam = SimpleNamespace(width=w, height=h_, fx=fx, fy=fy, cx=cx, cy=cy)
+        v4, n4, t2, node4 = m["arrays"]
+        ids[k] = sw.sw_server_open(srv, sw.params_for(cam, len(v4), len(node4)), v4, n4, t2, node4)
+
+    try:
+        for k in range(n):
+            if k not in late:
+                open_stream(k)
+        t_adm = time.perf_counter()
+        while not all(sw.sw_server_is_admitted(srv, ids[k]) for k in ids):
+            if time.perf_counter() - t_adm > 300:
+                raise RuntimeError("streams were not admitted")
+            time.sleep(0.01)
+        # frames: the member's depth frames back and forth
+        seqs = {k: [f for f in specs[k]["frames"]] + [f for f in specs[k]["frames"][-2:0:-1]] for k in range(n)}
+        pos = {k: 0 for k in range(n)}
+        t0 = time.perf_counter()
+        events = [(float(rng.exponential(1.0 / rate_hz)), k) for k in range(n) if k not in late]
+        heapq.heapify(events)
+        joined, left = False, False
+        sent = dropped = 0
+        while events:
+            t, k = heapq.heappop(events)
+            if t > seconds:
+                continue
+            if not joined and t >= seconds / 3:
+                for j in late:
+                    open_stream(j)
+                    heapq.heappush(events, (t + float(rng.exponential(1.0 / rate_hz)), j))
+                joined = True
+            if not left and t >= 2 * seconds / 3:
+                for j in leaving:
+                    sw.sw_server_close(srv, ids[j])
+                left = True
+            if left and k in leaving:
+                continue
+            delay = t0 + t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            seq = seqs[k]
+            st = sw.sw_server_submit(srv, ids[k], seq[pos[k] % len(seq)], 2 + pos[k])
+            if st == 0:
+                pos[k] += 1
+                sent += 1
+            else:
+                dropped += 1
+            heapq.heappush(events, (t + float(rng.exponential(1.0 / rate_hz)), k))
+        sw.sw_server_wait(srv, 120000)
+        res = []
+        while True:
+            got = sw.sw_server_poll(srv)
+            if not got:
+                break
+            res += got
+        stats = sw.sw_server_read_stats(srv)
+    finally:
+        sw.sw_server_destroy(srv)
+        sw.sw_set_memory_budget(0)
+    ok = [r for r in res if r["status"] == 0]
+    lat = np.array([r["done_ms"] - r["submit_ms"] for r in ok]) if ok else np.zeros(1)
+    span_s = (max(r["done_ms"] for r in ok) - min(r["submit_ms"] for r in ok)) / 1000.0 if ok else 1.0
+    return {"workload": f"{n_regular} streams of the uneven sizes + {n_large} large (640x480, 4096 nodes), "
+                        f"Poisson arrivals at {rate_hz:g} Hz per stream for {seconds:g} s; "
+                        f"{len(late)} join at 1/3, {len(leaving)} leave at 2/3; {gn} GN x {pcg} PCG + fusion",
+            "budget_gb": budget_gb, "frames_per_s": len(ok) / span_s, "offered_frames_per_s": rate_hz * n,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "frames_done": len(ok), "frames_failed": len(res) - len(ok), "frames_dropped": dropped,
+            "mean_batch": float(np.mean([r["batch_size"] for r in ok])) if ok else 0.0,
+            "steps": int(stats["steps"]), "gpu_busy_frac": float(stats["busy_ms"]) / 1000.0 / max(span_s, 1e-9),
+            "peak_admitted": n, "memory_gb_at_end": stats["memory_in_use"] / float(1 << 30)}
+
+
 def batch_workload(n_streams, frame_ids, scale=1.0):
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes=max(1, min(os.cpu_count() or 4, n_streams))) as pool:
@@ -327,6 +442,11 @@ def main():
     ap.add_argument("--batch-streams", type=int, default=16, help="streams of the uneven batched workload (0: skip)")
     ap.add_argument("--batch-rounds", type=int, default=5)
     ap.add_argument("--clocks-csv", default="", help="keep the nvidia-smi clock samples here ({rank} is replaced)")
+    ap.add_argument("--served-streams", type=int, default=64, help="regular streams of the serving run (0: skip)")
+    ap.add_argument("--served-large", type=int, default=8)
+    ap.add_argument("--served-seconds", type=float, default=4.0)
+    ap.add_argument("--served-rate", type=float, default=30.0)
+    ap.add_argument("--served-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -339,7 +459,9 @@ def main():
     ts = [1 + (k % (scene.n_frames - 1)) for k in range(n_frames)]
     frames = render_frames(0, sorted(set(ts)), os.cpu_count() or 4)
     frame_of = dict(zip(sorted(set(ts)), frames))
-    members = batch_workload(args.batch_streams, [2, 3, 4], 1.0) if args.batch_streams > 0 and rank == 0 else []
+    want_members = (args.batch_streams > 0 or args.served_streams > 0) and rank == 0
+    members = batch_workload(max(args.batch_streams, 16), [2, 3, 4], 1.0) if want_members else []
+    large = large_workload(2, [2, 3, 4]) if args.served_large > 0 and args.served_streams > 0 and rank == 0 else []
 
     import torch
     import paper_1904_13073_gb300 as sw
@@ -432,7 +554,11 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
     sw.sw_destroy_stream(h)
-    batched = run_batched(sw, torch, members, args.batch_rounds, 2, flush, stream) if members else None
+    batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
+        if members and args.batch_streams > 0 else None
+    served = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
+                        args.served_rate, args.served_budget_gb, gn, pcg) \
+        if members and args.served_streams > 0 else None
 
     if rank != 0:
         return
@@ -458,6 +584,8 @@ def main():
     }
     if batched:
         line["multi_stream"] = batched
+    if served:
+        line["served"] = served
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(scene, frame_of[ts[0]], gn, pcg)
     print(json.dumps(line))

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -223,8 +224,7 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     r->bh.total_tiles[k] = acc;
   }
   // PCG: one cooperative grid (every CTA resident); each stream gets its own
-  // CTAs, about one warp per block row and at most kPcgMaxCtas, scaled down
-  // in proportion when the batch asks for more CTAs than the GPU holds
+  // CTAs
   {
     const int prec = n ? devs[0].precision : SW_PRECISION_MIXED;
     for (int i = 1; i < n; ++i)
@@ -233,18 +233,25 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     const int per_sm = std::max(1, pcg_blocks_per_sm(prec));
     const int cap = sm_count() * per_sm;
     if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
+    // greedy: the next CTA goes to the stream with the most rows per CTA,
+    // which minimises the largest share (the launch ends with the slowest
+    // stream); a stream takes at most one CTA per 32 rows and kPcgMaxCtas
     const int warps = pcg_threads() / 32;
-    std::vector<int> want(n);
-    long long total_want = 0;
-    for (int i = 0; i < n; ++i) {
-      want[i] = std::max(1, std::min(kPcgMaxCtas, (devs[i].n_n + warps - 1) / warps));
-      total_want += want[i];
-    }
-    if (total_want > cap) {
-      const int left = cap - n;
-      const long long rest = total_want - n;
+    std::vector<int> want(n, 1);
+    int total = n;
+    {
+      auto limit = [&](int i) { return std::max(1, std::min(kPcgMaxCtas, (devs[i].n_n + warps - 1) / warps)); };
+      auto share = [&](int i) { return (devs[i].n_n + want[i] - 1) / want[i]; };
+      std::priority_queue<std::pair<int, int>> pq;   // (rows per CTA, stream)
       for (int i = 0; i < n; ++i)
-        want[i] = 1 + (rest > 0 ? (int)((long long)(want[i] - 1) * left / rest) : 0);
+        if (want[i] < limit(i)) pq.push({share(i), i});
+      while (total < cap && !pq.empty()) {
+        const int i = pq.top().second;
+        pq.pop();
+        ++want[i];
+        ++total;
+        if (want[i] < limit(i)) pq.push({share(i), i});
+      }
     }
     int acc = 0, rows_cap = 1;
     for (int i = 0; i < n; ++i) {
