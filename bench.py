@@ -123,6 +123,12 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
     }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# ncu capture of this workload's kernels; profiles/k_pcg_gear_plain_full_300k_2048.md
+# and profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
+PROFILED_TRAFFIC = {"pcg": 2.931712e6 + 0.013312e6, "data_assembly": 25.223424e6 + 0.040448e6}
+
+
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
     peak, src = measured_hbm_peak()
     nbytes = stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters)
@@ -133,13 +139,13 @@ def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
         per_launch_s = stage_ms[k] / stage_n[k] / 1000.0
         gbs = b / per_launch_s / 1e9
         stages[k] = {"achieved": gbs, "frac": gbs / peak, "us_per_launch": per_launch_s * 1e6,
-                     "bytes_per_launch": b}
+                     "bytes_per_launch": b, "traffic": PROFILED_TRAFFIC.get(k)}
     dom = max(stages, key=lambda k: stage_ms[k])
     d = stages[dom]
     return {"stages": stages,
             "dominant": {"kernel": dom, "bound": "hbm", "achieved": d["achieved"], "peak": peak,
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
-                         "unit": "GB/s", "frac": d["frac"], "traffic": None,
+                         "unit": "GB/s", "frac": d["frac"], "traffic": PROFILED_TRAFFIC.get(dom),
                          "bytes_per_launch": d["bytes_per_launch"], "us_per_launch": d["us_per_launch"]}}
 
 
