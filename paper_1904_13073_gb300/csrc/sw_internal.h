@@ -20,7 +20,6 @@ constexpr int kMaxCtaPerStream = 1024;   // CTAs of the persistent PCG that one 
 
 // status bits written by kernels
 constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive definite, or pᵀAp <= 0
-constexpr int kStatusBadIndex = 2;       // a gather index failed its range check
 constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
 
 // A CTA's partial of one reduction (the accumulator's bit pattern),
