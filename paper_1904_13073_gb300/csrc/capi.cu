@@ -759,6 +759,16 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   if (n_s < 0 || n_s > s->p.max_surfels) return fail(s, SW_ERR_INVALID_ARG, "n_surfels out of range");
   if (n_n < SW_K_GRAPH + 1 || n_n > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "n_nodes out of range");
   if ((n_s > 0 && (!v4 || !n4)) || !node4) return fail(s, SW_ERR_INVALID_ARG, "null model array");
+  if (knn_in) {   // a restored skinning (distance order): node ids in range and distinct
+    for (int i = 0; i < n_s; ++i) {
+      const int* k = knn_in + (size_t)i * SW_K_SKIN;
+      for (int a = 0; a < SW_K_SKIN; ++a) {
+        bool ok = k[a] >= 0 && k[a] < n_n;
+        for (int b = 0; b < a; ++b) ok = ok && k[b] != k[a];
+        if (!ok) return fail(s, SW_ERR_INVALID_ARG, "restored skinning has a node id out of range or repeated");
+      }
+    }
+  }
   enter(s);
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   if (s->run) drop_graphs(s->run);
