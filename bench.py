@@ -365,6 +365,7 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
         n_pix.append(w * h_)
     gn, pcg = members[0]["gn"], members[0]["pcg"]
     nf = len(members[0]["frames"])
+    pp = list(range(nf)) + list(range(nf - 2, 0, -1))   # the frames back and forth, no jumps
     S = len(members)
     for hd, fr in zip(handles, dev_frames):       # structure sizes and a first frame
         sw.sw_upload_depth(hd, fr[0], 1)
@@ -386,32 +387,41 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
                 lat.append(a.elapsed_time(b))
         return np.array(lat)
 
+    # both runs play the same continuous sequence from the same fresh models:
+    # round r is frame pp[r] (back and forth, no jumps) with frame id 2 + r
+    def reset_models():
+        for hd, m in zip(handles, members):
+            sw.sw_set_model(hd, *m["arrays"])
+
     def plain_round(r):
-        t = 2 + (r % nf)
         for hd, fr in zip(handles, dev_frames):
-            sw.sw_upload_depth(hd, fr[r % nf], t)
+            sw.sw_upload_depth(hd, fr[pp[r % len(pp)]], 2 + r)
             sw.sw_solve_frame(hd, gn, pcg, want_stats=False)
             sw.sw_fuse_frame(hd)
 
+    reset_models()
     lat_plain = timed(plain_round, rounds, warmup)
+    reset_models()
     b = sw.sw_batch_create(handles, stream)
 
-    def batch_round(r):
-        t = 2 + (r % nf)
-        sw.sw_batch_upload_depth(b, [fr[r % nf] for fr in dev_frames], [t] * S)
-        sw.sw_batch_solve(b, gn, pcg, want_stats=False)
+    def batch_round(r, stats=False):
+        sw.sw_batch_upload_depth(b, [fr[pp[r % len(pp)]] for fr in dev_frames], [2 + r] * S)
+        st = sw.sw_batch_solve(b, gn, pcg, want_stats=stats)
         sw.sw_batch_fuse(b)
+        return st
 
     lat_batch = timed(batch_round, rounds, warmup)
-    # live stage times of one profiled batched round, and its associations
+    # live stage times of two more profiled batched rounds, and their associations
     sw.sw_batch_set_profiling(b, True)
     prof = {}
-    for r in range(2):
-        batch_round(r)
+    n_corr_seen = [[] for _ in range(S)]
+    for r in range(warmup + rounds, warmup + rounds + 2):
+        st = batch_round(r, stats=True)
         prof = sw.sw_batch_read_profile(b)
+        for k in range(S):
+            n_corr_seen[k] += st[k]["n_corr"]
     sw.sw_batch_set_profiling(b, False)
-    stats = sw.sw_batch_solve(b, gn, pcg)
-    n_corr = [int(np.mean(st["n_corr"])) for st in stats]
+    n_corr = [int(np.mean(v)) for v in n_corr_seen]
     sw.sw_batch_destroy(b)
     for hd in handles:
         sw.sw_destroy_stream(hd)
@@ -461,8 +471,18 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     import synth
     scene = synth.plain_full(seed=0)
-    n_frames = args.warmup + args.steps
-    ts = [1 + (k % (scene.n_frames - 1)) for k in range(n_frames)]
+    # one continuous sequence for every pass (warm-up, timed, profiled, end to
+    # end), played back and forth past its last frame, so that tracking never
+    # jumps; frame ids keep counting up
+    prof_steps = min(args.steps, 8)
+    n_frames = args.warmup + args.steps + prof_steps + args.steps
+    last = scene.n_frames - 1
+    period = 2 * (last - 1)
+
+    def frame_at(k):
+        m = k % period
+        return 1 + (m if m < last else period - m)
+    ts = [frame_at(k) for k in range(n_frames)]
     frames = render_frames(0, sorted(set(ts)), os.cpu_count() or 4)
     frame_of = dict(zip(sorted(set(ts)), frames))
     want_members = (args.batch_streams > 0 or args.served_streams > 0) and rank == 0
@@ -491,14 +511,16 @@ def main():
     gn, pcg = scene.gn_iters, scene.pcg_iters
     torch.cuda.synchronize()
 
-    def step(t, host):
-        sw.sw_upload_depth(h, host_frames[t] if host else dev_frames[t], t)
-        sw.sw_solve_frame(h, gn, pcg, want_stats=False)
+    def step(k, host, stats=False):
+        t = ts[k]
+        sw.sw_upload_depth(h, host_frames[t] if host else dev_frames[t], k + 1)
+        st = sw.sw_solve_frame(h, gn, pcg, want_stats=stats)
         sw.sw_fuse_frame(h)
+        return st
 
     # warm-up (also captures the solve graph)
     for k in range(args.warmup):
-        step(ts[k], False)
+        step(k, False)
     torch.cuda.synchronize()
 
     # device-resident timed region
@@ -514,7 +536,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xff)
                 starts[k].record(stream)
-            step(ts[args.warmup + k], False)
+            step(args.warmup + k, False)
             ends[k].record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -530,20 +552,21 @@ def main():
     # stage timing, live: CUDA events recorded inside the captured solve graph
     # on the library's stream, over a second timed region of the same steps
     sw.sw_set_profiling(h, True)
-    prof_steps = min(args.steps, 8)
+    base = args.warmup + args.steps
+    n_corr_seen = []
     stage_ms = {k: 0.0 for k in sw.PROFILE_STAGES}
     stage_n = {k: 0 for k in sw.PROFILE_STAGES}
     for k in range(prof_steps):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xff)
-        step(ts[args.warmup + k], False)
+        st = step(base + k, False, stats=True)
+        n_corr_seen += st["n_corr"]
         pr = sw.sw_read_profile(h)
         for name, (t_ms, n_l) in pr.items():
             stage_ms[name] += t_ms
             stage_n[name] += n_l
     sw.sw_set_profiling(h, False)
-    stats = sw.sw_solve_frame(h, gn, pcg)   # the association count of a representative frame
-    n_corr = int(np.mean(stats["n_corr"]))
+    n_corr = int(np.mean(n_corr_seen))   # correspondences per Gauss-Newton iteration
     nnzb = sw.sw_debug_assemble(h)[0]
     roof = roofline(stage_ms, stage_n, len(v4), len(node4), nnzb, n_corr, c.width * c.height, pcg)
 
@@ -554,7 +577,7 @@ def main():
     e_lat = []
     for k in range(args.steps):
         s0 = time.perf_counter()
-        step(ts[args.warmup + k], True)
+        step(base + prof_steps + k, True)
         pos, dq = sw.sw_read_nodes(h)
         e_lat.append(time.perf_counter() - s0)
     torch.cuda.synchronize()

@@ -770,6 +770,8 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
   // ---- set-up, a thread per own row: M⁻¹, r = −g, u = M⁻¹ r (published), x = p = s = 0
   if (tid == 0) s_late = 0;
   bool broken = false;
+  // a thread per row, the rows packed into as few warps as possible: an FP64
+  // warp instruction costs the FP64 pipe the same however many lanes are active
   for (int a = tid; a < nr; a += kPcgThreads) {
     const int j = t + Gs * a;
     Real* mi = sMi + 21 * a;
@@ -817,10 +819,39 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
     if (spmv && kStaged) {
       const int ne = soff[nr];
       for (int e = tid; e < ne; e += kPcgThreads) {
-        const int2 ent = kMode == kSpmvSmemA ? make_int2(0, sj[e]) : sent[e];
         Real p[6], out[6];
-        late |= !get6_tagged(ucur, ent.y, tu, p, data_spins);
-        entry_product<kMode>(A, sA, ent_cap, e, ent, p, out);
+        if constexpr (kMode == kSpmvSmemA) {
+          late |= !get6_tagged(ucur, sj[e], tu, p, data_spins);
+          entry_product<kMode>(A, sA, ent_cap, e, make_int2(0, 0), p, out);
+        } else {
+          // the block's loads go out before the wait for u: one L2 round trip per entry
+          const int2 ent = sent[e];
+          const float4* B4 = reinterpret_cast<const float4*>(A + (size_t)(ent.x & 0x7fffffff) * 36);
+          float B[36];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            const float4 v = __ldg(B4 + q);
+            B[4 * q] = v.x; B[4 * q + 1] = v.y; B[4 * q + 2] = v.z; B[4 * q + 3] = v.w;
+          }
+          late |= !get6_tagged(ucur, ent.y, tu, p, data_spins);
+          if (ent.x >= 0) {
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+              Real v = 0;
+#pragma unroll
+              for (int q = 0; q < 6; ++q) v += B[6 * b + q] * p[q];
+              out[b] = v;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              Real v = 0;
+#pragma unroll
+              for (int b = 0; b < 6; ++b) v += B[6 * b + q] * p[b];
+              out[q] = v;
+            }
+          }
+        }
 #pragma unroll
         for (int b = 0; b < 6; ++b) sOut[(size_t)b * ent_cap + e] = out[b];
       }
@@ -921,24 +952,28 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
       const Real alpha = sc.alpha, beta = sc.beta;
       const unsigned tn = (unsigned)(base + 2 + k);
       unsigned long long* unext = ub[(k + 1) & 1];
-      for (int a = warp; a < nr; a += kPcgWarps) {
-        if (lane < 6) {
-          const Real pc = V(kGu, a)[lane] + beta * V(kGp, a)[lane];
-          const Real sc_ = V(kGw, a)[lane] + beta * V(kGs, a)[lane];
-          V(kGp, a)[lane] = pc;
-          V(kGs, a)[lane] = sc_;
-          V(kGx, a)[lane] += alpha * pc;
-          V(kGr, a)[lane] -= alpha * sc_;
+      // five rows per warp at a time, six lanes each (lanes 30 and 31 idle)
+      const int grp = lane / 6, c = lane - 6 * grp;
+      for (int a0 = warp; a0 < nr; a0 += 5 * kPcgWarps) {
+        const int a = a0 + grp * kPcgWarps;
+        const bool on = grp < 5 && a < nr;
+        if (on) {
+          const Real pc = V(kGu, a)[c] + beta * V(kGp, a)[c];
+          const Real sc_ = V(kGw, a)[c] + beta * V(kGs, a)[c];
+          V(kGp, a)[c] = pc;
+          V(kGs, a)[c] = sc_;
+          V(kGx, a)[c] += alpha * pc;
+          V(kGr, a)[c] -= alpha * sc_;
         }
         __syncwarp();
-        if (lane < 6) {
+        if (on) {
           const Real* mi = sMi + 21 * a;
           const Real* r = V(kGr, a);
           Real u = 0;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) u += mi[sym(lane, c)] * r[c];
-          V(kGu, a)[lane] = u;
-          put_tagged(unext, 6 * (size_t)(t + Gs * a) + lane, u, tn);
+          for (int k2 = 0; k2 < 6; ++k2) u += mi[sym(c, k2)] * r[k2];
+          V(kGu, a)[c] = u;
+          put_tagged(unext, 6 * (size_t)(t + Gs * a) + c, u, tn);
         }
         __syncwarp();
       }
