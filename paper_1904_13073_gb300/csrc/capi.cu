@@ -20,6 +20,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>   // CUtensorMap and its encoder's signature; the encoder itself comes from the runtime's
+                    // driver entry-point query, so the library does not link the driver library
+
 #include "sw_internal.h"
 
 using namespace sw;
@@ -569,6 +572,33 @@ sw_status sw_set_memory_budget(size_t bytes) {
 
 size_t sw_memory_in_use(void) { return g_in_use.load(); }
 
+// A TMA descriptor of a stream's depth image for k_depth_maps: 2D FP32,
+// width x height, rows width*4 bytes apart, a 40x10 box, zeros outside the
+// image.  False (plain loads) if the rows are not 16-byte aligned or the
+// encoder is unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_depth_tmap(float* depth, int width, int height, CUtensorMap* out) {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  if (!fn || width % 4 != 0 || (reinterpret_cast<uintptr_t>(depth) & 15) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+  const cuuint64_t strides[1] = {(cuuint64_t)width * sizeof(float)};
+  const cuuint32_t box[2] = {40, 10};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, depth, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out) {
   std::string why;
   if (!out) return fail(nullptr, SW_ERR_INVALID_ARG, "null output handle");
@@ -620,6 +650,19 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.status, 1); ALLOC(h.t_now, 1);
 #undef ALLOC
   if (st != SW_OK) return cleanup(st);
+  {
+    CUtensorMap tm;
+    unsigned char* dev_tm = nullptr;
+    h.depth_tmap = nullptr;
+    if (encode_depth_tmap(h.depth, h.W, h.H, &tm)) {
+      if ((st = A(s, &dev_tm, sizeof(CUtensorMap))) != SW_OK) return cleanup(st);
+      if (cudaMemcpy(dev_tm, &tm, sizeof(tm), cudaMemcpyHostToDevice) != cudaSuccess) {
+        s->err = "tensor map upload failed";
+        return cleanup(SW_ERR_CUDA);
+      }
+      h.depth_tmap = dev_tm;
+    }
+  }
   // the index map is cleared here once; fusion leaves it empty after every frame
   if (cudaMemsetAsync(h.status, 0, sizeof(int), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.t_now, 0, sizeof(int), s->st) != cudaSuccess ||

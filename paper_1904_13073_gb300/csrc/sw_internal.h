@@ -62,6 +62,7 @@ struct SwDev {
   int* in_src;
   // depth maps
   float* depth;
+  const void* depth_tmap;   // TMA descriptor (CUtensorMap) of `depth`, or null: plain loads
   float4* vmap;       // V(u) and the depth-surfel confidence (0 if unusable)
   float4* nmap;       // N(u) and the depth-surfel radius
   unsigned long long* imap;  // 4W x 4H: (z bits << 32) | caller's surfel index

@@ -62,6 +62,26 @@ def test_depth_maps(which, tiny, small):
         p.close()
 
 
+def test_depth_maps_without_tensor_map_path():
+    """A width that is not a multiple of 4 (rows not 16-byte aligned) takes the
+    plain-load staging instead of the TMA copy; same maps."""
+    scene = synth.random_scene(seed=11, n_surfels=2000, n_nodes=30, width=162, height=98, f=130.0)
+    c = scene.cam
+    p = Pair(scene)
+    try:
+        d = scene.frame(1).copy()
+        d[:, 40] = 0.0
+        sw.sw_upload_depth(p.h, d, 1)
+        V, N = sw.sw_read_maps(p.h, c.height, c.width)
+        m = ODEPTH.depth_maps(d, c.fx, c.fy, c.cx, c.cy)
+        np.testing.assert_array_equal(V[..., 3] > 0, m["valid"])
+        ok = m["valid"]
+        np.testing.assert_allclose(V[..., :3][ok], m["V"][ok], rtol=0, atol=4e-7)
+        np.testing.assert_allclose(N[..., :3][ok], m["N"][ok], rtol=0, atol=2e-5)
+    finally:
+        p.close()
+
+
 # ---------------------------------------------------------------- K2/K3 skinning, graph
 
 @pytest.mark.parametrize("which", ["tiny", "small"])
