@@ -413,8 +413,11 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
             sw.sw_solve_frame(hd, gn, pcg, want_stats=False)
             sw.sw_fuse_frame(hd)
 
+    # round 0 is played untimed by both runs (the batched run tunes its PCG
+    # on it; the autotune leaves the state as it found it); rounds 1.. are timed
     reset_models()
-    lat_plain = timed(plain_round, rounds, warmup)
+    plain_round(0)
+    lat_plain = timed(lambda r: plain_round(r + 1), rounds, warmup)
     reset_models()
     b = sw.sw_batch_create(handles, stream)
 
@@ -424,12 +427,14 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
         sw.sw_batch_fuse(b)
         return st
 
-    lat_batch = timed(batch_round, rounds, warmup)
+    batch_round(0)
+    tuned = sw.sw_batch_autotune(b, pcg)
+    lat_batch = timed(lambda r: batch_round(r + 1), rounds, warmup)
     # live stage times of two more profiled batched rounds, and their associations
     sw.sw_batch_set_profiling(b, True)
     prof = {}
     n_corr_seen = [[] for _ in range(S)]
-    for r in range(warmup + rounds, warmup + rounds + 2):
+    for r in range(warmup + rounds + 1, warmup + rounds + 3):
         st = batch_round(r, stats=True)
         prof = sw.sw_batch_read_profile(b)
         for k in range(S):
@@ -453,6 +458,7 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
                     "round_ms_p50": float(np.percentile(lat_batch, 50)),
                     "round_ms_p99": float(np.percentile(lat_batch, 99))},
         "speedup": float(lat_plain.mean() / lat_batch.mean()),
+        "autotune": {"pcg_rows_per_cta": tuned[0], "pcg_us_per_launch": tuned[1]},
         "stages_ms_per_round": {k: v[0] for k, v in prof.items()},
         "data_assembly_roofline": {"bound": "hbm", "achieved": data_bytes / t_data / 1e9, "peak": peak,
                                    "unit": "GB/s", "frac": data_bytes / t_data / 1e9 / peak,
@@ -532,8 +538,11 @@ def main():
         sw.sw_fuse_frame(h)
         return st
 
-    # warm-up (also captures the solve graph)
-    for k in range(args.warmup):
+    # warm-up (also captures the solve graph), with the PCG granularity
+    # autotuned on the first frame's system
+    step(0, False)
+    tuned_rows, tuned_us = sw.sw_autotune(h, pcg)
+    for k in range(1, args.warmup):
         step(k, False)
     torch.cuda.synchronize()
 
@@ -622,6 +631,7 @@ def main():
         "roofline": roof["dominant"],
         "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
         "stage_roofline": roof["stages"],
+        "autotune": {"pcg_rows_per_cta": tuned_rows, "pcg_us_per_launch": tuned_us},
     }
     if batched:
         line["multi_stream"] = batched

@@ -369,6 +369,21 @@ sw_status sw_server_read_nodes(sw_server_handle s, int stream_id, float* pos4, f
 sw_status sw_server_set_batch_window(sw_server_handle s, double window_ms);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 
+/* ---------------------------------------------------------------------------
+ * Autotuning (addition; no counterpart in the paper).  Chooses the PCG's
+ * granularity -- one persistent CTA per rows_per_cta block rows of a stream,
+ * from 16, 24, 32, 48, 64, 96; it sets the CTA count, how much of the matrix
+ * fits in shared memory and how many CTAs each reduction waits for -- by
+ * timing the persistent launch on the stream's (or the batch members')
+ * current system.  Needs a model and a depth frame on every stream; the
+ * node transforms are restored afterwards and a batch's members are all made
+ * active.  *rows_per_cta and *pcg_us (nullable) receive the choice and its
+ * time per launch in microseconds.  The choice stays with the stream (or
+ * the batch) until the next autotune call.
+ * ------------------------------------------------------------------------- */
+sw_status sw_autotune(sw_handle h, int pcg_iters, int* rows_per_cta, double* pcg_us);
+sw_status sw_batch_autotune(sw_batch_handle b, int pcg_iters, int* rows_per_cta, double* pcg_us);
+
 /* Reason of the last error on this handle ("" if none); NULL handle: the last
  * process-wide error (e.g. of sw_create_stream). */
 const char* sw_last_error(sw_handle h);

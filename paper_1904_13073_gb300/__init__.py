@@ -123,6 +123,8 @@ _SIGS = {
     "sw_server_read_nodes": [_P, _I, _P, _P, _I, ctypes.POINTER(_I)],
     "sw_server_read_stats": [_P, ctypes.POINTER(sw_server_stats)],
     "sw_server_set_batch_window": [_P, ctypes.c_double],
+    "sw_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
+    "sw_batch_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
 }
 
 PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion")
@@ -566,3 +568,18 @@ def sw_server_read_stats(srv):
     st = sw_server_stats()
     _check(lib().sw_server_read_stats(srv, ctypes.byref(st)))
     return st.as_dict()
+
+
+# ---------------------------------------------------------------- autotuning
+
+def sw_autotune(h, pcg_iters):
+    """(rows per PCG CTA chosen, PCG microseconds per launch)."""
+    r, us = ctypes.c_int(), ctypes.c_double()
+    _check(lib().sw_autotune(h, pcg_iters, ctypes.byref(r), ctypes.byref(us)), h)
+    return r.value, us.value
+
+
+def sw_batch_autotune(b, pcg_iters):
+    r, us = ctypes.c_int(), ctypes.c_double()
+    _check(lib().sw_batch_autotune(b, pcg_iters, ctypes.byref(r), ctypes.byref(us)))
+    return r.value, us.value

@@ -81,6 +81,7 @@ struct Runner {
   bool profiling = false;
   std::vector<ProfEvent> eager_prof;   // events of the last upload / fusion
   std::vector<cudaEvent_t> event_pool;
+  int pcg_rows_per_cta = 32;     // PCG granularity: a stream takes one CTA per this many rows (autotuned)
   std::string err;
 };
 
@@ -113,7 +114,6 @@ struct sw_batch {
 
 namespace {
 
-constexpr int kPcgMaxCtas = 64;   // persistent-PCG CTAs one stream may own
 
 sw_status fail(sw_stream* s, sw_status code, const std::string& msg) {
   if (s) s->err = msg; else set_global_error(msg);
@@ -238,12 +238,12 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
     // greedy: the next CTA goes to the stream with the most rows per CTA,
     // which minimises the largest share (the launch ends with the slowest
-    // stream); a stream takes at most one CTA per 32 rows and kPcgMaxCtas
-    const int warps = pcg_threads() / 32;
+    // stream); a stream takes at most one CTA per pcg_rows_per_cta rows
     std::vector<int> want(n, 1);
     int total = n;
     {
-      auto limit = [&](int i) { return std::max(1, std::min(kPcgMaxCtas, (devs[i].n_n + warps - 1) / warps)); };
+      const int rows = std::max(8, r->pcg_rows_per_cta);
+      auto limit = [&](int i) { return std::max(1, std::min(kMaxCtaPerStream, (devs[i].n_n + rows - 1) / rows)); };
       auto share = [&](int i) { return (devs[i].n_n + want[i] - 1) / want[i]; };
       std::priority_queue<std::pair<int, int>> pq;   // (rows per CTA, stream)
       for (int i = 0; i < n; ++i)
@@ -357,18 +357,25 @@ void prof_mark(Runner* r, std::vector<ProfEvent>* list, int stage, bool begin, b
   }
 }
 
+// The two assembly stages of a Gauss-Newton iteration in the batch's precision.
+void launch_reg_stage(const BatchHost& b, int it, cudaStream_t st) {
+  if (b.precision == SW_PRECISION_FP64) launch_reg_assemble64(b, it, st);
+  else launch_reg_assemble(b, it, st);
+}
+void launch_data_stage(const BatchHost& b, int it, cudaStream_t st) {
+  if (b.precision == SW_PRECISION_FP64) launch_data_assemble64(b, it, st);
+  else launch_data_assemble(b, it, st);
+}
+
 sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vector<ProfEvent>* prof) {
   cudaStream_t st = r->st;
   launch_solve_begin(r->bh, st);
   for (int it = 0; it < gn; ++it) {
-    const bool f64 = r->bh.precision == SW_PRECISION_FP64;
     prof_mark(r, prof, kProfReg, true, true);
-    if (f64) launch_reg_assemble64(r->bh, it, st);
-    else launch_reg_assemble(r->bh, it, st);
+    launch_reg_stage(r->bh, it, st);
     prof_mark(r, prof, kProfReg, false, true);
     prof_mark(r, prof, kProfData, true, true);
-    if (f64) launch_data_assemble64(r->bh, it, st);
-    else launch_data_assemble(r->bh, it, st);
+    launch_data_stage(r->bh, it, st);
     prof_mark(r, prof, kProfData, false, true);
     prof_mark(r, prof, kProfPcg, true, true);
     SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
@@ -542,6 +549,82 @@ __global__ void k_set_frames(Batch bt, const int* __restrict__ frames) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ autotuning
+
+// Choose the PCG's granularity (rows per CTA) for a runner by timing its
+// persistent launch on the members' current systems: for each candidate the
+// runner is rebuilt (CTA allocation and SpMV staging follow), the system is
+// assembled again (which also starts a new PCG epoch) and the PCG launch
+// alone is timed with events, three times after one untimed launch.  The
+// node transforms are saved before and restored after every candidate, so
+// the call leaves the streams' state as it found it.  Every member is made
+// active.
+sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows, double* best_us) {
+  static const int kCand[] = {16, 24, 32, 48, 64, 96};
+  cudaStream_t st = r->st;
+  struct Saved { void* dst; void* copy; size_t bytes; };
+  std::vector<Saved> saved;
+  auto release = [&] { for (auto& sv : saved) cudaFree(sv.copy); };
+  for (sw_stream* m : r->members) {
+    if (!m->has_model || !m->has_depth) { release(); return fail(err_to, SW_ERR_NOT_INITIALIZED, "a member has no model or depth frame"); }
+    const size_t nb[2] = {(size_t)m->h.n_n * 32, m->h.dq64 ? (size_t)m->h.n_n * 64 : 0};
+    void* src[2] = {m->h.dq, m->h.dq64};
+    for (int k = 0; k < 2; ++k) {
+      if (!nb[k]) continue;
+      void* cp = nullptr;
+      if (cudaMalloc(&cp, nb[k]) != cudaSuccess) { release(); return fail(err_to, SW_ERR_NO_MEMORY, "autotune scratch"); }
+      saved.push_back({src[k], cp, nb[k]});
+      SW_CUDA(err_to, cudaMemcpyAsync(cp, src[k], nb[k], cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  auto restore = [&]() -> cudaError_t {
+    for (auto& sv : saved) {
+      const cudaError_t e = cudaMemcpyAsync(sv.dst, sv.copy, sv.bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = r->pcg_rows_per_cta;
+  double best_t = 1e30;
+  for (int rows : kCand) {
+    r->pcg_rows_per_cta = rows;
+    if (build_runner(r, nullptr) != SW_OK) continue;   // does not fit on chip: skip
+    launch_solve_begin(r->bh, st);
+    double sum = 0.0;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
+      launch_reg_stage(r->bh, 0, st);
+      launch_data_stage(r->bh, 0, st);
+      cudaEventRecord(e0, st);
+      ok = launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
+      cudaEventRecord(e1, st);
+      ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) sum += ms;
+    }
+    ok = ok && restore() == cudaSuccess;
+    if (ok && sum / 3.0 < best_t) {
+      best_t = sum / 3.0;
+      best = rows;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  r->pcg_rows_per_cta = best;
+  const sw_status bs = build_runner(r, err_to);
+  const cudaError_t re = restore();
+  SW_CUDA(err_to, cudaStreamSynchronize(st));
+  release();
+  if (bs != SW_OK) return bs;
+  if (re != cudaSuccess) return fail(err_to, SW_ERR_CUDA, "autotune restore failed");
+  if (best_rows) *best_rows = best;
+  if (best_us) *best_us = best_t * 1000.0;
+  return SW_OK;
+}
 
 // ------------------------------------------------------------------ public API
 
@@ -1452,6 +1535,23 @@ sw_status batch_member_status(sw_batch_handle b, int* status) {
   return SW_OK;
 }
 }  // namespace sw
+
+sw_status sw_autotune(sw_handle s, int pcg_iters, int* rows_per_cta, double* pcg_us) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (pcg_iters < 1 || pcg_iters > kMaxPcg) return fail(s, SW_ERR_INVALID_ARG, "pcg_iters out of range");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "needs a model and a depth frame");
+  enter(s);
+  return runner_autotune(s->run, s, pcg_iters, rows_per_cta, pcg_us);
+}
+
+sw_status sw_batch_autotune(sw_batch_handle b, int pcg_iters, int* rows_per_cta, double* pcg_us) {
+  SW_TRY(batch_check(b));
+  if (pcg_iters < 1 || pcg_iters > kMaxPcg) return fail(nullptr, SW_ERR_INVALID_ARG, "pcg_iters out of range");
+  batch_enter(b);
+  const sw_status st = runner_autotune(&b->run, nullptr, pcg_iters, rows_per_cta, pcg_us);
+  batch_leave(b);
+  return st;
+}
 
 sw_status sw_set_profiling(sw_handle s, int enable) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");

@@ -130,3 +130,29 @@ def test_bounded_barrier_wait_reports_timeout_and_context_survives():
         assert st["n_corr"][0] > 0
     finally:
         sw.sw_destroy_stream(h)
+
+
+def test_batch_autotune_then_matches_alone():
+    scenes = _scenes()
+    alone = [_make(s) for s in scenes]
+    mixed = [_make(s) for s in scenes]
+    b = sw.sw_batch_create(mixed)
+    try:
+        sw.sw_batch_upload_depth(b, [s.frame(1) for s in scenes], [1] * 3)
+        rows, us = sw.sw_batch_autotune(b, 8)
+        assert rows in (16, 24, 32, 48, 64, 96) and us > 0
+        sw.sw_batch_solve(b, 3, 8)
+        sw.sw_batch_fuse(b)
+        for h, s in zip(alone, scenes):
+            sw.sw_upload_depth(h, s.frame(1), 1)
+            sw.sw_solve_frame(h, 3, 8)
+            sw.sw_fuse_frame(h)
+        for ha, hm, s in zip(alone, mixed, scenes):
+            qa, pa = _warped(ha, s.node_p)
+            qm, pm = _warped(hm, s.node_p)
+            assert np.max(rotation_angle_between(qa, qm)) < 1e-5
+            assert np.max(np.abs(pa - pm)) < 2e-6
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in alone + mixed:
+            sw.sw_destroy_stream(h)

@@ -253,3 +253,24 @@ def test_precision_report():
         with open(os.path.join(out, "precision_report.json"), "w") as f:
             json.dump(report, f, indent=1)
     assert report["fp64"]["max_rot_err_rad"] <= report["fp32_assembly_doublefloat_dots"]["max_rot_err_rad"]
+
+
+def test_autotune_keeps_state_and_parity():
+    """The PCG autotuner times candidate granularities on the current system:
+    it leaves the node transforms as they were, and the solve that follows
+    still matches the oracle."""
+    scene = synth.plain_tiny(seed=0)
+    p = Pair(scene)
+    try:
+        p.upload(1)
+        _, before = sw.sw_read_nodes(p.h)
+        rows, us = sw.sw_autotune(p.h, scene.pcg_iters)
+        assert rows in (16, 24, 32, 48, 64, 96) and us > 0
+        _, after = sw.sw_read_nodes(p.h)
+        np.testing.assert_array_equal(before, after)
+        sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
+        p.o.solve_frame(scene.gn_iters, scene.pcg_iters)
+        rot, trans = _compare_nodes(p)
+        assert rot <= ROT_TOL and trans <= TRANS_TOL, (rows, rot, trans)
+    finally:
+        p.close()
