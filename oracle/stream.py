@@ -16,6 +16,7 @@ from . import depth as DEPTH
 from . import skinning as SKIN
 from . import solver as SOLVER
 from . import fusion as FUSION
+from . import rigid as RIGID
 
 
 @dataclass
@@ -92,6 +93,14 @@ class OracleStream:
             self.v_ref, self.n_ref, self.knn, self.w, self.node_p, self.node_dq,
             self.graph, self.pattern, self.p.lam, gn_iters, pcg_iters,
             associate_fn=self.associate, keep_masks=keep_masks)
+        return stats
+
+    def rigid_align(self, iters):
+        """Rigid pre-alignment of the current frame (see rigid.py); returns
+        [(correspondences, Σ r²)] per iteration."""
+        self.node_dq, T, stats = RIGID.rigid_align(self.v_ref, self.n_ref, self.knn, self.w, self.node_dq,
+                                                  self.associate, iters)
+        self.last_rigid = T
         return stats
 
     def fuse_frame(self):

@@ -128,3 +128,16 @@ def test_wrong_fusion_preference(monkeypatch):
         return orig(imap, v, n, -np.asarray(conf), *a)   # lowest confidence wins
     monkeypatch.setattr(FU, "select_fusion_targets", bad)
     _fails(T_FU.test_window_search_brute_force_and_update)
+
+
+def test_flipped_cross_product_in_rigid_jacobian(monkeypatch):
+    """y × n_d turned into n_d × y: the finite-difference pin fails."""
+    import test_oracle_rigid as T
+    from oracle import rigid as R
+
+    def bad_terms(y, n_d, v_d):
+        r = np.einsum('ij,ij->i', n_d, y - v_d)
+        return r, np.concatenate([np.cross(n_d, y), n_d], axis=1)
+    monkeypatch.setattr(R, "rigid_terms", bad_terms)
+    with pytest.raises(AssertionError):
+        T.test_rigid_jacobian_matches_finite_differences()
