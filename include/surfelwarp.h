@@ -33,6 +33,7 @@ extern "C" {
 
 #define SW_MAX_GN_ITERS 16     /* Sec. 8 caps Gauss-Newton at 10 iterations */
 #define SW_MAX_PCG_ITERS 128
+#define SW_MAX_RIGID_ITERS 16
 #define SW_MAX_NODES 65535     /* node ids are packed in 16 bits */
 #define SW_K_SKIN 4            /* nearest nodes per surfel (Eq. 1) */
 #define SW_K_GRAPH 8           /* graph neighbours per node (Eq. 11) */
@@ -368,6 +369,21 @@ sw_status sw_server_read_nodes(sw_server_handle s, int stream_id, float* pos4, f
  * frames (0 = start at once, the default). */
 sw_status sw_server_set_batch_window(sw_server_handle s, double window_ms);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
+
+/* Rigid pre-alignment of the current frame (Sec. 7: before the non-rigid
+ * estimation a rigid alignment in the manner of KinectFusion).  Runs `iters`
+ * (0..SW_MAX_RIGID_ITERS) point-to-plane ICP iterations of the warped model
+ * against the uploaded depth: association exactly as in sw_solve_frame, the
+ * model moved by one rigid transform T solved from 6x6 normal equations
+ * (FP64 Cholesky; a system that is not positive definite ends the
+ * iterations with T as it is), and finally T composed into every node
+ * transform (T_j <- T T_j).  Call between sw_upload_depth and
+ * sw_solve_frame.  n_corr / energy (nullable, `iters` entries each) receive
+ * each iteration's correspondence count and sum of squared point-to-plane
+ * residuals before its update; the call then synchronises. */
+sw_status sw_rigid_align(sw_handle h, int iters, int* n_corr, double* energy);
+/* The same for every active member of a batch (no statistics). */
+sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
 
 /* ---------------------------------------------------------------------------
  * Autotuning (addition; no counterpart in the paper).  Chooses the PCG's

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libsurfelwarp.so")
 
 SW_MAX_GN_ITERS = 16
 SW_MAX_PCG_ITERS = 128
+SW_MAX_RIGID_ITERS = 16
 SW_PRECISION_MIXED = 0           # FP32 solve, double-float PCG inner products, FP64 6x6 inverses
 SW_PRECISION_FP64 = 1            # the whole solve in FP64
 SW_PRECISION_MIXED_F64DOTS = 2   # FP32 solve, FP64 PCG inner products, FP64 6x6 inverses
@@ -124,6 +125,8 @@ _SIGS = {
     "sw_server_read_stats": [_P, ctypes.POINTER(sw_server_stats)],
     "sw_server_set_batch_window": [_P, ctypes.c_double],
     "sw_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
+    "sw_rigid_align": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
+    "sw_batch_rigid_align": [_P, _I],
     "sw_batch_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
 }
 
@@ -583,3 +586,17 @@ def sw_batch_autotune(b, pcg_iters):
     r, us = ctypes.c_int(), ctypes.c_double()
     _check(lib().sw_batch_autotune(b, pcg_iters, ctypes.byref(r), ctypes.byref(us)))
     return r.value, us.value
+
+
+# ---------------------------------------------------------------- rigid pre-alignment
+
+def sw_rigid_align(h, iters):
+    """Per iteration (correspondences, sum of squared residuals) before its update."""
+    n = (_I * max(1, iters))()
+    e = (ctypes.c_double * max(1, iters))()
+    _check(lib().sw_rigid_align(h, iters, n, e), h)
+    return [(n[k], e[k]) for k in range(iters)]
+
+
+def sw_batch_rigid_align(b, iters):
+    _check(lib().sw_batch_rigid_align(b, iters))

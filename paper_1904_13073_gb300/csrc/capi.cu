@@ -728,6 +728,8 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
   ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
   ALLOC(h.xz, 6 * nn); ALLOC(h.xp, 12 * nn);
+  ALLOC(h.rigid, kRigidSlots); ALLOC(h.rigid_stats, 2 * kMaxRigid);
+  ALLOC(h.rigid_part, (size_t)kRigidSums * ((ns + kSurfTile - 1) / kSurfTile));
   if (p->precision == SW_PRECISION_FP64) { ALLOC(h.g64, 6 * nn); ALLOC(h.v64, 18 * nn); ALLOC(h.dq64, 8 * nn); }
   ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
   ALLOC(h.status, 1); ALLOC(h.t_now, 1);
@@ -1535,6 +1537,42 @@ sw_status batch_member_status(sw_batch_handle b, int* status) {
   return SW_OK;
 }
 }  // namespace sw
+
+sw_status sw_rigid_align(sw_handle s, int iters, int* n_corr, double* energy) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (iters < 0 || iters > kMaxRigid) return fail(s, SW_ERR_INVALID_ARG, "iters out of range");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "needs a model and a depth frame");
+  if (iters == 0) return SW_OK;
+  enter(s);
+  if (runner_stale(s->run)) SW_TRY(build_runner(s->run, s));
+  launch_rigid_align(s->run->bh, iters, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  if (n_corr || energy) {
+    std::vector<double> st(2 * iters);
+    SW_CUDA(s, cudaMemcpyAsync(st.data(), s->h.rigid_stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaStreamSynchronize(s->st));
+    for (int k = 0; k < iters; ++k) {
+      if (n_corr) n_corr[k] = (int)st[2 * k];
+      if (energy) energy[k] = st[2 * k + 1];
+    }
+  }
+  return SW_OK;
+}
+
+sw_status sw_batch_rigid_align(sw_batch_handle b, int iters) {
+  SW_TRY(batch_check(b));
+  if (iters < 0 || iters > kMaxRigid) return fail(nullptr, SW_ERR_INVALID_ARG, "iters out of range");
+  Runner* r = &b->run;
+  for (int i = 0; i < (int)r->members.size(); ++i)
+    if (r->active_host[i] && !r->members[i]->has_depth)
+      return fail(nullptr, SW_ERR_NOT_INITIALIZED, "an active member has no depth frame");
+  if (iters == 0) return SW_OK;
+  batch_enter(b);
+  launch_rigid_align(r->bh, iters, r->st);
+  SW_CUDA(nullptr, cudaGetLastError());
+  batch_leave(b);
+  return SW_OK;
+}
 
 sw_status sw_autotune(sw_handle s, int pcg_iters, int* rows_per_cta, double* pcg_us) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");

@@ -17,6 +17,9 @@ namespace sw {
 constexpr int kMaxGn = SW_MAX_GN_ITERS;
 constexpr int kMaxPcg = SW_MAX_PCG_ITERS;
 constexpr int kMaxCtaPerStream = 1024;   // CTAs of the persistent PCG that one stream may own
+constexpr int kMaxRigid = SW_MAX_RIGID_ITERS;
+constexpr int kRigidSlots = 16;          // rigid pre-alignment state: T (8), stopped flag, spare
+constexpr int kRigidSums = 29;           // per surfel tile: 21 (J Jᵀ upper) + 6 (J r) + count + Σ r²
 
 // status bits written by kernels
 constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive definite, or pᵀAp <= 0
@@ -90,6 +93,10 @@ struct SwDev {
   double* g64;        // 6 n_n
   double* v64;        // 3 * 6 n_n
   double* dq64;       // 8 per node
+  // rigid pre-alignment
+  double* rigid;        // kRigidSlots: T as a dual quaternion, then a stopped flag
+  float* rigid_part;    // per surfel tile, kRigidSums partial sums
+  double* rigid_stats;  // per iteration: correspondences, Σ r²
   // per-GN-iteration statistics
   double* e_depth;    // kMaxGn
   double* e_reg;      // kMaxGn
@@ -126,7 +133,7 @@ struct GridBarrier {   // counter barrier used by the timeout probe
 
 // ------------------------------------------------------------------ launchers
 
-enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileKinds };
+enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTileKinds };
 
 struct BatchHost {
   Batch bt;
@@ -151,6 +158,7 @@ void launch_reg_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_dq_widen(const SwDev& d, cudaStream_t st);
 void launch_warp_live(const BatchHost& b, cudaStream_t st);
+void launch_rigid_align(const BatchHost& b, int iters, cudaStream_t st);
 void launch_index_map(const BatchHost& b, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
@@ -175,6 +183,7 @@ inline int tiles_for(int kind, const SwDev& d) {
     case kTileSurfelsAssembly: return (d.n_s + kAsmTile - 1) / kAsmTile;
     case kTileBlocks: return (d.nnzb + kBlkTile - 1) / kBlkTile;
     case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
+    case kTileNodes: return (d.n_n + kBlkTile - 1) / kBlkTile;
   }
   return 0;
 }
