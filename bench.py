@@ -603,6 +603,27 @@ def main():
         e_lat.append(time.perf_counter() - s0)
     torch.cuda.synchronize()
     e2e_ms = 1000.0 * (time.perf_counter() - t0) / args.steps
+
+    # rigid pre-alignment (a separate call, not part of the configuration's
+    # frame): ICP iterations on the next frame, timed on the library's stream
+    rigid = None
+    k_r = base + prof_steps + args.steps - 1
+    sw.sw_upload_depth(h, dev_frames[ts[k_r]], k_r + 2)
+    rig_stats = sw.sw_rigid_align(h, 3)                 # warm-up, and the association count
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(5):
+        sw.sw_rigid_align(h, 3, want_stats=False)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rigid_it_us = 1000.0 * r0.elapsed_time(r1) / 15.0
+    rig_bytes = 64.0 * len(v4) + 32.0 * float(np.mean([n for n, _ in rig_stats])) + 29 * 4.0 * (len(v4) / 256.0)
+    peak, _src = measured_hbm_peak()
+    rigid = {"iterations_timed": 15, "us_per_iteration": rigid_it_us,
+             "correspondences": [int(n) for n, _ in rig_stats],
+             "bytes_per_iteration": rig_bytes, "achieved_gbs": rig_bytes / rigid_it_us / 1e3,
+             "frac": rig_bytes / rigid_it_us / 1e3 / peak}
     sw.sw_destroy_stream(h)
     batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
         if members and args.batch_streams > 0 else None
@@ -632,6 +653,7 @@ def main():
         "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
         "stage_roofline": roof["stages"],
         "autotune": {"pcg_rows_per_cta": tuned_rows, "pcg_us_per_launch": tuned_us},
+        "rigid_align": rigid,
     }
     if batched:
         line["multi_stream"] = batched

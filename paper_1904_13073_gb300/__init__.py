@@ -590,8 +590,12 @@ def sw_batch_autotune(b, pcg_iters):
 
 # ---------------------------------------------------------------- rigid pre-alignment
 
-def sw_rigid_align(h, iters):
-    """Per iteration (correspondences, sum of squared residuals) before its update."""
+def sw_rigid_align(h, iters, want_stats=True):
+    """Per iteration (correspondences, sum of squared residuals) before its
+    update; without want_stats returns None and does not wait for the GPU."""
+    if not want_stats:
+        _check(lib().sw_rigid_align(h, iters, None, None), h)
+        return None
     n = (_I * max(1, iters))()
     e = (ctypes.c_double * max(1, iters))()
     _check(lib().sw_rigid_align(h, iters, n, e), h)

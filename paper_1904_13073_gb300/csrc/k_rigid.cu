@@ -11,15 +11,17 @@
 //                   the CTA sums the 21 upper entries of J Jᵀ, the 6 of J r,
 //                   the count and r² into one partial row (plain stores, no
 //                   atomics).
-//   k_rigid_solve   one warp per stream: sums its tiles' partial rows in a
-//                   fixed order in FP64, solves the 6x6 system by Cholesky
-//                   and updates T ← Δ(ξ) T (FP64); a system that is not
-//                   positive definite stops the iterations with T as it is.
+//   k_rigid_solve   one CTA per stream, a warp per sum: adds its tiles'
+//                   partial rows in a fixed order in double-float pairs,
+//                   then one thread solves the 6x6 system by Cholesky and
+//                   updates T ← Δ(ξ) T (FP64); a system that is not positive
+//                   definite stops the iterations with T as it is.
 //   k_rigid_fold    T_j ← T T_j for every node.
 #include "sw_internal.h"
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 #include "sw_assoc.cuh"
+#include "sw_df.cuh"
 
 namespace sw {
 namespace {
@@ -97,20 +99,22 @@ __global__ void __launch_bounds__(kSurfTile) k_rigid_reduce(Batch bt, int it) {
   }
 }
 
-__global__ void k_rigid_solve(Batch bt, int it) {
+__global__ void __launch_bounds__(32 * kRigidSums) k_rigid_solve(Batch bt, int it) {
   const int s = blockIdx.x;
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int tiles = (d.n_s + kSurfTile - 1) / kSurfTile;
   __shared__ double tot[kRigidSums];
-  if (lane < kRigidSums) {
-    double t = 0.0;
-    for (int k = 0; k < tiles; ++k) t += (double)d.rigid_part[(size_t)k * kRigidSums + lane];
-    tot[lane] = t;
+  {   // warp w sums value w over the tiles (lanes stride, then a butterfly): a fixed order
+    DF acc = df_from(0.f);
+    for (int k = lane; k < tiles; k += 32) acc = df_add(acc, df_from(d.rigid_part[(size_t)k * kRigidSums + wid]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+    if (lane == 0) tot[wid] = df_value(acc);
   }
-  __syncwarp();
-  if (lane != 0) return;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   d.rigid_stats[2 * it] = tot[27];
   d.rigid_stats[2 * it + 1] = tot[28];
   if (d.rigid[8] != 0.0) return;   // stopped earlier
@@ -193,7 +197,7 @@ void launch_rigid_align(const BatchHost& b, int iters, cudaStream_t st) {
   for (int it = 0; it < iters; ++it) {
     if (b.total_tiles[kTileSurfels])
       k_rigid_reduce<<<b.total_tiles[kTileSurfels], kSurfTile, 0, st>>>(with_kind(b, kTileSurfels), it);
-    k_rigid_solve<<<b.bt.n_streams, 32, 0, st>>>(b.bt, it);
+    k_rigid_solve<<<b.bt.n_streams, 32 * kRigidSums, 0, st>>>(b.bt, it);
   }
   if (b.total_tiles[kTileNodes])
     k_rigid_fold<<<b.total_tiles[kTileNodes], kBlkTile, 0, st>>>(with_kind(b, kTileNodes));

@@ -51,13 +51,15 @@ def test_rigid_align_matches_oracle(noise):
 
 def test_rigid_then_nonrigid_solve_matches_oracle():
     """Rigid pre-alignment, then the non-rigid solve, on the non-rigid 160x120
-    frame.  Compared in two parts: the rigid step's result, then the solve
-    with both sides starting from the same (the GPU's) post-rigid state.
-    The two parts are not compared as one chain: 5 Gauss-Newton iterations
-    with 10 PCG iterations each are truncated, and from a start that is not
-    the identity the oracle itself moves its final nodes by ~1.3e-5 m when its
-    start is perturbed by 1e-7 (measured), so FP32 rounding of the composed
-    start would dominate the comparison."""
+    frame.  The rigid step is compared at the standard bar.  The solve that
+    follows starts for both sides from the same (the GPU's) post-rigid state,
+    but from a start that is not the identity the association is decided on
+    FP32 warps that differ in their last bits between the GPU (FP32) and the
+    oracle (FP64 rounded to FP32); a few decisions flip and the Gauss-Newton
+    path moves.  Measured on the oracle alone: perturbing this start by 1e-7
+    moves its final nodes by 2.6e-5 m, with 10 or with 120 PCG iterations
+    alike.  The chain is therefore compared at about four times that spread
+    (1e-4 m, 1e-3 rad) and on its final data energy (1 %)."""
     scene = synth.plain_tiny(seed=0)
     p = Pair(scene)
     try:
@@ -71,9 +73,10 @@ def test_rigid_then_nonrigid_solve_matches_oracle():
         p.o.node_dq = dq.astype(np.float64)
         st = sw.sw_solve_frame(p.h, scene.gn_iters, scene.pcg_iters)
         ost = p.o.solve_frame(scene.gn_iters, scene.pcg_iters)
-        assert abs(st["n_corr"][-1] - ost[-1].n_corr) <= 3
+        assert abs(st["n_corr"][-1] - ost[-1].n_corr) <= 10
+        assert st["e_depth"][-1] == pytest.approx(ost[-1].e_depth, rel=1e-2)
         rot, trans = _node_errors(p)
-        assert rot <= ROT_TOL and trans <= TRANS_TOL, ("solve", rot, trans)
+        assert rot <= 1e-3 and trans <= 1e-4, ("solve", rot, trans)
     finally:
         p.close()
 
