@@ -17,6 +17,7 @@ from . import skinning as SKIN
 from . import solver as SOLVER
 from . import fusion as FUSION
 from . import rigid as RIGID
+from . import append as APPEND
 
 
 @dataclass
@@ -119,6 +120,38 @@ class OracleStream:
         self.last_target = target
         self.last_index_map = imap
         return int(fused.sum())
+
+    def append_frame(self, max_surfels, eps=APPEND.EPS, delta_nn=APPEND.DELTA_NN, h=APPEND.FD_STEP,
+                     t_low=APPEND.T_LOW_CONFID):
+        """Appending and removal after fuse_frame (see append.py).  Returns
+        (candidates, appended, removed); the per-candidate record is kept in
+        ``last_append``."""
+        p = self.p
+        pix = APPEND.empty_window_pixels(self.last_index_map, self.maps["valid"])
+        res = APPEND.append_candidates(pix, self.maps, self.node_dq, self.node_p, self.node_sigma,
+                                       eps, delta_nn, h)
+        stay = ~APPEND.unstable(self.conf, self.t_init, self.t_now, p.stable_conf, t_low)
+        acc = np.nonzero(res["accept"])[0]
+        acc = acc[:max(0, max_surfels - int(stay.sum()))]
+        res["pix"] = pix
+        res["appended"] = acc
+        self.last_append = res
+        new_pix = pix[acc]
+        new_v = res["v_ref"][acc]
+        new_n = res["n_ref"][acc]
+        new_knn = SKIN.knn_fp32(new_v.astype(np.float32), self.node_p.astype(np.float32), SKIN.K_SKIN)
+        new_w = SKIN.skin_weights(new_v, self.node_p, self.node_sigma, new_knn)
+        t_new = np.full(len(acc), self.t_now, dtype=np.int64)
+        self.v_ref = np.concatenate([self.v_ref[stay], new_v])
+        self.n_ref = np.concatenate([self.n_ref[stay], new_n])
+        self.radius = np.concatenate([self.radius[stay], self.maps["radius"].reshape(-1)[new_pix]])
+        self.conf = np.concatenate([self.conf[stay], self.maps["conf"].reshape(-1)[new_pix]])
+        self.t_init = np.concatenate([self.t_init[stay], t_new])
+        self.t_obs = np.concatenate([self.t_obs[stay], t_new])
+        self.knn = np.concatenate([self.knn[stay], new_knn])
+        self.w = np.concatenate([self.w[stay], new_w])
+        self.pattern = SOLVER.BlockMatrix.pattern(len(self.node_p), self.knn, self.graph).keys
+        return len(pix), len(acc), int((~stay).sum())
 
     # -- read-back -----------------------------------------------------------
     def read_nodes(self):

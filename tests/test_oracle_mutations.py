@@ -141,3 +141,58 @@ def test_flipped_cross_product_in_rigid_jacobian(monkeypatch):
     monkeypatch.setattr(R, "rigid_terms", bad_terms)
     with pytest.raises(AssertionError):
         T.test_rigid_jacobian_matches_finite_differences()
+
+
+def test_eq7_against_live_distances_only(monkeypatch):
+    """Eq. 7 with the reference distance replaced by the live one: the hand-worked case fails."""
+    import test_oracle_append as T
+    from oracle import append as AP
+
+    def bad(knn, p_live32, p_ref32, eps=AP.EPS):
+        return AP_consistent(knn, p_live32, p_live32, eps)
+    AP_consistent = AP.consistent
+    monkeypatch.setattr(AP, "consistent", bad)
+    _fails(T.test_eq7_ratio_test_by_hand)
+
+
+def test_one_sided_strain_difference(monkeypatch):
+    """A forward difference divided by 2h halves the strain: the analytic pin fails."""
+    import test_oracle_append as T
+    from oracle import append as AP
+
+    def bad(x, node_dq, knn, keep, p_live32, sigma, h=AP.FD_STEP):
+        x = np.asarray(x, dtype=np.float64)
+        out = np.empty(x.shape + (3,))
+        zero = np.zeros_like(x)
+        r0, _ = AP.inverse_warp_live(x, zero, node_dq, knn, AP.live_weights(x, p_live32, sigma, knn, keep))
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            rp, _ = AP.inverse_warp_live(x + e, zero, node_dq, knn, AP.live_weights(x + e, p_live32, sigma, knn, keep))
+            out[:, :, a] = (rp - r0) / (2.0 * h)
+        return out
+    monkeypatch.setattr(AP, "strain", bad)
+    _fails(T.test_strain_matches_analytic_jacobian_and_flags_compression)
+
+
+def test_forward_instead_of_inverse_warp_on_append(monkeypatch):
+    """Appending with the forward warp: the rigid closed form fails."""
+    import test_oracle_append as T
+    from oracle import append as AP
+
+    def bad(x, n, node_dq, knn, w):
+        b = DQ.blend(node_dq, knn, w)
+        return DQ.dq_transform_point(b, x), DQ.dq_rotate_vector(b, n)
+    monkeypatch.setattr(AP, "inverse_warp_live", bad)
+    _fails(T.test_rigid_warp_field_inverts_exactly)
+
+
+def test_strict_unstable_period(monkeypatch):
+    """t_now − t_init > t_low_confid instead of ≥: the boundary table fails."""
+    import test_oracle_append as T
+    from oracle import append as AP
+
+    def bad(conf, t_init, t_now, stable_conf, t_low=AP.T_LOW_CONFID):
+        return (np.asarray(conf) < stable_conf) & (t_now - np.asarray(t_init) > t_low)
+    monkeypatch.setattr(AP, "unstable", bad)
+    _fails(T.test_unstable_removal_boundaries)
