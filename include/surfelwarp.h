@@ -81,6 +81,11 @@ typedef struct {
   float stable_conf;            /* δ_stable (Table 1: 10) */
   int recent_frames;            /* δ_recent (Table 1: 2) */
   int precision;                /* SW_PRECISION_* (default SW_PRECISION_MIXED) */
+  /* appending (sw_append_frame) */
+  float eps;                    /* ε of Eq. 7-8 (Table 1: 0.2) */
+  float delta_nn;               /* δ_nn, least sum of a new surfel's live weights (not in Table 1: 0.3) */
+  float fd_step;                /* finite-difference step of the Eq. 8 strain, metres (1 mm) */
+  int t_low_confid;             /* t_low_confid, frames (Table 1: 30) */
 } sw_params;
 
 /* Per-call statistics of sw_solve_frame; entry i describes Gauss-Newton
@@ -384,6 +389,50 @@ sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 sw_status sw_rigid_align(sw_handle h, int iters, int* n_corr, double* energy);
 /* The same for every active member of a batch (no statistics). */
 sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
+
+/* ---------------------------------------------------------------------------
+ * Appending and removal (Sec. 6.2 live skinning with the consistency test of
+ * Eq. 7; Sec. 6.3 the compressive-warp bound of Eq. 8; Sec. 6.4 appending and
+ * removal; the GPU selection that compacts the surfel array, Sec. 6.6).
+ * Call after sw_fuse_frame (SW_ERR_NOT_INITIALIZED if no fusion ran since
+ * the last depth frame).  Candidates are the usable depth pixels whose
+ * fusion window (their 16 index-map sub-pixels) held no live surfel.  Each
+ * is skinned to its 4 nearest warped nodes T_j p_j; node i != 0 stays when
+ * 1-eps < |p^_i - p^_0| / |p_i - p_0| < 1+eps (decided on squares in FP32);
+ * the live weights exp(-|x - p^_i|^2 / 2 sigma_i^2) of the nodes that stay
+ * must sum to at least delta_nn; the depth vertex and normal are warped back
+ * (Eq. 3, FP64) and the strain d x_ref / d x_live, by central differences of
+ * step fd_step, must have no singular value above 1+eps.  Accepted
+ * candidates become surfels with the depth surfel's radius and confidence,
+ * t_init = t_observed = the frame id, and a skinning recomputed at their
+ * reference position by the initialisation rule.  Existing surfels with
+ * confidence below stable_conf and t_now - t_init >= t_low_confid are
+ * removed.  The new caller order is the surviving surfels in their order,
+ * then the appended ones in pixel order; appended surfels beyond max_surfels
+ * are dropped from the end.  Node positions, the graph and the transforms
+ * are unchanged; the JᵀJ pattern, the runner and the solve graphs are
+ * rebuilt (the call synchronises and allocates scratch).  A batch holding
+ * the stream must be re-created afterwards.  *stats (nullable) receives
+ * the counts.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int candidates;        /* usable pixels with an empty fusion window */
+  int rejected_nn;       /* of those, weight sum below delta_nn */
+  int rejected_strain;   /* of those, strain singular value above 1+eps (Eq. 8) */
+  int appended;          /* surfels added */
+  int removed;           /* unstable surfels removed */
+  int n_surfels;         /* surfels after the call */
+} sw_append_stats;
+sw_status sw_append_frame(sw_handle h, sw_append_stats* stats);
+/* Per-candidate record of the last sw_append_frame, candidate order (row-
+ * major pixel order); each pointer nullable; cap entries: pix (1), knn4 (4
+ * node ids, live distance order), flags (1: bits 0-3 the nodes Eq. 7 keeps,
+ * 16 accepted, 32 weight sum below delta_nn, 64 compressive), wsum (1),
+ * strain9 (9, row-major), w4 (4 live weights), v4 (v_ref, radius), n4
+ * (n_ref, confidence).  *n_out receives the candidate count; with every
+ * array pointer null only the count is returned. */
+sw_status sw_debug_read_append(sw_handle h, int* pix, int* knn4, int* flags, double* wsum, double* strain9,
+                               float* w4, float* v4, float* n4, int cap, int* n_out);
 
 /* ---------------------------------------------------------------------------
  * Autotuning (addition; no counterpart in the paper).  Chooses the PCG's

@@ -37,7 +37,9 @@ class sw_params(ctypes.Structure):
                 ("max_surfels", ctypes.c_int), ("max_nodes", ctypes.c_int),
                 ("lambda_", ctypes.c_float), ("fuse_dist", ctypes.c_float), ("fuse_normal", ctypes.c_float),
                 ("corr_dist", ctypes.c_float), ("corr_normal", ctypes.c_float), ("stable_conf", ctypes.c_float),
-                ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int),
+                ("eps", ctypes.c_float), ("delta_nn", ctypes.c_float), ("fd_step", ctypes.c_float),
+                ("t_low_confid", ctypes.c_int)]
 
 
 class sw_solve_stats(ctypes.Structure):
@@ -51,6 +53,14 @@ class sw_solve_stats(ctypes.Structure):
         n = self.gn_iters
         return {"gn_iters": n, "e_depth": list(self.e_depth[:n]), "e_reg": list(self.e_reg[:n]),
                 "n_corr": list(self.n_corr[:n]), "pcg_rz": list(self.pcg_rz[:n])}
+
+
+class sw_append_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int), ("rejected_nn", ctypes.c_int), ("rejected_strain", ctypes.c_int),
+                ("appended", ctypes.c_int), ("removed", ctypes.c_int), ("n_surfels", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sw_frame_result(ctypes.Structure):
@@ -128,6 +138,8 @@ _SIGS = {
     "sw_rigid_align": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_batch_rigid_align": [_P, _I],
     "sw_batch_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
+    "sw_append_frame": [_P, ctypes.POINTER(sw_append_stats)],
+    "sw_debug_read_append": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(_I)],
 }
 
 PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion")
@@ -600,6 +612,27 @@ def sw_rigid_align(h, iters, want_stats=True):
     e = (ctypes.c_double * max(1, iters))()
     _check(lib().sw_rigid_align(h, iters, n, e), h)
     return [(n[k], e[k]) for k in range(iters)]
+
+
+def sw_append_frame(h):
+    """Appending and removal after fusion; returns the counts as a dict."""
+    st = sw_append_stats()
+    _check(lib().sw_append_frame(h, ctypes.byref(st)), h)
+    return st.as_dict()
+
+
+def sw_debug_read_append(h):
+    """The per-candidate record of the last sw_append_frame (candidate order)."""
+    n = _I(0)
+    _check(lib().sw_debug_read_append(h, None, None, None, None, None, None, None, None, 0, ctypes.byref(n)), h)
+    m = n.value
+    out = {"pix": np.zeros(m, np.int32), "knn": np.zeros((m, 4), np.int32), "flags": np.zeros(m, np.int32),
+           "wsum": np.zeros(m, np.float64), "strain": np.zeros((m, 3, 3), np.float64),
+           "w": np.zeros((m, 4), np.float32), "v4": np.zeros((m, 4), np.float32), "n4": np.zeros((m, 4), np.float32)}
+    if m:
+        ptrs = [out[k].ctypes.data_as(ctypes.c_void_p) for k in ("pix", "knn", "flags", "wsum", "strain", "w", "v4", "n4")]
+        _check(lib().sw_debug_read_append(h, *ptrs, m, ctypes.byref(n)), h)
+    return out
 
 
 def sw_batch_rigid_align(b, iters):

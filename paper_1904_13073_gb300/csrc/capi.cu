@@ -105,6 +105,11 @@ struct sw_stream {
   cudaEvent_t batch_done = nullptr;   // recorded by the last batch call (owned by the batch)
   cudaEvent_t own_ev = nullptr;       // recorded before a batch call when own work is pending
   bool own_pending = false;
+  // appending (allocated on first use)
+  bool fused = false;         // fusion ran since the last depth frame (its per-pixel results are current)
+  bool app_ready = false;
+  AppendBufs app{};
+  int app_last_cand = 0;      // candidates of the last sw_append_frame
 };
 
 struct sw_batch {
@@ -461,6 +466,10 @@ bool params_ok(const sw_params* p, std::string& why) {
   if (p->max_surfels < 0 || p->max_surfels > (1 << 28)) { why = "max_surfels out of range"; return false; }
   if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
   if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
+  if (!(p->eps > 0 && p->eps < 1 && p->delta_nn >= 0 && p->fd_step > 0)) {
+    why = "appending parameters out of range (0 < eps < 1, delta_nn >= 0, fd_step > 0)";
+    return false;
+  }
   if (p->precision != SW_PRECISION_MIXED && p->precision != SW_PRECISION_FP64 &&
       p->precision != SW_PRECISION_MIXED_F64DOTS) {
     why = "precision must be one of SW_PRECISION_MIXED, SW_PRECISION_FP64, SW_PRECISION_MIXED_F64DOTS";
@@ -645,6 +654,10 @@ sw_status sw_params_default(sw_params* p, int width, int height, float fx, float
   p->stable_conf = 10.f;    // Table 1
   p->recent_frames = 2;     // Table 1
   p->precision = SW_PRECISION_MIXED;
+  p->eps = 0.2f;            // Table 1
+  p->delta_nn = 0.3f;
+  p->fd_step = 1e-3f;
+  p->t_low_confid = 30;     // Table 1
   return SW_OK;
 }
 
@@ -881,93 +894,65 @@ sw_status upload_vec(sw_stream* s, T** dst, const std::vector<T>& v) {
 }  // namespace
 
 namespace {
-sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const int* t2, int n_s, const float* node4,
-                         int n_n, const int* knn_in, const float* w_in) {
-  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
-  if (n_s < 0 || n_s > s->p.max_surfels) return fail(s, SW_ERR_INVALID_ARG, "n_surfels out of range");
-  if (n_n < SW_K_GRAPH + 1 || n_n > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "n_nodes out of range");
-  if ((n_s > 0 && (!v4 || !n4)) || !node4) return fail(s, SW_ERR_INVALID_ARG, "null model array");
-  if (knn_in) {   // a restored skinning (distance order): node ids in range and distinct
-    for (int i = 0; i < n_s; ++i) {
-      const int* k = knn_in + (size_t)i * SW_K_SKIN;
-      for (int a = 0; a < SW_K_SKIN; ++a) {
-        bool ok = k[a] >= 0 && k[a] < n_n;
-        for (int b = 0; b < a; ++b) ok = ok && k[b] != k[a];
-        if (!ok) return fail(s, SW_ERR_INVALID_ARG, "restored skinning has a node id out of range or repeated");
-      }
-    }
-  }
-  enter(s);
-  SW_CUDA(s, cudaStreamSynchronize(s->st));
-  if (s->run) drop_graphs(s->run);
-  free_list(s->model_allocs);
-  s->version++;
+// The surfel half of the set-up, from caller-order device arrays (which may
+// be scratch): the caller-order skinning is kept for inspection, the surfels
+// are sorted by their 4-node set and gathered into the internal order, and the
+// distinct sets are returned (host) for the pattern.
+sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
+                        const float4* tw, int n_s, std::vector<int4>& sets) {
   SwDev& h = s->h;
-  h.n_s = n_s; h.n_n = n_n;
   cudaStream_t st = s->st;
-  // nodes, identity transforms, graph
-  SW_CUDA(s, cudaMemcpyAsync(h.node_p, node4, (size_t)n_n * sizeof(float4), cudaMemcpyHostToDevice, st));
-  k_identity_dq<<<(n_n + 127) / 128, 128, 0, st>>>(h.dq, n_n);
-  launch_dq_widen(h, st);
-  launch_node_graph(h, st);
+  const size_t n = n_s;
+  sets.clear();
+  SW_TRY(A(s, &s->knn_dist, std::max<size_t>(1, n), true));
+  SW_TRY(A(s, &s->w_dist, std::max<size_t>(1, n), true));
+  if (n_s == 0) {
+    SW_CUDA(s, cudaStreamSynchronize(st));
+    return SW_OK;
+  }
+  Tmp keys(n * 8), keys2(n * 8), vals(n * 4), perm(n * 4), head(n * 4);
+  if (!keys.p || !keys2.p || !vals.p || !perm.p || !head.p) return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
+  SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn, n * 16, cudaMemcpyDeviceToDevice, st));
+  SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw, n * 16, cudaMemcpyDeviceToDevice, st));
+  k_set_keys<<<(n_s + 255) / 256, 256, 0, st>>>(tknn, n_s, keys.as<unsigned long long>(), vals.as<int>());
+  size_t tmp_bytes = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(), keys2.as<unsigned long long>(),
+                                  vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
+  Tmp cubtmp(tmp_bytes);
+  if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
+  SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, tmp_bytes, keys.as<unsigned long long>(),
+                                             keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0,
+                                             64, st));
+  k_gather_model<<<(n_s + 255) / 256, 256, 0, st>>>(h, keys2.as<unsigned long long>(), perm.as<int>(), tv, tn, tt,
+                                                    tknn, tw, head.as<int>());
+  size_t scan_bytes = 0;
+  cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
+  Tmp scantmp(scan_bytes);
+  if (!scantmp.p) return fail(s, SW_ERR_NO_MEMORY, "scan scratch allocation failed");
+  SW_CUDA(s, cub::DeviceScan::InclusiveSum(scantmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
+  k_minus_one<<<(n_s + 255) / 256, 256, 0, st>>>(h.set_id, n_s);
+  int last = 0;
+  SW_CUDA(s, cudaMemcpyAsync(&last, h.set_id + n_s - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(s, cudaStreamSynchronize(st));
+  const int n_sets = last + 1;
+  Tmp setn((size_t)n_sets * 16);
+  if (!setn.p) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
+  k_set_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(h, head.as<int>(), setn.as<int4>());
+  sets.resize(n_sets);
+  SW_CUDA(s, cudaMemcpyAsync(sets.data(), setn.p, (size_t)n_sets * 16, cudaMemcpyDeviceToHost, st));
+  SW_CUDA(s, cudaStreamSynchronize(st));
+  return SW_OK;
+}
+
+// The JᵀJ pattern from the surfels' sets and the node graph: uploaded, the
+// system cleared, the stream re-described to its runner and warped live.
+sw_status install_pattern(sw_stream* s, const std::vector<int4>& sets) {
+  SwDev& h = s->h;
+  cudaStream_t st = s->st;
+  const int n_n = h.n_n, n_s = h.n_s;
   std::vector<int> graph((size_t)n_n * SW_K_GRAPH);
   SW_CUDA(s, cudaMemcpyAsync(graph.data(), h.graph, graph.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
-
-  std::vector<int4> sets;
-  if (n_s > 0) {
-    const size_t n = n_s;
-    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(n * 16), d2(n * 16), keys(n * 8),
-        keys2(n * 8), vals(n * 4), perm(n * 4), head(n * 4);
-    if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p || !keys.p || !keys2.p || !vals.p ||
-        !perm.p || !head.p)
-      return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
-    SW_CUDA(s, cudaMemcpyAsync(tv.p, v4, n * 16, cudaMemcpyHostToDevice, st));
-    SW_CUDA(s, cudaMemcpyAsync(tn.p, n4, n * 16, cudaMemcpyHostToDevice, st));
-    if (t2) SW_CUDA(s, cudaMemcpyAsync(tt.p, t2, n * 8, cudaMemcpyHostToDevice, st));
-    else SW_CUDA(s, cudaMemsetAsync(tt.p, 0, n * 8, st));
-    if (knn_in) {
-      SW_CUDA(s, cudaMemcpyAsync(tknn.p, knn_in, n * 16, cudaMemcpyHostToDevice, st));
-      SW_CUDA(s, cudaMemcpyAsync(tw.p, w_in, n * 16, cudaMemcpyHostToDevice, st));
-    } else {
-      launch_knn_skin(h, tv.as<float4>(), n_s, ids.as<int>(), d2.as<float>(), tknn.as<int4>(), tw.as<float4>(), st);
-    }
-    SW_TRY(A(s, &s->knn_dist, n, true));
-    SW_TRY(A(s, &s->w_dist, n, true));
-    SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn.p, n * 16, cudaMemcpyDeviceToDevice, st));
-    SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw.p, n * 16, cudaMemcpyDeviceToDevice, st));
-    k_set_keys<<<(n_s + 255) / 256, 256, 0, st>>>(tknn.as<int4>(), n_s, keys.as<unsigned long long>(), vals.as<int>());
-    size_t tmp_bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(),
-                                    keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
-    {
-      Tmp cubtmp(tmp_bytes);
-      if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
-      SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, tmp_bytes, keys.as<unsigned long long>(),
-                                                 keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(),
-                                                 n_s, 0, 64, st));
-      k_gather_model<<<(n_s + 255) / 256, 256, 0, st>>>(h, keys2.as<unsigned long long>(), perm.as<int>(),
-                                                        tv.as<float4>(), tn.as<float4>(), tt.as<int2>(),
-                                                        tknn.as<int4>(), tw.as<float4>(), head.as<int>());
-      size_t scan_bytes = 0;
-      cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
-      Tmp scantmp(scan_bytes);
-      if (!scantmp.p) return fail(s, SW_ERR_NO_MEMORY, "scan scratch allocation failed");
-      SW_CUDA(s, cub::DeviceScan::InclusiveSum(scantmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
-      k_minus_one<<<(n_s + 255) / 256, 256, 0, st>>>(h.set_id, n_s);
-      int last = 0;
-      SW_CUDA(s, cudaMemcpyAsync(&last, h.set_id + n_s - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-      SW_CUDA(s, cudaStreamSynchronize(st));
-      const int n_sets = last + 1;
-      Tmp setn((size_t)n_sets * 16);
-      if (!setn.p) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
-      k_set_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(h, head.as<int>(), setn.as<int4>());
-      sets.resize(n_sets);
-      SW_CUDA(s, cudaMemcpyAsync(sets.data(), setn.p, (size_t)n_sets * 16, cudaMemcpyDeviceToHost, st));
-      SW_CUDA(s, cudaStreamSynchronize(st));
-    }
-  } else {
-    SW_CUDA(s, cudaStreamSynchronize(st));
-  }
+  SW_CUDA(s, cudaStreamSynchronize(st));
   Pattern P;
   std::string why;
   if (!build_pattern(n_n, sets, graph, P, why)) return fail(s, SW_ERR_INVALID_ARG, why);
@@ -999,6 +984,61 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   s->has_model = true;
   return SW_OK;
 }
+
+sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const int* t2, int n_s, const float* node4,
+                         int n_n, const int* knn_in, const float* w_in) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (n_s < 0 || n_s > s->p.max_surfels) return fail(s, SW_ERR_INVALID_ARG, "n_surfels out of range");
+  if (n_n < SW_K_GRAPH + 1 || n_n > s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "n_nodes out of range");
+  if ((n_s > 0 && (!v4 || !n4)) || !node4) return fail(s, SW_ERR_INVALID_ARG, "null model array");
+  if (knn_in) {   // a restored skinning (distance order): node ids in range and distinct
+    for (int i = 0; i < n_s; ++i) {
+      const int* k = knn_in + (size_t)i * SW_K_SKIN;
+      for (int a = 0; a < SW_K_SKIN; ++a) {
+        bool ok = k[a] >= 0 && k[a] < n_n;
+        for (int b = 0; b < a; ++b) ok = ok && k[b] != k[a];
+        if (!ok) return fail(s, SW_ERR_INVALID_ARG, "restored skinning has a node id out of range or repeated");
+      }
+    }
+  }
+  enter(s);
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (s->run) drop_graphs(s->run);
+  free_list(s->model_allocs);
+  s->version++;
+  s->fused = false;
+  SwDev& h = s->h;
+  h.n_s = n_s; h.n_n = n_n;
+  cudaStream_t st = s->st;
+  // nodes, identity transforms, graph
+  SW_CUDA(s, cudaMemcpyAsync(h.node_p, node4, (size_t)n_n * sizeof(float4), cudaMemcpyHostToDevice, st));
+  k_identity_dq<<<(n_n + 127) / 128, 128, 0, st>>>(h.dq, n_n);
+  launch_dq_widen(h, st);
+  launch_node_graph(h, st);
+
+  std::vector<int4> sets;
+  if (n_s > 0) {
+    const size_t n = n_s;
+    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(n * 16), d2(n * 16);
+    if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p)
+      return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
+    SW_CUDA(s, cudaMemcpyAsync(tv.p, v4, n * 16, cudaMemcpyHostToDevice, st));
+    SW_CUDA(s, cudaMemcpyAsync(tn.p, n4, n * 16, cudaMemcpyHostToDevice, st));
+    if (t2) SW_CUDA(s, cudaMemcpyAsync(tt.p, t2, n * 8, cudaMemcpyHostToDevice, st));
+    else SW_CUDA(s, cudaMemsetAsync(tt.p, 0, n * 8, st));
+    if (knn_in) {
+      SW_CUDA(s, cudaMemcpyAsync(tknn.p, knn_in, n * 16, cudaMemcpyHostToDevice, st));
+      SW_CUDA(s, cudaMemcpyAsync(tw.p, w_in, n * 16, cudaMemcpyHostToDevice, st));
+    } else {
+      launch_knn_skin(h, tv.as<float4>(), n_s, ids.as<int>(), d2.as<float>(), tknn.as<int4>(), tw.as<float4>(), st);
+    }
+    SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(), n_s,
+                         sets));
+  } else {
+    SW_TRY(setup_surfels(s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, sets));
+  }
+  return install_pattern(s, sets);
+}
 }  // namespace
 
 sw_status sw_set_model(sw_handle s, const float* v4, const float* n4, const int* t2, int n_s, const float* node4,
@@ -1023,6 +1063,7 @@ sw_status sw_upload_depth(sw_handle s, const float* depth, int on_device, int fr
   prof_mark(r, prof, kProfDepth, false, false);
   SW_CUDA(s, cudaGetLastError());
   s->has_depth = true;
+  s->fused = false;
   return SW_OK;
 }
 
@@ -1062,7 +1103,9 @@ sw_status sw_fuse_frame(sw_handle s) {
   if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
   if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "fusion needs a model and a depth frame");
   enter(s);
-  return runner_fuse(s->run, s);
+  SW_TRY(runner_fuse(s->run, s));
+  s->fused = true;
+  return SW_OK;
 }
 
 sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_out) {
@@ -1176,6 +1219,7 @@ sw_status sw_debug_set_maps(sw_handle s, const float* V4, const float* N4) {
   SW_CUDA(s, cudaMemcpyAsync(s->h.nmap, N4, np * 16, cudaMemcpyHostToDevice, s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   s->has_depth = true;
+  s->fused = false;
   return SW_OK;
 }
 
@@ -1240,10 +1284,119 @@ sw_status sw_debug_fusion_targets(sw_handle s, int* target, int* imap) {
   }
   SW_CUDA(s, cudaMemsetAsync(s->h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
+  s->fused = true;
   if (target)
     for (size_t p = 0; p < np; ++p) target[p] = t[p] < 0 ? -1 : orig[t[p]];
   if (imap)
     for (size_t p = 0; p < im.size(); ++p) imap[p] = im[p] == ~0ull ? -1 : (int)(im[p] & 0xffffffffu);
+  return SW_OK;
+}
+
+namespace {
+sw_status ensure_append_bufs(sw_stream* s) {
+  if (s->app_ready) return SW_OK;
+  AppendBufs& a = s->app;
+  const size_t np = (size_t)s->h.W * s->h.H, nn = std::max(1, s->p.max_nodes);
+  const size_t nmax = std::max(np, (size_t)std::max(1, s->p.max_surfels));
+  SW_TRY(A(s, &a.live, nn)); SW_TRY(A(s, &a.cand, np)); SW_TRY(A(s, &a.query, np)); SW_TRY(A(s, &a.knn, 4 * np));
+  SW_TRY(A(s, &a.flags, np)); SW_TRY(A(s, &a.wsum, np)); SW_TRY(A(s, &a.strain, 9 * np)); SW_TRY(A(s, &a.w, np));
+  SW_TRY(A(s, &a.v, np)); SW_TRY(A(s, &a.n, np)); SW_TRY(A(s, &a.acc, np)); SW_TRY(A(s, &a.stay, nmax));
+  SW_TRY(A(s, &a.pos, nmax)); SW_TRY(A(s, &a.counts, kAppCounts));
+  a.cub_bytes = append_cub_bytes((int)np, (int)nmax);
+  unsigned char* tmp = nullptr;
+  SW_TRY(A(s, &tmp, std::max<size_t>(16, a.cub_bytes)));
+  a.cub_tmp = tmp;
+  s->app_ready = true;
+  return SW_OK;
+}
+}  // namespace
+
+sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model || !s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "appending needs a model and a depth frame");
+  if (!s->fused) return fail(s, SW_ERR_NOT_INITIALIZED, "no fusion since the last depth frame");
+  enter(s);
+  SW_TRY(ensure_append_bufs(s));
+  const AppendBufs& a = s->app;
+  SwDev& h = s->h;
+  cudaStream_t st = s->st;
+  const double eps = s->p.eps;
+  AppendParams ap;
+  ap.lo2 = (float)((1.0 - eps) * (1.0 - eps));
+  ap.hi2 = (float)((1.0 + eps) * (1.0 + eps));
+  ap.bound2 = (1.0 + eps) * (1.0 + eps);
+  ap.delta_nn = s->p.delta_nn;
+  ap.h = s->p.fd_step;
+  ap.t_low = s->p.t_low_confid;
+  int counts[kAppCounts];
+  SW_CUDA(s, launch_append_candidates(h, a, st));
+  SW_CUDA(s, cudaMemcpyAsync(counts, a.counts, sizeof(counts), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(s, cudaStreamSynchronize(st));
+  const int n_cand = counts[kAppNCand];
+  SW_CUDA(s, launch_append_eval(h, a, ap, n_cand, st));
+  SW_CUDA(s, launch_append_removal(h, a, ap.t_low, st));
+  SW_CUDA(s, cudaMemcpyAsync(counts, a.counts, sizeof(counts), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(s, cudaStreamSynchronize(st));
+  const int n_stay = counts[kAppNStay];
+  const int n_app = std::min(counts[kAppNAcc], std::max(0, s->p.max_surfels - n_stay));
+  const int n_new = n_stay + n_app, n_old = h.n_s;
+  {
+    const size_t n = std::max(1, n_new), m = std::max(1, n_app);
+    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(m * 16), d2(m * 16);
+    if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p)
+      return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
+    launch_append_compose(h, a, s->knn_dist, s->w_dist, n_stay, n_app, tv.as<float4>(), tn.as<float4>(),
+                          tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(), st);
+    launch_knn_skin(h, tv.as<float4>() + n_stay, n_app, ids.as<int>(), d2.as<float>(), tknn.as<int4>() + n_stay,
+                    tw.as<float4>() + n_stay, st);
+    SW_CUDA(s, cudaGetLastError());
+    SW_CUDA(s, cudaStreamSynchronize(st));
+    // the model's layout changes: rebuild its structure (nodes and transforms stay)
+    s->has_model = false;
+    if (s->run) drop_graphs(s->run);
+    free_list(s->model_allocs);
+    s->version++;
+    h.n_s = n_new;
+    std::vector<int4> sets;
+    SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
+                         n_new, sets));
+    SW_TRY(install_pattern(s, sets));
+  }
+  s->fused = false;
+  s->app_last_cand = n_cand;
+  if (stats) {
+    stats->candidates = n_cand;
+    stats->rejected_nn = counts[kAppNLow];
+    stats->rejected_strain = counts[kAppNComp];
+    stats->appended = n_app;
+    stats->removed = n_old - n_stay;
+    stats->n_surfels = n_new;
+  }
+  return SW_OK;
+}
+
+sw_status sw_debug_read_append(sw_handle s, int* pix, int* knn4, int* flags, double* wsum, double* strain9,
+                               float* w4, float* v4, float* n4, int cap, int* n_out) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->app_ready) return fail(s, SW_ERR_NOT_INITIALIZED, "no appending step has run");
+  const int n = s->app_last_cand;
+  if (n_out) *n_out = n;
+  if (!pix && !knn4 && !flags && !wsum && !strain9 && !w4 && !v4 && !n4) return SW_OK;   // count only
+  if (cap < n) return fail(s, SW_ERR_INVALID_ARG, "capacity too small");
+  const AppendBufs& a = s->app;
+  auto get = [&](void* dst, const void* src, size_t bytes) -> sw_status {
+    if (dst && bytes) SW_CUDA(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
+    return SW_OK;
+  };
+  SW_TRY(get(pix, a.cand, (size_t)n * 4));
+  SW_TRY(get(knn4, a.knn, (size_t)n * 16));
+  SW_TRY(get(flags, a.flags, (size_t)n * 4));
+  SW_TRY(get(wsum, a.wsum, (size_t)n * 8));
+  SW_TRY(get(strain9, a.strain, (size_t)n * 72));
+  SW_TRY(get(w4, a.w, (size_t)n * 16));
+  SW_TRY(get(v4, a.v, (size_t)n * 16));
+  SW_TRY(get(n4, a.n, (size_t)n * 16));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
   return SW_OK;
 }
 
@@ -1469,6 +1622,7 @@ sw_status sw_batch_upload_depth(sw_batch_handle b, const float* const* depths, i
     SW_CUDA(nullptr, cudaMemcpyAsync(m->h.depth, depths[i], bytes,
                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, r->st));
     m->has_depth = true;
+    m->fused = false;
   }
   SW_CUDA(nullptr, ring_copy(r, r->frames_dev, frame_ids, n));
   k_set_frames<<<(n + 127) / 128, 128, 0, r->st>>>(r->bh.bt, r->frames_dev);
@@ -1518,6 +1672,8 @@ sw_status sw_batch_fuse(sw_batch_handle b) {
   SW_TRY(batch_check(b));
   batch_enter(b);
   SW_TRY(runner_fuse(&b->run, nullptr));
+  for (size_t i = 0; i < b->run.members.size(); ++i)
+    if (b->run.active_host[i]) b->run.members[i]->fused = true;
   batch_leave(b);
   return SW_OK;
 }

@@ -1,0 +1,295 @@
+// Surfel appending after fusion: live skinning with the consistency test of
+// Eq. 7 (Sec. 6.2), the compressive-warp bound of Eq. 8 (Sec. 6.3), the
+// weight-sum test, appending and the removal of unstable surfels (Sec. 6.4),
+// and the GPU selection that compacts the surfel array (Sec. 6.6).
+//
+//   k_live_nodes    p̂_j = T_j p_j in FP64, rounded to FP32 (the precision the
+//                   k-NN and Eq. 7 decide in); w carries σ_j.
+//   k_cand_flags    a pixel is a candidate when fusion found it usable with
+//                   an empty window (kTargetEmptyWindow).
+//   scan + scatter  candidate pixels in row-major order (an exclusive scan of
+//                   the flags, then a scatter: order-preserving, deterministic).
+//   k_cand_queries  the candidates' depth vertices, for the skinning k-NN
+//                   kernel (4 nearest warped nodes, FP32 distances in a fixed
+//                   order, ties to the lower id; slot 0 is node_0).
+//   k_append_eval   one thread per candidate:
+//                     Eq. 7 on squares in exact-order FP32:
+//                       (1−ε)² d_ref² < d_live² < (1+ε)² d_ref²;
+//                     weights at the live frame, w_i = exp(−‖x − p̂_i‖²/2σ_i²)
+//                     for the nodes that stay (FP64); the weight-sum test;
+//                     the blend (signs against node_0, Eq. 1) and the inverse
+//                     warp (Eq. 3) of the depth vertex and normal (FP64);
+//                     the strain ∂x_ref/∂x_live by central differences with
+//                     the node set and signs held and the weights
+//                     re-evaluated; Eq. 8 as λ_max(JᵀJ) < (1+ε)², i.e.
+//                     (1+ε)² I − JᵀJ positive definite, read off the pivots
+//                     of its LDLᵀ factorisation.
+//   k_stay_flags    an existing surfel stays unless c < δ_stable and
+//                   t_now − t_init ≥ t_low_confid (flag at its caller index).
+//   k_compose_*     the new model in caller order: the survivors in their
+//                   order, then the accepted candidates in pixel order.
+#include <cub/cub.cuh>
+
+#include "sw_internal.h"
+#include "sw_math.cuh"
+#include "sw_math64.cuh"
+
+namespace sw {
+namespace {
+
+__device__ __forceinline__ DQ64 node_dq64(const SwDev& d, int j) {
+  if (d.dq64) return load_dq64(d.dq64, j);
+  const float4 a = d.dq[2 * j], b = d.dq[2 * j + 1];
+  return DQ64{a.x, D3{a.y, a.z, a.w}, b.x, D3{b.y, b.z, b.w}};
+}
+
+// R⁻¹ y for the rotation of the normalised real part: conjugate (W, −A)
+__device__ __forceinline__ D3 inv_rotate64(const DQ64& b, double inv_n2, D3 y) {
+  const D3 axy = cross3(b.A, y);
+  return y + (2.0 * inv_n2) * (cross3(b.A, axy) - b.W * axy);
+}
+
+__device__ __forceinline__ double comp(const D3& v, int a) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
+
+// The live skinning of one candidate: its 4 nodes' transforms with the signs
+// of Eq. 1 folded in, their warped positions, σ and which of them Eq. 7 keeps.
+struct LiveSkin {
+  DQ64 q[4];
+  D3 p[4];
+  double s[4];
+  bool keep[4];
+
+  __device__ double weights(D3 x, double* w) const {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const D3 e = x - p[k];
+      w[k] = keep[k] ? exp(-dot3(e, e) / (2.0 * s[k] * s[k])) : 0.0;
+      sum += w[k];
+    }
+    return sum;
+  }
+  // x_ref = b⁻¹ x with b = Σ w_k q_k; an all-zero blend leaves the point in place
+  __device__ D3 inverse(D3 x, const double* w, D3* n_in = nullptr, D3* n_out = nullptr) const {
+    DQ64 b{0.0, D3{0.0, 0.0, 0.0}, 0.0, D3{0.0, 0.0, 0.0}};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      b.W += w[k] * q[k].W; b.A = b.A + w[k] * q[k].A;
+      b.We += w[k] * q[k].We; b.Ae = b.Ae + w[k] * q[k].Ae;
+    }
+    const double n2 = dq_norm2(b);
+    if (!(n2 > 0.0)) {
+      if (n_out) *n_out = *n_in;
+      return x;
+    }
+    const double inv = 1.0 / n2;
+    if (n_out) *n_out = inv_rotate64(b, inv, *n_in);
+    return inv_rotate64(b, inv, x - dq_translation(b, inv));
+  }
+};
+
+__global__ void k_live_nodes(SwDev d, float4* __restrict__ live) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.n_n) return;
+  const DQ64 q = node_dq64(d, j);
+  const float4 p = d.node_p[j];
+  const double n2 = dq_norm2(q);
+  const D3 y = n2 > 0.0 ? dq_transform(q, 1.0 / n2, d3(p)) : d3(p);
+  live[j] = make_float4((float)y.x, (float)y.y, (float)y.z, p.w);
+}
+
+__global__ void k_cand_flags(SwDev d, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.W * d.H) flag[i] = d.fuse_target[i] == kTargetEmptyWindow ? 1 : 0;
+}
+
+__global__ void k_acc_flags(AppendBufs a, int n_cand, int* __restrict__ flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_cand) flag[c] = (a.flags[c] & kAppAccepted) ? 1 : 0;
+}
+
+// out[pos[i]] = i for flagged i; the count goes to *count
+__global__ void k_scatter(const int* __restrict__ flag, const int* __restrict__ pos, int n, int* __restrict__ out,
+                          int* __restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (flag[i] && out) out[pos[i]] = i;
+  if (i == n - 1) *count = pos[i] + flag[i];
+}
+
+__global__ void k_cand_queries(SwDev d, AppendBufs a, int n_cand) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_cand) a.query[c] = d.vmap[a.cand[c]];
+}
+
+__global__ void __launch_bounds__(128) k_append_eval(SwDev d, AppendBufs a, AppendParams ap, int n_cand) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cand) return;
+  const int pix = a.cand[c];
+  const float4 V = d.vmap[pix], N = d.nmap[pix];
+  int id[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) id[k] = a.knn[4 * c + k];
+  LiveSkin sk;
+  int flags = 1;
+  {   // Eq. 7 on squares, exact-order FP32; node_0 always stays
+    const float4 l0 = a.live[id[0]], r0 = d.node_p[id[0]];
+    sk.keep[0] = true;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      const float4 l = a.live[id[k]], r = d.node_p[id[k]];
+      const float dl = dist2_rn(l.x, l.y, l.z, l0.x, l0.y, l0.z);
+      const float dr = dist2_rn(r.x, r.y, r.z, r0.x, r0.y, r0.z);
+      sk.keep[k] = dl > __fmul_rn(ap.lo2, dr) && dl < __fmul_rn(ap.hi2, dr);
+      if (sk.keep[k]) flags |= 1 << k;
+    }
+  }
+  const DQ64 q0 = node_dq64(d, id[0]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    DQ64 q = node_dq64(d, id[k]);
+    if (q.W * q0.W + dot3(q.A, q0.A) < 0.0) {   // sign of Eq. 1 against node_0, sign(0) = +1
+      q.W = -q.W; q.A = -1.0 * q.A; q.We = -q.We; q.Ae = -1.0 * q.Ae;
+    }
+    sk.q[k] = q;
+    const float4 l = a.live[id[k]];
+    sk.p[k] = d3(l);
+    sk.s[k] = (double)l.w;
+  }
+  const D3 x = d3(V);
+  D3 n_in = d3(N), n_ref;
+  double w[4];
+  const double wsum = sk.weights(x, w);
+  const D3 v_ref = sk.inverse(x, w, &n_in, &n_ref);
+  // strain: column e is (x_ref(x + h e) − x_ref(x − h e)) / 2h
+  double J[9];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const D3 de = D3{e == 0 ? ap.h : 0.0, e == 1 ? ap.h : 0.0, e == 2 ? ap.h : 0.0};
+    double wp[4], wm[4];
+    const D3 xp = x + de, xm = x - de;
+    sk.weights(xp, wp);
+    sk.weights(xm, wm);
+    const D3 yp = sk.inverse(xp, wp), ym = sk.inverse(xm, wm);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) J[3 * r + e] = (comp(yp, r) - comp(ym, r)) / (2.0 * ap.h);
+  }
+  // Eq. 8: M = (1+ε)² I − JᵀJ must be positive definite (LDLᵀ pivots > 0)
+  double S[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S[i][j] = J[i] * J[j] + J[3 + i] * J[3 + j] + J[6 + i] * J[6 + j];
+  const double m00 = ap.bound2 - S[0][0], m11 = ap.bound2 - S[1][1], m22 = ap.bound2 - S[2][2];
+  const double m10 = -S[1][0], m20 = -S[2][0], m21 = -S[2][1];
+  bool pd = m00 > 0.0;
+  if (pd) {
+    const double d1 = m11 - m10 * m10 / m00;
+    pd = d1 > 0.0;
+    if (pd) {
+      const double l21 = (m21 - m20 * m10 / m00) / d1;
+      const double d2 = m22 - m20 * m20 / m00 - l21 * l21 * d1;
+      pd = d2 > 0.0;
+    }
+  }
+  const bool low = !(wsum >= ap.delta_nn);
+  const bool compressive = !pd;
+  if (low) { flags |= kAppLowWeight; atomicAdd(a.counts + kAppNLow, 1); }
+  if (compressive) { flags |= kAppCompressive; atomicAdd(a.counts + kAppNComp, 1); }
+  if (!low && !compressive) flags |= kAppAccepted;
+  a.flags[c] = flags;
+  a.wsum[c] = wsum;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a.strain[9 * (size_t)c + k] = J[k];
+  a.w[c] = make_float4((float)w[0], (float)w[1], (float)w[2], (float)w[3]);
+  a.v[c] = make_float4((float)v_ref.x, (float)v_ref.y, (float)v_ref.z, N.w);
+  a.n[c] = make_float4((float)n_ref.x, (float)n_ref.y, (float)n_ref.z, V.w);
+}
+
+__global__ void k_stay_flags(SwDev d, int t_low, int* __restrict__ stay) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_s) return;
+  const float c = d.n_ref[i].w;
+  const int age = *d.t_now - d.tt[i].x;
+  stay[d.orig_id[i]] = (c < d.stable_conf && age >= t_low) ? 0 : 1;
+}
+
+__global__ void k_compose_stay(SwDev d, AppendBufs a, const int4* __restrict__ knn_dist,
+                               const float4* __restrict__ w_dist, float4* tv, float4* tn, int2* tt, int4* tknn,
+                               float4* tw) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= d.n_s || !a.stay[o]) return;
+  const int j = a.pos[o], i = d.inv_perm[o];
+  tv[j] = d.v_ref[i];
+  tn[j] = d.n_ref[i];
+  tt[j] = d.tt[i];
+  tknn[j] = knn_dist[o];
+  tw[j] = w_dist[o];
+}
+
+__global__ void k_compose_app(SwDev d, AppendBufs a, int n_stay, int n_app, float4* tv, float4* tn, int2* tt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_app) return;
+  const int c = a.acc[k], j = n_stay + k;
+  tv[j] = a.v[c];
+  tn[j] = a.n[c];
+  const int t = *d.t_now;
+  tt[j] = make_int2(t, t);
+}
+
+inline int blocks(int n, int t) { return (n + t - 1) / t; }
+
+// order-preserving compaction of flag[0, n): out[k] = k-th flagged index
+cudaError_t compact(const AppendBufs& a, const int* flag, int n, int* out, int* count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+  if (e != cudaSuccess || n == 0) return e;
+  size_t bytes = a.cub_bytes;
+  e = cub::DeviceScan::ExclusiveSum(a.cub_tmp, bytes, flag, a.pos, n, st);
+  if (e != cudaSuccess) return e;
+  k_scatter<<<blocks(n, 256), 256, 0, st>>>(flag, a.pos, n, out, count);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t append_cub_bytes(int n_pixels, int n_surfels) {
+  size_t bytes = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, bytes, (const int*)nullptr, (int*)nullptr, std::max(n_pixels, n_surfels));
+  return bytes;
+}
+
+// Steps up to the candidate list: warped nodes, candidate pixels (count in
+// counts[kAppNCand]) and their depth vertices are left in `a`.
+cudaError_t launch_append_candidates(const SwDev& d, const AppendBufs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.counts, 0, kAppCounts * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  if (d.n_n) k_live_nodes<<<blocks(d.n_n, 128), 128, 0, st>>>(d, a.live);
+  const int np = d.W * d.H;
+  k_cand_flags<<<blocks(np, 256), 256, 0, st>>>(d, a.stay);
+  return compact(a, a.stay, np, a.cand, a.counts + kAppNCand, st);
+}
+
+cudaError_t launch_append_eval(const SwDev& d, const AppendBufs& a, const AppendParams& ap, int n_cand,
+                               cudaStream_t st) {
+  if (n_cand == 0) return cudaMemsetAsync(a.counts + kAppNAcc, 0, sizeof(int), st);
+  k_cand_queries<<<blocks(n_cand, 256), 256, 0, st>>>(d, a, n_cand);
+  launch_knn4(a.query, n_cand, a.live, d.n_n, a.knn, st);
+  k_append_eval<<<blocks(n_cand, 128), 128, 0, st>>>(d, a, ap, n_cand);
+  k_acc_flags<<<blocks(n_cand, 256), 256, 0, st>>>(a, n_cand, a.stay);
+  return compact(a, a.stay, n_cand, a.acc, a.counts + kAppNAcc, st);
+}
+
+// stay flags in caller order and the survivors' new indices (count in counts[kAppNStay])
+cudaError_t launch_append_removal(const SwDev& d, const AppendBufs& a, int t_low, cudaStream_t st) {
+  if (d.n_s) k_stay_flags<<<blocks(d.n_s, 256), 256, 0, st>>>(d, t_low, a.stay);
+  return compact(a, a.stay, d.n_s, nullptr, a.counts + kAppNStay, st);
+}
+
+void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_dist, const float4* w_dist,
+                           int n_stay, int n_app, float4* tv, float4* tn, int2* tt, int4* tknn, float4* tw,
+                           cudaStream_t st) {
+  if (d.n_s) k_compose_stay<<<blocks(d.n_s, 256), 256, 0, st>>>(d, a, knn_dist, w_dist, tv, tn, tt, tknn, tw);
+  if (n_app) k_compose_app<<<blocks(n_app, 256), 256, 0, st>>>(d, a, n_stay, n_app, tv, tn, tt);
+}
+
+}  // namespace sw

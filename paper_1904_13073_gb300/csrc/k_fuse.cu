@@ -14,6 +14,8 @@
 //                 t_observed and warps it back to the reference frame with
 //                 its own skinning (Eq. 3).  Every surfel belongs to exactly
 //                 one pixel's window, so no two threads update one surfel.
+//                 A usable pixel whose window held no surfel at all is marked
+//                 kTargetEmptyWindow: the appending step's candidates.
 #include "sw_internal.h"
 #include "sw_math.cuh"
 
@@ -82,8 +84,12 @@ __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
   // for the next frame, so the map is cleared once at creation and never again.
   unsigned long long* row0 = d.imap + (size_t)(4 * y) * (4 * d.W) + 4 * x;
   unsigned long long keys[16];
+  bool empty = true;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) keys[k] = row0[(size_t)(k >> 2) * (4 * d.W) + (k & 3)];
+  for (int k = 0; k < 16; ++k) {
+    keys[k] = row0[(size_t)(k >> 2) * (4 * d.W) + (k & 3)];
+    empty = empty && keys[k] == kEmpty;
+  }
   if (!select_only) {
 #pragma unroll
     for (int k = 0; k < 16; ++k)
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
       d.tt[best].y = *d.t_now;
     }
   }
-  d.fuse_target[pix] = best;
+  d.fuse_target[pix] = best >= 0 ? best : (V.w > 0.f && empty ? kTargetEmptyWindow : kTargetNone);
 }
 
 inline Batch with_kind(const BatchHost& b, int kind) {

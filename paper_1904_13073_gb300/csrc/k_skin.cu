@@ -91,6 +91,11 @@ void launch_knn_skin(const SwDev& d, const float4* v_orig, int n_s, int* ids, fl
   k_skin_weights<<<(n_s + 255) / 256, 256, 0, st>>>(d2, ids, d.node_p, n_s, knn_out, w_out);
 }
 
+void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st) {
+  if (n_q == 0) return;
+  k_knn<4><<<(n_q + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(queries, n_q, nodes, n_n, 0, ids, nullptr);
+}
+
 void launch_node_graph(const SwDev& d, cudaStream_t st) {
   k_knn<8><<<(d.n_n + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(d.node_p, d.n_n, d.node_p, d.n_n, 1,
                                                                        d.graph, nullptr);

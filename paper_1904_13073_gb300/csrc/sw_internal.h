@@ -21,6 +21,10 @@ constexpr int kMaxRigid = SW_MAX_RIGID_ITERS;
 constexpr int kRigidSlots = 16;          // rigid pre-alignment state: T (8), stopped flag, spare
 constexpr int kRigidSums = 29;           // per surfel tile: 21 (J Jᵀ upper) + 6 (J r) + count + Σ r²
 
+// fusion result of a pixel without a target surfel
+constexpr int kTargetNone = -1;          // its window held surfels, none passed the tests (or unusable)
+constexpr int kTargetEmptyWindow = -2;   // usable, and its window held no surfel: an append candidate
+
 // status bits written by kernels
 constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive definite, or pᵀAp <= 0
 constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
@@ -69,7 +73,7 @@ struct SwDev {
   float4* vmap;       // V(u) and the depth-surfel confidence (0 if unusable)
   float4* nmap;       // N(u) and the depth-surfel radius
   unsigned long long* imap;  // 4W x 4H: (z bits << 32) | caller's surfel index
-  int* fuse_target;   // per pixel: internal surfel index or -1
+  int* fuse_target;   // per pixel: internal surfel index, kTargetNone or kTargetEmptyWindow
   // block-sparse JᵀJ (upper triangle incl. diagonal, 6x6 blocks, row-major)
   int* row_ptr;       // n_n + 1; the diagonal block leads its row
   int* col;           // nnzb
@@ -170,6 +174,47 @@ size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
 sw_status batch_member_status(sw_batch_handle b, int* status);
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
                                  int* status, cudaStream_t st);
+
+// ------------------------------------------------------------------ appending
+// Per-candidate records and scratch of the appending step (k_append.cu),
+// owned by the stream and sized for W·H candidates.
+struct AppendBufs {
+  float4* live;       // n_n warped nodes: T_j p_j rounded to FP32, w = σ_j
+  int* cand;          // candidate pixels, row-major order
+  float4* query;      // the candidates' depth vertices
+  int* knn;           // 4 per candidate: nearest warped nodes, distance order
+  int* flags;         // per candidate: bits 0-3 the nodes Eq. 7 keeps, then kApp* bits
+  double* wsum;       // Σ of the live weights
+  double* strain;     // 9 per candidate: ∂x_ref/∂x_live, row-major
+  float4* w;          // the live weights (0 for removed nodes)
+  float4* v;          // v_ref and the depth surfel's radius
+  float4* n;          // n_ref and the depth surfel's confidence
+  int* acc;           // accepted candidates, in candidate order
+  int* stay;          // per existing surfel, caller order: 1 if it stays
+  int* pos;           // its new caller index (exclusive scan of stay)
+  int* counts;        // kAppCounts device counters
+  void* cub_tmp;      // selection / scan scratch
+  size_t cub_bytes;
+};
+constexpr int kAppAccepted = 16, kAppLowWeight = 32, kAppCompressive = 64;
+enum AppCount { kAppNCand = 0, kAppNAcc, kAppNLow, kAppNComp, kAppNStay, kAppCounts = 8 };
+struct AppendParams {
+  float lo2, hi2;     // (1 − ε)², (1 + ε)² rounded to FP32 (Eq. 7 on squares)
+  double bound2;      // (1 + ε)² (Eq. 8 on λ_max(JᵀJ))
+  double delta_nn;    // weight-sum threshold
+  double h;           // finite-difference step of the strain, metres
+  int t_low;          // t_low_confid
+};
+size_t append_cub_bytes(int n_pixels, int n_surfels);
+cudaError_t launch_append_candidates(const SwDev& d, const AppendBufs& a, cudaStream_t st);
+cudaError_t launch_append_eval(const SwDev& d, const AppendBufs& a, const AppendParams& ap, int n_cand,
+                               cudaStream_t st);
+cudaError_t launch_append_removal(const SwDev& d, const AppendBufs& a, int t_low, cudaStream_t st);
+// the new model in caller order: survivors, then the first n_app accepted candidates
+void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_dist, const float4* w_dist,
+                           int n_stay, int n_app, float4* tv, float4* tn, int2* tt, int4* tknn, float4* tw,
+                           cudaStream_t st);
+void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st);
 
 // tile sizes
 constexpr int kSurfTile = 256;
