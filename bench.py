@@ -624,7 +624,34 @@ def main():
              "correspondences": [int(n) for n, _ in rig_stats],
              "bytes_per_iteration": rig_bytes, "achieved_gbs": rig_bytes / rigid_it_us / 1e3,
              "frac": rig_bytes / rigid_it_us / 1e3 / peak}
+    # appending (a separate call after fusion, not part of the configuration's
+    # frame): steady state on the full model, where the candidates are the
+    # few pixels no surfel covers, frame after frame; the first call loads
+    # the kernels and is not reported
     sw.sw_destroy_stream(h)
+    room = len(v4) + c.width * c.height
+
+    def append_case(keep, n_calls):
+        ha = sw.sw_create_stream(sw.params_for(c, room, len(node4)), stream)
+        sw.sw_set_model(ha, v4[keep], n4[keep], t2[keep], node4)
+        out = []
+        for k in range(n_calls):
+            sw.sw_upload_depth(ha, dev_frames[ts[k]], k + 1)
+            sw.sw_solve_frame(ha, gn, pcg)
+            sw.sw_fuse_frame(ha)
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            a_st = sw.sw_append_frame(ha)
+            a_st["call_ms"] = 1000.0 * (time.perf_counter() - a0)
+            out.append(a_st)
+        sw.sw_destroy_stream(ha)
+        return out
+    appends = append_case(np.ones(len(v4), bool), 3)
+    # and a model with 30% of its surfels cut away (the early-frame regime)
+    cut_st = append_case(scene.surfel_v[:, 0] < np.quantile(scene.surfel_v[:, 0], 0.7), 1)[0]
+    appending = {"steady": appends[1:], "model_cut_30pct": cut_st,
+                 "note": "kernel_ms: device time of the appending kernels (events); rebuild_ms: host-side "
+                         "model rebuild (set sort, JtJ pattern, runner); call_ms: the whole call"}
     batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
         if members and args.batch_streams > 0 else None
     served = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
@@ -654,6 +681,7 @@ def main():
         "stage_roofline": roof["stages"],
         "autotune": {"pcg_rows_per_cta": tuned_rows, "pcg_us_per_launch": tuned_us},
         "rigid_align": rigid,
+        "appending": appending,
     }
     if batched:
         line["multi_stream"] = batched

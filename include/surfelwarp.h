@@ -422,6 +422,8 @@ typedef struct {
   int appended;          /* surfels added */
   int removed;           /* unstable surfels removed */
   int n_surfels;         /* surfels after the call */
+  double kernel_ms;      /* device time of the appending kernels (CUDA events), model rebuild excluded */
+  double rebuild_ms;     /* host time of the model rebuild (set sort, JᵀJ pattern, runner) */
 } sw_append_stats;
 sw_status sw_append_frame(sw_handle h, sw_append_stats* stats);
 /* Per-candidate record of the last sw_append_frame, candidate order (row-

@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <chrono>
+
 #include <cuda.h>   // CUtensorMap and its encoder's signature; the encoder itself comes from the runtime's
                     // driver entry-point query, so the library does not link the driver library
 
@@ -1329,6 +1331,8 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
   ap.h = s->p.fd_step;
   ap.t_low = s->p.t_low_confid;
   int counts[kAppCounts];
+  cudaEvent_t ev0 = take_event(s->run), ev1 = take_event(s->run);
+  SW_CUDA(s, cudaEventRecord(ev0, st));
   SW_CUDA(s, launch_append_candidates(h, a, st));
   SW_CUDA(s, cudaMemcpyAsync(counts, a.counts, sizeof(counts), cudaMemcpyDeviceToHost, st));
   SW_CUDA(s, cudaStreamSynchronize(st));
@@ -1340,6 +1344,27 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
   const int n_stay = counts[kAppNStay];
   const int n_app = std::min(counts[kAppNAcc], std::max(0, s->p.max_surfels - n_stay));
   const int n_new = n_stay + n_app, n_old = h.n_s;
+  if (stats) {
+    stats->candidates = n_cand;
+    stats->rejected_nn = counts[kAppNLow];
+    stats->rejected_strain = counts[kAppNComp];
+    stats->appended = n_app;
+    stats->removed = n_old - n_stay;
+    stats->n_surfels = n_new;
+    stats->kernel_ms = stats->rebuild_ms = 0.0;
+  }
+  s->app_last_cand = n_cand;
+  if (n_app == 0 && n_stay == n_old) {   // nothing appended or removed: the model stands as it is
+    SW_CUDA(s, cudaEventRecord(ev1, st));
+    SW_CUDA(s, cudaEventSynchronize(ev1));
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (stats) stats->kernel_ms = kms;
+    s->fused = false;
+    return SW_OK;
+  }
   {
     const size_t n = std::max(1, n_new), m = std::max(1, n_app);
     Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(m * 16), d2(m * 16);
@@ -1350,7 +1375,14 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     launch_knn_skin(h, tv.as<float4>() + n_stay, n_app, ids.as<int>(), d2.as<float>(), tknn.as<int4>() + n_stay,
                     tw.as<float4>() + n_stay, st);
     SW_CUDA(s, cudaGetLastError());
+    SW_CUDA(s, cudaEventRecord(ev1, st));
     SW_CUDA(s, cudaStreamSynchronize(st));
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (stats) stats->kernel_ms = kms;
+    const auto t0 = std::chrono::steady_clock::now();
     // the model's layout changes: rebuild its structure (nodes and transforms stay)
     s->has_model = false;
     if (s->run) drop_graphs(s->run);
@@ -1361,17 +1393,9 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets));
     SW_TRY(install_pattern(s, sets));
+    if (stats) stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   s->fused = false;
-  s->app_last_cand = n_cand;
-  if (stats) {
-    stats->candidates = n_cand;
-    stats->rejected_nn = counts[kAppNLow];
-    stats->rejected_strain = counts[kAppNComp];
-    stats->appended = n_app;
-    stats->removed = n_old - n_stay;
-    stats->n_surfels = n_new;
-  }
   return SW_OK;
 }
 

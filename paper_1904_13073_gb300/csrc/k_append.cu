@@ -122,7 +122,7 @@ __global__ void k_cand_queries(SwDev d, AppendBufs a, int n_cand) {
   if (c < n_cand) a.query[c] = d.vmap[a.cand[c]];
 }
 
-__global__ void __launch_bounds__(128) k_append_eval(SwDev d, AppendBufs a, AppendParams ap, int n_cand) {
+__global__ void __launch_bounds__(64) k_append_eval(SwDev d, AppendBufs a, AppendParams ap, int n_cand) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cand) return;
   const int pix = a.cand[c];
@@ -274,7 +274,7 @@ cudaError_t launch_append_eval(const SwDev& d, const AppendBufs& a, const Append
   if (n_cand == 0) return cudaMemsetAsync(a.counts + kAppNAcc, 0, sizeof(int), st);
   k_cand_queries<<<blocks(n_cand, 256), 256, 0, st>>>(d, a, n_cand);
   launch_knn4(a.query, n_cand, a.live, d.n_n, a.knn, st);
-  k_append_eval<<<blocks(n_cand, 128), 128, 0, st>>>(d, a, ap, n_cand);
+  k_append_eval<<<blocks(n_cand, 64), 64, 0, st>>>(d, a, ap, n_cand);   // small CTAs: spread over every SM
   k_acc_flags<<<blocks(n_cand, 256), 256, 0, st>>>(a, n_cand, a.stay);
   return compact(a, a.stay, n_cand, a.acc, a.counts + kAppNAcc, st);
 }

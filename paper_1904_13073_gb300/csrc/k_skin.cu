@@ -64,6 +64,84 @@ k_knn(const float4* __restrict__ queries, int n_q, const float4* __restrict__ no
   }
 }
 
+// (d, i) < (e, j) in the order of the selection: distance, then node id
+__device__ __forceinline__ bool knn_less(float d, int i, float e, int j) { return d < e || (d == e && i < j); }
+
+__device__ __forceinline__ void knn_cswap(float* d, int* i, int a, int b) {
+  if (knn_less(d[b], i[b], d[a], i[a])) {
+    const float td = d[a]; d[a] = d[b]; d[b] = td;
+    const int ti = i[a]; i[a] = i[b]; i[b] = ti;
+  }
+}
+
+// The same selection with one warp per query, for few queries: lane l scans
+// nodes l, l + 32, ... and keeps its own 4 best; five butterfly rounds merge
+// the lanes' sorted lists (the lower half of a bitonic merge, c_k =
+// min(a_k, b_{3-k}), then a 4-element bitonic sort), so every lane ends with
+// the 4 smallest (d², id) of all nodes: the same unique result as k_knn<4>.
+__global__ void __launch_bounds__(kQThreads)
+k_knn4_warp(const float4* __restrict__ queries, int n_q, const float4* __restrict__ nodes, int n_n,
+            int* __restrict__ out_ids, float* __restrict__ out_d2) {
+  const int qi = (blockIdx.x * kQThreads + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (qi >= n_q) return;   // uniform across the warp
+  const float3 q = f3(queries[qi]);
+  float bd[4];
+  int bi[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0x7fffffff; }
+  for (int j = lane; j < n_n; j += 32) {
+    const float4 p = __ldg(nodes + j);
+    float cd = dist2_rn(q.x, q.y, q.z, p.x, p.y, p.z);
+    int ci = j;
+    if (knn_less(cd, ci, bd[3], bi[3])) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (knn_less(cd, ci, bd[k], bi[k])) {
+          const float td = bd[k]; const int ti = bi[k];
+          bd[k] = cd; bi[k] = ci;
+          cd = td; ci = ti;
+        }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float od[4];
+    int oi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      od[k] = __shfl_xor_sync(0xffffffffu, bd[k], o);
+      oi[k] = __shfl_xor_sync(0xffffffffu, bi[k], o);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (knn_less(od[3 - k], oi[3 - k], bd[k], bi[k])) { bd[k] = od[3 - k]; bi[k] = oi[3 - k]; }
+    knn_cswap(bd, bi, 0, 2);
+    knn_cswap(bd, bi, 1, 3);
+    knn_cswap(bd, bi, 0, 1);
+    knn_cswap(bd, bi, 2, 3);
+  }
+  if (lane < 4) {
+    int id = bi[0];
+    float d = bd[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+      if (lane == k) { id = bi[k]; d = bd[k]; }
+    out_ids[(size_t)qi * 4 + lane] = id;
+    if (out_d2) out_d2[(size_t)qi * 4 + lane] = d;
+  }
+}
+
+// queries up to which a warp per query beats a thread per query (fills the GPU)
+constexpr int kWarpKnnMaxQueries = 40000;
+
+void knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, float* d2, cudaStream_t st) {
+  if (n_q <= kWarpKnnMaxQueries)
+    k_knn4_warp<<<(int)(((size_t)n_q * 32 + kQThreads - 1) / kQThreads), kQThreads, 0, st>>>(queries, n_q, nodes,
+                                                                                              n_n, ids, d2);
+  else
+    k_knn<4><<<(n_q + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(queries, n_q, nodes, n_n, 0, ids, d2);
+}
+
 __global__ void k_skin_weights(const float* __restrict__ d2, const int* __restrict__ ids,
                                const float4* __restrict__ nodes, int n_q,
                                int4* __restrict__ knn_out, float4* __restrict__ w_out) {
@@ -87,13 +165,13 @@ __global__ void k_skin_weights(const float* __restrict__ d2, const int* __restri
 void launch_knn_skin(const SwDev& d, const float4* v_orig, int n_s, int* ids, float* d2, int4* knn_out,
                      float4* w_out, cudaStream_t st) {
   if (n_s == 0) return;
-  k_knn<4><<<(n_s + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(v_orig, n_s, d.node_p, d.n_n, 0, ids, d2);
+  knn4(v_orig, n_s, d.node_p, d.n_n, ids, d2, st);
   k_skin_weights<<<(n_s + 255) / 256, 256, 0, st>>>(d2, ids, d.node_p, n_s, knn_out, w_out);
 }
 
 void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st) {
   if (n_q == 0) return;
-  k_knn<4><<<(n_q + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(queries, n_q, nodes, n_n, 0, ids, nullptr);
+  knn4(queries, n_q, nodes, n_n, ids, nullptr, st);
 }
 
 void launch_node_graph(const SwDev& d, cudaStream_t st) {
