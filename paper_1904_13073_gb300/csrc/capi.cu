@@ -800,98 +800,40 @@ namespace {
 // temporary device buffer freed at scope exit (set-up only)
 struct Tmp {
   void* p = nullptr;
-  explicit Tmp(size_t bytes) { if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) p = nullptr; }
+  Tmp() = default;
+  explicit Tmp(size_t bytes) { alloc(bytes); }
+  Tmp(const Tmp&) = delete;
+  Tmp& operator=(const Tmp&) = delete;
   ~Tmp() { if (p) cudaFree(p); }
+  bool alloc(size_t bytes) {
+    if (p) cudaFree(p);
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) p = nullptr;
+    return p != nullptr;
+  }
   template <typename T> T* as() { return reinterpret_cast<T*>(p); }
 };
 
-struct Pattern {
-  std::vector<int> row_ptr, col, blk_row, blk_edge, rl_ptr, in_ptr, in_src, set_slots;
-  std::vector<int2> rl_ent;
-};
-
-// Block-sparse pattern of JᵀJ: upper blocks (a <= b) of every node pair that
-// shares a surfel's 4-node set, every graph edge and every diagonal block.
-bool build_pattern(int n_n, const std::vector<int4>& sets, const std::vector<int>& graph, Pattern& P,
-                   std::string& why) {
-  std::vector<uint32_t> keys;
-  keys.reserve(sets.size() * 10 + (size_t)n_n * 9);
-  for (int j = 0; j < n_n; ++j) keys.push_back(((uint32_t)j << 16) | (uint32_t)j);
-  for (const int4& s : sets) {
-    const int id[4] = {s.x, s.y, s.z, s.w};
-    for (int a = 0; a < 4; ++a)
-      for (int b = a; b < 4; ++b) keys.push_back(((uint32_t)id[a] << 16) | (uint32_t)id[b]);
-  }
-  for (int j = 0; j < n_n; ++j)
-    for (int e = 0; e < SW_K_GRAPH; ++e) {
-      const int i = graph[(size_t)j * SW_K_GRAPH + e];
-      if (i < 0 || i >= n_n) { why = "node graph index out of range"; return false; }
-      const int a = std::min(i, j), b = std::max(i, j);
-      keys.push_back(((uint32_t)a << 16) | (uint32_t)b);
-    }
-  std::sort(keys.begin(), keys.end());
-  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-  const int nb = (int)keys.size();
-  P.col.resize(nb); P.blk_row.resize(nb); P.blk_edge.assign(nb, 0);
-  P.row_ptr.assign(n_n + 1, 0);
-  for (int b = 0; b < nb; ++b) {
-    P.blk_row[b] = (int)(keys[b] >> 16);
-    P.col[b] = (int)(keys[b] & 0xffff);
-    P.row_ptr[P.blk_row[b] + 1]++;
-  }
-  for (int j = 0; j < n_n; ++j) P.row_ptr[j + 1] += P.row_ptr[j];
-  auto find = [&](int a, int b) {
-    const uint32_t key = ((uint32_t)a << 16) | (uint32_t)b;
-    return (int)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
-  };
-  // graph edges: flags on off-diagonal blocks; in-edge lists sorted by source
+// In-edges of the node graph (m -> j for j in N_m), CSR by j, sources
+// ascending; the graph comes from the library's own k-NN kernel.
+bool build_in_edges(int n_n, const std::vector<int>& graph, std::vector<int>& in_ptr, std::vector<int>& in_src,
+                    std::string& why) {
   std::vector<std::vector<int>> in(n_n);
   for (int j = 0; j < n_n; ++j)
     for (int e = 0; e < SW_K_GRAPH; ++e) {
       const int i = graph[(size_t)j * SW_K_GRAPH + e];
+      if (i < 0 || i >= n_n || i == j) { why = "node graph index out of range"; return false; }
       in[i].push_back(j);
-      if (i == j) continue;
-      const int b = find(std::min(i, j), std::max(i, j));
-      P.blk_edge[b] |= (j < i) ? 1 : 2;   // bit0: edge row->col
     }
-  P.in_ptr.assign(n_n + 1, 0);
-  P.in_src.clear();
+  in_ptr.assign(n_n + 1, 0);
+  in_src.clear();
   for (int j = 0; j < n_n; ++j) {
     std::sort(in[j].begin(), in[j].end());
-    P.in_src.insert(P.in_src.end(), in[j].begin(), in[j].end());
-    P.in_ptr[j + 1] = (int)P.in_src.size();
-  }
-  // per block row i, every block that multiplies into it: its own upper
-  // blocks (i, j) and, transposed, the upper blocks (j, i) with j < i
-  std::vector<std::vector<int2>> rows(n_n);
-  for (int b = 0; b < nb; ++b) {
-    rows[P.blk_row[b]].push_back(make_int2(b, P.col[b]));
-    if (P.blk_row[b] != P.col[b]) rows[P.col[b]].push_back(make_int2(b | int(0x80000000u), P.blk_row[b]));
-  }
-  P.rl_ptr.assign(n_n + 1, 0);
-  P.rl_ent.clear();
-  for (int i = 0; i < n_n; ++i) {
-    P.rl_ent.insert(P.rl_ent.end(), rows[i].begin(), rows[i].end());
-    P.rl_ptr[i + 1] = (int)P.rl_ent.size();
-  }
-  // per set: 10 upper blocks in (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3) order + 4 node ids
-  P.set_slots.resize(sets.size() * 14);
-  for (size_t s = 0; s < sets.size(); ++s) {
-    const int id[4] = {sets[s].x, sets[s].y, sets[s].z, sets[s].w};
-    int k = 0;
-    for (int a = 0; a < 4; ++a)
-      for (int b = a; b < 4; ++b) P.set_slots[s * 14 + k++] = find(id[a], id[b]);
-    for (int a = 0; a < 4; ++a) P.set_slots[s * 14 + 10 + a] = id[a];
+    in_src.insert(in_src.end(), in[j].begin(), in[j].end());
+    in_ptr[j + 1] = (int)in_src.size();
   }
   return true;
 }
 
-template <typename T>
-sw_status upload_vec(sw_stream* s, T** dst, const std::vector<T>& v) {
-  SW_TRY(A(s, dst, std::max<size_t>(1, v.size()), true));
-  if (!v.empty()) SW_CUDA(s, cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s->st));
-  return SW_OK;
-}
 
 }  // namespace
 
@@ -899,17 +841,17 @@ namespace {
 // The surfel half of the set-up, from caller-order device arrays (which may
 // be scratch): the caller-order skinning is kept for inspection, the surfels
 // are sorted by their 4-node set and gathered into the internal order, and the
-// distinct sets are returned (host) for the pattern.
+// distinct sets are left in `sets` (device, *n_sets of them) for the pattern.
 sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
-                        const float4* tw, int n_s, std::vector<int4>& sets) {
+                        const float4* tw, int n_s, Tmp& sets, int* n_sets) {
   SwDev& h = s->h;
   cudaStream_t st = s->st;
   const size_t n = n_s;
-  sets.clear();
+  *n_sets = 0;
   SW_TRY(A(s, &s->knn_dist, std::max<size_t>(1, n), true));
   SW_TRY(A(s, &s->w_dist, std::max<size_t>(1, n), true));
   if (n_s == 0) {
-    SW_CUDA(s, cudaStreamSynchronize(st));
+    if (!sets.alloc(16)) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
     return SW_OK;
   }
   Tmp keys(n * 8), keys2(n * 8), vals(n * 4), perm(n * 4), head(n * 4);
@@ -917,59 +859,73 @@ sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const 
   SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn, n * 16, cudaMemcpyDeviceToDevice, st));
   SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw, n * 16, cudaMemcpyDeviceToDevice, st));
   k_set_keys<<<(n_s + 255) / 256, 256, 0, st>>>(tknn, n_s, keys.as<unsigned long long>(), vals.as<int>());
-  size_t tmp_bytes = 0;
-  cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(), keys2.as<unsigned long long>(),
+  size_t sort_bytes = 0, scan_bytes = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, keys.as<unsigned long long>(), keys2.as<unsigned long long>(),
                                   vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
-  Tmp cubtmp(tmp_bytes);
+  cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
+  Tmp cubtmp(std::max(sort_bytes, scan_bytes));
   if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
-  SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, tmp_bytes, keys.as<unsigned long long>(),
+  SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, sort_bytes, keys.as<unsigned long long>(),
                                              keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0,
                                              64, st));
   k_gather_model<<<(n_s + 255) / 256, 256, 0, st>>>(h, keys2.as<unsigned long long>(), perm.as<int>(), tv, tn, tt,
                                                     tknn, tw, head.as<int>());
-  size_t scan_bytes = 0;
-  cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
-  Tmp scantmp(scan_bytes);
-  if (!scantmp.p) return fail(s, SW_ERR_NO_MEMORY, "scan scratch allocation failed");
-  SW_CUDA(s, cub::DeviceScan::InclusiveSum(scantmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
+  SW_CUDA(s, cub::DeviceScan::InclusiveSum(cubtmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
   k_minus_one<<<(n_s + 255) / 256, 256, 0, st>>>(h.set_id, n_s);
   int last = 0;
   SW_CUDA(s, cudaMemcpyAsync(&last, h.set_id + n_s - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   SW_CUDA(s, cudaStreamSynchronize(st));
-  const int n_sets = last + 1;
-  Tmp setn((size_t)n_sets * 16);
-  if (!setn.p) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
-  k_set_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(h, head.as<int>(), setn.as<int4>());
-  sets.resize(n_sets);
-  SW_CUDA(s, cudaMemcpyAsync(sets.data(), setn.p, (size_t)n_sets * 16, cudaMemcpyDeviceToHost, st));
-  SW_CUDA(s, cudaStreamSynchronize(st));
+  *n_sets = last + 1;
+  if (!sets.alloc((size_t)*n_sets * 16)) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
+  k_set_nodes<<<(n_s + 255) / 256, 256, 0, st>>>(h, head.as<int>(), sets.as<int4>());
+  SW_CUDA(s, cudaGetLastError());
   return SW_OK;
 }
 
-// The JᵀJ pattern from the surfels' sets and the node graph: uploaded, the
-// system cleared, the stream re-described to its runner and warped live.
-sw_status install_pattern(sw_stream* s, const std::vector<int4>& sets) {
+// The JᵀJ pattern from the surfels' sets (device) and the node graph, built
+// on the device; the system is cleared, the stream re-described to its runner
+// and warped live.  `graph_changed`: the node graph's in-edge lists are
+// rebuilt too (set-up), or kept (appending leaves the nodes alone).
+sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph_changed) {
   SwDev& h = s->h;
   cudaStream_t st = s->st;
   const int n_n = h.n_n, n_s = h.n_s;
-  std::vector<int> graph((size_t)n_n * SW_K_GRAPH);
-  SW_CUDA(s, cudaMemcpyAsync(graph.data(), h.graph, graph.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (graph_changed) {
+    std::vector<int> graph((size_t)n_n * SW_K_GRAPH), in_ptr, in_src;
+    SW_CUDA(s, cudaMemcpyAsync(graph.data(), h.graph, graph.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(s, cudaStreamSynchronize(st));
+    std::string why;
+    if (!build_in_edges(n_n, graph, in_ptr, in_src, why)) return fail(s, SW_ERR_INVALID_ARG, why);
+    SW_CUDA(s, cudaMemcpyAsync(h.in_ptr, in_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    SW_CUDA(s, cudaMemcpyAsync(h.in_src, in_src.data(), in_src.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  const int K = 10 * n_sets + (1 + SW_K_GRAPH) * n_n;
+  Tmp keys((size_t)K * 4), skeys((size_t)K * 4), flag((size_t)K * 4), pos((size_t)K * 4), cnt(16);
+  Tmp tmp(pattern_scratch_bytes(K, 2 * K));
+  if (!keys.p || !skeys.p || !flag.p || !pos.p || !cnt.p || !tmp.p)
+    return fail(s, SW_ERR_NO_MEMORY, "pattern scratch allocation failed");
+  PatternScratch w{keys.as<uint32_t>(), skeys.as<uint32_t>(), flag.as<int>(), pos.as<int>(), cnt.as<int>(), tmp.p,
+                   pattern_scratch_bytes(K, 2 * K)};
+  SW_CUDA(s, launch_pattern_blocks(sets, n_sets, h.graph, n_n, w, st));
+  int nnzb = 0;
+  SW_CUDA(s, cudaMemcpyAsync(&nnzb, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
   SW_CUDA(s, cudaStreamSynchronize(st));
-  Pattern P;
-  std::string why;
-  if (!build_pattern(n_n, sets, graph, P, why)) return fail(s, SW_ERR_INVALID_ARG, why);
-  s->rl_ptr_host = P.rl_ptr;
-  h.n_sets = (int)sets.size();
-  h.nnzb = (int)P.col.size();
-  SW_CUDA(s, cudaMemcpyAsync(h.row_ptr, P.row_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  SW_CUDA(s, cudaMemcpyAsync(h.rl_ptr, P.rl_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  SW_CUDA(s, cudaMemcpyAsync(h.in_ptr, P.in_ptr.data(), (n_n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-  SW_CUDA(s, cudaMemcpyAsync(h.in_src, P.in_src.data(), P.in_src.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  SW_TRY(upload_vec(s, &h.col, P.col));
-  SW_TRY(upload_vec(s, &h.blk_row, P.blk_row));
-  SW_TRY(upload_vec(s, &h.blk_edge, P.blk_edge));
-  SW_TRY(upload_vec(s, &h.rl_ent, P.rl_ent));
-  SW_TRY(upload_vec(s, &h.set_slots, P.set_slots));
+  h.n_sets = n_sets;
+  h.nnzb = nnzb;
+  SW_TRY(A(s, &h.col, nnzb, true));
+  SW_TRY(A(s, &h.blk_row, nnzb, true));
+  SW_TRY(A(s, &h.blk_edge, nnzb, true));
+  SW_TRY(A(s, &h.rl_ent, (size_t)2 * nnzb - n_n, true));
+  SW_TRY(A(s, &h.set_slots, (size_t)std::max(1, n_sets) * 14, true));
+  {
+    Tmp rlk((size_t)nnzb * 16), rlsk((size_t)nnzb * 16);
+    if (!rlk.p || !rlsk.p) return fail(s, SW_ERR_NO_MEMORY, "pattern scratch allocation failed");
+    SW_CUDA(s, launch_pattern_fill(sets, n_sets, h.graph, n_n, nnzb, w, rlk.as<unsigned long long>(),
+                                   rlsk.as<unsigned long long>(), h, st));
+    s->rl_ptr_host.resize(n_n + 1);
+    SW_CUDA(s, cudaMemcpyAsync(s->rl_ptr_host.data(), h.rl_ptr, (n_n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(s, cudaStreamSynchronize(st));
+  }
   SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
   SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
   if (h.precision == SW_PRECISION_FP64) {
@@ -1018,7 +974,8 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   launch_dq_widen(h, st);
   launch_node_graph(h, st);
 
-  std::vector<int4> sets;
+  Tmp sets;
+  int n_sets = 0;
   if (n_s > 0) {
     const size_t n = n_s;
     Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(n * 16), d2(n * 16);
@@ -1035,11 +992,11 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
       launch_knn_skin(h, tv.as<float4>(), n_s, ids.as<int>(), d2.as<float>(), tknn.as<int4>(), tw.as<float4>(), st);
     }
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(), n_s,
-                         sets));
+                         sets, &n_sets));
   } else {
-    SW_TRY(setup_surfels(s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, sets));
+    SW_TRY(setup_surfels(s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, sets, &n_sets));
   }
-  return install_pattern(s, sets);
+  return install_pattern(s, sets.as<int4>(), n_sets, true);
 }
 }  // namespace
 
@@ -1389,10 +1346,11 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     free_list(s->model_allocs);
     s->version++;
     h.n_s = n_new;
-    std::vector<int4> sets;
+    Tmp sets;
+    int n_sets = 0;
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
-                         n_new, sets));
-    SW_TRY(install_pattern(s, sets));
+                         n_new, sets, &n_sets));
+    SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, false));
     if (stats) stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   s->fused = false;

@@ -216,6 +216,28 @@ void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_
                            cudaStream_t st);
 void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st);
 
+// ------------------------------------------------------------------ JᵀJ pattern
+// Device scratch of the pattern build (k_pattern.cu); K = 10 n_sets + 9 n_n keys.
+struct PatternScratch {
+  uint32_t* keys;     // K: the pair keys, then the unique blocks in order
+  uint32_t* skeys;    // K: sorted keys
+  int* flag;          // K
+  int* pos;           // K
+  int* count;         // 1: blocks (nnzb)
+  void* tmp;          // sort / scan scratch
+  size_t tmp_bytes;
+};
+size_t pattern_scratch_bytes(int n_keys, int n_rl_keys);
+// the unique upper blocks of the sets, the diagonal and the graph edges, in
+// row-major order, to w.keys[0, *w.count)
+cudaError_t launch_pattern_blocks(const int4* sets, int n_sets, const int* graph, int n_n, PatternScratch& w,
+                                  cudaStream_t st);
+// row_ptr, col, blk_row, blk_edge, rl_ptr, rl_ent and set_slots of `d` from
+// the nnzb blocks in w.keys (rl_keys / rl_skeys: 2 nnzb scratch each)
+cudaError_t launch_pattern_fill(const int4* sets, int n_sets, const int* graph, int n_n, int nnzb,
+                                PatternScratch& w, unsigned long long* rl_keys, unsigned long long* rl_skeys,
+                                const SwDev& d, cudaStream_t st);
+
 // tile sizes
 constexpr int kSurfTile = 256;
 constexpr int kAsmTile = 256;
