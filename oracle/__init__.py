@@ -16,6 +16,7 @@ paper's order and notation (SurfelWarp, Gao & Tedrake 2019):
 * ``fusion``    -- index map, live-frame fusion, inverse warp (Sec. 6.1,
                    Eq. 5-6; Sec. 4, Eq. 3)
 * ``rigid``     -- rigid pre-alignment before the non-rigid solve (Sec. 7)
+* ``visibility`` -- opaque splat visibility before the solve (Sec. 7)
 * ``append``    -- live skinning, compressive test, appending and removal
                    (Sec. 6.2-6.4, Eq. 7-8)
 * ``stream``    -- the five per-stream calls over host memory
@@ -30,5 +31,5 @@ that implements them.  Parity unpinned: the
 paper-faithfulness of those readings (thresholds, node radius, association
 method, parameterisation); they are decisions, not facts the paper fixes.
 """
-from . import dq, depth, skinning, solver, fusion, rigid, append, stream  # noqa: F401
+from . import dq, depth, skinning, solver, fusion, rigid, visibility, append, stream  # noqa: F401
 from .stream import OracleStream, Params  # noqa: F401

@@ -18,6 +18,7 @@ from . import solver as SOLVER
 from . import fusion as FUSION
 from . import rigid as RIGID
 from . import append as APPEND
+from . import visibility as VIS
 
 
 @dataclass
@@ -36,6 +37,7 @@ class Params:
     corr_normal: float = 0.7       # association normal dot (reading)
     stable_conf: float = 10.0      # δ_stable, Table 1
     recent_frames: int = 2         # δ_recent, Table 1
+    visibility: bool = False       # splat visibility before the solve (see visibility.py)
 
     @property
     def cam(self):
@@ -77,10 +79,22 @@ class OracleStream:
         self.N32 = self.maps["N"].astype(np.float32)
         self.t_now = frame_id
 
-    def associate(self, v_live, n_live):
+    def predict_visibility(self):
+        """Sec. 7: the selected live surfels under the current warp rendered as
+        opaque splats at the depth resolution; the surfels that keep a pixel."""
+        p = self.p
+        _, v_live, n_live = SOLVER.warp_surfels(self.v_ref, self.n_ref, self.knn, self.w, self.node_dq)
+        sel = SOLVER.select_surfels(self.conf, self.t_obs, self.t_now, p.stable_conf, p.recent_frames)
+        self.vis_map = VIS.visibility_map(v_live, n_live, self.radius, sel, p.cam)
+        self.visible = VIS.visible_mask(self.vis_map, len(self.v_ref))
+        return self.visible
+
+    def associate(self, v_live, n_live, visibility=True):
         p = self.p
         sel = SOLVER.select_surfels(self.conf, self.t_obs, self.t_now,
                                     p.stable_conf, p.recent_frames)
+        if p.visibility and visibility:
+            sel = sel & self.visible
         ok, pix = SOLVER.associate(v_live, n_live, sel, self.V32, self.N32,
                                    self.maps["valid"], p.cam, p.corr_dist, p.corr_normal)
         tv = np.zeros_like(v_live)
@@ -90,6 +104,8 @@ class OracleStream:
         return ok, tv, tn
 
     def solve_frame(self, gn_iters, pcg_iters, keep_masks=False):
+        if self.p.visibility:
+            self.predict_visibility()
         self.node_dq, stats = SOLVER.gauss_newton(
             self.v_ref, self.n_ref, self.knn, self.w, self.node_p, self.node_dq,
             self.graph, self.pattern, self.p.lam, gn_iters, pcg_iters,
@@ -100,7 +116,7 @@ class OracleStream:
         """Rigid pre-alignment of the current frame (see rigid.py); returns
         [(correspondences, Σ r²)] per iteration."""
         self.node_dq, T, stats = RIGID.rigid_align(self.v_ref, self.n_ref, self.knn, self.w, self.node_dq,
-                                                  self.associate, iters)
+                                                  lambda y, ny: self.associate(y, ny, visibility=False), iters)
         self.last_rigid = T
         return stats
 

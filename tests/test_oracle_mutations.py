@@ -196,3 +196,37 @@ def test_strict_unstable_period(monkeypatch):
         return (np.asarray(conf) < stable_conf) & (t_now - np.asarray(t_init) > t_low)
     monkeypatch.setattr(AP, "unstable", bad)
     _fails(T.test_unstable_removal_boundaries)
+
+
+def test_wrong_splat_intersection_depth(monkeypatch):
+    """The ray-plane depth taken as (n·v)/(n·q) with q's z dropped: the closed-form disk pin fails."""
+    import test_oracle_visibility as T
+    from oracle import visibility as V
+    orig = V.splat_cover
+
+    def bad(v32, n32, r32, xs, ys, cx, cy, fx, fy):
+        qx = (xs.astype(np.float32) - np.float32(cx)) / np.float32(fx)
+        qy = (ys.astype(np.float32) - np.float32(cy)) / np.float32(fy)
+        nv = ((n32[:, 0] * v32[:, 0]) + (n32[:, 1] * v32[:, 1])) + (n32[:, 2] * v32[:, 2])
+        nq = (n32[:, 0] * qx) + (n32[:, 1] * qy) - n32[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+            t = nv / nq
+            d2 = ((t * qx - v32[:, 0]) ** 2 + (t * qy - v32[:, 1]) ** 2) + (t - v32[:, 2]) ** 2
+            return (t > 0) & (d2 <= r32 * r32), t
+    monkeypatch.setattr(V, "splat_cover", bad)
+    assert orig is not bad
+    _fails(T.test_fronto_parallel_disk_closed_form)
+
+
+def test_splat_ties_to_the_higher_id(monkeypatch):
+    import test_oracle_visibility as T
+    from oracle import visibility as V
+    orig = V.visibility_map
+
+    def bad(v_live, n_live, radius, selected, cam, chunk=4096):
+        k = len(v_live)
+        rev = orig(np.asarray(v_live)[::-1], np.asarray(n_live)[::-1], np.asarray(radius)[::-1],
+                   np.asarray(selected)[::-1], cam, chunk)
+        return np.where(rev >= 0, k - 1 - rev, -1)
+    monkeypatch.setattr(V, "visibility_map", bad)
+    _fails(T.test_equal_depths_go_to_the_lower_id_and_hidden_splats_are_invisible)
