@@ -81,6 +81,12 @@ typedef struct {
   float stable_conf;            /* δ_stable (Table 1: 10) */
   int recent_frames;            /* δ_recent (Table 1: 2) */
   int precision;                /* SW_PRECISION_* (default SW_PRECISION_MIXED) */
+  int visibility;               /* 1: predict visibility before each solve (Sec. 7): the
+                                   selected live surfels are drawn as opaque disk splats
+                                   (position, normal, radius) into an index map at the depth
+                                   resolution, and only surfels that keep a pixel are
+                                   associated; 0 (default): every selected surfel is
+                                   associated and occlusion is left to the distance test */
   /* appending (sw_append_frame) */
   float eps;                    /* ε of Eq. 7-8 (Table 1: 0.2) */
   float delta_nn;               /* δ_nn, least sum of a new surfel's live weights (not in Table 1: 0.3) */
@@ -198,6 +204,12 @@ sw_status sw_debug_associate(sw_handle h);
 sw_status sw_debug_fusion_targets(sw_handle h, int* target, int* imap);
 /* Assemble JᵀJ and Jᵀe at the current node transforms and maps (one
  * Gauss-Newton linearisation, no solve).  Sizes: *nnzb_out upper blocks. */
+/* Splat visibility of the live surfels as they are stored (e.g. by
+ * sw_debug_set_live; each surfel keeps its own radius): vis_map (W*H, nullable) gets the caller's
+ * surfel index drawn at each pixel or -1, visible (n_surfels, caller order,
+ * nullable) 1 for the surfels that keep a pixel.  Independent of
+ * sw_params.visibility; the call synchronises. */
+sw_status sw_debug_visibility(sw_handle h, int* vis_map, int* visible);
 sw_status sw_debug_assemble(sw_handle h, int* nnzb_out, int* n_corr_out);
 /* Read the last assembled system: rows/cols [nnzb] block coordinates
  * (row <= col), vals [nnzb][36] row-major 6x6, g [6 n_nodes]. */
@@ -242,12 +254,13 @@ sw_status sw_batch_fuse(sw_batch_handle b);
 /* ---------------------------------------------------------------------------
  * Stage timing (CUDA events recorded on the launching stream, inside the
  * captured solve graph).  Stages: 0 depth processing, 1 regulariser
- * assembly, 2 data-term assembly, 3 PCG + update, 4 fusion.  Enabling or
+ * assembly, 2 data-term assembly, 3 PCG + update, 4 fusion, 5 visibility
+ * prediction (streams with sw_params.visibility).  Enabling or
  * disabling re-captures the solve graph.  sw_read_profile synchronises and
  * returns, per stage, the summed milliseconds and the number of launches of
  * the last upload, solve and fusion.
  * ------------------------------------------------------------------------- */
-#define SW_PROFILE_STAGES 5
+#define SW_PROFILE_STAGES 6
 sw_status sw_set_profiling(sw_handle h, int enable);
 sw_status sw_read_profile(sw_handle h, double* ms, int* launches);
 sw_status sw_batch_set_profiling(sw_batch_handle b, int enable);

@@ -37,7 +37,7 @@ class sw_params(ctypes.Structure):
                 ("max_surfels", ctypes.c_int), ("max_nodes", ctypes.c_int),
                 ("lambda_", ctypes.c_float), ("fuse_dist", ctypes.c_float), ("fuse_normal", ctypes.c_float),
                 ("corr_dist", ctypes.c_float), ("corr_normal", ctypes.c_float), ("stable_conf", ctypes.c_float),
-                ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int),
+                ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int), ("visibility", ctypes.c_int),
                 ("eps", ctypes.c_float), ("delta_nn", ctypes.c_float), ("fd_step", ctypes.c_float),
                 ("t_low_confid", ctypes.c_int)]
 
@@ -107,6 +107,7 @@ _SIGS = {
     "sw_debug_set_live": [_P, _P, _P, _I],
     "sw_debug_associate": [_P],
     "sw_debug_fusion_targets": [_P, _P, _P],
+    "sw_debug_visibility": [_P, _P, _P],
     "sw_debug_assemble": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "sw_debug_read_jtj": [_P, _P, _P, _P, _P, _I],
     "sw_export_state": [_P, _P, ctypes.POINTER(ctypes.c_size_t)],
@@ -143,7 +144,7 @@ _SIGS = {
     "sw_debug_read_append": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(_I)],
 }
 
-PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion")
+PROFILE_STAGES = ("depth", "reg_assembly", "data_assembly", "pcg", "fusion", "visibility")
 
 
 def exported_symbols():
@@ -345,6 +346,15 @@ def sw_debug_set_live(h, v, n):
     pv, a = _ptr(_pad4(v, 0.0))
     pn, b = _ptr(_pad4(n, 0.0))
     _check(lib().sw_debug_set_live(h, pv, pn, a.shape[0]), h)
+
+
+def sw_debug_visibility(h, height, width):
+    """(vis_map (H, W) caller ids or -1, visible (n,) bool) of the stored live surfels."""
+    n = _count_surfels(h)
+    vm = np.empty((height, width), np.int32)
+    vis = np.empty(max(1, n), np.int32)
+    _check(lib().sw_debug_visibility(h, vm.ctypes.data_as(_P), vis.ctypes.data_as(_P)), h)
+    return vm, vis[:n].astype(bool)
 
 
 def sw_debug_associate(h):

@@ -54,7 +54,7 @@ void set_process_error(const std::string& msg) { set_global_error(msg); }
 // streams: it owns the device tile tables, the descriptor array, the active
 // mask, the grid barrier of the persistent PCG, the captured solve graphs and
 // the profiling events.
-enum ProfStage { kProfDepth = 0, kProfReg, kProfData, kProfPcg, kProfFuse, kProfStages };
+enum ProfStage { kProfDepth = 0, kProfReg, kProfData, kProfPcg, kProfFuse, kProfVis, kProfStages };
 
 struct ProfEvent {
   int stage;
@@ -240,6 +240,8 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     for (int i = 1; i < n; ++i)
       if (devs[i].precision != prec) return fail(err_to, SW_ERR_INVALID_ARG, "batch members differ in precision");
     r->bh.precision = prec;
+    r->bh.any_visibility = 0;
+    for (int i = 0; i < n; ++i) r->bh.any_visibility |= devs[i].visibility;
     const int per_sm = std::max(1, pcg_blocks_per_sm(prec));
     const int cap = sm_count() * per_sm;
     if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
@@ -377,6 +379,12 @@ void launch_data_stage(const BatchHost& b, int it, cudaStream_t st) {
 sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vector<ProfEvent>* prof) {
   cudaStream_t st = r->st;
   launch_solve_begin(r->bh, st);
+  if (r->bh.any_visibility) {   // Sec. 7: visibility predicted once, under the warp the solve starts from
+    prof_mark(r, prof, kProfVis, true, true);
+    launch_vis_splat(r->bh, 0, st);
+    launch_vis_mark(r->bh, 0, st);
+    prof_mark(r, prof, kProfVis, false, true);
+  }
   for (int it = 0; it < gn; ++it) {
     prof_mark(r, prof, kProfReg, true, true);
     launch_reg_stage(r->bh, it, st);
@@ -468,6 +476,7 @@ bool params_ok(const sw_params* p, std::string& why) {
   if (p->max_surfels < 0 || p->max_surfels > (1 << 28)) { why = "max_surfels out of range"; return false; }
   if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
   if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
+  if (p->visibility != 0 && p->visibility != 1) { why = "visibility must be 0 or 1"; return false; }
   if (!(p->eps > 0 && p->eps < 1 && p->delta_nn >= 0 && p->fd_step > 0)) {
     why = "appending parameters out of range (0 < eps < 1, delta_nn >= 0, fd_step > 0)";
     return false;
@@ -656,6 +665,7 @@ sw_status sw_params_default(sw_params* p, int width, int height, float fx, float
   p->stable_conf = 10.f;    // Table 1
   p->recent_frames = 2;     // Table 1
   p->precision = SW_PRECISION_MIXED;
+  p->visibility = 0;
   p->eps = 0.2f;            // Table 1
   p->delta_nn = 0.3f;
   p->fd_step = 1e-3f;
@@ -727,6 +737,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   h.fx = p->fx; h.fy = p->fy; h.cx = p->cx; h.cy = p->cy;
   h.sqrt_lambda = std::sqrt(p->lambda);
   h.precision = p->precision;
+  h.visibility = p->visibility;
   h.corr_dist = p->corr_dist; h.corr_normal = p->corr_normal;
   h.fuse_dist = p->fuse_dist; h.fuse_normal = p->fuse_normal;
   h.stable_conf = p->stable_conf; h.recent_frames = p->recent_frames;
@@ -739,6 +750,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.node_p, nn); ALLOC(h.dq, 2 * nn); ALLOC(h.graph, SW_K_GRAPH * nn);
   ALLOC(h.in_ptr, nn + 1); ALLOC(h.in_src, SW_K_GRAPH * nn);
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
+  ALLOC(h.vis_map, np); ALLOC(h.visible, ns);
   ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Li, 21 * nn);
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
   ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
@@ -771,6 +783,8 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
       cudaMemsetAsync(h.xp, 0, 12 * nn * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.pcg_epoch, 0, sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.vis_map, 0xff, np * sizeof(unsigned long long), s->st) != cudaSuccess ||
+      cudaMemsetAsync(h.visible, 0, ns * sizeof(int), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.vmap, 0, np * sizeof(float4), s->st) != cudaSuccess) {
     s->err = "cudaMemset failed";
     return cleanup(SW_ERR_CUDA);
@@ -1379,6 +1393,29 @@ sw_status sw_debug_read_append(sw_handle s, int* pix, int* knn4, int* flags, dou
   SW_TRY(get(v4, a.v, (size_t)n * 16));
   SW_TRY(get(n4, a.n, (size_t)n * 16));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_debug_visibility(sw_handle s, int* vis_map, int* visible) {
+  SW_TRY(need_model(s, s ? s->h.n_s : 0));
+  if (!s->has_depth) return fail(s, SW_ERR_NOT_INITIALIZED, "no depth frame");
+  const size_t np = (size_t)s->h.W * s->h.H;
+  const int n = s->h.n_s;
+  launch_vis_splat(s->run->bh, 1, s->st);
+  std::vector<unsigned long long> vm(np);
+  SW_CUDA(s, cudaMemcpyAsync(vm.data(), s->h.vis_map, np * 8, cudaMemcpyDeviceToHost, s->st));
+  launch_vis_mark(s->run->bh, 1, s->st);
+  SW_CUDA(s, cudaGetLastError());
+  std::vector<int> vis(std::max(1, n)), orig(std::max(1, n));
+  if (n) {
+    SW_CUDA(s, cudaMemcpyAsync(vis.data(), s->h.visible, n * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    SW_CUDA(s, cudaMemcpyAsync(orig.data(), s->h.orig_id, n * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  }
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (vis_map)
+    for (size_t p = 0; p < np; ++p) vis_map[p] = vm[p] == ~0ull ? -1 : (int)(vm[p] & 0xffffffffu);
+  if (visible)
+    for (int i = 0; i < n; ++i) visible[orig[i]] = vis[i];
   return SW_OK;
 }
 

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       inv = 1.f / n2;
       vl = dq_transform(b, inv, f3(v4));
       nl = dq_rotate(b, inv, f3(n4));
-      if (surfel_selected(d, t_now, n4.w, d.tt[i].y)) pix = associate_one(d, vl, nl);
+      if (surfel_visible(d, i) && surfel_selected(d, t_now, n4.w, d.tt[i].y)) pix = associate_one(d, vl, nl);
     }
     d.corr_pix[i] = pix;
     if (write_live) {
@@ -317,7 +317,7 @@ __global__ void k_associate_only(Batch bt) {
   if (i >= d.n_s) return;
   const float4 vl = d.v_live[i], nl = d.n_live[i];
   int pix = -1;
-  if (surfel_selected(d, *d.t_now, d.n_ref[i].w, d.tt[i].y)) pix = associate_one(d, f3(vl), f3(nl));
+  if (surfel_visible(d, i) && surfel_selected(d, *d.t_now, d.n_ref[i].w, d.tt[i].y)) pix = associate_one(d, f3(vl), f3(nl));
   d.corr_pix[i] = pix;
 }
 

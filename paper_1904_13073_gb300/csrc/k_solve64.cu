@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kSurfTile) k_data_assemble64(Batch bt, int gn_
       inv = 1.0 / n2;
       vl = dq_transform(b, inv, d3(v4));
       nl = dq_rotate(b, inv, d3(n4));
-      if (surfel_selected(d, *d.t_now, n4.w, d.tt[i].y))
+      if (surfel_visible(d, i) && surfel_selected(d, *d.t_now, n4.w, d.tt[i].y))
         pix = associate_one(d, make_float3((float)vl.x, (float)vl.y, (float)vl.z),
                             make_float3((float)nl.x, (float)nl.y, (float)nl.z));
     }

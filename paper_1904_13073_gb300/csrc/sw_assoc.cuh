@@ -14,6 +14,10 @@ __device__ __forceinline__ bool surfel_selected(const SwDev& d, int t_now, float
   return conf > d.stable_conf || (t_now - t_obs) <= d.recent_frames;
 }
 
+// With visibility prediction on, only the surfels that kept a pixel of the
+// frame's splat index map are associated (k_visibility.cu).
+__device__ __forceinline__ bool surfel_visible(const SwDev& d, int i) { return !d.visibility || d.visible[i]; }
+
 // Projective association of one warped surfel; the depth pixel it projects
 // to, or -1 if rejected (behind the camera, outside the image, not a usable
 // depth surfel, farther than corr_dist, normals within corr_normal).

@@ -45,6 +45,7 @@ struct SwDev {
   float sqrt_lambda, corr_dist, corr_normal, fuse_dist, fuse_normal, stable_conf;
   int recent_frames;
   int precision;      // SW_PRECISION_*
+  int visibility;     // 1: splat visibility gates the association
   // sizes
   int n_s, n_n, n_sets, nnzb;
   int* t_now;         // current frame id (device scalar)
@@ -74,6 +75,8 @@ struct SwDev {
   float4* nmap;       // N(u) and the depth-surfel radius
   unsigned long long* imap;  // 4W x 4H: (z bits << 32) | caller's surfel index
   int* fuse_target;   // per pixel: internal surfel index, kTargetNone or kTargetEmptyWindow
+  unsigned long long* vis_map;   // W x H splat index map: (depth bits << 32) | caller's surfel index
+  int* visible;       // per surfel: kept a pixel of the frame's splat index map
   // block-sparse JᵀJ (upper triangle incl. diagonal, 6x6 blocks, row-major)
   int* row_ptr;       // n_n + 1; the diagonal block leads its row
   int* col;           // nnzb
@@ -148,6 +151,7 @@ struct BatchHost {
   int precision;                    // SW_PRECISION_* shared by every member
   int pcg_ent_cap;                  // most matrix entries (block-row terms) one PCG CTA owns
   int pcg_mode;                     // how the PCG's SpMV reaches the matrix (k_pcg.cu: SpmvMode)
+  int any_visibility;               // some member predicts splat visibility
 };
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st);
@@ -164,6 +168,11 @@ void launch_dq_widen(const SwDev& d, cudaStream_t st);
 void launch_warp_live(const BatchHost& b, cudaStream_t st);
 void launch_rigid_align(const BatchHost& b, int iters, cudaStream_t st);
 void launch_index_map(const BatchHost& b, cudaStream_t st);
+// splat visibility: from_live = 0 warps each surfel with the current node
+// transforms (members without visibility skip), 1 renders the stored live
+// surfels of every member
+void launch_vis_splat(const BatchHost& b, int from_live, cudaStream_t st);
+void launch_vis_mark(const BatchHost& b, int from_live, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
 int pcg_blocks_per_sm(int precision);

@@ -1,0 +1,102 @@
+"""Splat visibility on the GPU (Sec. 7) against the oracle: bit for bit on
+given FP32 live surfels, and the solve with visibility on against the
+oracle's solve with visibility on."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1904_13073_gb300 as sw
+from oracle import solver as OS
+from oracle import visibility as OV
+
+from gpu_helpers import Pair, ensure_built, rigid_dq8_from, rotation_angle_between
+
+pytestmark = pytest.mark.gpu
+F32 = np.float32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+def _depth_radii(scene, n_surfels=None):
+    """The scene with each surfel's radius as a depth pixel would give it
+    (Sec. 5: √2 z / (f max(|cos|, cos 75°))), so that the splats close."""
+    c = scene.cam
+    v, n = scene.surfel_v.astype(float), scene.surfel_n.astype(float)
+    view = v / np.linalg.norm(v, axis=1, keepdims=True)
+    cosv = np.abs(np.einsum('ij,ij->i', n, view))
+    r = np.sqrt(2.0) * v[:, 2] / (c.fx * np.maximum(cosv, np.cos(np.deg2rad(75.0))))
+    return dataclasses.replace(scene, surfel_r=r.astype(F32))
+
+
+SCENES = {
+    "sphere": lambda: _depth_radii(synth.random_scene(seed=6, n_surfels=40000, n_nodes=64)),
+    "tiny": lambda: synth.plain_tiny(seed=1),
+}
+
+
+@pytest.mark.parametrize("which", ["sphere", "tiny"])
+def test_visibility_bit_exact_on_given_live_surfels(which):
+    scene = SCENES[which]()
+    c = scene.cam
+    p = Pair(scene)
+    try:
+        p.upload(1)
+        axis, ang, tr = synth.random_rigid_dq_inputs(7, len(scene.node_p), 3.0, 0.01)
+        dq8 = rigid_dq8_from(axis, ang, tr)
+        _, vl, nl = OS.warp_surfels(p.o.v_ref, p.o.n_ref, p.o.knn, p.o.w, dq8.astype(np.float64))
+        vl32, nl32 = vl.astype(F32), nl.astype(F32)
+        sw.sw_debug_set_live(p.h, vl32, nl32)
+        vm, vis = sw.sw_debug_visibility(p.h, c.height, c.width)
+        sel = OS.select_surfels(p.o.conf, p.o.t_obs, 1, p.o.p.stable_conf, p.o.p.recent_frames)
+        ovm = OV.visibility_map(vl32, nl32, scene.surfel_r, sel, p.o.p.cam)
+        np.testing.assert_array_equal(vm, ovm)
+        np.testing.assert_array_equal(vis, OV.visible_mask(ovm, len(vl32)))
+        assert vis.sum() > 100 and (~vis & sel).sum() > 100
+        # the map is left empty: a second call gives the same result
+        vm2, vis2 = sw.sw_debug_visibility(p.h, c.height, c.width)
+        np.testing.assert_array_equal(vm2, vm)
+    finally:
+        p.close()
+
+
+def test_solve_with_visibility_matches_oracle():
+    """Sphere with depth radii over three frames of solve + fusion, visibility
+    on both sides.  The GPU predicts visibility from its FP32 warp and the
+    oracle from its FP64 one, so a few splat decisions may differ; the warp
+    fields agree within the solve's tolerances."""
+    scene = _depth_radii(synth.random_scene(seed=3, n_surfels=40000, n_nodes=48))
+    p = Pair(scene, visibility=1)
+    q = Pair(scene)   # the same stream without visibility, for comparison
+    try:
+        for t in (1, 2, 3):
+            p.upload(t)
+            q.upload(t)
+            st = sw.sw_solve_frame(p.h, 3, 10)
+            st_off = sw.sw_solve_frame(q.h, 3, 10)
+            ost = p.o.solve_frame(3, 10)
+            for k in range(3):
+                assert abs(st["n_corr"][k] - ost[k].n_corr) <= max(5, ost[k].n_corr // 200), (t, k)
+            # visibility keeps at most one surfel per pixel of the splat map
+            assert st["n_corr"][0] <= p.o.visible.sum() + 10 and st["n_corr"][0] < st_off["n_corr"][0]
+            _, dq = sw.sw_read_nodes(p.h)
+            dq = dq.astype(np.float64)
+            assert rotation_angle_between(dq, p.o.node_dq).max() < 1e-4
+            got = OS.node_transform(dq, p.o.node_p)
+            assert np.linalg.norm(got - p.o.warped_nodes(), axis=1).max() < 2e-5
+            sw.sw_fuse_frame(p.h)
+            p.o.fuse_frame()
+            sw.sw_fuse_frame(q.h)
+        sw.sw_set_profiling(p.h, True)
+        p.upload(4)
+        sw.sw_solve_frame(p.h, 3, 10)
+        pr = sw.sw_read_profile(p.h)
+        assert pr["visibility"][1] == 1 and pr["visibility"][0] > 0
+        sw.sw_set_profiling(p.h, False)
+    finally:
+        p.close()
+        q.close()
