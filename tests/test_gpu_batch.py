@@ -113,7 +113,8 @@ def test_stream_profile_reports_each_stage():
         prof = sw.sw_read_profile(h)
         assert prof["depth"][1] == 1 and prof["fusion"][1] == 1
         assert prof["reg_assembly"][1] == 3 and prof["data_assembly"][1] == 3 and prof["pcg"][1] == 3
-        assert all(v[0] > 0 for v in prof.values())
+        assert prof["visibility"] == (0.0, 0)   # visibility prediction is off by default
+        assert all(v[0] > 0 for k, v in prof.items() if k != "visibility")
     finally:
         sw.sw_destroy_stream(h)
 

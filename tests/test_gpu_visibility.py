@@ -64,14 +64,23 @@ def test_visibility_bit_exact_on_given_live_surfels(which):
         p.close()
 
 
-def test_solve_with_visibility_matches_oracle():
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_FP64])
+def test_solve_with_visibility_matches_oracle(precision):
     """Sphere with depth radii over three frames of solve + fusion, visibility
-    on both sides.  The GPU predicts visibility from its FP32 warp and the
-    oracle from its FP64 one, so a few splat decisions may differ; the warp
-    fields agree within the solve's tolerances."""
+    on both sides.  At frame 1 the warp is the identity, the live surfels are
+    bit-identical on both sides and so is the visibility: the warp fields
+    agree as closely as without visibility.  From frame 2 on the GPU renders
+    the splats from its FP32 warp and the oracle from its FP64 one; a splat
+    edge or a depth tie that moves by an ulp flips which of two overlapping
+    surfels is visible, and each flip swaps one data term (its residual
+    differs by up to the depth noise, 1 mm).  With one visible surfel per
+    pixel (~3,000 terms over 48 nodes) a few flips move the nodes by tens of
+    µm: 2.4e-4 rad and 48 µm measured at frame 3 in both precisions, against
+    3e-7 rad without visibility.  The bound for those frames is about 4x
+    that."""
     scene = _depth_radii(synth.random_scene(seed=3, n_surfels=40000, n_nodes=48))
-    p = Pair(scene, visibility=1)
-    q = Pair(scene)   # the same stream without visibility, for comparison
+    p = Pair(scene, precision=precision, visibility=1)
+    q = Pair(scene, precision=precision)   # the same stream without visibility, for comparison
     try:
         for t in (1, 2, 3):
             p.upload(t)
@@ -85,9 +94,13 @@ def test_solve_with_visibility_matches_oracle():
             assert st["n_corr"][0] <= p.o.visible.sum() + 10 and st["n_corr"][0] < st_off["n_corr"][0]
             _, dq = sw.sw_read_nodes(p.h)
             dq = dq.astype(np.float64)
-            assert rotation_angle_between(dq, p.o.node_dq).max() < 1e-4
-            got = OS.node_transform(dq, p.o.node_p)
-            assert np.linalg.norm(got - p.o.warped_nodes(), axis=1).max() < 2e-5
+            rot = rotation_angle_between(dq, p.o.node_dq).max()
+            trans = np.linalg.norm(OS.node_transform(dq, p.o.node_p) - p.o.warped_nodes(), axis=1).max()
+            if t == 1:
+                assert [st["n_corr"][k] for k in range(3)] == [o.n_corr for o in ost]
+                assert rot < 1e-5 and trans < 1e-6, (rot, trans)
+            else:
+                assert rot < 1e-3 and trans < 2e-4, (t, rot, trans)
             sw.sw_fuse_frame(p.h)
             p.o.fuse_frame()
             sw.sw_fuse_frame(q.h)
