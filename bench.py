@@ -624,6 +624,42 @@ def main():
              "correspondences": [int(n) for n, _ in rig_stats],
              "bytes_per_iteration": rig_bytes, "achieved_gbs": rig_bytes / rigid_it_us / 1e3,
              "frac": rig_bytes / rigid_it_us / 1e3 / peak}
+    # splat visibility (Sec. 7, sw_params.visibility): the same frames on a
+    # stream that predicts visibility before each solve, timed the same way
+    hv = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4), visibility=1), stream)
+    sw.sw_set_model(hv, v4, n4, t2, node4)
+
+    def vstep(k):
+        sw.sw_upload_depth(hv, dev_frames[ts[k]], k + 1)
+        sw.sw_solve_frame(hv, gn, pcg)
+        sw.sw_fuse_frame(hv)
+    for k in range(args.warmup):
+        vstep(k)
+    torch.cuda.synchronize()
+    v_lat = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vstep(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v_lat.append(e0.elapsed_time(e1))
+    sw.sw_set_profiling(hv, True)
+    k_v = args.warmup + args.steps
+    sw.sw_upload_depth(hv, dev_frames[ts[k_v]], k_v + 1)
+    v_stats = sw.sw_solve_frame(hv, gn, pcg, want_stats=True)
+    sw.sw_fuse_frame(hv)
+    v_prof = sw.sw_read_profile(hv)
+    sw.sw_set_profiling(hv, False)
+    sw.sw_destroy_stream(hv)
+    visibility = {"frames_per_s": 1000.0 / float(np.mean(v_lat)), "ms_per_step": float(np.mean(v_lat)),
+                  "visibility_ms": v_prof["visibility"][0], "n_corr_per_gn_iter": v_stats["n_corr"],
+                  "n_corr_without": n_corr,
+                  "note": "same workload and timing as the headline, with sw_params.visibility = 1: the "
+                          "selected live surfels drawn as opaque disk splats before each solve, only "
+                          "surfels that keep a pixel associated"}
     # appending (a separate call after fusion, not part of the configuration's
     # frame): steady state on the full model, where the candidates are the
     # few pixels no surfel covers, frame after frame; the first call loads
@@ -682,6 +718,7 @@ def main():
         "autotune": {"pcg_rows_per_cta": tuned_rows, "pcg_us_per_launch": tuned_us},
         "rigid_align": rigid,
         "appending": appending,
+        "visibility": visibility,
     }
     if batched:
         line["multi_stream"] = batched
