@@ -154,3 +154,92 @@ def append_candidates(pix, maps, node_dq, node_p, node_sigma, eps=EPS, delta_nn=
     accept = (wsum >= delta_nn) & ~(snorm > 1.0 + eps)
     return dict(knn=knn, keep=keep, w=w, wsum=wsum, v_ref=v_ref, n_ref=n_ref, strain=J,
                 strain_norm=snorm, accept=accept)
+
+
+# ---------------------------------------------------------------------------
+# node-graph extension (Sec. 6.4, last paragraph; the paper defers the details
+# to DynamicFusion's Sec. 3.4, which is summarised there: the coverage of the
+# appended reference geometry by the node graph is computed, the uncovered
+# vertices are sub-sampled into new nodes, and the edges are recomputed; the
+# surfels' nearest-neighbour sets are then compared with the new nodes)
+#
+# Readings:
+# * an appended surfel at v is covered when some node j has ‖v − p_j‖² < σ_j²
+#   (inside the node's radius parameter), decided in FP32 with the k-NN's
+#   fixed operation order;
+# * sub-sampling: the uncovered surfels are visited in their (caller) order;
+#   one becomes a node when it is at least σ away from every node, old or
+#   accepted before it (‖v − p‖² ≥ σ², FP32), σ being the radius parameter of
+#   its nearest old node (the local sampling distance); the new node takes
+#   that σ;
+# * a new node's transform starts as the current warp at its position: the
+#   normalised blend (Eq. 1) of its 4 nearest old nodes with their weights;
+# * the graph is recomputed over all nodes (the 8-NN rule);
+# * every surfel's set is compared with the new nodes: the 4 smallest
+#   (FP32 distance, id) among its old set and the new nodes, all measured at
+#   its current reference position; a surfel whose set changed gets that set
+#   in distance order and its Eq. 1 weights at its current position, the
+#   others keep their set and weights (fusion may have moved them a little
+#   since they were skinned);
+# * new nodes past the stream's node capacity are not added.
+# ---------------------------------------------------------------------------
+
+def covered(v_app, node_p, node_sigma):
+    """Step 1: (n,) mask of appended surfels inside some node's radius."""
+    v32 = np.asarray(v_app, dtype=_F32)
+    p32 = np.asarray(node_p, dtype=_F32)
+    s32 = np.asarray(node_sigma, dtype=_F32)
+    out = np.zeros(len(v32), dtype=bool)
+    for j in range(len(p32)):
+        out |= d2_fp32(v32, p32[j][None, :]) < s32[j] * s32[j]
+    return out
+
+
+def subsample_nodes(v_unc, node_p, node_sigma, max_new):
+    """Step 2: greedy sub-sampling of the uncovered surfels (in order);
+    returns (positions (k, 3) float32, σ (k,) float32)."""
+    v32 = np.asarray(v_unc, dtype=_F32)
+    p32 = np.asarray(node_p, dtype=_F32)
+    s32 = np.asarray(node_sigma, dtype=_F32)
+    new_p, new_s = [], []
+    for v in v32:
+        if len(new_p) >= max_new:
+            break
+        d_old = d2_fp32(p32, v[None, :])
+        j0 = int(np.lexsort((np.arange(len(p32)), d_old.view(np.uint32)))[0])   # nearest old node, ties to the lower id
+        sig = s32[j0]
+        s2 = sig * sig
+        if np.any(d_old < s2):
+            continue
+        if new_p and np.any(d2_fp32(np.asarray(new_p, dtype=_F32), v[None, :]) < s2):
+            continue
+        new_p.append(v)
+        new_s.append(sig)
+    return np.asarray(new_p, dtype=_F32).reshape(-1, 3), np.asarray(new_s, dtype=_F32)
+
+
+def new_node_transforms(new_p, node_p, node_sigma, node_dq):
+    """Step 3: the current warp at each new node, as a unit dual quaternion."""
+    if len(new_p) == 0:
+        return np.zeros((0, 8))
+    knn = SKIN.knn_fp32(np.asarray(new_p, dtype=_F32), np.asarray(node_p, dtype=_F32), SKIN.K_SKIN)
+    w = SKIN.skin_weights(new_p, node_p, node_sigma, knn)
+    return DQ.dq_normalize(DQ.blend(node_dq, knn, w))
+
+
+def merge_skinning(v_ref, knn, w, node_p, node_sigma, first_new):
+    """Step 5: each surfel's set compared with the nodes from `first_new` on."""
+    v32 = np.asarray(v_ref, dtype=_F32)
+    p32 = np.asarray(node_p, dtype=_F32)
+    new_ids = np.arange(first_new, len(p32))
+    cand = np.concatenate([knn, np.broadcast_to(new_ids, (len(knn), len(new_ids)))], axis=1)
+    d2 = d2_fp32(v32[:, None, :], p32[cand])
+    key = (d2.view(np.uint32).astype(np.uint64) << np.uint64(32)) | cand.astype(np.uint64)
+    best = np.sort(key, axis=1)[:, :SKIN.K_SKIN]
+    ids = (best & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    changed = np.any(np.sort(ids, axis=1) != np.sort(knn, axis=1), axis=1)
+    knn_out, w_out = knn.copy(), w.copy()
+    knn_out[changed] = ids[changed]
+    w_out[changed] = SKIN.skin_weights(np.asarray(v_ref, dtype=np.float64)[changed], node_p, node_sigma,
+                                       ids[changed])
+    return knn_out, w_out, changed

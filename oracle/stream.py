@@ -138,7 +138,7 @@ class OracleStream:
         return int(fused.sum())
 
     def append_frame(self, max_surfels, eps=APPEND.EPS, delta_nn=APPEND.DELTA_NN, h=APPEND.FD_STEP,
-                     t_low=APPEND.T_LOW_CONFID):
+                     t_low=APPEND.T_LOW_CONFID, extend_nodes=False, max_nodes=0):
         """Appending and removal after fuse_frame (see append.py).  Returns
         (candidates, appended, removed); the per-candidate record is kept in
         ``last_append``."""
@@ -166,8 +166,30 @@ class OracleStream:
         self.t_obs = np.concatenate([self.t_obs[stay], t_new])
         self.knn = np.concatenate([self.knn[stay], new_knn])
         self.w = np.concatenate([self.w[stay], new_w])
+        self.new_nodes = 0
+        if extend_nodes and len(acc):
+            self.extend_nodes(new_v, max_nodes)
         self.pattern = SOLVER.BlockMatrix.pattern(len(self.node_p), self.knn, self.graph).keys
         return len(pix), len(acc), int((~stay).sum())
+
+    def extend_nodes(self, v_app, max_nodes):
+        """Node-graph extension over the appended reference surfels (see
+        append.py): new nodes, their transforms, the graph and every surfel's
+        skinning over all nodes."""
+        unc = ~APPEND.covered(v_app, self.node_p, self.node_sigma)
+        new_p, new_s = APPEND.subsample_nodes(np.asarray(v_app)[unc], self.node_p, self.node_sigma,
+                                              max(0, max_nodes - len(self.node_p)))
+        self.new_nodes = len(new_p)
+        if not len(new_p):
+            return
+        new_dq = APPEND.new_node_transforms(new_p, self.node_p, self.node_sigma, self.node_dq)
+        self.node_p = np.concatenate([self.node_p, new_p.astype(np.float64)])
+        self.node_sigma = np.concatenate([self.node_sigma, new_s.astype(np.float64)])
+        self.node_dq = np.concatenate([self.node_dq, new_dq])
+        self.graph = SKIN.node_graph(self.node_p.astype(np.float32))
+        self.knn_pre_extension = self.knn.copy()
+        self.knn, self.w, self.reskinned = APPEND.merge_skinning(self.v_ref, self.knn, self.w, self.node_p,
+                                                                 self.node_sigma, len(self.node_p) - len(new_p))
 
     # -- read-back -----------------------------------------------------------
     def read_nodes(self):

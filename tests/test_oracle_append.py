@@ -214,3 +214,98 @@ def test_append_frame_compaction_and_round_trip():
     _, n_app2, _ = st2.append_frame(max_surfels=cap)
     assert n_app2 == 5 and len(st2.v_ref) == cap
     np.testing.assert_array_equal(st2.v_ref[-5:], st.v_ref[int(stay.sum()):int(stay.sum()) + 5])
+
+
+# ---------------------------------------------------------------- node-graph extension
+
+def test_coverage_and_greedy_subsampling_by_hand():
+    node_p = np.array([[0.0, 0.0, 1.0], [10.0, 0.0, 1.0]])
+    sig = np.array([1.0, 1.0])
+    pts = np.array([[0.5, 0.0, 1.0], [0.0, 0.99, 1.0], [0.0, 1.01, 1.0], [9.5, 0.5, 1.0], [5.0, 0.0, 1.0]])
+    assert list(AP.covered(pts, node_p, sig)) == [True, True, False, True, False]
+    # uncovered points on a line far from both nodes: 0, 0.3, 0.6, 1.0, 1.5, 2.2 (σ = 1)
+    line = np.array([[4.0 + x, 5.0, 1.0] for x in (0.0, 0.3, 0.6, 1.0, 1.5, 2.2)])
+    p, s = AP.subsample_nodes(line, node_p, sig, max_new=10)
+    np.testing.assert_allclose(p[:, 0], [4.0, 5.0, 6.2], atol=1e-6)
+    assert list(s) == [1.0, 1.0, 1.0]
+    p2, _ = AP.subsample_nodes(line, node_p, sig, max_new=2)
+    assert len(p2) == 2
+    # a point within σ of an old node is never taken
+    p3, _ = AP.subsample_nodes(np.array([[0.5, 0.0, 1.0]]), node_p, sig, max_new=10)
+    assert len(p3) == 0
+
+
+def test_new_node_takes_the_rigid_warp():
+    """Every old node moves by one rigid motion: a new node's transform is it."""
+    rot = Rotation.from_rotvec([0.1, 0.2, -0.05])
+    q = rot.as_quat()
+    q0 = np.array([q[3], q[0], q[1], q[2]])
+    t = np.array([0.02, 0.01, -0.03])
+    rng = np.random.default_rng(2)
+    node_p = rng.uniform(-0.1, 0.1, (12, 3)) + [0, 0, 1.0]
+    dq = np.tile(DQ.dq_from_rt(q0[None], t[None])[0], (12, 1))
+    new = AP.new_node_transforms(np.array([[0.01, 0.02, 1.01], [0.05, -0.05, 0.95]], np.float32), node_p,
+                                 np.full(12, 0.05), dq)
+    for d in new:
+        s = np.sign(d[0] * dq[0, 0])
+        np.testing.assert_allclose(s * d, dq[0], atol=1e-12)
+
+
+def _cut_nodes_scene():
+    """plain_tiny with 30% of its surfels and every node in that region removed."""
+    sc = synth.plain_tiny(seed=2)
+    x_cut = np.quantile(sc.surfel_v[:, 0], 0.7)
+    keep = sc.surfel_v[:, 0] < x_cut
+    keep_n = sc.node_p[:, 0] < x_cut - 0.05
+    return sc, keep, keep_n
+
+
+def test_extend_nodes_on_a_stream_matches_the_definitions():
+    from scipy.spatial import cKDTree
+    sc, keep, keep_n = _cut_nodes_scene()
+    c = sc.cam
+    st = OST.OracleStream(OST.Params(c.width, c.height, c.fx, c.fy, c.cx, c.cy))
+    n = int(keep.sum())
+    st.set_model(sc.surfel_v[keep], sc.surfel_n[keep], np.full(n, 0.002), np.full(n, 15.0),
+                 np.zeros((n, 2), np.int64), sc.node_p[keep_n], sc.node_sigma[keep_n])
+    n_old = len(st.node_p)
+    st.upload_depth(sc.frame(1), 1)
+    st.solve_frame(2, 8)
+    st.fuse_frame()
+    dq_old = st.node_dq.copy()
+    st.append_frame(10 ** 9, extend_nodes=True, max_nodes=n_old + 100)
+    k = st.new_nodes
+    assert k > 0 and len(st.node_p) == n_old + k
+    np.testing.assert_array_equal(st.node_dq[:n_old], dq_old)
+    new_p = st.node_p[n_old:]
+    sig = st.node_sigma[n_old:]
+    # new nodes are appended surfels, uncovered by the old nodes, at least σ apart
+    app = st.v_ref[-len(st.last_append["appended"]):].astype(np.float32)
+    assert all(np.any(np.all(app == p.astype(np.float32), axis=1)) for p in new_p)
+    d_old = cKDTree(st.node_p[:n_old]).query(new_p)[0]
+    assert np.all(d_old >= sig - 1e-6)
+    if k > 1:
+        dd = cKDTree(new_p).query(new_p, k=2)[0][:, 1]
+        assert np.all(dd >= sig - 1e-6)
+    # graph and skinning over all nodes (k-d tree, no ties expected on this data)
+    _, g = cKDTree(st.node_p).query(st.node_p, k=9)
+    np.testing.assert_array_equal(np.sort(st.graph, axis=1), np.sort(g[:, 1:], axis=1))
+    # where a surfel's old set is still its 4-NN over the old nodes at its
+    # current position (fusion may have moved it), the merged set is its
+    # 4-NN over all nodes
+    _, nn_old = cKDTree(st.node_p[:n_old]).query(st.v_ref, k=4)
+    _, nn = cKDTree(st.node_p).query(st.v_ref, k=4)
+    knn_before = st.knn_pre_extension
+    fresh = np.all(np.sort(knn_before, axis=1) == np.sort(nn_old, axis=1), axis=1)
+    assert fresh.mean() > 0.95
+    np.testing.assert_array_equal(np.sort(st.knn[fresh], axis=1), np.sort(nn[fresh], axis=1))
+    assert st.reskinned.sum() > 0 and np.all(st.knn[~st.reskinned] == knn_before[~st.reskinned])
+    # a second stream with no room for new nodes keeps its graph
+    st2 = OST.OracleStream(OST.Params(c.width, c.height, c.fx, c.fy, c.cx, c.cy))
+    st2.set_model(sc.surfel_v[keep], sc.surfel_n[keep], np.full(n, 0.002), np.full(n, 15.0),
+                  np.zeros((n, 2), np.int64), sc.node_p[keep_n], sc.node_sigma[keep_n])
+    st2.upload_depth(sc.frame(1), 1)
+    st2.solve_frame(2, 8)
+    st2.fuse_frame()
+    st2.append_frame(10 ** 9, extend_nodes=True, max_nodes=n_old)
+    assert st2.new_nodes == 0 and len(st2.node_p) == n_old

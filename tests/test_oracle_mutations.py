@@ -230,3 +230,25 @@ def test_splat_ties_to_the_higher_id(monkeypatch):
         return np.where(rev >= 0, k - 1 - rev, -1)
     monkeypatch.setattr(V, "visibility_map", bad)
     _fails(T.test_equal_depths_go_to_the_lower_id_and_hidden_splats_are_invisible)
+
+
+def test_subsampling_ignores_accepted_nodes(monkeypatch):
+    """Sub-sampling that checks only the old nodes: the hand-worked line gives too many nodes."""
+    import test_oracle_append as T
+    from oracle import append as AP
+
+    def bad(v_unc, node_p, node_sigma, max_new):
+        v32 = np.asarray(v_unc, dtype=np.float32)
+        p32 = np.asarray(node_p, dtype=np.float32)
+        s32 = np.asarray(node_sigma, dtype=np.float32)
+        new_p, new_s = [], []
+        for v in v32[:max_new]:
+            d_old = AP.d2_fp32(p32, v[None, :])
+            j0 = int(np.argmin(d_old))
+            if np.any(d_old < s32[j0] * s32[j0]):
+                continue
+            new_p.append(v)
+            new_s.append(s32[j0])
+        return np.asarray(new_p, np.float32).reshape(-1, 3), np.asarray(new_s, np.float32)
+    monkeypatch.setattr(AP, "subsample_nodes", bad)
+    _fails(T.test_coverage_and_greedy_subsampling_by_hand)
