@@ -92,6 +92,8 @@ typedef struct {
   float delta_nn;               /* δ_nn, least sum of a new surfel's live weights (not in Table 1: 0.3) */
   float fd_step;                /* finite-difference step of the Eq. 8 strain, metres (1 mm) */
   int t_low_confid;             /* t_low_confid, frames (Table 1: 30) */
+  int extend_nodes;             /* 1 (default): node-graph extension after appending, while the
+                                   stream has room below max_nodes (sw_append_frame) */
 } sw_params;
 
 /* Per-call statistics of sw_solve_frame; entry i describes Gauss-Newton
@@ -423,7 +425,13 @@ sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
  * removed.  The new caller order is the surviving surfels in their order,
  * then the appended ones in pixel order; appended surfels beyond max_surfels
  * are dropped from the end.  Node positions, the graph and the transforms
- * are unchanged; the JᵀJ pattern, the runner and the solve graphs are
+ * are unchanged unless the node graph is extended: with extend_nodes and
+ * room below max_nodes, appended surfels farther than every node's radius
+ * (σ_j, node4.w) from it are sub-sampled in order into new nodes (at least
+ * the nearest old node's σ apart from every node; each takes that σ and the
+ * current warp at its position as its transform), the 8-NN graph is
+ * recomputed and every surfel whose 4 nearest nodes now include a new node
+ * is re-skinned.  The JᵀJ pattern, the runner and the solve graphs are
  * rebuilt (the call synchronises and allocates scratch).  A batch holding
  * the stream must be re-created afterwards.  *stats (nullable) receives
  * the counts.
@@ -437,6 +445,7 @@ typedef struct {
   int n_surfels;         /* surfels after the call */
   double kernel_ms;      /* device time of the appending kernels (CUDA events), model rebuild excluded */
   double rebuild_ms;     /* host time of the model rebuild (set sort, JᵀJ pattern, runner) */
+  int new_nodes;         /* nodes added by the node-graph extension */
 } sw_append_stats;
 sw_status sw_append_frame(sw_handle h, sw_append_stats* stats);
 /* Per-candidate record of the last sw_append_frame, candidate order (row-

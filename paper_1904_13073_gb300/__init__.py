@@ -39,7 +39,7 @@ class sw_params(ctypes.Structure):
                 ("corr_dist", ctypes.c_float), ("corr_normal", ctypes.c_float), ("stable_conf", ctypes.c_float),
                 ("recent_frames", ctypes.c_int), ("precision", ctypes.c_int), ("visibility", ctypes.c_int),
                 ("eps", ctypes.c_float), ("delta_nn", ctypes.c_float), ("fd_step", ctypes.c_float),
-                ("t_low_confid", ctypes.c_int)]
+                ("t_low_confid", ctypes.c_int), ("extend_nodes", ctypes.c_int)]
 
 
 class sw_solve_stats(ctypes.Structure):
@@ -58,7 +58,7 @@ class sw_solve_stats(ctypes.Structure):
 class sw_append_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int), ("rejected_nn", ctypes.c_int), ("rejected_strain", ctypes.c_int),
                 ("appended", ctypes.c_int), ("removed", ctypes.c_int), ("n_surfels", ctypes.c_int),
-                ("kernel_ms", ctypes.c_double), ("rebuild_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("rebuild_ms", ctypes.c_double), ("new_nodes", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -477,6 +477,7 @@ bool params_ok(const sw_params* p, std::string& why) {
   if (p->max_nodes < 9 || p->max_nodes > SW_MAX_NODES) { why = "max_nodes must be in [9, 65535]"; return false; }
   if (!(p->lambda >= 0 && p->fuse_dist >= 0 && p->corr_dist >= 0)) { why = "negative threshold"; return false; }
   if (p->visibility != 0 && p->visibility != 1) { why = "visibility must be 0 or 1"; return false; }
+  if (p->extend_nodes != 0 && p->extend_nodes != 1) { why = "extend_nodes must be 0 or 1"; return false; }
   if (!(p->eps > 0 && p->eps < 1 && p->delta_nn >= 0 && p->fd_step > 0)) {
     why = "appending parameters out of range (0 < eps < 1, delta_nn >= 0, fd_step > 0)";
     return false;
@@ -666,6 +667,7 @@ sw_status sw_params_default(sw_params* p, int width, int height, float fx, float
   p->recent_frames = 2;     // Table 1
   p->precision = SW_PRECISION_MIXED;
   p->visibility = 0;
+  p->extend_nodes = 1;
   p->eps = 0.2f;            // Table 1
   p->delta_nn = 0.3f;
   p->fd_step = 1e-3f;
@@ -1323,6 +1325,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     stats->removed = n_old - n_stay;
     stats->n_surfels = n_new;
     stats->kernel_ms = stats->rebuild_ms = 0.0;
+    stats->new_nodes = 0;
   }
   s->app_last_cand = n_cand;
   if (n_app == 0 && n_stay == n_old) {   // nothing appended or removed: the model stands as it is
@@ -1345,6 +1348,31 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
                           tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(), st);
     launch_knn_skin(h, tv.as<float4>() + n_stay, n_app, ids.as<int>(), d2.as<float>(), tknn.as<int4>() + n_stay,
                     tw.as<float4>() + n_stay, st);
+    // node-graph extension over the appended surfels (Sec. 6.4, last paragraph)
+    int new_nodes = 0;
+    const int n_old_nodes = h.n_n;
+    if (s->p.extend_nodes && n_app > 0 && h.n_n < s->p.max_nodes) {
+      Tmp unc((size_t)n_app * 4), list((size_t)n_app * 4), cnt(16), sig((size_t)n_app * 4), near((size_t)n_app * 4);
+      if (!unc.p || !list.p || !cnt.p || !sig.p || !near.p)
+        return fail(s, SW_ERR_NO_MEMORY, "node extension scratch allocation failed");
+      launch_node_cover(h, tv.as<float4>(), n_stay, n_app, unc.as<int>(), st);
+      SW_CUDA(s, launch_node_subsample(h, a, tv.as<float4>(), n_stay, n_app, unc.as<int>(), list.as<int>(),
+                                       cnt.as<int>(), sig.as<float>(), near.as<int>(), n_old_nodes,
+                                       s->p.max_nodes - n_old_nodes, cnt.as<int>() + 1, st));
+      SW_CUDA(s, cudaMemcpyAsync(&new_nodes, cnt.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(s, cudaStreamSynchronize(st));
+      if (new_nodes > 0) {
+        Tmp nid((size_t)new_nodes * 16);
+        if (!nid.p) return fail(s, SW_ERR_NO_MEMORY, "node extension scratch allocation failed");
+        launch_knn4(h.node_p + n_old_nodes, new_nodes, h.node_p, n_old_nodes, nid.as<int>(), st);
+        launch_new_node_dq(h, n_old_nodes, new_nodes, nid.as<int>(), st);
+        h.n_n = n_old_nodes + new_nodes;
+        launch_node_graph(h, st);
+        launch_skin_merge(h, tv.as<float4>(), n_new, n_old_nodes, tknn.as<int4>(), tw.as<float4>(), st);
+        SW_CUDA(s, cudaStreamSynchronize(st));
+      }
+    }
+    if (stats) stats->new_nodes = new_nodes;
     SW_CUDA(s, cudaGetLastError());
     SW_CUDA(s, cudaEventRecord(ev1, st));
     SW_CUDA(s, cudaStreamSynchronize(st));
@@ -1364,7 +1392,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     int n_sets = 0;
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets, &n_sets));
-    SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, false));
+    SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, new_nodes > 0));
     if (stats) stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   s->fused = false;

@@ -250,7 +250,175 @@ cudaError_t compact(const AppendBufs& a, const int* flag, int n, int* out, int* 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ node-graph extension
+// (Sec. 6.4, last paragraph): coverage of the appended reference surfels by
+// the node radii, greedy sub-sampling of the uncovered ones into new nodes,
+// their transforms from the current warp, and each surfel's set compared
+// with the new nodes.  Distances that decide are exact-order FP32.
+
+// a warp per appended surfel: 1 when no node j has ‖v − p_j‖² < σ_j²
+__global__ void k_node_cover(SwDev d, const float4* __restrict__ tv, int first, int n, int* __restrict__ unc) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const float4 v = tv[first + k];
+  bool cov = false;
+  for (int j = lane; j < d.n_n && !cov; j += 32) {
+    const float4 p = __ldg(d.node_p + j);
+    cov = dist2_rn(v.x, v.y, v.z, p.x, p.y, p.z) < __fmul_rn(p.w, p.w);
+  }
+  cov = __any_sync(0xffffffffu, cov);
+  if (lane == 0) unc[k] = cov ? 0 : 1;
+}
+
+// a warp per uncovered surfel: σ of its nearest old node (ties to the lower
+// id) and whether some old node lies within that σ
+__global__ void k_node_near(SwDev d, const float4* __restrict__ tv, int first, const int* __restrict__ list,
+                            const int* __restrict__ n_list, float* __restrict__ sig, int* __restrict__ near) {
+  const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (u >= *n_list) return;
+  const float4 v = tv[first + list[u]];
+  float bd = __int_as_float(0x7f800000);
+  int bi = 0x7fffffff;
+  for (int j = lane; j < d.n_n; j += 32) {
+    const float4 p = __ldg(d.node_p + j);
+    const float d2 = dist2_rn(p.x, p.y, p.z, v.x, v.y, v.z);
+    if (d2 < bd || (d2 == bd && j < bi)) { bd = d2; bi = j; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (od < bd || (od == bd && oi < bi)) { bd = od; bi = oi; }
+  }
+  const float s = __ldg(d.node_p + bi).w, s2 = __fmul_rn(s, s);
+  bool close = false;
+  for (int j = lane; j < d.n_n && !close; j += 32) {
+    const float4 p = __ldg(d.node_p + j);
+    close = dist2_rn(p.x, p.y, p.z, v.x, v.y, v.z) < s2;
+  }
+  close = __any_sync(0xffffffffu, close);
+  if (lane == 0) { sig[u] = s; near[u] = close ? 1 : 0; }
+}
+
+// one warp, in order: an uncovered surfel becomes node n_old + count unless an
+// old node or a node taken before it lies within its σ
+__global__ void k_node_greedy(SwDev d, const float4* __restrict__ tv, int first, const int* __restrict__ list,
+                              const int* __restrict__ n_list, const float* __restrict__ sig,
+                              const int* __restrict__ near, int n_old, int max_new, int* __restrict__ n_new) {
+  const int lane = threadIdx.x & 31;
+  const int n = *n_list;
+  int count = 0;
+  for (int u = 0; u < n && count < max_new; ++u) {
+    if (near[u]) continue;
+    const float4 v = tv[first + list[u]];
+    const float s2 = __fmul_rn(sig[u], sig[u]);
+    bool close = false;
+    for (int k = lane; k < count; k += 32) {
+      const float4 p = d.node_p[n_old + k];
+      close = close || dist2_rn(p.x, p.y, p.z, v.x, v.y, v.z) < s2;
+    }
+    close = __any_sync(0xffffffffu, close);
+    if (!close) {
+      if (lane == 0) d.node_p[n_old + count] = make_float4(v.x, v.y, v.z, sig[u]);
+      ++count;
+      __syncwarp();
+    }
+  }
+  if (lane == 0) *n_new = count;
+}
+
+// a new node's transform: the normalised blend (Eq. 1, FP64) of its 4 nearest
+// old nodes with their weights at its position
+__global__ void k_new_node_dq(SwDev d, int n_old, int k_new, const int* __restrict__ ids) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= k_new) return;
+  const int j = n_old + k;
+  const D3 x = d3(d.node_p[j]);
+  DQ64 b{0.0, D3{0.0, 0.0, 0.0}, 0.0, D3{0.0, 0.0, 0.0}};
+  const DQ64 q0 = node_dq64(d, ids[4 * k]);
+  for (int a = 0; a < 4; ++a) {
+    const int id = ids[4 * k + a];
+    const float4 p = d.node_p[id];
+    const D3 e = x - d3(p);
+    const double sg = (double)p.w;
+    double w = exp(-dot3(e, e) / (2.0 * sg * sg));
+    const DQ64 q = node_dq64(d, id);
+    if (q.W * q0.W + dot3(q.A, q0.A) < 0.0) w = -w;
+    b.W += w * q.W; b.A = b.A + w * q.A; b.We += w * q.We; b.Ae = b.Ae + w * q.Ae;
+  }
+  const double inv = 1.0 / sqrt(dq_norm2(b));
+  double o[8] = {b.W * inv, b.A.x * inv, b.A.y * inv, b.A.z * inv, b.We * inv, b.Ae.x * inv, b.Ae.y * inv, b.Ae.z * inv};
+  const double dd = o[0] * o[4] + o[1] * o[5] + o[2] * o[6] + o[3] * o[7];
+  for (int c = 0; c < 4; ++c) o[4 + c] -= dd * o[c];
+  if (d.dq64)
+    for (int c = 0; c < 8; ++c) d.dq64[8 * (size_t)j + c] = o[c];
+  d.dq[2 * j] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+  d.dq[2 * j + 1] = make_float4((float)o[4], (float)o[5], (float)o[6], (float)o[7]);
+}
+
+// each surfel's set against the nodes n_old .. n_n − 1: the 4 smallest (d², id)
+// of the old set and the new nodes at its position; a changed set is written
+// in distance order with its Eq. 1 weights, an unchanged one is left alone
+__global__ void k_skin_merge(SwDev d, const float4* __restrict__ tv, int n, int n_old, int4* __restrict__ tknn,
+                             float4* __restrict__ tw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = tv[i];
+  const int4 k0 = tknn[i];
+  const int old_ids[4] = {k0.x, k0.y, k0.z, k0.w};
+  float bd[4];
+  int bi[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) { bd[a] = __int_as_float(0x7f800000); bi[a] = 0x7fffffff; }
+  auto offer = [&](int id) {
+    const float4 p = __ldg(d.node_p + id);
+    float cd = dist2_rn(v.x, v.y, v.z, p.x, p.y, p.z);
+    int ci = id;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      if (cd < bd[a] || (cd == bd[a] && ci < bi[a])) {
+        const float td = bd[a]; const int ti = bi[a];
+        bd[a] = cd; bi[a] = ci;
+        cd = td; ci = ti;
+      }
+  };
+#pragma unroll
+  for (int a = 0; a < 4; ++a) offer(old_ids[a]);
+  for (int j = n_old; j < d.n_n; ++j) offer(j);
+  bool same = true;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) same = same && bi[a] < n_old;   // no new node entered: the old set stands
+  if (same) return;
+  float w[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float sg = __ldg(&d.node_p[bi[a]].w);
+    w[a] = expf(-bd[a] / (2.f * sg * sg));
+  }
+  tknn[i] = make_int4(bi[0], bi[1], bi[2], bi[3]);
+  tw[i] = make_float4(w[0], w[1], w[2], w[3]);
+}
+
 }  // namespace
+
+void launch_node_cover(const SwDev& d, const float4* tv, int first, int n, int* unc, cudaStream_t st) {
+  if (n) k_node_cover<<<(int)(((size_t)n * 32 + 127) / 128), 128, 0, st>>>(d, tv, first, n, unc);
+}
+cudaError_t launch_node_subsample(const SwDev& d, const AppendBufs& a, const float4* tv, int first, int n_app,
+                                  const int* unc_flags, int* unc_list, int* n_unc, float* sig, int* near,
+                                  int n_old, int max_new, int* n_new, cudaStream_t st) {
+  cudaError_t e = compact(a, unc_flags, n_app, unc_list, n_unc, st);
+  if (e != cudaSuccess) return e;
+  if (n_app) k_node_near<<<(int)(((size_t)n_app * 32 + 127) / 128), 128, 0, st>>>(d, tv, first, unc_list, n_unc, sig, near);
+  k_node_greedy<<<1, 32, 0, st>>>(d, tv, first, unc_list, n_unc, sig, near, n_old, max_new, n_new);
+  return cudaGetLastError();
+}
+void launch_new_node_dq(const SwDev& d, int n_old, int k_new, const int* ids, cudaStream_t st) {
+  if (k_new) k_new_node_dq<<<(k_new + 63) / 64, 64, 0, st>>>(d, n_old, k_new, ids);
+}
+void launch_skin_merge(const SwDev& d, const float4* tv, int n, int n_old, int4* tknn, float4* tw, cudaStream_t st) {
+  if (n) k_skin_merge<<<(n + 255) / 256, 256, 0, st>>>(d, tv, n, n_old, tknn, tw);
+}
 
 size_t append_cub_bytes(int n_pixels, int n_surfels) {
   size_t bytes = 0;

@@ -224,6 +224,17 @@ void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_
                            int n_stay, int n_app, float4* tv, float4* tn, int2* tt, int4* tknn, float4* tw,
                            cudaStream_t st);
 void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st);
+// node-graph extension after appending (k_append.cu): coverage flags of the
+// surfels tv[first, first + n) (1 = uncovered), the greedy sub-sampling that
+// writes new nodes to node_p[n_old ..] and their count to *n_new, the new
+// transforms from the current warp (ids: their 4 nearest old nodes), and the
+// merge of every surfel's set with the new nodes
+void launch_node_cover(const SwDev& d, const float4* tv, int first, int n, int* unc, cudaStream_t st);
+cudaError_t launch_node_subsample(const SwDev& d, const AppendBufs& a, const float4* tv, int first, int n_app,
+                                  const int* unc_flags, int* unc_list, int* n_unc, float* sig, int* near,
+                                  int n_old, int max_new, int* n_new, cudaStream_t st);
+void launch_new_node_dq(const SwDev& d, int n_old, int k_new, const int* ids, cudaStream_t st);
+void launch_skin_merge(const SwDev& d, const float4* tv, int n, int n_old, int4* tknn, float4* tw, cudaStream_t st);
 
 // ------------------------------------------------------------------ JᵀJ pattern
 // Device scratch of the pattern build (k_pattern.cu); K = 10 n_sets + 9 n_n keys.

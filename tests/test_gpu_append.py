@@ -50,11 +50,11 @@ def _cut(scene, frac=0.3, unstable=7):
 
 
 class Both:
-    def __init__(self, scene, max_surfels, precision=sw.SW_PRECISION_MIXED):
+    def __init__(self, scene, max_surfels, precision=sw.SW_PRECISION_MIXED, max_nodes=None):
         c = scene.cam
         self.scene = scene
         v4, n4, t2, node4 = sw.model_arrays(scene)
-        self.h = sw.sw_create_stream(sw.params_for(c, max_surfels, len(node4), precision=precision))
+        self.h = sw.sw_create_stream(sw.params_for(c, max_surfels, max_nodes or len(node4), precision=precision))
         sw.sw_set_model(self.h, v4, n4, t2, node4)
         self.o = oracle.OracleStream(oracle.Params(c.width, c.height, c.fx, c.fy, c.cx, c.cy))
         self.o.set_model(scene.surfel_v, scene.surfel_n, scene.surfel_r, scene.surfel_c, scene.surfel_t,
@@ -261,5 +261,68 @@ def test_append_end_to_end_then_solve_on_the_grown_model():
         assert rotation_angle_between(dq, b.o.node_dq).max() < 1e-4
         got = OS.node_transform(dq, b.o.node_p)
         assert np.linalg.norm(got - b.o.warped_nodes(), axis=1).max() < 2e-5
+    finally:
+        b.close()
+
+
+def _cut_nodes(scene, frac=0.3):
+    """The scene with its largest-x surfels and the nodes in that region removed,
+    so that the appended surfels there are farther than every node's radius."""
+    x_cut = np.quantile(scene.surfel_v[:, 0], 1.0 - frac)
+    sc = _cut(scene, frac)
+    keep_n = scene.node_p[:, 0] < x_cut - 0.05
+    return dataclasses.replace(sc, node_p=scene.node_p[keep_n], node_sigma=scene.node_sigma[keep_n])
+
+
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_FP64])
+def test_node_extension_matches_oracle(precision):
+    """Identical FP32 inputs on both sides (maps, node transforms, live
+    surfels); appending with node-graph extension: the new nodes, their
+    transforms, the graph and every surfel's skinning agree, and the next
+    solve runs on the extended graph."""
+    scene = _cut_nodes(synth.plain_tiny(seed=2))
+    c = scene.cam
+    n_old = len(scene.node_p)
+    b = Both(scene, len(scene.surfel_v) + c.width * c.height, precision, max_nodes=n_old + 64)
+    try:
+        d = scene.frame(1)
+        sw.sw_upload_depth(b.h, d, 1)
+        b.o.upload_depth(d, 1)
+        b.set_maps()
+        dq8 = _warp(scene, 5, 0.5, 0.002, alpha=0.0)
+        sw.sw_set_node_dq(b.h, dq8)
+        b.o.node_dq = dq8.astype(np.float64)
+        _, vl, nl = OS.warp_surfels(b.o.v_ref, b.o.n_ref, b.o.knn, b.o.w, b.o.node_dq)
+        vl32, nl32 = vl.astype(F32), nl.astype(F32)
+        sw.sw_debug_set_live(b.h, vl32, nl32)
+        sw.sw_debug_fusion_targets(b.h, c.height, c.width)
+        st = sw.sw_append_frame(b.h)
+        b.o.last_index_map = OFU.index_map(vl32, b.o.p.cam)
+        _, n_app, n_rem = b.o.append_frame(b.max_surfels, EPS, DNN, FDH, extend_nodes=True, max_nodes=n_old + 64)
+        assert st["appended"] == n_app and st["removed"] == n_rem
+        assert st["new_nodes"] == b.o.new_nodes > 0
+        pos, dq = sw.sw_read_nodes(b.h)
+        assert len(pos) == len(b.o.node_p) == n_old + st["new_nodes"]
+        np.testing.assert_allclose(pos[:, :3], b.o.node_p, atol=2e-6)
+        np.testing.assert_array_equal(pos[:, 3], b.o.node_sigma.astype(F32))
+        np.testing.assert_array_equal(dq[:n_old], dq8)
+        assert np.max(rotation_angle_between(dq[n_old:].astype(np.float64), b.o.node_dq[n_old:])) < 1e-6
+        np.testing.assert_allclose(OS.node_transform(dq[n_old:].astype(np.float64), b.o.node_p[n_old:]),
+                                   OS.node_transform(b.o.node_dq[n_old:], b.o.node_p[n_old:]), atol=2e-6)
+        np.testing.assert_array_equal(sw.sw_read_graph(b.h), b.o.graph)
+        knn, w = sw.sw_read_skinning(b.h)
+        np.testing.assert_array_equal(knn, b.o.knn)
+        np.testing.assert_allclose(w, b.o.w, rtol=2e-6, atol=1e-30)
+        # the next frame solves on the extended graph
+        sw.sw_upload_depth(b.h, d, 2)
+        b.o.upload_depth(d, 2)
+        b.set_maps()
+        st2 = sw.sw_solve_frame(b.h, 2, 8)
+        ost2 = b.o.solve_frame(2, 8)
+        assert abs(st2["n_corr"][0] - ost2[0].n_corr) <= 3
+        _, dq2 = sw.sw_read_nodes(b.h)
+        dq2 = dq2.astype(np.float64)
+        assert rotation_angle_between(dq2, b.o.node_dq).max() < 1e-4
+        assert np.linalg.norm(OS.node_transform(dq2, b.o.node_p) - b.o.warped_nodes(), axis=1).max() < 2e-5
     finally:
         b.close()
