@@ -667,9 +667,10 @@ def main():
     sw.sw_destroy_stream(h)
     room = len(v4) + c.width * c.height
 
-    def append_case(keep, n_calls):
-        ha = sw.sw_create_stream(sw.params_for(c, room, len(node4)), stream)
-        sw.sw_set_model(ha, v4[keep], n4[keep], t2[keep], node4)
+    def append_case(keep, n_calls, keep_nodes=None, node_room=0):
+        nodes = node4 if keep_nodes is None else node4[keep_nodes]
+        ha = sw.sw_create_stream(sw.params_for(c, room, len(nodes) + node_room), stream)
+        sw.sw_set_model(ha, v4[keep], n4[keep], t2[keep], nodes)
         out = []
         for k in range(n_calls):
             sw.sw_upload_depth(ha, dev_frames[ts[k]], k + 1)
@@ -684,8 +685,12 @@ def main():
         return out
     appends = append_case(np.ones(len(v4), bool), 3)
     # and a model with 30% of its surfels cut away (the early-frame regime)
-    cut_st = append_case(scene.surfel_v[:, 0] < np.quantile(scene.surfel_v[:, 0], 0.7), 1)[0]
-    appending = {"steady": appends[1:], "model_cut_30pct": cut_st,
+    x_cut = np.quantile(scene.surfel_v[:, 0], 0.7)
+    cut_st = append_case(scene.surfel_v[:, 0] < x_cut, 1)[0]
+    # and with the nodes of that region cut too, and room for 256 more: the
+    # node graph is extended over the appended surfels
+    ext_st = append_case(scene.surfel_v[:, 0] < x_cut, 1, scene.node_p[:, 0] < x_cut - scene.node_sigma[0], 256)[0]
+    appending = {"steady": appends[1:], "model_cut_30pct": cut_st, "model_and_nodes_cut_30pct": ext_st,
                  "note": "kernel_ms: device time of the appending kernels (events); rebuild_ms: host-side "
                          "model rebuild (set sort, JtJ pattern, runner); call_ms: the whole call"}
     batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
