@@ -57,6 +57,7 @@ EPS = 0.2            # ε, Table 1
 DELTA_NN = 0.3       # δ_nn (reading)
 FD_STEP = 1e-3       # finite-difference step of Eq. 8, metres (reading)
 T_LOW_CONFID = 30    # t_low_confid, Table 1
+MAX_NEW_NODES = 2048  # node-graph extension: most new nodes per call (reading)
 
 
 def empty_window_pixels(imap, usable):
@@ -181,7 +182,8 @@ def append_candidates(pix, maps, node_dq, node_p, node_sigma, eps=EPS, delta_nn=
 #   in distance order and its Eq. 1 weights at its current position, the
 #   others keep their set and weights (fusion may have moved them a little
 #   since they were skinned);
-# * new nodes past the stream's node capacity are not added.
+# * new nodes past the stream's node capacity, or past 2048 in one call, are
+#   not added.
 # ---------------------------------------------------------------------------
 
 def covered(v_app, node_p, node_sigma):

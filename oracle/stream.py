@@ -178,7 +178,7 @@ class OracleStream:
         skinning over all nodes."""
         unc = ~APPEND.covered(v_app, self.node_p, self.node_sigma)
         new_p, new_s = APPEND.subsample_nodes(np.asarray(v_app)[unc], self.node_p, self.node_sigma,
-                                              max(0, max_nodes - len(self.node_p)))
+                                              min(APPEND.MAX_NEW_NODES, max(0, max_nodes - len(self.node_p))))
         self.new_nodes = len(new_p)
         if not len(new_p):
             return

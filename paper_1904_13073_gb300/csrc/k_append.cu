@@ -301,27 +301,51 @@ __global__ void k_node_near(SwDev d, const float4* __restrict__ tv, int first, c
 }
 
 // one warp, in order: an uncovered surfel becomes node n_old + count unless an
-// old node or a node taken before it lies within its σ
-__global__ void k_node_greedy(SwDev d, const float4* __restrict__ tv, int first, const int* __restrict__ list,
-                              const int* __restrict__ n_list, const float* __restrict__ sig,
-                              const int* __restrict__ near, int n_old, int max_new, int* __restrict__ n_new) {
+// old node or a node taken before it lies within its σ.  The surfels come in
+// chunks of 32 (one per lane, loaded together); the lanes that are not next to
+// an old node are taken in lane order by a ballot, their position passed by
+// shuffles, and tested against the nodes taken so far, which are kept in
+// shared memory (at most kMaxNewNodes per call).
+constexpr int kMaxNewNodes = 2048;
+
+__global__ void __launch_bounds__(32) k_node_greedy(SwDev d, const float4* __restrict__ tv, int first,
+                                                    const int* __restrict__ list, const int* __restrict__ n_list,
+                                                    const float* __restrict__ sig, const int* __restrict__ near,
+                                                    int n_old, int max_new, int* __restrict__ n_new) {
+  __shared__ float4 taken[kMaxNewNodes];
   const int lane = threadIdx.x & 31;
-  const int n = *n_list;
+  const int n = *n_list, cap = min(max_new, kMaxNewNodes);
   int count = 0;
-  for (int u = 0; u < n && count < max_new; ++u) {
-    if (near[u]) continue;
-    const float4 v = tv[first + list[u]];
-    const float s2 = __fmul_rn(sig[u], sig[u]);
-    bool close = false;
-    for (int k = lane; k < count; k += 32) {
-      const float4 p = d.node_p[n_old + k];
-      close = close || dist2_rn(p.x, p.y, p.z, v.x, v.y, v.z) < s2;
+  for (int base = 0; base < n && count < cap; base += 32) {
+    const int u = base + lane;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool cand = false;
+    if (u < n && !near[u]) {
+      v = tv[first + list[u]];
+      v.w = sig[u];
+      cand = true;
     }
-    close = __any_sync(0xffffffffu, close);
-    if (!close) {
-      if (lane == 0) d.node_p[n_old + count] = make_float4(v.x, v.y, v.z, sig[u]);
-      ++count;
-      __syncwarp();
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    while (m && count < cap) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      const float vx = __shfl_sync(0xffffffffu, v.x, b), vy = __shfl_sync(0xffffffffu, v.y, b);
+      const float vz = __shfl_sync(0xffffffffu, v.z, b), vs = __shfl_sync(0xffffffffu, v.w, b);
+      const float s2 = __fmul_rn(vs, vs);
+      bool close = false;
+      for (int k = lane; k < count; k += 32) {
+        const float4 p = taken[k];
+        close = close || dist2_rn(p.x, p.y, p.z, vx, vy, vz) < s2;
+      }
+      close = __any_sync(0xffffffffu, close);
+      if (!close) {
+        if (lane == 0) {
+          taken[count] = make_float4(vx, vy, vz, vs);
+          d.node_p[n_old + count] = make_float4(vx, vy, vz, vs);
+        }
+        ++count;
+        __syncwarp();
+      }
     }
   }
   if (lane == 0) *n_new = count;
