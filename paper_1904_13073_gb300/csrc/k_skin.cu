@@ -75,27 +75,42 @@ __device__ __forceinline__ void knn_cswap(float* d, int* i, int a, int b) {
 }
 
 // The same selection with one warp per query, for few queries: lane l scans
-// nodes l, l + 32, ... and keeps its own 4 best; five butterfly rounds merge
+// nodes l, l + 32, ... and keeps its own K best; five butterfly rounds merge
 // the lanes' sorted lists (the lower half of a bitonic merge, c_k =
-// min(a_k, b_{3-k}), then a 4-element bitonic sort), so every lane ends with
-// the 4 smallest (d², id) of all nodes: the same unique result as k_knn<4>.
+// min(a_k, b_{K-1-k}), then a K-element bitonic sort), so every lane ends
+// with the K smallest (d², id) of all nodes: the same unique result as
+// k_knn<K>.
+template <int K>
+__device__ __forceinline__ void knn_bitonic_sort(float* d, int* i) {
+  if (K == 8) {
+    knn_cswap(d, i, 0, 4); knn_cswap(d, i, 1, 5); knn_cswap(d, i, 2, 6); knn_cswap(d, i, 3, 7);
+  }
+  knn_cswap(d, i, 0, 2); knn_cswap(d, i, 1, 3);
+  if (K == 8) { knn_cswap(d, i, 4, 6); knn_cswap(d, i, 5, 7); }
+  knn_cswap(d, i, 0, 1); knn_cswap(d, i, 2, 3);
+  if (K == 8) { knn_cswap(d, i, 4, 5); knn_cswap(d, i, 6, 7); }
+}
+
+template <int K>
 __global__ void __launch_bounds__(kQThreads)
-k_knn4_warp(const float4* __restrict__ queries, int n_q, const float4* __restrict__ nodes, int n_n,
-            int* __restrict__ out_ids, float* __restrict__ out_d2) {
+k_knn_warp(const float4* __restrict__ queries, int n_q, const float4* __restrict__ nodes, int n_n, int exclude_self,
+           int* __restrict__ out_ids, float* __restrict__ out_d2) {
+  static_assert(K == 4 || K == 8, "bitonic network for 4 or 8");
   const int qi = (blockIdx.x * kQThreads + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (qi >= n_q) return;   // uniform across the warp
   const float3 q = f3(queries[qi]);
-  float bd[4];
-  int bi[4];
+  float bd[K];
+  int bi[K];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0x7fffffff; }
+  for (int k = 0; k < K; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0x7fffffff; }
   for (int j = lane; j < n_n; j += 32) {
+    if (exclude_self && j == qi) continue;
     const float4 p = __ldg(nodes + j);
     float cd = dist2_rn(q.x, q.y, q.z, p.x, p.y, p.z);
     int ci = j;
-    if (knn_less(cd, ci, bd[3], bi[3])) {
+    if (knn_less(cd, ci, bd[K - 1], bi[K - 1])) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < K; ++k)
         if (knn_less(cd, ci, bd[k], bi[k])) {
           const float td = bd[k]; const int ti = bi[k];
           bd[k] = cd; bi[k] = ci;
@@ -105,29 +120,26 @@ k_knn4_warp(const float4* __restrict__ queries, int n_q, const float4* __restric
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    float od[4];
-    int oi[4];
+    float od[K];
+    int oi[K];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < K; ++k) {
       od[k] = __shfl_xor_sync(0xffffffffu, bd[k], o);
       oi[k] = __shfl_xor_sync(0xffffffffu, bi[k], o);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (knn_less(od[3 - k], oi[3 - k], bd[k], bi[k])) { bd[k] = od[3 - k]; bi[k] = oi[3 - k]; }
-    knn_cswap(bd, bi, 0, 2);
-    knn_cswap(bd, bi, 1, 3);
-    knn_cswap(bd, bi, 0, 1);
-    knn_cswap(bd, bi, 2, 3);
+    for (int k = 0; k < K; ++k)
+      if (knn_less(od[K - 1 - k], oi[K - 1 - k], bd[k], bi[k])) { bd[k] = od[K - 1 - k]; bi[k] = oi[K - 1 - k]; }
+    knn_bitonic_sort<K>(bd, bi);
   }
-  if (lane < 4) {
+  if (lane < K) {
     int id = bi[0];
     float d = bd[0];
 #pragma unroll
-    for (int k = 1; k < 4; ++k)
+    for (int k = 1; k < K; ++k)
       if (lane == k) { id = bi[k]; d = bd[k]; }
-    out_ids[(size_t)qi * 4 + lane] = id;
-    if (out_d2) out_d2[(size_t)qi * 4 + lane] = d;
+    out_ids[(size_t)qi * K + lane] = id;
+    if (out_d2) out_d2[(size_t)qi * K + lane] = d;
   }
 }
 
@@ -136,8 +148,8 @@ constexpr int kWarpKnnMaxQueries = 40000;
 
 void knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, float* d2, cudaStream_t st) {
   if (n_q <= kWarpKnnMaxQueries)
-    k_knn4_warp<<<(int)(((size_t)n_q * 32 + kQThreads - 1) / kQThreads), kQThreads, 0, st>>>(queries, n_q, nodes,
-                                                                                              n_n, ids, d2);
+    k_knn_warp<4><<<(int)(((size_t)n_q * 32 + kQThreads - 1) / kQThreads), kQThreads, 0, st>>>(queries, n_q, nodes,
+                                                                                                n_n, 0, ids, d2);
   else
     k_knn<4><<<(n_q + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(queries, n_q, nodes, n_n, 0, ids, d2);
 }
@@ -175,8 +187,12 @@ void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, i
 }
 
 void launch_node_graph(const SwDev& d, cudaStream_t st) {
-  k_knn<8><<<(d.n_n + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(d.node_p, d.n_n, d.node_p, d.n_n, 1,
-                                                                       d.graph, nullptr);
+  if (d.n_n <= kWarpKnnMaxQueries)
+    k_knn_warp<8><<<(int)(((size_t)d.n_n * 32 + kQThreads - 1) / kQThreads), kQThreads, 0, st>>>(
+        d.node_p, d.n_n, d.node_p, d.n_n, 1, d.graph, nullptr);
+  else
+    k_knn<8><<<(d.n_n + kQThreads - 1) / kQThreads, kQThreads, 0, st>>>(d.node_p, d.n_n, d.node_p, d.n_n, 1,
+                                                                         d.graph, nullptr);
 }
 
 }  // namespace sw
