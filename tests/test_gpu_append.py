@@ -181,9 +181,9 @@ def test_append_records_and_model_match_oracle(which, precision):
         np.testing.assert_array_equal(n[ns:, 3], m["conf"].reshape(-1)[pix[ia]].astype(F32))
         assert np.all(t2[ns:] == 1)
         # reference skinning of the appended surfels by the initialisation rule
-        oknn = OSK.knn_fp32(v[ns:, :3], b.o.node_p.astype(F32), 4)
+        oknn = OSK.knn_fp32(res["v_ref"][ia].astype(F32), b.o.node_p.astype(F32), 4)
         np.testing.assert_array_equal(knn[ns:], oknn)
-        ow = OSK.skin_weights(v[ns:, :3].astype(np.float64), b.o.node_p, b.o.node_sigma, oknn)
+        ow = OSK.skin_weights(res["v_ref"][ia], b.o.node_p, b.o.node_sigma, oknn)
         np.testing.assert_allclose(w[ns:], ow, rtol=2e-6, atol=1e-30)
         # the node transforms are untouched
         np.testing.assert_array_equal(sw.sw_read_nodes(b.h)[1], dq8)
