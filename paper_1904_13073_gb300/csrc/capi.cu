@@ -1352,7 +1352,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     int new_nodes = 0;
     const int n_old_nodes = h.n_n;
     if (s->p.extend_nodes && n_app > 0 && h.n_n < s->p.max_nodes) {
-      Tmp unc((size_t)n_app * 4), list((size_t)n_app * 4), cnt(16), sig((size_t)n_app * 4), near((size_t)n_app * 4);
+      Tmp unc((size_t)n_app * 4), list((size_t)n_app * 4), cnt(16), sig((size_t)n_app * 20 + 16), near((size_t)n_app * 8);
       if (!unc.p || !list.p || !cnt.p || !sig.p || !near.p)
         return fail(s, SW_ERR_NO_MEMORY, "node extension scratch allocation failed");
       launch_node_cover(h, tv.as<float4>(), n_stay, n_app, unc.as<int>(), st);

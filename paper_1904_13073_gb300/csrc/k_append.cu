@@ -300,45 +300,67 @@ __global__ void k_node_near(SwDev d, const float4* __restrict__ tv, int first, c
   if (lane == 0) { sig[u] = s; near[u] = close ? 1 : 0; }
 }
 
-// one warp, in order: an uncovered surfel becomes node n_old + count unless an
-// old node or a node taken before it lies within its σ.  The surfels come in
-// chunks of 32 (one per lane, loaded together); the lanes that are not next to
-// an old node are taken in lane order by a ballot, their position passed by
-// shuffles, and tested against the nodes taken so far, which are kept in
-// shared memory (at most kMaxNewNodes per call).
+// The greedy pass only needs the uncovered surfels that no old node is near:
+// their flag, then (after an order-preserving compaction) their position and
+// σ packed as one float4 each.
+__global__ void k_node_free_flags(const int* __restrict__ near, const int* __restrict__ n_list, int n,
+                                  int* __restrict__ flag) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) flag[u] = (u < *n_list && !near[u]) ? 1 : 0;
+}
+
+__global__ void k_node_pack(const float4* __restrict__ tv, int first, const int* __restrict__ list,
+                            const float* __restrict__ sig, const int* __restrict__ free_idx,
+                            const int* __restrict__ n_free, float4* __restrict__ cand) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= *n_free) return;
+  const int u = free_idx[k];
+  const float4 v = tv[first + list[u]];
+  cand[k] = make_float4(v.x, v.y, v.z, sig[u]);
+}
+
+// One warp, in order: candidate k becomes node n_old + count unless a node
+// taken before it lies within its σ.  Chunks of 32 candidates (one coalesced
+// load, the next chunk's issued before the current one is worked on): each
+// lane first tests its candidate against the nodes taken before the chunk
+// (kept in shared memory); the survivors are then taken or rejected in lane
+// order against the nodes taken inside the chunk.  At most kMaxNewNodes per
+// call.
 constexpr int kMaxNewNodes = 2048;
 
-__global__ void __launch_bounds__(32) k_node_greedy(SwDev d, const float4* __restrict__ tv, int first,
-                                                    const int* __restrict__ list, const int* __restrict__ n_list,
-                                                    const float* __restrict__ sig, const int* __restrict__ near,
-                                                    int n_old, int max_new, int* __restrict__ n_new) {
+__global__ void __launch_bounds__(32) k_node_greedy(SwDev d, const float4* __restrict__ cand,
+                                                    const int* __restrict__ n_cand, int n_old, int max_new,
+                                                    int* __restrict__ n_new) {
   __shared__ float4 taken[kMaxNewNodes];
   const int lane = threadIdx.x & 31;
-  const int n = *n_list, cap = min(max_new, kMaxNewNodes);
+  const int n = *n_cand, cap = min(max_new, kMaxNewNodes);
   int count = 0;
+  float4 next = lane < n ? cand[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int base = 0; base < n && count < cap; base += 32) {
-    const int u = base + lane;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool cand = false;
-    if (u < n && !near[u]) {
-      v = tv[first + list[u]];
-      v.w = sig[u];
-      cand = true;
+    const float4 v = next;
+    const bool mine = base + lane < n;
+    if (base + 32 + lane < n) next = cand[base + 32 + lane];
+    const float s2 = __fmul_rn(v.w, v.w);
+    bool close = false;
+    for (int k = 0; k < count; ++k) {   // every lane its own candidate against the earlier nodes
+      const float4 p = taken[k];
+      close = close || dist2_rn(p.x, p.y, p.z, v.x, v.y, v.z) < s2;
     }
-    unsigned m = __ballot_sync(0xffffffffu, cand);
+    unsigned m = __ballot_sync(0xffffffffu, mine && !close);
+    const int count0 = count;
     while (m && count < cap) {
       const int b = __ffs(m) - 1;
       m &= m - 1;
       const float vx = __shfl_sync(0xffffffffu, v.x, b), vy = __shfl_sync(0xffffffffu, v.y, b);
       const float vz = __shfl_sync(0xffffffffu, v.z, b), vs = __shfl_sync(0xffffffffu, v.w, b);
-      const float s2 = __fmul_rn(vs, vs);
-      bool close = false;
-      for (int k = lane; k < count; k += 32) {
+      const float t2 = __fmul_rn(vs, vs);
+      bool c2 = false;
+      for (int k = count0 + lane; k < count; k += 32) {
         const float4 p = taken[k];
-        close = close || dist2_rn(p.x, p.y, p.z, vx, vy, vz) < s2;
+        c2 = c2 || dist2_rn(p.x, p.y, p.z, vx, vy, vz) < t2;
       }
-      close = __any_sync(0xffffffffu, close);
-      if (!close) {
+      c2 = __any_sync(0xffffffffu, c2);
+      if (!c2) {
         if (lane == 0) {
           taken[count] = make_float4(vx, vy, vz, vs);
           d.node_p[n_old + count] = make_float4(vx, vy, vz, vs);
@@ -347,6 +369,7 @@ __global__ void __launch_bounds__(32) k_node_greedy(SwDev d, const float4* __res
         __syncwarp();
       }
     }
+    __syncwarp();
   }
   if (lane == 0) *n_new = count;
 }
@@ -432,9 +455,19 @@ cudaError_t launch_node_subsample(const SwDev& d, const AppendBufs& a, const flo
                                   const int* unc_flags, int* unc_list, int* n_unc, float* sig, int* near,
                                   int n_old, int max_new, int* n_new, cudaStream_t st) {
   cudaError_t e = compact(a, unc_flags, n_app, unc_list, n_unc, st);
+  if (e != cudaSuccess || n_app == 0) return e;
+  k_node_near<<<(int)(((size_t)n_app * 32 + 127) / 128), 128, 0, st>>>(d, tv, first, unc_list, n_unc, sig, near);
+  // the free ones (no old node near), packed in order; the scratch after the
+  // n_app entries of each buffer holds the packed copies
+  int* free_flag = const_cast<int*>(unc_flags);   // the coverage flags are consumed
+  int* free_idx = near + n_app;
+  int* n_free = n_new + 1;
+  float4* cand = reinterpret_cast<float4*>(sig + ((n_app + 3) & ~3));   // 16-byte aligned after the σ
+  k_node_free_flags<<<blocks(n_app, 256), 256, 0, st>>>(near, n_unc, n_app, free_flag);
+  e = compact(a, free_flag, n_app, free_idx, n_free, st);
   if (e != cudaSuccess) return e;
-  if (n_app) k_node_near<<<(int)(((size_t)n_app * 32 + 127) / 128), 128, 0, st>>>(d, tv, first, unc_list, n_unc, sig, near);
-  k_node_greedy<<<1, 32, 0, st>>>(d, tv, first, unc_list, n_unc, sig, near, n_old, max_new, n_new);
+  k_node_pack<<<blocks(n_app, 256), 256, 0, st>>>(tv, first, unc_list, sig, free_idx, n_free, cand);
+  k_node_greedy<<<1, 32, 0, st>>>(d, cand, n_free, n_old, max_new, n_new);
   return cudaGetLastError();
 }
 void launch_new_node_dq(const SwDev& d, int n_old, int k_new, const int* ids, cudaStream_t st) {

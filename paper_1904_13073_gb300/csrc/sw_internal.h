@@ -226,7 +226,9 @@ void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_
 void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st);
 // node-graph extension after appending (k_append.cu): coverage flags of the
 // surfels tv[first, first + n) (1 = uncovered), the greedy sub-sampling that
-// writes new nodes to node_p[n_old ..] and their count to *n_new, the new
+// writes new nodes to node_p[n_old ..] and their count to *n_new (scratch:
+// unc_list n_app ints; near 2 n_app ints; sig 20 n_app + 16 bytes, the σ then
+// n_app float4 from a 16-byte boundary; n_new two ints), the new
 // transforms from the current warp (ids: their 4 nearest old nodes), and the
 // merge of every surfel's set with the new nodes
 void launch_node_cover(const SwDev& d, const float4* tv, int first, int n, int* unc, cudaStream_t st);
