@@ -231,8 +231,9 @@ sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, floa
  * Results equal those of running each member alone up to floating-point
  * summation order.  Work that a member's own calls enqueued is ordered before
  * the next batch call, and batch work before the member's next own call.
- * A batch becomes invalid when a member's model is replaced (sw_set_model /
- * sw_import_state): batch calls then return SW_ERR_INVALID_ARG.  Errors of
+ * When a member's model changes (sw_set_model, sw_import_state,
+ * sw_append_frame) the batch rebuilds its tables and solve graphs at its next
+ * call, keeping the active flags.  Errors of
  * batch calls are reported by sw_last_error(NULL).
  * ------------------------------------------------------------------------- */
 typedef struct sw_batch* sw_batch_handle;
@@ -345,7 +346,9 @@ typedef struct {
   int batch_size;      /* frames processed in the same step */
   double submit_ms;    /* sw_server_submit took the frame */
   double start_ms;     /* its step began */
-  double done_ms;      /* its fusion had finished on the device */
+  double done_ms;      /* its fusion (and appending) had finished on the device */
+  int appended;        /* surfels the frame appended (sw_server_set_appending) */
+  int n_surfels;       /* the stream's surfels after the frame */
 } sw_frame_result;
 
 typedef struct {
@@ -388,6 +391,11 @@ sw_status sw_server_read_nodes(sw_server_handle s, int stream_id, float* pos4, f
  * to window_ms (0..1000) after its oldest frame arrived for the others'
  * frames (0 = start at once, the default). */
 sw_status sw_server_set_batch_window(sw_server_handle s, double window_ms);
+/* Appending (sw_append_frame) after every served frame, stream by stream,
+ * once the batch's fusion has finished (0 = off, the default).  The model
+ * grows within each stream's max_surfels (and max_nodes, with extend_nodes);
+ * a frame whose appending fails reports that status. */
+sw_status sw_server_set_appending(sw_server_handle s, int enable);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 
 /* Rigid pre-alignment of the current frame (Sec. 7: before the non-rigid
@@ -433,7 +441,8 @@ sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
  * recomputed and every surfel whose 4 nearest nodes now include a new node
  * is re-skinned.  The JᵀJ pattern, the runner and the solve graphs are
  * rebuilt (the call synchronises and allocates scratch).  A batch holding
- * the stream must be re-created afterwards.  *stats (nullable) receives
+ * the stream rebuilds its tables at its next call (its active flags are
+ * kept).  *stats (nullable) receives
  * the counts.
  * ------------------------------------------------------------------------- */
 typedef struct {

@@ -67,7 +67,7 @@ class sw_append_stats(ctypes.Structure):
 class sw_frame_result(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_int), ("frame_id", ctypes.c_int), ("status", ctypes.c_int),
                 ("batch_size", ctypes.c_int), ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
-                ("done_ms", ctypes.c_double)]
+                ("done_ms", ctypes.c_double), ("appended", ctypes.c_int), ("n_surfels", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -136,6 +136,7 @@ _SIGS = {
     "sw_server_read_nodes": [_P, _I, _P, _P, _I, ctypes.POINTER(_I)],
     "sw_server_read_stats": [_P, ctypes.POINTER(sw_server_stats)],
     "sw_server_set_batch_window": [_P, ctypes.c_double],
+    "sw_server_set_appending": [_P, _I],
     "sw_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_rigid_align": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_batch_rigid_align": [_P, _I],
@@ -588,6 +589,10 @@ def sw_server_read_nodes(srv, stream_id, n_nodes):
 
 def sw_server_set_batch_window(srv, window_ms):
     _check(lib().sw_server_set_batch_window(srv, float(window_ms)))
+
+
+def sw_server_set_appending(s, enable):
+    _check(lib().sw_server_set_appending(s, int(bool(enable))))
 
 
 def sw_server_read_stats(srv):

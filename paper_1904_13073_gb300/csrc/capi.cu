@@ -1571,9 +1571,20 @@ const char* sw_status_string(sw_status s) {
 
 namespace {
 
+// A member's model changed since the batch's tables were built (sw_set_model,
+// sw_append_frame): rebuild them, keeping the active flags.
 sw_status batch_check(sw_batch* b) {
   if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
-  if (runner_stale(&b->run)) return fail(nullptr, SW_ERR_INVALID_ARG, "a member's model changed; re-create the batch");
+  Runner* r = &b->run;
+  if (!runner_stale(r)) return SW_OK;
+  for (sw_stream* m : r->members)
+    if (!m->has_model) return fail(nullptr, SW_ERR_NOT_INITIALIZED, "a batch member has no model");
+  const int n = (int)r->members.size();
+  std::vector<int> act(r->active_host, r->active_host + n);
+  SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
+  SW_TRY(build_runner(r, nullptr));
+  for (int i = 0; i < n; ++i) r->active_host[i] = act[i];
+  SW_CUDA(nullptr, ring_copy(r, const_cast<int*>(r->bh.bt.active), r->active_host, n));
   return SW_OK;
 }
 

@@ -52,7 +52,7 @@ struct SrvStream {
   sw_params p{};
   std::vector<float> v4, n4, node4;
   std::vector<int> t2;
-  int n_s = 0, n_n = 0;
+  int n_s = 0, n_n = 0;       // surfels (current, after appending) and nodes at opening
   sw_handle h = nullptr;      // null while waiting for admission
   bool closing = false;
   std::deque<Frame> queue;
@@ -73,6 +73,7 @@ struct sw_server {
   int device = 0;
   int gn = 10, pcg = 20, qdepth = 4;
   double window_ms = 0.0;        // how long a step may wait for more streams' frames
+  bool appending = false;        // sw_append_frame after every served frame
   std::chrono::steady_clock::time_point t0;
   int next_id = 1;
   std::map<int, SrvStream*> streams;    // every open stream, by id
@@ -238,6 +239,13 @@ void worker_main(sw_server* S) {
     if (status == SW_OK) status = sw_batch_fuse(S->batch);
     std::vector<int> member_status(n, 0);
     const sw_status sync = sw::batch_member_status(S->batch, member_status.data());
+    std::vector<sw_append_stats> app(taken.size());
+    std::vector<sw_status> app_status(taken.size(), SW_OK);
+    if (S->appending && status == SW_OK && sync == SW_OK)
+      for (size_t k = 0; k < taken.size(); ++k) {
+        const int pos = (int)(std::find(S->batch_ids.begin(), S->batch_ids.end(), taken_ids[k]) - S->batch_ids.begin());
+        if (member_status[pos] == SW_OK) app_status[k] = sw_append_frame(taken_ptrs[k]->h, &app[k]);
+      }
     const double t_done = now_ms(S->t0);
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -250,7 +258,11 @@ void worker_main(sw_server* S) {
         sw_frame_result r{};
         r.stream = taken_ids[k];
         r.frame_id = taken[k].frame_id;
-        r.status = status != SW_OK ? status : sync != SW_OK ? sync : member_status[pos];
+        r.status = status != SW_OK ? status : sync != SW_OK ? sync
+                   : member_status[pos] != SW_OK ? member_status[pos] : app_status[k];
+        if (S->appending && app_status[k] == SW_OK && r.status == SW_OK) s->n_s = app[k].n_surfels;
+        r.appended = S->appending && r.status == SW_OK ? app[k].appended : 0;
+        r.n_surfels = s->n_s;
         r.submit_ms = taken[k].submit_ms;
         r.start_ms = t_start;
         r.done_ms = t_done;
@@ -412,6 +424,13 @@ sw_status sw_server_set_batch_window(sw_server_handle S, double window_ms) {
   if (!S || !(window_ms >= 0.0) || window_ms > 1000.0) return SW_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(S->mu);
   S->window_ms = window_ms;
+  return SW_OK;
+}
+
+sw_status sw_server_set_appending(sw_server_handle S, int enable) {
+  if (!S || (enable != 0 && enable != 1)) return SW_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->appending = enable != 0;
   return SW_OK;
 }
 

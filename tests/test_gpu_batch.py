@@ -157,3 +157,48 @@ def test_batch_autotune_then_matches_alone():
         sw.sw_batch_destroy(b)
         for h in alone + mixed:
             sw.sw_destroy_stream(h)
+
+
+def test_batch_refreshes_after_a_member_appends():
+    """A member's model grows by appending between batch calls: the batch
+    rebuilds its tables at its next call, keeps the active flags (an inactive
+    member stays untouched) and gives the grown member the result it gets
+    alone through the same calls."""
+    from test_gpu_append import _cut
+    scenes = [_cut(synth.plain_tiny(seed=3)), synth.random_scene(seed=24, n_surfels=4000, n_nodes=40)]
+
+    def make(scene):
+        v4, n4, t2, node4 = sw.model_arrays(scene)
+        c = scene.cam
+        h = sw.sw_create_stream(sw.params_for(c, len(v4) + c.width * c.height, len(node4)))
+        sw.sw_set_model(h, v4, n4, t2, node4)
+        return h
+    alone = make(scenes[0])
+    mixed = [make(s) for s in scenes]
+    b = sw.sw_batch_create(mixed)
+    try:
+        sw.sw_upload_depth(alone, scenes[0].frame(1), 1)
+        sw.sw_solve_frame(alone, 3, 8)
+        sw.sw_fuse_frame(alone)
+        st_alone = sw.sw_append_frame(alone)
+        sw.sw_batch_upload_depth(b, [s.frame(1) for s in scenes], [1, 1])
+        sw.sw_batch_solve(b, 3, 8)
+        sw.sw_batch_fuse(b)
+        sw.sw_batch_set_active(b, [1, 0])
+        st = sw.sw_append_frame(mixed[0])
+        assert st["appended"] > 500 and abs(st["appended"] - st_alone["appended"]) <= max(3, st["appended"] // 200)
+        _, dq1_before = sw.sw_read_nodes(mixed[1])
+        # frame 2 through the batch (member 1 inactive) and alone
+        sw.sw_batch_upload_depth(b, [scenes[0].frame(1), None], [2, 0])
+        sw.sw_batch_solve(b, 3, 8)
+        sw.sw_upload_depth(alone, scenes[0].frame(1), 2)
+        sw.sw_solve_frame(alone, 3, 8)
+        np.testing.assert_array_equal(sw.sw_read_nodes(mixed[1])[1], dq1_before)
+        qa, pa = _warped(alone, scenes[0].node_p)
+        qm, pm = _warped(mixed[0], scenes[0].node_p)
+        assert np.max(rotation_angle_between(qa, qm)) < 1e-4
+        assert np.max(np.abs(pa - pm)) < 2e-5
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in mixed + [alone]:
+            sw.sw_destroy_stream(h)

@@ -167,3 +167,59 @@ def test_admission_waits_for_memory():
     finally:
         sw.sw_server_destroy(srv)
         sw.sw_set_memory_budget(0)
+
+
+def test_served_streams_append():
+    """Appending on: every served frame is followed by sw_append_frame on its
+    stream.  Two streams with a hole cut in their models grow at frame 1, the
+    results report it, and each stream's warp field after frame 2 is the one
+    it gets alone through solve + fusion + appending (within the appending
+    tests' end-to-end tolerance: fusion and appending decisions may flip on
+    the batch's summation order)."""
+    from test_gpu_append import _cut
+    scenes = [_cut(synth.plain_tiny(seed=4)), _cut(synth.random_scene(seed=35, n_surfels=6000, n_nodes=50))]
+
+    def params(sc):
+        v4, n4, t2, node4 = sw.model_arrays(sc)
+        return (sw.params_for(sc.cam, len(v4) + sc.cam.width * sc.cam.height, len(node4)), v4, n4, t2, node4)
+    refs = []
+    for sc in scenes:
+        p, v4, n4, t2, node4 = params(sc)
+        h = sw.sw_create_stream(p)
+        try:
+            sw.sw_set_model(h, v4, n4, t2, node4)
+            grown = []
+            for t in (1, 2):
+                sw.sw_upload_depth(h, sc.frame(1), t)
+                sw.sw_solve_frame(h, GN, PCG)
+                sw.sw_fuse_frame(h)
+                grown.append(sw.sw_append_frame(h)["n_surfels"])
+            refs.append((sw.sw_read_nodes(h)[1].astype(np.float64), grown))
+        finally:
+            sw.sw_destroy_stream(h)
+    srv = sw.sw_server_create(0, GN, PCG, queue_depth=2)
+    try:
+        sw.sw_server_set_appending(srv, True)
+        ids = []
+        for sc in scenes:
+            p, v4, n4, t2, node4 = params(sc)
+            ids.append(sw.sw_server_open(srv, p, v4, n4, t2, node4))
+        for sid in ids:
+            _wait_admitted(srv, sid)
+        for t in (1, 2):
+            for sid, sc in zip(ids, scenes):
+                _submit(srv, sid, sc.frame(1), t)
+            assert sw.sw_server_wait(srv, 60000)
+        res = sw.sw_server_poll(srv)
+        assert len(res) == 4 and all(r["status"] == 0 for r in res)
+        for k, (sid, sc) in enumerate(zip(ids, scenes)):
+            mine = [r for r in res if r["stream"] == sid]
+            assert mine[0]["appended"] > 100 and mine[0]["n_surfels"] > len(sc.surfel_v)
+            for r, want in zip(mine, refs[k][1]):
+                assert abs(r["n_surfels"] - want) <= max(3, want // 200)
+            got = sw.sw_server_read_nodes(srv, sid, len(sc.node_p))[1].astype(np.float64)
+            assert np.max(rotation_angle_between(got, refs[k][0])) < 1e-4
+            p_ = sc.node_p.astype(np.float64)
+            assert np.max(np.abs(OS.node_transform(got, p_) - OS.node_transform(refs[k][0], p_))) < 2e-5
+    finally:
+        sw.sw_server_destroy(srv)
