@@ -54,3 +54,22 @@ def test_host_only_calls_work_without_gpu(built):
 def test_graft_entry_build_imports_package(built):
     import __graft_entry__
     __graft_entry__.build()
+
+
+def test_appending_and_visibility_parameters_are_checked_on_the_host(built):
+    """Defaults follow Table 1 (ε, t_low_confid) and the readings (δ_nn,
+    finite-difference step, visibility off, node extension on); values out of
+    range are refused before any device work."""
+    p = sw.sw_params_default(640, 480, 570.0, 570.0, 320.0, 240.0, 1000, 64)
+    assert p.eps == pytest.approx(0.2) and p.t_low_confid == 30
+    assert p.delta_nn == pytest.approx(0.3) and p.fd_step == pytest.approx(1e-3)
+    assert p.visibility == 0 and p.extend_nodes == 1
+    for field, value, word in (("visibility", 2, "visibility"), ("extend_nodes", -1, "extend_nodes"),
+                               ("eps", 1.5, "appending"), ("eps", 0.0, "appending"),
+                               ("delta_nn", -0.1, "appending"), ("fd_step", 0.0, "appending"),
+                               ("precision", 7, "precision")):
+        bad = sw.sw_params_default(640, 480, 570.0, 570.0, 320.0, 240.0, 1000, 64)
+        setattr(bad, field, value)
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_create_stream(bad)
+        assert e.value.status == 1 and word in str(e.value), (field, str(e.value))
