@@ -112,6 +112,9 @@ struct sw_stream {
   bool app_ready = false;
   AppendBufs app{};
   int app_last_cand = 0;      // candidates of the last sw_append_frame
+  // device blocks of earlier models and set-up scratch, kept for reuse (their
+  // bytes stay counted against the budget until the stream is destroyed)
+  std::multimap<size_t, void*> cache;
 };
 
 struct sw_batch {
@@ -167,9 +170,61 @@ void free_list(std::vector<std::pair<void*, size_t>>& list) {
   list.clear();
 }
 
+#define SW_TRY_(expr)                   \
+  do {                                  \
+    sw_status st_ = (expr);             \
+    if (st_ != SW_OK) return st_;       \
+  } while (0)
+
+// A device block of at least `bytes` for stream s: a cached one of at most
+// twice the size, else a new one.  *got is its size.
+sw_status cached_alloc(sw_stream* s, void** out, size_t bytes, size_t* got) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  auto it = s->cache.lower_bound(bytes);
+  if (it != s->cache.end() && it->first <= 2 * bytes) {
+    *out = it->second;
+    *got = it->first;
+    s->cache.erase(it);
+    return SW_OK;
+  }
+  if (!reserve(bytes)) return fail(s, SW_ERR_NO_MEMORY, "device memory budget exceeded");
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    g_in_use -= bytes;
+    return fail(s, e == cudaErrorMemoryAllocation ? SW_ERR_NO_MEMORY : SW_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  *out = p;
+  *got = bytes;
+  return SW_OK;
+}
+
+// The model's blocks go back to the stream's cache (work on the stream that
+// uses them is ordered before any later use, which is on the same stream).
+void recycle_model(sw_stream* s) {
+  for (auto& a : s->model_allocs) s->cache.emplace(a.second, a.first);
+  s->model_allocs.clear();
+}
+
+void release_cache(sw_stream* s) {
+  for (auto& kv : s->cache) {
+    cudaFree(kv.second);
+    g_in_use -= kv.first;
+  }
+  s->cache.clear();
+}
+
 template <typename T>
 sw_status A(sw_stream* s, T** out, size_t count, bool model = false) {
-  return dalloc(s, model ? s->model_allocs : s->allocs, reinterpret_cast<void**>(out), count * sizeof(T));
+  if (!model) return dalloc(s, s->allocs, reinterpret_cast<void**>(out), count * sizeof(T));
+  void* p = nullptr;
+  size_t got = 0;
+  SW_TRY_(cached_alloc(s, &p, count * sizeof(T), &got));
+  s->model_allocs.emplace_back(p, got);
+  *out = reinterpret_cast<T*>(p);
+  return SW_OK;
 }
 
 #define SW_TRY(expr)                    \
@@ -805,6 +860,7 @@ sw_status sw_destroy_stream(sw_handle s) {
   if (s->run) { destroy_runner(s->run); delete s->run; s->run = nullptr; }
   if (s->own_ev) cudaEventDestroy(s->own_ev);
   free_list(s->model_allocs);
+  release_cache(s);
   free_list(s->allocs);
   if (s->own_stream) cudaStreamDestroy(s->st);
   delete s;
@@ -815,15 +871,21 @@ namespace {
 
 // temporary device buffer freed at scope exit (set-up only)
 struct Tmp {
+  sw_stream* s = nullptr;
   void* p = nullptr;
-  Tmp() = default;
-  explicit Tmp(size_t bytes) { alloc(bytes); }
+  size_t got = 0;
+  explicit Tmp(sw_stream* st) : s(st) {}
+  Tmp(sw_stream* st, size_t bytes) : s(st) { alloc(bytes); }
   Tmp(const Tmp&) = delete;
   Tmp& operator=(const Tmp&) = delete;
-  ~Tmp() { if (p) cudaFree(p); }
+  ~Tmp() { put(); }
+  void put() {
+    if (p) s->cache.emplace(got, p);
+    p = nullptr;
+  }
   bool alloc(size_t bytes) {
-    if (p) cudaFree(p);
-    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) p = nullptr;
+    put();
+    if (cached_alloc(s, &p, bytes, &got) != SW_OK) p = nullptr;
     return p != nullptr;
   }
   template <typename T> T* as() { return reinterpret_cast<T*>(p); }
@@ -870,7 +932,7 @@ sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const 
     if (!sets.alloc(16)) return fail(s, SW_ERR_NO_MEMORY, "set table allocation failed");
     return SW_OK;
   }
-  Tmp keys(n * 8), keys2(n * 8), vals(n * 4), perm(n * 4), head(n * 4);
+  Tmp keys(s, n * 8), keys2(s, n * 8), vals(s, n * 4), perm(s, n * 4), head(s, n * 4);
   if (!keys.p || !keys2.p || !vals.p || !perm.p || !head.p) return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
   SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn, n * 16, cudaMemcpyDeviceToDevice, st));
   SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw, n * 16, cudaMemcpyDeviceToDevice, st));
@@ -879,7 +941,7 @@ sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const 
   cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, keys.as<unsigned long long>(), keys2.as<unsigned long long>(),
                                   vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
   cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
-  Tmp cubtmp(std::max(sort_bytes, scan_bytes));
+  Tmp cubtmp(s, std::max(sort_bytes, scan_bytes));
   if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
   SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, sort_bytes, keys.as<unsigned long long>(),
                                              keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0,
@@ -916,8 +978,8 @@ sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph
     SW_CUDA(s, cudaMemcpyAsync(h.in_src, in_src.data(), in_src.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   const int K = 10 * n_sets + (1 + SW_K_GRAPH) * n_n;
-  Tmp keys((size_t)K * 4), skeys((size_t)K * 4), flag((size_t)K * 4), pos((size_t)K * 4), cnt(16);
-  Tmp tmp(pattern_scratch_bytes(K, 2 * K));
+  Tmp keys(s, (size_t)K * 4), skeys(s, (size_t)K * 4), flag(s, (size_t)K * 4), pos(s, (size_t)K * 4), cnt(s, 16);
+  Tmp tmp(s, pattern_scratch_bytes(K, 2 * K));
   if (!keys.p || !skeys.p || !flag.p || !pos.p || !cnt.p || !tmp.p)
     return fail(s, SW_ERR_NO_MEMORY, "pattern scratch allocation failed");
   PatternScratch w{keys.as<uint32_t>(), skeys.as<uint32_t>(), flag.as<int>(), pos.as<int>(), cnt.as<int>(), tmp.p,
@@ -934,7 +996,7 @@ sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph
   SW_TRY(A(s, &h.rl_ent, (size_t)2 * nnzb - n_n, true));
   SW_TRY(A(s, &h.set_slots, (size_t)std::max(1, n_sets) * 14, true));
   {
-    Tmp rlk((size_t)nnzb * 16), rlsk((size_t)nnzb * 16);
+    Tmp rlk(s, (size_t)nnzb * 16), rlsk(s, (size_t)nnzb * 16);
     if (!rlk.p || !rlsk.p) return fail(s, SW_ERR_NO_MEMORY, "pattern scratch allocation failed");
     SW_CUDA(s, launch_pattern_fill(sets, n_sets, h.graph, n_n, nnzb, w, rlk.as<unsigned long long>(),
                                    rlsk.as<unsigned long long>(), h, st));
@@ -978,7 +1040,7 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   enter(s);
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   if (s->run) drop_graphs(s->run);
-  free_list(s->model_allocs);
+  recycle_model(s);
   s->version++;
   s->fused = false;
   SwDev& h = s->h;
@@ -990,11 +1052,11 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   launch_dq_widen(h, st);
   launch_node_graph(h, st);
 
-  Tmp sets;
+  Tmp sets(s);
   int n_sets = 0;
   if (n_s > 0) {
     const size_t n = n_s;
-    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(n * 16), d2(n * 16);
+    Tmp tv(s, n * 16), tn(s, n * 16), tt(s, n * 8), tknn(s, n * 16), tw(s, n * 16), ids(s, n * 16), d2(s, n * 16);
     if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p)
       return fail(s, SW_ERR_NO_MEMORY, "set-up scratch allocation failed");
     SW_CUDA(s, cudaMemcpyAsync(tv.p, v4, n * 16, cudaMemcpyHostToDevice, st));
@@ -1012,7 +1074,10 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   } else {
     SW_TRY(setup_surfels(s, nullptr, nullptr, nullptr, nullptr, nullptr, 0, sets, &n_sets));
   }
-  return install_pattern(s, sets.as<int4>(), n_sets, true);
+  SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, true));
+  sets.put();
+  release_cache(s);   // set-up scratch and the previous model: a new model starts lean
+  return SW_OK;
 }
 }  // namespace
 
@@ -1341,7 +1406,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
   }
   {
     const size_t n = std::max(1, n_new), m = std::max(1, n_app);
-    Tmp tv(n * 16), tn(n * 16), tt(n * 8), tknn(n * 16), tw(n * 16), ids(m * 16), d2(m * 16);
+    Tmp tv(s, n * 16), tn(s, n * 16), tt(s, n * 8), tknn(s, n * 16), tw(s, n * 16), ids(s, m * 16), d2(s, m * 16);
     if (!tv.p || !tn.p || !tt.p || !tknn.p || !tw.p || !ids.p || !d2.p)
       return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
     launch_append_compose(h, a, s->knn_dist, s->w_dist, n_stay, n_app, tv.as<float4>(), tn.as<float4>(),
@@ -1352,7 +1417,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     int new_nodes = 0;
     const int n_old_nodes = h.n_n;
     if (s->p.extend_nodes && n_app > 0 && h.n_n < s->p.max_nodes) {
-      Tmp unc((size_t)n_app * 4), list((size_t)n_app * 4), cnt(16), sig((size_t)n_app * 20 + 16), near((size_t)n_app * 8);
+      Tmp unc(s, (size_t)n_app * 4), list(s, (size_t)n_app * 4), cnt(s, 16), sig(s, (size_t)n_app * 20 + 16), near(s, (size_t)n_app * 8);
       if (!unc.p || !list.p || !cnt.p || !sig.p || !near.p)
         return fail(s, SW_ERR_NO_MEMORY, "node extension scratch allocation failed");
       launch_node_cover(h, tv.as<float4>(), n_stay, n_app, unc.as<int>(), st);
@@ -1362,7 +1427,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       SW_CUDA(s, cudaMemcpyAsync(&new_nodes, cnt.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
       SW_CUDA(s, cudaStreamSynchronize(st));
       if (new_nodes > 0) {
-        Tmp nid((size_t)new_nodes * 16);
+        Tmp nid(s, (size_t)new_nodes * 16);
         if (!nid.p) return fail(s, SW_ERR_NO_MEMORY, "node extension scratch allocation failed");
         launch_knn4(h.node_p + n_old_nodes, new_nodes, h.node_p, n_old_nodes, nid.as<int>(), st);
         launch_new_node_dq(h, n_old_nodes, new_nodes, nid.as<int>(), st);
@@ -1385,10 +1450,10 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     // the model's layout changes: rebuild its structure (nodes and transforms stay)
     s->has_model = false;
     if (s->run) drop_graphs(s->run);
-    free_list(s->model_allocs);
+    recycle_model(s);
     s->version++;
     h.n_s = n_new;
-    Tmp sets;
+    Tmp sets(s);
     int n_sets = 0;
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets, &n_sets));
