@@ -77,7 +77,10 @@ def test_solve_with_visibility_matches_oracle(precision):
     pixel (~3,000 terms over 48 nodes) a few flips move the nodes by tens of
     µm: 2.4e-4 rad and 48 µm measured at frame 3 in both precisions, against
     3e-7 rad without visibility.  The bound for those frames is about 4x
-    that."""
+    that.  The exact frame-1 bound holds for the FP64 variant; the mixed
+    mode's FP32 assembly is not bitwise repeatable (atomics in launch order),
+    so a later re-association may flip there too (2.3e-5 rad seen once), and
+    it gets the solve's usual bound."""
     scene = _depth_radii(synth.random_scene(seed=3, n_surfels=40000, n_nodes=48))
     p = Pair(scene, precision=precision, visibility=1)
     q = Pair(scene, precision=precision)   # the same stream without visibility, for comparison
@@ -96,9 +99,13 @@ def test_solve_with_visibility_matches_oracle(precision):
             dq = dq.astype(np.float64)
             rot = rotation_angle_between(dq, p.o.node_dq).max()
             trans = np.linalg.norm(OS.node_transform(dq, p.o.node_p) - p.o.warped_nodes(), axis=1).max()
-            if t == 1:
+            if t == 1 and precision == sw.SW_PRECISION_FP64:
                 assert [st["n_corr"][k] for k in range(3)] == [o.n_corr for o in ost]
-                assert rot < 1e-5 and trans < 1e-6, (rot, trans)
+                assert rot < 1e-6 and trans < 1e-7, (rot, trans)
+            elif t == 1:
+                # the FP32 assembly sums with atomics in launch order, so a
+                # re-association at iterations 2-3 may flip on a run's noise
+                assert rot < 1e-4 and trans < 1e-5, (rot, trans)
             else:
                 assert rot < 1e-3 and trans < 2e-4, (t, rot, trans)
             sw.sw_fuse_frame(p.h)
