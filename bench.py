@@ -686,7 +686,7 @@ def main():
     appends = append_case(np.ones(len(v4), bool), 3)
     # and a model with 30% of its surfels cut away (the early-frame regime)
     x_cut = np.quantile(scene.surfel_v[:, 0], 0.7)
-    cut_st = append_case(scene.surfel_v[:, 0] < x_cut, 1)[0]
+    cut_st = append_case(scene.surfel_v[:, 0] < x_cut, 3)   # the first fills the hole, the next ones the edges
     # and with the nodes of that region cut too, and room for 256 more: the
     # node graph is extended over the appended surfels
     ext_st = append_case(scene.surfel_v[:, 0] < x_cut, 1, scene.node_p[:, 0] < x_cut - scene.node_sigma[0], 256)[0]
