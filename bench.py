@@ -690,7 +690,34 @@ def main():
     # and with the nodes of that region cut too, and room for 256 more: the
     # node graph is extended over the appended surfels
     ext_st = append_case(scene.surfel_v[:, 0] < x_cut, 1, scene.node_p[:, 0] < x_cut - scene.node_sigma[0], 256)[0]
+    # the paper's whole per-frame pipeline, upload + solve + fusion + appending,
+    # frame after frame on the cut model (wall clock with the device drained:
+    # it includes the model rebuilds and the solve graph's re-capture after
+    # each change)
+    hp = sw.sw_create_stream(sw.params_for(c, room, len(node4)), stream)
+    keep = scene.surfel_v[:, 0] < x_cut
+    sw.sw_set_model(hp, v4[keep], n4[keep], t2[keep], node4)
+    pipe = []
+    for k in range(2 + args.steps):
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        sw.sw_upload_depth(hp, dev_frames[ts[k]], k + 1)
+        sw.sw_solve_frame(hp, gn, pcg, want_stats=False)
+        sw.sw_fuse_frame(hp)
+        a_st = sw.sw_append_frame(hp)
+        torch.cuda.synchronize()
+        pipe.append((1000.0 * (time.perf_counter() - a0), a_st["appended"], a_st["n_surfels"]))
+    sw.sw_destroy_stream(hp)
+    steady_pipe = pipe[2:]   # the first frames fill the cut-away hole
+    pipeline = {"frames_per_s": 1000.0 / float(np.mean([m for m, _, _ in steady_pipe])),
+                "ms_per_frame": float(np.mean([m for m, _, _ in steady_pipe])),
+                "appended_per_frame": float(np.mean([a for _, a, _ in steady_pipe])),
+                "frames_with_appends": int(sum(1 for _, a, _ in steady_pipe if a > 0)),
+                "first_frames": [{"ms": m, "appended": a, "surfels": n} for m, a, n in pipe[:2]],
+                "note": "upload + solve + fusion + sw_append_frame per frame, wall clock, on the model cut by "
+                        "30%; steady frames after the first two"}
     appending = {"steady": appends[1:], "model_cut_30pct": cut_st, "model_and_nodes_cut_30pct": ext_st,
+                 "pipeline": pipeline,
                  "note": "kernel_ms: device time of the appending kernels (events); rebuild_ms: host-side "
                          "model rebuild (set sort, JtJ pattern, runner); call_ms: the whole call"}
     batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
