@@ -84,6 +84,7 @@ struct Runner {
   std::vector<ProfEvent> eager_prof;   // events of the last upload / fusion
   std::vector<cudaEvent_t> event_pool;
   int pcg_rows_per_cta = 32;     // PCG granularity: a stream takes one CTA per this many rows (autotuned)
+  int alloc_n = -1;              // member count the device tables in `allocs` were sized for
   std::string err;
 };
 
@@ -272,7 +273,6 @@ int sm_count() {
 // (Re)build the device tables of a runner for its members.
 sw_status build_runner(Runner* r, sw_stream* err_to) {
   drop_graphs(r);
-  free_list(r->allocs);
   const int n = (int)r->members.size();
   r->versions.clear();
   for (auto* m : r->members) r->versions.push_back(m->version);
@@ -356,10 +356,20 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
   SwDev* devs_dev = nullptr;
   int* tile_dev = nullptr;
   int* active_dev = nullptr;
-  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&devs_dev), sizeof(SwDev) * std::max(1, n)));
-  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&tile_dev), sizeof(int) * tiles.size()));
-  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&active_dev), sizeof(int) * std::max(1, n)));
-  SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&r->frames_dev), sizeof(int) * std::max(1, n)));
+  if (r->alloc_n == n && r->allocs.size() == 4) {   // same members: the tables are rewritten in stream order
+    devs_dev = reinterpret_cast<SwDev*>(r->allocs[0].first);
+    tile_dev = reinterpret_cast<int*>(r->allocs[1].first);
+    active_dev = reinterpret_cast<int*>(r->allocs[2].first);
+    r->frames_dev = reinterpret_cast<int*>(r->allocs[3].first);
+  } else {
+    free_list(r->allocs);
+    r->alloc_n = -1;
+    SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&devs_dev), sizeof(SwDev) * std::max(1, n)));
+    SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&tile_dev), sizeof(int) * tiles.size()));
+    SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&active_dev), sizeof(int) * std::max(1, n)));
+    SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&r->frames_dev), sizeof(int) * std::max(1, n)));
+    r->alloc_n = n;
+  }
   if (!r->ring) {
     if (cudaMallocHost(&r->ring, sizeof(int) * Runner::kRing * Runner::kSlotInts) != cudaSuccess)
       return fail(err_to, SW_ERR_NO_MEMORY, "pinned host allocation failed");
@@ -1440,14 +1450,11 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     if (stats) stats->new_nodes = new_nodes;
     SW_CUDA(s, cudaGetLastError());
     SW_CUDA(s, cudaEventRecord(ev1, st));
-    SW_CUDA(s, cudaStreamSynchronize(st));
-    float kms = 0.f;
-    cudaEventElapsedTime(&kms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (stats) stats->kernel_ms = kms;
     const auto t0 = std::chrono::steady_clock::now();
-    // the model's layout changes: rebuild its structure (nodes and transforms stay)
+    // the model's layout changes: rebuild its structure (nodes and transforms
+    // stay).  The old model's blocks go back to the cache while the kernels
+    // above may still read them: anything that reuses them is later on the
+    // same stream.
     s->has_model = false;
     if (s->run) drop_graphs(s->run);
     recycle_model(s);
@@ -1458,7 +1465,14 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets, &n_sets));
     SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, new_nodes > 0));
-    if (stats) stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, ev0, ev1);   // both are complete: install_pattern synchronised
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (stats) {
+      stats->kernel_ms = kms;
+      stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
   }
   s->fused = false;
   return SW_OK;
