@@ -1,10 +1,9 @@
 // K4-K6: the assembly half of one Gauss-Newton iteration of the non-rigid
 // solve (Sec. 7-8).
 //
-//   K6 k_reg_assemble   writes the as-rigid-as-possible part (Eq. 11) of every
-//                       upper 6x6 block of JᵀJ with plain stores: a thread per
-//                       off-diagonal block, a warp per node for the diagonal
-//                       block and Jᵀe (lanes over the node's edges).  It runs
+//   K6 k_reg_assemble   one thread per upper 6x6 block of JᵀJ: writes the
+//                       as-rigid-as-possible part (Eq. 11) of that block, and
+//                       of Jᵀe on diagonal blocks, with plain stores.  It runs
 //                       first and so also initialises the whole system.
 //   K4+K5 k_data_assemble  one thread per surfel: dual-quaternion blend and
 //                       forward warp (Eq. 1-2), projective association,
@@ -89,71 +88,35 @@ __global__ void k_solve_begin(Batch bt) {
   if (threadIdx.x == 0) *d.status = 0;
 }
 
-// One launch, two roles.  CTAs below `blk_total` take a thread per
-// off-diagonal block (at most two edges each); the others take a warp per
-// node and write its diagonal block and its six entries of Jᵀe, the lanes
-// sharing the node's out-edges (lanes 0-7) and in-edges (lanes 8-31, strided),
-// then a butterfly sum.  Every block is written by exactly one thread or warp.
-__global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, const int* __restrict__ node_tile_base,
-                                                           int blk_total, int gn_it) {
+__global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) {
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
+  // a new epoch for the generation stamps of the PCG launch that follows
+  if (b == 0) *d.pcg_epoch += 1;
   float ereg = 0.f;
-  if ((int)blockIdx.x < blk_total) {
-    const int s = find_stream(bt, blockIdx.x);
-    if (!stream_active(bt, s)) return;
-    const SwDev d = bt.devs[s];
-    const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
-    // a new epoch for the generation stamps of the PCG launch that follows
-    if (b == 0) *d.pcg_epoch += 1;
-    if (b < d.nnzb) {
-      const int i = d.blk_row[b], j = d.col[b];
-      if (i != j) {
-        const float sl = d.sqrt_lambda, l = sl * sl;
-        float acc[36];
-#pragma unroll
-        for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-        const int fl = d.blk_edge[b];
-        if (fl & 1) {   // edge i -> j: J_i = sl[−[T_i p_i]×|I], J_j = −sl[−[T_j p_i]×|I]
-          const float3 pi = f3(d.node_p[i]);
-          add_reg_pair(acc, -l, node_apply(d, i, pi), node_apply(d, j, pi));
-        }
-        if (fl & 2) {   // edge j -> i: J_j = sl[−[T_j p_j]×|I], J_i = −sl[−[T_i p_j]×|I]
-          const float3 pj = f3(d.node_p[j]);
-          add_reg_pair(acc, -l, node_apply(d, i, pj), node_apply(d, j, pj));
-        }
-        float4* dst = reinterpret_cast<float4*>(d.A + (size_t)b * 36);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
-      }
-    }
-    return;   // the energy is summed by the node role
-  }
-  Batch bn = bt;
-  bn.tile_base = node_tile_base;
-  const int bid = blockIdx.x - blk_total;
-  const int s = find_stream(bn, bid);
-  if (!stream_active(bn, s)) return;
-  const SwDev d = bn.devs[s];
-  const int lane = threadIdx.x & 31;
-  const int j = (bid - __ldg(node_tile_base + s)) * (kBlkTile / 32) + (threadIdx.x >> 5);
-  if (j < d.n_n) {
+  if (b < d.nnzb) {
+    const int i = d.blk_row[b], j = d.col[b];
     const float sl = d.sqrt_lambda, l = sl * sl;
-    float acc[36], gj[6];
+    float acc[36];
 #pragma unroll
     for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) gj[k] = 0.f;
-    if (lane < SW_K_GRAPH) {   // out-edge j -> m
+    if (i == j) {
+      float gj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const float3 pj = f3(d.node_p[j]);
       const float3 x = node_apply(d, j, pj);
-      const int m = d.graph[j * SW_K_GRAPH + lane];
-      const float3 r = sl * (x - node_apply(d, m, pj));
-      ereg += dot3(r, r);
-      add_reg_pair(acc, l, x, x);
-      const float3 xr = cross3(x, r);
-      gj[0] += sl * xr.x; gj[1] += sl * xr.y; gj[2] += sl * xr.z;
-      gj[3] += sl * r.x; gj[4] += sl * r.y; gj[5] += sl * r.z;
-    } else {                   // in-edges m -> j
-      for (int e = d.in_ptr[j] + lane - SW_K_GRAPH; e < d.in_ptr[j + 1]; e += 32 - SW_K_GRAPH) {
+      for (int e = 0; e < SW_K_GRAPH; ++e) {      // out-edges j -> m
+        const int m = d.graph[j * SW_K_GRAPH + e];
+        const float3 y = node_apply(d, m, pj);
+        const float3 r = sl * (x - y);
+        ereg += dot3(r, r);
+        add_reg_pair(acc, l, x, x);
+        const float3 xr = cross3(x, r);
+        gj[0] += sl * xr.x; gj[1] += sl * xr.y; gj[2] += sl * xr.z;
+        gj[3] += sl * r.x; gj[4] += sl * r.y; gj[5] += sl * r.z;
+      }
+      for (int e = d.in_ptr[j]; e < d.in_ptr[j + 1]; ++e) {   // in-edges m -> j
         const int m = d.in_src[e];
         const float3 pm = f3(d.node_p[m]);
         const float3 y = node_apply(d, j, pm);
@@ -163,25 +126,22 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, const int* 
         gj[0] -= sl * yr.x; gj[1] -= sl * yr.y; gj[2] -= sl * yr.z;
         gj[3] -= sl * r.x; gj[4] -= sl * r.y; gj[5] -= sl * r.z;
       }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d.g[6 * j + k] = gj[k];
+    } else {
+      const int fl = d.blk_edge[b];
+      if (fl & 1) {   // edge i -> j: J_i = sl[−[T_i p_i]×|I], J_j = −sl[−[T_j p_i]×|I]
+        const float3 pi = f3(d.node_p[i]);
+        add_reg_pair(acc, -l, node_apply(d, i, pi), node_apply(d, j, pi));
+      }
+      if (fl & 2) {   // edge j -> i: J_j = sl[−[T_j p_j]×|I], J_i = −sl[−[T_i p_j]×|I]
+        const float3 pj = f3(d.node_p[j]);
+        add_reg_pair(acc, -l, node_apply(d, i, pj), node_apply(d, j, pj));
+      }
     }
+    float4* dst = reinterpret_cast<float4*>(d.A + (size_t)b * 36);
 #pragma unroll
-    for (int k = 0; k < 36; ++k) acc[k] = warp_sum(acc[k]);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) gj[k] = warp_sum(gj[k]);
-    const int b = __ldg(d.row_ptr + j);   // the diagonal block leads its row
-    if (lane < 9) {
-      float4 v = make_float4(acc[0], acc[1], acc[2], acc[3]);
-#pragma unroll
-      for (int k = 1; k < 9; ++k)
-        if (lane == k) v = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
-      reinterpret_cast<float4*>(d.A + (size_t)b * 36)[lane] = v;
-    } else if (lane < 15) {
-      float g = gj[0];
-#pragma unroll
-      for (int k = 1; k < 6; ++k)
-        if (lane - 9 == k) g = gj[k];
-      d.g[6 * j + lane - 9] = g;
-    }
+    for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
   }
   block_atomic_sum<double>((double)ereg, d.e_reg + gn_it);
 }
@@ -373,10 +333,7 @@ void launch_solve_begin(const BatchHost& b, cudaStream_t st) {
   if (b.bt.n_streams) k_solve_begin<<<b.bt.n_streams, 32, 0, st>>>(b.bt);
 }
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
-  const int grid = b.total_tiles[kTileBlocks] + b.total_tiles[kTileNodeWarps];
-  if (grid)
-    k_reg_assemble<<<grid, kBlkTile, 0, st>>>(with_kind(b, kTileBlocks), b.tile_base_dev[kTileNodeWarps],
-                                              b.total_tiles[kTileBlocks], gn_it);
+  if (b.total_tiles[kTileBlocks]) k_reg_assemble<<<b.total_tiles[kTileBlocks], kBlkTile, 0, st>>>(with_kind(b, kTileBlocks), gn_it);
 }
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileSurfelsAssembly])

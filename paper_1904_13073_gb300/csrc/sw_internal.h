@@ -140,8 +140,7 @@ struct GridBarrier {   // counter barrier used by the timeout probe
 
 // ------------------------------------------------------------------ launchers
 
-enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTileNodeWarps,
-                kTileKinds };
+enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTileKinds };
 
 struct BatchHost {
   Batch bt;
@@ -274,7 +273,6 @@ inline int tiles_for(int kind, const SwDev& d) {
     case kTileBlocks: return (d.nnzb + kBlkTile - 1) / kBlkTile;
     case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
     case kTileNodes: return (d.n_n + kBlkTile - 1) / kBlkTile;
-    case kTileNodeWarps: return (d.n_n + kBlkTile / 32 - 1) / (kBlkTile / 32);   // a warp per node
   }
   return 0;
 }
