@@ -103,7 +103,13 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
 #pragma unroll
     for (int k = 0; k < 36; ++k) acc[k] = 0.f;
     if (i == j) {
+      // Every edge adds the same form to the diagonal block: for the point
+      // y = T_j p (p_j on an out-edge, p_m on an in-edge) the block of
+      // [−[y]×|I]ᵀ[−[y]×|I] is [[|y|²I − y yᵀ, [y]×], [−[y]×, I]], so the
+      // block needs only the edges' count, Σy and Σ y yᵀ; the out-edges all
+      // share y = T_j p_j.
       float gj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float sy[3] = {0.f, 0.f, 0.f}, syy[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // xx xy xz yy yz zz
       const float3 pj = f3(d.node_p[j]);
       const float3 x = node_apply(d, j, pj);
       for (int e = 0; e < SW_K_GRAPH; ++e) {      // out-edges j -> m
@@ -111,20 +117,41 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
         const float3 y = node_apply(d, m, pj);
         const float3 r = sl * (x - y);
         ereg += dot3(r, r);
-        add_reg_pair(acc, l, x, x);
         const float3 xr = cross3(x, r);
         gj[0] += sl * xr.x; gj[1] += sl * xr.y; gj[2] += sl * xr.z;
         gj[3] += sl * r.x; gj[4] += sl * r.y; gj[5] += sl * r.z;
       }
+      const float ko = (float)SW_K_GRAPH;
+      sy[0] = ko * x.x; sy[1] = ko * x.y; sy[2] = ko * x.z;
+      syy[0] = ko * x.x * x.x; syy[1] = ko * x.x * x.y; syy[2] = ko * x.x * x.z;
+      syy[3] = ko * x.y * x.y; syy[4] = ko * x.y * x.z; syy[5] = ko * x.z * x.z;
+      float cnt = ko;
       for (int e = d.in_ptr[j]; e < d.in_ptr[j + 1]; ++e) {   // in-edges m -> j
         const int m = d.in_src[e];
         const float3 pm = f3(d.node_p[m]);
         const float3 y = node_apply(d, j, pm);
         const float3 r = sl * (node_apply(d, m, pm) - y);
-        add_reg_pair(acc, l, y, y);
+        cnt += 1.f;
+        sy[0] += y.x; sy[1] += y.y; sy[2] += y.z;
+        syy[0] += y.x * y.x; syy[1] += y.x * y.y; syy[2] += y.x * y.z;
+        syy[3] += y.y * y.y; syy[4] += y.y * y.z; syy[5] += y.z * y.z;
         const float3 yr = cross3(y, r);
         gj[0] -= sl * yr.x; gj[1] -= sl * yr.y; gj[2] -= sl * yr.z;
         gj[3] -= sl * r.x; gj[4] -= sl * r.y; gj[5] -= sl * r.z;
+      }
+      {
+        const float S[9] = {syy[0], syy[1], syy[2], syy[1], syy[3], syy[4], syy[2], syy[4], syy[5]};
+        const float tr = syy[0] + syy[3] + syy[5];
+        const float ax[9] = {0.f, -sy[2], sy[1], sy[2], 0.f, -sy[0], -sy[1], sy[0], 0.f};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            acc[p * 6 + q] = l * ((p == q ? tr : 0.f) - S[p * 3 + q]);
+            acc[p * 6 + 3 + q] = l * ax[p * 3 + q];
+            acc[(3 + p) * 6 + q] = -l * ax[p * 3 + q];
+            acc[(3 + p) * 6 + 3 + q] = p == q ? l * cnt : 0.f;
+          }
       }
 #pragma unroll
       for (int k = 0; k < 6; ++k) d.g[6 * j + k] = gj[k];
