@@ -177,11 +177,20 @@ void free_list(std::vector<std::pair<void*, size_t>>& list) {
     if (st_ != SW_OK) return st_;       \
   } while (0)
 
+// Block sizes come in classes, eight per power of two (at most 12.5% over the
+// request), so that arrays which grow a little with every appended frame keep
+// fitting the blocks of the frame before.
+size_t size_class(size_t bytes) {
+  if (bytes <= 4096) return bytes <= 256 ? 256 : (bytes + 255) & ~size_t(255);
+  int e = 63 - __builtin_clzll((unsigned long long)bytes);   // 2^e <= bytes < 2^(e+1)
+  const size_t step = size_t(1) << (e - 3);
+  return (bytes + step - 1) & ~(step - 1);
+}
+
 // A device block of at least `bytes` for stream s: a cached one of at most
-// twice the size, else a new one.  *got is its size.
+// twice the size, else a new one of its size class.  *got is its size.
 sw_status cached_alloc(sw_stream* s, void** out, size_t bytes, size_t* got) {
-  bytes = (bytes + 255) & ~size_t(255);
-  if (bytes == 0) bytes = 256;
+  bytes = size_class(bytes);
   auto it = s->cache.lower_bound(bytes);
   if (it != s->cache.end() && it->first <= 2 * bytes) {
     *out = it->second;
