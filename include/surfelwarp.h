@@ -440,9 +440,12 @@ sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
  * current warp at its position as its transform), the 8-NN graph is
  * recomputed and every surfel whose 4 nearest nodes now include a new node
  * is re-skinned.  The JᵀJ pattern, the runner and the solve graphs are
- * rebuilt (the call synchronises and allocates scratch).  A batch holding
- * the stream rebuilds its tables at its next call (its active flags are
- * kept).  *stats (nullable) receives
+ * rebuilt (the call synchronises; its scratch and the model's arrays come
+ * from a per-stream cache of device blocks that repeated calls reuse).  A
+ * batch holding the stream rebuilds its tables at its next call (its active
+ * flags are kept).  If the rebuild fails (SW_ERR_NO_MEMORY under the memory
+ * budget, SW_ERR_CUDA), the stream has no model until the next sw_set_model
+ * or sw_import_state.  *stats (nullable) receives
  * the counts.
  * ------------------------------------------------------------------------- */
 typedef struct {
