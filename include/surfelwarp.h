@@ -458,6 +458,10 @@ typedef struct {
   double kernel_ms;      /* device time of the appending kernels (CUDA events), model rebuild excluded */
   double rebuild_ms;     /* host time of the model rebuild (set sort, JᵀJ pattern, runner) */
   int new_nodes;         /* nodes added by the node-graph extension */
+  int resorted;          /* 1: the surfels were re-sorted by node set and the JᵀJ pattern rebuilt;
+                            0: no change, or the appended surfels were placed after the sorted ones
+                            (nothing removed, no new node, every 4-node set already present, and the
+                            surfels so placed since the last re-sort at most 1/16 of the model) */
 } sw_append_stats;
 sw_status sw_append_frame(sw_handle h, sw_append_stats* stats);
 /* Per-candidate record of the last sw_append_frame, candidate order (row-

@@ -58,7 +58,8 @@ class sw_solve_stats(ctypes.Structure):
 class sw_append_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int), ("rejected_nn", ctypes.c_int), ("rejected_strain", ctypes.c_int),
                 ("appended", ctypes.c_int), ("removed", ctypes.c_int), ("n_surfels", ctypes.c_int),
-                ("kernel_ms", ctypes.c_double), ("rebuild_ms", ctypes.c_double), ("new_nodes", ctypes.c_int)]
+                ("kernel_ms", ctypes.c_double), ("rebuild_ms", ctypes.c_double), ("new_nodes", ctypes.c_int),
+                ("resorted", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

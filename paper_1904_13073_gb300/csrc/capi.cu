@@ -113,6 +113,7 @@ struct sw_stream {
   bool app_ready = false;
   AppendBufs app{};
   int app_last_cand = 0;      // candidates of the last sw_append_frame
+  int unsorted = 0;           // surfels appended after the set-sorted ones since the last full rebuild
   // device blocks of earlier models and set-up scratch, kept for reuse (their
   // bytes stay counted against the budget until the stream is destroyed)
   std::multimap<size_t, void*> cache;
@@ -213,6 +214,13 @@ sw_status cached_alloc(sw_stream* s, void** out, size_t bytes, size_t* got) {
 
 // The model's blocks go back to the stream's cache (work on the stream that
 // uses them is ordered before any later use, which is on the same stream).
+// Size of the model block that starts at p (0 if none).
+size_t model_block_size(const sw_stream* s, const void* p) {
+  for (const auto& a : s->model_allocs)
+    if (a.first == p) return a.second;
+  return 0;
+}
+
 void recycle_model(sw_stream* s) {
   for (auto& a : s->model_allocs) s->cache.emplace(a.second, a.first);
   s->model_allocs.clear();
@@ -1062,6 +1070,7 @@ sw_status set_model_impl(sw_handle s, const float* v4, const float* n4, const in
   recycle_model(s);
   s->version++;
   s->fused = false;
+  s->unsorted = 0;
   SwDev& h = s->h;
   h.n_s = n_s; h.n_n = n_n;
   cudaStream_t st = s->st;
@@ -1410,6 +1419,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     stats->n_surfels = n_new;
     stats->kernel_ms = stats->rebuild_ms = 0.0;
     stats->new_nodes = 0;
+    stats->resorted = 0;
   }
   s->app_last_cand = n_cand;
   if (n_app == 0 && n_stay == n_old) {   // nothing appended or removed: the model stands as it is
@@ -1460,6 +1470,53 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_CUDA(s, cudaGetLastError());
     SW_CUDA(s, cudaEventRecord(ev1, st));
     const auto t0 = std::chrono::steady_clock::now();
+    auto finish = [&](bool rebuilt) -> sw_status {
+      float kms = 0.f;
+      cudaEventElapsedTime(&kms, ev0, ev1);   // both are complete: the caller synchronised
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      if (stats) {
+        stats->kernel_ms = kms;
+        stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
+      if (stats) stats->resorted = rebuilt ? 1 : 0;
+      s->fused = false;
+      return SW_OK;
+    };
+    // Fast update: nothing removed, no new node, every appended surfel's set
+    // already known, and the surfels appended since the last set sort a small
+    // share of the model.  The JᵀJ pattern stays; the appended surfels follow
+    // the sorted ones in the internal order (the data term sums runs of equal
+    // sets, so any order is correct; the sort only keeps the runs long).
+    if (n_stay == n_old && new_nodes == 0 && n_app > 0 && (s->unsorted + n_app) * 16 <= n_new &&
+        model_block_size(s, s->knn_dist) >= (size_t)n_new * 16 && model_block_size(s, s->w_dist) >= (size_t)n_new * 16) {
+      Tmp set_of(s, (size_t)n_app * 4), miss(s, 16);
+      if (!set_of.p || !miss.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
+      SW_CUDA(s, cudaMemsetAsync(miss.p, 0, sizeof(int), st));
+      launch_find_sets(h, tknn.as<int4>(), n_stay, n_app, set_of.as<int>(), miss.as<int>(), st);
+      int missing = 0;
+      SW_CUDA(s, cudaMemcpyAsync(&missing, miss.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(s, cudaStreamSynchronize(st));
+      if (missing == 0) {
+        SW_CUDA(s, cudaMemcpyAsync(s->knn_dist + n_old, tknn.as<int4>() + n_stay, (size_t)n_app * 16,
+                                   cudaMemcpyDeviceToDevice, st));
+        SW_CUDA(s, cudaMemcpyAsync(s->w_dist + n_old, tw.as<float4>() + n_stay, (size_t)n_app * 16,
+                                   cudaMemcpyDeviceToDevice, st));
+        launch_append_internal(h, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
+                               n_old, n_app, set_of.as<int>(), st);
+        SW_CUDA(s, cudaGetLastError());
+        if (s->run) drop_graphs(s->run);
+        s->version++;
+        h.n_s = n_new;
+        s->unsorted += n_app;
+        SW_TRY(sync_desc(s));
+        launch_warp_live(s->run->bh, st);
+        SW_CUDA(s, cudaGetLastError());
+        SW_CUDA(s, cudaStreamSynchronize(st));
+        return finish(false);
+      }
+    }
+    s->unsorted = 0;
     // the model's layout changes: rebuild its structure (nodes and transforms
     // stay).  The old model's blocks go back to the cache while the kernels
     // above may still read them: anything that reuses them is later on the
@@ -1474,17 +1531,8 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets, &n_sets));
     SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, new_nodes > 0));
-    float kms = 0.f;
-    cudaEventElapsedTime(&kms, ev0, ev1);   // both are complete: install_pattern synchronised
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (stats) {
-      stats->kernel_ms = kms;
-      stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    }
+    return finish(true);
   }
-  s->fused = false;
-  return SW_OK;
 }
 
 sw_status sw_debug_read_append(sw_handle s, int* pix, int* knn4, int* flags, double* wsum, double* strain9,

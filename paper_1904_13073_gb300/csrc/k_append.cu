@@ -446,7 +446,82 @@ __global__ void k_skin_merge(SwDev d, const float4* __restrict__ tv, int n, int 
   tw[i] = make_float4(w[0], w[1], w[2], w[3]);
 }
 
+// ------------------------------------------------------------------ fast model update
+// When no surfel is removed and every appended surfel's 4-node set is already
+// in the set table, the pattern of JᵀJ does not change: the appended surfels
+// are put after the existing ones in the internal order with their set's id.
+
+// the set of each appended surfel (its 4 ids sorted ascending, searched among
+// the sets, which are in increasing key order), or -1; *missing counts the -1s
+__global__ void k_find_sets(SwDev d, const int4* __restrict__ tknn, int first, int n_app, int* __restrict__ set_of,
+                            int* __restrict__ missing) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_app) return;
+  const int4 q = tknn[first + k];
+  int a[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3 - x; ++y)
+      if (a[y] > a[y + 1]) { const int t = a[y]; a[y] = a[y + 1]; a[y + 1] = t; }
+  const unsigned long long key = ((unsigned long long)a[0] << 48) | ((unsigned long long)a[1] << 32) |
+                                 ((unsigned long long)a[2] << 16) | (unsigned long long)a[3];
+  int lo = 0, hi = d.n_sets - 1, found = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int* sl = d.set_slots + (size_t)mid * 14 + 10;
+    const unsigned long long mk = ((unsigned long long)sl[0] << 48) | ((unsigned long long)sl[1] << 32) |
+                                  ((unsigned long long)sl[2] << 16) | (unsigned long long)sl[3];
+    if (mk == key) { found = mid; break; }
+    if (mk < key) lo = mid + 1; else hi = mid - 1;
+  }
+  set_of[k] = found;
+  if (found < 0) atomicAdd(missing, 1);
+}
+
+// appended surfel k becomes internal (and caller) index first + k
+__global__ void k_append_internal(SwDev d, const float4* __restrict__ tv, const float4* __restrict__ tn,
+                                  const int2* __restrict__ tt, const int4* __restrict__ tknn,
+                                  const float4* __restrict__ tw, int first, int n_app, const int* __restrict__ set_of) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_app) return;
+  const int o = first + k, i = first + k;
+  d.v_ref[i] = tv[o];
+  d.n_ref[i] = tn[o];
+  d.tt[i] = tt[o];
+  d.orig_id[i] = o;
+  d.inv_perm[o] = i;
+  d.set_id[i] = set_of[k];
+  const int4 kk = tknn[o];
+  const float4 ww = tw[o];
+  int id[4] = {kk.x, kk.y, kk.z, kk.w};
+  float w[4] = {ww.x, ww.y, ww.z, ww.w};
+  int slot0 = 0;   // where the nearest node (distance slot 0) goes
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3 - x; ++y)
+      if (id[y] > id[y + 1]) {
+        const int t = id[y]; id[y] = id[y + 1]; id[y + 1] = t;
+        const float u = w[y]; w[y] = w[y + 1]; w[y + 1] = u;
+        if (slot0 == y) slot0 = y + 1; else if (slot0 == y + 1) slot0 = y;
+      }
+  d.knn[i] = make_int4(id[0], id[1], id[2], id[3]);
+  d.w[i] = make_float4(w[0], w[1], w[2], w[3]);
+  d.ref_slot[i] = slot0;
+  d.corr_pix[i] = -1;
+}
+
 }  // namespace
+
+void launch_find_sets(const SwDev& d, const int4* tknn, int first, int n_app, int* set_of, int* missing,
+                      cudaStream_t st) {
+  if (n_app) k_find_sets<<<blocks(n_app, 256), 256, 0, st>>>(d, tknn, first, n_app, set_of, missing);
+}
+void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
+                            const float4* tw, int first, int n_app, const int* set_of, cudaStream_t st) {
+  if (n_app) k_append_internal<<<blocks(n_app, 256), 256, 0, st>>>(d, tv, tn, tt, tknn, tw, first, n_app, set_of);
+}
 
 void launch_node_cover(const SwDev& d, const float4* tv, int first, int n, int* unc, cudaStream_t st) {
   if (n) k_node_cover<<<(int)(((size_t)n * 32 + 127) / 128), 128, 0, st>>>(d, tv, first, n, unc);

@@ -224,6 +224,13 @@ void launch_append_compose(const SwDev& d, const AppendBufs& a, const int4* knn_
                            int n_stay, int n_app, float4* tv, float4* tn, int2* tt, int4* tknn, float4* tw,
                            cudaStream_t st);
 void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, int* ids, cudaStream_t st);
+// the fast model update after appending (k_append.cu): each appended surfel's
+// existing set (or -1, counted in *missing), then the appended surfels placed
+// after the first `first` surfels of the internal order with those sets
+void launch_find_sets(const SwDev& d, const int4* tknn, int first, int n_app, int* set_of, int* missing,
+                      cudaStream_t st);
+void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
+                            const float4* tw, int first, int n_app, const int* set_of, cudaStream_t st);
 // node-graph extension after appending (k_append.cu): coverage flags of the
 // surfels tv[first, first + n) (1 = uncovered), the greedy sub-sampling that
 // writes new nodes to node_p[n_old ..] and their count to *n_new (scratch:

@@ -326,3 +326,54 @@ def test_node_extension_matches_oracle(precision):
         assert np.linalg.norm(OS.node_transform(dq2, b.o.node_p) - b.o.warped_nodes(), axis=1).max() < 2e-5
     finally:
         b.close()
+
+
+def test_fast_update_on_a_growing_model_matches_oracle():
+    """Three appending frames on identical inputs.  The first fills a hole
+    (new node sets: re-sorted, pattern rebuilt); the next two append a few
+    dozen to a few hundred surfels along its edges, all in node sets the model
+    already has, so they are placed after the sorted surfels without a re-sort.
+    The model, its skinning and the next solve agree with the oracle."""
+    scene = _cut(synth.plain_tiny(seed=0), unstable=0)
+    c = scene.cam
+    b = Both(scene, len(scene.surfel_v) + c.width * c.height)
+    try:
+        d = scene.frame(1)
+        resorted = []
+        for t, seed in ((1, 5), (2, 6), (3, 7)):
+            sw.sw_upload_depth(b.h, d, t)
+            b.o.upload_depth(d, t)
+            b.set_maps()
+            dq8 = _warp(scene, seed, 0.5, 0.002, alpha=0.0)
+            sw.sw_set_node_dq(b.h, dq8)
+            b.o.node_dq = dq8.astype(np.float64)
+            _, vl, nl = OS.warp_surfels(b.o.v_ref, b.o.n_ref, b.o.knn, b.o.w, b.o.node_dq)
+            vl32, nl32 = vl.astype(F32), nl.astype(F32)
+            sw.sw_debug_set_live(b.h, vl32, nl32)
+            sw.sw_debug_fusion_targets(b.h, c.height, c.width)
+            st = sw.sw_append_frame(b.h)
+            b.o.last_index_map = OFU.index_map(vl32, b.o.p.cam)
+            _, n_app, _ = b.o.append_frame(b.max_surfels, EPS, DNN, FDH)
+            assert st["appended"] == n_app and st["n_surfels"] == len(b.o.v_ref), (t, st, n_app)
+            resorted.append(st["resorted"])
+        assert resorted == [1, 0, 0]
+        v, n, t2 = sw.sw_read_surfels(b.h)
+        np.testing.assert_allclose(v[:, :3], b.o.v_ref, atol=2e-6)
+        np.testing.assert_allclose(n[:, :3], b.o.n_ref, atol=2e-6)
+        np.testing.assert_array_equal(t2[:, 0], b.o.t_init)
+        knn, w = sw.sw_read_skinning(b.h)
+        np.testing.assert_array_equal(knn, b.o.knn)
+        np.testing.assert_allclose(w, b.o.w, rtol=2e-6, atol=1e-30)
+        # the next solve runs on the appended surfels in their unsorted place
+        sw.sw_upload_depth(b.h, d, 4)
+        b.o.upload_depth(d, 4)
+        b.set_maps()
+        st4 = sw.sw_solve_frame(b.h, 2, 8)
+        ost4 = b.o.solve_frame(2, 8)
+        assert abs(st4["n_corr"][0] - ost4[0].n_corr) <= 3
+        _, dq = sw.sw_read_nodes(b.h)
+        dq = dq.astype(np.float64)
+        assert rotation_angle_between(dq, b.o.node_dq).max() < 1e-4
+        assert np.linalg.norm(OS.node_transform(dq, b.o.node_p) - b.o.warped_nodes(), axis=1).max() < 2e-5
+    finally:
+        b.close()
