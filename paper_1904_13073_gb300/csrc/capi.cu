@@ -114,6 +114,7 @@ struct sw_stream {
   AppendBufs app{};
   int app_last_cand = 0;      // candidates of the last sw_append_frame
   int unsorted = 0;           // surfels appended after the set-sorted ones since the last full rebuild
+  int sorted_sets = 0;        // sets in increasing key order; sets added by fast updates follow them
   // device blocks of earlier models and set-up scratch, kept for reuse (their
   // bytes stay counted against the budget until the stream is destroyed)
   std::multimap<size_t, void*> cache;
@@ -1016,6 +1017,7 @@ sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph
   SW_CUDA(s, cudaMemcpyAsync(&nnzb, w.count, sizeof(int), cudaMemcpyDeviceToHost, st));
   SW_CUDA(s, cudaStreamSynchronize(st));
   h.n_sets = n_sets;
+  s->sorted_sets = n_sets;
   h.nnzb = nnzb;
   SW_TRY(A(s, &h.col, nnzb, true));
   SW_TRY(A(s, &h.blk_row, nnzb, true));
@@ -1484,19 +1486,39 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       return SW_OK;
     };
     // Fast update: nothing removed, no new node, every appended surfel's set
-    // already known, and the surfels appended since the last set sort a small
-    // share of the model.  The JᵀJ pattern stays; the appended surfels follow
-    // the sorted ones in the internal order (the data term sums runs of equal
-    // sets, so any order is correct; the sort only keeps the runs long).
+    // already known or new with all its node pairs already blocks of the
+    // pattern, and the surfels appended since the last set sort a small share
+    // of the model.  The JᵀJ pattern stays; new sets are added after the
+    // known ones and the appended surfels follow the sorted ones in the
+    // internal order (the data term sums runs of equal sets, so any order is
+    // correct; the sort only keeps the runs long).
     if (n_stay == n_old && new_nodes == 0 && n_app > 0 && (s->unsorted + n_app) * 16 <= n_new &&
         model_block_size(s, s->knn_dist) >= (size_t)n_new * 16 && model_block_size(s, s->w_dist) >= (size_t)n_new * 16) {
-      Tmp set_of(s, (size_t)n_app * 4), miss(s, 16);
-      if (!set_of.p || !miss.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
-      SW_CUDA(s, cudaMemsetAsync(miss.p, 0, sizeof(int), st));
-      launch_find_sets(h, tknn.as<int4>(), n_stay, n_app, set_of.as<int>(), miss.as<int>(), st);
-      int missing = 0;
-      SW_CUDA(s, cudaMemcpyAsync(&missing, miss.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      Tmp set_of(s, (size_t)n_app * 4), keys(s, (size_t)n_app * 8), miss(s, 16);
+      if (!set_of.p || !keys.p || !miss.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
+      SW_CUDA(s, cudaMemsetAsync(miss.p, 0, 4 * sizeof(int), st));
+      launch_find_sets(h, s->sorted_sets, tknn.as<int4>(), n_stay, n_app, set_of.as<int>(),
+                       keys.as<unsigned long long>(), miss.as<int>(), st);
+      int cnt[4] = {0, 0, 0, 0};
+      SW_CUDA(s, cudaMemcpyAsync(cnt, miss.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
       SW_CUDA(s, cudaStreamSynchronize(st));
+      int missing = 0;
+      if (cnt[0] > 0 && model_block_size(s, h.set_slots) >= (size_t)(h.n_sets + cnt[0]) * 14 * sizeof(int)) {
+        // new sets: usable when all their node pairs are already blocks of the pattern
+        const size_t nb = new_sets_cub_bytes(n_app);
+        Tmp sorted(s, (size_t)n_app * 8), head(s, (size_t)n_app * 4), rank(s, (size_t)n_app * 4), tmp(s, nb);
+        if (!sorted.p || !head.p || !rank.p || !tmp.p)
+          return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
+        SW_CUDA(s, launch_new_sets(h, keys.as<unsigned long long>(), sorted.as<unsigned long long>(), head.as<int>(),
+                                   rank.as<int>(), n_app, cnt[0], set_of.as<int>(), miss.as<int>() + 1,
+                                   miss.as<int>() + 2, tmp.p, nb, st));
+        SW_CUDA(s, cudaMemcpyAsync(cnt, miss.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        SW_CUDA(s, cudaStreamSynchronize(st));
+        if (cnt[2] == 0) h.n_sets += cnt[1];   // the new sets' slots are in place
+        else missing = cnt[0];
+      } else {
+        missing = cnt[0];
+      }
       if (missing == 0) {
         SW_CUDA(s, cudaMemcpyAsync(s->knn_dist + n_old, tknn.as<int4>() + n_stay, (size_t)n_app * 16,
                                    cudaMemcpyDeviceToDevice, st));

@@ -451,10 +451,21 @@ __global__ void k_skin_merge(SwDev d, const float4* __restrict__ tv, int n, int 
 // in the set table, the pattern of JᵀJ does not change: the appended surfels
 // are put after the existing ones in the internal order with their set's id.
 
-// the set of each appended surfel (its 4 ids sorted ascending, searched among
-// the sets, which are in increasing key order), or -1; *missing counts the -1s
-__global__ void k_find_sets(SwDev d, const int4* __restrict__ tknn, int first, int n_app, int* __restrict__ set_of,
-                            int* __restrict__ missing) {
+__device__ __forceinline__ unsigned long long set_key(const int* a) {
+  return ((unsigned long long)a[0] << 48) | ((unsigned long long)a[1] << 32) | ((unsigned long long)a[2] << 16) |
+         (unsigned long long)a[3];
+}
+__device__ __forceinline__ unsigned long long slot_key(const SwDev& d, int set) {
+  const int* sl = d.set_slots + (size_t)set * 14 + 10;
+  return set_key(sl);
+}
+
+// the set of each appended surfel (its 4 ids sorted ascending), searched among
+// the sets: the first `sorted_sets` are in increasing key order (binary
+// search), the ones added since by fast updates follow (a scan); -1 and the
+// key in `keys` (~0 for a found one) when it has none; *missing counts them
+__global__ void k_find_sets(SwDev d, int sorted_sets, const int4* __restrict__ tknn, int first, int n_app,
+                            int* __restrict__ set_of, unsigned long long* __restrict__ keys, int* __restrict__ missing) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_app) return;
   const int4 q = tknn[first + k];
@@ -464,19 +475,74 @@ __global__ void k_find_sets(SwDev d, const int4* __restrict__ tknn, int first, i
 #pragma unroll
     for (int y = 0; y < 3 - x; ++y)
       if (a[y] > a[y + 1]) { const int t = a[y]; a[y] = a[y + 1]; a[y + 1] = t; }
-  const unsigned long long key = ((unsigned long long)a[0] << 48) | ((unsigned long long)a[1] << 32) |
-                                 ((unsigned long long)a[2] << 16) | (unsigned long long)a[3];
-  int lo = 0, hi = d.n_sets - 1, found = -1;
+  const unsigned long long key = set_key(a);
+  int lo = 0, hi = sorted_sets - 1, found = -1;
   while (lo <= hi) {
     const int mid = (lo + hi) >> 1;
-    const int* sl = d.set_slots + (size_t)mid * 14 + 10;
-    const unsigned long long mk = ((unsigned long long)sl[0] << 48) | ((unsigned long long)sl[1] << 32) |
-                                  ((unsigned long long)sl[2] << 16) | (unsigned long long)sl[3];
+    const unsigned long long mk = slot_key(d, mid);
     if (mk == key) { found = mid; break; }
     if (mk < key) lo = mid + 1; else hi = mid - 1;
   }
+  for (int t = sorted_sets; found < 0 && t < d.n_sets; ++t)
+    if (slot_key(d, t) == key) found = t;
   set_of[k] = found;
+  keys[k] = found < 0 ? key : ~0ull;
   if (found < 0) atomicAdd(missing, 1);
+}
+
+// block (a, b), a <= b, of the pattern, or -1 when it has none
+__device__ __forceinline__ int find_block_or_none(const SwDev& d, int a, int b) {
+  int lo = d.row_ptr[a], hi = d.row_ptr[a + 1] - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (d.col[mid] < b) lo = mid + 1; else hi = mid;
+  }
+  return d.col[lo] == b ? lo : -1;
+}
+
+// head[k] = 1 where sorted key k starts a run of equal keys
+__global__ void k_key_heads(const unsigned long long* __restrict__ sorted, int n, int* __restrict__ head) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) head[k] = (k == 0 || sorted[k] != sorted[k - 1]) ? 1 : 0;
+}
+
+// the distinct new sets (rank[k] among the distinct sorted keys), each with
+// its 10 blocks found in the pattern and written after the n_sets known ones;
+// *no_block is set when a pair of nodes has no block (the pattern would have
+// to grow)
+__global__ void k_new_sets(SwDev d, const unsigned long long* __restrict__ sorted, const int* __restrict__ head,
+                           const int* __restrict__ rank, int n_missing, int* __restrict__ n_new_sets,
+                           int* __restrict__ no_block) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_missing) return;
+  if (k == n_missing - 1) *n_new_sets = rank[k] + head[k];
+  if (!head[k]) return;
+  const unsigned long long key = sorted[k];
+  const int id[4] = {(int)(key >> 48), (int)((key >> 32) & 0xffff), (int)((key >> 16) & 0xffff), (int)(key & 0xffff)};
+  int* out = d.set_slots + (size_t)(d.n_sets + rank[k]) * 14;
+  int q = 0;
+  for (int x = 0; x < 4; ++x)
+    for (int y = x; y < 4; ++y) {
+      const int blk = find_block_or_none(d, id[x], id[y]);
+      if (blk < 0) atomicOr(no_block, 1);
+      out[q++] = blk < 0 ? 0 : blk;
+    }
+  for (int x = 0; x < 4; ++x) out[10 + x] = id[x];
+}
+
+// each surfel without a set takes its new set's id: n_sets + the rank of its key
+__global__ void k_assign_new_sets(SwDev d, const unsigned long long* __restrict__ keys,
+                                  const unsigned long long* __restrict__ sorted, const int* __restrict__ rank,
+                                  int n_missing, int n_app, int* __restrict__ set_of) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_app || set_of[k] >= 0) return;
+  const unsigned long long key = keys[k];
+  int lo = 0, hi = n_missing - 1;
+  while (lo < hi) {   // first position of the key
+    const int mid = (lo + hi) >> 1;
+    if (sorted[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  set_of[k] = d.n_sets + rank[lo];
 }
 
 // appended surfel k becomes internal (and caller) index first + k
@@ -514,10 +580,34 @@ __global__ void k_append_internal(SwDev d, const float4* __restrict__ tv, const 
 
 }  // namespace
 
-void launch_find_sets(const SwDev& d, const int4* tknn, int first, int n_app, int* set_of, int* missing,
-                      cudaStream_t st) {
-  if (n_app) k_find_sets<<<blocks(n_app, 256), 256, 0, st>>>(d, tknn, first, n_app, set_of, missing);
+void launch_find_sets(const SwDev& d, int sorted_sets, const int4* tknn, int first, int n_app, int* set_of,
+                      unsigned long long* keys, int* missing, cudaStream_t st) {
+  if (n_app) k_find_sets<<<blocks(n_app, 256), 256, 0, st>>>(d, sorted_sets, tknn, first, n_app, set_of, keys, missing);
 }
+
+size_t new_sets_cub_bytes(int n) {
+  size_t b = 0, c = 0;
+  cub::DeviceRadixSort::SortKeys(nullptr, b, (const unsigned long long*)nullptr, (unsigned long long*)nullptr, n);
+  cub::DeviceScan::ExclusiveSum(nullptr, c, (const int*)nullptr, (int*)nullptr, n);
+  return std::max(b, c);
+}
+
+cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsigned long long* sorted, int* head,
+                            int* rank, int n_app, int n_missing, int* set_of, int* n_new_sets, int* no_block,
+                            void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  // the found surfels' keys are ~0 and sort last: the first n_missing are the new sets' keys
+  size_t bytes = tmp_bytes;
+  cudaError_t e = cub::DeviceRadixSort::SortKeys(tmp, bytes, keys, sorted, n_app, 0, 64, st);
+  if (e != cudaSuccess) return e;
+  k_key_heads<<<blocks(n_missing, 256), 256, 0, st>>>(sorted, n_missing, head);
+  bytes = tmp_bytes;
+  e = cub::DeviceScan::ExclusiveSum(tmp, bytes, head, rank, n_missing, st);
+  if (e != cudaSuccess) return e;
+  k_new_sets<<<blocks(n_missing, 128), 128, 0, st>>>(d, sorted, head, rank, n_missing, n_new_sets, no_block);
+  k_assign_new_sets<<<blocks(n_app, 128), 128, 0, st>>>(d, keys, sorted, rank, n_missing, n_app, set_of);
+  return cudaGetLastError();
+}
+
 void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
                             const float4* tw, int first, int n_app, const int* set_of, cudaStream_t st) {
   if (n_app) k_append_internal<<<blocks(n_app, 256), 256, 0, st>>>(d, tv, tn, tt, tknn, tw, first, n_app, set_of);

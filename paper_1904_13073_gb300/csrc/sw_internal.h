@@ -227,8 +227,17 @@ void launch_knn4(const float4* queries, int n_q, const float4* nodes, int n_n, i
 // the fast model update after appending (k_append.cu): each appended surfel's
 // existing set (or -1, counted in *missing), then the appended surfels placed
 // after the first `first` surfels of the internal order with those sets
-void launch_find_sets(const SwDev& d, const int4* tknn, int first, int n_app, int* set_of, int* missing,
-                      cudaStream_t st);
+void launch_find_sets(const SwDev& d, int sorted_sets, const int4* tknn, int first, int n_app, int* set_of,
+                      unsigned long long* keys, int* missing, cudaStream_t st);
+// new sets of the appended surfels: the distinct keys among the n_missing
+// that `keys` holds (~0 for surfels that have a set) get the ids n_sets,
+// n_sets + 1, ... and their 10 blocks of the pattern in set_slots (which must
+// have room); *no_block = 1 when a pair of their nodes has no block (scratch:
+// sorted n_app keys, head and rank n_app ints each)
+size_t new_sets_cub_bytes(int n);
+cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsigned long long* sorted, int* head,
+                            int* rank, int n_app, int n_missing, int* set_of, int* n_new_sets, int* no_block,
+                            void* tmp, size_t tmp_bytes, cudaStream_t st);
 void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
                             const float4* tw, int first, int n_app, const int* set_of, cudaStream_t st);
 // node-graph extension after appending (k_append.cu): coverage flags of the

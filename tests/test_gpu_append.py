@@ -329,22 +329,25 @@ def test_node_extension_matches_oracle(precision):
 
 
 def test_fast_update_on_a_growing_model_matches_oracle():
-    """Three appending frames on identical inputs.  The first fills a hole
-    (new node sets: re-sorted, pattern rebuilt); the next two append a few
-    dozen to a few hundred surfels along its edges, all in node sets the model
-    already has, so they are placed after the sorted surfels without a re-sort.
-    The model, its skinning and the next solve agree with the oracle."""
-    scene = _cut(synth.plain_tiny(seed=0), unstable=0)
+    """Four appending frames on identical inputs, on a model with 5% of its
+    surfels cut away, under growing warps.  Worked out on the oracle's model:
+    frame 1 appends 892 surfels forming 4 new node sets whose node pairs are
+    all blocks of the pattern already (fast update: new sets added, no
+    re-sort); frame 2 forms 2 new sets with a pair the pattern lacks (re-sort,
+    pattern rebuilt); frame 3 appends 365 surfels in known sets (fast);
+    frame 4 again needs a new block (re-sort).  The model, its skinning and
+    the next solve agree with the oracle."""
+    scene = _cut(synth.plain_tiny(seed=0), frac=0.05, unstable=0)
     c = scene.cam
     b = Both(scene, len(scene.surfel_v) + c.width * c.height)
     try:
         d = scene.frame(1)
         resorted = []
-        for t, seed in ((1, 5), (2, 6), (3, 7)):
+        for t, (seed, amp, tr) in enumerate([(5, 0.5, 0.002), (6, 0.6, 0.003), (7, 0.7, 0.004), (8, 0.8, 0.005)], 1):
             sw.sw_upload_depth(b.h, d, t)
             b.o.upload_depth(d, t)
             b.set_maps()
-            dq8 = _warp(scene, seed, 0.5, 0.002, alpha=0.0)
+            dq8 = _warp(scene, seed, amp, tr, alpha=0.0)
             sw.sw_set_node_dq(b.h, dq8)
             b.o.node_dq = dq8.astype(np.float64)
             _, vl, nl = OS.warp_surfels(b.o.v_ref, b.o.n_ref, b.o.knn, b.o.w, b.o.node_dq)
@@ -356,7 +359,15 @@ def test_fast_update_on_a_growing_model_matches_oracle():
             _, n_app, _ = b.o.append_frame(b.max_surfels, EPS, DNN, FDH)
             assert st["appended"] == n_app and st["n_surfels"] == len(b.o.v_ref), (t, st, n_app)
             resorted.append(st["resorted"])
-        assert resorted == [1, 0, 0]
+            if t == 3:   # a solve on the fast-updated model (appended surfels after the sorted ones)
+                st3 = sw.sw_solve_frame(b.h, 2, 8)
+                ost3 = b.o.solve_frame(2, 8)
+                assert abs(st3["n_corr"][0] - ost3[0].n_corr) <= 3
+                _, dq3 = sw.sw_read_nodes(b.h)
+                dq3 = dq3.astype(np.float64)
+                assert rotation_angle_between(dq3, b.o.node_dq).max() < 1e-4
+                assert np.linalg.norm(OS.node_transform(dq3, b.o.node_p) - b.o.warped_nodes(), axis=1).max() < 2e-5
+        assert resorted == [0, 1, 0, 1]
         v, n, t2 = sw.sw_read_surfels(b.h)
         np.testing.assert_allclose(v[:, :3], b.o.v_ref, atol=2e-6)
         np.testing.assert_allclose(n[:, :3], b.o.n_ref, atol=2e-6)
@@ -364,7 +375,7 @@ def test_fast_update_on_a_growing_model_matches_oracle():
         knn, w = sw.sw_read_skinning(b.h)
         np.testing.assert_array_equal(knn, b.o.knn)
         np.testing.assert_allclose(w, b.o.w, rtol=2e-6, atol=1e-30)
-        # the next solve runs on the appended surfels in their unsorted place
+        # and a solve on the re-sorted model
         sw.sw_upload_depth(b.h, d, 4)
         b.o.upload_depth(d, 4)
         b.set_maps()
