@@ -222,6 +222,28 @@ size_t model_block_size(const sw_stream* s, const void* p) {
   return 0;
 }
 
+// Make the model block *p hold `need` bytes, keeping its first `used` bytes:
+// a larger block from the cache, the old one back into it (stream order keeps
+// the copy ahead of any reuse).
+sw_status grow_model_block(sw_stream* s, void** p, size_t used, size_t need) {
+  if (model_block_size(s, *p) >= need) return SW_OK;
+  void* q = nullptr;
+  size_t got = 0;
+  SW_TRY_(cached_alloc(s, &q, need, &got));
+  if (used) {
+    const cudaError_t e = cudaMemcpyAsync(q, *p, used, cudaMemcpyDeviceToDevice, s->st);
+    if (e != cudaSuccess) return fail(s, SW_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  }
+  for (auto& a : s->model_allocs)
+    if (a.first == *p) {
+      s->cache.emplace(a.second, a.first);
+      a = std::make_pair(q, got);
+      break;
+    }
+  *p = q;
+  return SW_OK;
+}
+
 void recycle_model(sw_stream* s) {
   for (auto& a : s->model_allocs) s->cache.emplace(a.second, a.first);
   s->model_allocs.clear();
@@ -1492,8 +1514,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     // known ones and the appended surfels follow the sorted ones in the
     // internal order (the data term sums runs of equal sets, so any order is
     // correct; the sort only keeps the runs long).
-    if (n_stay == n_old && new_nodes == 0 && n_app > 0 && (s->unsorted + n_app) * 16 <= n_new &&
-        model_block_size(s, s->knn_dist) >= (size_t)n_new * 16 && model_block_size(s, s->w_dist) >= (size_t)n_new * 16) {
+    if (n_stay == n_old && new_nodes == 0 && n_app > 0 && (s->unsorted + n_app) * 16 <= n_new) {
       Tmp set_of(s, (size_t)n_app * 4), keys(s, (size_t)n_app * 8), miss(s, 16);
       if (!set_of.p || !keys.p || !miss.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
       SW_CUDA(s, cudaMemsetAsync(miss.p, 0, 4 * sizeof(int), st));
@@ -1503,8 +1524,11 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       SW_CUDA(s, cudaMemcpyAsync(cnt, miss.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
       SW_CUDA(s, cudaStreamSynchronize(st));
       int missing = 0;
-      if (cnt[0] > 0 && model_block_size(s, h.set_slots) >= (size_t)(h.n_sets + cnt[0]) * 14 * sizeof(int)) {
-        // new sets: usable when all their node pairs are already blocks of the pattern
+      if (cnt[0] > 0) {
+        // new sets: usable when all their node pairs are already blocks of the
+        // pattern; their slots go after the known sets' (the table grows if needed)
+        SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&h.set_slots), (size_t)h.n_sets * 14 * sizeof(int),
+                                (size_t)(h.n_sets + cnt[0]) * 14 * sizeof(int)));
         const size_t nb = new_sets_cub_bytes(n_app);
         Tmp sorted(s, (size_t)n_app * 8), head(s, (size_t)n_app * 4), rank(s, (size_t)n_app * 4), tmp(s, nb);
         if (!sorted.p || !head.p || !rank.p || !tmp.p)
@@ -1516,10 +1540,11 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
         SW_CUDA(s, cudaStreamSynchronize(st));
         if (cnt[2] == 0) h.n_sets += cnt[1];   // the new sets' slots are in place
         else missing = cnt[0];
-      } else {
-        missing = cnt[0];
       }
       if (missing == 0) {
+        // the caller-order skinning copies grow into a larger block if needed
+        SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->knn_dist), (size_t)n_old * 16, (size_t)n_new * 16));
+        SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->w_dist), (size_t)n_old * 16, (size_t)n_new * 16));
         SW_CUDA(s, cudaMemcpyAsync(s->knn_dist + n_old, tknn.as<int4>() + n_stay, (size_t)n_app * 16,
                                    cudaMemcpyDeviceToDevice, st));
         SW_CUDA(s, cudaMemcpyAsync(s->w_dist + n_old, tw.as<float4>() + n_stay, (size_t)n_app * 16,
