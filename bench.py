@@ -707,14 +707,16 @@ def main():
         sw.sw_fuse_frame(hp)
         a_st = sw.sw_append_frame(hp)
         torch.cuda.synchronize()
-        pipe.append((1000.0 * (time.perf_counter() - a0), a_st["appended"], a_st["n_surfels"]))
+        pipe.append((1000.0 * (time.perf_counter() - a0), a_st["appended"], a_st["n_surfels"], a_st["resorted"]))
     sw.sw_destroy_stream(hp)
     steady_pipe = pipe[2:]   # the first frames fill the cut-away hole
-    pipeline = {"frames_per_s": 1000.0 / float(np.mean([m for m, _, _ in steady_pipe])),
-                "ms_per_frame": float(np.mean([m for m, _, _ in steady_pipe])),
-                "appended_per_frame": float(np.mean([a for _, a, _ in steady_pipe])),
-                "frames_with_appends": int(sum(1 for _, a, _ in steady_pipe if a > 0)),
-                "first_frames": [{"ms": m, "appended": a, "surfels": n} for m, a, n in pipe[:2]],
+    pipeline = {"frames_per_s": 1000.0 / float(np.mean([m for m, _, _, _ in steady_pipe])),
+                "ms_per_frame": float(np.mean([m for m, _, _, _ in steady_pipe])),
+                "appended_per_frame": float(np.mean([a for _, a, _, _ in steady_pipe])),
+                "frames_with_appends": int(sum(1 for _, a, _, _ in steady_pipe if a > 0)),
+                "frames_resorted": int(sum(1 for _, _, _, r in steady_pipe if r == 1)),
+                "frames_pattern_rebuilt": int(sum(1 for _, _, _, r in steady_pipe if r == 2)),
+                "first_frames": [{"ms": m, "appended": a, "surfels": n, "resorted": r} for m, a, n, r in pipe[:2]],
                 "note": "upload + solve + fusion + sw_append_frame per frame, wall clock, on the model cut by "
                         "30%; steady frames after the first two"}
     appending = {"steady": appends[1:], "model_cut_30pct": cut_st, "model_and_nodes_cut_30pct": ext_st,

@@ -460,8 +460,10 @@ typedef struct {
   int new_nodes;         /* nodes added by the node-graph extension */
   int resorted;          /* 1: the surfels were re-sorted by node set and the JᵀJ pattern rebuilt;
                             0: no change, or the appended surfels were placed after the sorted ones
-                            (nothing removed, no new node, every 4-node set already present, and the
-                            surfels so placed since the last re-sort at most 1/16 of the model) */
+                            (nothing removed, no new node, and the surfels so placed since the last
+                            re-sort at most 1/16 of the model), new node sets added to the set table,
+                            the JᵀJ pattern kept (every new set's node pairs already blocks of it);
+                            2: as 0, with the JᵀJ pattern rebuilt for node pairs it lacked */
 } sw_append_stats;
 sw_status sw_append_frame(sw_handle h, sw_append_stats* stats);
 /* Per-candidate record of the last sw_append_frame, candidate order (row-

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <queue>
@@ -242,6 +243,19 @@ sw_status grow_model_block(sw_stream* s, void** p, size_t used, size_t need) {
     }
   *p = q;
   return SW_OK;
+}
+
+// The given model blocks (null entries skipped) go back to the cache.
+void recycle_blocks(sw_stream* s, std::initializer_list<const void*> blocks) {
+  for (const void* p : blocks) {
+    if (!p) continue;
+    for (size_t k = 0; k < s->model_allocs.size(); ++k)
+      if (s->model_allocs[k].first == p) {
+        s->cache.emplace(s->model_allocs[k].second, s->model_allocs[k].first);
+        s->model_allocs.erase(s->model_allocs.begin() + (long)k);
+        break;
+      }
+  }
 }
 
 void recycle_model(sw_stream* s) {
@@ -1494,7 +1508,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_CUDA(s, cudaGetLastError());
     SW_CUDA(s, cudaEventRecord(ev1, st));
     const auto t0 = std::chrono::steady_clock::now();
-    auto finish = [&](bool rebuilt) -> sw_status {
+    auto finish = [&](int resorted) -> sw_status {
       float kms = 0.f;
       cudaEventElapsedTime(&kms, ev0, ev1);   // both are complete: the caller synchronised
       cudaEventDestroy(ev0);
@@ -1503,17 +1517,18 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
         stats->kernel_ms = kms;
         stats->rebuild_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       }
-      if (stats) stats->resorted = rebuilt ? 1 : 0;
+      if (stats) stats->resorted = resorted;
       s->fused = false;
       return SW_OK;
     };
-    // Fast update: nothing removed, no new node, every appended surfel's set
-    // already known or new with all its node pairs already blocks of the
-    // pattern, and the surfels appended since the last set sort a small share
-    // of the model.  The JᵀJ pattern stays; new sets are added after the
-    // known ones and the appended surfels follow the sorted ones in the
+    // Fast update: nothing removed, no new node, and the surfels appended
+    // since the last set sort a small share of the model.  Each appended
+    // surfel takes its node set's id: a known set's, or a new one added after
+    // the known sets.  The appended surfels follow the sorted ones in the
     // internal order (the data term sums runs of equal sets, so any order is
-    // correct; the sort only keeps the runs long).
+    // correct; the sort only keeps the runs long).  The JᵀJ pattern stays when
+    // every new set's node pairs are blocks of it already, else it is rebuilt
+    // from the extended set table (the surfels keep their order).
     if (n_stay == n_old && new_nodes == 0 && n_app > 0 && (s->unsorted + n_app) * 16 <= n_new) {
       Tmp set_of(s, (size_t)n_app * 4), keys(s, (size_t)n_app * 8), miss(s, 16);
       if (!set_of.p || !keys.p || !miss.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
@@ -1523,10 +1538,10 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       int cnt[4] = {0, 0, 0, 0};
       SW_CUDA(s, cudaMemcpyAsync(cnt, miss.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
       SW_CUDA(s, cudaStreamSynchronize(st));
-      int missing = 0;
+      int n_sets_all = h.n_sets;
+      bool new_pairs = false;
       if (cnt[0] > 0) {
-        // new sets: usable when all their node pairs are already blocks of the
-        // pattern; their slots go after the known sets' (the table grows if needed)
+        // the new sets' slots go after the known sets' (the table grows if needed)
         SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&h.set_slots), (size_t)h.n_sets * 14 * sizeof(int),
                                 (size_t)(h.n_sets + cnt[0]) * 14 * sizeof(int)));
         const size_t nb = new_sets_cub_bytes(n_app);
@@ -1538,30 +1553,43 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
                                    miss.as<int>() + 2, tmp.p, nb, st));
         SW_CUDA(s, cudaMemcpyAsync(cnt, miss.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         SW_CUDA(s, cudaStreamSynchronize(st));
-        if (cnt[2] == 0) h.n_sets += cnt[1];   // the new sets' slots are in place
-        else missing = cnt[0];
+        n_sets_all = h.n_sets + cnt[1];
+        if (cnt[2] == 0) h.n_sets = n_sets_all;   // the new sets' slots are complete
+        else new_pairs = true;                    // a pair of nodes has no block yet
       }
-      if (missing == 0) {
-        // the caller-order skinning copies grow into a larger block if needed
-        SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->knn_dist), (size_t)n_old * 16, (size_t)n_new * 16));
-        SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->w_dist), (size_t)n_old * 16, (size_t)n_new * 16));
-        SW_CUDA(s, cudaMemcpyAsync(s->knn_dist + n_old, tknn.as<int4>() + n_stay, (size_t)n_app * 16,
-                                   cudaMemcpyDeviceToDevice, st));
-        SW_CUDA(s, cudaMemcpyAsync(s->w_dist + n_old, tw.as<float4>() + n_stay, (size_t)n_app * 16,
-                                   cudaMemcpyDeviceToDevice, st));
-        launch_append_internal(h, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
-                               n_old, n_app, set_of.as<int>(), st);
-        SW_CUDA(s, cudaGetLastError());
-        if (s->run) drop_graphs(s->run);
-        s->version++;
-        h.n_s = n_new;
-        s->unsorted += n_app;
+      // the caller-order skinning copies grow into a larger block if needed
+      SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->knn_dist), (size_t)n_old * 16, (size_t)n_new * 16));
+      SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&s->w_dist), (size_t)n_old * 16, (size_t)n_new * 16));
+      SW_CUDA(s, cudaMemcpyAsync(s->knn_dist + n_old, tknn.as<int4>() + n_stay, (size_t)n_app * 16,
+                                 cudaMemcpyDeviceToDevice, st));
+      SW_CUDA(s, cudaMemcpyAsync(s->w_dist + n_old, tw.as<float4>() + n_stay, (size_t)n_app * 16,
+                                 cudaMemcpyDeviceToDevice, st));
+      launch_append_internal(h, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
+                             n_old, n_app, set_of.as<int>(), st);
+      SW_CUDA(s, cudaGetLastError());
+      if (s->run) drop_graphs(s->run);
+      s->version++;
+      h.n_s = n_new;
+      s->unsorted += n_app;
+      if (!new_pairs) {
         SW_TRY(sync_desc(s));
         launch_warp_live(s->run->bh, st);
         SW_CUDA(s, cudaGetLastError());
         SW_CUDA(s, cudaStreamSynchronize(st));
-        return finish(false);
+        return finish(0);
       }
+      // the pattern gains the new sets' node pairs: rebuilt from the set
+      // table (known sets first, in their order), the surfels untouched
+      Tmp all_sets(s, (size_t)n_sets_all * 16);
+      if (!all_sets.p) return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
+      launch_slot_sets(h.set_slots, n_sets_all, all_sets.as<int4>(), st);
+      SW_CUDA(s, cudaGetLastError());
+      const int sorted_sets = s->sorted_sets;
+      s->has_model = false;
+      recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A64});
+      SW_TRY(install_pattern(s, all_sets.as<int4>(), n_sets_all, false));
+      s->sorted_sets = sorted_sets;
+      return finish(2);
     }
     s->unsorted = 0;
     // the model's layout changes: rebuild its structure (nodes and transforms
@@ -1578,7 +1606,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     SW_TRY(setup_surfels(s, tv.as<float4>(), tn.as<float4>(), tt.as<int2>(), tknn.as<int4>(), tw.as<float4>(),
                          n_new, sets, &n_sets));
     SW_TRY(install_pattern(s, sets.as<int4>(), n_sets, new_nodes > 0));
-    return finish(true);
+    return finish(1);
   }
 }
 

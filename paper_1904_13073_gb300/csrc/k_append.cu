@@ -545,6 +545,14 @@ __global__ void k_assign_new_sets(SwDev d, const unsigned long long* __restrict_
   set_of[k] = d.n_sets + rank[lo];
 }
 
+// the node ids of sets [0, n) from the set table (entries 10-13 of each row)
+__global__ void k_slot_sets(const int* __restrict__ slots, int n, int4* __restrict__ sets) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int* r = slots + (size_t)t * 14 + 10;
+  sets[t] = make_int4(r[0], r[1], r[2], r[3]);
+}
+
 // appended surfel k becomes internal (and caller) index first + k
 __global__ void k_append_internal(SwDev d, const float4* __restrict__ tv, const float4* __restrict__ tn,
                                   const int2* __restrict__ tt, const int4* __restrict__ tknn,
@@ -606,6 +614,10 @@ cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsi
   k_new_sets<<<blocks(n_missing, 128), 128, 0, st>>>(d, sorted, head, rank, n_missing, n_new_sets, no_block);
   k_assign_new_sets<<<blocks(n_app, 128), 128, 0, st>>>(d, keys, sorted, rank, n_missing, n_app, set_of);
   return cudaGetLastError();
+}
+
+void launch_slot_sets(const int* slots, int n, int4* sets, cudaStream_t st) {
+  if (n) k_slot_sets<<<blocks(n, 256), 256, 0, st>>>(slots, n, sets);
 }
 
 void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,

@@ -238,6 +238,8 @@ size_t new_sets_cub_bytes(int n);
 cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsigned long long* sorted, int* head,
                             int* rank, int n_app, int n_missing, int* set_of, int* n_new_sets, int* no_block,
                             void* tmp, size_t tmp_bytes, cudaStream_t st);
+// the node ids of the sets [0, n) of a set table (14 ints per set) into sets[n]
+void launch_slot_sets(const int* slots, int n, int4* sets, cudaStream_t st);
 void launch_append_internal(const SwDev& d, const float4* tv, const float4* tn, const int2* tt, const int4* tknn,
                             const float4* tw, int first, int n_app, const int* set_of, cudaStream_t st);
 // node-graph extension after appending (k_append.cu): coverage flags of the
