@@ -141,7 +141,7 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
 # ncu capture of this workload's kernels as they are now;
 # profiles/k_pcg_gear_plain_full_300k_2048.md and
 # profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": 2.931712e6 + 0.013312e6, "data_assembly": 25.230848e6 + 0.028416e6}
+PROFILED_TRAFFIC = {"pcg": None, "data_assembly": 25.230848e6 + 0.028416e6}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
@@ -745,8 +745,9 @@ def main():
                 "p50_ms": 1000.0 * float(np.percentile(e_lat, 50)), "p99_ms": 1000.0 * float(np.percentile(e_lat, 99))},
         "clocks": clocks,
         # kernels of this library per step: depth (frame id + maps), solve
-        # (stats reset + 3 per Gauss-Newton iteration), fusion (3)
-        "gpu_launches": args.steps * (2 + 1 + 3 * gn + 3),
+        # (stats reset + 4 per Gauss-Newton iteration: regulariser, data term,
+        # preconditioner, PCG), fusion (3)
+        "gpu_launches": args.steps * (2 + 1 + 4 * gn + 3),
         "roofline": roof["dominant"],
         "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
         "stage_roofline": roof["stages"],

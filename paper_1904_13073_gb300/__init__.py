@@ -126,6 +126,7 @@ _SIGS = {
     "sw_batch_set_profiling": [_P, _I],
     "sw_batch_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "sw_debug_barrier_timeout": [_I, ctypes.POINTER(_I)],
+    "sw_debug_block_inverse": [_P, _I, _I, _P, _P],
     "sw_server_create": [ctypes.c_size_t, _I, _I, _I, ctypes.POINTER(_P)],
     "sw_server_destroy": [_P],
     "sw_server_open": [_P, ctypes.POINTER(sw_params), _P, _P, _P, _I, _P, _I, ctypes.POINTER(_I)],
@@ -487,6 +488,18 @@ def sw_batch_set_profiling(b, enable):
 
 def sw_batch_read_profile(b):
     return _profile(lib().sw_batch_read_profile, b, None)
+
+
+def sw_debug_block_inverse(blocks, fp64=False):
+    """(inverses (n, 21) packed lower, ok (n,) bool) of the PCG's block inverse on (n, 6, 6) blocks."""
+    dt = np.float64 if fp64 else np.float32
+    b = np.ascontiguousarray(np.asarray(blocks, dt).reshape(-1, 36))
+    n = b.shape[0]
+    out = np.empty((max(1, n), 21), dt)
+    ok = np.empty(max(1, n), np.int32)
+    _check(lib().sw_debug_block_inverse(b.ctypes.data_as(_P), n, int(bool(fp64)), out.ctypes.data_as(_P),
+                                        ok.ctypes.data_as(_P)), None)
+    return out[:n], ok[:n].astype(bool)
 
 
 def sw_debug_barrier_timeout(spin_limit):

@@ -512,6 +512,7 @@ sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vect
     launch_data_stage(r->bh, it, st);
     prof_mark(r, prof, kProfData, false, true);
     prof_mark(r, prof, kProfPcg, true, true);
+    launch_precond(r->bh, st);
     SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
     prof_mark(r, prof, kProfPcg, false, true);
   }
@@ -739,6 +740,7 @@ sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows,
     for (int rep = 0; rep < 4 && ok; ++rep) {
       launch_reg_stage(r->bh, 0, st);
       launch_data_stage(r->bh, 0, st);
+      launch_precond(r->bh, st);
       cudaEventRecord(e0, st);
       ok = launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
       cudaEventRecord(e1, st);
@@ -872,13 +874,15 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.in_ptr, nn + 1); ALLOC(h.in_src, SW_K_GRAPH * nn);
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
   ALLOC(h.vis_map, np); ALLOC(h.visible, ns);
-  ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.Li, 21 * nn);
+  ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.minv, 21 * nn);
   ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
   ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
   ALLOC(h.xz, 6 * nn); ALLOC(h.xp, 12 * nn);
   ALLOC(h.rigid, kRigidSlots); ALLOC(h.rigid_stats, 2 * kMaxRigid);
   ALLOC(h.rigid_part, (size_t)kRigidSums * ((ns + kSurfTile - 1) / kSurfTile));
-  if (p->precision == SW_PRECISION_FP64) { ALLOC(h.g64, 6 * nn); ALLOC(h.v64, 18 * nn); ALLOC(h.dq64, 8 * nn); }
+  if (p->precision == SW_PRECISION_FP64) {
+    ALLOC(h.g64, 6 * nn); ALLOC(h.v64, 18 * nn); ALLOC(h.dq64, 8 * nn); ALLOC(h.minv64, 21 * nn);
+  }
   ALLOC(h.e_depth, kMaxGn); ALLOC(h.e_reg, kMaxGn); ALLOC(h.n_corr, kMaxGn); ALLOC(h.pcg_rz, kMaxGn);
   ALLOC(h.status, 1); ALLOC(h.t_now, 1);
 #undef ALLOC
@@ -2042,6 +2046,27 @@ sw_status sw_batch_set_profiling(sw_batch_handle b, int enable) {
 sw_status sw_batch_read_profile(sw_batch_handle b, double* ms, int* launches) {
   if (!b) return fail(nullptr, SW_ERR_INVALID_ARG, "null batch");
   return runner_profile(&b->run, nullptr, ms, launches);
+}
+
+sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* inv21, int* ok) {
+  if (n < 0 || n > (1 << 24)) return fail(nullptr, SW_ERR_INVALID_ARG, "n out of range");
+  if (n > 0 && (!blocks36 || !inv21 || !ok)) return fail(nullptr, SW_ERR_INVALID_ARG, "null array");
+  if (n == 0) return SW_OK;
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  void *db = nullptr, *dout = nullptr;
+  int* dok = nullptr;
+  cudaError_t e = cudaMalloc(&db, (size_t)n * 36 * es);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)n * 21 * es);
+  if (e == cudaSuccess) e = cudaMalloc(&dok, (size_t)n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(db, blocks36, (size_t)n * 36 * es, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_debug_block_inverse(db, n, fp64, dout, dok, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(inv21, dout, (size_t)n * 21 * es, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ok, dok, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(db);
+  cudaFree(dout);
+  cudaFree(dok);
+  if (e != cudaSuccess) return fail(nullptr, SW_ERR_CUDA, std::string("block inverse: ") + cudaGetErrorString(e));
+  return SW_OK;
 }
 
 sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out) {

@@ -94,39 +94,95 @@ __device__ __forceinline__ float ratio_f32(double a, double b) {
 __device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }   // packed, r >= c
 __device__ __forceinline__ int sym(int r, int c) { return r >= c ? tri(r, c) : tri(c, r); }
 
-// M⁻¹ of one diagonal block (symmetric, packed lower) by Cholesky A = L Lᵀ in
-// FP64: M⁻¹ = L⁻ᵀ L⁻¹.  The block's two triangles are averaged first.  False
-// if the block is not positive definite.
+// 1/x for a positive FP64 x: the FP32 reciprocal as the seed, refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each of which about doubles the
+// number of correct bits (24 -> 48 -> the FP64 rounding limit).  A division
+// in FP64 is a chain of several hundred cycles on this part; this is ~6
+// dependent FP64 operations.  Outside the range where the FP32 seed is
+// accurate, the plain division.
+__device__ __forceinline__ double recip64(double x) {
+  const float xf = (float)x;
+  if (!(xf >= 1e-30f && xf <= 1e30f)) return 1.0 / x;
+  double r = (double)__frcp_rn(xf);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ int sl(int r, int c) { return r * (r - 1) / 2 + c; }   // strict lower, r > c
+
+// M⁻¹ of one diagonal block (symmetric, packed lower) in FP64 by the
+// factorisation A = L D Lᵀ (L unit lower triangular): M⁻¹ = L⁻ᵀ D⁻¹ L⁻¹.
+// The block's two triangles are averaged first.  No square roots, and the
+// six pivots' reciprocals by recip64, so the dependent chain is short.
+// False if the block is not positive definite (a pivot <= 0).
 template <typename Real>
 __device__ bool block_inverse(const Real* a, Real* out) {
-  double L[21], Li[21];
+  // every loop has a constant trip count (bounds as predicates), so that all
+  // of them unroll and the arrays live in registers.
+  // S: the averaged block (packed lower); its strict lower part is then
+  // overwritten by E = L D (E_rc = L_rc d_c) and finally by Y = D⁻¹ L⁻¹
+  double S[21], L[15], Di[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (c < r) S[tri(r, c)] = 0.5 * ((double)a[r * 6 + c] + (double)a[c * 6 + r]);
+      if (c == r) S[tri(r, r)] = (double)a[r * 6 + r];
+    }
+  // column by column: d_c = a_cc − Σ_{k<c} L_ck E_ck, E_rc = a_rc − Σ_{k<c} L_rk E_ck, L_rc = E_rc / d_c
+#pragma unroll
   for (int c = 0; c < 6; ++c) {
-    double s = (double)a[c * 6 + c];
-    for (int k = 0; k < c; ++k) s -= L[tri(c, k)] * L[tri(c, k)];
-    if (!(s > 0.0)) return false;
-    const double lcc = sqrt(s), inv = 1.0 / lcc;
-    L[tri(c, c)] = lcc;
-    Li[tri(c, c)] = inv;
-    for (int r = c + 1; r < 6; ++r) {
-      double t = 0.5 * ((double)a[r * 6 + c] + (double)a[c * 6 + r]);
-      for (int k = 0; k < c; ++k) t -= L[tri(r, k)] * L[tri(c, k)];
-      L[tri(r, c)] = t * inv;
+    double dc = S[tri(c, c)];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < c) dc = fma(-L[sl(c, k)], S[tri(c, k)], dc);
+    if (!(dc > 0.0)) return false;
+    Di[c] = recip64(dc);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (r <= c) continue;
+      double e = S[tri(r, c)];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < c) e = fma(-L[sl(r, k)], S[tri(c, k)], e);
+      S[tri(r, c)] = e;
+      L[sl(r, c)] = e * Di[c];
     }
   }
-  for (int c = 0; c < 6; ++c) {   // Li = L⁻¹ by forward substitution, column by column
-    for (int r = c + 1; r < 6; ++r) {
-      double t = 0.0;
-      for (int k = c; k < r; ++k) t += L[tri(r, k)] * Li[tri(k, c)];
-      Li[tri(r, c)] = -t * Li[tri(r, r)];
+  // X = L⁻¹ (unit lower), over L column by column (column c reads only
+  // columns > c of L): X_rc = −L_rc − Σ_{c<k<r} L_rk X_kc
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (r <= c) continue;
+      double x = -L[sl(r, c)];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k > c && k < r) x = fma(-L[sl(r, k)], L[sl(k, c)], x);
+      L[sl(r, c)] = x;
     }
-  }
-  for (int r = 0; r < 6; ++r) {   // (L⁻ᵀ L⁻¹)_rc = Σ_{k >= r} Li_kr Li_kc, r >= c
-    for (int c = 0; c <= r; ++c) {
-      double t = 0.0;
-      for (int k = r; k < 6; ++k) t += Li[tri(k, r)] * Li[tri(k, c)];
-      out[tri(r, c)] = (Real)t;
+  // M⁻¹_rc = Σ_{k>=r} X_kr D⁻¹_k X_kc (r >= c, X_kk = 1) = Y_rc + Σ_{k>r} X_kr Y_kc, Y = D⁻¹ X
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (k == c) S[tri(c, c)] = Di[c];
+      if (k > c) S[tri(k, c)] = Di[k] * L[sl(k, c)];
     }
-  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (c > r) continue;
+      double m = S[tri(r, c)];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k > r) m = fma(L[sl(k, r)], S[tri(k, c)], m);
+      out[tri(r, c)] = (Real)m;
+    }
   return true;
 }
 
@@ -298,6 +354,23 @@ __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, Pa
   return s_ok != 0;
 }
 
+// The CTA's sum of v (nonzero only in lanes below `lanes` of each warp, a
+// power of two) added to *dst with one FP64 atomic.
+template <typename Acc>
+__device__ __forceinline__ void block_add_value(Acc v, int lanes, double* dst) {
+  using O = AccOps<Acc>;
+  __shared__ Acc s_w[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = lanes >> 1; o > 0; o >>= 1) v = O::add(v, O::shfl_xor(v, o));
+  if (lane == 0) s_w[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    Acc b = lane < nw ? s_w[lane] : O::zero();
+    b = warp_sum_acc(b);
+    if (lane == 0) atomicAdd(dst, O::value(b));
+  }
+}
+
 // One value, release / acquire: the value, one acq_rel fence and a relaxed
 // store of the stamp, so the CTA's global writes before the call go with it;
 // pollers take acquire loads of the stamps.
@@ -402,14 +475,16 @@ __host__ __device__ constexpr SmemLayout pcg_layout(int rows_cap, int ent_cap, i
   return L;
 }
 
-// Staged modes, at set-up: the rows' entry offsets (warp 0, an exclusive
-// scan of the row lengths), then per entry its block turned to multiply the
-// neighbour's vector (kSpmvSmemA) or where to find it (kSpmvSmemOut).
+// Staged modes, at set-up, by the warps [w0, kPcgWarps) of the CTA (the
+// others may be busy with other set-up work): the rows' entry offsets (warp
+// w0, an exclusive scan of the row lengths), then per entry its block turned
+// to multiply the neighbour's vector (kSpmvSmemA) or where to find it
+// (kSpmvSmemOut).  The participating warps meet at named barrier 1.
 template <int kMode, typename Real>
 __device__ __forceinline__ void stage_entries(const SwDev& d, const Real* A, int t, int Gs, int nr, int ent_cap,
-                                              Real* sA, int* sj, int2* sent, int* soff) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
+                                              Real* sA, int* sj, int2* sent, int* soff, int w0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kPcgWarps - w0;
+  if (warp == w0) {
     int run = 0;
     for (int a0 = 0; a0 < nr; a0 += 32) {
       const int a = a0 + lane;
@@ -426,8 +501,8 @@ __device__ __forceinline__ void stage_entries(const SwDev& d, const Real* A, int
     }
     if (lane == 0) soff[0] = 0;
   }
-  __syncthreads();
-  for (int a = warp; a < nr; a += kPcgWarps) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+  for (int a = warp - w0; a < nr; a += nw) {
     const int i = t + Gs * a;
     const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
     for (int k = lane; k < len; k += 32) {
@@ -524,8 +599,10 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
   for (int a = tid; a < nr; a += kPcgThreads) {
     const int j = t + Gs * a;
     double* mi = sMi + 21 * a;
-    if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
-      atomicOr(d.status, kStatusBreakdown);
+    const double* src = d.minv64 + 21 * (size_t)j;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) mi[k] = __ldg(src + k);
+    if (mi[0] != mi[0]) {   // not positive definite (flagged by the preconditioner launch)
       broken = true;
 #pragma unroll
       for (int k = 0; k < 21; ++k) mi[k] = 0;
@@ -547,7 +624,7 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
     }
   }
   if (broken) pa = acc_nan<Acc>();   // reaches every CTA through the first reduction
-  if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff);
+  if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff, 0);
   if (!stream_reduce_fenced(pa, 32, d.part, t, Gs, base + 1, spin_limit, [&](Acc rz) {
         sc.rz = rz;
         sc.bad = acc_is_nan(rz);
@@ -731,34 +808,40 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
   // ---- set-up, a thread per own row: M⁻¹, r = −g, u = M⁻¹ r (published), x = p = s = 0
   if (tid == 0) s_late = 0;
   bool broken = false;
-  // a thread per row, the rows packed into as few warps as possible: an FP64
-  // warp instruction costs the FP64 pipe the same however many lanes are active
-  for (int a = tid; a < nr; a += kPcgThreads) {
-    const int j = t + Gs * a;
-    Real* mi = sMi + 21 * a;
-    if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, mi)) {
-      atomicOr(d.status, kStatusBreakdown);
-      broken = true;
+  // a thread per row (M⁻¹ from the preconditioner launch); the other warps
+  // stage the matrix entries meanwhile
+  const int inv_warps = min(kPcgWarps - 1, (rows_cap + 31) >> 5);
+  if (warp < inv_warps) {
+    for (int a = tid; a < nr; a += inv_warps * 32) {
+      const int j = t + Gs * a;
+      Real* mi = sMi + 21 * a;
+      const Real* src = d.minv + 21 * (size_t)j;
 #pragma unroll
-      for (int k = 0; k < 21; ++k) mi[k] = 0;
+      for (int k = 0; k < 21; ++k) mi[k] = __ldg(src + k);
+      if (mi[0] != mi[0]) {   // not positive definite (flagged by the preconditioner launch)
+        broken = true;
+#pragma unroll
+        for (int k = 0; k < 21; ++k) mi[k] = 0;
+      }
+      Real r[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) r[c] = -d.g[6 * j + c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        Real u = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) u += mi[sym(c, k)] * r[k];
+        V(kGr, a)[c] = r[c];
+        V(kGu, a)[c] = u;
+        V(kGx, a)[c] = 0;
+        V(kGp, a)[c] = 0;
+        V(kGs, a)[c] = 0;
+        put_tagged(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
+      }
     }
-    Real r[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) r[c] = -d.g[6 * j + c];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      Real u = 0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) u += mi[sym(c, k)] * r[k];
-      V(kGr, a)[c] = r[c];
-      V(kGu, a)[c] = u;
-      V(kGx, a)[c] = 0;
-      V(kGp, a)[c] = 0;
-      V(kGs, a)[c] = 0;
-      put_tagged(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
-    }
+  } else if constexpr (kStaged) {
+    stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff, inv_warps);
   }
-  if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff);
   if (tid == 0) {
     sc.alpha = 0; sc.beta = 0; sc.rz = O::zero(); sc.bad = 0; sc.work = 1;
     s_gprev = O::zero(); s_aprev = 1.f;
@@ -770,7 +853,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
 
   for (int k = 0; k <= K; ++k) {
     // ---- w = A u (u of iteration k, from the rows' owners) and the shares of γ = (r, u), δ = (w, u)
-    const bool last = k == K;   // the final reduction only measures γ for the statistics
+    const bool last = k == K;   // the final pass only measures γ for the statistics
     const unsigned tu = (unsigned)(base + 1 + k);
     const unsigned long long* ucur = ub[k & 1];
     Acc pg = carry, pd = O::zero();
@@ -859,12 +942,14 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
       s_late = 1;
       pg = acc_nan<Acc>();
     }
+    if (last) {
+      // the final γ is only a statistic: each CTA adds its share with one
+      // FP64 atomic and nobody waits (the order of the additions varies)
+      block_add_value(pg, 8, d.pcg_rz + gn_it);
+      break;
+    }
     // ---- one reduction: γ and δ together
     if (!stream_reduce_pair(pg, pd, k == 0 ? 32 : 8, d.part, t, Gs, base + 1 + k, spin_limit, [&](Acc g, Acc dl) {
-          if (last) {
-            if (t == 0) d.pcg_rz[gn_it] = O::value(g);
-            return;
-          }
           if (!sc.work) return;
           if (acc_is_nan(g) || acc_is_nan(dl)) {
             sc.bad = 1; sc.work = 0;
@@ -907,7 +992,6 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
       atomicOr(d.status, kStatusTimeout);
       return;
     }
-    if (last) break;
     // ---- p = u + β p, s = w + β s, x += α p, r −= α s, then u = M⁻¹ r (published)
     if (sc.work) {
       const Real alpha = sc.alpha, beta = sc.beta;
@@ -994,6 +1078,41 @@ __global__ void k_barrier_probe(GridBarrier* gb, unsigned expected, int spin_lim
   }
 }
 
+// The block-Jacobi preconditioner, one thread per node of every active
+// stream, launched between the assembly and the PCG: its own launch gives the
+// FP64 inverse the registers that the 1024-thread PCG cannot, and spreads the
+// FP64 work (the slow pipe on this part) over many SMs, kPrecondTile nodes
+// per CTA.  M⁻¹_j, packed
+// lower, to minv (FP32 modes) or minv64 (FP64 mode).  A diagonal block that
+// is not positive definite sets kStatusBreakdown and leaves a NaN in its
+// first entry, which the PCG turns into a breakdown of the whole solve.
+template <typename Real>
+__global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kPrecondTile + threadIdx.x;
+  if (j >= d.n_n) return;
+  const Real* A;
+  Real* out;
+  if constexpr (std::is_same<Real, double>::value) {
+    A = d.A64; out = d.minv64 + 21 * (size_t)j;
+  } else {
+    A = d.A; out = d.minv + 21 * (size_t)j;
+  }
+  if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, out)) {
+    atomicOr(d.status, kStatusBreakdown);
+    out[0] = (Real)__longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// the preconditioner's block inverse alone, one thread per block (stage checks)
+template <typename Real>
+__global__ void k_debug_block_inverse(const Real* blocks, int n, Real* out, int* ok) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ok[i] = block_inverse(blocks + (size_t)i * 36, out + (size_t)i * 21) ? 1 : 0;
+}
+
 template <typename Acc>
 const void* pcg_gear_fn(int mode) {
   switch (mode) {
@@ -1066,6 +1185,25 @@ cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+void launch_precond(const BatchHost& b, cudaStream_t st) {
+  const int nb = b.total_tiles[kTilePrecond];
+  if (nb == 0) return;
+  Batch bt = b.bt;
+  bt.tile_base = b.tile_base_dev[kTilePrecond];
+  if (b.precision == SW_PRECISION_FP64) k_precond<double><<<nb, kPrecondTile, 0, st>>>(bt);
+  else k_precond<float><<<nb, kPrecondTile, 0, st>>>(bt);
+}
+
+cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void* out, int* ok, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (n + 127) / 128;
+  if (fp64)
+    k_debug_block_inverse<double><<<nb, 128, 0, st>>>(static_cast<const double*>(blocks), n, static_cast<double*>(out), ok);
+  else
+    k_debug_block_inverse<float><<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,

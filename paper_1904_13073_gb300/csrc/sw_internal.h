@@ -88,7 +88,7 @@ struct SwDev {
   float* A;           // nnzb * 36
   float* g;           // 6 n_n
   // PCG
-  float* Li;          // n_n * 21: inverse Cholesky factor of each diagonal block, packed lower
+  float* minv;        // n_n * 21: block-Jacobi preconditioner, inverse of each diagonal block, packed lower
   float* x; float* r; float* z; float* p0; float* p1; float* q;
   struct PartSlot* part;   // 4 * kMaxCtaPerStream slots for the per-CTA partials of the PCG's reductions
   unsigned long long* xz;  // 6 n_n tagged words: z as other CTAs of the PCG read it
@@ -98,6 +98,7 @@ struct SwDev {
   // vectors (u, m even, m odd) and the authoritative node transforms
   double* A64;        // nnzb * 36
   double* g64;        // 6 n_n
+  double* minv64;     // n_n * 21, the preconditioner in the FP64 mode
   double* v64;        // 3 * 6 n_n
   double* dq64;       // 8 per node
   // rigid pre-alignment
@@ -140,7 +141,8 @@ struct GridBarrier {   // counter barrier used by the timeout probe
 
 // ------------------------------------------------------------------ launchers
 
-enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTileKinds };
+enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTilePrecond,
+                kTileKinds };
 
 struct BatchHost {
   Batch bt;
@@ -161,6 +163,8 @@ void launch_node_graph(const SwDev& d, cudaStream_t st);
 void launch_solve_begin(const BatchHost& b, cudaStream_t st);
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
+// the block-Jacobi preconditioner of every active stream (inverse of each diagonal block)
+void launch_precond(const BatchHost& b, cudaStream_t st);
 cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
 void launch_reg_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
@@ -181,6 +185,8 @@ size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
 // Wait for a batch's work and turn each member's device status word into
 // its sw_status (SW_OK for inactive members); `status` has one entry per member.
 sw_status batch_member_status(sw_batch_handle b, int* status);
+// the PCG's 6x6 block inverse on n row-major blocks (float, or double with fp64), packed lower out
+cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void* out, int* ok, cudaStream_t st);
 cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
                                  int* status, cudaStream_t st);
 
@@ -282,6 +288,9 @@ cudaError_t launch_pattern_fill(const int4* sets, int n_sets, const int* graph, 
 constexpr int kSurfTile = 256;
 constexpr int kAsmTile = 256;
 constexpr int kBlkTile = 128;
+// nodes per CTA of the preconditioner launch: few, so that its FP64 work
+// spreads over as many SMs as possible
+constexpr int kPrecondTile = 16;
 
 inline int tiles_for(int kind, const SwDev& d) {
   switch (kind) {
@@ -291,6 +300,7 @@ inline int tiles_for(int kind, const SwDev& d) {
     case kTileBlocks: return (d.nnzb + kBlkTile - 1) / kBlkTile;
     case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
     case kTileNodes: return (d.n_n + kBlkTile - 1) / kBlkTile;
+    case kTilePrecond: return (d.n_n + kPrecondTile - 1) / kPrecondTile;
   }
   return 0;
 }
