@@ -138,10 +138,11 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# ncu capture of this workload's kernels as they are now;
+# ncu capture of this workload's kernels as they are now (the "pcg" stage is
+# the preconditioner launch plus the PCG launch);
 # profiles/k_pcg_gear_plain_full_300k_2048.md and
 # profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": None, "data_assembly": 25.230848e6 + 0.028416e6}
+PROFILED_TRAFFIC = {"pcg": 0.566272e6 + 3.071744e6 + 0.00384e6, "data_assembly": 25.230848e6 + 0.028416e6}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
