@@ -43,7 +43,8 @@ extern "C" {
  *   SW_PRECISION_MIXED         residuals, Jacobians, JᵀJ, SpMV and vectors in
  *                              FP32; PCG inner products accumulated in
  *                              double-float pairs (about 48 significant bits);
- *                              6x6 block inverses by FP64 Cholesky.
+ *                              6x6 block inverses (the block-Jacobi
+ *                              preconditioner) by LDLᵀ in FP64.
  *   SW_PRECISION_FP64          the whole solve in FP64: node transforms, warp,
  *                              residuals, Jacobians, JᵀJ, PCG (the association
  *                              still decided in FP32 from the FP64 warp).
