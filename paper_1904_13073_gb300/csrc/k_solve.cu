@@ -176,7 +176,11 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
 // ------------------------------------------------------------------ K4+K5: data term
 
 constexpr int kJS = 25;   // 24 Jacobian entries + residual per term
-constexpr int kAsmChunks = kAsmTile / 14;                        // 18 chunks x 14 outputs = 252 threads
+// chunks of terms per output: 9 x 14 outputs = 126 threads.  Every chunk
+// flushes at least once (9 or 36 floats by vector atomics), and the atomics
+// cost more than the products: measured on the full-size frame, 18 chunks
+// 39.5 us, 12 36.8, 9 35.8, 6 36.2, 5 37.5 per launch
+constexpr int kAsmChunks = 9;
 
 __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_it, int write_live) {
   const int s = find_stream(bt, blockIdx.x);
