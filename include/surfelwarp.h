@@ -495,8 +495,10 @@ sw_status sw_debug_read_append(sw_handle h, int* pix, int* knn4, int* flags, dou
  * timing the persistent launch on the stream's (or the batch members')
  * current system.  Needs a model and a depth frame on every stream; the
  * node transforms are restored afterwards and a batch's members are all made
- * active.  *rows_per_cta and *pcg_us (nullable) receive the choice and its
- * time per launch in microseconds.  The choice stays with the stream (or
+ * active.  Each candidate's launch is timed twelve times (two sweeps of six)
+ * and its fastest launch counts.  *rows_per_cta and *pcg_us (nullable)
+ * receive the choice and its time per launch in microseconds (that fastest
+ * launch).  The choice stays with the stream (or
  * the batch) until the next autotune call.
  * ------------------------------------------------------------------------- */
 sw_status sw_autotune(sw_handle h, int pcg_iters, int* rows_per_cta, double* pcg_us);

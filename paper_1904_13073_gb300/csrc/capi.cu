@@ -697,8 +697,9 @@ __global__ void k_set_frames(Batch bt, const int* __restrict__ frames) {
 // persistent launch on the members' current systems: for each candidate the
 // runner is rebuilt (CTA allocation and SpMV staging follow), the system is
 // assembled again (which also starts a new PCG epoch) and the PCG launch
-// alone is timed with events, three times after one untimed launch.  The
-// node transforms are saved before and restored after every candidate, so
+// alone is timed with events, six times after one untimed launch, in two
+// sweeps over the candidates; the fastest launch is a candidate's figure.
+// The node transforms are saved before and restored after every candidate, so
 // the call leaves the streams' state as it found it.  Every member is made
 // active.
 sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows, double* best_us) {
@@ -729,31 +730,40 @@ sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows,
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // two sweeps over the candidates, each timing a candidate's launch six
+  // times after one untimed launch; a candidate's figure is its fastest
+  // launch, which is robust to the run-to-run spread of the launches'
+  // synchronisation waits
+  constexpr int kSweeps = 2, kTimed = 6;
+  const int n_cand = (int)(sizeof(kCand) / sizeof(kCand[0]));
+  std::vector<double> cand_t(n_cand, 1e30);
+  for (int sweep = 0; sweep < kSweeps; ++sweep)
+    for (int c = 0; c < n_cand; ++c) {
+      r->pcg_rows_per_cta = kCand[c];
+      if (build_runner(r, nullptr) != SW_OK) continue;   // does not fit on chip: skip
+      launch_solve_begin(r->bh, st);
+      bool ok = true;
+      for (int rep = 0; rep <= kTimed && ok; ++rep) {
+        launch_reg_stage(r->bh, 0, st);
+        launch_data_stage(r->bh, 0, st);
+        launch_precond(r->bh, st);
+        cudaEventRecord(e0, st);
+        ok = launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
+        cudaEventRecord(e1, st);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) cand_t[c] = std::min(cand_t[c], (double)ms);
+      }
+      ok = ok && restore() == cudaSuccess;
+      if (!ok) cand_t[c] = 1e30;
+    }
   int best = r->pcg_rows_per_cta;
   double best_t = 1e30;
-  for (int rows : kCand) {
-    r->pcg_rows_per_cta = rows;
-    if (build_runner(r, nullptr) != SW_OK) continue;   // does not fit on chip: skip
-    launch_solve_begin(r->bh, st);
-    double sum = 0.0;
-    bool ok = true;
-    for (int rep = 0; rep < 4 && ok; ++rep) {
-      launch_reg_stage(r->bh, 0, st);
-      launch_data_stage(r->bh, 0, st);
-      launch_precond(r->bh, st);
-      cudaEventRecord(e0, st);
-      ok = launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
-      cudaEventRecord(e1, st);
-      ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
-      float ms = 0.f;
-      if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) sum += ms;
+  for (int c = 0; c < n_cand; ++c)
+    if (cand_t[c] < best_t) {
+      best_t = cand_t[c];
+      best = kCand[c];
     }
-    ok = ok && restore() == cudaSuccess;
-    if (ok && sum / 3.0 < best_t) {
-      best_t = sum / 3.0;
-      best = rows;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   r->pcg_rows_per_cta = best;

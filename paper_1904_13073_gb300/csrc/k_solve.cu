@@ -1,10 +1,11 @@
 // K4-K6: the assembly half of one Gauss-Newton iteration of the non-rigid
 // solve (Sec. 7-8).
 //
-//   K6 k_reg_assemble   one thread per upper 6x6 block of JᵀJ: writes the
-//                       as-rigid-as-possible part (Eq. 11) of that block, and
-//                       of Jᵀe on diagonal blocks, with plain stores.  It runs
-//                       first and so also initialises the whole system.
+//   K6 k_reg_assemble   the as-rigid-as-possible part (Eq. 11) of every
+//                       upper 6x6 block of JᵀJ and of Jᵀe, with plain stores:
+//                       8 lanes per node for the diagonal blocks and Jᵀe, one
+//                       thread per off-diagonal block.  It runs first and so
+//                       also initialises the whole system.
 //   K4+K5 k_data_assemble  one thread per surfel: dual-quaternion blend and
 //                       forward warp (Eq. 1-2), projective association,
 //                       point-to-plane residual (Eq. 10) and its 1x24
@@ -88,6 +89,17 @@ __global__ void k_solve_begin(Batch bt) {
   if (threadIdx.x == 0) *d.status = 0;
 }
 
+// Threads [0, n8), n8 = 8 n_n rounded up to a whole warp: a group of 8
+// lanes per node j writes the diagonal block (j, j) and the Jᵀe segment of
+// j (the groups past the last node only join the shuffles, which need whole
+// warps).  Every edge adds the same form to
+// the diagonal block: for the point y = T_j p (p_j on an out-edge, p_m on an
+// in-edge) the block of [−[y]×|I]ᵀ[−[y]×|I] is [[|y|²I − y yᵀ, [y]×],
+// [−[y]×, I]], so the block needs only the edges' count, Σy and Σ y yᵀ; the
+// out-edges all share y = T_j p_j.  Lane q of the group takes out-edge q and
+// the in-edges q, q + 8, ...; the group sums its lanes' shares by shuffles.
+// Threads [n8, n8 + nnzb): one per block; the off-diagonal ones write their
+// block (zero unless a graph edge joins its two nodes).
 __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) {
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
@@ -95,68 +107,82 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
   const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
   // a new epoch for the generation stamps of the PCG launch that follows
   if (b == 0) *d.pcg_epoch += 1;
+  const float sl = d.sqrt_lambda, l = sl * sl;
+  const int n8 = reg_diag_threads(d.n_n);   // a multiple of 32: no warp straddles the two parts
   float ereg = 0.f;
-  if (b < d.nnzb) {
-    const int i = d.blk_row[b], j = d.col[b];
-    const float sl = d.sqrt_lambda, l = sl * sl;
-    float acc[36];
+  if (b < n8) {
+    const int j = b >> 3, q = b & 7;
+    const bool on = j < d.n_n;
+    float3 x = make_float3(0.f, 0.f, 0.f);
+    // [gj (6), Σy (3), Σyyᵀ (xx xy xz yy yz zz), in-edge count]
+    float v[16];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-    if (i == j) {
-      // Every edge adds the same form to the diagonal block: for the point
-      // y = T_j p (p_j on an out-edge, p_m on an in-edge) the block of
-      // [−[y]×|I]ᵀ[−[y]×|I] is [[|y|²I − y yᵀ, [y]×], [−[y]×, I]], so the
-      // block needs only the edges' count, Σy and Σ y yᵀ; the out-edges all
-      // share y = T_j p_j.
-      float gj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float sy[3] = {0.f, 0.f, 0.f}, syy[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // xx xy xz yy yz zz
+    for (int k = 0; k < 16; ++k) v[k] = 0.f;
+    static_assert(SW_K_GRAPH == 8, "one out-edge per lane of the group");
+    if (on) {   // out-edge j -> m
       const float3 pj = f3(d.node_p[j]);
-      const float3 x = node_apply(d, j, pj);
-      for (int e = 0; e < SW_K_GRAPH; ++e) {      // out-edges j -> m
-        const int m = d.graph[j * SW_K_GRAPH + e];
-        const float3 y = node_apply(d, m, pj);
-        const float3 r = sl * (x - y);
-        ereg += dot3(r, r);
-        const float3 xr = cross3(x, r);
-        gj[0] += sl * xr.x; gj[1] += sl * xr.y; gj[2] += sl * xr.z;
-        gj[3] += sl * r.x; gj[4] += sl * r.y; gj[5] += sl * r.z;
-      }
+      x = node_apply(d, j, pj);
+      const int m = d.graph[j * SW_K_GRAPH + q];
+      const float3 y = node_apply(d, m, pj);
+      const float3 r = sl * (x - y);
+      ereg += dot3(r, r);
+      const float3 xr = cross3(x, r);
+      v[0] += sl * xr.x; v[1] += sl * xr.y; v[2] += sl * xr.z;
+      v[3] += sl * r.x; v[4] += sl * r.y; v[5] += sl * r.z;
+    }
+    const int e1 = on ? d.in_ptr[j + 1] : 0;
+    for (int e = (on ? d.in_ptr[j] : 0) + q; e < e1; e += 8) {   // in-edges m -> j
+      const int m = d.in_src[e];
+      const float3 pm = f3(d.node_p[m]);
+      const float3 y = node_apply(d, j, pm);
+      const float3 r = sl * (node_apply(d, m, pm) - y);
+      v[6] += y.x; v[7] += y.y; v[8] += y.z;
+      v[9] += y.x * y.x; v[10] += y.x * y.y; v[11] += y.x * y.z;
+      v[12] += y.y * y.y; v[13] += y.y * y.z; v[14] += y.z * y.z;
+      v[15] += 1.f;
+      const float3 yr = cross3(y, r);
+      v[0] -= sl * yr.x; v[1] -= sl * yr.y; v[2] -= sl * yr.z;
+      v[3] -= sl * r.x; v[4] -= sl * r.y; v[5] -= sl * r.z;
+    }
+    // the group's sums (its 8 lanes are aligned within the warp, and every
+    // lane of the warp is here)
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (on && q == 0) {
       const float ko = (float)SW_K_GRAPH;
-      sy[0] = ko * x.x; sy[1] = ko * x.y; sy[2] = ko * x.z;
-      syy[0] = ko * x.x * x.x; syy[1] = ko * x.x * x.y; syy[2] = ko * x.x * x.z;
-      syy[3] = ko * x.y * x.y; syy[4] = ko * x.y * x.z; syy[5] = ko * x.z * x.z;
-      float cnt = ko;
-      for (int e = d.in_ptr[j]; e < d.in_ptr[j + 1]; ++e) {   // in-edges m -> j
-        const int m = d.in_src[e];
-        const float3 pm = f3(d.node_p[m]);
-        const float3 y = node_apply(d, j, pm);
-        const float3 r = sl * (node_apply(d, m, pm) - y);
-        cnt += 1.f;
-        sy[0] += y.x; sy[1] += y.y; sy[2] += y.z;
-        syy[0] += y.x * y.x; syy[1] += y.x * y.y; syy[2] += y.x * y.z;
-        syy[3] += y.y * y.y; syy[4] += y.y * y.z; syy[5] += y.z * y.z;
-        const float3 yr = cross3(y, r);
-        gj[0] -= sl * yr.x; gj[1] -= sl * yr.y; gj[2] -= sl * yr.z;
-        gj[3] -= sl * r.x; gj[4] -= sl * r.y; gj[5] -= sl * r.z;
-      }
-      {
-        const float S[9] = {syy[0], syy[1], syy[2], syy[1], syy[3], syy[4], syy[2], syy[4], syy[5]};
-        const float tr = syy[0] + syy[3] + syy[5];
-        const float ax[9] = {0.f, -sy[2], sy[1], sy[2], 0.f, -sy[0], -sy[1], sy[0], 0.f};
+      const float cnt = ko + v[15];
+      const float sy[3] = {ko * x.x + v[6], ko * x.y + v[7], ko * x.z + v[8]};
+      const float S[9] = {ko * x.x * x.x + v[9],  ko * x.x * x.y + v[10], ko * x.x * x.z + v[11],
+                          ko * x.x * x.y + v[10], ko * x.y * x.y + v[12], ko * x.y * x.z + v[13],
+                          ko * x.x * x.z + v[11], ko * x.y * x.z + v[13], ko * x.z * x.z + v[14]};
+      const float tr = S[0] + S[4] + S[8];
+      const float ax[9] = {0.f, -sy[2], sy[1], sy[2], 0.f, -sy[0], -sy[1], sy[0], 0.f};
+      float acc[36];
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+      for (int p = 0; p < 3; ++p)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            acc[p * 6 + q] = l * ((p == q ? tr : 0.f) - S[p * 3 + q]);
-            acc[p * 6 + 3 + q] = l * ax[p * 3 + q];
-            acc[(3 + p) * 6 + q] = -l * ax[p * 3 + q];
-            acc[(3 + p) * 6 + 3 + q] = p == q ? l * cnt : 0.f;
-          }
-      }
+        for (int c = 0; c < 3; ++c) {
+          acc[p * 6 + c] = l * ((p == c ? tr : 0.f) - S[p * 3 + c]);
+          acc[p * 6 + 3 + c] = l * ax[p * 3 + c];
+          acc[(3 + p) * 6 + c] = -l * ax[p * 3 + c];
+          acc[(3 + p) * 6 + 3 + c] = p == c ? l * cnt : 0.f;
+        }
+      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)d.row_ptr[j] * 36);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) d.g[6 * j + k] = gj[k];
-    } else {
-      const int fl = d.blk_edge[b];
+      for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d.g[6 * j + k] = v[k];
+    }
+  } else if (b - n8 < d.nnzb) {
+    const int bi = b - n8;
+    const int i = d.blk_row[bi], j = d.col[bi];
+    if (i != j) {
+      float acc[36];
+#pragma unroll
+      for (int k = 0; k < 36; ++k) acc[k] = 0.f;
+      const int fl = d.blk_edge[bi];
       if (fl & 1) {   // edge i -> j: J_i = sl[−[T_i p_i]×|I], J_j = −sl[−[T_j p_i]×|I]
         const float3 pi = f3(d.node_p[i]);
         add_reg_pair(acc, -l, node_apply(d, i, pi), node_apply(d, j, pi));
@@ -165,10 +191,10 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
         const float3 pj = f3(d.node_p[j]);
         add_reg_pair(acc, -l, node_apply(d, i, pj), node_apply(d, j, pj));
       }
-    }
-    float4* dst = reinterpret_cast<float4*>(d.A + (size_t)b * 36);
+      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)bi * 36);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+      for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    }
   }
   block_atomic_sum<double>((double)ereg, d.e_reg + gn_it);
 }
@@ -364,7 +390,8 @@ void launch_solve_begin(const BatchHost& b, cudaStream_t st) {
   if (b.bt.n_streams) k_solve_begin<<<b.bt.n_streams, 32, 0, st>>>(b.bt);
 }
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
-  if (b.total_tiles[kTileBlocks]) k_reg_assemble<<<b.total_tiles[kTileBlocks], kBlkTile, 0, st>>>(with_kind(b, kTileBlocks), gn_it);
+  if (b.total_tiles[kTileRegAssembly])
+    k_reg_assemble<<<b.total_tiles[kTileRegAssembly], kBlkTile, 0, st>>>(with_kind(b, kTileRegAssembly), gn_it);
 }
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileSurfelsAssembly])

@@ -142,7 +142,7 @@ struct GridBarrier {   // counter barrier used by the timeout probe
 // ------------------------------------------------------------------ launchers
 
 enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTilePrecond,
-                kTileKinds };
+                kTileRegAssembly, kTileKinds };
 
 struct BatchHost {
   Batch bt;
@@ -292,6 +292,10 @@ constexpr int kBlkTile = 128;
 // spreads over as many SMs as possible
 constexpr int kPrecondTile = 16;
 
+// threads of the regulariser assembly's diagonal part: 8 per node, rounded
+// up to a whole warp
+__host__ __device__ inline int reg_diag_threads(int n_n) { return (8 * n_n + 31) & ~31; }
+
 inline int tiles_for(int kind, const SwDev& d) {
   switch (kind) {
     case kTilePixels: return ((d.W + 31) / 32) * ((d.H + 7) / 8);   // 32x8 pixel tiles
@@ -301,6 +305,7 @@ inline int tiles_for(int kind, const SwDev& d) {
     case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
     case kTileNodes: return (d.n_n + kBlkTile - 1) / kBlkTile;
     case kTilePrecond: return (d.n_n + kPrecondTile - 1) / kPrecondTile;
+    case kTileRegAssembly: return (reg_diag_threads(d.n_n) + d.nnzb + kBlkTile - 1) / kBlkTile;   // 8 lanes per node, then a thread per block
   }
   return 0;
 }
