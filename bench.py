@@ -415,8 +415,9 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
             sw.sw_solve_frame(hd, gn, pcg, want_stats=False)
             sw.sw_fuse_frame(hd)
 
-    # round 0 is played untimed by both runs (the batched run tunes its PCG
-    # on it; the autotune leaves the state as it found it); rounds 1.. are timed
+    # frame round 0 (one frame of every stream) is played untimed by both
+    # runs (the batched run tunes its PCG on it; the autotune leaves the
+    # state as it found it); frame rounds 1.. are timed
     reset_models()
     plain_round(0)
     lat_plain = timed(lambda r: plain_round(r + 1), rounds, warmup)
