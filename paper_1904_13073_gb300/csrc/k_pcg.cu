@@ -1,6 +1,8 @@
 // K7+K8: block-Jacobi preconditioned conjugate gradients on JᵀJ Δ = −Jᵀe
 // and the node update T_j ← Δ_j T_j (Sec. 7), one persistent cooperative
-// launch per Gauss-Newton iteration for every stream of a batch.
+// launch per Gauss-Newton iteration for every stream of a batch, after the
+// preconditioner's own launch (k_precond: the FP64 inverse of every
+// diagonal block).
 //
 // Both kernels run x₀ = 0 and exactly K iterations, stopping early only when
 // rᵀM⁻¹r is exactly zero; pᵀAp <= 0 (or a diagonal block that is not
@@ -10,7 +12,7 @@
 // Work split.  Stream s owns the CTAs [tile_base[s], tile_base[s+1]), all
 // co-resident.  CTA t of a stream with G CTAs owns the block rows and nodes
 // i = t + G a (a = 0, 1, ...) and keeps everything about them in shared
-// memory for the whole solve: the 6x6 block of M⁻¹ (FP64 Cholesky) and the
+// memory for the whole solve: the 6x6 block of M⁻¹ (from k_precond) and the
 // rows' vectors.  Global memory carries only the vector other CTAs read for
 // the SpMV.  The reductions are per stream, so streams never wait for one
 // another.
