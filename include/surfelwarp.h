@@ -279,8 +279,8 @@ sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out);
 
 /* Test hook for the block-Jacobi preconditioner (Sec. 7): the inverse of
  * each of n symmetric 6x6 blocks (host, row-major, 36 values each; float, or
- * double when fp64 is nonzero) as the PCG forms it -- the two triangles
- * averaged, then an LDLᵀ factorisation in FP64 -- written to inv21 (host,
+ * double when fp64 is nonzero) as the PCG forms it -- from its lower
+ * triangle, by an LDLᵀ factorisation in FP64 -- written to inv21 (host,
  * 21 values per block, packed lower triangle row by row: (0,0) (1,0) (1,1)
  * (2,0) ...), same element type.  ok[i] (host) is 1, or 0 when block i is not
  * positive definite (its inv21 entries are then unspecified).  Needs a GPU;

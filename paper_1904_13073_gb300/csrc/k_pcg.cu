@@ -96,43 +96,48 @@ __device__ __forceinline__ float ratio_f32(double a, double b) {
 __device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }   // packed, r >= c
 __device__ __forceinline__ int sym(int r, int c) { return r >= c ? tri(r, c) : tri(c, r); }
 
-// 1/x for a positive FP64 x: the FP32 reciprocal as the seed, refined by two
-// Newton-Raphson steps r <- r + r (1 - x r), each of which about doubles the
-// number of correct bits (24 -> 48 -> the FP64 rounding limit).  A division
-// in FP64 is a chain of several hundred cycles on this part; this is ~6
-// dependent FP64 operations.  Outside the range where the FP32 seed is
-// accurate, the plain division.
+// 1/x for a positive FP64 x: the FP32 reciprocal as the seed, refined by
+// kSteps Newton-Raphson steps r <- r + r (1 - x r), each of which about
+// doubles the number of correct bits (24 -> 46 -> the FP64 rounding limit).
+// A division in FP64 is a chain of several hundred cycles on this part; this
+// is 2 + 2 kSteps dependent FP64 operations.  Outside the range where the
+// FP32 seed is accurate, the plain division.
+template <int kSteps>
 __device__ __forceinline__ double recip64(double x) {
   const float xf = (float)x;
   if (!(xf >= 1e-30f && xf <= 1e30f)) return 1.0 / x;
   double r = (double)__frcp_rn(xf);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+#pragma unroll
+  for (int k = 0; k < kSteps; ++k) {
+    const double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+  }
+  return r;
 }
 
 __device__ __forceinline__ int sl(int r, int c) { return r * (r - 1) / 2 + c; }   // strict lower, r > c
 
 // M⁻¹ of one diagonal block (symmetric, packed lower) in FP64 by the
-// factorisation A = L D Lᵀ (L unit lower triangular): M⁻¹ = L⁻ᵀ D⁻¹ L⁻¹.
-// The block's two triangles are averaged first.  No square roots, and the
-// six pivots' reciprocals by recip64, so the dependent chain is short.
-// False if the block is not positive definite (a pivot <= 0).
+// factorisation A = L D Lᵀ (L unit lower triangular): M⁻¹ = L⁻ᵀ D⁻¹ L⁻¹,
+// from the block's lower triangle (the assembly writes the upper one equal
+// up to the rounding order of its atomics).  No square roots, and the six
+// pivots' reciprocals by recip64 -- one Newton step for an FP32 result (about
+// 46 correct bits), two for an FP64 one -- so the dependent chain, and the
+// FP64 instruction stream that bounds a warp here, stay short.  False if the
+// block is not positive definite (a pivot <= 0).
 template <typename Real>
 __device__ bool block_inverse(const Real* a, Real* out) {
   // every loop has a constant trip count (bounds as predicates), so that all
   // of them unroll and the arrays live in registers.
-  // S: the averaged block (packed lower); its strict lower part is then
+  // S: the lower triangle (packed); its strict lower part is then
   // overwritten by E = L D (E_rc = L_rc d_c) and finally by Y = D⁻¹ L⁻¹
+  constexpr int kSteps = std::is_same<Real, float>::value ? 1 : 2;
   double S[21], L[15], Di[6];
 #pragma unroll
   for (int r = 0; r < 6; ++r)
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      if (c < r) S[tri(r, c)] = 0.5 * ((double)a[r * 6 + c] + (double)a[c * 6 + r]);
-      if (c == r) S[tri(r, r)] = (double)a[r * 6 + r];
-    }
+    for (int c = 0; c < 6; ++c)
+      if (c <= r) S[tri(r, c)] = (double)a[r * 6 + c];
   // column by column: d_c = a_cc − Σ_{k<c} L_ck E_ck, E_rc = a_rc − Σ_{k<c} L_rk E_ck, L_rc = E_rc / d_c
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -141,7 +146,7 @@ __device__ bool block_inverse(const Real* a, Real* out) {
     for (int k = 0; k < 6; ++k)
       if (k < c) dc = fma(-L[sl(c, k)], S[tri(c, k)], dc);
     if (!(dc > 0.0)) return false;
-    Di[c] = recip64(dc);
+    Di[c] = recip64<kSteps>(dc);
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
       if (r <= c) continue;

@@ -1,9 +1,10 @@
 """The block-Jacobi preconditioner's 6x6 inverse (Sec. 7) as the PCG forms
-it on the device -- triangles averaged, LDLᵀ in FP64 with Newton-refined
-pivot reciprocals -- against the FP64 inverse from LAPACK, over conditioning
-from 1 to 1e6, magnitudes from 1e-33 to 1e6 (the smallest below the range
-where the reciprocal's FP32 seed is used), slightly asymmetric input, and
-blocks that are not positive definite."""
+it on the device -- from the block's lower triangle, LDLᵀ in FP64 with
+Newton-refined pivot reciprocals -- against the FP64 inverse from LAPACK,
+over conditioning from 1 to 1e6, magnitudes from 1e-33 to 1e6 (the smallest
+below the range where the reciprocal's FP32 seed is used), an upper triangle
+that differs from the lower one, and blocks that are not positive
+definite."""
 import numpy as np
 import pytest
 
@@ -48,19 +49,19 @@ def test_block_inverse_matches_lapack(fp64):
     B, conds = _blocks(rng)
     dt = np.float64 if fp64 else np.float32
     Bd = B.astype(dt)
-    # one triangle off by a few ulps: the device averages the two
-    Bd[::3, 4, 1] = np.nextafter(np.nextafter(Bd[::3, 4, 1], np.inf), np.inf)
+    # the upper triangle off by a few ulps: the device reads the lower one
+    Bd[::3, 1, 4] = np.nextafter(np.nextafter(Bd[::3, 1, 4], np.inf), np.inf)
     inv, ok = sw.sw_debug_block_inverse(Bd, fp64=fp64)
     assert ok.all()
     for k in range(len(Bd)):
-        S = Bd[k].astype(np.float64)
-        S = 0.5 * (S + S.T)
+        S = np.tril(Bd[k].astype(np.float64))
+        S = S + np.tril(S, -1).T
         want = _packed(np.linalg.inv(S))
         got = inv[k].astype(np.float64)
         big = np.abs(want).max()
         if fp64:
             tol = 1e-13 * conds[k] * big
-        else:   # the FP64 result rounded to FP32: one rounding, plus FP64 error far below it
+        else:   # the FP32 result: one rounding, plus an error far below it (46-bit reciprocals)
             tol = np.spacing(np.abs(want).astype(np.float32)).astype(np.float64) + 1e-12 * conds[k] * big
         assert np.all(np.abs(got - want) <= tol), (k, conds[k], np.abs(got - want).max(), big)
 
