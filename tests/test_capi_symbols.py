@@ -73,3 +73,14 @@ def test_appending_and_visibility_parameters_are_checked_on_the_host(built):
         with pytest.raises(sw.SwError) as e:
             sw.sw_create_stream(bad)
         assert e.value.status == 1 and word in str(e.value), (field, str(e.value))
+
+
+def test_block_inverse_hook_checks_its_arguments_on_the_host(built):
+    """Zero blocks is a no-op and a negative count or a missing array is
+    refused, both before any device work."""
+    import ctypes
+    lib = sw.lib()
+    ok = (ctypes.c_int * 1)()
+    assert lib.sw_debug_block_inverse(None, 0, 0, None, None) == 0
+    assert lib.sw_debug_block_inverse(None, -1, 0, None, ok) == 1
+    assert lib.sw_debug_block_inverse(None, 3, 1, None, ok) == 1
