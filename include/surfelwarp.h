@@ -450,13 +450,18 @@ sw_status sw_batch_rigid_align(sw_batch_handle b, int iters);
  * the nearest old node's σ apart from every node; each takes that σ and the
  * current warp at its position as its transform), the 8-NN graph is
  * recomputed and every surfel whose 4 nearest nodes now include a new node
- * is re-skinned.  The JᵀJ pattern, the runner and the solve graphs are
- * rebuilt (the call synchronises; its scratch and the model's arrays come
- * from a per-stream cache of device blocks that repeated calls reuse).  A
+ * is re-skinned.  The model's internal structure is then updated: when
+ * nothing was removed, no node was added and few surfels were placed since
+ * the last sort, the appended surfels follow the sorted ones and only new
+ * node sets are added (the JᵀJ pattern rebuilt only for node pairs it
+ * lacked); otherwise the surfels are re-sorted by node set and the pattern
+ * rebuilt.  Either way the runner and the solve graphs are re-described
+ * (the call synchronises; its scratch and the model's arrays come from a
+ * per-stream cache of device blocks that repeated calls reuse).  A
  * batch holding the stream rebuilds its tables at its next call (its active
- * flags are kept).  If the rebuild fails (SW_ERR_NO_MEMORY under the memory
- * budget, SW_ERR_CUDA), the stream has no model until the next sw_set_model
- * or sw_import_state.  *stats (nullable) receives
+ * flags are kept).  If the model update fails (SW_ERR_NO_MEMORY under the
+ * memory budget, SW_ERR_CUDA), by the fast update or the rebuild, the stream
+ * has no model until the next sw_set_model or sw_import_state.  *stats (nullable) receives
  * the counts.
  * ------------------------------------------------------------------------- */
 typedef struct {

@@ -1554,6 +1554,9 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       SW_CUDA(s, cudaStreamSynchronize(st));
       int n_sets_all = h.n_sets;
       bool new_pairs = false;
+      // from here the model changes: a failure leaves the stream without one
+      // (as a failed rebuild does) until the next sw_set_model or import
+      s->has_model = false;
       if (cnt[0] > 0) {
         // the new sets' slots go after the known sets' (the table grows if needed)
         SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&h.set_slots), (size_t)h.n_sets * 14 * sizeof(int),
@@ -1590,6 +1593,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
         launch_warp_live(s->run->bh, st);
         SW_CUDA(s, cudaGetLastError());
         SW_CUDA(s, cudaStreamSynchronize(st));
+        s->has_model = true;
         return finish(0);
       }
       // the pattern gains the new sets' node pairs: rebuilt from the set
@@ -1599,7 +1603,6 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       launch_slot_sets(h.set_slots, n_sets_all, all_sets.as<int4>(), st);
       SW_CUDA(s, cudaGetLastError());
       const int sorted_sets = s->sorted_sets;
-      s->has_model = false;
       recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A64});
       SW_TRY(install_pattern(s, all_sets.as<int4>(), n_sets_all, false));
       s->sorted_sets = sorted_sets;
