@@ -885,9 +885,8 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
   ALLOC(h.vis_map, np); ALLOC(h.visible, ns);
   ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.minv, 21 * nn);
-  ALLOC(h.x, 6 * nn); ALLOC(h.r, 6 * nn); ALLOC(h.z, 6 * nn); ALLOC(h.p0, 6 * nn); ALLOC(h.p1, 6 * nn);
-  ALLOC(h.q, 6 * nn); ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
-  ALLOC(h.xz, 6 * nn); ALLOC(h.xp, 12 * nn);
+  ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
+  ALLOC(h.xp, 12 * nn);
   ALLOC(h.rigid, kRigidSlots); ALLOC(h.rigid_stats, 2 * kMaxRigid);
   ALLOC(h.rigid_part, (size_t)kRigidSums * ((ns + kSurfTile - 1) / kSurfTile));
   if (p->precision == SW_PRECISION_FP64) {
@@ -914,7 +913,6 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   if (cudaMemsetAsync(h.status, 0, sizeof(int), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.t_now, 0, sizeof(int), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.part, 0, 4 * kMaxCtaPerStream * sizeof(PartSlot), s->st) != cudaSuccess ||
-      cudaMemsetAsync(h.xz, 0, 6 * nn * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.xp, 0, 12 * nn * sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.pcg_epoch, 0, sizeof(unsigned long long), s->st) != cudaSuccess ||
       cudaMemsetAsync(h.imap, 0xff, 16 * np * sizeof(unsigned long long), s->st) != cudaSuccess ||

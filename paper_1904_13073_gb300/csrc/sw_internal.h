@@ -89,10 +89,8 @@ struct SwDev {
   float* g;           // 6 n_n
   // PCG
   float* minv;        // n_n * 21: block-Jacobi preconditioner, inverse of each diagonal block, packed lower
-  float* x; float* r; float* z; float* p0; float* p1; float* q;
   struct PartSlot* part;   // 4 * kMaxCtaPerStream slots for the per-CTA partials of the PCG's reductions
-  unsigned long long* xz;  // 6 n_n tagged words: z as other CTAs of the PCG read it
-  unsigned long long* xp;  // 12 n_n tagged words: p, by iteration parity
+  unsigned long long* xp;  // 12 n_n tagged words: the PCG's u = M⁻¹ r as other CTAs read it, by iteration parity
   unsigned long long* pcg_epoch;   // launches of the persistent PCG so far
   // all-FP64 variant only (null otherwise): the system, the PCG's shared
   // vectors (u, m even, m odd) and the authoritative node transforms
