@@ -176,56 +176,119 @@ def oracle_stream(scene):
     return st
 
 
-def oracle_frame_seconds(st, frame, t, gn, pcg, gn_sample=1):
-    """Seconds of one oracle frame: depth processing and fusion timed whole,
-    ``gn_sample`` of the ``gn`` Gauss-Newton iterations timed and scaled."""
-    t0 = time.perf_counter()
-    st.upload_depth(frame, t)
-    t1 = time.perf_counter()
-    st.solve_frame(gn_sample, pcg)
-    t2 = time.perf_counter()
-    st.fuse_frame()
-    t3 = time.perf_counter()
-    return (t1 - t0) + (t2 - t1) * gn / gn_sample + (t3 - t2)
+def host_cpu():
+    """(CPU model, logical cores) of this host, for the baseline's record."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and not model:
+                model = line.split(":", 1)[1].strip()
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return model or "unknown", os.cpu_count() or 1
 
 
-def oracle_sample_text(gn, pcg):
-    return (f"per frame: depth processing and fusion timed whole, 1 of {gn} Gauss-Newton iterations "
-            f"(x {pcg} PCG) timed and scaled by {gn}; numpy FP64 oracle, 1 thread")
-
-
-def cpu_baseline_sample(scene, frame, gn, pcg):
-    """The FP64 oracle on a bounded sample of the same workload (one frame)."""
+def _oracle_replica(args):
+    """One replica stream of the oracle on the full-size workload: set-up
+    and `n_warm` whole frames untimed, then, once every replica is ready
+    (the barrier), `n_frames` whole frames (depth processing, 10
+    Gauss-Newton x 20 PCG iterations, fusion); returns their (start, end)
+    wall-clock times."""
+    seed, first_t, n_warm, n_frames, barrier = args
+    import synth
+    scene = synth.plain_full(seed=seed)
+    ts = [1 + (first_t + k) % (scene.n_frames - 1) for k in range(n_warm + n_frames)]
+    frames = [scene.frame(t) for t in ts]
     st = oracle_stream(scene)
-    sec = oracle_frame_seconds(st, frame, 1, gn, pcg)
-    return {"value": 1.0 / sec, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": oracle_sample_text(gn, pcg)}
+
+    def run(k):
+        st.upload_depth(frames[k], k + 1)
+        st.solve_frame(scene.gn_iters, scene.pcg_iters)
+        st.fuse_frame()
+    for k in range(n_warm):
+        run(k)
+    barrier.wait()
+    out = []
+    for k in range(n_warm, n_warm + n_frames):
+        t0 = time.time()
+        run(k)
+        out.append((t0, time.time()))
+    return out
+
+
+def oracle_whole_frames(n_frames, procs, n_warm=0):
+    """The FP64 oracle as it stands on the host cores: `procs` independent
+    replica streams (one single-threaded process each) share `n_frames`
+    whole frames of the full-size workload after `n_warm` untimed frames
+    each; the timed region runs from their common start to the last frame's
+    end.  Returns (frames/s over the region, seconds per frame of one
+    replica, region seconds, procs)."""
+    procs = max(1, min(procs, n_frames))
+    share = [n_frames // procs + (1 if k < n_frames % procs else 0) for k in range(procs)]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        barrier = m.Barrier(procs)
+        with ctx.Pool(processes=procs) as pool:
+            res = pool.map(_oracle_replica, [(0, 7 * k, n_warm, share[k], barrier) for k in range(procs)])
+    starts = [a for r in res for a, _ in r]
+    ends = [b for r in res for _, b in r]
+    region = max(ends) - min(starts)
+    per_frame = float(np.mean([b - a for r in res for a, b in r]))
+    return n_frames / region, per_frame, region, procs
+
+
+def oracle_sample_text(n_frames, procs, per_frame):
+    model, ncpu = host_cpu()
+    return (f"{n_frames} whole frames of the full-size workload (depth processing, 10 Gauss-Newton x 20 PCG, "
+            f"fusion; nothing extrapolated) on {procs} independent single-threaded replica streams of the "
+            f"numpy FP64 oracle; {per_frame:.2f} s per frame per replica; host {model}, {ncpu} logical cores")
+
+
+def cpu_baseline_sample(n_frames=None):
+    """The FP64 oracle on a bounded sample of the same workload: one whole
+    timed frame per host core (at most 16), all in parallel, after set-up."""
+    _, ncpu = host_cpu()
+    procs = max(1, min(16, ncpu))
+    n = n_frames or procs
+    fps, per_frame, region, procs = oracle_whole_frames(n, procs)
+    model, ncpu = host_cpu()
+    return {"value": fps, "unit": "frames/s", "cores": procs, "kind": "oracle",
+            "sample": oracle_sample_text(n, procs, per_frame), "cpu": model, "nproc": ncpu,
+            "seconds_per_frame_one_core": per_frame, "timed_region_s": region}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import synth
-    scene = synth.plain_full(seed=0)
-    n = args.warmup + args.steps
-    ts = [1 + (k % (scene.n_frames - 1)) for k in range(n)]
-    frames = dict(zip(sorted(set(ts)), render_frames(0, sorted(set(ts)), os.cpu_count() or 4)))
-    st = oracle_stream(scene)
-    times = []
-    for k in range(n):
-        sec = oracle_frame_seconds(st, frames[ts[k]], ts[k], scene.gn_iters, scene.pcg_iters)
-        if k >= args.warmup:
-            times.append(sec)
-    ms = 1000.0 * float(np.mean(times))
-    sample = oracle_sample_text(scene.gn_iters, scene.pcg_iters)
-    line = {"impl": "reference", "metric": METRIC, "value": 1000.0 / ms, "unit": "frames/s", "n_gpus": args.gpus,
+    _, ncpu = host_cpu()
+    procs = max(1, min(16, ncpu, args.steps))
+    # warm-up: whole frames on every replica, untimed (W in all, at least
+    # one per replica), then the timed region over the K steps
+    n_warm = max(1, -(-args.warmup // procs))
+    fps, per_frame, region, procs = oracle_whole_frames(args.steps, procs, n_warm)
+    model, ncpu = host_cpu()
+    ms = 1000.0 * region / args.steps
+    sample = oracle_sample_text(args.steps, procs, per_frame)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": 1000.0 / ms, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": 1000.0 / ms, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": procs, "kind": "oracle",
+                             "sample": sample, "cpu": model, "nproc": ncpu,
+                             "seconds_per_frame_one_core": per_frame},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -261,15 +324,21 @@ def large_workload(n_models, frame_ids):
     return [out[k] for k in range(n_models)]
 
 
-def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_gb, gn, pcg, seed=0):
+def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_gb, gn, pcg, seed=0,
+               plain=False, wait_admission=True):
     """The serving workload: n_regular streams of the uneven sizes (models
     reused from the uneven batch) plus n_large large ones, each submitting
-    depth frames as a Poisson process of rate_hz; an eighth of the regular
-    streams joins a third into the run and another eighth leaves at two
-    thirds.  Frames go through the library's server (admission against the
-    budget, continuous batching); latency is completion minus submission on
-    the server's clock.  A frame refused because its stream's queue is full
-    (or not admitted yet) is counted as dropped."""
+    depth frames as a Poisson process of rate_hz (the same arrival trace for
+    a given seed and rate); an eighth of the regular streams joins a third
+    into the run and another eighth leaves at two thirds.  Frames go through
+    the library's server: admission against the budget, then continuous
+    batching (plain=False) or the plain one-frame-at-a-time path
+    (plain=True, sw_server_set_plain).  Latency is completion minus
+    submission on the server's clock.  A frame refused because its stream's
+    queue is full or the stream is not admitted yet is counted as dropped.
+    With wait_admission the arrivals start once every initial stream is
+    admitted; without it (a budget that binds) they start at once and the
+    admitted / waiting counts are sampled through the run."""
     import heapq
     from types import SimpleNamespace
     rng = np.random.default_rng(seed)
@@ -278,6 +347,8 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
     late = set(range(n_regular - n_regular // 8, n_regular))
     leaving = set(range(n_regular // 8))
     srv = sw.sw_server_create(int(budget_gb * (1 << 30)), gn, pcg, queue_depth=4)
+    if plain:
+        sw.sw_server_set_plain(srv, True)
     ids = {}
 
     def open_stream(k):
@@ -287,12 +358,13 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
         v4, n4, t2, node4 = m["arrays"]
         ids[k] = sw.sw_server_open(srv, sw.params_for(cam, len(v4), len(node4)), v4, n4, t2, node4)
 
+    samples = []
     try:
         for k in range(n):
             if k not in late:
                 open_stream(k)
         t_adm = time.perf_counter()
-        while not all(sw.sw_server_is_admitted(srv, ids[k]) for k in ids):
+        while wait_admission and not all(sw.sw_server_is_admitted(srv, ids[k]) for k in ids):
             if time.perf_counter() - t_adm > 300:
                 raise RuntimeError("streams were not admitted")
             time.sleep(0.01)
@@ -304,10 +376,15 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
         heapq.heapify(events)
         joined, left = False, False
         sent = dropped = 0
+        next_sample = 0.0
         while events:
             t, k = heapq.heappop(events)
             if t > seconds:
                 continue
+            if t >= next_sample:
+                st_ = sw.sw_server_read_stats(srv)
+                samples.append((t, int(st_["admitted"]), int(st_["waiting"])))
+                next_sample = t + 0.1
             if not joined and t >= seconds / 3:
                 for j in late:
                     open_stream(j)
@@ -344,16 +421,58 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
     ok = [r for r in res if r["status"] == 0]
     lat = np.array([r["done_ms"] - r["submit_ms"] for r in ok]) if ok else np.zeros(1)
     span_s = (max(r["done_ms"] for r in ok) - min(r["submit_ms"] for r in ok)) / 1000.0 if ok else 1.0
-    return {"workload": f"{n_regular} streams of the uneven sizes + {n_large} large (640x480, 4096 nodes), "
-                        f"Poisson arrivals at {rate_hz:g} Hz per stream for {seconds:g} s; "
-                        f"{len(late)} join at 1/3, {len(leaving)} leave at 2/3; {gn} GN x {pcg} PCG + fusion",
-            "budget_gb": budget_gb, "frames_per_s": len(ok) / span_s, "offered_frames_per_s": rate_hz * n,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "frames_done": len(ok), "frames_failed": len(res) - len(ok), "frames_dropped": dropped,
-            "mean_batch": float(np.mean([r["batch_size"] for r in ok])) if ok else 0.0,
-            "steps": int(stats["steps"]), "gpu_busy_frac": float(stats["busy_ms"]) / 1000.0 / max(span_s, 1e-9),
-            "peak_admitted": n, "memory_gb_at_end": stats["memory_in_use"] / float(1 << 30)}
+    offered = rate_hz * n
+    out = {"workload": f"{n_regular} streams of the uneven sizes + {n_large} large (640x480, 4096 nodes), "
+                       f"Poisson arrivals at {rate_hz:.3g} Hz per stream for {seconds:g} s; "
+                       f"{len(late)} join at 1/3, {len(leaving)} leave at 2/3; {gn} GN x {pcg} PCG + fusion",
+           "path": "plain (one frame at a time)" if plain else "continuous batching",
+           "budget_gb": budget_gb, "frames_per_s": len(ok) / span_s, "offered_frames_per_s": offered,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+           "frames_done": len(ok), "frames_failed": len(res) - len(ok), "frames_dropped": dropped,
+           "drop_rate": dropped / max(1, dropped + sent),
+           "mean_batch": float(np.mean([r["batch_size"] for r in ok])) if ok else 0.0,
+           "steps": int(stats["steps"]), "gpu_busy_frac": float(stats["busy_ms"]) / 1000.0 / max(span_s, 1e-9),
+           "streams": n, "memory_gb_at_end": stats["memory_in_use"] / float(1 << 30)}
+    if samples:
+        out["admitted_max"] = max(a for _, a, _ in samples)
+        out["waiting_max"] = max(w for _, _, w in samples)
+        out["admitted_waiting_samples"] = [[round(t, 2), a, w] for t, a, w in samples[::5]]
+    return out
+
+
+def served_summary(r):
+    return {k: r[k] for k in ("frames_per_s", "offered_frames_per_s", "latency_ms", "frames_done", "frames_dropped",
+                              "drop_rate", "mean_batch", "gpu_busy_frac")}
+
+
+def run_served_sweep(sw, members, large, args, gn, pcg):
+    """Continuous batching against the plain server on the same arrival
+    traces: the saturating point first (its served frames/s is the batched
+    capacity), then offered loads of 25, 50 and 75% of that capacity for
+    both paths, and one run whose memory budget admits only part of the
+    streams at a time (admission binds; the arrivals do not wait for it)."""
+    n_streams = args.served_streams + args.served_large
+    sat = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
+                     args.served_rate, args.served_budget_gb, gn, pcg)
+    cap = sat["frames_per_s"]
+    points = []
+    for frac in (0.25, 0.5, 0.75):
+        rate = frac * cap / n_streams
+        b = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds, rate,
+                       args.served_budget_gb, gn, pcg, seed=1)
+        pl = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds, rate,
+                        args.served_budget_gb, gn, pcg, seed=1, plain=True)
+        points.append({"offered_frac_of_batched_capacity": frac, "rate_hz_per_stream": rate,
+                       "batched": served_summary(b), "plain": served_summary(pl)})
+    # a budget of about half what the streams hold: admission binds
+    need_gb = max(sat["memory_gb_at_end"], 0.1)
+    tight = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
+                       0.5 * cap / n_streams, 0.5 * need_gb, gn, pcg, seed=2, wait_admission=False)
+    out = dict(sat)
+    out["load_sweep"] = points
+    out["binding_budget"] = tight
+    return out
 
 
 def batch_workload(n_streams, frame_ids, scale=1.0):
@@ -485,7 +604,7 @@ def main():
     ap.add_argument("--clocks-csv", default="", help="keep the nvidia-smi clock samples here ({rank} is replaced)")
     ap.add_argument("--served-streams", type=int, default=64, help="regular streams of the serving run (0: skip)")
     ap.add_argument("--served-large", type=int, default=8)
-    ap.add_argument("--served-seconds", type=float, default=4.0)
+    ap.add_argument("--served-seconds", type=float, default=3.0)
     ap.add_argument("--served-rate", type=float, default=30.0)
     ap.add_argument("--served-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
@@ -729,9 +848,7 @@ def main():
                          "model rebuild (set sort, JtJ pattern, runner); call_ms: the whole call"}
     batched = run_batched(sw, torch, members[:args.batch_streams], args.batch_rounds, 2, flush, stream) \
         if members and args.batch_streams > 0 else None
-    served = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
-                        args.served_rate, args.served_budget_gb, gn, pcg) \
-        if members and args.served_streams > 0 else None
+    served = run_served_sweep(sw, members, large, args, gn, pcg) if members and args.served_streams > 0 else None
 
     if rank != 0:
         return
@@ -765,7 +882,7 @@ def main():
     if served:
         line["served"] = served
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(scene, frame_of[ts[0]], gn, pcg)
+        line["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(line))
 
 

@@ -254,6 +254,9 @@ sw_status sw_batch_upload_depth(sw_batch_handle b, const float* const* depths, i
 sw_status sw_batch_solve(sw_batch_handle b, int gn_iters, int pcg_iters, sw_solve_stats* stats);
 /* sw_fuse_frame for every active member. */
 sw_status sw_batch_fuse(sw_batch_handle b);
+/* The PCG's SpMV staging mode of the batch's current launch plan (see
+ * sw_debug_set_pcg_mode below); test hook. */
+sw_status sw_batch_debug_pcg_mode(sw_batch_handle b, int* mode);
 
 /* ---------------------------------------------------------------------------
  * Stage timing (CUDA events recorded on the launching stream, inside the
@@ -270,12 +273,80 @@ sw_status sw_read_profile(sw_handle h, double* ms, int* launches);
 sw_status sw_batch_set_profiling(sw_batch_handle b, int enable);
 sw_status sw_batch_read_profile(sw_batch_handle b, double* ms, int* launches);
 
-/* Test hook for failure detection: a cooperative launch whose grid barrier
- * expects one more CTA than it has, so that every wait runs out after
- * spin_limit polls.  Returns SW_ERR_TIMEOUT with *status_out holding the
- * device status bits when the bounded waits ended as they must; the CUDA
- * context stays usable. */
-sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out);
+/* Test hook for failure detection (an addition; the paper has no
+ * counterpart): make the product's own bounded device waits run out, without
+ * any fault on the GPU, by having a kernel withhold what another waits for.
+ *   kind 0  off (the default)
+ *   kind 1  in the persistent PCG (Sec. 7), CTA 1 of the first stream of a
+ *           launch does not publish its share of the first reduction: every
+ *           CTA of that stream stops polling after spin_limit polls
+ *   kind 2  the same CTA does not publish its rows' first vector u = M⁻¹ r:
+ *           the neighbours' waits for those rows run out
+ *   kind 3  the depth stage (Sec. 5) does not issue its TMA tile copies: each
+ *           CTA's bounded mbarrier wait runs out and it loads the tile with
+ *           plain loads instead (the maps stay exact)
+ * spin_limit (0..2^22): the poll limit that replaces the PCG's own while the
+ * hook is on (0 = keep the PCG's, 2^22 reduction polls); small values keep
+ * the test short.  The setting is process-wide on the current device, read
+ * by every later launch (captured graphs included), and the call
+ * synchronises the device.  A wait that ran out makes the next synchronising
+ * call of the stream (sw_solve_frame with stats, sw_batch_solve with stats)
+ * return SW_ERR_TIMEOUT; after a PCG wait ran out the node transforms are
+ * left as they were.  The CUDA context stays usable. */
+sw_status sw_debug_inject_wait_fault(int kind, int spin_limit);
+
+/* Test hooks for the PCG's modes (Sec. 7; additions).  Mode 3: a stream
+ * whose JᵀJ fits one thread-block cluster's shared memory (FP32 modes) runs
+ * its PCG as one cluster of CTAs that exchange vectors through distributed
+ * shared memory.  Otherwise the cooperative PCG keeps what fits of each
+ * CTA's share of JᵀJ in shared memory: mode 2 stages the rows' 6x6 blocks
+ * and the per-entry products, mode 1 only the products (blocks read from
+ * global memory every iteration), mode 0 nothing (a warp per block row).
+ * The mode is chosen per stream (per batch for the cooperative kernel) when
+ * its launch plan is built, as the highest that fits.  sw_debug_set_pcg_mode
+ * caps it (0..3; 3 = no cap) for launch plans built after the call (streams
+ * given a model, batches created or rebuilt after it), process-wide.
+ * sw_debug_pcg_mode reports the mode a stream's current plan uses;
+ * sw_batch_debug_pcg_mode 3 when every member runs on clusters, else the
+ * cooperative kernel's mode. */
+sw_status sw_debug_set_pcg_mode(int max_mode);
+sw_status sw_debug_pcg_mode(sw_handle h, int* mode);
+
+/* The launch plan of the cluster PCG (an addition; host code only, needs no
+ * GPU): the PCG of a stream whose JᵀJ fits the shared memory of one
+ * thread-block cluster runs as one cluster of `ctas` CTAs, each holding the
+ * upper 6x6 blocks of the node rows it owns.  Input (host): the upper block
+ * pattern as the library keeps it, row_ptr [n_nodes + 1] and col
+ * [row_ptr[n_nodes]] with every row leading with its diagonal block;
+ * node4 [n_nodes][4] the node positions (x y z, w unused).  Output: plan
+ * (host, cap ints, nullable to ask for the size in *n_out) laid out as
+ * header {ctas, most rows, most home blocks, most receive slots of a CTA,
+ * n_nodes, most halo rows, most u pushes}; per CTA prefix tables
+ * (ctas + 1 each) of rows, home blocks, receive slots and u pushes; each
+ * CTA's rows (node ids, its local order); per CTA the rows' home-block,
+ * receive-slot and u-push offsets (rows + 1 each); per home block its block
+ * index, the local u slot of its column (own row, or halo slot after the
+ * own rows) and the target of its transposed product ((owner CTA << 16) |
+ * receive slot, -1 on the diagonal); per u push (peer CTA << 16) | the
+ * peer's u slot.  *smem_out: the shared memory a CTA needs.
+ * SW_ERR_INVALID_ARG if the system does not fit smem_limit bytes per CTA
+ * (or 192 rows per CTA) or the pattern is malformed. */
+sw_status sw_debug_cluster_plan(int ctas, int n_nodes, const int* row_ptr, const int* col, const float* node4,
+                                size_t smem_limit, int* plan, size_t cap, size_t* n_out, size_t* smem_out);
+
+/* Cluster-PCG inspection (an addition): with h non-null, the cluster size
+ * and per-CTA shared memory of the stream's plan (0, 0 if it has none);
+ * with active_clusters non-null, how many clusters of `ctas` CTAs with
+ * `smem` bytes of shared memory each the device runs at once in the given
+ * precision (a negative value is a CUDA error code). */
+sw_status sw_debug_pcg_cluster(sw_handle h, int precision, int ctas, size_t smem, int* plan_ctas,
+                               size_t* plan_smem, int* active_clusters);
+
+/* Splat visibility (Sec. 7) that the last solve of a stream with
+ * sw_params.visibility = 1 predicted before its first Gauss-Newton
+ * iteration: visible [n_surfels] (host, caller's order) 1 for the surfels
+ * that kept a pixel of the splat index map, else 0.  Synchronous. */
+sw_status sw_read_visibility(sw_handle h, int* visible, int cap, int* n_out);
 
 /* Test hook for the block-Jacobi preconditioner (Sec. 7): the inverse of
  * each of n symmetric 6x6 blocks (host, row-major, 36 values each; float, or
@@ -407,6 +478,13 @@ sw_status sw_server_set_batch_window(sw_server_handle s, double window_ms);
  * grows within each stream's max_surfels (and max_nodes, with extend_nodes);
  * a frame whose appending fails reports that status. */
 sw_status sw_server_set_appending(sw_server_handle s, int enable);
+/* Plain serving (1), the reference for continuous batching: each step takes
+ * only the oldest queued frame of all admitted streams and runs it through
+ * that stream's own calls (sw_upload_depth, sw_solve_frame, sw_fuse_frame),
+ * one frame and one stream at a time, with the same admission, queues and
+ * time stamps.  0 (the default) batches every admitted stream's oldest
+ * frame into one step. */
+sw_status sw_server_set_plain(sw_server_handle s, int enable);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 
 /* Rigid pre-alignment of the current frame (Sec. 7: before the non-rigid

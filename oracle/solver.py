@@ -402,14 +402,17 @@ class IterStats:
 
 def gauss_newton(v_ref, n_ref, knn, w, node_p, node_dq, graph, pattern_keys,
                  lam, gn_iters, pcg_iters, associate_fn=None, fixed_targets=None,
-                 keep_masks=False):
+                 keep_masks=False, linear_solver=None):
     """Gauss-Newton over the node transforms (Sec. 7-8).
 
     ``associate_fn(v_live, n_live) -> (mask, target_v, target_n)`` finds the
     correspondences at each iteration (the ICP-style re-association of
     Sec. 4); alternatively ``fixed_targets = (mask, target_v, target_n)``
-    holds them fixed.  Returns (node_dq, [IterStats]).
+    holds them fixed.  ``linear_solver(A, b, Minv, iters) -> (x, rᵀz, n)``
+    replaces ``pcg`` (tests measure how the result depends on the linear
+    solve's arithmetic with it).  Returns (node_dq, [IterStats]).
     """
+    linear_solver = pcg if linear_solver is None else linear_solver
     n = len(node_p)
     stats = []
     for _ in range(gn_iters):
@@ -424,7 +427,7 @@ def gauss_newton(v_ref, n_ref, knn, w, node_p, node_dq, graph, pattern_keys,
         reg = reg_terms(node_p, node_dq, graph, lam)
         A, g = assemble(pattern_keys, n, knn[idx], J, r, reg)
         Minv = block_jacobi_inverse(A)
-        x, rz, _ = pcg(A, -g.reshape(-1), Minv, pcg_iters)
+        x, rz, _ = linear_solver(A, -g.reshape(-1), Minv, pcg_iters)
         stats.append(IterStats(float(r @ r), float(np.sum(reg[2] ** 2)), len(idx), rz,
                                mask.copy() if keep_masks else None))
         node_dq = apply_increment(node_dq, x)

@@ -103,13 +103,20 @@ class OracleStream:
         tn[ok] = self.maps["N"].reshape(-1, 3)[pix[ok]]
         return ok, tv, tn
 
-    def solve_frame(self, gn_iters, pcg_iters, keep_masks=False):
+    def solve_frame(self, gn_iters, pcg_iters, keep_masks=False, visible=None, linear_solver=None):
+        """Sec. 7: the frame's Gauss-Newton solve.  With visibility on, the
+        visible surfels are predicted first, unless ``visible`` gives them
+        (a mask over the surfels, for comparisons on identical inputs).
+        ``linear_solver`` replaces the PCG (see solver.gauss_newton)."""
         if self.p.visibility:
-            self.predict_visibility()
+            if visible is None:
+                self.predict_visibility()
+            else:
+                self.visible = np.asarray(visible, dtype=bool).copy()
         self.node_dq, stats = SOLVER.gauss_newton(
             self.v_ref, self.n_ref, self.knn, self.w, self.node_p, self.node_dq,
             self.graph, self.pattern, self.p.lam, gn_iters, pcg_iters,
-            associate_fn=self.associate, keep_masks=keep_masks)
+            associate_fn=self.associate, keep_masks=keep_masks, linear_solver=linear_solver)
         return stats
 
     def rigid_align(self, iters):
@@ -190,6 +197,22 @@ class OracleStream:
         self.knn_pre_extension = self.knn.copy()
         self.knn, self.w, self.reskinned = APPEND.merge_skinning(self.v_ref, self.knn, self.w, self.node_p,
                                                                  self.node_sigma, len(self.node_p) - len(new_p))
+
+    def load_state(self, v4, n4, t2, knn, w, node_dq):
+        """Replace the surfel model, its skinning and the node transforms by
+        given values (v4: x y z radius, n4: nx ny nz confidence, t2: t_init,
+        t_observed; knn / w in distance order), keeping the nodes and the
+        graph: a frame can then be compared on identical inputs."""
+        v4, n4 = np.asarray(v4, dtype=np.float64), np.asarray(n4, dtype=np.float64)
+        self.v_ref, self.radius = v4[:, :3].copy(), v4[:, 3].copy()
+        self.n_ref, self.conf = n4[:, :3].copy(), n4[:, 3].copy()
+        t2 = np.asarray(t2)
+        self.t_init = t2[:, 0].astype(np.int64).copy()
+        self.t_obs = t2[:, 1].astype(np.int64).copy()
+        self.knn = np.asarray(knn).astype(np.int64).copy()
+        self.w = np.asarray(w, dtype=np.float64).copy()
+        self.node_dq = np.asarray(node_dq, dtype=np.float64).copy()
+        self.pattern = SOLVER.BlockMatrix.pattern(len(self.node_p), self.knn, self.graph).keys
 
     # -- read-back -----------------------------------------------------------
     def read_nodes(self):

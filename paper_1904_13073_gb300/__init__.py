@@ -125,7 +125,15 @@ _SIGS = {
     "sw_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
     "sw_batch_set_profiling": [_P, _I],
     "sw_batch_read_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
-    "sw_debug_barrier_timeout": [_I, ctypes.POINTER(_I)],
+    "sw_debug_inject_wait_fault": [_I, _I],
+    "sw_debug_set_pcg_mode": [_I],
+    "sw_debug_pcg_mode": [_P, ctypes.POINTER(_I)],
+    "sw_batch_debug_pcg_mode": [_P, ctypes.POINTER(_I)],
+    "sw_read_visibility": [_P, _P, _I, ctypes.POINTER(_I)],
+    "sw_debug_pcg_cluster": [_P, _I, _I, ctypes.c_size_t, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t),
+                             ctypes.POINTER(_I)],
+    "sw_debug_cluster_plan": [_I, _I, _P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
+                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
     "sw_debug_block_inverse": [_P, _I, _I, _P, _P],
     "sw_server_create": [ctypes.c_size_t, _I, _I, _I, ctypes.POINTER(_P)],
     "sw_server_destroy": [_P],
@@ -139,6 +147,7 @@ _SIGS = {
     "sw_server_read_stats": [_P, ctypes.POINTER(sw_server_stats)],
     "sw_server_set_batch_window": [_P, ctypes.c_double],
     "sw_server_set_appending": [_P, _I],
+    "sw_server_set_plain": [_P, _I],
     "sw_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_rigid_align": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_batch_rigid_align": [_P, _I],
@@ -502,11 +511,64 @@ def sw_debug_block_inverse(blocks, fp64=False):
     return out[:n], ok[:n].astype(bool)
 
 
-def sw_debug_barrier_timeout(spin_limit):
-    """Returns (status code, device status bits) of a barrier that cannot complete."""
-    st = _I()
-    code = lib().sw_debug_barrier_timeout(spin_limit, ctypes.byref(st))
-    return code, st.value
+# failure kinds of sw_debug_inject_wait_fault
+SW_FAULT_NONE, SW_FAULT_PCG_PARTIAL, SW_FAULT_PCG_VECTOR, SW_FAULT_DEPTH_TMA = 0, 1, 2, 3
+
+
+def sw_debug_inject_wait_fault(kind, spin_limit=0):
+    """Make the product's bounded device waits run out (kind 0 turns it off)."""
+    _check(lib().sw_debug_inject_wait_fault(int(kind), int(spin_limit)), None)
+
+
+def sw_debug_set_pcg_mode(max_mode):
+    """Cap the PCG's SpMV staging mode (2 = no cap) for launch plans built afterwards."""
+    _check(lib().sw_debug_set_pcg_mode(int(max_mode)), None)
+
+
+def sw_debug_pcg_mode(h):
+    m = _I()
+    _check(lib().sw_debug_pcg_mode(h, ctypes.byref(m)), h)
+    return m.value
+
+
+def sw_batch_debug_pcg_mode(b):
+    m = _I()
+    _check(lib().sw_batch_debug_pcg_mode(b, ctypes.byref(m)), None)
+    return m.value
+
+
+def sw_debug_cluster_plan(ctas, row_ptr, col, node4, smem_limit):
+    """(plan int32 array, shared-memory bytes per CTA) of the cluster PCG for
+    an upper block pattern (host code; raises SwError if it does not fit)."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32)
+    nd = np.ascontiguousarray(node4, np.float32).reshape(-1, 4)
+    n = len(rp) - 1
+    size, smem = ctypes.c_size_t(), ctypes.c_size_t()
+    args = (int(ctas), n, rp.ctypes.data_as(_P), cl.ctypes.data_as(_P), nd.ctypes.data_as(_P),
+            int(smem_limit))
+    _check(lib().sw_debug_cluster_plan(*args, None, 0, ctypes.byref(size), ctypes.byref(smem)), None)
+    out = np.empty(max(1, size.value), np.int32)
+    _check(lib().sw_debug_cluster_plan(*args, out.ctypes.data_as(_P), size.value, None, None), None)
+    return out[:size.value], smem.value
+
+
+def sw_debug_pcg_cluster(h=None, precision=0, ctas=16, smem=0):
+    """(plan cluster size, plan shared memory per CTA, clusters of `ctas`
+    CTAs with `smem` bytes that the device runs at once)."""
+    c, b, a = _I(), ctypes.c_size_t(), _I()
+    _check(lib().sw_debug_pcg_cluster(h, int(precision), int(ctas), int(smem), ctypes.byref(c), ctypes.byref(b),
+                                      ctypes.byref(a)), h)
+    return c.value, b.value, a.value
+
+
+def sw_read_visibility(h):
+    """Per surfel (caller order) 1 if the last solve's visibility prediction kept it."""
+    n = _count_surfels(h)
+    out = np.empty(max(1, n), np.int32)
+    got = _I()
+    _check(lib().sw_read_visibility(h, out.ctypes.data_as(_P), max(1, n), ctypes.byref(got)), h)
+    return out[:got.value]
 
 
 def sw_last_error(h=None):
@@ -607,6 +669,10 @@ def sw_server_set_batch_window(srv, window_ms):
 
 def sw_server_set_appending(s, enable):
     _check(lib().sw_server_set_appending(s, int(bool(enable))))
+
+
+def sw_server_set_plain(s, enable):
+    _check(lib().sw_server_set_plain(s, int(bool(enable))), None)
 
 
 def sw_server_read_stats(srv):

@@ -38,6 +38,11 @@ std::mutex g_err_mu;
 std::string g_last_error;
 std::atomic<size_t> g_budget{0};
 std::atomic<size_t> g_in_use{0};
+// highest PCG mode a launch plan may take: 3 the cluster PCG
+// (k_pcg_cluster.cu) where a stream's system fits it, else the cooperative
+// PCG's SpMV staging mode 2, 1 or 0 (k_pcg.cu: SpmvMode); lowered only by
+// sw_debug_set_pcg_mode
+std::atomic<int> g_pcg_mode_cap{3};
 
 void set_global_error(const std::string& s) {
   std::lock_guard<std::mutex> lk(g_err_mu);
@@ -86,6 +91,7 @@ struct Runner {
   std::vector<cudaEvent_t> event_pool;
   int pcg_rows_per_cta = 32;     // PCG granularity: a stream takes one CTA per this many rows (autotuned)
   int alloc_n = -1;              // member count the device tables in `allocs` were sized for
+  std::vector<int> cluster_list; // members on the cluster PCG (their indices)
   std::string err;
 };
 
@@ -105,6 +111,8 @@ struct sw_stream {
   float4* w_dist = nullptr;
   Runner* run = nullptr;     // the stream's own one-stream runner
   std::vector<int> rl_ptr_host;   // per block row, the start of its SpMV entries (PCG work sizing)
+  int cplan_ctas = 0;             // cluster size of the stream's cluster-PCG plan (0: none)
+  size_t cplan_smem = 0;          // shared memory per CTA that plan needs
   // ordering against batches this stream belongs to
   cudaEvent_t batch_done = nullptr;   // recorded by the last batch call (owned by the batch)
   cudaEvent_t own_ev = nullptr;       // recorded before a batch call when own work is pending
@@ -351,21 +359,39 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     r->bh.precision = prec;
     r->bh.any_visibility = 0;
     for (int i = 0; i < n; ++i) r->bh.any_visibility |= devs[i].visibility;
+    // members whose system has a cluster plan run on the cluster PCG (one
+    // cluster each, its own launch); the others share the cooperative grid
+    std::vector<int> cl;
+    size_t cl_smem = 0;
+    int cl_ctas = 0;
+    std::vector<char> in_cluster(n, 0);
+    if (g_pcg_mode_cap.load() >= 3)
+      for (int i = 0; i < n; ++i) {
+        const sw_stream* m = r->members[i];
+        if (!devs[i].cplan || m->cplan_ctas == 0 || (cl_ctas && m->cplan_ctas != cl_ctas)) continue;
+        cl_ctas = m->cplan_ctas;
+        cl_smem = std::max(cl_smem, m->cplan_smem);
+        cl.push_back(i);
+        in_cluster[i] = 1;
+      }
+    const int n_coop = n - (int)cl.size();
     const int per_sm = std::max(1, pcg_blocks_per_sm(prec));
     const int cap = sm_count() * per_sm;
-    if (n > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
+    if (n_coop > cap) return fail(err_to, SW_ERR_INVALID_ARG, "too many streams for one persistent launch");
     // greedy: the next CTA goes to the stream with the most rows per CTA,
     // which minimises the largest share (the launch ends with the slowest
     // stream); a stream takes at most one CTA per pcg_rows_per_cta rows
     std::vector<int> want(n, 1);
-    int total = n;
+    for (int i = 0; i < n; ++i)
+      if (in_cluster[i]) want[i] = 0;
+    int total = n_coop;
     {
       const int rows = std::max(8, r->pcg_rows_per_cta);
       auto limit = [&](int i) { return std::max(1, std::min(kMaxCtaPerStream, (devs[i].n_n + rows - 1) / rows)); };
       auto share = [&](int i) { return (devs[i].n_n + want[i] - 1) / want[i]; };
       std::priority_queue<std::pair<int, int>> pq;   // (rows per CTA, stream)
       for (int i = 0; i < n; ++i)
-        if (want[i] < limit(i)) pq.push({share(i), i});
+        if (!in_cluster[i] && want[i] < limit(i)) pq.push({share(i), i});
       while (total < cap && !pq.empty()) {
         const int i = pq.top().second;
         pq.pop();
@@ -378,8 +404,12 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     for (int i = 0; i < n; ++i) {
       tiles[(size_t)kTilePcg * (n + 1) + i] = acc;
       acc += want[i];
-      rows_cap = std::max(rows_cap, (devs[i].n_n + want[i] - 1) / want[i]);
+      if (want[i]) rows_cap = std::max(rows_cap, (devs[i].n_n + want[i] - 1) / want[i]);
     }
+    r->cluster_list = cl;
+    r->bh.n_cluster = (int)cl.size();
+    r->bh.cluster_ctas = cl_ctas;
+    r->bh.cluster_smem = cl_smem;
     tiles[(size_t)kTilePcg * (n + 1) + n] = acc;
     r->bh.total_tiles[kTilePcg] = acc;
     // the most SpMV entries one CTA owns (its rows are i = t + G a)
@@ -387,7 +417,7 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     for (int i = 0; i < n; ++i) {
       const std::vector<int>& rp = r->members[i]->rl_ptr_host;
       const int G = want[i], nn = devs[i].n_n;
-      if (nn == 0) continue;   // a stream without a model yet
+      if (nn == 0 || G == 0) continue;   // a stream without a model yet, or on the cluster PCG
       if ((int)rp.size() != nn + 1) return fail(err_to, SW_ERR_INVALID_ARG, "batch member without a JᵀJ pattern");
       for (int t = 0; t < G; ++t) {
         int e = 0;
@@ -400,7 +430,7 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // the SpMV stages as much in shared memory as fits: the rows' blocks and
     // the entries' outputs (2), the outputs only (1), or nothing (0)
-    int mode = 2;
+    int mode = std::min(2, g_pcg_mode_cap.load());
     while (mode >= 0 && pcg_smem_bytes(rows_cap, ent_cap, prec, mode) > (size_t)optin) --mode;
     if (mode < 0) return fail(err_to, SW_ERR_INVALID_ARG, "a stream has too many nodes for the PCG's on-chip state");
     r->bh.pcg_rows_cap = rows_cap;
@@ -410,11 +440,13 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
   SwDev* devs_dev = nullptr;
   int* tile_dev = nullptr;
   int* active_dev = nullptr;
-  if (r->alloc_n == n && r->allocs.size() == 4) {   // same members: the tables are rewritten in stream order
+  int* cl_dev = nullptr;
+  if (r->alloc_n == n && r->allocs.size() == 5) {   // same members: the tables are rewritten in stream order
     devs_dev = reinterpret_cast<SwDev*>(r->allocs[0].first);
     tile_dev = reinterpret_cast<int*>(r->allocs[1].first);
     active_dev = reinterpret_cast<int*>(r->allocs[2].first);
     r->frames_dev = reinterpret_cast<int*>(r->allocs[3].first);
+    cl_dev = reinterpret_cast<int*>(r->allocs[4].first);
   } else {
     free_list(r->allocs);
     r->alloc_n = -1;
@@ -422,8 +454,13 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
     SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&tile_dev), sizeof(int) * tiles.size()));
     SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&active_dev), sizeof(int) * std::max(1, n)));
     SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&r->frames_dev), sizeof(int) * std::max(1, n)));
+    SW_TRY(dalloc(err_to, r->allocs, reinterpret_cast<void**>(&cl_dev), sizeof(int) * std::max(1, n)));
     r->alloc_n = n;
   }
+  if (!r->cluster_list.empty())
+    SW_CUDA(err_to, cudaMemcpyAsync(cl_dev, r->cluster_list.data(), sizeof(int) * r->cluster_list.size(),
+                                    cudaMemcpyHostToDevice, r->st));
+  r->bh.cluster_members_dev = cl_dev;
   if (!r->ring) {
     if (cudaMallocHost(&r->ring, sizeof(int) * Runner::kRing * Runner::kSlotInts) != cudaSuccess)
       return fail(err_to, SW_ERR_NO_MEMORY, "pinned host allocation failed");
@@ -513,6 +550,7 @@ sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vect
     prof_mark(r, prof, kProfData, false, true);
     prof_mark(r, prof, kProfPcg, true, true);
     launch_precond(r->bh, st);
+    SW_CUDA(err_to, launch_pcg_cluster(r->bh, it, pcg, st));
     SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
     prof_mark(r, prof, kProfPcg, false, true);
   }
@@ -684,9 +722,18 @@ __global__ void k_identity_dq(float4* dq, int n) {
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
+// a depth frame arrives: its id, and the depth stage's wait status cleared
+__global__ void k_frame_begin(int* t_now, int v, int* status) {
+  *t_now = v;
+  atomicAnd(status, ~kStatusDepthTimeout);
+}
+
 __global__ void k_set_frames(Batch bt, const int* __restrict__ frames) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < bt.n_streams && stream_active(bt, s)) *bt.devs[s].t_now = frames[s];
+  if (s < bt.n_streams && stream_active(bt, s)) {
+    *bt.devs[s].t_now = frames[s];
+    atomicAnd(bt.devs[s].status, ~kStatusDepthTimeout);
+  }
 }
 
 }  // namespace
@@ -748,7 +795,7 @@ sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows,
         launch_data_stage(r->bh, 0, st);
         launch_precond(r->bh, st);
         cudaEventRecord(e0, st);
-        ok = launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
+        ok = launch_pcg_cluster(r->bh, 0, pcg, st) == cudaSuccess && launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
         cudaEventRecord(e1, st);
         ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
         float ms = 0.f;
@@ -1036,6 +1083,60 @@ sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const 
   return SW_OK;
 }
 
+// The cluster size of the cluster PCG on the current device (16 CTAs where
+// the hardware runs such clusters, else 8, else 0: no cluster PCG), found
+// once per device with a modest shared-memory request.
+int device_cluster_ctas(int precision) {
+  static std::mutex mu;
+  static std::map<int, int> known;   // device -> cluster size
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find(dev);
+  if (it != known.end()) return it->second;
+  int C = 0;
+  for (int c : {16, 8})
+    if (cluster_pcg_fits(precision, c, 64 * 1024)) { C = c; break; }
+  known[dev] = C;
+  return C;
+}
+
+// The cluster PCG's plan for the stream's JᵀJ pattern (FP32 modes), built on
+// the host from the pattern and the node positions, or none when the system
+// does not fit one cluster's shared memory.
+sw_status build_plan(sw_stream* s) {
+  SwDev& h = s->h;
+  h.cplan = nullptr;
+  s->cplan_ctas = 0;
+  s->cplan_smem = 0;
+  if (h.precision == SW_PRECISION_FP64 || h.n_n < 1) return SW_OK;
+  const int C = device_cluster_ctas(h.precision);
+  if (C == 0) return SW_OK;
+  const int n_n = h.n_n, nnzb = h.nnzb;
+  std::vector<int> rp(n_n + 1), col(nnzb);
+  std::vector<float> node4((size_t)n_n * 4);
+  SW_CUDA(s, cudaMemcpyAsync(rp.data(), h.row_ptr, (n_n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaMemcpyAsync(col.data(), h.col, nnzb * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaMemcpyAsync(node4.data(), h.node_p, node4.size() * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t limit = optin > 4096 ? (size_t)optin - 2048 : 0;   // the kernel's static shared memory
+  std::vector<int> plan;
+  size_t smem = 0;
+  if (!build_cluster_plan(C, n_n, rp, col, node4, limit, plan, &smem)) return SW_OK;
+  if (!cluster_pcg_fits(h.precision, C, smem)) return SW_OK;
+  int* dp = nullptr;
+  SW_TRY(A(s, &dp, plan.size(), true));
+  SW_CUDA(s, cudaMemcpyAsync(dp, plan.data(), plan.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  h.cplan = dp;
+  s->cplan_ctas = C;
+  s->cplan_smem = smem;
+  return SW_OK;
+}
+
 // The JᵀJ pattern from the surfels' sets (device) and the node graph, built
 // on the device; the system is cleared, the stream re-described to its runner
 // and warped live.  `graph_changed`: the node graph's in-edge lists are
@@ -1081,6 +1182,7 @@ sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph
     SW_CUDA(s, cudaMemcpyAsync(s->rl_ptr_host.data(), h.rl_ptr, (n_n + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
     SW_CUDA(s, cudaStreamSynchronize(st));
   }
+  SW_TRY(build_plan(s));
   SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
   SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
   if (h.precision == SW_PRECISION_FP64) {
@@ -1175,7 +1277,7 @@ sw_status sw_upload_depth(sw_handle s, const float* depth, int on_device, int fr
   Runner* r = s->run;
   std::vector<ProfEvent>* prof = nullptr;
   if (r->profiling) { reset_eager_prof(r); prof = &r->eager_prof; }
-  k_set_int<<<1, 1, 0, s->st>>>(s->h.t_now, frame_id);
+  k_frame_begin<<<1, 1, 0, s->st>>>(s->h.t_now, frame_id, s->h.status);
   prof_mark(r, prof, kProfDepth, true, false);
   launch_depth_maps(r->bh, s->st);
   prof_mark(r, prof, kProfDepth, false, false);
@@ -1199,7 +1301,12 @@ sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
     SW_CUDA(s, cudaMemcpyAsync(out->pcg_rz, s->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
   }
   SW_CUDA(s, cudaStreamSynchronize(s->st));
-  if (status & kStatusTimeout) return fail(s, SW_ERR_TIMEOUT, "a bounded grid-barrier wait of the PCG gave up");
+  if (status & kStatusTimeout)
+    return fail(s, SW_ERR_TIMEOUT, "a bounded wait of the PCG gave up (a reduction or a neighbour's vector); "
+                                   "the node transforms were left as they were");
+  if (status & kStatusDepthTimeout)
+    return fail(s, SW_ERR_TIMEOUT, "the depth stage's bounded wait for a TMA tile gave up (the tile was read with "
+                                   "plain loads instead)");
   if (status & kStatusBreakdown) return fail(s, SW_ERR_SOLVER_BREAKDOWN, "a diagonal block is not positive definite or pᵀAp <= 0");
   return SW_OK;
 }
@@ -1601,7 +1708,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       launch_slot_sets(h.set_slots, n_sets_all, all_sets.as<int4>(), st);
       SW_CUDA(s, cudaGetLastError());
       const int sorted_sets = s->sorted_sets;
-      recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A64});
+      recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A64, h.cplan});
       SW_TRY(install_pattern(s, all_sets.as<int4>(), n_sets_all, false));
       s->sorted_sets = sorted_sets;
       return finish(2);
@@ -1945,7 +2052,7 @@ sw_status sw_batch_solve(sw_batch_handle b, int gn_iters, int pcg_iters, sw_solv
     SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].n_corr, m->h.n_corr, kMaxGn * sizeof(int), cudaMemcpyDeviceToHost, r->st));
     SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].pcg_rz, m->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, r->st));
     SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
-    if (status & kStatusTimeout) worst = SW_ERR_TIMEOUT;
+    if (status & (kStatusTimeout | kStatusDepthTimeout)) worst = SW_ERR_TIMEOUT;
     else if ((status & kStatusBreakdown) && worst == SW_OK) worst = SW_ERR_SOLVER_BREAKDOWN;
   }
   if (worst != SW_OK) return fail(nullptr, worst, "a member's solve broke down or timed out (see its stats)");
@@ -1973,7 +2080,9 @@ sw_status batch_member_status(sw_batch_handle b, int* status) {
       SW_CUDA(nullptr, cudaMemcpyAsync(&raw[i], r->members[i]->h.status, sizeof(int), cudaMemcpyDeviceToHost, r->st));
   SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
   for (int i = 0; i < n; ++i)
-    status[i] = (raw[i] & kStatusTimeout) ? SW_ERR_TIMEOUT : (raw[i] & kStatusBreakdown) ? SW_ERR_SOLVER_BREAKDOWN : SW_OK;
+    status[i] = (raw[i] & (kStatusTimeout | kStatusDepthTimeout)) ? SW_ERR_TIMEOUT
+                : (raw[i] & kStatusBreakdown)                       ? SW_ERR_SOLVER_BREAKDOWN
+                                                                     : SW_OK;
   return SW_OK;
 }
 }  // namespace sw
@@ -2080,23 +2189,79 @@ sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* in
   return SW_OK;
 }
 
-sw_status sw_debug_barrier_timeout(int spin_limit, int* status_out) {
-  if (spin_limit < 1 || spin_limit > (1 << 24)) return fail(nullptr, SW_ERR_INVALID_ARG, "spin_limit out of range");
-  GridBarrier* gb = nullptr;
-  int* status = nullptr;
-  SW_CUDA(nullptr, cudaMalloc(&gb, sizeof(GridBarrier)));
-  if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) { cudaFree(gb); return fail(nullptr, SW_ERR_CUDA, "cudaMalloc failed"); }
-  cudaMemset(gb, 0, sizeof(GridBarrier));
-  cudaMemset(status, 0, sizeof(int));
-  // two CTAs run, the barrier waits for three: no wait can complete
-  cudaError_t e = launch_barrier_probe(gb, 2, 3, spin_limit, status, 0);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  int st = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaFree(gb);
-  cudaFree(status);
-  if (e != cudaSuccess) return fail(nullptr, SW_ERR_CUDA, std::string("barrier probe: ") + cudaGetErrorString(e));
-  if (status_out) *status_out = st;
-  if (st & kStatusTimeout) return fail(nullptr, SW_ERR_TIMEOUT, "bounded grid-barrier wait ran out (expected)");
+sw_status sw_debug_set_pcg_mode(int max_mode) {
+  if (max_mode < 0 || max_mode > 3) return fail(nullptr, SW_ERR_INVALID_ARG, "max_mode must be 0, 1, 2 or 3");
+  g_pcg_mode_cap.store(max_mode);
+  return SW_OK;
+}
+
+sw_status sw_debug_pcg_mode(sw_handle s, int* mode) {
+  if (!s || !mode) return fail(s, SW_ERR_INVALID_ARG, "null argument");
+  if (!s->has_model || !s->run) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  *mode = s->run->bh.n_cluster ? 3 : s->run->bh.pcg_mode;
+  return SW_OK;
+}
+
+sw_status sw_batch_debug_pcg_mode(sw_batch_handle b, int* mode) {
+  SW_TRY(batch_check(b));
+  if (!mode) return fail(nullptr, SW_ERR_INVALID_ARG, "null argument");
+  *mode = b->run.bh.n_cluster == (int)b->run.members.size() ? 3 : b->run.bh.pcg_mode;
+  return SW_OK;
+}
+
+sw_status sw_read_visibility(sw_handle s, int* visible, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  if (n_out) *n_out = s->h.n_s;
+  if (visible) SW_TRY(d2h_perm(s, s->h.visible, visible, 1, true));
+  return SW_OK;
+}
+
+sw_status sw_debug_inject_wait_fault(int kind, int spin_limit) {
+  if (kind < kFaultNone || kind > kFaultDepthTma) return fail(nullptr, SW_ERR_INVALID_ARG, "unknown fault kind");
+  if (spin_limit < 0 || spin_limit > (1 << 22)) return fail(nullptr, SW_ERR_INVALID_ARG, "spin_limit out of range");
+  SW_CUDA(nullptr, cudaDeviceSynchronize());   // no launch in flight sees a half-written setting
+  set_pcg_wait_fault(kind == kFaultPcgPartial || kind == kFaultPcgVector ? kind : kFaultNone, spin_limit);
+  set_depth_wait_fault(kind == kFaultDepthTma ? kind : kFaultNone);
+  SW_CUDA(nullptr, cudaDeviceSynchronize());
+  SW_CUDA(nullptr, cudaGetLastError());
+  return SW_OK;
+}
+
+sw_status sw_debug_cluster_plan(int ctas, int n_nodes, const int* row_ptr, const int* col, const float* node4,
+                                size_t smem_limit, int* plan, size_t cap, size_t* n_out, size_t* smem_out) {
+  if (ctas < 1 || ctas > 16 || n_nodes < 1 || !row_ptr || !col || !node4)
+    return fail(nullptr, SW_ERR_INVALID_ARG, "bad cluster-plan arguments");
+  const int nnzb = row_ptr[n_nodes];
+  if (nnzb < n_nodes) return fail(nullptr, SW_ERR_INVALID_ARG, "row_ptr does not describe a pattern");
+  std::vector<int> rp(row_ptr, row_ptr + n_nodes + 1), cl(col, col + nnzb);
+  for (int i = 0; i < n_nodes; ++i) {
+    if (rp[i + 1] <= rp[i] || cl[rp[i]] != i) return fail(nullptr, SW_ERR_INVALID_ARG, "a row does not lead with its diagonal block");
+    for (int b = rp[i]; b < rp[i + 1]; ++b)
+      if (cl[b] < i || cl[b] >= n_nodes) return fail(nullptr, SW_ERR_INVALID_ARG, "a block outside the upper triangle");
+  }
+  std::vector<float> nd(node4, node4 + (size_t)n_nodes * 4);
+  std::vector<int> out;
+  size_t smem = 0;
+  if (!build_cluster_plan(ctas, n_nodes, rp, cl, nd, smem_limit, out, &smem))
+    return fail(nullptr, SW_ERR_INVALID_ARG, "the system does not fit the cluster's shared memory");
+  if (n_out) *n_out = out.size();
+  if (smem_out) *smem_out = smem;
+  if (plan) {
+    if (cap < out.size()) return fail(nullptr, SW_ERR_INVALID_ARG, "plan capacity too small");
+    std::memcpy(plan, out.data(), out.size() * sizeof(int));
+  }
+  return SW_OK;
+}
+
+sw_status sw_debug_pcg_cluster(sw_handle s, int precision, int ctas, size_t smem, int* plan_ctas,
+                               size_t* plan_smem, int* active_clusters) {
+  if (active_clusters) {
+    if (ctas < 1 || ctas > 16) return fail(s, SW_ERR_INVALID_ARG, "ctas out of range");
+    *active_clusters = cluster_pcg_active(precision, ctas, smem);
+  }
+  if (s) {
+    if (plan_ctas) *plan_ctas = s->cplan_ctas;
+    if (plan_smem) *plan_smem = s->cplan_smem;
+  }
   return SW_OK;
 }

@@ -6,7 +6,9 @@
 // has a tensor map of its depth image (width a multiple of 4, so that rows
 // are 16-byte aligned): a 40x10 box starting 4 columns and 1 row before the
 // tile, so the box's first column stays on a 16-byte boundary, and reading
-// zeros (= no depth) outside the image; else plain loads.  Writes V (x y z,
+// zeros (= no depth) outside the image; else plain loads (and plain loads
+// too if the copy's bounded wait runs out, which sets kStatusDepthTimeout:
+// the maps are still right, the host reports the wait).  Writes V (x y z,
 // confidence) and N (nx ny nz, radius) as float4; confidence 0 marks a pixel
 // that is not a usable depth surfel (depth <= 0, image border, a neighbour
 // without depth, or a zero cross product).
@@ -24,9 +26,27 @@ constexpr unsigned kBoxBytes = BX * BY * sizeof(float);
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// failure injection for the test of the bounded wait below: kFaultDepthTma
+// withholds the copies (read at every launch)
+__device__ int g_depth_fault;
+
+// Bounded wait for phase 0 of the tile's mbarrier; true if it completed.
+__device__ __forceinline__ bool wait_box(unsigned b) {
+  unsigned done = 0;
+  for (int spins = 0; spins < (1 << 16) && !done; ++spins) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(b), "r"(0u)
+        : "memory");
+  }
+  return __syncthreads_and(done != 0) != 0;
+}
+
 // One TMA copy of the tile's box into shared memory, completed on an
 // mbarrier; false if it did not complete within a bounded wait.
-__device__ __forceinline__ bool tma_load_box(float (*box)[BX], unsigned long long* bar, const void* tmap, int x, int y) {
+__device__ __forceinline__ bool tma_load_box(float (*box)[BX], unsigned long long* bar, const void* tmap, int x, int y,
+                                             bool issue) {
   const unsigned b = smem_u32(bar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
@@ -38,21 +58,14 @@ __device__ __forceinline__ bool tma_load_box(float (*box)[BX], unsigned long lon
     unsigned long long state;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(state) : "r"(b), "r"(kBoxBytes) : "memory");
     (void)state;
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(&box[0][0])),
-        "l"(tmap), "r"(x), "r"(y), "r"(b)
-        : "memory");
+    if (issue)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              smem_u32(&box[0][0])),
+          "l"(tmap), "r"(x), "r"(y), "r"(b)
+          : "memory");
   }
-  unsigned done = 0;
-  for (int spins = 0; spins < (1 << 16) && !done; ++spins) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(b), "r"(0u)
-        : "memory");
-  }
-  return __syncthreads_and(done != 0) != 0;
+  return wait_box(b);
 }
 
 __global__ void __launch_bounds__(TX * TY) k_depth_maps(Batch bt) {
@@ -69,8 +82,15 @@ __global__ void __launch_bounds__(TX * TY) k_depth_maps(Batch bt) {
   bool staged = false;
   if (d.depth_tmap) {
     // x0 is a multiple of 32, so x0 - BOX_X0 is a multiple of 4 (16 bytes)
-    staged = tma_load_box(box, &bar, d.depth_tmap, x0 - BOX_X0, y0 - 1);
-    if (!staged && threadIdx.x == 0) atomicOr(d.status, kStatusTimeout);
+    const bool issue = g_depth_fault != kFaultDepthTma;
+    staged = tma_load_box(box, &bar, d.depth_tmap, x0 - BOX_X0, y0 - 1, issue);
+    if (!staged) {
+      if (threadIdx.x == 0) atomicOr(d.status, kStatusDepthTimeout);
+      // a copy still in flight writes the same values the plain loads
+      // below do; wait for it once more (bounded) so that none is left
+      // running when the CTA ends
+      if (issue) wait_box(smem_u32(&bar));
+    }
   }
   if (!staged) {   // plain loads into the same layout
     for (int i = threadIdx.x; i < BX * BY; i += TX * TY) {
@@ -120,6 +140,8 @@ __global__ void __launch_bounds__(TX * TY) k_depth_maps(Batch bt) {
 }
 
 }  // namespace
+
+void set_depth_wait_fault(int kind) { cudaMemcpyToSymbol(g_depth_fault, &kind, sizeof(int)); }
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st) {
   const int n = b.total_tiles[kTilePixels];

@@ -32,69 +32,18 @@
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 #include "sw_df.cuh"
+#include "sw_pcg.cuh"
 
 namespace sw {
 namespace {
 
-// ------------------------------------------------------------------ accumulators
-
-// Operations the PCG needs from an accumulator type.  TwoSum's error term is
-// exact, so df_add(a, b) == df_add(b, a) bit for bit and every lane of a
-// butterfly ends with the same value; the same holds for FP64 addition.
-template <typename Acc>
-struct AccOps;
-
-template <>
-struct AccOps<DF> {
-  static __device__ __forceinline__ DF zero() { return DF{0.f, 0.f}; }
-  static __device__ __forceinline__ DF prod(float a, float b) { return df_prod(a, b); }
-  static __device__ __forceinline__ DF add(DF a, DF b) { return df_add(a, b); }
-  static __device__ __forceinline__ DF shfl_xor(DF v, int o) {
-    return DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-  }
-  static __device__ __forceinline__ unsigned long long bits(DF v) {
-    return (unsigned long long)__float_as_uint(v.hi) | ((unsigned long long)__float_as_uint(v.lo) << 32);
-  }
-  static __device__ __forceinline__ DF from_bits(unsigned long long b) {
-    return DF{__uint_as_float((unsigned)(b & 0xffffffffu)), __uint_as_float((unsigned)(b >> 32))};
-  }
-  static __device__ __forceinline__ bool nonzero(DF v) { return v.hi != 0.f; }
-  static __device__ __forceinline__ double value(DF v) { return (double)v.hi + (double)v.lo; }
-};
-
-template <>
-struct AccOps<double> {
-  static __device__ __forceinline__ double zero() { return 0.0; }
-  static __device__ __forceinline__ double prod(float a, float b) { return (double)a * (double)b; }   // exact
-  static __device__ __forceinline__ double prod(double a, double b) { return a * b; }
-  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-  static __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-  static __device__ __forceinline__ unsigned long long bits(double v) { return (unsigned long long)__double_as_longlong(v); }
-  static __device__ __forceinline__ double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
-  static __device__ __forceinline__ bool nonzero(double v) { return v != 0.0; }
-  static __device__ __forceinline__ double value(double v) { return v; }
-};
-
-template <typename Acc>
-__device__ __forceinline__ Acc warp_sum_acc(Acc v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = AccOps<Acc>::add(v, AccOps<Acc>::shfl_xor(v, o));
-  return v;
-}
-
-// a / b for positive FP64 values, rounded to FP32: the exponents are split
-// off exactly (frexp) and only the mantissa ratio is divided, in FP32 (an
-// FP64 division is several hundred cycles on this part).
-__device__ __forceinline__ float ratio_f32(double a, double b) {
-  int ea, eb;
-  const double ma = frexp(a, &ea), mb = frexp(b, &eb);
-  return ldexpf(__fdiv_rn((float)ma, (float)mb), ea - eb);
-}
+// failure injection for the tests of the bounded waits: {WaitFault kind,
+// poll limit that replaces the launch's (0: the launch's)}; read at every
+// launch, so captured graphs follow the current setting
+__device__ int g_wait_fault[2];
 
 // ------------------------------------------------------------------ 6x6 blocks
 
-__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }   // packed, r >= c
-__device__ __forceinline__ int sym(int r, int c) { return r >= c ? tri(r, c) : tri(c, r); }
 
 // 1/x for a positive FP64 x: the FP32 reciprocal as the seed, refined by
 // kSteps Newton-Raphson steps r <- r + r (1 - x r), each of which about
@@ -309,9 +258,13 @@ __device__ __forceinline__ Real warp_sum_r(Real v) {
 // Two values, tagged: CTA t writes each value's two 32-bit halves as tagged
 // words into slots 2t and 2t+1 of the generation's half of `part`
 // (2 kMaxCtaPerStream slots per parity); pollers check all four tags at once.
+// A tag is the generation's low 31 bits; its top bit says that the
+// publishing CTA's wait for a neighbour's vector ran out (*late nonzero),
+// and on_total(a, b, any_late) learns whether any CTA of the stream was late.
 template <typename Acc, typename F>
 __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, PartSlot* part, int t, int gs,
-                                                   unsigned long long gen, int spin_limit, F&& on_total) {
+                                                   unsigned long long gen, int spin_limit, bool publish,
+                                                   const int* late, F&& on_total) {
   using O = AccOps<Acc>;
   __shared__ Acc s_w[2][32];
   __shared__ int s_ok;
@@ -323,18 +276,21 @@ __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, Pa
   if (lane == 0) { s_w[0][wid] = va; s_w[1][wid] = vb; }
   __syncthreads();
   PartSlot* buf = part + (gen & 1ull) * 2 * kMaxCtaPerStream;
-  const unsigned tag = (unsigned)gen;
+  constexpr unsigned kLateBit = 0x80000000u;
+  const unsigned tag = (unsigned)gen & ~kLateBit;
   if (wid == 0) {
     Acc a = lane < nw ? s_w[0][lane] : O::zero();
     Acc b = lane < nw ? s_w[1][lane] : O::zero();
     a = warp_sum_acc(a);
     b = warp_sum_acc(b);
-    if (lane == 0) {
+    if (lane == 0 && publish) {   // (publish is false only under failure injection)
       const unsigned long long ba = O::bits(a), bb = O::bits(b);
-      st_relaxed_v2(&buf[2 * t].v, tagged((unsigned)ba, tag), tagged((unsigned)(ba >> 32), tag));
-      st_relaxed_v2(&buf[2 * t + 1].v, tagged((unsigned)bb, tag), tagged((unsigned)(bb >> 32), tag));
+      const unsigned tg = tag | (*late ? kLateBit : 0u);
+      st_relaxed_v2(&buf[2 * t].v, tagged((unsigned)ba, tg), tagged((unsigned)(ba >> 32), tg));
+      st_relaxed_v2(&buf[2 * t + 1].v, tagged((unsigned)bb, tg), tagged((unsigned)(bb >> 32), tg));
     }
     int ok = 1;
+    unsigned any_late = 0;
     Acc ca = O::zero(), cb = O::zero();
     for (int k = lane; k < gs; k += 32) {
       ulonglong2 wa, wb;
@@ -342,19 +298,24 @@ __device__ __forceinline__ bool stream_reduce_pair(Acc va, Acc vb, int lanes, Pa
       for (;;) {
         wa = ld_relaxed_v2(&buf[2 * k].v);
         wb = ld_relaxed_v2(&buf[2 * k + 1].v);
-        if (((tag_of(wa.x) ^ tag) | (tag_of(wa.y) ^ tag) | (tag_of(wb.x) ^ tag) | (tag_of(wb.y) ^ tag)) == 0) break;
+        const unsigned m = ~kLateBit;
+        if ((((tag_of(wa.x) & m) ^ tag) | ((tag_of(wa.y) & m) ^ tag) | ((tag_of(wb.x) & m) ^ tag) |
+             ((tag_of(wb.y) & m) ^ tag)) == 0)
+          break;
         if (++spins > spin_limit) { ok = 0; break; }
       }
       if (!ok) break;
+      any_late |= tag_of(wa.x) & kLateBit;
       ca = O::add(ca, O::from_bits((wa.x & 0xffffffffull) | (wa.y << 32)));
       cb = O::add(cb, O::from_bits((wb.x & 0xffffffffull) | (wb.y << 32)));
     }
     ok = __all_sync(0xffffffffu, ok);
+    any_late = __any_sync(0xffffffffu, any_late != 0);
     ca = warp_sum_acc(ca);
     cb = warp_sum_acc(cb);
     if (lane == 0) {
       s_ok = ok;
-      on_total(ca, cb);
+      on_total(ca, cb, any_late != 0);
     }
   }
   __syncthreads();
@@ -383,7 +344,8 @@ __device__ __forceinline__ void block_add_value(Acc v, int lanes, double* dst) {
 // pollers take acquire loads of the stamps.
 template <typename Acc, typename F>
 __device__ __forceinline__ bool stream_reduce_fenced(Acc v, int lanes, PartSlot* part, int t, int gs,
-                                                     unsigned long long gen, int spin_limit, F&& on_total) {
+                                                     unsigned long long gen, int spin_limit, bool publish,
+                                                     F&& on_total) {
   using O = AccOps<Acc>;
   __shared__ Acc s_w[32];
   __shared__ int s_ok;
@@ -395,7 +357,7 @@ __device__ __forceinline__ bool stream_reduce_fenced(Acc v, int lanes, PartSlot*
   if (wid == 0) {
     Acc b = lane < nw ? s_w[lane] : O::zero();
     b = warp_sum_acc(b);
-    if (lane == 0) {
+    if (lane == 0 && publish) {   // (publish is false only under failure injection)
       buf[t].v = O::bits(b);
       fence_acq_rel_gpu();
       st_relaxed_u64(&buf[t].gen, gen);
@@ -433,18 +395,6 @@ struct Scalars {
   int work;    // rᵀM⁻¹r != 0 and no breakdown
   int bad;     // breakdown seen
 };
-
-template <typename Acc>
-__device__ __forceinline__ Acc acc_nan() {
-  if constexpr (std::is_same<Acc, DF>::value) return DF{__int_as_float(0x7fffffff), 0.f};
-  else return __longlong_as_double(0x7ff8000000000000ll);
-}
-
-template <typename Acc>
-__device__ __forceinline__ bool acc_is_nan(Acc a) {
-  if constexpr (std::is_same<Acc, DF>::value) return a.hi != a.hi;
-  else return a != a;
-}
 
 // How the SpMV reaches the matrix (chosen per batch by what fits in shared
 // memory):
@@ -571,7 +521,7 @@ enum { kX = 0, kR, kZ, kP, kQ, kRowVecs };
 
 template <int kMode>
 __global__ void __launch_bounds__(kPcgThreads, 1)
-k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+k_pcg_f64(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) {
   using Acc = double;
   using O = AccOps<Acc>;
   constexpr bool kStaged = kMode != kSpmvRows;
@@ -580,6 +530,8 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
   const SwDev d = bt.devs[s];
   const int t = blockIdx.x - __ldg(bt.tile_base + s);
   const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
+  const int spin_limit = g_wait_fault[1] > 0 ? g_wait_fault[1] : spin_arg;
+  const bool withhold_first = g_wait_fault[0] == kFaultPcgPartial && s == 0 && t == 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d.n_n;
   const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
@@ -632,7 +584,7 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
   }
   if (broken) pa = acc_nan<Acc>();   // reaches every CTA through the first reduction
   if constexpr (kStaged) stage_entries<kMode>(d, A, t, Gs, nr, ent_cap, sA, sj, sent, soff, 0);
-  if (!stream_reduce_fenced(pa, 32, d.part, t, Gs, base + 1, spin_limit, [&](Acc rz) {
+  if (!stream_reduce_fenced(pa, 32, d.part, t, Gs, base + 1, spin_limit, !withhold_first, [&](Acc rz) {
         sc.rz = rz;
         sc.bad = acc_is_nan(rz);
         sc.work = !sc.bad && O::nonzero(rz);
@@ -698,7 +650,7 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
         }
       }
     }
-    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 2 + 2 * k, spin_limit, [&](Acc pq) {
+    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 2 + 2 * k, spin_limit, true, [&](Acc pq) {
           if (!sc.work) return;
           if (!(pq > 0.0)) {   // pᵀAp <= 0: nothing moves from here on
             sc.bad = 1;
@@ -734,7 +686,7 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap)
         __syncwarp();
       }
     }
-    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 3 + 2 * k, spin_limit, [&](Acc rz) {
+    if (!stream_reduce_fenced(pa, 8, d.part, t, Gs, base + 3 + 2 * k, spin_limit, true, [&](Acc rz) {
           if (!sc.work) return;
           sc.beta = rz / sc.rz;
           sc.rz = rz;
@@ -781,7 +733,7 @@ enum { kGx = 0, kGr, kGu, kGw, kGp, kGs, kGearVecs };
 
 template <typename Acc, int kMode>
 __global__ void __launch_bounds__(kPcgThreads, 1)
-k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap) {
+k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) {
   using O = AccOps<Acc>;
   using Real = float;
   constexpr bool kStaged = kMode != kSpmvRows;
@@ -790,6 +742,10 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
   const SwDev d = bt.devs[s];
   const int t = blockIdx.x - __ldg(bt.tile_base + s);
   const int Gs = __ldg(bt.tile_base + s + 1) - __ldg(bt.tile_base + s);
+  // failure injection (tests only): CTA 1 of the first stream withholds its
+  // first partial or its rows' first u, and the waits get a small poll limit
+  const int fault = (s == 0 && t == 1) ? g_wait_fault[0] : kFaultNone;
+  const int spin_limit = g_wait_fault[1] > 0 ? g_wait_fault[1] : spin_arg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d.n_n;
   const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
@@ -843,7 +799,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
         V(kGx, a)[c] = 0;
         V(kGp, a)[c] = 0;
         V(kGs, a)[c] = 0;
-        put_tagged(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
+        if (fault != kFaultPcgVector) put_tagged(ub[0], 6 * (size_t)j + c, u, (unsigned)(base + 1));
       }
     }
   } else if constexpr (kStaged) {
@@ -945,10 +901,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
         }
       }
     }
-    if (late) {   // every CTA stops iterating; the host gets a timeout
-      s_late = 1;
-      pg = acc_nan<Acc>();
-    }
+    if (late) s_late = 1;   // every CTA stops iterating; the host gets a timeout
     if (last) {
       // the final γ is only a statistic: each CTA adds its share with one
       // FP64 atomic and nobody waits (the order of the additions varies)
@@ -956,41 +909,18 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
       break;
     }
     // ---- one reduction: γ and δ together
-    if (!stream_reduce_pair(pg, pd, k == 0 ? 32 : 8, d.part, t, Gs, base + 1 + k, spin_limit, [&](Acc g, Acc dl) {
+    if (!stream_reduce_pair(pg, pd, k == 0 ? 32 : 8, d.part, t, Gs, base + 1 + k, spin_limit,
+                            !(k == 0 && fault == kFaultPcgPartial), &s_late, [&](Acc g, Acc dl, bool any_late) {
           if (!sc.work) return;
-          if (acc_is_nan(g) || acc_is_nan(dl)) {
+          Real alpha, beta;
+          const int step = any_late ? kGearLate : gear_step(k, g, dl, s_gprev, s_aprev, &alpha, &beta);
+          if (step == kGearBreakdown || step == kGearLate) {   // nothing moves from here on
             sc.bad = 1; sc.work = 0;
-            atomicOr(d.status, kStatusBreakdown);
+            atomicOr(d.status, step == kGearLate ? kStatusTimeout : kStatusBreakdown);
             return;
           }
           sc.rz = g;
-          if (!O::nonzero(g)) { sc.work = 0; return; }   // r = 0: converged exactly
-          Real beta = 0;
-          bool pos;
-          Real alpha;
-          if constexpr (std::is_same<Acc, DF>::value) {
-            float den = dl.hi;
-            if (k > 0) {
-              beta = __fdiv_rn(g.hi, s_gprev.hi);
-              const float tt = __fmul_rn(beta, __fdiv_rn(g.hi, s_aprev));
-              den = df_add(dl, DF{-tt, 0.f}).hi;
-            }
-            pos = den > 0.f;
-            alpha = pos ? __fdiv_rn(g.hi, den) : 0.f;
-          } else {
-            double den = dl;
-            if (k > 0) {
-              beta = ratio_f32(g, s_gprev);
-              den = dl - (double)beta * (double)ratio_f32(g, (double)s_aprev);
-            }
-            pos = den > 0.0;
-            alpha = pos ? ratio_f32(g, den) : 0.f;
-          }
-          if (!pos) {   // pᵀAp <= 0: nothing moves from here on
-            sc.bad = 1; sc.work = 0;
-            atomicOr(d.status, kStatusBreakdown);
-            return;
-          }
+          if (step == kGearConverged) { sc.work = 0; return; }
           sc.alpha = alpha;
           sc.beta = beta;
           s_aprev = alpha;
@@ -1044,44 +974,6 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_limit, int rows_cap, int ent_cap
     apply_increment(q0, qe, xi);
     d.dq[2 * j] = q0;
     d.dq[2 * j + 1] = qe;
-  }
-}
-
-// ------------------------------------------------------------------ timeout probe
-
-// Counter barrier over all CTAs of a cooperative launch, with a bounded wait.
-__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned nblocks, int spin_limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &gb->gen;
-    const unsigned g = *vgen;
-    int ok = 1;
-    __threadfence();
-    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      int spins = 0;
-      while (*vgen == g) {
-        if (++spins > spin_limit) { ok = 0; break; }
-        if (spins > 64) __nanosleep(32);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// A grid barrier that never completes when fewer CTAs run than it expects:
-// used to check that a wait which cannot finish ends by its bound and reports
-// a status the host can read.
-__global__ void k_barrier_probe(GridBarrier* gb, unsigned expected, int spin_limit, int* status) {
-  if (!grid_sync(gb, expected, spin_limit)) {
-    if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   }
 }
 
@@ -1143,6 +1035,11 @@ const void* pcg_kernel(int precision, int mode) {
 }
 
 }  // namespace
+
+void set_pcg_wait_fault(int kind, int spin_limit) {
+  const int v[2] = {kind, spin_limit};
+  cudaMemcpyToSymbol(g_wait_fault, v, sizeof(v));
+}
 
 int pcg_blocks_per_sm(int precision) {
   int n = 0;
@@ -1211,22 +1108,6 @@ cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void
   else
     k_debug_block_inverse<float><<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
   return cudaGetLastError();
-}
-
-cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
-                                 int* status, cudaStream_t st) {
-  unsigned expected = (unsigned)nblocks_expected;
-  void* args[] = {&gb, &expected, &spin_limit, &status};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nblocks_launched);
-  cfg.blockDim = dim3(32);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(k_barrier_probe), args);
 }
 
 }  // namespace sw

@@ -1,0 +1,754 @@
+// K7+K8 on one thread-block cluster per stream: block-Jacobi preconditioned
+// conjugate gradients on JᵀJ Δ = −Jᵀe (Sec. 7's linear solve, x₀ = 0,
+// exactly K iterations, stopping early only when rᵀM⁻¹r is exactly zero) and
+// the node update T_j ← Δ_j T_j, for streams whose system fits the cluster's
+// shared memory (FP32 modes).
+//
+// Why a cluster.  The solve is small (2048 nodes: 12,288 unknowns, ~17k
+// upper 6x6 blocks) and each iteration needs every CTA to agree on two inner
+// products, so it is bound by synchronisation, not by HBM.  Here the C CTAs
+// of a cluster (C = 16, one per SM, 768 threads each) keep the whole system
+// in their shared memory, exchange what they share through distributed
+// shared memory, and synchronise with the hardware cluster barrier
+// (barrier.cluster arrive.release / wait.acquire): nothing of the iteration
+// goes through global memory and nothing polls.
+//
+// Work split.  The host partitions the nodes into C contiguous ranges of
+// their Morton order (a spatially compact share per CTA, balanced by shared
+// memory bytes) and gives every upper block (i, j), i <= j, to the CTA that
+// owns row i (its "home").  A home block serves both halves of the
+// symmetric product: y_i += A_ij u_j and, off the diagonal, y_j += A_ijᵀ u_i.
+// Within a CTA, a group of 8 lanes serves up to two rows (the second row of
+// group g is row 2 G − 1 − g of the CTA's cost-sorted order, G groups, so
+// that the dearest row pairs with the cheapest); lane c < 6 of the group
+// keeps component c of the row's r in a register, and x, p, s sit in shared
+// memory.
+//
+// Exchange, all by the producer into the consumer's shared memory (remote
+// stores: st.shared::cluster), so that every read on the critical path is a
+// local one:
+//   u     each owner writes its rows' new u into the halo slots of the CTAs
+//         whose home blocks reference them (a push list per row);
+//   A_ijᵀ u_i  each home block writes its transposed product into a receive
+//         slot of row j's owner, which sums its slots in a fixed order, so
+//         the sums, and the solve, are deterministic;
+//   γ, δ  each CTA writes its two partial sums into slot `me` of every CTA.
+// One iteration (Chronopoulos-Gear: u = M⁻¹r and w = A u formed, γ = (r, u)
+// and δ = (w, u) from one reduction, p and s = A p by recurrence):
+//   A  w's home part from the local u and halo, the transposed products out,
+//      δ's share blockwise as uᵀA u (each off-diagonal block counts twice),
+//      γ's share from the previous step, the partials out;
+//                                                   -> cluster barrier
+//   B  every CTA sums the C partials in the same order and takes the same
+//      step (α, β); own rows add their received products, then p = u + βp,
+//      s = w + βs, x += αp, r −= αs, u = M⁻¹r, u out, γ's next share;
+//                                                   -> cluster barrier
+// Every CTA takes the same decisions from bit-identical totals, so all of
+// them pass the same barriers and leave the loop together; after the last
+// barrier no CTA touches another's shared memory.
+#include <algorithm>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "sw_internal.h"
+#include "sw_math.cuh"
+#include "sw_pcg.cuh"
+
+namespace sw {
+
+namespace {
+
+constexpr int kCThreads = 768;                 // 24 warps: 80 registers a thread
+constexpr int kGroup = 8;                      // lanes per row group
+constexpr int kGroups = kCThreads / kGroup;    // 96
+constexpr int kMaxRowsPerCta = 2 * kGroups;    // two rows per group at most
+constexpr int kMaxCluster = 16;
+
+// ------------------------------------------------------------------ the plan (host-built, device-resident)
+
+// int buffer: header {C, NR, NB, NG, n_n, NH, NP}; per CTA prefix tables
+// (C + 1 each) of rows, home blocks, receive slots and u pushes; then
+//   rows  [n_n]        the CTAs' rows (global node ids) in local order
+//   hb    [n_n + C]    per CTA, its rows' home-block offsets (nr + 1)
+//   go    [n_n + C]    per CTA, its rows' receive-slot offsets (nr + 1)
+//   po    [n_n + C]    per CTA, its rows' u-push offsets (nr + 1)
+//   blk   [nnzb]       per home block (CTA-major), its index in A
+//   col   [nnzb]       per home block, the local u slot of its column (own
+//                      row a, or halo slot nr + h)
+//   o2t   [nnzb]       per home block off the diagonal, (owner of its column
+//                      << 16) | receive slot there; -1 on the diagonal
+//   push  [total]      per u push, (peer CTA << 16) | the peer's u slot
+// NH and NP are the most halo rows and u pushes of a CTA.
+struct PlanOff {
+  int rb, bb, gb, pb, rows, hb, go, po, blk, col, o2t, push, total;
+};
+constexpr int kPlanHeader = 7;
+__host__ __device__ inline PlanOff plan_off(int C, int n_n, int nnzb, int n_push) {
+  PlanOff o{};
+  o.rb = kPlanHeader;
+  o.bb = o.rb + C + 1;
+  o.gb = o.bb + C + 1;
+  o.pb = o.gb + C + 1;
+  o.rows = o.pb + C + 1;
+  o.hb = o.rows + n_n;
+  o.go = o.hb + n_n + C;
+  o.po = o.go + n_n + C;
+  o.blk = o.po + n_n + C;
+  o.col = o.blk + nnzb;
+  o.o2t = o.col + nnzb;
+  o.push = o.o2t + nnzb;
+  o.total = o.push + n_push;
+  return o;
+}
+
+// shared memory of one CTA, sized by the largest share of any CTA, so that
+// the remotely written sections (partials, u, receive slots) sit at the same
+// offsets in every CTA
+struct SmemPlan {   // byte offsets
+  unsigned part, u, recv, a, col, o2t, mi, xps, hb, go, po, push, rows, total;
+};
+__host__ __device__ constexpr unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, int NP) {
+  SmemPlan L{};
+  L.part = 0;                                       // per sender CTA, its two partial sums (16 bytes)
+  L.u = 16u * kMaxCluster;                          // u of the own rows, then the halo: 8 floats each
+  L.recv = al16(L.u + 32u * (NR + NH));             // received A_ijᵀ u_i: 6 floats per slot
+  L.a = al16(L.recv + 24u * NG);                    // home blocks, 36 floats each, row-major
+  L.col = al16(L.a + 144u * NB);
+  L.o2t = al16(L.col + 4u * NB);
+  L.mi = al16(L.o2t + 4u * NB);                     // M⁻¹ of each row, packed lower (21 floats)
+  L.xps = al16(L.mi + 84u * NR);                    // x, p, s of each row (3 x 6 floats)
+  L.hb = al16(L.xps + 72u * NR);
+  L.go = al16(L.hb + 4u * (NR + 1));
+  L.po = al16(L.go + 4u * (NR + 1));
+  L.push = al16(L.po + 4u * (NR + 1));
+  L.rows = al16(L.push + 4u * NP);
+  L.total = al16(L.rows + 4u * NR);
+  return L;
+}
+
+// ------------------------------------------------------------------ distributed shared memory
+
+__device__ __forceinline__ unsigned cta_rank_in_cluster() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// the address of the same shared-memory location in CTA `rank` of the
+// cluster (a CTA's own addresses are valid cluster addresses as they are)
+__device__ __forceinline__ unsigned at_rank(unsigned a, unsigned rank, unsigned me) {
+  if (rank == me) return a;
+  unsigned r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cl_f4(unsigned a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cl_f2(unsigned a, float x, float y) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ void st_cl_u64x2(unsigned a, unsigned long long x, unsigned long long y) {
+  asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
+}
+// every thread of every CTA of the cluster: the shared-memory writes before
+// it, local and remote, are visible to every CTA's reads after it
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// sum of v over the 8 lanes of a group (every lane gets it)
+__device__ __forceinline__ float group_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// The CTA's sums of two accumulators (every thread holds shares), in a
+// fixed order; every lane of warp 0 returns them.
+template <typename Acc>
+__device__ __forceinline__ void cta_sum2(Acc& a, Acc& b, Acc (*s_w)[32]) {
+  using O = AccOps<Acc>;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  a = warp_sum_acc(a);
+  b = warp_sum_acc(b);
+  if (lane == 0) { s_w[0][wid] = a; s_w[1][wid] = b; }
+  __syncthreads();
+  if (wid == 0) {
+    constexpr int kWarps = kCThreads / 32;
+    a = lane < kWarps ? s_w[0][lane] : O::zero();
+    b = lane < kWarps ? s_w[1][lane] : O::zero();
+    a = warp_sum_acc(a);
+    b = warp_sum_acc(b);
+  }
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <typename Acc>
+__global__ void __launch_bounds__(kCThreads, 1)
+k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it) {
+  using O = AccOps<Acc>;
+  const unsigned me = cta_rank_in_cluster();
+  const int s = __ldg(members + blockIdx.x / C);
+  if (!stream_active(bt, s)) return;   // the whole cluster leaves together
+  const SwDev d = bt.devs[s];
+  const int* __restrict__ P = d.cplan;
+  const int NR = __ldg(P + 1), NB = __ldg(P + 2), NG = __ldg(P + 3), NH = __ldg(P + 5), NP = __ldg(P + 6);
+  const int n_push = __ldg(P + kPlanHeader + 4 * (C + 1) - 1);   // the push prefix table's last entry
+  const PlanOff off = plan_off(C, d.n_n, d.nnzb, n_push);
+  const int row0 = __ldg(P + off.rb + me), nr = __ldg(P + off.rb + me + 1) - row0;
+  const int blk0 = __ldg(P + off.bb + me);
+  const int push0 = __ldg(P + off.pb + me);
+  const SmemPlan L = smem_plan(NR, NB, NG, NH, NP);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* sPart = reinterpret_cast<Acc*>(smem_raw + L.part);   // [sender][2]
+  float* sU = reinterpret_cast<float*>(smem_raw + L.u);
+  float* sRecv = reinterpret_cast<float*>(smem_raw + L.recv);
+  float* sA = reinterpret_cast<float*>(smem_raw + L.a);
+  int* sCol = reinterpret_cast<int*>(smem_raw + L.col);
+  int* sO2t = reinterpret_cast<int*>(smem_raw + L.o2t);
+  float* sMi = reinterpret_cast<float*>(smem_raw + L.mi);
+  float* sXps = reinterpret_cast<float*>(smem_raw + L.xps);   // row a: x at 18a, p at 18a + 6, s at 18a + 12
+  int* sHb = reinterpret_cast<int*>(smem_raw + L.hb);
+  int* sGo = reinterpret_cast<int*>(smem_raw + L.go);
+  int* sPo = reinterpret_cast<int*>(smem_raw + L.po);
+  int* sPush = reinterpret_cast<int*>(smem_raw + L.push);
+  int* sRows = reinterpret_cast<int*>(smem_raw + L.rows);
+  __shared__ Acc s_w[2][32];
+  __shared__ float s_alpha, s_beta;
+  __shared__ int s_state;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = tid >> 3, gl = tid & 7;           // row group, lane in the group
+  const int gbase = lane & ~7;                    // the group's first lane in the warp
+  const bool comp = gl < 6;                       // this lane holds component gl of its rows
+  const unsigned uBase = smem_u32(sU), recvBase = smem_u32(sRecv), partBase = smem_u32(sPart);
+
+  // ---- set-up: the plan's tables, the home blocks and M⁻¹ into shared memory
+  for (int a = tid; a < nr; a += kCThreads) sRows[a] = __ldg(P + off.rows + row0 + a);
+  for (int a = tid; a <= nr; a += kCThreads) {
+    sHb[a] = __ldg(P + off.hb + row0 + me + a);
+    sGo[a] = __ldg(P + off.go + row0 + me + a);
+    sPo[a] = __ldg(P + off.po + row0 + me + a);
+  }
+  __syncthreads();
+  const int nb = sHb[nr], np = sPo[nr];
+  for (int x = tid; x < np; x += kCThreads) sPush[x] = __ldg(P + off.push + push0 + x);
+  for (int e = tid; e < nb; e += kCThreads) {
+    sCol[e] = __ldg(P + off.col + blk0 + e);
+    sO2t[e] = __ldg(P + off.o2t + blk0 + e);
+  }
+  {
+    const float4* A4 = reinterpret_cast<const float4*>(d.A);
+    float4* sA4 = reinterpret_cast<float4*>(sA);
+    const int* blk = P + off.blk + blk0;
+    // one block (9 float4) per thread per pass, its index read once
+    for (int e = tid; e < nb; e += kCThreads) {
+      const float4* src = A4 + (size_t)__ldg(blk + e) * 9;
+      float4 v[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = __ldg(src + q);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) sA4[9 * e + q] = v[q];
+    }
+  }
+  for (int t = tid; t < nr * 21; t += kCThreads) {
+    const int a = t / 21, q = t - 21 * a;
+    sMi[t] = __ldg(d.minv + 21 * (size_t)sRows[a] + q);
+  }
+  for (int t = tid; t < 18 * nr; t += kCThreads) sXps[t] = 0.f;
+  __syncthreads();
+
+  // rows of this group: a = g, and a = 2G − 1 − g
+  int arow[2];
+  arow[0] = g;
+  arow[1] = 2 * kGroups - 1 - g;
+  float rr[2] = {0.f, 0.f};   // component gl of the rows' r
+  Acc gam = O::zero();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int a = arow[h];
+    const bool on = a < nr;
+    const float* mi = sMi + 21 * (on ? a : 0);
+    const float r = (on && comp) ? -__ldg(d.g + 6 * (size_t)sRows[a] + gl) : 0.f;
+    float u = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float rk = __shfl_sync(0xffffffffu, r, gbase + k);
+      if (comp) u += mi[sym(gl, k)] * rk;
+    }
+    if (on && comp) {
+      rr[h] = r;
+      sU[8 * a + gl] = u;
+      // a diagonal block that is not positive definite (its inverse's first
+      // entry is a NaN) reaches every CTA through the first reduction
+      gam = (mi[0] != mi[0]) ? acc_nan<Acc>() : O::add(gam, O::prod(r, u));
+    }
+  }
+  __syncthreads();
+  cluster_barrier();   // every CTA runs: its shared memory may be written now
+
+  // u of the own rows out to the CTAs that hold them as halo (one lane per push)
+  auto push_u = [&]() {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = arow[h];
+      const bool on = a < nr;
+      const int x1 = on ? sPo[a + 1] : 0;
+      for (int x = (on ? sPo[a] : 0) + gl; x < x1; x += kGroup) {
+        const int tg = sPush[x];
+        const float4 v = *reinterpret_cast<const float4*>(sU + 8 * a);
+        const float2 w2 = *reinterpret_cast<const float2*>(sU + 8 * a + 4);
+        const unsigned ta = at_rank(uBase + 32u * (unsigned)(tg & 0xffff), (unsigned)(tg >> 16), me);
+        st_cl_f4(ta, v);
+        st_cl_f2(ta + 16, w2.x, w2.y);
+      }
+    }
+  };
+  push_u();
+  float a_prev = 1.f;     // warp 0, lane 0: the previous step's α and γ
+  Acc g_prev = O::zero();
+  int state = kGearOk;
+  cluster_barrier();   // every CTA's halo holds u₀
+
+  for (int k = 0; k < K; ++k) {
+    // ---- A: w's home part, the transposed products out, δ's share
+    Acc del = O::zero();
+    float wh[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = arow[h];
+      const bool on = a < nr;
+      const int e0 = on ? sHb[a] : 0, e1 = on ? sHb[a + 1] : 0;
+      float ui[6], o1[6];
+      {
+        const float4 v = *reinterpret_cast<const float4*>(sU + 8 * (on ? a : 0));
+        const float2 w2 = *reinterpret_cast<const float2*>(sU + 8 * (on ? a : 0) + 4);
+        ui[0] = v.x; ui[1] = v.y; ui[2] = v.z; ui[3] = v.w; ui[4] = w2.x; ui[5] = w2.y;
+      }
+#pragma unroll
+      for (int b = 0; b < 6; ++b) o1[b] = 0.f;
+      for (int e = e0 + gl; e < e1; e += kGroup) {
+        const int ci = sCol[e];
+        const float4 u4 = *reinterpret_cast<const float4*>(sU + 8 * ci);
+        const float2 u2 = *reinterpret_cast<const float2*>(sU + 8 * ci + 4);
+        const float uj[6] = {u4.x, u4.y, u4.z, u4.w, u2.x, u2.y};
+        const float4* A4 = reinterpret_cast<const float4*>(sA + 36 * (size_t)e);
+        float o2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float dt = 0.f;
+#pragma unroll
+        for (int bp = 0; bp < 3; ++bp) {   // rows 2bp and 2bp + 1 of the block
+          const float4 q0 = A4[3 * bp], q1 = A4[3 * bp + 1], q2 = A4[3 * bp + 2];
+          const float ra[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+          const float rb[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+          float ta = 0.f, tb = 0.f;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            ta += ra[c] * uj[c];
+            tb += rb[c] * uj[c];
+            o2[c] += ra[c] * ui[2 * bp] + rb[c] * ui[2 * bp + 1];
+          }
+          o1[2 * bp] += ta;
+          o1[2 * bp + 1] += tb;
+          dt += ui[2 * bp] * ta + ui[2 * bp + 1] * tb;
+        }
+        const bool diag = e == e0;   // the diagonal block leads its row
+        del = O::add(del, O::prod(dt, diag ? 1.f : 2.f));
+        if (!diag) {
+          const int tg = sO2t[e];
+          const unsigned ta = at_rank(recvBase + 24u * (unsigned)(tg & 0xffff), (unsigned)(tg >> 16), me);
+          st_cl_f2(ta, o2[0], o2[1]);
+          st_cl_f2(ta + 8, o2[2], o2[3]);
+          st_cl_f2(ta + 16, o2[4], o2[5]);
+        }
+      }
+      float mine = 0.f;
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        const float v = group_sum(o1[b]);
+        if (gl == b) mine = v;
+      }
+      wh[h] = mine;
+    }
+    Acc ga = gam, da = del;
+    cta_sum2(ga, da, s_w);
+    if (warp == 0 && lane < C)   // the CTA's partials into slot `me` of every CTA
+      st_cl_u64x2(at_rank(partBase + 16u * me, (unsigned)lane, me), O::bits(ga), O::bits(da));
+    cluster_barrier();   // 1: partials and transposed products delivered
+
+    // ---- B: the step, the received products, the update, u out
+    if (warp == 0) {
+      Acc gs = O::zero(), ds = O::zero();
+      if (lane < C) {
+        gs = sPart[2 * lane];
+        ds = sPart[2 * lane + 1];
+      }
+      gs = warp_sum_acc(gs);
+      ds = warp_sum_acc(ds);
+      if (lane == 0) {
+        float al, be;
+        const int st = gear_step(k, gs, ds, g_prev, a_prev, &al, &be);
+        s_state = st;
+        s_alpha = al;
+        s_beta = be;
+        a_prev = al;
+        g_prev = gs;
+      }
+    }
+    float wt[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = arow[h];
+      const bool on = a < nr;
+      const int x1 = on ? sGo[a + 1] : 0;
+      float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int x = (on ? sGo[a] : 0) + gl; x < x1; x += kGroup) {
+        const float2* v = reinterpret_cast<const float2*>(sRecv + 6 * (size_t)x);
+#pragma unroll
+        for (int hh = 0; hh < 3; ++hh) {
+          const float2 q = v[hh];
+          acc[2 * hh] += q.x;
+          acc[2 * hh + 1] += q.y;
+        }
+      }
+      float mine = 0.f;
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        const float v = group_sum(acc[b]);
+        if (gl == b) mine = v;
+      }
+      wt[h] = wh[h] + mine;
+    }
+    __syncthreads();
+    state = s_state;
+    if (state == kGearOk) {
+      const float al = s_alpha, be = s_beta;
+      gam = O::zero();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int a = arow[h];
+        const bool on = a < nr;
+        const float* mi = sMi + 21 * (on ? a : 0);
+        if (on && comp) {
+          float* xps = sXps + 18 * a + gl;
+          const float pc = sU[8 * a + gl] + be * xps[6];
+          const float sc = wt[h] + be * xps[12];
+          xps[6] = pc;
+          xps[12] = sc;
+          xps[0] += al * pc;
+          rr[h] -= al * sc;
+        }
+        float u = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+          const float rk = __shfl_sync(0xffffffffu, rr[h], gbase + kk);
+          if (comp) u += mi[sym(gl, kk)] * rk;
+        }
+        if (on && comp) {
+          sU[8 * a + gl] = u;
+          gam = O::add(gam, O::prod(rr[h], u));
+        }
+      }
+      __syncwarp();   // the group's six components of u written before its lanes push them
+      push_u();
+    }
+    cluster_barrier();   // 2: the new u delivered; partial and receive slots free again
+    if (state != kGearOk) break;
+  }
+
+  // ---- the final rᵀM⁻¹r (a statistic: one FP64 atomic per CTA, nobody waits)
+  if (state == kGearOk || state == kGearConverged) {
+    Acc ga = gam, zero = O::zero();
+    cta_sum2(ga, zero, s_w);
+    if (tid == 0) atomicAdd(d.pcg_rz + gn_it, O::value(ga));
+  }
+  if (state == kGearBreakdown) {
+    if (tid == 0 && me == 0) atomicOr(d.status, kStatusBreakdown);
+    return;
+  }
+  // ---- T_j ← Δ_j T_j for the own rows (nothing moves after a breakdown)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int a = arow[h];
+    if (a < nr && gl == 0) {
+      float xi[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) xi[c] = sXps[18 * a + c];
+      const int j = sRows[a];
+      float4 q0 = d.dq[2 * j], qe = d.dq[2 * j + 1];
+      apply_increment(q0, qe, xi);
+      d.dq[2 * j] = q0;
+      d.dq[2 * j + 1] = qe;
+    }
+  }
+}
+
+template <typename Acc>
+const void* cluster_kernel() {
+  return reinterpret_cast<const void*>(k_pcg_cluster<Acc>);
+}
+
+const void* cluster_kernel_for(int precision) {
+  return precision == SW_PRECISION_MIXED_F64DOTS ? cluster_kernel<double>() : cluster_kernel<DF>();
+}
+
+// The function attributes a launch of `smem` bytes in clusters of C needs.
+// The shared-memory limit only ever grows (per kernel and device), so a
+// query for a small plan never lowers what a large plan's launches rely on.
+cudaError_t prepare_cluster_kernel(const void* fn, int C, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set_to;   // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set_to[{fn, dev}];
+  if (smem > cur) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cur = smem;
+  }
+  if (C > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// Morton code of a point in the unit cube, 10 bits per axis
+uint32_t morton3(float x, float y, float z) {
+  auto spread = [](uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+  };
+  auto q = [](float t) { return (uint32_t)std::min(1023.f, std::max(0.f, t * 1023.f)); };
+  return spread(q(x)) | (spread(q(y)) << 1) | (spread(q(z)) << 2);
+}
+
+}  // namespace
+
+// The plan of one stream for clusters of C CTAs (see the file comment):
+// false if some CTA would need more than kMaxRowsPerCta rows or more than
+// smem_limit bytes of shared memory.
+bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const std::vector<int>& col,
+                        const std::vector<float>& node4, size_t smem_limit, std::vector<int>& plan,
+                        size_t* smem_out) {
+  if (C < 1 || C > kMaxCluster || n_n < 1 || (int)row_ptr.size() != n_n + 1) return false;
+  const int nnzb = row_ptr[n_n];
+  if ((int)col.size() != nnzb) return false;
+  // receive slots: the off-diagonal upper blocks of each column
+  std::vector<int> ng_col(n_n, 0);
+  for (int i = 0; i < n_n; ++i)
+    for (int b = row_ptr[i] + 1; b < row_ptr[i + 1]; ++b) ++ng_col[col[b]];
+  // Morton order of the node positions
+  float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+  for (int j = 0; j < n_n; ++j)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], node4[4 * j + a]);
+      hi[a] = std::max(hi[a], node4[4 * j + a]);
+    }
+  const float ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-12f});
+  std::vector<uint32_t> code(n_n);
+  for (int j = 0; j < n_n; ++j)
+    code[j] = morton3((node4[4 * j] - lo[0]) / ext, (node4[4 * j + 1] - lo[1]) / ext,
+                      (node4[4 * j + 2] - lo[2]) / ext);
+  std::vector<int> order(n_n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return code[a] < code[b]; });
+  // contiguous ranges of that order, balanced by shared-memory bytes
+  auto bytes = [&](int j) { return 160.0 + 180.0 * (row_ptr[j + 1] - row_ptr[j]) + 24.0 * ng_col[j]; };
+  double total = 0;
+  for (int j = 0; j < n_n; ++j) total += bytes(j);
+  std::vector<int> cut(C + 1, n_n);
+  cut[0] = 0;
+  {
+    double acc = 0;
+    int c = 1;
+    for (int t = 0; t < n_n && c < C; ++t) {
+      acc += bytes(order[t]);
+      if (acc >= total * c / C) cut[c++] = t + 1;
+    }
+  }
+  // per CTA: rows sorted by cost, placed so that group g serves positions g and 2G − 1 − g
+  std::vector<int> owner(n_n), local(n_n);
+  std::vector<std::vector<int>> rows(C);
+  int NR = 0;
+  for (int c = 0; c < C; ++c) {
+    std::vector<int> r(order.begin() + cut[c], order.begin() + cut[c + 1]);
+    if ((int)r.size() > kMaxRowsPerCta) return false;
+    auto cost = [&](int j) {
+      return (row_ptr[j + 1] - row_ptr[j] + kGroup - 1) / kGroup + (ng_col[j] + kGroup - 1) / kGroup;
+    };
+    std::stable_sort(r.begin(), r.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    for (size_t a = 0; a < r.size(); ++a) {
+      owner[r[a]] = c;
+      local[r[a]] = (int)a;
+    }
+    NR = std::max(NR, (int)r.size());
+    rows[c] = std::move(r);
+  }
+  // halos: per CTA, the other CTAs' rows its home blocks reference, in
+  // (owner, local row) order; each gets a u slot after the CTA's own rows
+  std::vector<std::map<int, int>> halo(C);   // CTA -> (global row -> u slot)
+  int NH = 0, NB = 0, NG = 0;
+  for (int c = 0; c < C; ++c) {
+    std::vector<std::pair<int, int>> ext_rows;
+    int nb = 0, ng = 0;
+    for (int i : rows[c]) {
+      nb += row_ptr[i + 1] - row_ptr[i];
+      ng += ng_col[i];
+      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b)
+        if (owner[col[b]] != c) ext_rows.push_back({owner[col[b]], local[col[b]]});
+    }
+    std::sort(ext_rows.begin(), ext_rows.end());
+    ext_rows.erase(std::unique(ext_rows.begin(), ext_rows.end()), ext_rows.end());
+    const int nr = (int)rows[c].size();
+    for (size_t h = 0; h < ext_rows.size(); ++h)
+      halo[c][rows[ext_rows[h].first][ext_rows[h].second]] = nr + (int)h;
+    NH = std::max(NH, (int)ext_rows.size());
+    NB = std::max(NB, nb);
+    NG = std::max(NG, ng);
+  }
+  // u pushes: per own row, the CTAs holding it as halo, with their slot
+  std::vector<std::vector<int>> pushes(n_n);
+  for (int c = 0; c < C; ++c)
+    for (const auto& kv : halo[c]) pushes[kv.first].push_back((c << 16) | kv.second);
+  int NP = 0, n_push = 0;
+  for (int c = 0; c < C; ++c) {
+    int np = 0;
+    for (int i : rows[c]) np += (int)pushes[i].size();
+    NP = std::max(NP, np);
+    n_push += np;
+  }
+  if (NB >= (1 << 16) || NG >= (1 << 16) || NR + NH >= (1 << 16)) return false;
+  const SmemPlan L = smem_plan(NR, NB, NG, NH, NP);
+  if (L.total > smem_limit) return false;
+  const PlanOff o = plan_off(C, n_n, nnzb, n_push);
+  plan.assign(o.total, 0);
+  plan[0] = C; plan[1] = NR; plan[2] = NB; plan[3] = NG; plan[4] = n_n; plan[5] = NH; plan[6] = NP;
+  // home block index of each block within its CTA
+  std::vector<int> home(nnzb, 0);
+  for (int c = 0; c < C; ++c) {
+    int e = 0;
+    for (int i : rows[c])
+      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) home[b] = e++;
+  }
+  // receive slots of each row j at its owner: its column's off-diagonal
+  // blocks (i, j) in (home CTA, home block index) order
+  std::vector<std::vector<std::pair<long long, int>>> incoming(n_n);   // (order key, block)
+  for (int i = 0; i < n_n; ++i)
+    for (int b = row_ptr[i] + 1; b < row_ptr[i + 1]; ++b)
+      incoming[col[b]].push_back({((long long)owner[i] << 32) | home[b], b});
+  std::vector<int> slot_of(nnzb, -1);
+  int rb = 0, bb = 0, gb = 0, pb = 0;
+  for (int c = 0; c < C; ++c) {
+    plan[o.rb + c] = rb;
+    plan[o.bb + c] = bb;
+    plan[o.gb + c] = gb;
+    plan[o.pb + c] = pb;
+    int e = 0, x = 0, y = 0;
+    for (size_t a = 0; a < rows[c].size(); ++a) {
+      const int i = rows[c][a];
+      plan[o.rows + rb + (int)a] = i;
+      plan[o.hb + rb + c + (int)a] = e;
+      plan[o.go + rb + c + (int)a] = x;
+      plan[o.po + rb + c + (int)a] = y;
+      e += row_ptr[i + 1] - row_ptr[i];
+      auto& inc = incoming[i];
+      std::sort(inc.begin(), inc.end());
+      for (const auto& kv : inc) slot_of[kv.second] = x++;
+      for (int tg : pushes[i]) plan[o.push + pb + y++] = tg;
+    }
+    const int nr = (int)rows[c].size();
+    plan[o.hb + rb + c + nr] = e;
+    plan[o.go + rb + c + nr] = x;
+    plan[o.po + rb + c + nr] = y;
+    rb += nr;
+    bb += e;
+    gb += x;
+    pb += y;
+  }
+  plan[o.rb + C] = rb;
+  plan[o.bb + C] = bb;
+  plan[o.gb + C] = gb;
+  plan[o.pb + C] = pb;
+  // per home block: A's index, its column's u slot, its transposed product's target
+  for (int c = 0; c < C; ++c) {
+    const int base = plan[o.bb + c];
+    for (int i : rows[c])
+      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        const int e = home[b], j = col[b];
+        plan[o.blk + base + e] = b;
+        plan[o.col + base + e] = owner[j] == c ? local[j] : halo[c].at(j);
+        plan[o.o2t + base + e] = b == row_ptr[i] ? -1 : ((owner[j] << 16) | slot_of[b]);
+      }
+  }
+  *smem_out = L.total;
+  return true;
+}
+
+// How many clusters of C CTAs with `smem` bytes each can run at once (0 if
+// none, or a negative CUDA error code).
+int cluster_pcg_active(int precision, int C, size_t smem) {
+  const void* fn = cluster_kernel_for(precision);
+  cudaError_t pe = prepare_cluster_kernel(fn, C, smem);
+  if (pe != cudaSuccess) {
+    cudaGetLastError();
+    return -(int)pe;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kCThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -(int)e;
+  }
+  return n;
+}
+
+bool cluster_pcg_fits(int precision, int C, size_t smem) { return cluster_pcg_active(precision, C, smem) >= 1; }
+
+cudaError_t launch_pcg_cluster(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st) {
+  if (b.n_cluster == 0) return cudaSuccess;
+  const int C = b.cluster_ctas;
+  const void* fn = cluster_kernel_for(b.precision);
+  const cudaError_t pe = prepare_cluster_kernel(fn, C, b.cluster_smem);
+  if (pe != cudaSuccess) return pe;
+  Batch bt = b.bt;
+  const int* members = b.cluster_members_dev;
+  int c = C, kk = pcg_iters, it = gn_it;
+  void* args[] = {&bt, &members, &c, &kk, &it};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * b.n_cluster);
+  cfg.blockDim = dim3(kCThreads);
+  cfg.dynamicSmemBytes = b.cluster_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+}  // namespace sw

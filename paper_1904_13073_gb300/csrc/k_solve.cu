@@ -86,7 +86,7 @@ __global__ void k_solve_begin(Batch bt) {
   for (int k = threadIdx.x; k < kMaxGn; k += blockDim.x) {
     d.e_depth[k] = 0.0; d.e_reg[k] = 0.0; d.n_corr[k] = 0; d.pcg_rz[k] = 0.0;
   }
-  if (threadIdx.x == 0) *d.status = 0;
+  if (threadIdx.x == 0) *d.status &= kStatusDepthTimeout;   // the solve's bits; the frame's depth stage keeps its own
 }
 
 // Threads [0, n8), n8 = 8 n_n rounded up to a whole warp: a group of 8

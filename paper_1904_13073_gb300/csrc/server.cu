@@ -19,6 +19,10 @@
 // other admitted streams.  Every stream's surfels, node graph and
 // warp field stay resident on the device between its frames.
 //
+// In the plain mode (sw_server_set_plain) each step instead takes the single
+// oldest queued frame and runs it through its stream's own calls, one stream
+// at a time: the reference that continuous batching is measured against.
+//
 // Each stream queues up to `queue_depth` frames in pinned host slots that the
 // submit call fills; a full queue refuses further frames (SW_ERR_NO_MEMORY)
 // until the worker drains it.
@@ -74,6 +78,7 @@ struct sw_server {
   int gn = 10, pcg = 20, qdepth = 4;
   double window_ms = 0.0;        // how long a step may wait for more streams' frames
   bool appending = false;        // sw_append_frame after every served frame
+  bool plain = false;            // one frame per step through its stream's own calls (no batching)
   std::chrono::steady_clock::time_point t0;
   int next_id = 1;
   std::map<int, SrvStream*> streams;    // every open stream, by id
@@ -199,7 +204,15 @@ void worker_main(sw_server* S) {
         S->cv.wait_for(lk, std::chrono::milliseconds(1));
         continue;
       }
-      if (S->window_ms > 0.0 && taken.size() < S->order.size()) {   // batching window
+      if (S->plain && taken.size() > 1) {   // one frame at a time: the oldest queued one
+        size_t best = 0;
+        for (size_t k = 1; k < taken.size(); ++k)
+          if (taken[k].submit_ms < taken[best].submit_ms) best = k;
+        taken = {taken[best]};
+        taken_ids = {taken_ids[best]};
+        taken_ptrs = {taken_ptrs[best]};
+      }
+      if (!S->plain && S->window_ms > 0.0 && taken.size() < S->order.size()) {   // batching window
         double oldest = taken[0].submit_ms;
         for (const Frame& f : taken) oldest = std::min(oldest, f.submit_ms);
         const double left = oldest + S->window_ms - now_ms(S->t0);
@@ -212,6 +225,22 @@ void worker_main(sw_server* S) {
     }
     std::lock_guard<std::mutex> g(S->gpu);
     sw_status status = SW_OK;
+    std::vector<sw_status> fstat(taken.size(), SW_OK);   // per taken frame
+    std::vector<sw_append_stats> app(taken.size());
+    std::vector<sw_status> app_status(taken.size(), SW_OK);
+    double t_start = 0.0;
+    if (S->plain) {
+      // the plain path: the frame's stream alone, through its own calls
+      SrvStream* s = taken_ptrs[0];
+      t_start = now_ms(S->t0);
+      sw_status st = sw_upload_depth(s->h, s->slots[taken[0].slot], 0, taken[0].frame_id);
+      if (st == SW_OK) st = sw_solve_frame(s->h, S->gn, S->pcg, nullptr);
+      if (st == SW_OK) st = sw_fuse_frame(s->h);
+      int nn = 0;
+      if (st == SW_OK) st = sw_read_nodes(s->h, nullptr, nullptr, 0, &nn);   // waits; reports a breakdown
+      fstat[0] = st;
+      if (S->appending && st == SW_OK) app_status[0] = sw_append_frame(s->h, &app[0]);
+    } else {
     if (S->composition_changed || !S->batch) {
       if (S->batch) sw_batch_destroy(S->batch);
       S->batch = nullptr;
@@ -232,34 +261,33 @@ void worker_main(sw_server* S) {
       frame_ids[pos] = taken[k].frame_id;
       active[pos] = 1;
     }
-    const double t_start = now_ms(S->t0);
+    t_start = now_ms(S->t0);
     if (status == SW_OK) status = sw_batch_set_active(S->batch, active.data());
     if (status == SW_OK) status = sw_batch_upload_depth(S->batch, depths.data(), 0, frame_ids.data());
     if (status == SW_OK) status = sw_batch_solve(S->batch, S->gn, S->pcg, nullptr);
     if (status == SW_OK) status = sw_batch_fuse(S->batch);
     std::vector<int> member_status(n, 0);
-    const sw_status sync = sw::batch_member_status(S->batch, member_status.data());
-    std::vector<sw_append_stats> app(taken.size());
-    std::vector<sw_status> app_status(taken.size(), SW_OK);
+    const sw_status sync = S->batch ? sw::batch_member_status(S->batch, member_status.data()) : status;
+    for (size_t k = 0; k < taken.size(); ++k) {
+      const int pos = (int)(std::find(S->batch_ids.begin(), S->batch_ids.end(), taken_ids[k]) - S->batch_ids.begin());
+      fstat[k] = status != SW_OK ? status : sync != SW_OK ? sync : (sw_status)member_status[pos];
+    }
     if (S->appending && status == SW_OK && sync == SW_OK)
-      for (size_t k = 0; k < taken.size(); ++k) {
-        const int pos = (int)(std::find(S->batch_ids.begin(), S->batch_ids.end(), taken_ids[k]) - S->batch_ids.begin());
-        if (member_status[pos] == SW_OK) app_status[k] = sw_append_frame(taken_ptrs[k]->h, &app[k]);
-      }
+      for (size_t k = 0; k < taken.size(); ++k)
+        if (fstat[k] == SW_OK) app_status[k] = sw_append_frame(taken_ptrs[k]->h, &app[k]);
+    }
     const double t_done = now_ms(S->t0);
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (size_t k = 0; k < taken.size(); ++k) {
         SrvStream* s = S->streams[taken_ids[k]];
-        const int pos = (int)(std::find(S->batch_ids.begin(), S->batch_ids.end(), taken_ids[k]) - S->batch_ids.begin());
         s->queue.pop_front();
         s->free_slots.push_back(taken[k].slot);
         s->frames_done++;
         sw_frame_result r{};
         r.stream = taken_ids[k];
         r.frame_id = taken[k].frame_id;
-        r.status = status != SW_OK ? status : sync != SW_OK ? sync
-                   : member_status[pos] != SW_OK ? member_status[pos] : app_status[k];
+        r.status = fstat[k] != SW_OK ? fstat[k] : app_status[k];
         if (S->appending && app_status[k] == SW_OK && r.status == SW_OK) s->n_s = app[k].n_surfels;
         r.appended = S->appending && r.status == SW_OK ? app[k].appended : 0;
         r.n_surfels = s->n_s;
@@ -439,5 +467,12 @@ sw_status sw_server_read_stats(sw_server_handle S, sw_server_stats* out) {
   std::lock_guard<std::mutex> lk(S->mu);
   *out = S->st;
   out->memory_in_use = sw_memory_in_use();
+  return SW_OK;
+}
+
+sw_status sw_server_set_plain(sw_server_handle S, int enable) {
+  if (!S || (enable != 0 && enable != 1)) return SW_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->plain = enable != 0;
   return SW_OK;
 }

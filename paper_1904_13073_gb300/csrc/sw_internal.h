@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/surfelwarp.h"
 
 namespace sw {
@@ -27,7 +29,22 @@ constexpr int kTargetEmptyWindow = -2;   // usable, and its window held no surfe
 
 // status bits written by kernels
 constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive definite, or pᵀAp <= 0
-constexpr int kStatusTimeout = 4;        // a bounded grid-barrier wait gave up
+constexpr int kStatusTimeout = 4;        // a bounded wait of the PCG (a reduction or a neighbour's vector) gave up
+constexpr int kStatusDepthTimeout = 8;   // the depth stage's bounded wait for its TMA tile gave up (the tile was
+                                         // then loaded with plain loads); cleared by the next depth upload
+
+// Failure injection for the tests of the bounded device waits
+// (sw_debug_inject_wait_fault): what a kernel withholds so that the waits
+// that depend on it must run out.  Each kernel file keeps its own device
+// copy of the setting, read at every launch.
+enum WaitFault {
+  kFaultNone = 0,
+  kFaultPcgPartial = 1,   // CTA 1 of the first stream does not publish its share of the PCG's first reduction
+  kFaultPcgVector = 2,    // CTA 1 of the first stream does not publish its rows' first PCG vector
+  kFaultDepthTma = 3,     // the depth tiles' TMA copies are not issued (their mbarrier waits run out)
+};
+void set_pcg_wait_fault(int kind, int spin_limit);   // k_pcg.cu
+void set_depth_wait_fault(int kind);                 // k_depth.cu
 
 // A CTA's partial of one reduction (the accumulator's bit pattern),
 // published with a generation stamp (release pattern: the value, a fence,
@@ -92,6 +109,7 @@ struct SwDev {
   struct PartSlot* part;   // 4 * kMaxCtaPerStream slots for the per-CTA partials of the PCG's reductions
   unsigned long long* xp;  // 12 n_n tagged words: the PCG's u = M⁻¹ r as other CTAs read it, by iteration parity
   unsigned long long* pcg_epoch;   // launches of the persistent PCG so far
+  const int* cplan;   // the cluster PCG's plan of this stream (k_pcg_cluster.cu), or null: the cooperative PCG
   // all-FP64 variant only (null otherwise): the system, the PCG's shared
   // vectors (u, m even, m odd) and the authoritative node transforms
   double* A64;        // nnzb * 36
@@ -132,11 +150,6 @@ __device__ __forceinline__ int find_stream(const Batch& bt, int b) {
 
 __device__ __forceinline__ bool stream_active(const Batch& bt, int s) { return !bt.active || __ldg(bt.active + s); }
 
-struct GridBarrier {   // counter barrier used by the timeout probe
-  unsigned int count;
-  unsigned int gen;
-};
-
 // ------------------------------------------------------------------ launchers
 
 enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTilePrecond,
@@ -152,6 +165,12 @@ struct BatchHost {
   int pcg_ent_cap;                  // most matrix entries (block-row terms) one PCG CTA owns
   int pcg_mode;                     // how the PCG's SpMV reaches the matrix (k_pcg.cu: SpmvMode)
   int any_visibility;               // some member predicts splat visibility
+  // members solved by the cluster PCG (k_pcg_cluster.cu): one cluster of
+  // cluster_ctas CTAs each, cluster_smem bytes of shared memory per CTA
+  int n_cluster;
+  int cluster_ctas;
+  size_t cluster_smem;
+  const int* cluster_members_dev;   // device, n_cluster stream indices
 };
 
 void launch_depth_maps(const BatchHost& b, cudaStream_t st);
@@ -177,6 +196,16 @@ void launch_vis_splat(const BatchHost& b, int from_live, cudaStream_t st);
 void launch_vis_mark(const BatchHost& b, int from_live, cudaStream_t st);
 void launch_fuse(const BatchHost& b, int select_only, cudaStream_t st);
 void launch_associate_only(const BatchHost& b, cudaStream_t st);
+// the cluster PCG (k_pcg_cluster.cu): the plan's host
+// build (false if the stream does not fit clusters of C CTAs with smem_limit
+// bytes each), whether such clusters can run, and the launch over the
+// batch's cluster members
+bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const std::vector<int>& col,
+                        const std::vector<float>& node4, size_t smem_limit, std::vector<int>& plan,
+                        size_t* smem_out);
+bool cluster_pcg_fits(int precision, int C, size_t smem);
+int cluster_pcg_active(int precision, int C, size_t smem);   // clusters that can run at once (< 0: CUDA error)
+cudaError_t launch_pcg_cluster(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
 int pcg_blocks_per_sm(int precision);
 int pcg_threads();
 size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
@@ -185,8 +214,6 @@ size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
 sw_status batch_member_status(sw_batch_handle b, int* status);
 // the PCG's 6x6 block inverse on n row-major blocks (float, or double with fp64), packed lower out
 cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void* out, int* ok, cudaStream_t st);
-cudaError_t launch_barrier_probe(GridBarrier* gb, int nblocks_launched, int nblocks_expected, int spin_limit,
-                                 int* status, cudaStream_t st);
 
 // ------------------------------------------------------------------ appending
 // Per-candidate records and scratch of the appending step (k_append.cu),

@@ -13,7 +13,7 @@ import synth
 import paper_1904_13073_gb300 as sw
 from oracle import solver as OS
 
-from gpu_helpers import Pair, ensure_built, rotation_angle_between
+from gpu_helpers import Pair, ensure_built, load_gpu_state_into_oracle, oracle_for, rotation_angle_between
 
 pytestmark = pytest.mark.gpu
 ROT_TOL = 1e-4
@@ -79,41 +79,71 @@ def test_fp64_variant_matches_oracle_closely():
     assert rot64 <= rot32 and trans64 <= trans32, errs
 
 
-@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_FP64])
-def test_small_sequence_solve_and_fuse_matches_oracle(precision):
-    """Bending sphere with outliers over three frames of solve + fusion.  The
-    FP64 variant repeats and stays within 1e-6 rad / 1e-7 m at every frame.
-    The mixed mode's FP32 assembly is not bitwise repeatable, and from the
-    second frame on a fusion or association decision that flips on that noise
-    changes a term (measured up to 2.3e-4 rad at the third frame on this
-    sphere), so after the first frame it gets 1e-3 rad / 2e-4 m."""
+def _report(name, data):
+    """Write a JSON report to $SW_REPORT_DIR when that is set."""
+    import json
+    import os
+    out = os.environ.get("SW_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, name), "w") as f:
+            json.dump(data, f, indent=1)
+
+
+@pytest.mark.parametrize("precision", [sw.SW_PRECISION_MIXED, sw.SW_PRECISION_MIXED_F64DOTS, sw.SW_PRECISION_FP64])
+def test_sequence_frames_match_oracle_on_identical_inputs(precision):
+    """Bending sphere with outliers over three frames of solve + fusion.
+
+    Every frame is compared on identical inputs: both sides take the same
+    FP32 depth maps, and before each solve the oracle takes the library's
+    own model (its fused surfels, skinning and node transforms, FP32 values;
+    load_gpu_state_into_oracle) -- after that model was compared with the
+    oracle's own fusion of the previous frame.  Each frame's warp field must
+    then agree to the configuration's 1e-4 rad / 1e-5 m (the FP64 variant to
+    1e-6 rad / 1e-7 m).  A second oracle stream runs the whole sequence on
+    its own inputs; its distance from the library after each frame (the
+    multi-frame drift, where an FP32 fusion decision that flips changes the
+    next frame's model) is reported, not asserted."""
     scene = synth.random_scene(seed=3, n_surfels=6000, n_nodes=48, outliers=0.01)
     p = Pair(scene, precision=precision)
+    free = oracle_for(scene)    # runs the sequence on its own inputs
+    tol = (1e-6, 1e-7) if precision == sw.SW_PRECISION_FP64 else (ROT_TOL, TRANS_TOL)
+    report = {"frames": []}
     try:
         for t in (1, 2, 3):
             p.upload(t)
             p.set_maps_from_oracle()   # identical FP32 depth maps on both sides
-            sw.sw_solve_frame(p.h, 3, 10)
-            p.o.solve_frame(3, 10)
+            load_gpu_state_into_oracle(p)
+            st = sw.sw_solve_frame(p.h, 3, 10)
+            ost = p.o.solve_frame(3, 10)
             rot, trans = _compare_nodes(p)
-            if precision == sw.SW_PRECISION_FP64:
-                assert rot <= 1e-6 and trans <= 1e-7, (t, rot, trans)
-            elif t == 1:
-                assert rot <= ROT_TOL and trans <= TRANS_TOL, (t, rot, trans)
-            else:
-                assert rot <= 1e-3 and trans <= 2e-4, (t, rot, trans)
+            flips = [int(st["n_corr"][k] - ost[k].n_corr) for k in range(3)]
+            free.upload_depth(scene.frame(t), t)
+            free.solve_frame(3, 10)
+            _, dq = sw.sw_read_nodes(p.h)
+            dq = dq.astype(np.float64)
+            drift_rot = float(rotation_angle_between(dq, free.node_dq).max())
+            drift_trans = float(np.linalg.norm(OS.node_transform(dq, free.node_p) - free.warped_nodes(),
+                                               axis=1).max())
+            report["frames"].append({"frame": t, "rot_err_rad": rot, "trans_err_m": trans,
+                                     "corr_count_diff": flips, "drift_rot_rad": drift_rot,
+                                     "drift_trans_m": drift_trans})
+            assert rot <= tol[0] and trans <= tol[1], (t, rot, trans)
             sw.sw_fuse_frame(p.h)
             n_fused = p.o.fuse_frame()
+            free.fuse_frame()
             v, n, tt = sw.sw_read_surfels(p.h)
             fused_gpu = tt[:, 1] == t
             fused_ora = p.o.t_obs == t
-            # a few fusion decisions may flip on 1-ulp differences of the warps
+            # a fusion decision may flip on a 1-ulp difference of the two warps
             assert np.sum(fused_gpu != fused_ora) <= max(3, n_fused // 200)
             both = fused_gpu & fused_ora
             assert np.max(np.abs(v[both, :3] - p.o.v_ref[both])) < 2e-5
             assert np.max(np.abs(n[both, 3] - p.o.conf[both])) < 1e-4
     finally:
         p.close()
+        _report(f"sequence_identical_inputs_prec{precision}.json", report)
+        print(report)
 
 
 def test_identity_zero_residual_gives_identity_update():
