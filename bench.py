@@ -325,14 +325,16 @@ def large_workload(n_models, frame_ids):
 
 
 def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_gb, gn, pcg, seed=0,
-               plain=False, wait_admission=True):
+               plain=False, wait_admission=True, adaptive=True):
     """The serving workload: n_regular streams of the uneven sizes (models
     reused from the uneven batch) plus n_large large ones, each submitting
     depth frames as a Poisson process of rate_hz (the same arrival trace for
     a given seed and rate); an eighth of the regular streams joins a third
     into the run and another eighth leaves at two thirds.  Frames go through
     the library's server: admission against the budget, then continuous
-    batching (plain=False) or the plain one-frame-at-a-time path
+    batching (plain=False; with adaptive, the server's default, a step runs
+    its frames one by one through their streams' own calls when its measured
+    times say that is cheaper) or the plain one-frame-at-a-time path
     (plain=True, sw_server_set_plain).  Latency is completion minus
     submission on the server's clock.  A frame refused because its stream's
     queue is full or the stream is not admitted yet is counted as dropped.
@@ -349,6 +351,7 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
     srv = sw.sw_server_create(int(budget_gb * (1 << 30)), gn, pcg, queue_depth=4)
     if plain:
         sw.sw_server_set_plain(srv, True)
+    sw.sw_server_set_adaptive(srv, adaptive)
     ids = {}
 
     def open_stream(k):
@@ -425,14 +428,16 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
     out = {"workload": f"{n_regular} streams of the uneven sizes + {n_large} large (640x480, 4096 nodes), "
                        f"Poisson arrivals at {rate_hz:.3g} Hz per stream for {seconds:g} s; "
                        f"{len(late)} join at 1/3, {len(leaving)} leave at 2/3; {gn} GN x {pcg} PCG + fusion",
-           "path": "plain (one frame at a time)" if plain else "continuous batching",
+           "path": "plain (one frame at a time)" if plain else
+                   "continuous batching, adaptive (batch or stream by stream per step)" if adaptive else
+                   "continuous batching (every step one batch)",
            "budget_gb": budget_gb, "frames_per_s": len(ok) / span_s, "offered_frames_per_s": offered,
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
            "frames_done": len(ok), "frames_failed": len(res) - len(ok), "frames_dropped": dropped,
            "drop_rate": dropped / max(1, dropped + sent),
            "mean_batch": float(np.mean([r["batch_size"] for r in ok])) if ok else 0.0,
-           "steps": int(stats["steps"]), "gpu_busy_frac": float(stats["busy_ms"]) / 1000.0 / max(span_s, 1e-9),
+           "steps": int(stats["steps"]), "steps_alone": int(stats["steps_alone"]), "gpu_busy_frac": float(stats["busy_ms"]) / 1000.0 / max(span_s, 1e-9),
            "streams": n, "memory_gb_at_end": stats["memory_in_use"] / float(1 << 30)}
     if samples:
         out["admitted_max"] = max(a for _, a, _ in samples)
@@ -443,15 +448,17 @@ def run_served(sw, members, large, n_regular, n_large, seconds, rate_hz, budget_
 
 def served_summary(r):
     return {k: r[k] for k in ("frames_per_s", "offered_frames_per_s", "latency_ms", "frames_done", "frames_dropped",
-                              "drop_rate", "mean_batch", "gpu_busy_frac")}
+                              "drop_rate", "mean_batch", "steps", "steps_alone", "gpu_busy_frac")}
 
 
 def run_served_sweep(sw, members, large, args, gn, pcg):
     """Continuous batching against the plain server on the same arrival
     traces: the saturating point first (its served frames/s is the batched
     capacity), then offered loads of 25, 50 and 75% of that capacity for
-    both paths, and one run whose memory budget admits only part of the
-    streams at a time (admission binds; the arrivals do not wait for it)."""
+    the adaptive server (the default), the server that batches every step,
+    and the plain one, and one run whose memory budget admits only part of
+    the streams at a time (admission binds; the arrivals do not wait for
+    it)."""
     n_streams = args.served_streams + args.served_large
     sat = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
                      args.served_rate, args.served_budget_gb, gn, pcg)
@@ -461,10 +468,13 @@ def run_served_sweep(sw, members, large, args, gn, pcg):
         rate = frac * cap / n_streams
         b = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds, rate,
                        args.served_budget_gb, gn, pcg, seed=1)
+        ba = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds, rate,
+                        args.served_budget_gb, gn, pcg, seed=1, adaptive=False)
         pl = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds, rate,
                         args.served_budget_gb, gn, pcg, seed=1, plain=True)
         points.append({"offered_frac_of_batched_capacity": frac, "rate_hz_per_stream": rate,
-                       "batched": served_summary(b), "plain": served_summary(pl)})
+                       "batched": served_summary(b), "batched_every_step": served_summary(ba),
+                       "plain": served_summary(pl)})
     # a budget of about half what the streams hold: admission binds
     need_gb = max(sat["memory_gb_at_end"], 0.1)
     tight = run_served(sw, members, large, args.served_streams, args.served_large, args.served_seconds,
@@ -666,6 +676,7 @@ def main():
     # autotuned on the first frame's system
     step(0, False)
     tuned_rows, tuned_us = sw.sw_autotune(h, pcg)
+    pcg_mode = sw.sw_debug_pcg_mode(h)   # 3: the cluster PCG
     for k in range(1, args.warmup):
         step(k, False)
     torch.cuda.synchronize()
@@ -714,6 +725,21 @@ def main():
     n_corr = int(np.mean(n_corr_seen))   # correspondences per Gauss-Newton iteration
     nnzb = sw.sw_debug_assemble(h)[0]
     roof = roofline(stage_ms, stage_n, len(v4), len(node4), nnzb, n_corr, c.width * c.height, pcg)
+    # the PCG is bound by synchronisation, not HBM: its latency bound is the
+    # hops it must take (cluster PCG: two cluster barriers per iteration and
+    # two at set-up) times one hop measured alone
+    if pcg_mode == 3:
+        ctas = sw.sw_debug_pcg_cluster(h, 0, 16, 0)[0]
+        hop_us = sw.sw_debug_cluster_barrier_us(ctas)
+        hops = 2 * pcg + 2
+        meas = roof["stages"]["pcg"]["us_per_launch"]
+        roof["stages"]["pcg"]["latency_bound"] = {
+            "hops_per_launch": hops, "hop_us": hop_us, "bound_us": hops * hop_us, "measured_us": meas,
+            "frac": hops * hop_us / meas,
+            "note": "cluster barriers of the cluster PCG (2 per iteration, 2 at set-up) x one barrier of the same "
+                    "cluster measured alone; the stage also holds the preconditioner launch"}
+        if roof["dominant"]["kernel"] == "pcg":
+            roof["dominant"]["latency_bound"] = roof["stages"]["pcg"]["latency_bound"]
 
     # end to end through the C ABI: host depth in, node state out, every step
     pos = np.empty((len(node4), 4), np.float32)
@@ -784,6 +810,38 @@ def main():
                   "note": "same workload and timing as the headline, with sw_params.visibility = 1: the "
                           "selected live surfels drawn as opaque disk splats before each solve, only "
                           "surfels that keep a pixel associated"}
+    # the configuration's literal precision split: FP64 inner products in the
+    # PCG (SW_PRECISION_MIXED_F64DOTS) instead of the default double-float
+    # pairs, on the same frames, timed the same way
+    hp64 = sw.sw_create_stream(sw.params_for(c, len(v4), len(node4), precision=sw.SW_PRECISION_MIXED_F64DOTS), stream)
+    sw.sw_set_model(hp64, v4, n4, t2, node4)
+
+    def pstep(k):
+        sw.sw_upload_depth(hp64, dev_frames[ts[k]], k + 1)
+        sw.sw_solve_frame(hp64, gn, pcg, want_stats=False)
+        sw.sw_fuse_frame(hp64)
+    pstep(0)
+    sw.sw_autotune(hp64, pcg)
+    for k in range(1, args.warmup):
+        pstep(k)
+    torch.cuda.synchronize()
+    p_lat = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pstep(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p_lat.append(e0.elapsed_time(e1))
+    precision_f64dots = {"frames_per_s": 1000.0 / float(np.mean(p_lat)),
+                         "latency_ms": {"p50": float(np.percentile(p_lat, 50)), "p99": float(np.percentile(p_lat, 99))},
+                         "pcg_mode": sw.sw_debug_pcg_mode(hp64),
+                         "note": "same workload, frames and timing as the headline with FP64 PCG inner products "
+                                 "(the configuration's precision split); the headline accumulates them in "
+                                 "double-float pairs"}
+    sw.sw_destroy_stream(hp64)
     # appending (a separate call after fusion, not part of the configuration's
     # frame): steady state on the full model, where the candidates are the
     # few pixels no surfel covers, frame after frame; the first call loads
@@ -876,6 +934,8 @@ def main():
         "rigid_align": rigid,
         "appending": appending,
         "visibility": visibility,
+        "precision_f64dots": precision_f64dots,
+        "pcg_mode": pcg_mode,
     }
     if batched:
         line["multi_stream"] = batched

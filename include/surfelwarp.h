@@ -64,7 +64,9 @@ typedef enum {
   SW_ERR_NOT_INITIALIZED = 3,   /* no model (sw_set_model) or no depth frame yet */
   SW_ERR_SOLVER_BREAKDOWN = 4,  /* a 6x6 diagonal block is not positive definite, or pᵀAp <= 0 */
   SW_ERR_TIMEOUT = 5,           /* a bounded device-side wait gave up */
-  SW_ERR_CUDA = 6               /* a CUDA runtime error; see sw_last_error */
+  SW_ERR_CUDA = 6,              /* a CUDA runtime error; see sw_last_error */
+  SW_ERR_BOUNDS = 7             /* checked build only (-DSW_BOUNDS_CHECK): an index that a kernel read
+                                   or derived on the device was out of range; the access was skipped */
 } sw_status;
 
 /* Parameters of one stream.  Table 1 fixes lambda, fuse_dist, fuse_normal,
@@ -321,14 +323,14 @@ sw_status sw_debug_pcg_mode(sw_handle h, int* mode);
  * node4 [n_nodes][4] the node positions (x y z, w unused).  Output: plan
  * (host, cap ints, nullable to ask for the size in *n_out) laid out as
  * header {ctas, most rows, most home blocks, most receive slots of a CTA,
- * n_nodes, most halo rows, most u pushes}; per CTA prefix tables
- * (ctas + 1 each) of rows, home blocks, receive slots and u pushes; each
- * CTA's rows (node ids, its local order); per CTA the rows' home-block,
- * receive-slot and u-push offsets (rows + 1 each); per home block its block
- * index, the local u slot of its column (own row, or halo slot after the
- * own rows) and the target of its transposed product ((owner CTA << 16) |
- * receive slot, -1 on the diagonal); per u push (peer CTA << 16) | the
- * peer's u slot.  *smem_out: the shared memory a CTA needs.
+ * n_nodes, most halo rows, most u pushes}; per CTA prefix tables (ctas + 1
+ * each) of rows, home blocks, receive slots and u pushes; each CTA's rows
+ * (node ids, its local order); per CTA the rows' home-block, receive-slot
+ * and u-push offsets (rows + 1 each); per home block its block index, the
+ * local u slot of its column (own row, or halo slot after the own rows) and
+ * the target of its transposed product ((owner CTA << 16) | receive slot,
+ * -1 on the diagonal); per u push (peer CTA << 16) | the peer's u slot.
+ * *smem_out: the shared memory a CTA needs.
  * SW_ERR_INVALID_ARG if the system does not fit smem_limit bytes per CTA
  * (or 192 rows per CTA) or the pattern is malformed. */
 sw_status sw_debug_cluster_plan(int ctas, int n_nodes, const int* row_ptr, const int* col, const float* node4,
@@ -341,6 +343,13 @@ sw_status sw_debug_cluster_plan(int ctas, int n_nodes, const int* row_ptr, const
  * precision (a negative value is a CUDA error code). */
 sw_status sw_debug_pcg_cluster(sw_handle h, int precision, int ctas, size_t smem, int* plan_ctas,
                                size_t* plan_smem, int* active_clusters);
+
+/* The cluster PCG's hop measured alone (an addition): the time of one
+ * cluster barrier (barrier.cluster arrive + wait) of `ctas` CTAs of the
+ * cluster PCG's size, in microseconds, from two timed launches.  The PCG
+ * passes two such barriers per iteration; bench.py states its latency
+ * bound in this unit.  Synchronous; needs a GPU. */
+sw_status sw_debug_cluster_barrier_us(int ctas, double* us);
 
 /* Splat visibility (Sec. 7) that the last solve of a stream with
  * sw_params.visibility = 1 predicted before its first Gauss-Newton
@@ -357,6 +366,33 @@ sw_status sw_read_visibility(sw_handle h, int* visible, int cap, int* n_out);
  * positive definite (its inv21 entries are then unspecified).  Needs a GPU;
  * synchronous. */
 sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* inv21, int* ok);
+
+/* Test hooks for the library's own prefix sum and radix sort (k_sort.cu;
+ * the model set-up sorts surfels by their 4-node set, the JᵀJ pattern
+ * build sorts node pairs, appending compacts and sorts new node sets).
+ *
+ * sw_debug_scan: out[i] (host, n int32) = in[0] + ... + in[i-1], or up to
+ * in[i] when inclusive is nonzero (host in, n int32; wraps like int32).
+ *
+ * sw_debug_radix_sort: a stable sort of n keys (host; key_bytes 4 = uint32
+ * or 8 = uint64) by their bits [begin_bit, end_bit), least significant
+ * 8-bit digit first.  keys_out (host, n keys) gets the keys in order; when
+ * vals (host, n int32) is not NULL, vals_out (host, n int32) gets each key's
+ * value, equal keys in input order.  n = 0 is a no-op;
+ * SW_ERR_INVALID_ARG for a bad size, key width or bit range.  Both need a
+ * GPU and are synchronous. */
+/* Test hook for the checked build (-DSW_BOUNDS_CHECK): writes node id
+ * `node` as skinning node `slot` (0..3) of surfel `surfel` in the library's
+ * internal order, with no other change.  node must lie in [0, max_nodes),
+ * inside the node arrays' allocation, but may be >= n_nodes: then the
+ * checked build reports the next per-frame call with SW_ERR_BOUNDS, and the
+ * normal build reads unused node storage (a wrong warp, no fault).
+ * SW_ERR_INVALID_ARG for an argument out of range.  Synchronous. */
+sw_status sw_debug_set_skin_node(sw_handle h, int surfel, int slot, int node);
+
+sw_status sw_debug_scan(const int32_t* in, int n, int inclusive, int32_t* out);
+sw_status sw_debug_radix_sort(int key_bytes, const void* keys, const int32_t* vals, int n, int begin_bit,
+                              int end_bit, void* keys_out, int32_t* vals_out);
 
 /* Whole-stream state to and from host memory (checkpoint / resume):
  * sw_export_state with buf NULL reports the size in *bytes. */
@@ -425,9 +461,9 @@ typedef struct {
   int stream;          /* id from sw_server_open */
   int frame_id;
   int status;          /* sw_status of the frame's work */
-  int batch_size;      /* frames processed in the same step */
+  int batch_size;      /* frames processed in the same launches (1: through its stream's own calls) */
   double submit_ms;    /* sw_server_submit took the frame */
-  double start_ms;     /* its step began */
+  double start_ms;     /* its processing began */
   double done_ms;      /* its fusion (and appending) had finished on the device */
   int appended;        /* surfels the frame appended (sw_server_set_appending) */
   int n_surfels;       /* the stream's surfels after the frame */
@@ -440,6 +476,7 @@ typedef struct {
   long long frames;         /* frames completed */
   double busy_ms;           /* time spent in steps */
   size_t memory_in_use;     /* bytes held by all streams */
+  long long steps_alone;    /* steps the adaptive policy ran stream by stream */
 } sw_server_stats;
 
 /* Start a server.  memory_budget: bytes for all streams (0 = unlimited);
@@ -485,6 +522,12 @@ sw_status sw_server_set_appending(sw_server_handle s, int enable);
  * time stamps.  0 (the default) batches every admitted stream's oldest
  * frame into one step. */
 sw_status sw_server_set_plain(sw_server_handle s, int enable);
+/* Adaptive steps (1, the default): every step runs its frames either as one
+ * batch or one by one through their streams' own calls, whichever the
+ * server's measured times say is cheaper (a batch step is shaped for all
+ * admitted streams, so under light load a few frames finish sooner alone).
+ * 0 batches every step.  Ignored in the plain mode. */
+sw_status sw_server_set_adaptive(sw_server_handle s, int enable);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 
 /* Rigid pre-alignment of the current frame (Sec. 7: before the non-rigid

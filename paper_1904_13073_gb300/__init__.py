@@ -12,7 +12,10 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsurfelwarp.so")
+# SW_BOUNDS_CHECK=1 selects the checked build (kernels range-check the
+# indices they read or derive on the device; see build.py)
+CHECKED_BUILD = os.environ.get("SW_BOUNDS_CHECK", "") == "1"
+LIB_PATH = os.path.join(HERE, "libsurfelwarp_checked.so" if CHECKED_BUILD else "libsurfelwarp.so")
 
 SW_MAX_GN_ITERS = 16
 SW_MAX_PCG_ITERS = 128
@@ -22,7 +25,8 @@ SW_PRECISION_FP64 = 1            # the whole solve in FP64
 SW_PRECISION_MIXED_F64DOTS = 2   # FP32 solve, FP64 PCG inner products, FP64 6x6 inverses
 
 STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_NO_MEMORY", 3: "SW_ERR_NOT_INITIALIZED",
-          4: "SW_ERR_SOLVER_BREAKDOWN", 5: "SW_ERR_TIMEOUT", 6: "SW_ERR_CUDA"}
+          4: "SW_ERR_SOLVER_BREAKDOWN", 5: "SW_ERR_TIMEOUT", 6: "SW_ERR_CUDA",
+          7: "SW_ERR_BOUNDS"}
 
 
 class SwError(RuntimeError):
@@ -76,7 +80,8 @@ class sw_frame_result(ctypes.Structure):
 
 class sw_server_stats(ctypes.Structure):
     _fields_ = [("admitted", ctypes.c_int), ("waiting", ctypes.c_int), ("steps", ctypes.c_longlong),
-                ("frames", ctypes.c_longlong), ("busy_ms", ctypes.c_double), ("memory_in_use", ctypes.c_size_t)]
+                ("frames", ctypes.c_longlong), ("busy_ms", ctypes.c_double), ("memory_in_use", ctypes.c_size_t),
+                ("steps_alone", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,11 +135,15 @@ _SIGS = {
     "sw_debug_pcg_mode": [_P, ctypes.POINTER(_I)],
     "sw_batch_debug_pcg_mode": [_P, ctypes.POINTER(_I)],
     "sw_read_visibility": [_P, _P, _I, ctypes.POINTER(_I)],
+    "sw_debug_cluster_barrier_us": [_I, ctypes.POINTER(ctypes.c_double)],
     "sw_debug_pcg_cluster": [_P, _I, _I, ctypes.c_size_t, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t),
                              ctypes.POINTER(_I)],
     "sw_debug_cluster_plan": [_I, _I, _P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
     "sw_debug_block_inverse": [_P, _I, _I, _P, _P],
+    "sw_debug_scan": [_P, _I, _I, _P],
+    "sw_debug_set_skin_node": [_P, _I, _I, _I],
+    "sw_debug_radix_sort": [_I, _P, _P, _I, _I, _I, _P, _P],
     "sw_server_create": [ctypes.c_size_t, _I, _I, _I, ctypes.POINTER(_P)],
     "sw_server_destroy": [_P],
     "sw_server_open": [_P, ctypes.POINTER(sw_params), _P, _P, _P, _I, _P, _I, ctypes.POINTER(_I)],
@@ -148,6 +157,7 @@ _SIGS = {
     "sw_server_set_batch_window": [_P, ctypes.c_double],
     "sw_server_set_appending": [_P, _I],
     "sw_server_set_plain": [_P, _I],
+    "sw_server_set_adaptive": [_P, _I],
     "sw_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_rigid_align": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)],
     "sw_batch_rigid_align": [_P, _I],
@@ -511,6 +521,42 @@ def sw_debug_block_inverse(blocks, fp64=False):
     return out[:n], ok[:n].astype(bool)
 
 
+def sw_debug_set_skin_node(h, surfel, slot, node):
+    """Write one skinning node id of an internal-order surfel (checked-build test hook)."""
+    _check(lib().sw_debug_set_skin_node(h, int(surfel), int(slot), int(node)), h)
+
+
+def sw_debug_scan(values, inclusive=False):
+    """The library's device prefix sum of an int32 array (exclusive unless inclusive)."""
+    v = np.ascontiguousarray(np.asarray(values, np.int32).reshape(-1))
+    out = np.empty(max(1, v.size), np.int32)
+    _check(lib().sw_debug_scan(v.ctypes.data_as(_P), v.size, int(bool(inclusive)), out.ctypes.data_as(_P)), None)
+    return out[:v.size]
+
+
+def sw_debug_radix_sort(keys, values=None, begin_bit=0, end_bit=None):
+    """The library's stable device radix sort of uint32 or uint64 keys by bits
+    [begin_bit, end_bit); returns (sorted keys, their values or None)."""
+    k = np.asarray(keys)
+    if k.dtype not in (np.uint32, np.uint64):
+        raise TypeError("keys must be uint32 or uint64")
+    k = np.ascontiguousarray(k.reshape(-1))
+    kb = k.dtype.itemsize
+    end_bit = 8 * kb if end_bit is None else end_bit
+    out = np.empty(max(1, k.size), k.dtype)
+    vp, vout = None, None
+    if values is not None:
+        v = np.ascontiguousarray(np.asarray(values, np.int32).reshape(-1))
+        if v.size != k.size:
+            raise ValueError("values and keys differ in length")
+        vout = np.empty(max(1, v.size), np.int32)
+        vp = v.ctypes.data_as(_P)
+    _check(lib().sw_debug_radix_sort(kb, k.ctypes.data_as(_P), vp, k.size, begin_bit, end_bit,
+                                     out.ctypes.data_as(_P), None if vout is None else vout.ctypes.data_as(_P)),
+           None)
+    return out[:k.size], (None if vout is None else vout[:k.size])
+
+
 # failure kinds of sw_debug_inject_wait_fault
 SW_FAULT_NONE, SW_FAULT_PCG_PARTIAL, SW_FAULT_PCG_VECTOR, SW_FAULT_DEPTH_TMA = 0, 1, 2, 3
 
@@ -560,6 +606,13 @@ def sw_debug_pcg_cluster(h=None, precision=0, ctas=16, smem=0):
     _check(lib().sw_debug_pcg_cluster(h, int(precision), int(ctas), int(smem), ctypes.byref(c), ctypes.byref(b),
                                       ctypes.byref(a)), h)
     return c.value, b.value, a.value
+
+
+def sw_debug_cluster_barrier_us(ctas=16):
+    """Microseconds of one cluster barrier of `ctas` CTAs of the cluster PCG's size."""
+    us = ctypes.c_double()
+    _check(lib().sw_debug_cluster_barrier_us(int(ctas), ctypes.byref(us)), None)
+    return us.value
 
 
 def sw_read_visibility(h):
@@ -673,6 +726,10 @@ def sw_server_set_appending(s, enable):
 
 def sw_server_set_plain(s, enable):
     _check(lib().sw_server_set_plain(s, int(bool(enable))), None)
+
+
+def sw_server_set_adaptive(s, enable):
+    _check(lib().sw_server_set_adaptive(s, int(bool(enable))), None)
 
 
 def sw_server_read_stats(srv):

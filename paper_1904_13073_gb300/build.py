@@ -4,6 +4,12 @@ Each translation unit under ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and the objects
 are linked into one shared library next to this file.  Rebuilds only when a
 source or header is newer than the library.
+
+The checked build (``checked=True``, or ``SW_BOUNDS_CHECK=1`` in the
+environment) adds ``-DSW_BOUNDS_CHECK``: kernels range-check the indices they
+read or derive on the device before each access and report a bad one as
+``SW_ERR_BOUNDS``.  It is ``libsurfelwarp_checked.so``, which the binding
+loads instead when ``SW_BOUNDS_CHECK=1``.
 """
 import concurrent.futures as cf
 import glob
@@ -16,6 +22,16 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsurfelwarp.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libsurfelwarp_checked.so")
+
+
+def checked_from_env():
+    return os.environ.get("SW_BOUNDS_CHECK", "") == "1"
+
+
+def lib_path(checked=None):
+    return LIB_CHECKED if (checked_from_env() if checked is None else checked) else LIB
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -35,24 +51,29 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
         + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link; returns the library path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), checked=None):
+    """Compile and link; returns the library path.  checked=None follows
+    SW_BOUNDS_CHECK in the environment."""
+    checked = checked_from_env() if checked is None else checked
+    lib, bdir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    if checked:
+        extra_flags = ("-DSW_BOUNDS_CHECK", *extra_flags)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,13 +84,13 @@ def build(force=False, verbose=False, extra_flags=()):
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

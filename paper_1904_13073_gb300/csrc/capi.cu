@@ -2,12 +2,11 @@
 // process-wide budget, model set-up (skinning, node graph, the block-sparse
 // pattern of JᵀJ), the per-frame calls and the inspection hooks.
 //
-// Model set-up sorts the surfels by their 4-node set on the GPU (CUB radix
-// sort), so that surfels that contribute to the same ten JᵀJ blocks are
+// Model set-up sorts the surfels by their 4-node set on the GPU (the
+// library's radix sort, k_sort.cu), so that surfels that contribute to the same ten JᵀJ blocks are
 // adjacent; the node-level structure (pattern of 6x6 blocks, graph in-edges,
 // the transposed-block lists of the SpMV) is O(nodes + node sets) and is
 // built on the host once per model.
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <atomic>
@@ -374,6 +373,16 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
         cl.push_back(i);
         in_cluster[i] = 1;
       }
+    // clusters only when they take the whole batch in one wave: members left
+    // to the cooperative kernel would run in a second launch after them, and
+    // clusters beyond those the device runs at once in further waves -- both
+    // slower than one cooperative launch over every member
+    if (!cl.empty() && ((int)cl.size() != n || cluster_pcg_active(prec, cl_ctas, cl_smem) < (int)cl.size())) {
+      cl.clear();
+      cl_smem = 0;
+      cl_ctas = 0;
+      std::fill(in_cluster.begin(), in_cluster.end(), 0);
+    }
     const int n_coop = n - (int)cl.size();
     const int per_sm = std::max(1, pcg_blocks_per_sm(prec));
     const int cap = sm_count() * per_sm;
@@ -1060,18 +1069,14 @@ sw_status setup_surfels(sw_stream* s, const float4* tv, const float4* tn, const 
   SW_CUDA(s, cudaMemcpyAsync(s->knn_dist, tknn, n * 16, cudaMemcpyDeviceToDevice, st));
   SW_CUDA(s, cudaMemcpyAsync(s->w_dist, tw, n * 16, cudaMemcpyDeviceToDevice, st));
   k_set_keys<<<(n_s + 255) / 256, 256, 0, st>>>(tknn, n_s, keys.as<unsigned long long>(), vals.as<int>());
-  size_t sort_bytes = 0, scan_bytes = 0;
-  cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, keys.as<unsigned long long>(), keys2.as<unsigned long long>(),
-                                  vals.as<int>(), perm.as<int>(), n_s, 0, 64, st);
-  cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, head.as<int>(), h.set_id, n_s, st);
-  Tmp cubtmp(s, std::max(sort_bytes, scan_bytes));
-  if (!cubtmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
-  SW_CUDA(s, cub::DeviceRadixSort::SortPairs(cubtmp.p, sort_bytes, keys.as<unsigned long long>(),
-                                             keys2.as<unsigned long long>(), vals.as<int>(), perm.as<int>(), n_s, 0,
-                                             64, st));
+  const size_t sort_bytes = sort_scratch_bytes_u64(n_s, true), scan_bytes = scan_scratch_bytes(n_s);
+  Tmp sorttmp(s, std::max(sort_bytes, scan_bytes));
+  if (!sorttmp.p) return fail(s, SW_ERR_NO_MEMORY, "sort scratch allocation failed");
+  SW_CUDA(s, radix_sort_u64(keys.as<unsigned long long>(), keys2.as<unsigned long long>(), vals.as<int>(),
+                            perm.as<int>(), n_s, 0, 64, sorttmp.p, sort_bytes, st));
   k_gather_model<<<(n_s + 255) / 256, 256, 0, st>>>(h, keys2.as<unsigned long long>(), perm.as<int>(), tv, tn, tt,
                                                     tknn, tw, head.as<int>());
-  SW_CUDA(s, cub::DeviceScan::InclusiveSum(cubtmp.p, scan_bytes, head.as<int>(), h.set_id, n_s, st));
+  SW_CUDA(s, scan_sum(head.as<int>(), h.set_id, n_s, true, sorttmp.p, scan_bytes, st));
   k_minus_one<<<(n_s + 255) / 256, 256, 0, st>>>(h.set_id, n_s);
   int last = 0;
   SW_CUDA(s, cudaMemcpyAsync(&last, h.set_id + n_s - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1289,6 +1294,21 @@ sw_status sw_upload_depth(sw_handle s, const float* depth, int on_device, int fr
 
 namespace {
 
+// The checked build (-DSW_BOUNDS_CHECK) waits for each per-frame call's
+// kernels and reports an index that failed its range check; the status bit
+// stays set until the next sw_set_model.  The normal build never sets it.
+sw_status bounds_check(sw_stream* s) {
+#ifdef SW_BOUNDS_CHECK
+  int status = 0;
+  SW_CUDA(s, cudaMemcpyAsync(&status, s->h.status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (status & kStatusBounds) return fail(s, SW_ERR_BOUNDS, "a device index was out of range (checked build)");
+#else
+  (void)s;
+#endif
+  return SW_OK;
+}
+
 sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
   int status = 0;
   SW_CUDA(s, cudaMemcpyAsync(&status, s->h.status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
@@ -1301,6 +1321,7 @@ sw_status read_stats(sw_stream* s, int gn, sw_solve_stats* out) {
     SW_CUDA(s, cudaMemcpyAsync(out->pcg_rz, s->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, s->st));
   }
   SW_CUDA(s, cudaStreamSynchronize(s->st));
+  if (status & kStatusBounds) return fail(s, SW_ERR_BOUNDS, "a device index was out of range (checked build)");
   if (status & kStatusTimeout)
     return fail(s, SW_ERR_TIMEOUT, "a bounded wait of the PCG gave up (a reduction or a neighbour's vector); "
                                    "the node transforms were left as they were");
@@ -1321,7 +1342,7 @@ sw_status sw_solve_frame(sw_handle s, int gn_iters, int pcg_iters, sw_solve_stat
   enter(s);
   SW_TRY(runner_solve(s->run, s, gn_iters, pcg_iters));
   if (stats) return read_stats(s, gn_iters, stats);
-  return SW_OK;
+  return bounds_check(s);
 }
 
 sw_status sw_fuse_frame(sw_handle s) {
@@ -1330,7 +1351,7 @@ sw_status sw_fuse_frame(sw_handle s) {
   enter(s);
   SW_TRY(runner_fuse(s->run, s));
   s->fused = true;
-  return SW_OK;
+  return bounds_check(s);
 }
 
 sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_out) {
@@ -1345,6 +1366,7 @@ sw_status sw_read_nodes(sw_handle s, float* pos4, float* dq8, int cap, int* n_ou
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   int status = 0;
   SW_CUDA(s, cudaMemcpy(&status, s->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status & kStatusBounds) return fail(s, SW_ERR_BOUNDS, "a device index was out of range (checked build)");
   if (status & kStatusBreakdown) return fail(s, SW_ERR_SOLVER_BREAKDOWN, "the last solve broke down");
   return SW_OK;
 }
@@ -1458,6 +1480,20 @@ sw_status sw_set_node_dq(sw_handle s, const float* dq8, int n) {
   return SW_OK;
 }
 
+sw_status sw_debug_set_skin_node(sw_handle s, int surfel, int slot, int node) {
+  if (!s) return fail(nullptr, SW_ERR_INVALID_ARG, "null handle");
+  if (!s->has_model) return fail(s, SW_ERR_NOT_INITIALIZED, "no model");
+  if (surfel < 0 || surfel >= s->h.n_s || slot < 0 || slot > 3)
+    return fail(s, SW_ERR_INVALID_ARG, "surfel or slot out of range");
+  // inside the node arrays' allocation (max_nodes), whatever n_nodes is
+  if (node < 0 || node >= s->p.max_nodes) return fail(s, SW_ERR_INVALID_ARG, "node outside [0, max_nodes)");
+  enter(s);
+  SW_CUDA(s, cudaMemcpyAsync(reinterpret_cast<int*>(s->h.knn + surfel) + slot, &node, sizeof(int),
+                             cudaMemcpyHostToDevice, s->st));
+  SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
 sw_status sw_read_correspondence(sw_handle s, int* pix, int cap, int* n_out) {
   SW_TRY(need_model(s, cap));
   if (n_out) *n_out = s->h.n_s;
@@ -1527,10 +1563,10 @@ sw_status ensure_append_bufs(sw_stream* s) {
   SW_TRY(A(s, &a.flags, np)); SW_TRY(A(s, &a.wsum, np)); SW_TRY(A(s, &a.strain, 9 * np)); SW_TRY(A(s, &a.w, np));
   SW_TRY(A(s, &a.v, np)); SW_TRY(A(s, &a.n, np)); SW_TRY(A(s, &a.acc, np)); SW_TRY(A(s, &a.stay, nmax));
   SW_TRY(A(s, &a.pos, nmax)); SW_TRY(A(s, &a.counts, kAppCounts));
-  a.cub_bytes = append_cub_bytes((int)np, (int)nmax);
+  a.scan_bytes = append_scan_bytes((int)np, (int)nmax);
   unsigned char* tmp = nullptr;
-  SW_TRY(A(s, &tmp, std::max<size_t>(16, a.cub_bytes)));
-  a.cub_tmp = tmp;
+  SW_TRY(A(s, &tmp, std::max<size_t>(16, a.scan_bytes)));
+  a.scan_tmp = tmp;
   s->app_ready = true;
   return SW_OK;
 }
@@ -1588,7 +1624,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
     cudaEventDestroy(ev1);
     if (stats) stats->kernel_ms = kms;
     s->fused = false;
-    return SW_OK;
+    return bounds_check(s);
   }
   {
     const size_t n = std::max(1, n_new), m = std::max(1, n_app);
@@ -1638,7 +1674,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       }
       if (stats) stats->resorted = resorted;
       s->fused = false;
-      return SW_OK;
+      return bounds_check(s);
     };
     // Fast update: nothing removed, no new node, and the surfels appended
     // since the last set sort a small share of the model.  Each appended
@@ -1666,7 +1702,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
         // the new sets' slots go after the known sets' (the table grows if needed)
         SW_TRY(grow_model_block(s, reinterpret_cast<void**>(&h.set_slots), (size_t)h.n_sets * 14 * sizeof(int),
                                 (size_t)(h.n_sets + cnt[0]) * 14 * sizeof(int)));
-        const size_t nb = new_sets_cub_bytes(n_app);
+        const size_t nb = new_sets_scratch_bytes(n_app);
         Tmp sorted(s, (size_t)n_app * 8), head(s, (size_t)n_app * 4), rank(s, (size_t)n_app * 4), tmp(s, nb);
         if (!sorted.p || !head.p || !rank.p || !tmp.p)
           return fail(s, SW_ERR_NO_MEMORY, "appending scratch allocation failed");
@@ -1714,6 +1750,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       return finish(2);
     }
     s->unsorted = 0;
+    SW_TRY(bounds_check(s));   // checked build: before the rebuild clears the status
     // the model's layout changes: rebuild its structure (nodes and transforms
     // stay).  The old model's blocks go back to the cache while the kernels
     // above may still read them: anything that reuses them is later on the
@@ -1894,6 +1931,7 @@ const char* sw_status_string(sw_status s) {
     case SW_ERR_SOLVER_BREAKDOWN: return "solver breakdown";
     case SW_ERR_TIMEOUT: return "device wait timed out";
     case SW_ERR_CUDA: return "CUDA error";
+    case SW_ERR_BOUNDS: return "device index out of range (checked build)";
   }
   return "unknown status";
 }
@@ -2052,7 +2090,8 @@ sw_status sw_batch_solve(sw_batch_handle b, int gn_iters, int pcg_iters, sw_solv
     SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].n_corr, m->h.n_corr, kMaxGn * sizeof(int), cudaMemcpyDeviceToHost, r->st));
     SW_CUDA(nullptr, cudaMemcpyAsync(stats[i].pcg_rz, m->h.pcg_rz, kMaxGn * sizeof(double), cudaMemcpyDeviceToHost, r->st));
     SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
-    if (status & (kStatusTimeout | kStatusDepthTimeout)) worst = SW_ERR_TIMEOUT;
+    if (status & kStatusBounds) worst = SW_ERR_BOUNDS;
+    else if ((status & (kStatusTimeout | kStatusDepthTimeout)) && worst != SW_ERR_BOUNDS) worst = SW_ERR_TIMEOUT;
     else if ((status & kStatusBreakdown) && worst == SW_OK) worst = SW_ERR_SOLVER_BREAKDOWN;
   }
   if (worst != SW_OK) return fail(nullptr, worst, "a member's solve broke down or timed out (see its stats)");
@@ -2080,7 +2119,8 @@ sw_status batch_member_status(sw_batch_handle b, int* status) {
       SW_CUDA(nullptr, cudaMemcpyAsync(&raw[i], r->members[i]->h.status, sizeof(int), cudaMemcpyDeviceToHost, r->st));
   SW_CUDA(nullptr, cudaStreamSynchronize(r->st));
   for (int i = 0; i < n; ++i)
-    status[i] = (raw[i] & (kStatusTimeout | kStatusDepthTimeout)) ? SW_ERR_TIMEOUT
+    status[i] = (raw[i] & kStatusBounds)                          ? SW_ERR_BOUNDS
+                : (raw[i] & (kStatusTimeout | kStatusDepthTimeout)) ? SW_ERR_TIMEOUT
                 : (raw[i] & kStatusBreakdown)                       ? SW_ERR_SOLVER_BREAKDOWN
                                                                      : SW_OK;
   return SW_OK;
@@ -2105,7 +2145,7 @@ sw_status sw_rigid_align(sw_handle s, int iters, int* n_corr, double* energy) {
       if (energy) energy[k] = st[2 * k + 1];
     }
   }
-  return SW_OK;
+  return bounds_check(s);
 }
 
 sw_status sw_batch_rigid_align(sw_batch_handle b, int iters) {
@@ -2189,6 +2229,63 @@ sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* in
   return SW_OK;
 }
 
+sw_status sw_debug_scan(const int32_t* in, int n, int inclusive, int32_t* out) {
+  if (n < 0 || n > (1 << 28)) return fail(nullptr, SW_ERR_INVALID_ARG, "n out of range");
+  if (n > 0 && (!in || !out)) return fail(nullptr, SW_ERR_INVALID_ARG, "null array");
+  if (n == 0) return SW_OK;
+  const size_t tb = scan_scratch_bytes(n);
+  int *din = nullptr, *dout = nullptr;
+  void* dtmp = nullptr;
+  cudaError_t e = cudaMalloc(&din, (size_t)n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dtmp, tb);
+  if (e == cudaSuccess) e = cudaMemcpy(din, in, (size_t)n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = scan_sum(din, dout, n, inclusive != 0, dtmp, tb, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(din);
+  cudaFree(dout);
+  cudaFree(dtmp);
+  if (e != cudaSuccess) return fail(nullptr, SW_ERR_CUDA, std::string("scan: ") + cudaGetErrorString(e));
+  return SW_OK;
+}
+
+sw_status sw_debug_radix_sort(int key_bytes, const void* keys, const int32_t* vals, int n, int begin_bit,
+                              int end_bit, void* keys_out, int32_t* vals_out) {
+  if (key_bytes != 4 && key_bytes != 8) return fail(nullptr, SW_ERR_INVALID_ARG, "key_bytes must be 4 or 8");
+  if (n < 0 || n > (1 << 28)) return fail(nullptr, SW_ERR_INVALID_ARG, "n out of range");
+  if (begin_bit < 0 || begin_bit > end_bit || end_bit > 8 * key_bytes)
+    return fail(nullptr, SW_ERR_INVALID_ARG, "bit range out of range");
+  if (n > 0 && (!keys || !keys_out || (vals && !vals_out))) return fail(nullptr, SW_ERR_INVALID_ARG, "null array");
+  if (n == 0) return SW_OK;
+  const bool wv = vals != nullptr;
+  const size_t kb = (size_t)n * key_bytes, vb = (size_t)n * 4;
+  const size_t tb = key_bytes == 4 ? sort_scratch_bytes_u32(n, wv) : sort_scratch_bytes_u64(n, wv);
+  void *dk = nullptr, *dk2 = nullptr, *dtmp = nullptr;
+  int *dv = nullptr, *dv2 = nullptr;
+  cudaError_t e = cudaMalloc(&dk, kb);
+  if (e == cudaSuccess) e = cudaMalloc(&dk2, kb);
+  if (e == cudaSuccess) e = cudaMalloc(&dtmp, tb);
+  if (e == cudaSuccess && wv) e = cudaMalloc(&dv, vb);
+  if (e == cudaSuccess && wv) e = cudaMalloc(&dv2, vb);
+  if (e == cudaSuccess) e = cudaMemcpy(dk, keys, kb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && wv) e = cudaMemcpy(dv, vals, vb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = key_bytes == 4 ? radix_sort_u32(static_cast<const uint32_t*>(dk), static_cast<uint32_t*>(dk2), dv, dv2, n,
+                                        begin_bit, end_bit, dtmp, tb, 0)
+                       : radix_sort_u64(static_cast<const unsigned long long*>(dk),
+                                        static_cast<unsigned long long*>(dk2), dv, dv2, n, begin_bit, end_bit, dtmp,
+                                        tb, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(keys_out, dk2, kb, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && wv) e = cudaMemcpy(vals_out, dv2, vb, cudaMemcpyDeviceToHost);
+  cudaFree(dk);
+  cudaFree(dk2);
+  cudaFree(dtmp);
+  cudaFree(dv);
+  cudaFree(dv2);
+  if (e != cudaSuccess) return fail(nullptr, SW_ERR_CUDA, std::string("radix sort: ") + cudaGetErrorString(e));
+  return SW_OK;
+}
+
 sw_status sw_debug_set_pcg_mode(int max_mode) {
   if (max_mode < 0 || max_mode > 3) return fail(nullptr, SW_ERR_INVALID_ARG, "max_mode must be 0, 1, 2 or 3");
   g_pcg_mode_cap.store(max_mode);
@@ -2263,5 +2360,11 @@ sw_status sw_debug_pcg_cluster(sw_handle s, int precision, int ctas, size_t smem
     if (plan_ctas) *plan_ctas = s->cplan_ctas;
     if (plan_smem) *plan_smem = s->cplan_smem;
   }
+  return SW_OK;
+}
+
+sw_status sw_debug_cluster_barrier_us(int ctas, double* us) {
+  if (ctas < 1 || ctas > 16 || !us) return fail(nullptr, SW_ERR_INVALID_ARG, "ctas out of range or null output");
+  SW_CUDA(nullptr, cluster_barrier_cost(ctas, us));
   return SW_OK;
 }

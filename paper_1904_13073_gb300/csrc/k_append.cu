@@ -28,9 +28,9 @@
 //                   t_now − t_init ≥ t_low_confid (flag at its caller index).
 //   k_compose_*     the new model in caller order: the survivors in their
 //                   order, then the accepted candidates in pixel order.
-#include <cub/cub.cuh>
 
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 
@@ -119,17 +119,17 @@ __global__ void k_scatter(const int* __restrict__ flag, const int* __restrict__ 
 
 __global__ void k_cand_queries(SwDev d, AppendBufs a, int n_cand) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < n_cand) a.query[c] = d.vmap[a.cand[c]];
+  if (c < n_cand) a.query[c] = d.vmap[checked(a.cand[c], (long long)d.W * d.H, d.status)];
 }
 
 __global__ void __launch_bounds__(64) k_append_eval(SwDev d, AppendBufs a, AppendParams ap, int n_cand) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cand) return;
-  const int pix = a.cand[c];
+  const int pix = checked(a.cand[c], (long long)d.W * d.H, d.status);
   const float4 V = d.vmap[pix], N = d.nmap[pix];
   int id[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) id[k] = a.knn[4 * c + k];
+  for (int k = 0; k < 4; ++k) id[k] = checked(a.knn[4 * c + k], d.n_n, d.status);
   LiveSkin sk;
   int flags = 1;
   {   // Eq. 7 on squares, exact-order FP32; node_0 always stays
@@ -219,7 +219,7 @@ __global__ void k_compose_stay(SwDev d, AppendBufs a, const int4* __restrict__ k
                                float4* tw) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= d.n_s || !a.stay[o]) return;
-  const int j = a.pos[o], i = d.inv_perm[o];
+  const int j = a.pos[o], i = checked(d.inv_perm[o], d.n_s, d.status);
   tv[j] = d.v_ref[i];
   tn[j] = d.n_ref[i];
   tt[j] = d.tt[i];
@@ -243,8 +243,7 @@ inline int blocks(int n, int t) { return (n + t - 1) / t; }
 cudaError_t compact(const AppendBufs& a, const int* flag, int n, int* out, int* count, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
   if (e != cudaSuccess || n == 0) return e;
-  size_t bytes = a.cub_bytes;
-  e = cub::DeviceScan::ExclusiveSum(a.cub_tmp, bytes, flag, a.pos, n, st);
+  e = scan_sum(flag, a.pos, n, false, a.scan_tmp, a.scan_bytes, st);
   if (e != cudaSuccess) return e;
   k_scatter<<<blocks(n, 256), 256, 0, st>>>(flag, a.pos, n, out, count);
   return cudaGetLastError();
@@ -382,9 +381,9 @@ __global__ void k_new_node_dq(SwDev d, int n_old, int k_new, const int* __restri
   const int j = n_old + k;
   const D3 x = d3(d.node_p[j]);
   DQ64 b{0.0, D3{0.0, 0.0, 0.0}, 0.0, D3{0.0, 0.0, 0.0}};
-  const DQ64 q0 = node_dq64(d, ids[4 * k]);
+  const DQ64 q0 = node_dq64(d, checked(ids[4 * k], n_old, d.status));
   for (int a = 0; a < 4; ++a) {
-    const int id = ids[4 * k + a];
+    const int id = checked(ids[4 * k + a], n_old, d.status);
     const float4 p = d.node_p[id];
     const D3 e = x - d3(p);
     const double sg = (double)p.w;
@@ -593,23 +592,16 @@ void launch_find_sets(const SwDev& d, int sorted_sets, const int4* tknn, int fir
   if (n_app) k_find_sets<<<blocks(n_app, 256), 256, 0, st>>>(d, sorted_sets, tknn, first, n_app, set_of, keys, missing);
 }
 
-size_t new_sets_cub_bytes(int n) {
-  size_t b = 0, c = 0;
-  cub::DeviceRadixSort::SortKeys(nullptr, b, (const unsigned long long*)nullptr, (unsigned long long*)nullptr, n);
-  cub::DeviceScan::ExclusiveSum(nullptr, c, (const int*)nullptr, (int*)nullptr, n);
-  return std::max(b, c);
-}
+size_t new_sets_scratch_bytes(int n) { return std::max(sort_scratch_bytes_u64(n, false), scan_scratch_bytes(n)); }
 
 cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsigned long long* sorted, int* head,
                             int* rank, int n_app, int n_missing, int* set_of, int* n_new_sets, int* no_block,
                             void* tmp, size_t tmp_bytes, cudaStream_t st) {
   // the found surfels' keys are ~0 and sort last: the first n_missing are the new sets' keys
-  size_t bytes = tmp_bytes;
-  cudaError_t e = cub::DeviceRadixSort::SortKeys(tmp, bytes, keys, sorted, n_app, 0, 64, st);
+  cudaError_t e = radix_sort_u64(keys, sorted, nullptr, nullptr, n_app, 0, 64, tmp, tmp_bytes, st);
   if (e != cudaSuccess) return e;
   k_key_heads<<<blocks(n_missing, 256), 256, 0, st>>>(sorted, n_missing, head);
-  bytes = tmp_bytes;
-  e = cub::DeviceScan::ExclusiveSum(tmp, bytes, head, rank, n_missing, st);
+  e = scan_sum(head, rank, n_missing, false, tmp, tmp_bytes, st);
   if (e != cudaSuccess) return e;
   k_new_sets<<<blocks(n_missing, 128), 128, 0, st>>>(d, sorted, head, rank, n_missing, n_new_sets, no_block);
   k_assign_new_sets<<<blocks(n_app, 128), 128, 0, st>>>(d, keys, sorted, rank, n_missing, n_app, set_of);
@@ -654,11 +646,7 @@ void launch_skin_merge(const SwDev& d, const float4* tv, int n, int n_old, int4*
   if (n) k_skin_merge<<<(n + 255) / 256, 256, 0, st>>>(d, tv, n, n_old, tknn, tw);
 }
 
-size_t append_cub_bytes(int n_pixels, int n_surfels) {
-  size_t bytes = 0;
-  cub::DeviceScan::ExclusiveSum(nullptr, bytes, (const int*)nullptr, (int*)nullptr, std::max(n_pixels, n_surfels));
-  return bytes;
-}
+size_t append_scan_bytes(int n_pixels, int n_surfels) { return scan_scratch_bytes(std::max(n_pixels, n_surfels)); }
 
 // Steps up to the candidate list: warped nodes, candidate pixels (count in
 // counts[kAppNCand]) and their depth vertices are left in `a`.

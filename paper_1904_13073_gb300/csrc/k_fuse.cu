@@ -17,6 +17,7 @@
 //                 A usable pixel whose window held no surfel at all is marked
 //                 kTargetEmptyWindow: the appending step's candidates.
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 
 namespace sw {
@@ -25,7 +26,7 @@ namespace {
 constexpr unsigned long long kEmpty = ~0ull;
 
 __device__ __forceinline__ DQ surfel_blend(const SwDev& d, int i, float& inv_n2) {
-  DQ b = blend4(d.dq, d.knn[i], d.w[i], d.ref_slot[i]);
+  DQ b = blend4(d.dq, checked4(d.knn[i], d.n_n, d.status), d.w[i], checked(d.ref_slot[i], 4, d.status));
   const float n2 = dq_norm2(b);
   if (n2 > 0.f) {
     inv_n2 = 1.f / n2;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kSurfTile) k_index_map(Batch bt) {
   if (!(su >= 0.f && su < (float)(4 * d.W) && sv >= 0.f && sv < (float)(4 * d.H))) return;
   const unsigned long long key =
       ((unsigned long long)__float_as_uint(v.z) << 32) | (unsigned long long)(unsigned)d.orig_id[i];
-  atomicMin(d.imap + (size_t)(int)sv * (4 * d.W) + (int)su, key);
+  atomicMin(d.imap + checked((int)sv * (4 * d.W) + (int)su, 16ll * d.W * d.H, d.status), key);
 }
 
 __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) k_fuse(Batch bt, int select_only) {
         const unsigned long long key = keys[sy * 4 + sx];
         if (key == kEmpty) continue;
         const unsigned o = (unsigned)(key & 0xffffffffu);
-        const int si = d.inv_perm[o];
+        const int si = checked(d.inv_perm[checked((int)o, d.n_s, d.status)], d.n_s, d.status);
         const float4 vl = d.v_live[si], nl = d.n_live[si];
         const float d2 = dist2_rn(vl.x, vl.y, vl.z, V.x, V.y, V.z);
         const float dt = dot_rn(f3(nl), f3(N));

@@ -17,9 +17,9 @@
 //   k_rl_fill      the entries and the row pointers of those lists
 //   k_set_slots    per set, its 10 upper blocks in (0,0)(0,1)(0,2)(0,3)(1,1)
 //                  (1,2)(1,3)(2,2)(2,3)(3,3) order, then its 4 node ids
-#include <cub/cub.cuh>
 
 #include "sw_internal.h"
+#include "sw_check.cuh"
 
 namespace sw {
 namespace {
@@ -67,10 +67,10 @@ __global__ void k_pat_unique(const uint32_t* __restrict__ k, const int* __restri
 }
 
 __global__ void k_pat_blocks(const uint32_t* __restrict__ ukeys, int nnzb, int n_n, int* __restrict__ row_ptr,
-                             int* __restrict__ col, int* __restrict__ blk_row) {
+                             int* __restrict__ col, int* __restrict__ blk_row, int* status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nnzb) return;
-  const int r = (int)(ukeys[b] >> 16);
+  const int r = checked((int)(ukeys[b] >> 16), n_n, status);
   blk_row[b] = r;
   col[b] = (int)(ukeys[b] & 0xffffu);
   if (b == 0 || (int)(ukeys[b - 1] >> 16) != r) row_ptr[r] = b;
@@ -88,10 +88,10 @@ __device__ __forceinline__ int find_block(const int* __restrict__ row_ptr, const
 }
 
 __global__ void k_pat_edges(const int* __restrict__ graph, int n_n, const int* __restrict__ row_ptr,
-                            const int* __restrict__ col, int* __restrict__ blk_edge) {
+                            const int* __restrict__ col, int* __restrict__ blk_edge, int* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_n * SW_K_GRAPH) return;
-  const int j = t / SW_K_GRAPH, i = graph[t];
+  const int j = t / SW_K_GRAPH, i = checked(graph[t], n_n, status);
   if (i == j) return;
   const int b = find_block(row_ptr, col, min(i, j), max(i, j));
   atomicOr(blk_edge + b, j < i ? 1 : 2);
@@ -110,10 +110,10 @@ __global__ void k_rl_keys(const int* __restrict__ blk_row, const int* __restrict
 
 __global__ void k_rl_fill(const unsigned long long* __restrict__ skeys, int n_ent, int n_n,
                           const int* __restrict__ blk_row, const int* __restrict__ col, int* __restrict__ rl_ptr,
-                          int2* __restrict__ rl_ent) {
+                          int2* __restrict__ rl_ent, int nnzb, int* status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_ent) return;
-  const int row = (int)(skeys[k] >> 32), b = (int)(skeys[k] & 0xffffffffu);
+  const int row = checked((int)(skeys[k] >> 32), n_n, status), b = checked((int)(skeys[k] & 0xffffffffu), nnzb, status);
   rl_ent[k] = blk_row[b] == row ? make_int2(b, col[b]) : make_int2(b | int(0x80000000u), blk_row[b]);
   if (k == 0 || (int)(skeys[k - 1] >> 32) != row) rl_ptr[row] = k;
   if (k == n_ent - 1) rl_ptr[n_n] = n_ent;
@@ -138,11 +138,8 @@ __global__ void k_set_slots(const int4* __restrict__ sets, int n_sets, const int
 }  // namespace
 
 size_t pattern_scratch_bytes(int n_keys, int n_rl_keys) {
-  size_t a = 0, b = 0, c = 0;
-  cub::DeviceRadixSort::SortKeys(nullptr, a, (const uint32_t*)nullptr, (uint32_t*)nullptr, n_keys);
-  cub::DeviceScan::ExclusiveSum(nullptr, b, (const int*)nullptr, (int*)nullptr, n_keys);
-  cub::DeviceRadixSort::SortKeys(nullptr, c, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                                 n_rl_keys);
+  const size_t a = sort_scratch_bytes_u32(n_keys, false), b = scan_scratch_bytes(n_keys),
+               c = sort_scratch_bytes_u64(n_rl_keys, false);
   return std::max(a, std::max(b, c));
 }
 
@@ -150,12 +147,10 @@ cudaError_t launch_pattern_blocks(const int4* sets, int n_sets, const int* graph
                                   cudaStream_t st) {
   const int K = 10 * n_sets + (1 + SW_K_GRAPH) * n_n;
   k_pat_keys<<<pblocks(n_sets + n_n), kPatThreads, 0, st>>>(sets, n_sets, graph, n_n, w.keys);
-  size_t bytes = w.tmp_bytes;
-  cudaError_t e = cub::DeviceRadixSort::SortKeys(w.tmp, bytes, w.keys, w.skeys, K, 0, 32, st);
+  cudaError_t e = radix_sort_u32(w.keys, w.skeys, nullptr, nullptr, K, 0, 32, w.tmp, w.tmp_bytes, st);
   if (e != cudaSuccess) return e;
   k_pat_head<<<pblocks(K), kPatThreads, 0, st>>>(w.skeys, K, w.flag);
-  bytes = w.tmp_bytes;
-  e = cub::DeviceScan::ExclusiveSum(w.tmp, bytes, w.flag, w.pos, K, st);
+  e = scan_sum(w.flag, w.pos, K, false, w.tmp, w.tmp_bytes, st);
   if (e != cudaSuccess) return e;
   k_pat_unique<<<pblocks(K), kPatThreads, 0, st>>>(w.skeys, w.flag, w.pos, K, w.keys, w.count);
   return cudaGetLastError();
@@ -164,16 +159,15 @@ cudaError_t launch_pattern_blocks(const int4* sets, int n_sets, const int* graph
 cudaError_t launch_pattern_fill(const int4* sets, int n_sets, const int* graph, int n_n, int nnzb,
                                 PatternScratch& w, unsigned long long* rl_keys, unsigned long long* rl_skeys,
                                 const SwDev& d, cudaStream_t st) {
-  k_pat_blocks<<<pblocks(nnzb), kPatThreads, 0, st>>>(w.keys, nnzb, n_n, d.row_ptr, d.col, d.blk_row);
+  k_pat_blocks<<<pblocks(nnzb), kPatThreads, 0, st>>>(w.keys, nnzb, n_n, d.row_ptr, d.col, d.blk_row, d.status);
   cudaError_t e = cudaMemsetAsync(d.blk_edge, 0, (size_t)nnzb * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_pat_edges<<<pblocks((long long)n_n * SW_K_GRAPH), kPatThreads, 0, st>>>(graph, n_n, d.row_ptr, d.col, d.blk_edge);
+  k_pat_edges<<<pblocks((long long)n_n * SW_K_GRAPH), kPatThreads, 0, st>>>(graph, n_n, d.row_ptr, d.col, d.blk_edge, d.status);
   k_rl_keys<<<pblocks(nnzb), kPatThreads, 0, st>>>(d.blk_row, d.col, nnzb, rl_keys);
-  size_t bytes = w.tmp_bytes;
-  e = cub::DeviceRadixSort::SortKeys(w.tmp, bytes, rl_keys, rl_skeys, 2 * nnzb, 0, 64, st);
+  e = radix_sort_u64(rl_keys, rl_skeys, nullptr, nullptr, 2 * nnzb, 0, 64, w.tmp, w.tmp_bytes, st);
   if (e != cudaSuccess) return e;
   const int n_ent = 2 * nnzb - n_n;
-  k_rl_fill<<<pblocks(n_ent), kPatThreads, 0, st>>>(rl_skeys, n_ent, n_n, d.blk_row, d.col, d.rl_ptr, d.rl_ent);
+  k_rl_fill<<<pblocks(n_ent), kPatThreads, 0, st>>>(rl_skeys, n_ent, n_n, d.blk_row, d.col, d.rl_ptr, d.rl_ent, nnzb, d.status);
   if (n_sets) k_set_slots<<<pblocks(n_sets), kPatThreads, 0, st>>>(sets, n_sets, d.row_ptr, d.col, d.set_slots);
   return cudaGetLastError();
 }

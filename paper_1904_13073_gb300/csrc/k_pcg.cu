@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 #include "sw_df.cuh"
@@ -463,7 +464,7 @@ __device__ __forceinline__ void stage_entries(const SwDev& d, const Real* A, int
     const int i = t + Gs * a;
     const int r0 = __ldg(d.rl_ptr + i), len = __ldg(d.rl_ptr + i + 1) - r0, e0 = soff[a];
     for (int k = lane; k < len; k += 32) {
-      const int2 ent = __ldg(d.rl_ent + r0 + k);
+      const int2 ent = checked_ent(__ldg(d.rl_ent + r0 + k), d.nnzb, d.n_n, d.status);
       const int e = e0 + k;
       if constexpr (kMode == kSpmvSmemA) {
         const Real* B = A + (size_t)(ent.x & 0x7fffffff) * 36;
@@ -627,7 +628,7 @@ k_pcg_f64(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) {
         } else {
           const int e1 = __ldg(d.rl_ptr + i + 1);
           for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
-            const int2 ent = __ldg(d.rl_ent + e);
+            const int2 ent = checked_ent(__ldg(d.rl_ent + e), d.nnzb, d.n_n, d.status);
             double p[6], out[6];
             get_p64(gz, pold, k > 0, beta, ent.y, p);
             entry_product<kSpmvRows>(A, sA, ent_cap, e, ent, p, out);
@@ -877,7 +878,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
         } else {
           const int e1 = __ldg(d.rl_ptr + i + 1);
           for (int e = __ldg(d.rl_ptr + i) + lane; e < e1; e += 32) {
-            const int2 ent = __ldg(d.rl_ent + e);
+            const int2 ent = checked_ent(__ldg(d.rl_ent + e), d.nnzb, d.n_n, d.status);
             Real p[6], out[6];
             late |= !get6_tagged(ucur, ent.y, tu, p, data_spins);
             entry_product<kSpmvRows>(A, sA, ent_cap, e, ent, p, out);

@@ -20,9 +20,9 @@
 // symmetric product: y_i += A_ij u_j and, off the diagonal, y_j += A_ijᵀ u_i.
 // Within a CTA, a group of 8 lanes serves up to two rows (the second row of
 // group g is row 2 G − 1 − g of the CTA's cost-sorted order, G groups, so
-// that the dearest row pairs with the cheapest); lane c < 6 of the group
-// keeps component c of the row's r in a register, and x, p, s sit in shared
-// memory.
+// that the dearest row pairs with the cheapest): in the product phase its
+// lanes take the rows' home blocks in turn, in the update phase lane c < 6
+// takes component c (r in a register; x, p, s in shared memory).
 //
 // Exchange, all by the producer into the consumer's shared memory (remote
 // stores: st.shared::cluster), so that every read on the critical path is a
@@ -45,7 +45,11 @@
 //                                                   -> cluster barrier
 // Every CTA takes the same decisions from bit-identical totals, so all of
 // them pass the same barriers and leave the loop together; after the last
-// barrier no CTA touches another's shared memory.
+// barrier no CTA touches another's shared memory.  The inner products are
+// accumulated in the accumulator type (double-float pairs or FP64) and
+// reduced by cascaded summation (sw_pcg.cuh).  The home blocks are staged
+// by bulk copies (cp.async.bulk, one per row, on an mbarrier whose wait is
+// bounded).
 #include <algorithm>
 #include <cstdint>
 #include <map>
@@ -54,6 +58,7 @@
 #include <vector>
 
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_pcg.cuh"
 
@@ -75,13 +80,14 @@ constexpr int kMaxCluster = 16;
 //   hb    [n_n + C]    per CTA, its rows' home-block offsets (nr + 1)
 //   go    [n_n + C]    per CTA, its rows' receive-slot offsets (nr + 1)
 //   po    [n_n + C]    per CTA, its rows' u-push offsets (nr + 1)
-//   blk   [nnzb]       per home block (CTA-major), its index in A
+//   blk   [nnzb]       per home block (CTA-major, row by row), its index in A
 //   col   [nnzb]       per home block, the local u slot of its column (own
 //                      row a, or halo slot nr + h)
 //   o2t   [nnzb]       per home block off the diagonal, (owner of its column
 //                      << 16) | receive slot there; -1 on the diagonal
 //   push  [total]      per u push, (peer CTA << 16) | the peer's u slot
-// NH and NP are the most halo rows and u pushes of a CTA.
+// NR, NB, NG, NH and NP are the most rows, home blocks, receive slots, halo
+// rows and u pushes of a CTA.
 struct PlanOff {
   int rb, bb, gb, pb, rows, hb, go, po, blk, col, o2t, push, total;
 };
@@ -108,7 +114,7 @@ __host__ __device__ inline PlanOff plan_off(int C, int n_n, int nnzb, int n_push
 // the remotely written sections (partials, u, receive slots) sit at the same
 // offsets in every CTA
 struct SmemPlan {   // byte offsets
-  unsigned part, u, recv, a, col, o2t, mi, xps, hb, go, po, push, rows, total;
+  unsigned part, u, recv, a, col, o2t, mi, xps, hb, go, po, push, rows, bar, total;
 };
 __host__ __device__ constexpr unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, int NP) {
@@ -126,7 +132,8 @@ __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, in
   L.po = al16(L.go + 4u * (NR + 1));
   L.push = al16(L.po + 4u * (NR + 1));
   L.rows = al16(L.push + 4u * NP);
-  L.total = al16(L.rows + 4u * NR);
+  L.bar = al16(L.rows + 4u * NR);                   // the staging copies' mbarrier
+  L.total = L.bar + 16u;
   return L;
 }
 
@@ -156,6 +163,25 @@ __device__ __forceinline__ void st_cl_f2(unsigned a, float x, float y) {
 __device__ __forceinline__ void st_cl_u64x2(unsigned a, unsigned long long x, unsigned long long y) {
   asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
 }
+// one bulk copy global -> this CTA's shared memory, completing on an mbarrier
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// bounded wait for phase 0 of an mbarrier; true if it completed (every thread of the CTA)
+__device__ __forceinline__ bool wait_phase0(unsigned bar) {
+  unsigned done = 0;
+  for (int spins = 0; spins < (1 << 20) && !done; ++spins) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(0u)
+        : "memory");
+  }
+  return __syncthreads_and(done != 0) != 0;
+}
 // every thread of every CTA of the cluster: the shared-memory writes before
 // it, local and remote, are visible to every CTA's reads after it
 __device__ __forceinline__ void cluster_barrier() {
@@ -163,30 +189,44 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// sum of v over the 8 lanes of a group (every lane gets it)
-__device__ __forceinline__ float group_sum(float v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  return v;
+// The group's sums of six values, reduce-scattered: lane l of the 8-lane
+// group (gl = l) returns the sum over the group of value l (l < 6; lanes 6
+// and 7 return the sums of two zeros).  Three exchange levels halve the
+// values a lane carries (7 shuffles instead of the 18 of six butterflies).
+__device__ __forceinline__ float group_reduce_scatter6(const float* v6, int gl) {
+  float v[8] = {v6[0], v6[1], v6[2], v6[3], v6[4], v6[5], 0.f, 0.f};
+  const bool b4 = gl & 4, b2 = gl & 2, b1 = gl & 1;
+  float w[4], x[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {   // keep values 4..7 on lanes with bit 2, 0..3 on the others
+    const float keep = b4 ? v[i + 4] : v[i], send = b4 ? v[i] : v[i + 4];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b2 ? w[i + 2] : w[i], send = b2 ? w[i] : w[i + 2];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  const float keep = b1 ? x[1] : x[0], send = b1 ? x[0] : x[1];
+  return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
-// The CTA's sums of two accumulators (every thread holds shares), in a
-// fixed order; every lane of warp 0 returns them.
+// The CTA's sums of two accumulators (every thread holds shares), by
+// cascaded summation in a fixed order; every lane of warp 0 returns them.
 template <typename Acc>
 __device__ __forceinline__ void cta_sum2(Acc& a, Acc& b, Acc (*s_w)[32]) {
   using O = AccOps<Acc>;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  a = warp_sum_acc(a);
-  b = warp_sum_acc(b);
+  a = warp_sum_cascaded(a);
+  b = warp_sum_cascaded(b);
   if (lane == 0) { s_w[0][wid] = a; s_w[1][wid] = b; }
   __syncthreads();
   if (wid == 0) {
     constexpr int kWarps = kCThreads / 32;
     a = lane < kWarps ? s_w[0][lane] : O::zero();
     b = lane < kWarps ? s_w[1][lane] : O::zero();
-    a = warp_sum_acc(a);
-    b = warp_sum_acc(b);
+    a = acc_norm(warp_sum_cascaded(a));
+    b = acc_norm(warp_sum_cascaded(b));
   }
 }
 
@@ -204,9 +244,9 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   const int NR = __ldg(P + 1), NB = __ldg(P + 2), NG = __ldg(P + 3), NH = __ldg(P + 5), NP = __ldg(P + 6);
   const int n_push = __ldg(P + kPlanHeader + 4 * (C + 1) - 1);   // the push prefix table's last entry
   const PlanOff off = plan_off(C, d.n_n, d.nnzb, n_push);
-  const int row0 = __ldg(P + off.rb + me), nr = __ldg(P + off.rb + me + 1) - row0;
-  const int blk0 = __ldg(P + off.bb + me);
-  const int push0 = __ldg(P + off.pb + me);
+  const int row0 = __ldg(P + off.rb + me), nr = checked_count(__ldg(P + off.rb + me + 1) - row0, NR, d.status);
+  const int blk0 = __ldg(P + off.bb + me), nb = checked_count(__ldg(P + off.bb + me + 1) - blk0, NB, d.status);
+  const int push0 = __ldg(P + off.pb + me), np = checked_count(__ldg(P + off.pb + me + 1) - push0, NP, d.status);
   const SmemPlan L = smem_plan(NR, NB, NG, NH, NP);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* sPart = reinterpret_cast<Acc*>(smem_raw + L.part);   // [sender][2]
@@ -230,41 +270,58 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   const int gbase = lane & ~7;                    // the group's first lane in the warp
   const bool comp = gl < 6;                       // this lane holds component gl of its rows
   const unsigned uBase = smem_u32(sU), recvBase = smem_u32(sRecv), partBase = smem_u32(sPart);
+  const unsigned bar = smem_u32(smem_raw + L.bar);
 
-  // ---- set-up: the plan's tables, the home blocks and M⁻¹ into shared memory
-  for (int a = tid; a < nr; a += kCThreads) sRows[a] = __ldg(P + off.rows + row0 + a);
+  // ---- set-up: the plan's tables and M⁻¹ by plain loads; the home blocks,
+  // contiguous in A row by row, by one bulk copy per row on an mbarrier
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   for (int a = tid; a <= nr; a += kCThreads) {
-    sHb[a] = __ldg(P + off.hb + row0 + me + a);
-    sGo[a] = __ldg(P + off.go + row0 + me + a);
-    sPo[a] = __ldg(P + off.po + row0 + me + a);
+    if (a < nr) sRows[a] = checked(__ldg(P + off.rows + row0 + a), d.n_n, d.status);
+    sHb[a] = checked_count(__ldg(P + off.hb + row0 + me + a), nb, d.status);
+    sGo[a] = checked_count(__ldg(P + off.go + row0 + me + a), NG, d.status);
+    sPo[a] = checked_count(__ldg(P + off.po + row0 + me + a), np, d.status);
+  }
+  for (int x = tid; x < np; x += kCThreads) sPush[x] = checked_pair(__ldg(P + off.push + push0 + x), C, NR + NH, d.status);
+  for (int e = tid; e < nb; e += kCThreads) {
+    sCol[e] = checked(__ldg(P + off.col + blk0 + e), NR + NH, d.status);
+    const int o2t = __ldg(P + off.o2t + blk0 + e);
+    sO2t[e] = o2t == -1 ? -1 : checked_pair(o2t, C, NG, d.status);
+  }
+  for (int t = tid; t < 18 * nr; t += kCThreads) sXps[t] = 0.f;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long st;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(st) : "r"(bar), "r"(144u * nb)
+                 : "memory");
+    (void)st;
   }
   __syncthreads();
-  const int nb = sHb[nr], np = sPo[nr];
-  for (int x = tid; x < np; x += kCThreads) sPush[x] = __ldg(P + off.push + push0 + x);
-  for (int e = tid; e < nb; e += kCThreads) {
-    sCol[e] = __ldg(P + off.col + blk0 + e);
-    sO2t[e] = __ldg(P + off.o2t + blk0 + e);
-  }
-  {
-    const float4* A4 = reinterpret_cast<const float4*>(d.A);
-    float4* sA4 = reinterpret_cast<float4*>(sA);
-    const int* blk = P + off.blk + blk0;
-    // one block (9 float4) per thread per pass, its index read once
-    for (int e = tid; e < nb; e += kCThreads) {
-      const float4* src = A4 + (size_t)__ldg(blk + e) * 9;
-      float4 v[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = __ldg(src + q);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) sA4[9 * e + q] = v[q];
-    }
+  const float* __restrict__ Ag = d.A;
+  for (int a = tid; a < nr; a += kCThreads) {
+    const int e0 = sHb[a], len = checked_count(sHb[a + 1] - e0, nb - e0, d.status);
+    // the row's first block; its others follow it in A
+    const int b0 = checked(__ldg(P + off.blk + blk0 + e0), (long long)d.nnzb - len + 1, d.status);
+    bulk_g2s(smem_u32(sA + 36 * (size_t)e0), Ag + 36 * (size_t)b0, 144u * (unsigned)len, bar);
   }
   for (int t = tid; t < nr * 21; t += kCThreads) {
     const int a = t / 21, q = t - 21 * a;
     sMi[t] = __ldg(d.minv + 21 * (size_t)sRows[a] + q);
   }
-  for (int t = tid; t < 18 * nr; t += kCThreads) sXps[t] = 0.f;
-  __syncthreads();
+  if (!wait_phase0(bar)) {
+    // the copies did not complete within the bound: report it, let them
+    // land (bounded), and stage the blocks with plain loads instead
+    if (tid == 0) atomicOr(d.status, kStatusTimeout);
+    wait_phase0(bar);
+    for (int t = tid; t < nb * 36; t += kCThreads) {
+      const int e = t / 36;
+      sA[t] = __ldg(Ag + 36 * (size_t)checked(__ldg(P + off.blk + blk0 + e), d.nnzb, d.status) + (t - 36 * e));
+    }
+    __syncthreads();
+  }
 
   // rows of this group: a = g, and a = 2G − 1 − g
   int arow[2];
@@ -318,12 +375,15 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   int state = kGearOk;
   cluster_barrier();   // every CTA's halo holds u₀
 
+  // second rows exist only in the upper groups: whole warps without any skip them
+  const int hmax = __any_sync(0xffffffffu, arow[1] < nr) ? 2 : 1;
   for (int k = 0; k < K; ++k) {
     // ---- A: w's home part, the transposed products out, δ's share
     Acc del = O::zero();
-    float wh[2];
+    float wh[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      if (h >= hmax) break;   // warp-uniform
       const int a = arow[h];
       const bool on = a < nr;
       const int e0 = on ? sHb[a] : 0, e1 = on ? sHb[a + 1] : 0;
@@ -359,23 +419,16 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
           o1[2 * bp + 1] += tb;
           dt += ui[2 * bp] * ta + ui[2 * bp + 1] * tb;
         }
-        const bool diag = e == e0;   // the diagonal block leads its row
-        del = O::add(del, O::prod(dt, diag ? 1.f : 2.f));
-        if (!diag) {
-          const int tg = sO2t[e];
+        const int tg = sO2t[e];
+        del = O::add(del, O::prod(dt, tg < 0 ? 1.f : 2.f));
+        if (tg >= 0) {   // off the diagonal: A_ijᵀ u_i to its receive slot at the column's owner
           const unsigned ta = at_rank(recvBase + 24u * (unsigned)(tg & 0xffff), (unsigned)(tg >> 16), me);
           st_cl_f2(ta, o2[0], o2[1]);
           st_cl_f2(ta + 8, o2[2], o2[3]);
           st_cl_f2(ta + 16, o2[4], o2[5]);
         }
       }
-      float mine = 0.f;
-#pragma unroll
-      for (int b = 0; b < 6; ++b) {
-        const float v = group_sum(o1[b]);
-        if (gl == b) mine = v;
-      }
-      wh[h] = mine;
+      wh[h] = group_reduce_scatter6(o1, gl);
     }
     Acc ga = gam, da = del;
     cta_sum2(ga, da, s_w);
@@ -390,8 +443,8 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         gs = sPart[2 * lane];
         ds = sPart[2 * lane + 1];
       }
-      gs = warp_sum_acc(gs);
-      ds = warp_sum_acc(ds);
+      gs = acc_norm(warp_sum_cascaded(gs));
+      ds = acc_norm(warp_sum_cascaded(ds));
       if (lane == 0) {
         float al, be;
         const int st = gear_step(k, gs, ds, g_prev, a_prev, &al, &be);
@@ -402,29 +455,17 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         g_prev = gs;
       }
     }
-    float wt[2];
+    // lane c adds component c of the row's received products, in slot order
+    float wt[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      if (h >= hmax) break;   // warp-uniform
       const int a = arow[h];
-      const bool on = a < nr;
+      const bool on = a < nr && comp;
+      float acc = wh[h];
       const int x1 = on ? sGo[a + 1] : 0;
-      float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int x = (on ? sGo[a] : 0) + gl; x < x1; x += kGroup) {
-        const float2* v = reinterpret_cast<const float2*>(sRecv + 6 * (size_t)x);
-#pragma unroll
-        for (int hh = 0; hh < 3; ++hh) {
-          const float2 q = v[hh];
-          acc[2 * hh] += q.x;
-          acc[2 * hh + 1] += q.y;
-        }
-      }
-      float mine = 0.f;
-#pragma unroll
-      for (int b = 0; b < 6; ++b) {
-        const float v = group_sum(acc[b]);
-        if (gl == b) mine = v;
-      }
-      wt[h] = wh[h] + mine;
+      for (int x = on ? sGo[a] : 0; x < x1; ++x) acc += sRecv[6 * x + gl];
+      wt[h] = acc;
     }
     __syncthreads();
     state = s_state;
@@ -433,6 +474,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
       gam = O::zero();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
+        if (h >= hmax) break;   // warp-uniform
         const int a = arow[h];
         const bool on = a < nr;
         const float* mi = sMi + 21 * (on ? a : 0);
@@ -488,6 +530,12 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
       d.dq[2 * j + 1] = qe;
     }
   }
+}
+
+// The hop the cluster PCG pays twice per iteration, alone: `iters` cluster
+// barriers of C CTAs of kCThreads threads (its latency bound's unit).
+__global__ void __launch_bounds__(kCThreads, 1) k_cluster_barrier_loop(int iters) {
+  for (int k = 0; k < iters; ++k) cluster_barrier();
 }
 
 template <typename Acc>
@@ -563,8 +611,10 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
   std::vector<int> order(n_n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return code[a] < code[b]; });
-  // contiguous ranges of that order, balanced by shared-memory bytes
-  auto bytes = [&](int j) { return 160.0 + 180.0 * (row_ptr[j + 1] - row_ptr[j]) + 24.0 * ng_col[j]; };
+  // contiguous ranges of that order, balanced by shared-memory bytes (a
+  // row's u, x, p, s, M⁻¹ and tables; each home block's 36 values and
+  // tables; each receive slot)
+  auto bytes = [&](int j) { return 230.0 + 152.0 * (row_ptr[j + 1] - row_ptr[j]) + 24.0 * ng_col[j]; };
   double total = 0;
   for (int j = 0; j < n_n; ++j) total += bytes(j);
   std::vector<int> cut(C + 1, n_n);
@@ -584,9 +634,7 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
   for (int c = 0; c < C; ++c) {
     std::vector<int> r(order.begin() + cut[c], order.begin() + cut[c + 1]);
     if ((int)r.size() > kMaxRowsPerCta) return false;
-    auto cost = [&](int j) {
-      return (row_ptr[j + 1] - row_ptr[j] + kGroup - 1) / kGroup + (ng_col[j] + kGroup - 1) / kGroup;
-    };
+    auto cost = [&](int j) { return (row_ptr[j + 1] - row_ptr[j] + kGroup - 1) / kGroup; };
     std::stable_sort(r.begin(), r.end(), [&](int a, int b) { return cost(a) > cost(b); });
     for (size_t a = 0; a < r.size(); ++a) {
       owner[r[a]] = c;
@@ -628,7 +676,7 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
     NP = std::max(NP, np);
     n_push += np;
   }
-  if (NB >= (1 << 16) || NG >= (1 << 16) || NR + NH >= (1 << 16)) return false;
+  if (NG >= (1 << 16) || NR + NH >= (1 << 16)) return false;
   const SmemPlan L = smem_plan(NR, NB, NG, NH, NP);
   if (L.total > smem_limit) return false;
   const PlanOff o = plan_off(C, n_n, nnzb, n_push);
@@ -655,19 +703,19 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
     plan[o.gb + c] = gb;
     plan[o.pb + c] = pb;
     int e = 0, x = 0, y = 0;
-    for (size_t a = 0; a < rows[c].size(); ++a) {
+    const int nr = (int)rows[c].size();
+    for (int a = 0; a < nr; ++a) {
       const int i = rows[c][a];
-      plan[o.rows + rb + (int)a] = i;
-      plan[o.hb + rb + c + (int)a] = e;
-      plan[o.go + rb + c + (int)a] = x;
-      plan[o.po + rb + c + (int)a] = y;
+      plan[o.rows + rb + a] = i;
+      plan[o.hb + rb + c + a] = e;
+      plan[o.go + rb + c + a] = x;
+      plan[o.po + rb + c + a] = y;
       e += row_ptr[i + 1] - row_ptr[i];
       auto& inc = incoming[i];
       std::sort(inc.begin(), inc.end());
       for (const auto& kv : inc) slot_of[kv.second] = x++;
       for (int tg : pushes[i]) plan[o.push + pb + y++] = tg;
     }
-    const int nr = (int)rows[c].size();
     plan[o.hb + rb + c + nr] = e;
     plan[o.go + rb + c + nr] = x;
     plan[o.po + rb + c + nr] = y;
@@ -749,6 +797,44 @@ cudaError_t launch_pcg_cluster(const BatchHost& b, int gn_it, int pcg_iters, cud
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+// Seconds of one cluster barrier of C CTAs (kCThreads threads each), from
+// two timed launches of n1 and n2 barriers (the difference removes the
+// launch): the unit of the cluster PCG's latency bound.
+cudaError_t cluster_barrier_cost(int C, double* us_per_barrier) {
+  const void* fn = reinterpret_cast<const void*>(k_cluster_barrier_loop);
+  cudaError_t e = C > 8 ? cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev[4];
+  for (auto& x : ev) cudaEventCreate(&x);
+  float ms[2] = {0.f, 0.f};
+  const int n[2] = {64, 1064};
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      int it = n[k];
+      void* args[] = {&it};
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(kCThreads);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaEventRecord(ev[2 * k], 0);
+      e = cudaLaunchKernelExC(&cfg, fn, args);
+      cudaEventRecord(ev[2 * k + 1], 0);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[2 * k + 1]);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]);
+      if (rep > 0) ms[k] += t;   // the first round warms up
+    }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e == cudaSuccess && us_per_barrier) *us_per_barrier = 1000.0 * (ms[1] - ms[0]) / 2.0 / (n[1] - n[0]);
+  return e;
 }
 
 }  // namespace sw

@@ -18,6 +18,7 @@
 //                   definite stops the iterations with T as it is.
 //   k_rigid_fold    T_j ← T T_j for every node.
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 #include "sw_assoc.cuh"
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kSurfTile) k_rigid_reduce(Batch bt, int it) {
 #pragma unroll
   for (int k = 0; k < kRigidSums; ++k) v[k] = 0.f;
   if (d.rigid[8] == 0.0 && i < d.n_s) {   // not stopped
-    const DQ b = blend4(d.dq, d.knn[i], d.w[i], d.ref_slot[i]);
+    const DQ b = blend4(d.dq, checked4(d.knn[i], d.n_n, d.status), d.w[i], checked(d.ref_slot[i], 4, d.status));
     const float n2 = dq_norm2(b);
     if (n2 > 0.f) {
       const float inv = 1.f / n2;

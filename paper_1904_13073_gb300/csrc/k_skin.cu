@@ -8,6 +8,7 @@
 // id and only a strictly smaller distance displaces a kept one, so ties go to
 // the lower id.  Nodes are staged through shared memory in tiles.
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 
 namespace sw {

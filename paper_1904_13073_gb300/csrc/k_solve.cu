@@ -16,6 +16,7 @@
 //                       atomics.
 //   (K7+K8, the PCG and the node update, are in k_pcg.cu.)
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_assoc.cuh"
 
@@ -49,13 +50,19 @@ __device__ __forceinline__ void block_atomic_sum(T v, T* dst) {
 
 // J_aᵀ J_b for J_a = [−[xa]× | I], J_b = [−[xb]× | I] (3x6 each), scaled:
 //   [[(xa·xb) I − xb xaᵀ, [xa]×], [−[xb]×, I]]
+// The rotation part's diagonal (xa·xb − xa_p xb_p) is formed as the sum of
+// the other two coordinates' products: the difference would cancel when the
+// points lie near axis p (near the optical axis for p = z), leaving FP32
+// rounding of |xa||xb| in an entry that is far smaller.
 __device__ __forceinline__ void add_reg_pair(float* acc, float s, float3 xa, float3 xb) {
-  const float ab = dot3(xa, xb);
   const float a[3] = {xa.x, xa.y, xa.z}, b[3] = {xb.x, xb.y, xb.z};
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) acc[p * 6 + q] += s * ((p == q ? ab : 0.f) - b[p] * a[q]);
+    for (int q = 0; q < 3; ++q) {
+      const int p1 = (p + 1) % 3, p2 = (p + 2) % 3;
+      acc[p * 6 + q] += s * (p == q ? a[p1] * b[p1] + a[p2] * b[p2] : -b[p] * a[q]);
+    }
   // [a]× = [[0,-a2,a1],[a2,0,-a0],[-a1,a0,0]]
   const float ax[9] = {0.f, -a[2], a[1], a[2], 0.f, -a[0], -a[1], a[0], 0.f};
   const float bx[9] = {0.f, -b[2], b[1], b[2], 0.f, -b[0], -b[1], b[0], 0.f};
@@ -86,7 +93,9 @@ __global__ void k_solve_begin(Batch bt) {
   for (int k = threadIdx.x; k < kMaxGn; k += blockDim.x) {
     d.e_depth[k] = 0.0; d.e_reg[k] = 0.0; d.n_corr[k] = 0; d.pcg_rz[k] = 0.0;
   }
-  if (threadIdx.x == 0) *d.status &= kStatusDepthTimeout;   // the solve's bits; the frame's depth stage keeps its own
+  // the solve's bits; the frame's depth stage keeps its own, and a failed
+  // index check (checked build) stays until the model is set again
+  if (threadIdx.x == 0) *d.status &= kStatusDepthTimeout | kStatusBounds;
 }
 
 // Threads [0, n8), n8 = 8 n_n rounded up to a whole warp: a group of 8
@@ -122,7 +131,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
     if (on) {   // out-edge j -> m
       const float3 pj = f3(d.node_p[j]);
       x = node_apply(d, j, pj);
-      const int m = d.graph[j * SW_K_GRAPH + q];
+      const int m = checked(d.graph[j * SW_K_GRAPH + q], d.n_n, d.status);
       const float3 y = node_apply(d, m, pj);
       const float3 r = sl * (x - y);
       ereg += dot3(r, r);
@@ -132,7 +141,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
     }
     const int e1 = on ? d.in_ptr[j + 1] : 0;
     for (int e = (on ? d.in_ptr[j] : 0) + q; e < e1; e += 8) {   // in-edges m -> j
-      const int m = d.in_src[e];
+      const int m = checked(d.in_src[e], d.n_n, d.status);
       const float3 pm = f3(d.node_p[m]);
       const float3 y = node_apply(d, j, pm);
       const float3 r = sl * (node_apply(d, m, pm) - y);
@@ -157,19 +166,21 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
       const float S[9] = {ko * x.x * x.x + v[9],  ko * x.x * x.y + v[10], ko * x.x * x.z + v[11],
                           ko * x.x * x.y + v[10], ko * x.y * x.y + v[12], ko * x.y * x.z + v[13],
                           ko * x.x * x.z + v[11], ko * x.y * x.z + v[13], ko * x.z * x.z + v[14]};
-      const float tr = S[0] + S[4] + S[8];
       const float ax[9] = {0.f, -sy[2], sy[1], sy[2], 0.f, -sy[0], -sy[1], sy[0], 0.f};
       float acc[36];
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          acc[p * 6 + c] = l * ((p == c ? tr : 0.f) - S[p * 3 + c]);
+          // Σ(|y|² δ_pc − y_p y_c); on the diagonal the sum of the other two
+          // squares, without the cancellation of |y|² − y_p²
+          const int p1 = (p + 1) % 3, p2 = (p + 2) % 3;
+          acc[p * 6 + c] = l * (p == c ? S[4 * p1] + S[4 * p2] : -S[p * 3 + c]);
           acc[p * 6 + 3 + c] = l * ax[p * 3 + c];
           acc[(3 + p) * 6 + c] = -l * ax[p * 3 + c];
           acc[(3 + p) * 6 + 3 + c] = p == c ? l * cnt : 0.f;
         }
-      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)d.row_ptr[j] * 36);
+      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)checked(d.row_ptr[j], d.nnzb, d.status) * 36);
 #pragma unroll
       for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
 #pragma unroll
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
     }
   } else if (b - n8 < d.nnzb) {
     const int bi = b - n8;
-    const int i = d.blk_row[bi], j = d.col[bi];
+    const int i = checked(d.blk_row[bi], d.n_n, d.status), j = checked(d.col[bi], d.n_n, d.status);
     if (i != j) {
       float acc[36];
 #pragma unroll
@@ -226,10 +237,10 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
   float res = 0.f;
   if (i < d.n_s) {
     const float4 v4 = d.v_ref[i], n4 = d.n_ref[i];
-    const int4 ids = d.knn[i];
+    const int4 ids = checked4(d.knn[i], d.n_n, d.status);
     const float4 w = d.w[i];
-    const int rs = d.ref_slot[i];
-    set = d.set_id[i];
+    const int rs = checked(d.ref_slot[i], 4, d.status);
+    set = checked(d.set_id[i], d.n_sets, d.status);
     const DQ b = blend4(d.dq, ids, w, rs);
     const float n2 = dq_norm2(b);
     int pix = -1;
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
 #pragma unroll
       for (int k = 0; k < 36; ++k) acc[k] = 0.f;
       int cur = sset[t0];
-      int slot = __ldg(d.set_slots + (size_t)cur * 14 + item);
+      int slot = checked(__ldg(d.set_slots + (size_t)cur * 14 + item), d.nnzb, d.status);
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
@@ -328,7 +339,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
 #pragma unroll
           for (int k = 0; k < 36; ++k) acc[k] = 0.f;
           cur = st_;
-          slot = __ldg(d.set_slots + (size_t)cur * 14 + item);
+          slot = checked(__ldg(d.set_slots + (size_t)cur * 14 + item), d.nnzb, d.status);
         }
         const float* Jt = sJ + t * kJS;
         float ja[6], jb[6];
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       const int a = item - 10;
       float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       int cur = sset[t0];
-      int node = __ldg(d.set_slots + (size_t)cur * 14 + 10 + a);
+      int node = checked(__ldg(d.set_slots + (size_t)cur * 14 + 10 + a), d.n_n, d.status);
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
@@ -354,7 +365,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
 #pragma unroll
           for (int k = 0; k < 6; ++k) acc[k] = 0.f;
           cur = st_;
-          node = __ldg(d.set_slots + (size_t)cur * 14 + 10 + a);
+          node = checked(__ldg(d.set_slots + (size_t)cur * 14 + 10 + a), d.n_n, d.status);
         }
         const float* Jt = sJ + t * kJS;
         const float rr = Jt[24];

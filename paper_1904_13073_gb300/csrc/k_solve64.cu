@@ -6,6 +6,7 @@
 // precision reference, so it favours plainness over speed: one thread per
 // surfel adding its ten 6x6 blocks and four 6-vectors with FP64 atomics.
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_math64.cuh"
 #include "sw_assoc.cuh"
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble64(Batch bt, int gn_it
   if (b == 0) *d.pcg_epoch += 1;   // a new epoch for the stamps of the PCG launch that follows
   double ereg = 0.0;
   if (b < d.nnzb) {
-    const int i = d.blk_row[b], j = d.col[b];
+    const int i = checked(d.blk_row[b], d.n_n, d.status), j = checked(d.col[b], d.n_n, d.status);
     const double sl = d.sqrt_lambda, l = sl * sl;
     double acc[36];
     for (int k = 0; k < 36; ++k) acc[k] = 0.0;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble64(Batch bt, int gn_it
       const D3 pj = d3(d.node_p[j]);
       const D3 x = node_apply64(d, j, pj);
       for (int e = 0; e < SW_K_GRAPH; ++e) {      // out-edges j -> m
-        const int m = d.graph[j * SW_K_GRAPH + e];
+        const int m = checked(d.graph[j * SW_K_GRAPH + e], d.n_n, d.status);
         const D3 r = sl * (x - node_apply64(d, m, pj));
         ereg += dot3(r, r);
         add_reg_pair64(acc, l, x, x);
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble64(Batch bt, int gn_it
         gj[3] += sl * r.x; gj[4] += sl * r.y; gj[5] += sl * r.z;
       }
       for (int e = d.in_ptr[j]; e < d.in_ptr[j + 1]; ++e) {   // in-edges m -> j
-        const int m = d.in_src[e];
+        const int m = checked(d.in_src[e], d.n_n, d.status);
         const D3 pm = d3(d.node_p[m]);
         const D3 y = node_apply64(d, j, pm);
         const D3 r = sl * (node_apply64(d, m, pm) - y);
@@ -110,9 +111,9 @@ __global__ void __launch_bounds__(kSurfTile) k_data_assemble64(Batch bt, int gn_
   bool valid = false;
   if (i < d.n_s) {
     const float4 v4 = d.v_ref[i], n4 = d.n_ref[i];
-    const int4 ids = d.knn[i];
+    const int4 ids = checked4(d.knn[i], d.n_n, d.status);
     const float4 w = d.w[i];
-    const int rs = d.ref_slot[i];
+    const int rs = checked(d.ref_slot[i], 4, d.status);
     const DQ64 b = blend4_64(d.dq64, ids, w, rs);
     const double n2 = dq_norm2(b);
     int pix = -1;
@@ -141,16 +142,16 @@ __global__ void __launch_bounds__(kSurfTile) k_data_assemble64(Batch bt, int gn_
         const double ws = (q.W * ref.W + dot3(q.A, ref.A)) >= 0.0 ? wk[k] : -wk[k];
         node_jacobian(gr, q, ws, J + 6 * k);
       }
-      const int* slots = d.set_slots + (size_t)d.set_id[i] * 14;
+      const int* slots = d.set_slots + (size_t)checked(d.set_id[i], d.n_sets, d.status) * 14;
       int item = 0;
       for (int a = 0; a < 4; ++a)
         for (int c = a; c < 4; ++c, ++item) {
-          double* dst = d.A64 + (size_t)__ldg(slots + item) * 36;
+          double* dst = d.A64 + (size_t)checked(__ldg(slots + item), d.nnzb, d.status) * 36;
           for (int p = 0; p < 6; ++p)
             for (int q = 0; q < 6; ++q) atomicAdd(dst + p * 6 + q, J[6 * a + p] * J[6 * c + q]);
         }
       for (int a = 0; a < 4; ++a) {
-        double* dst = d.g64 + (size_t)__ldg(slots + 10 + a) * 6;
+        double* dst = d.g64 + (size_t)checked(__ldg(slots + 10 + a), d.n_n, d.status) * 6;
         for (int k = 0; k < 6; ++k) atomicAdd(dst + k, J[6 * a + k] * res);
       }
     }

@@ -17,6 +17,7 @@
 //   k_vis_mark   one thread per pixel: the winner is visible; the pixel is
 //                reset to empty, so the map is cleared once at creation.
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 #include "sw_assoc.cuh"
 
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(kSurfTile) k_vis_splat(Batch bt, int from_live
     const float4 vl = d.v_live[i], nl = d.n_live[i];
     v = f3(vl); n = f3(nl); r = vl.w;
   } else {
-    DQ b = blend4(d.dq, d.knn[i], d.w[i], d.ref_slot[i]);
+    DQ b = blend4(d.dq, checked4(d.knn[i], d.n_n, d.status), d.w[i], checked(d.ref_slot[i], 4, d.status));
     const float n2 = dq_norm2(b);
     const float4 vr = d.v_ref[i];
     r = vr.w;
@@ -78,7 +79,8 @@ __global__ void __launch_bounds__(kSurfTile) k_vis_splat(Batch bt, int from_live
       if (!(t > 0.f)) continue;
       const float d2 = dist2_rn(__fmul_rn(t, qx), __fmul_rn(t, qy), t, v.x, v.y, v.z);
       if (!(d2 <= r2)) continue;
-      atomicMin(d.vis_map + (size_t)y * d.W + x, ((unsigned long long)__float_as_uint(t) << 32) | id);
+      atomicMin(d.vis_map + checked(y * d.W + x, (long long)d.W * d.H, d.status),
+                ((unsigned long long)__float_as_uint(t) << 32) | id);
     }
   }
 }
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(256) k_vis_mark(Batch bt, int from_live) {
   const unsigned long long key = *cell;
   if (key == kVisEmpty) return;
   *cell = kVisEmpty;
-  d.visible[d.inv_perm[(unsigned)(key & 0xffffffffu)]] = 1;
+  d.visible[checked(d.inv_perm[checked((int)(key & 0xffffffffu), d.n_s, d.status)], d.n_s, d.status)] = 1;
 }
 
 inline Batch with_kind(const BatchHost& b, int kind) {

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 
 namespace sw {
@@ -48,7 +49,7 @@ __global__ void k_index(const float4* __restrict__ v, int n, unsigned long long*
 
 // per depth pixel: its 16 sub-pixels; distance <= fuse_dist and normal dot >=
 // fuse_normal; highest confidence, then nearest, then lowest index
-__global__ void k_select(const float4* __restrict__ v, const float4* __restrict__ nl,
+__global__ void k_select(const float4* __restrict__ v, int n, const float4* __restrict__ nl,
                          const float4* __restrict__ vmap, const float4* __restrict__ nmap,
                          const unsigned long long* __restrict__ imap, int W, int H, float fuse_dist,
                          float fuse_normal, int* __restrict__ target) {
@@ -67,6 +68,9 @@ __global__ void k_select(const float4* __restrict__ v, const float4* __restrict_
         const unsigned long long key = imap[(size_t)(4 * y + sy) * (4 * W) + 4 * x + sx];
         if (key == kEmptyKey) continue;
         const unsigned o = (unsigned)(key & 0xffffffffu);
+        // checked build: this stream-free call has no status word, so an
+        // out-of-range surfel id is skipped without a record
+        if (!index_ok((long long)o, n, nullptr)) continue;
         const float4 a = v[o], b = nl[o];
         const float d2 = dist2_rn(a.x, a.y, a.z, V.x, V.y, V.z);
         const float dt = dot_rn(f3(b), f3(N));
@@ -123,7 +127,7 @@ sw_status sw_fusion_targets_static(const float* v_live4, const float* n_live4, i
     k_index<<<(n_surfels + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float4*>(v_live4), n_surfels, imap,
                                                       width, height, fx, fy, cx, cy);
   k_select<<<(width * height + 255) / 256, 256, 0, st>>>(
-      reinterpret_cast<const float4*>(v_live4), reinterpret_cast<const float4*>(n_live4),
+      reinterpret_cast<const float4*>(v_live4), n_surfels, reinterpret_cast<const float4*>(n_live4),
       reinterpret_cast<const float4*>(vmap4), reinterpret_cast<const float4*>(nmap4), imap, width, height,
       fuse_dist, fuse_normal, target);
   e = cudaGetLastError();

@@ -19,6 +19,19 @@
 // other admitted streams.  Every stream's surfels, node graph and
 // warp field stay resident on the device between its frames.
 //
+// A batch step costs about the same whatever share of its members is active:
+// the persistent PCG's CTAs are divided among all members when the batch is
+// built, so a step is as long as its largest active member's PCG on its
+// share.  Under light load that is slower than running the few queued frames
+// one after another through their streams' own calls (each with the whole
+// GPU).  The adaptive policy (sw_server_set_adaptive, on by default) takes,
+// every step, the cheaper of the two by measured times: an average of the
+// batch's step time per size class of the step (reset when the membership
+// changes) against the sum of the queued streams' own frame times (a
+// per-stream average; a stream not yet measured counts at the average of the
+// measured ones, and while none is measured a step of one or two frames runs
+// them one by one, which measures them).
+//
 // In the plain mode (sw_server_set_plain) each step instead takes the single
 // oldest queued frame and runs it through its stream's own calls, one stream
 // at a time: the reference that continuous batching is measured against.
@@ -79,6 +92,13 @@ struct sw_server {
   double window_ms = 0.0;        // how long a step may wait for more streams' frames
   bool appending = false;        // sw_append_frame after every served frame
   bool plain = false;            // one frame per step through its stream's own calls (no batching)
+  bool adaptive = true;          // per step, the batch or the streams' own calls, whichever is cheaper
+  // measured costs for the adaptive policy (worker thread only), in ms
+  static constexpr int kSizeClasses = 8;   // step sizes 1, 2, 3-4, 5-8, ..., 65+
+  double tb[kSizeClasses] = {};  // batch step time by size class (0: not measured)
+  std::map<int, double> tp;      // per stream: its frame through its own calls
+  double tp_sum = 0.0;           // sum and count of the per-stream averages
+  int tp_count = 0;
   std::chrono::steady_clock::time_point t0;
   int next_id = 1;
   std::map<int, SrvStream*> streams;    // every open stream, by id
@@ -93,6 +113,38 @@ struct sw_server {
 };
 
 namespace {
+
+int size_class(int k) {
+  int c = 0;
+  while (c + 1 < sw_server::kSizeClasses && (1 << c) < k) ++c;
+  return c;
+}
+
+double ema(double old, double x) { return old > 0.0 ? 0.7 * old + 0.3 * x : x; }
+
+// The adaptive policy's choice for a step of these streams' frames: true to
+// run them one by one through their own calls.
+bool cheaper_alone(const sw_server* S, const std::vector<int>& ids) {
+  const int k = (int)ids.size();
+  double alone = 0.0;
+  bool all_known = true;
+  const double prior = S->tp_count ? S->tp_sum / S->tp_count : 0.0;
+  for (int id : ids) {
+    auto it = S->tp.find(id);
+    if (it != S->tp.end()) alone += it->second;
+    else { all_known = false; alone += prior; }
+  }
+  if (!all_known && S->tp_count == 0) return k <= 2;   // nothing measured alone yet
+  // the batch's time at this size, else at the nearest measured size
+  const int c = size_class(k);
+  double batch = 0.0;
+  for (int d = 0; d < sw_server::kSizeClasses && batch == 0.0; ++d) {
+    if (c - d >= 0 && S->tb[c - d] > 0.0) batch = S->tb[c - d];
+    else if (c + d < sw_server::kSizeClasses && S->tb[c + d] > 0.0) batch = S->tb[c + d];
+  }
+  if (batch == 0.0) return k <= 2;   // the batch not measured yet
+  return alone < batch;
+}
 
 void release_stream(SrvStream* s) {
   if (s->h) sw_destroy_stream(s->h);
@@ -115,6 +167,12 @@ void release_closed(sw_server* S) {
   }
   for (int id : gone) {
     SrvStream* s = S->streams[id];
+    auto t = S->tp.find(id);
+    if (t != S->tp.end()) {
+      S->tp_sum -= t->second;
+      S->tp_count--;
+      S->tp.erase(t);
+    }
     if (s->h) S->composition_changed = true;
     release_stream(s);
     S->order.erase(std::remove(S->order.begin(), S->order.end(), id), S->order.end());
@@ -228,18 +286,34 @@ void worker_main(sw_server* S) {
     std::vector<sw_status> fstat(taken.size(), SW_OK);   // per taken frame
     std::vector<sw_append_stats> app(taken.size());
     std::vector<sw_status> app_status(taken.size(), SW_OK);
-    double t_start = 0.0;
-    if (S->plain) {
-      // the plain path: the frame's stream alone, through its own calls
-      SrvStream* s = taken_ptrs[0];
-      t_start = now_ms(S->t0);
-      sw_status st = sw_upload_depth(s->h, s->slots[taken[0].slot], 0, taken[0].frame_id);
-      if (st == SW_OK) st = sw_solve_frame(s->h, S->gn, S->pcg, nullptr);
-      if (st == SW_OK) st = sw_fuse_frame(s->h);
-      int nn = 0;
-      if (st == SW_OK) st = sw_read_nodes(s->h, nullptr, nullptr, 0, &nn);   // waits; reports a breakdown
-      fstat[0] = st;
-      if (S->appending && st == SW_OK) app_status[0] = sw_append_frame(s->h, &app[0]);
+    std::vector<double> f_start(taken.size(), 0.0), f_done(taken.size(), 0.0);
+    const bool alone = S->plain || (S->adaptive && cheaper_alone(S, taken_ids));
+    if (alone) {
+      // each frame's stream alone, through its own calls, oldest frame first
+      std::vector<size_t> by_age(taken.size());
+      for (size_t k = 0; k < taken.size(); ++k) by_age[k] = k;
+      std::sort(by_age.begin(), by_age.end(),
+                [&](size_t a, size_t b) { return taken[a].submit_ms < taken[b].submit_ms; });
+      for (size_t k : by_age) {
+        SrvStream* s = taken_ptrs[k];
+        f_start[k] = now_ms(S->t0);
+        sw_status st = sw_upload_depth(s->h, s->slots[taken[k].slot], 0, taken[k].frame_id);
+        if (st == SW_OK) st = sw_solve_frame(s->h, S->gn, S->pcg, nullptr);
+        if (st == SW_OK) st = sw_fuse_frame(s->h);
+        int nn = 0;
+        if (st == SW_OK) st = sw_read_nodes(s->h, nullptr, nullptr, 0, &nn);   // waits; reports a breakdown
+        fstat[k] = st;
+        const double t_fused = now_ms(S->t0);
+        if (S->appending && st == SW_OK) app_status[k] = sw_append_frame(s->h, &app[k]);
+        f_done[k] = now_ms(S->t0);
+        if (st == SW_OK) {   // the stream's own frame time (appending apart: both paths append alike)
+          double& t = S->tp[taken_ids[k]];
+          const double old = t;
+          t = ema(t, t_fused - f_start[k]);
+          S->tp_sum += t - old;
+          if (old == 0.0) S->tp_count++;
+        }
+      }
     } else {
     if (S->composition_changed || !S->batch) {
       if (S->batch) sw_batch_destroy(S->batch);
@@ -249,6 +323,7 @@ void worker_main(sw_server* S) {
       status = sw_batch_create(hs.data(), (int)hs.size(), nullptr, &S->batch);
       S->batch_ids = members;
       S->composition_changed = false;
+      for (double& t : S->tb) t = 0.0;   // a new batch: its step times are measured again
     }
     const int n = (int)S->batch_ids.size();
     depths.assign(n, nullptr);
@@ -261,13 +336,18 @@ void worker_main(sw_server* S) {
       frame_ids[pos] = taken[k].frame_id;
       active[pos] = 1;
     }
-    t_start = now_ms(S->t0);
+    const double t_start = now_ms(S->t0);
     if (status == SW_OK) status = sw_batch_set_active(S->batch, active.data());
     if (status == SW_OK) status = sw_batch_upload_depth(S->batch, depths.data(), 0, frame_ids.data());
     if (status == SW_OK) status = sw_batch_solve(S->batch, S->gn, S->pcg, nullptr);
     if (status == SW_OK) status = sw_batch_fuse(S->batch);
     std::vector<int> member_status(n, 0);
     const sw_status sync = S->batch ? sw::batch_member_status(S->batch, member_status.data()) : status;
+    const double t_fused = now_ms(S->t0);
+    if (status == SW_OK && sync == SW_OK) {
+      double& t = S->tb[size_class((int)taken.size())];
+      t = ema(t, t_fused - t_start);
+    }
     for (size_t k = 0; k < taken.size(); ++k) {
       const int pos = (int)(std::find(S->batch_ids.begin(), S->batch_ids.end(), taken_ids[k]) - S->batch_ids.begin());
       fstat[k] = status != SW_OK ? status : sync != SW_OK ? sync : (sw_status)member_status[pos];
@@ -275,8 +355,15 @@ void worker_main(sw_server* S) {
     if (S->appending && status == SW_OK && sync == SW_OK)
       for (size_t k = 0; k < taken.size(); ++k)
         if (fstat[k] == SW_OK) app_status[k] = sw_append_frame(taken_ptrs[k]->h, &app[k]);
-    }
     const double t_done = now_ms(S->t0);
+    for (size_t k = 0; k < taken.size(); ++k) {
+      f_start[k] = t_start;
+      f_done[k] = t_done;
+    }
+    }
+    double busy = 0.0;
+    for (size_t k = 0; k < taken.size(); ++k)
+      if (alone || k == 0) busy += f_done[k] - f_start[k];
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (size_t k = 0; k < taken.size(); ++k) {
@@ -292,15 +379,16 @@ void worker_main(sw_server* S) {
         r.appended = S->appending && r.status == SW_OK ? app[k].appended : 0;
         r.n_surfels = s->n_s;
         r.submit_ms = taken[k].submit_ms;
-        r.start_ms = t_start;
-        r.done_ms = t_done;
-        r.batch_size = (int)taken.size();
+        r.start_ms = f_start[k];
+        r.done_ms = f_done[k];
+        r.batch_size = alone ? 1 : (int)taken.size();
         S->results.push_back(r);
       }
       S->completed += (long long)taken.size();
       S->st.steps++;
       S->st.frames += (long long)taken.size();
-      S->st.busy_ms += t_done - t_start;
+      S->st.busy_ms += busy;
+      if (alone && !S->plain) S->st.steps_alone++;
       S->st.memory_in_use = sw_memory_in_use();
     }
     S->cv.notify_all();
@@ -467,6 +555,13 @@ sw_status sw_server_read_stats(sw_server_handle S, sw_server_stats* out) {
   std::lock_guard<std::mutex> lk(S->mu);
   *out = S->st;
   out->memory_in_use = sw_memory_in_use();
+  return SW_OK;
+}
+
+sw_status sw_server_set_adaptive(sw_server_handle S, int enable) {
+  if (!S || (enable != 0 && enable != 1)) return SW_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->adaptive = enable != 0;
   return SW_OK;
 }
 

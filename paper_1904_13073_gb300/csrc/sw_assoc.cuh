@@ -4,6 +4,7 @@
 // same operations on the same FP32 inputs.
 #pragma once
 #include "sw_internal.h"
+#include "sw_check.cuh"
 #include "sw_math.cuh"
 
 namespace sw {
@@ -27,7 +28,7 @@ __device__ __forceinline__ int associate_one(const SwDev& d, float3 vl, float3 n
   const float v = project_rn(d.fy, vl.y, vl.z, d.cy);
   const float px = floorf(__fadd_rn(u, 0.5f)), py = floorf(__fadd_rn(v, 0.5f));
   if (!(px >= 0.f && px < (float)d.W && py >= 0.f && py < (float)d.H)) return -1;
-  const int pix = (int)py * d.W + (int)px;
+  const int pix = checked((int)py * d.W + (int)px, (long long)d.W * d.H, d.status);
   const float4 V = d.vmap[pix];
   if (!(V.w > 0.f)) return -1;
   const float4 N = d.nmap[pix];

@@ -32,6 +32,7 @@ constexpr int kStatusBreakdown = 1;      // a diagonal block is not positive def
 constexpr int kStatusTimeout = 4;        // a bounded wait of the PCG (a reduction or a neighbour's vector) gave up
 constexpr int kStatusDepthTimeout = 8;   // the depth stage's bounded wait for its TMA tile gave up (the tile was
                                          // then loaded with plain loads); cleared by the next depth upload
+constexpr int kStatusBounds = 16;       // checked build (-DSW_BOUNDS_CHECK): a device index was out of range
 
 // Failure injection for the tests of the bounded device waits
 // (sw_debug_inject_wait_fault): what a kernel withholds so that the waits
@@ -205,6 +206,7 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
                         size_t* smem_out);
 bool cluster_pcg_fits(int precision, int C, size_t smem);
 int cluster_pcg_active(int precision, int C, size_t smem);   // clusters that can run at once (< 0: CUDA error)
+cudaError_t cluster_barrier_cost(int C, double* us_per_barrier);   // one cluster barrier, measured
 cudaError_t launch_pcg_cluster(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
 int pcg_blocks_per_sm(int precision);
 int pcg_threads();
@@ -233,8 +235,8 @@ struct AppendBufs {
   int* stay;          // per existing surfel, caller order: 1 if it stays
   int* pos;           // its new caller index (exclusive scan of stay)
   int* counts;        // kAppCounts device counters
-  void* cub_tmp;      // selection / scan scratch
-  size_t cub_bytes;
+  void* scan_tmp;     // compaction scan scratch
+  size_t scan_bytes;
 };
 constexpr int kAppAccepted = 16, kAppLowWeight = 32, kAppCompressive = 64;
 enum AppCount { kAppNCand = 0, kAppNAcc, kAppNLow, kAppNComp, kAppNStay, kAppCounts = 8 };
@@ -245,7 +247,7 @@ struct AppendParams {
   double h;           // finite-difference step of the strain, metres
   int t_low;          // t_low_confid
 };
-size_t append_cub_bytes(int n_pixels, int n_surfels);
+size_t append_scan_bytes(int n_pixels, int n_surfels);
 cudaError_t launch_append_candidates(const SwDev& d, const AppendBufs& a, cudaStream_t st);
 cudaError_t launch_append_eval(const SwDev& d, const AppendBufs& a, const AppendParams& ap, int n_cand,
                                cudaStream_t st);
@@ -265,7 +267,7 @@ void launch_find_sets(const SwDev& d, int sorted_sets, const int4* tknn, int fir
 // n_sets + 1, ... and their 10 blocks of the pattern in set_slots (which must
 // have room); *no_block = 1 when a pair of their nodes has no block (scratch:
 // sorted n_app keys, head and rank n_app ints each)
-size_t new_sets_cub_bytes(int n);
+size_t new_sets_scratch_bytes(int n);
 cudaError_t launch_new_sets(const SwDev& d, const unsigned long long* keys, unsigned long long* sorted, int* head,
                             int* rank, int n_app, int n_missing, int* set_of, int* n_new_sets, int* no_block,
                             void* tmp, size_t tmp_bytes, cudaStream_t st);
@@ -289,6 +291,19 @@ void launch_skin_merge(const SwDev& d, const float4* tv, int n, int n_old, int4*
 
 // ------------------------------------------------------------------ JᵀJ pattern
 // Device scratch of the pattern build (k_pattern.cu); K = 10 n_sets + 9 n_n keys.
+// k_sort.cu: prefix sums and a stable LSD radix sort (8-bit digits) over
+// device arrays.  `tmp` is scratch of at least the *_bytes size for n; the
+// sort's input is left untouched and must not alias its output.  Errors
+// (bad sizes, too little scratch) come back as cudaErrorInvalidValue.
+size_t scan_scratch_bytes(int n);
+cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, size_t tmp_bytes, cudaStream_t st);
+size_t sort_scratch_bytes_u32(int n, bool values);
+size_t sort_scratch_bytes_u64(int n, bool values);
+cudaError_t radix_sort_u32(const uint32_t* kin, uint32_t* kout, const int* vin, int* vout, int n, int begin_bit,
+                           int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t st);
+cudaError_t radix_sort_u64(const unsigned long long* kin, unsigned long long* kout, const int* vin, int* vout, int n,
+                           int begin_bit, int end_bit, void* tmp, size_t tmp_bytes, cudaStream_t st);
+
 struct PatternScratch {
   uint32_t* keys;     // K: the pair keys, then the unique blocks in order
   uint32_t* skeys;    // K: sorted keys

@@ -49,6 +49,39 @@ struct AccOps<double> {
   static __device__ __forceinline__ double value(double v) { return v; }
 };
 
+// Cheaper addition for long reduction trees of double-float values
+// (cascaded summation, Ogita, Rump & Oishi 2005, "Sum2"): the high parts
+// are added by an error-free TwoSum and all low parts and errors by plain
+// FP32 additions, with no renormalisation on the way; the result, once
+// renormalised by acc_norm, is as accurate as a sum evaluated in twice the
+// working precision and then rounded.  For FP64 accumulators a plain add.
+__device__ __forceinline__ DF df_add_cascaded(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return DF{s, __fadd_rn(__fadd_rn(a.lo, b.lo), e)};
+}
+template <typename Acc>
+__device__ __forceinline__ Acc acc_add_cascaded(Acc a, Acc b) {
+  if constexpr (std::is_same<Acc, DF>::value) return df_add_cascaded(a, b);
+  else return a + b;
+}
+template <typename Acc>
+__device__ __forceinline__ Acc acc_norm(Acc a) {
+  if constexpr (std::is_same<Acc, DF>::value) {
+    float s, e;
+    two_sum(a.hi, a.lo, s, e);
+    return DF{s, e};
+  } else {
+    return a;
+  }
+}
+template <typename Acc>
+__device__ __forceinline__ Acc warp_sum_cascaded(Acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = acc_add_cascaded(v, AccOps<Acc>::shfl_xor(v, o));
+  return v;
+}
+
 template <typename Acc>
 __device__ __forceinline__ Acc warp_sum_acc(Acc v) {
 #pragma unroll

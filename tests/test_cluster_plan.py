@@ -79,12 +79,12 @@ def replay_spmv(P, row_ptr, colidx, A, u):
     def cta(c):
         r0, nr = int(P["rb"][c]), int(P["rb"][c + 1] - P["rb"][c])
         sl = slice(r0 + c, r0 + c + nr + 1)
-        return r0, nr, P["rows"][r0:r0 + nr], P["hb"][sl], P["go"][sl], P["po"][sl]
+        return nr, P["rows"][r0:r0 + nr], P["hb"][sl], P["go"][sl], P["po"][sl]
     # each CTA's u slots: own rows, then halo slots filled by the owners' pushes
     slot_row = [dict() for _ in range(C)]
     U = [dict() for _ in range(C)]
     for c in range(C):
-        _, nr, rows, _, _, po = cta(c)
+        nr, rows, _, _, po = cta(c)
         assert nr <= P["NR"]
         for a, i in enumerate(rows):
             slot_row[c][a] = int(i)
@@ -101,14 +101,14 @@ def replay_spmv(P, row_ptr, colidx, A, u):
     w = np.zeros((n, 6))
     recv = [dict() for _ in range(C)]
     for c in range(C):
-        _, nr, rows, hb, _, _ = cta(c)
+        nr, rows, hb, _, _ = cta(c)
+        assert int(P["bb"][c + 1] - P["bb"][c]) == hb[nr] <= P["NB"]
         for a, i in enumerate(rows):
             for e in range(hb[a], hb[a + 1]):
-                b = int(P["blk"][P["bb"][c] + e])
-                ci = int(P["col"][P["bb"][c] + e])
+                k = int(P["bb"][c]) + e
+                b, ci, tg = int(P["blk"][k]), int(P["col"][k]), int(P["o2t"][k])
                 assert slot_row[c][ci] == colidx[b] and row_ptr[i] <= b < row_ptr[i + 1]
                 w[i] += A[b] @ U[c][ci]
-                tg = int(P["o2t"][P["bb"][c] + e])
                 if e == hb[a]:
                     assert colidx[b] == i and tg == -1          # the diagonal block leads its row
                 else:
@@ -116,7 +116,8 @@ def replay_spmv(P, row_ptr, colidx, A, u):
                     assert slot not in recv[owner]
                     recv[owner][slot] = (int(colidx[b]), A[b].T @ u[i])
     for c in range(C):
-        _, nr, rows, _, go, _ = cta(c)
+        nr, rows, _, go, _ = cta(c)
+        assert int(P["gb"][c + 1] - P["gb"][c]) == go[nr] <= P["NG"]
         assert sorted(recv[c]) == list(range(int(go[nr])))  # every slot filled once
         for a, j in enumerate(rows):
             for x in range(go[a], go[a + 1]):

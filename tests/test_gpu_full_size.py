@@ -71,16 +71,22 @@ def _data_jacobian_magnitude(o, idx, odq, tn):
 
 
 def _oracle_scale(o, odq, pix):
-    """The entry-wise scale of the system's computation (see the JᵀJ test)."""
+    """The entry-wise scale of the system's computation (see the JᵀJ test),
+    and for Jᵀe also Σ |J̃| |n|ᵀ(|v'| + |V|): the magnitude of each
+    residual's computation n·(v' − V) from points ~1 m away, which an FP32
+    evaluation errs by a few unit roundoffs of however small r is."""
     mask = (pix >= 0) & ~OS.unskinned(OS.DQ.blend(odq, o.knn, o.w))
     idx = np.nonzero(mask)[0]
     tv = o.maps["V"].reshape(-1, 3)[pix[idx]]
     tn = o.maps["N"].reshape(-1, 3)[pix[idx]]
     r, _ = OS.data_terms(o.v_ref[idx], o.knn[idx], o.w[idx], odq, tv, tn)
+    _, vl, _ = OS.warp_surfels(o.v_ref[idx], o.n_ref[idx], o.knn[idx], o.w[idx], odq)
+    rmag = np.sum(np.abs(tn) * (np.abs(vl) + np.abs(tv)), axis=1)
     Jm = _data_jacobian_magnitude(o, idx, odq, tn)
     reg = OS.reg_terms(o.node_p, odq, o.graph, o.p.lam)
     _, _, S, gS = OS.assemble(o.pattern, len(o.node_p), o.knn[idx], Jm, np.abs(r), reg, absolute=True)
-    return S, gS
+    _, _, _, gR = OS.assemble(o.pattern, len(o.node_p), o.knn[idx], Jm, rmag, reg, absolute=True)
+    return S, gS, gR
 
 
 def test_full_size_jtj_matches_oracle(full):
@@ -90,8 +96,13 @@ def test_full_size_jtj_matches_oracle(full):
     the regulariser's Jacobian entries are its own magnitude), the bound of
     FP32 evaluation and summation in any order.  Every block entry within
     1e-4 of that scale; every entry not dominated by cancellation
-    (|A_ij| >= 1e-2 of its scale) within 1e-4 relative; Jᵀe likewise.  The
-    largest error relative to the plain sums |J|ᵀ|J| is reported beside it."""
+    (|A_ij| >= 1e-2 of its scale) within 1e-4 relative.  Jᵀe within 1e-4 of
+    Σ |J̃| |r|, and every entry within 1e-4 relative plus 8 unit roundoffs
+    of Σ |J̃| |n|ᵀ(|v'| + |V|): each FP32 residual errs by a few roundoffs
+    of the points' magnitude (an FP32 evaluation of the oracle's terms on
+    this linearisation errs by at most 0.16 of that second term, and by up
+    to 6e-4 relative on entries above 1e-2 of Σ |J̃| |r|).  The largest
+    error relative to the plain sums |J|ᵀ|J| is reported beside it."""
     scene = full
     p = Pair(scene)
     try:
@@ -111,7 +122,7 @@ def test_full_size_jtj_matches_oracle(full):
         # the oracle's system under its own decisions, the boundary surfels as the library decided
         pix = np.where(np.isin(np.arange(len(corr)), flipped), corr, pix_o)
         A, g, S0, gS0 = _oracle_system(o, odq, pix)
-        S, gS = _oracle_scale(o, odq, pix)
+        S, gS, gR = _oracle_scale(o, odq, pix)
         rows, cols, vals, gg = sw.sw_debug_read_jtj(p.h, nnzb, len(scene.node_p))
         orows, ocols = A.rows_cols()
         assert nnzb == int(np.sum(orows <= ocols)) and np.all(rows <= cols)
@@ -125,18 +136,20 @@ def test_full_size_jtj_matches_oracle(full):
               f"oracle {want[worst]:.9g} |J|ᵀ|J| {S0.vals[at][worst]:.6g} scale {scale[worst]:.6g}; "
               f"block diag gpu {np.diag(vals[b])} oracle {np.diag(want[b])}")
         assert np.all(err <= 1e-4 * scale + 1e-12), float(np.max(err / (scale + 1e-30)))
-        big = np.abs(want) >= 1e-2 * scale
+        big = (np.abs(want) >= 1e-2 * scale) & (want != 0)
         rel = float(np.max(err[big] / np.abs(want[big])))
         assert rel <= 1e-4, rel
         gerr = np.abs(gg - g.reshape(-1))
-        assert np.all(gerr <= 1e-4 * gS.reshape(-1) + 1e-12)
-        gbig = np.abs(g.reshape(-1)) >= 1e-2 * gS.reshape(-1)
-        grel = float(np.max(gerr[gbig] / np.abs(g.reshape(-1)[gbig])))
-        assert grel <= 1e-4, grel
+        assert np.all(gerr <= 1e-4 * gS.reshape(-1) + 1e-12), float(np.max(gerr / (gS.reshape(-1) + 1e-30)))
+        u32 = 2.0 ** -24
+        gexcess = np.maximum(gerr - 1e-4 * np.abs(g.reshape(-1)), 0.0) / (u32 * gR.reshape(-1) + 1e-30)
+        grel = float(np.max(gexcess))
+        assert grel <= 8.0, grel
         print(f"full-size JtJ: {nnzb} blocks, {n_corr} terms, {len(flipped)} boundary decisions, "
               f"max error {float(np.max(err / (scale + 1e-30))):.2e} of the computation scale "
               f"({plain:.2e} of |J|ᵀ|J|), max entry-relative error {rel:.2e} "
-              f"({int(big.sum())} of {big.size} entries), Jte {grel:.2e}")
+              f"({int(big.sum())} of {big.size} entries), Jte error beyond 1e-4 relative {grel:.2f} unit "
+              f"roundoffs of the residuals' magnitude")
     finally:
         p.close()
 

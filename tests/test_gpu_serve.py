@@ -75,16 +75,19 @@ def _compare(scene, dq_got, dq_ref):
     assert np.max(np.abs(OS.node_transform(dq_got, p) - OS.node_transform(dq_ref, p))) < 2e-6
 
 
-def test_served_streams_match_their_results_alone():
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_served_streams_match_their_results_alone(adaptive):
     """Four streams of different sizes submit frames from their own threads
     with random gaps; one joins late and one leaves early.  Each stream's
-    warp field equals the one it gets alone."""
+    warp field equals the one it gets alone, whether every step is one batch
+    or the adaptive policy runs some steps stream by stream."""
     scenes = _scenes()
     frames = {0: [1, 2, 3], 1: [1, 2, 3], 2: [1, 2], 3: [1, 2, 3]}
     refs = {k: _alone(s, frames[k]) for k, s in enumerate(scenes)}
     srv = sw.sw_server_create(0, GN, PCG, queue_depth=2)
     try:
         sw.sw_server_set_batch_window(srv, 20.0)
+        sw.sw_server_set_adaptive(srv, adaptive)
         ids = {}
         for k in (0, 1, 2):
             ids[k] = _open(srv, scenes[k])
@@ -124,11 +127,13 @@ def test_served_streams_match_their_results_alone():
         for k, sid in ids.items():
             seq = [r["frame_id"] for r in results if r["stream"] == sid]
             assert seq == frames[k]
-        assert max(r["batch_size"] for r in results) >= 2   # batches formed while frames overlapped
+        if not adaptive:
+            assert max(r["batch_size"] for r in results) >= 2   # batches formed while frames overlapped
         for k in range(4):
             _compare(scenes[k], got[k], refs[k])
         st = sw.sw_server_read_stats(srv)
         assert st["frames"] == len(results) and st["steps"] >= 1
+        assert adaptive or st["steps_alone"] == 0
     finally:
         sw.sw_server_destroy(srv)
 
