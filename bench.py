@@ -139,12 +139,10 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # ncu capture of this workload's kernels as they are now (the "pcg" stage is
-# the preconditioner launch plus the PCG launch);
-# profiles/k_pcg_gear_plain_full_300k_2048.md and
+# the preconditioner launch plus the cluster PCG launch);
+# profiles/k_pcg_cluster_plain_full_300k_2048.md and
 # profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-# (the preconditioner launch changed after its capture, so the "pcg" stage
-# has no current figure; the PCG launch alone read 3.07 MB)
-PROFILED_TRAFFIC = {"pcg": None, "data_assembly": 25.227264e6 + 0.021504e6}
+PROFILED_TRAFFIC = {"pcg": 557824.0 + 3039232.0, "data_assembly": 25.227264e6 + 0.021504e6}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):

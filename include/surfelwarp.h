@@ -198,6 +198,16 @@ sw_status sw_set_node_dq(sw_handle h, const float* dq8, int n_nodes);
 /* Association of the last Gauss-Newton iteration: pixel index y*W+x per
  * surfel, or -1. */
 sw_status sw_read_correspondence(sw_handle h, int* pix, int cap, int* n_out);
+/* Test hook: with enable = 1, every later solve of this stream also keeps
+ * each Gauss-Newton iteration's association (device memory for
+ * SW_MAX_GN_ITERS x max_surfels ints, from the stream's budget, allocated
+ * at the first enable); 0 stops keeping it.  sw_read_correspondence_iter
+ * returns iteration gn_iter's (0-based) of the last solve, as
+ * sw_read_correspondence does the last one (SW_ERR_NOT_INITIALIZED while
+ * recording is off).  A comparison can then give another implementation
+ * the library's decisions where the two differ at a rounding boundary. */
+sw_status sw_debug_record_correspondence(sw_handle h, int enable);
+sw_status sw_read_correspondence_iter(sw_handle h, int gn_iter, int* pix, int cap, int* n_out);
 /* Replace the live surfels (v4: x y z r, n4: nx ny nz c; only xyz are used). */
 sw_status sw_debug_set_live(sw_handle h, const float* v4, const float* n4, int n);
 /* Run projective association on the current live surfels (no warp); the

@@ -143,6 +143,8 @@ _SIGS = {
     "sw_debug_block_inverse": [_P, _I, _I, _P, _P],
     "sw_debug_scan": [_P, _I, _I, _P],
     "sw_debug_set_skin_node": [_P, _I, _I, _I],
+    "sw_debug_record_correspondence": [_P, _I],
+    "sw_read_correspondence_iter": [_P, _I, _P, _I, ctypes.POINTER(_I)],
     "sw_debug_radix_sort": [_I, _P, _P, _I, _I, _I, _P, _P],
     "sw_server_create": [ctypes.c_size_t, _I, _I, _I, ctypes.POINTER(_P)],
     "sw_server_destroy": [_P],
@@ -361,6 +363,18 @@ def sw_read_correspondence(h):
     n = _count_surfels(h)
     pix = np.empty(n, np.int32)
     _check(lib().sw_read_correspondence(h, pix.ctypes.data_as(_P), n, None), h)
+    return pix
+
+
+def sw_debug_record_correspondence(h, enable):
+    _check(lib().sw_debug_record_correspondence(h, int(bool(enable))), h)
+
+
+def sw_read_correspondence_iter(h, gn_iter):
+    """The association of Gauss-Newton iteration gn_iter of the last solve (recording on)."""
+    n = _count_surfels(h)
+    pix = np.empty(n, np.int32)
+    _check(lib().sw_read_correspondence_iter(h, int(gn_iter), pix.ctypes.data_as(_P), n, None), h)
     return pix
 
 

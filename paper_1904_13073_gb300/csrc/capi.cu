@@ -111,6 +111,7 @@ struct sw_stream {
   Runner* run = nullptr;     // the stream's own one-stream runner
   std::vector<int> rl_ptr_host;   // per block row, the start of its SpMV entries (PCG work sizing)
   int cplan_ctas = 0;             // cluster size of the stream's cluster-PCG plan (0: none)
+  int* corr_rec_buf = nullptr;    // sw_debug_record_correspondence: kMaxGn x max_surfels
   size_t cplan_smem = 0;          // shared memory per CTA that plan needs
   // ordering against batches this stream belongs to
   cudaEvent_t batch_done = nullptr;   // recorded by the last batch call (owned by the batch)
@@ -1491,6 +1492,31 @@ sw_status sw_debug_set_skin_node(sw_handle s, int surfel, int slot, int node) {
   SW_CUDA(s, cudaMemcpyAsync(reinterpret_cast<int*>(s->h.knn + surfel) + slot, &node, sizeof(int),
                              cudaMemcpyHostToDevice, s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
+  return SW_OK;
+}
+
+sw_status sw_debug_record_correspondence(sw_handle s, int enable) {
+  if (!s || (enable != 0 && enable != 1)) return fail(s, SW_ERR_INVALID_ARG, "bad argument");
+  if (enable && !s->corr_rec_buf)
+    SW_TRY(A(s, &s->corr_rec_buf, (size_t)kMaxGn * std::max(1, s->p.max_surfels)));
+  int* want = enable ? s->corr_rec_buf : nullptr;
+  if (s->h.corr_rec != want) {
+    SW_CUDA(s, cudaStreamSynchronize(s->st));
+    s->h.corr_rec = want;
+    // the runners' device tables carry the pointer: the stream's own is
+    // rebuilt now, a batch's at its next call
+    s->version++;
+    if (s->has_model && s->run) SW_TRY(build_runner(s->run, s));
+  }
+  return SW_OK;
+}
+
+sw_status sw_read_correspondence_iter(sw_handle s, int gn_iter, int* pix, int cap, int* n_out) {
+  SW_TRY(need_model(s, cap));
+  if (!s->h.corr_rec) return fail(s, SW_ERR_NOT_INITIALIZED, "recording is off (sw_debug_record_correspondence)");
+  if (gn_iter < 0 || gn_iter >= kMaxGn) return fail(s, SW_ERR_INVALID_ARG, "gn_iter out of range");
+  if (n_out) *n_out = s->h.n_s;
+  if (pix) SW_TRY(d2h_perm(s, s->h.corr_rec + (size_t)gn_iter * s->h.n_s, pix, 1, true));
   return SW_OK;
 }
 

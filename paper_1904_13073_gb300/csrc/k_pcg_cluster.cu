@@ -399,33 +399,46 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         const int ci = sCol[e];
         const float4 u4 = *reinterpret_cast<const float4*>(sU + 8 * ci);
         const float2 u2 = *reinterpret_cast<const float2*>(sU + 8 * ci + 4);
-        const float uj[6] = {u4.x, u4.y, u4.z, u4.w, u2.x, u2.y};
+        // u_j in component pairs; the products run on packed FP32 pairs
+        // (each lane of a pair an ordinary FP32 FMA, rounded alike)
+        const float2 uj[3] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w), u2};
         const float4* A4 = reinterpret_cast<const float4*>(sA + 36 * (size_t)e);
-        float o2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float2 o2[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         float dt = 0.f;
 #pragma unroll
         for (int bp = 0; bp < 3; ++bp) {   // rows 2bp and 2bp + 1 of the block
           const float4 q0 = A4[3 * bp], q1 = A4[3 * bp + 1], q2 = A4[3 * bp + 2];
-          const float ra[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
-          const float rb[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-          float ta = 0.f, tb = 0.f;
+          const float2 ra[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+          const float2 rb[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+          // (A u_j) of both rows as pairs of partial sums over even and odd columns
+          float2 ta = __fmul2_rn(ra[0], uj[0]), tb = __fmul2_rn(rb[0], uj[0]);
+          ta = __ffma2_rn(ra[1], uj[1], ta);
+          tb = __ffma2_rn(rb[1], uj[1], tb);
+          ta = __ffma2_rn(ra[2], uj[2], ta);
+          tb = __ffma2_rn(rb[2], uj[2], tb);
+          const float sa = ta.x + ta.y, sb = tb.x + tb.y;
+          // (A_ijᵀ u_i): rows 2bp and 2bp + 1 weighted by u_i's components
+          const float2 wa = make_float2(ui[2 * bp], ui[2 * bp]), wb = make_float2(ui[2 * bp + 1], ui[2 * bp + 1]);
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            ta += ra[c] * uj[c];
-            tb += rb[c] * uj[c];
-            o2[c] += ra[c] * ui[2 * bp] + rb[c] * ui[2 * bp + 1];
-          }
-          o1[2 * bp] += ta;
-          o1[2 * bp + 1] += tb;
-          dt += ui[2 * bp] * ta + ui[2 * bp + 1] * tb;
+          for (int c = 0; c < 3; ++c) o2[c] = __ffma2_rn(rb[c], wb, __ffma2_rn(ra[c], wa, o2[c]));
+          o1[2 * bp] += sa;
+          o1[2 * bp + 1] += sb;
+          dt += ui[2 * bp] * sa + ui[2 * bp + 1] * sb;
         }
         const int tg = sO2t[e];
-        del = O::add(del, O::prod(dt, tg < 0 ? 1.f : 2.f));
+        // δ's share: exact times 1 or 2, added by a cascaded (TwoSum) step
+        del = acc_add_cascaded(del, acc_from<Acc>(tg < 0 ? dt : 2.f * dt));
         if (tg >= 0) {   // off the diagonal: A_ijᵀ u_i to its receive slot at the column's owner
-          const unsigned ta = at_rank(recvBase + 24u * (unsigned)(tg & 0xffff), (unsigned)(tg >> 16), me);
-          st_cl_f2(ta, o2[0], o2[1]);
-          st_cl_f2(ta + 8, o2[2], o2[3]);
-          st_cl_f2(ta + 16, o2[4], o2[5]);
+          const unsigned slot = (unsigned)(tg & 0xffff);
+          const unsigned ta = at_rank(recvBase + 24u * slot, (unsigned)(tg >> 16), me);
+          // a slot is 24 bytes: even slots start 16-byte aligned, odd ones 8 bytes past
+          if (slot & 1u) {
+            st_cl_f2(ta, o2[0].x, o2[0].y);
+            st_cl_f4(ta + 8, make_float4(o2[1].x, o2[1].y, o2[2].x, o2[2].y));
+          } else {
+            st_cl_f4(ta, make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y));
+            st_cl_f2(ta + 16, o2[2].x, o2[2].y);
+          }
         }
       }
       wh[h] = group_reduce_scatter6(o1, gl);
@@ -495,7 +508,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         }
         if (on && comp) {
           sU[8 * a + gl] = u;
-          gam = O::add(gam, O::prod(rr[h], u));
+          gam = acc_add_cascaded(gam, O::prod(rr[h], u));
         }
       }
       __syncwarp();   // the group's six components of u written before its lanes push them
@@ -645,34 +658,52 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
   }
   // halos: per CTA, the other CTAs' rows its home blocks reference, in
   // (owner, local row) order; each gets a u slot after the CTA's own rows
-  std::vector<std::map<int, int>> halo(C);   // CTA -> (global row -> u slot)
+  // (halo_slot[c n_n + j], -1 where row j is not in CTA c's halo)
+  std::vector<int> halo_slot((size_t)C * n_n, -1);
+  std::vector<std::vector<int>> halo_rows(C);   // per CTA, its halo rows in slot order
   int NH = 0, NB = 0, NG = 0;
   for (int c = 0; c < C; ++c) {
-    std::vector<std::pair<int, int>> ext_rows;
+    std::vector<long long> ext;
     int nb = 0, ng = 0;
+    int* hs = halo_slot.data() + (size_t)c * n_n;
     for (int i : rows[c]) {
       nb += row_ptr[i + 1] - row_ptr[i];
       ng += ng_col[i];
-      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b)
-        if (owner[col[b]] != c) ext_rows.push_back({owner[col[b]], local[col[b]]});
+      for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        const int j = col[b];
+        if (owner[j] != c && hs[j] == -1) {
+          hs[j] = -2;
+          ext.push_back(((long long)owner[j] << 32) | local[j]);
+        }
+      }
     }
-    std::sort(ext_rows.begin(), ext_rows.end());
-    ext_rows.erase(std::unique(ext_rows.begin(), ext_rows.end()), ext_rows.end());
+    std::sort(ext.begin(), ext.end());
     const int nr = (int)rows[c].size();
-    for (size_t h = 0; h < ext_rows.size(); ++h)
-      halo[c][rows[ext_rows[h].first][ext_rows[h].second]] = nr + (int)h;
-    NH = std::max(NH, (int)ext_rows.size());
+    halo_rows[c].resize(ext.size());
+    for (size_t h = 0; h < ext.size(); ++h) {
+      const int j = rows[ext[h] >> 32][ext[h] & 0xffffffff];
+      hs[j] = nr + (int)h;
+      halo_rows[c][h] = j;
+    }
+    NH = std::max(NH, (int)ext.size());
     NB = std::max(NB, nb);
     NG = std::max(NG, ng);
   }
-  // u pushes: per own row, the CTAs holding it as halo, with their slot
-  std::vector<std::vector<int>> pushes(n_n);
+  // u pushes: per own row, the CTAs holding it as halo (in CTA order), with their slot
+  std::vector<int> push_ptr(n_n + 1, 0), push_tg;
   for (int c = 0; c < C; ++c)
-    for (const auto& kv : halo[c]) pushes[kv.first].push_back((c << 16) | kv.second);
+    for (int j : halo_rows[c]) ++push_ptr[j + 1];
+  for (int j = 0; j < n_n; ++j) push_ptr[j + 1] += push_ptr[j];
+  push_tg.resize(push_ptr[n_n]);
+  {
+    std::vector<int> fill(push_ptr.begin(), push_ptr.end() - 1);
+    for (int c = 0; c < C; ++c)
+      for (int j : halo_rows[c]) push_tg[fill[j]++] = (c << 16) | halo_slot[(size_t)c * n_n + j];
+  }
   int NP = 0, n_push = 0;
   for (int c = 0; c < C; ++c) {
     int np = 0;
-    for (int i : rows[c]) np += (int)pushes[i].size();
+    for (int i : rows[c]) np += push_ptr[i + 1] - push_ptr[i];
     NP = std::max(NP, np);
     n_push += np;
   }
@@ -690,11 +721,17 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
       for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) home[b] = e++;
   }
   // receive slots of each row j at its owner: its column's off-diagonal
-  // blocks (i, j) in (home CTA, home block index) order
-  std::vector<std::vector<std::pair<long long, int>>> incoming(n_n);   // (order key, block)
-  for (int i = 0; i < n_n; ++i)
-    for (int b = row_ptr[i] + 1; b < row_ptr[i + 1]; ++b)
-      incoming[col[b]].push_back({((long long)owner[i] << 32) | home[b], b});
+  // blocks (i, j) in (home CTA, home block index) order, which is the order
+  // of the CTAs, their rows and the rows' blocks
+  std::vector<int> inc_ptr(n_n + 1, 0), inc_blk;
+  for (int j = 0; j < n_n; ++j) inc_ptr[j + 1] = inc_ptr[j] + ng_col[j];
+  inc_blk.resize(inc_ptr[n_n]);
+  {
+    std::vector<int> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int c = 0; c < C; ++c)
+      for (int i : rows[c])
+        for (int b = row_ptr[i] + 1; b < row_ptr[i + 1]; ++b) inc_blk[fill[col[b]]++] = b;
+  }
   std::vector<int> slot_of(nnzb, -1);
   int rb = 0, bb = 0, gb = 0, pb = 0;
   for (int c = 0; c < C; ++c) {
@@ -711,10 +748,8 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
       plan[o.go + rb + c + a] = x;
       plan[o.po + rb + c + a] = y;
       e += row_ptr[i + 1] - row_ptr[i];
-      auto& inc = incoming[i];
-      std::sort(inc.begin(), inc.end());
-      for (const auto& kv : inc) slot_of[kv.second] = x++;
-      for (int tg : pushes[i]) plan[o.push + pb + y++] = tg;
+      for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) slot_of[inc_blk[q]] = x++;
+      for (int q = push_ptr[i]; q < push_ptr[i + 1]; ++q) plan[o.push + pb + y++] = push_tg[q];
     }
     plan[o.hb + rb + c + nr] = e;
     plan[o.go + rb + c + nr] = x;
@@ -735,7 +770,7 @@ bool build_cluster_plan(int C, int n_n, const std::vector<int>& row_ptr, const s
       for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
         const int e = home[b], j = col[b];
         plan[o.blk + base + e] = b;
-        plan[o.col + base + e] = owner[j] == c ? local[j] : halo[c].at(j);
+        plan[o.col + base + e] = owner[j] == c ? local[j] : halo_slot[(size_t)c * n_n + j];
         plan[o.o2t + base + e] = b == row_ptr[i] ? -1 : ((owner[j] << 16) | slot_of[b]);
       }
   }

@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       if (surfel_visible(d, i) && surfel_selected(d, t_now, n4.w, d.tt[i].y)) pix = associate_one(d, vl, nl);
     }
     d.corr_pix[i] = pix;
+    if (d.corr_rec) d.corr_rec[(size_t)gn_it * d.n_s + i] = pix;
     if (write_live) {
       d.v_live[i] = make_float4(vl.x, vl.y, vl.z, v4.w);
       d.n_live[i] = make_float4(nl.x, nl.y, nl.z, n4.w);

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kSurfTile) k_data_assemble64(Batch bt, int gn_
                             make_float3((float)nl.x, (float)nl.y, (float)nl.z));
     }
     d.corr_pix[i] = pix;
+    if (d.corr_rec) d.corr_rec[(size_t)gn_it * d.n_s + i] = pix;
     if (pix >= 0) {
       valid = true;
       const D3 V = d3(d.vmap[pix]), nd = d3(d.nmap[pix]);

@@ -80,6 +80,7 @@ struct SwDev {
   float4* v_live;     // forward-warped position (+ radius)
   float4* n_live;     // forward-warped normal (+ confidence)
   int* corr_pix;      // last association: pixel per surfel or -1
+  int* corr_rec;      // null, or [kMaxGn][n_s]: every Gauss-Newton iteration's association (test hook)
   // nodes
   float4* node_p;     // x y z sigma
   float4* dq;         // 2 per node

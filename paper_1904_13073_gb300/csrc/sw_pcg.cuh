@@ -65,6 +65,12 @@ __device__ __forceinline__ Acc acc_add_cascaded(Acc a, Acc b) {
   if constexpr (std::is_same<Acc, DF>::value) return df_add_cascaded(a, b);
   else return a + b;
 }
+// an FP32 value as an accumulator (exact)
+template <typename Acc>
+__device__ __forceinline__ Acc acc_from(float x) {
+  if constexpr (std::is_same<Acc, DF>::value) return DF{x, 0.f};
+  else return (double)x;
+}
 template <typename Acc>
 __device__ __forceinline__ Acc acc_norm(Acc a) {
   if constexpr (std::is_same<Acc, DF>::value) {

@@ -148,6 +148,44 @@ def association_flips(o, v_live, n_live, pix_gpu, visible=None):
     return flipped, edge | near, pix_o
 
 
+def handing_over(o, recorded):
+    """Make oracle stream o's association take the library's decisions where
+    the two differ at a rounding boundary: its k-th association (k-th
+    Gauss-Newton iteration of the solves that follow) compares its own
+    decisions with recorded[k] (the library's, sw_read_correspondence_iter);
+    every difference must lie at a decision boundary (association_flips),
+    and there the library's decision is taken.  Returns the list that
+    receives each iteration's number of such surfels; undo with
+    `del o.associate`."""
+    flips = []
+
+    def associate(v_live, n_live, visibility=True):
+        k = len(flips)
+        vis = o.visible if (o.p.visibility and visibility) else None
+        flipped, at_boundary, pix_o = association_flips(o, v_live, n_live, recorded[k], visible=vis)
+        # surfels without skinning take no term on either side (the library
+        # does not associate them; the oracle drops them after associating)
+        real = ~OS.unskinned(OS.DQ.blend(o.node_dq, o.knn, o.w))[flipped]
+        assert np.all(at_boundary[real]), (k, flipped[real & ~at_boundary])
+        sel = OS.select_surfels(o.conf, o.t_obs, o.t_now, o.p.stable_conf, o.p.recent_frames)
+        if vis is not None:
+            sel = sel & vis
+        ok, pix = OS.associate(v_live, n_live, sel, o.V32, o.N32, o.maps["valid"], o.p.cam,
+                               o.p.corr_dist, o.p.corr_normal)
+        dec = np.where(ok, pix, -1)
+        dec[flipped] = recorded[k][flipped]
+        flips.append(int(real.sum()))
+        mask = dec >= 0
+        tv = np.zeros_like(v_live)
+        tn = np.zeros_like(v_live)
+        tv[mask] = o.maps["V"].reshape(-1, 3)[dec[mask]]
+        tn[mask] = o.maps["N"].reshape(-1, 3)[dec[mask]]
+        return mask, tv, tn
+
+    o.associate = associate
+    return flips
+
+
 def set_maps_like(dst, src):
     """Give oracle stream dst the FP32 depth-surfel maps of src (same frame)."""
     dst.t_now = src.t_now
@@ -194,6 +232,47 @@ def pcg_fp32_spmv(A, b, Minv, iters):
     return x, rz, done
 
 
-def solve_with_fp32_spmv(o, gn, pcg):
+def solve_with_fp32_spmv(o, gn, pcg, visible=None):
     """The oracle stream's Gauss-Newton solve with pcg_fp32_spmv as its linear solve."""
-    return o.solve_frame(gn, pcg, linear_solver=pcg_fp32_spmv)
+    return o.solve_frame(gn, pcg, linear_solver=pcg_fp32_spmv, visible=visible)
+
+
+def solve_with_fp32_system(o, gn, pcg, visible=None):
+    """The oracle stream's Gauss-Newton solve with its linear system formed
+    as the configured precision forms it: the data and regulariser terms
+    evaluated in FP32 arithmetic from FP32 inputs, JᵀJ and Jᵀe summed in FP32
+    (term order), the block inverses in FP64 of the FP32 blocks, and the PCG
+    with an FP32 SpMV (pcg_fp32_spmv).  Warp, association (the oracle's, with
+    `visible` when given) and update are the oracle's.  Its distance from the
+    oracle's own solve measures the error that FP32 terms, sums and products
+    alone cause on a given system, the yardstick for the FP32 modes."""
+    f = np.float32
+    if o.p.visibility:
+        if visible is None:
+            o.predict_visibility()
+        else:
+            o.visible = np.asarray(visible, dtype=bool).copy()
+    n = len(o.node_p)
+    for _ in range(gn):
+        _, v_live, n_live = OS.warp_surfels(o.v_ref, o.n_ref, o.knn, o.w, o.node_dq)
+        mask, tv, tn = o.associate(v_live, n_live)
+        mask = mask & ~OS.unskinned(OS.DQ.blend(o.node_dq, o.knn, o.w))
+        idx = np.nonzero(mask)[0]
+        r, J = OS.data_terms(o.v_ref[idx].astype(f), o.knn[idx], o.w[idx].astype(f), o.node_dq.astype(f),
+                             tv[idx].astype(f), tn[idx].astype(f))
+        j, i, rr, Jj, Ji = OS.reg_terms(o.node_p.astype(f), o.node_dq.astype(f), o.graph, f(o.p.lam))
+        A = OS.BlockMatrix(n, o.pattern, np.zeros((len(o.pattern), 6, 6), f))
+        g = np.zeros((n, 6), f)
+        knn = o.knn[idx]
+        for a_ in range(knn.shape[1]):
+            np.add.at(g, knn[:, a_], (J[:, a_] * r[:, None]).astype(f))
+            for b_ in range(knn.shape[1]):
+                A.add(knn[:, a_], knn[:, b_], (J[:, a_, :, None] * J[:, b_, None, :]).astype(f))
+        for (ra, Ja), (rb, Jb) in (((j, Jj), (j, Jj)), ((j, Jj), (i, Ji)), ((i, Ji), (j, Jj)), ((i, Ji), (i, Ji))):
+            A.add(ra, rb, np.einsum('eri,erj->eij', Ja, Jb).astype(f))
+        np.add.at(g, j, np.einsum('eri,er->ei', Jj, rr).astype(f))
+        np.add.at(g, i, np.einsum('eri,er->ei', Ji, rr).astype(f))
+        A64 = OS.BlockMatrix(n, o.pattern, A.vals.astype(np.float64))
+        Minv = OS.block_jacobi_inverse(A64)
+        x, _, _ = pcg_fp32_spmv(A64, -g.astype(np.float64).reshape(-1), Minv, pcg)
+        o.node_dq = OS.apply_increment(o.node_dq, x)

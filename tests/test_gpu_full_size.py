@@ -72,9 +72,11 @@ def _data_jacobian_magnitude(o, idx, odq, tn):
 
 def _oracle_scale(o, odq, pix):
     """The entry-wise scale of the system's computation (see the JᵀJ test),
-    and for Jᵀe also Σ |J̃| |n|ᵀ(|v'| + |V|): the magnitude of each
-    residual's computation n·(v' − V) from points ~1 m away, which an FP32
-    evaluation errs by a few unit roundoffs of however small r is."""
+    and for Jᵀe also Σ |J̃| r̃, r̃ the magnitude of each residual's
+    computation: |n|ᵀ(|v'| + |V|) for a data term n·(v' − V) and
+    √λ (|T_j p_j| + |T_i p_j|) for a regulariser term, both formed from
+    points ~1 m away, which an FP32 evaluation errs by a few unit roundoffs
+    of however small r is."""
     mask = (pix >= 0) & ~OS.unskinned(OS.DQ.blend(odq, o.knn, o.w))
     idx = np.nonzero(mask)[0]
     tv = o.maps["V"].reshape(-1, 3)[pix[idx]]
@@ -85,7 +87,11 @@ def _oracle_scale(o, odq, pix):
     Jm = _data_jacobian_magnitude(o, idx, odq, tn)
     reg = OS.reg_terms(o.node_p, odq, o.graph, o.p.lam)
     _, _, S, gS = OS.assemble(o.pattern, len(o.node_p), o.knn[idx], Jm, np.abs(r), reg, absolute=True)
-    _, _, _, gR = OS.assemble(o.pattern, len(o.node_p), o.knn[idx], Jm, rmag, reg, absolute=True)
+    j, i, _, Jj, Ji = reg
+    pj = o.node_p[j]
+    rmag_reg = np.sqrt(o.p.lam) * (np.abs(OS.node_transform(odq[j], pj)) + np.abs(OS.node_transform(odq[i], pj)))
+    _, _, _, gR = OS.assemble(o.pattern, len(o.node_p), o.knn[idx], Jm, rmag, (j, i, rmag_reg, Jj, Ji),
+                              absolute=True)
     return S, gS, gR
 
 
@@ -97,12 +103,15 @@ def test_full_size_jtj_matches_oracle(full):
     FP32 evaluation and summation in any order.  Every block entry within
     1e-4 of that scale; every entry not dominated by cancellation
     (|A_ij| >= 1e-2 of its scale) within 1e-4 relative.  Jᵀe within 1e-4 of
-    Σ |J̃| |r|, and every entry within 1e-4 relative plus 8 unit roundoffs
-    of Σ |J̃| |n|ᵀ(|v'| + |V|): each FP32 residual errs by a few roundoffs
-    of the points' magnitude (an FP32 evaluation of the oracle's terms on
-    this linearisation errs by at most 0.16 of that second term, and by up
-    to 6e-4 relative on entries above 1e-2 of Σ |J̃| |r|).  The largest
-    error relative to the plain sums |J|ᵀ|J| is reported beside it."""
+    Σ |J̃| |r|, and every entry within 1e-4 relative plus 16 unit roundoffs
+    of Σ |J̃| r̃, r̃ the magnitude of each residual's computation
+    (_oracle_scale): an FP32 residual errs by a few roundoffs of the points'
+    magnitude however small it is.  FP32 evaluations of the oracle's terms
+    on this linearisation err by up to 16 roundoffs of r̃ in a single
+    regulariser residual (0.23 in a data residual), by 0.6 (0.16) of the
+    second term in Jᵀe, and by up to 6e-4 relative on Jᵀe entries above
+    1e-2 of Σ |J̃| |r|.  The largest error relative to the plain sums
+    |J|ᵀ|J| is reported beside it."""
     scene = full
     p = Pair(scene)
     try:
@@ -144,7 +153,10 @@ def test_full_size_jtj_matches_oracle(full):
         u32 = 2.0 ** -24
         gexcess = np.maximum(gerr - 1e-4 * np.abs(g.reshape(-1)), 0.0) / (u32 * gR.reshape(-1) + 1e-30)
         grel = float(np.max(gexcess))
-        assert grel <= 8.0, grel
+        wg = int(np.argmax(gexcess))
+        print(f"worst Jte entry: node {wg // 6} component {wg % 6}: gpu {gg[wg]:.9g} oracle {g.reshape(-1)[wg]:.9g} "
+              f"sum |J||r| {gS.reshape(-1)[wg]:.6g} sum |J| r-magnitude {gR.reshape(-1)[wg]:.6g}")
+        assert grel <= 16.0, grel
         print(f"full-size JtJ: {nnzb} blocks, {n_corr} terms, {len(flipped)} boundary decisions, "
               f"max error {float(np.max(err / (scale + 1e-30))):.2e} of the computation scale "
               f"({plain:.2e} of |J|ᵀ|J|), max entry-relative error {rel:.2e} "

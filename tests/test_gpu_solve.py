@@ -13,7 +13,8 @@ import synth
 import paper_1904_13073_gb300 as sw
 from oracle import solver as OS
 
-from gpu_helpers import Pair, ensure_built, load_gpu_state_into_oracle, oracle_for, rotation_angle_between
+from gpu_helpers import (Pair, ensure_built, handing_over, load_gpu_state_into_oracle, oracle_for,
+                         rotation_angle_between)
 
 pytestmark = pytest.mark.gpu
 ROT_TOL = 1e-4
@@ -98,9 +99,12 @@ def test_sequence_frames_match_oracle_on_identical_inputs(precision):
     FP32 depth maps, and before each solve the oracle takes the library's
     own model (its fused surfels, skinning and node transforms, FP32 values;
     load_gpu_state_into_oracle) -- after that model was compared with the
-    oracle's own fusion of the previous frame.  Each frame's warp field must
-    then agree to the configuration's 1e-4 rad / 1e-5 m (the FP64 variant to
-    1e-6 rad / 1e-7 m).  A second oracle stream runs the whole sequence on
+    oracle's own fusion of the previous frame.  Within the solve, the
+    library records each Gauss-Newton iteration's association; a decision
+    that differs from the oracle's must lie at a rounding boundary, and there
+    the oracle takes the library's (handing_over).  Each frame's warp field
+    must then agree to the configuration's 1e-4 rad / 1e-5 m (the FP64
+    variant to 1e-6 rad / 1e-7 m).  A second oracle stream runs the whole sequence on
     its own inputs; its distance from the library after each frame (the
     multi-frame drift, where an FP32 fusion decision that flips changes the
     next frame's model) is reported, not asserted."""
@@ -110,14 +114,18 @@ def test_sequence_frames_match_oracle_on_identical_inputs(precision):
     tol = (1e-6, 1e-7) if precision == sw.SW_PRECISION_FP64 else (ROT_TOL, TRANS_TOL)
     report = {"frames": []}
     try:
+        sw.sw_debug_record_correspondence(p.h, True)
         for t in (1, 2, 3):
             p.upload(t)
             p.set_maps_from_oracle()   # identical FP32 depth maps on both sides
             load_gpu_state_into_oracle(p)
             st = sw.sw_solve_frame(p.h, 3, 10)
+            boundary = handing_over(p.o, [sw.sw_read_correspondence_iter(p.h, k) for k in range(3)])
             ost = p.o.solve_frame(3, 10)
+            del p.o.associate
             rot, trans = _compare_nodes(p)
             flips = [int(st["n_corr"][k] - ost[k].n_corr) for k in range(3)]
+            assert flips == [0, 0, 0], flips
             free.upload_depth(scene.frame(t), t)
             free.solve_frame(3, 10)
             _, dq = sw.sw_read_nodes(p.h)
@@ -126,7 +134,8 @@ def test_sequence_frames_match_oracle_on_identical_inputs(precision):
             drift_trans = float(np.linalg.norm(OS.node_transform(dq, free.node_p) - free.warped_nodes(),
                                                axis=1).max())
             report["frames"].append({"frame": t, "rot_err_rad": rot, "trans_err_m": trans,
-                                     "corr_count_diff": flips, "drift_rot_rad": drift_rot,
+                                     "corr_count_diff": flips, "boundary_decisions": boundary,
+                                     "drift_rot_rad": drift_rot,
                                      "drift_trans_m": drift_trans})
             assert rot <= tol[0] and trans <= tol[1], (t, rot, trans)
             sw.sw_fuse_frame(p.h)

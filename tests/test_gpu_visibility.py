@@ -11,7 +11,8 @@ import paper_1904_13073_gb300 as sw
 from oracle import solver as OS
 from oracle import visibility as OV
 
-from gpu_helpers import Pair, ensure_built, load_gpu_state_into_oracle, rigid_dq8_from, rotation_angle_between
+from gpu_helpers import (Pair, ensure_built, handing_over, load_gpu_state_into_oracle, rigid_dq8_from,
+                         rotation_angle_between)
 
 pytestmark = pytest.mark.gpu
 F32 = np.float32
@@ -83,7 +84,12 @@ def test_solve_with_visibility_matches_oracle(precision):
     arithmetic is itself checked bit for bit on given live surfels above.
     So the flips are bounded (at most 10, or 1 in 200 visible surfels), and the
     oracle's solve then takes the library's visibility, making the frame's
-    inputs identical: the warp fields must agree to 1e-4 rad / 1e-5 m at
+    inputs identical.  Within the solve the same holds for the association:
+    the library records each Gauss-Newton iteration's decisions, every
+    difference from the oracle's must lie at a decision boundary, and there
+    the oracle takes the library's (a surfel that swaps its pixel at an
+    ulp moves the nodes of this sparse scene by up to ~6e-5 rad / 1e-5 m,
+    measured).  The warp fields must then agree to 1e-4 rad / 1e-5 m at
     every frame (the FP64 variant to 1e-6 rad / 1e-7 m at frame 1).  The
     errors with the oracle's own prediction are reported beside them."""
     scene = _depth_radii(synth.random_scene(seed=3, n_surfels=40000, n_nodes=48))
@@ -91,12 +97,14 @@ def test_solve_with_visibility_matches_oracle(precision):
     q = Pair(scene, precision=precision)   # the same stream without visibility, for comparison
     report = []
     try:
+        sw.sw_debug_record_correspondence(p.h, True)
         for t in (1, 2, 3):
             p.upload(t)
             q.upload(t)
             p.set_maps_from_oracle()
             load_gpu_state_into_oracle(p)
             st = sw.sw_solve_frame(p.h, 3, 10)
+            recorded = [sw.sw_read_correspondence_iter(p.h, k) for k in range(3)]
             st_off = sw.sw_solve_frame(q.h, 3, 10)
             vis_gpu = sw.sw_read_visibility(p.h).astype(bool)
             dq_start = p.o.node_dq.copy()
@@ -105,7 +113,9 @@ def test_solve_with_visibility_matches_oracle(precision):
             own = p.o.node_dq.copy()
             assert vis_flips <= max(10, vis_gpu.sum() // 200), vis_flips
             p.o.node_dq = dq_start
+            assoc_flips = handing_over(p.o, recorded)
             ost = p.o.solve_frame(3, 10, visible=vis_gpu)     # identical inputs
+            del p.o.associate
             for k in range(3):
                 assert abs(st["n_corr"][k] - ost[k].n_corr) <= max(5, ost[k].n_corr // 200), (t, k)
             # visibility keeps at most one surfel per pixel of the splat map
@@ -116,6 +126,7 @@ def test_solve_with_visibility_matches_oracle(precision):
             trans = float(np.linalg.norm(OS.node_transform(dq, p.o.node_p) - p.o.warped_nodes(), axis=1).max())
             own_rot = float(rotation_angle_between(dq, own).max())
             report.append({"frame": t, "rot_err_rad": rot, "trans_err_m": trans, "visibility_flips": vis_flips,
+                           "association_flips_per_iter": assoc_flips,
                            "rot_err_with_own_visibility_rad": own_rot,
                            "visible": int(vis_gpu.sum()), "n_corr": [int(x) for x in st["n_corr"][:3]],
                            "oracle_n_corr": [int(o.n_corr) for o in ost]})
