@@ -424,10 +424,14 @@ sw_status sw_import_state(sw_handle h, const void* buf, size_t bytes);
  * library.
  *
  * Scratch: 16 * SW_STATIC_MAX_PIXELS 64-bit entries (9.8 MB).  Every GPU
- * that loads the library holds this array until the process exits.  The
- * first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call on a device uses the same array and overwrites
+ * that loads the library holds this array until the process exits.  A call
+ * whose stream is not being captured looks up the array's device address in
+ * the current context (cudaGetSymbolAddress) and remembers it per device; a
+ * call under stream capture uses the remembered address.  So make one call
+ * outside capture before capturing, and again after cudaDeviceReset or
+ * after making another context current on the device (SW_ERR_CUDA if a
+ * captured call finds no address).  Every call on a device uses the same
+ * array and overwrites
  * it (the call clears it first), so calls whose work overlaps on the GPU --
  * on different streams, or from different host threads -- race and give
  * wrong results; serialise them.

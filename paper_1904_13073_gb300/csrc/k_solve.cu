@@ -213,11 +213,13 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
 // ------------------------------------------------------------------ K4+K5: data term
 
 constexpr int kJS = 25;   // 24 Jacobian entries + residual per term
-// chunks of terms per output: 9 x 14 outputs = 126 threads.  Every chunk
-// flushes at least once (9 or 36 floats by vector atomics), and the atomics
-// cost more than the products: measured on the full-size frame, 18 chunks
-// 39.5 us, 12 36.8, 9 35.8, 6 36.2, 5 37.5 per launch
-constexpr int kAsmChunks = 9;
+// chunks of terms per output third: 6 x 3 x 14 = 252 threads.  Every chunk
+// flushes at least once (3 float4 or one float2 vector atomic per third), and
+// the atomics cost more than the products (with whole outputs per thread
+// over 126 threads, measured on the full-size frame: 18 chunks 39.5 us, 12
+// 36.8, 9 35.8, 6 36.2, 5 37.5 per launch)
+constexpr int kAsmChunks = 6;
+static_assert(3 * kAsmChunks * 14 <= kAsmTile, "one thread per (item, part, chunk)");
 
 __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_it, int write_live) {
   const int s = find_stream(bt, blockIdx.x);
@@ -306,16 +308,20 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
   if (nvalid == 0) return;
 
   // JᵀJ and Jᵀe of the tile's terms, balanced over the threads: thread
-  // (item, chunk) owns one of the 14 outputs of a node set -- items 0..9 the
-  // upper blocks (a <= b) of its 4 nodes, 10..13 the Jᵀe segments -- over one
-  // chunk of consecutive terms.  It accumulates while the set id stays the
-  // same and adds the sum to the system (16-byte vector atomics) whenever the
-  // set changes or the chunk ends, so node sets of any size cost every thread
-  // about the same.
-  // item-major: a warp's lanes take the same item on neighbouring chunks (no
-  // divergence between block and Jᵀe items); an odd chunk length keeps the
-  // lanes' shared-memory rows in different banks
-  const int item = tid / kAsmChunks, chunk = tid - item * kAsmChunks;
+  // (item, part, chunk) owns a third of one of the 14 outputs of a node set
+  // -- items 0..9 the upper blocks (a <= b) of its 4 nodes, a part two of a
+  // block's six rows; items 10..13 the Jᵀe segments, a part two of a
+  // segment's six values -- over one chunk of consecutive terms.  It
+  // accumulates while the set id stays the same and adds the sum to the
+  // system (vector atomics) whenever the set changes or the chunk ends, so
+  // node sets of any size cost every thread about the same.  Splitting each
+  // output three ways keeps 252 of the 256 threads busy with a third of the
+  // products each, over fewer chunks (so fewer flushes).
+  // item-major: a warp's lanes take the same item and part on neighbouring
+  // chunks (no divergence between block and Jᵀe items); an odd chunk length
+  // keeps the lanes' shared-memory rows in different banks
+  const int item = tid / (3 * kAsmChunks), rem = tid - item * (3 * kAsmChunks);
+  const int part = rem / kAsmChunks, chunk = rem - part * kAsmChunks;
   const int len = ((nvalid + kAsmChunks - 1) / kAsmChunks) | 1;
   if (item < 14) {
     const int t0 = min(nvalid, chunk * len), t1 = min(nvalid, t0 + len);
@@ -324,54 +330,52 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       // pair index -> (a, b): (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3)
       const int a = item < 4 ? 0 : item < 7 ? 1 : item < 9 ? 2 : 3;
       const int bb = item < 4 ? item : item < 7 ? item - 3 : item < 9 ? item - 5 : 3;
-      float acc[36];
+      const int ra = 6 * a + 2 * part;   // rows 2 part and 2 part + 1 of the block
+      // acc[3 r + j]: entries (2 part + r, 2 j) and (2 part + r, 2 j + 1), on packed FP32 pairs
+      float2 acc[6];
 #pragma unroll
-      for (int k = 0; k < 36; ++k) acc[k] = 0.f;
+      for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
       int cur = sset[t0];
       int slot = checked(__ldg(d.set_slots + (size_t)cur * 14 + item), d.nnzb, d.status);
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
-          float4* dst = reinterpret_cast<float4*>(d.A + (size_t)slot * 36);
+          float4* dst = reinterpret_cast<float4*>(d.A + (size_t)slot * 36 + 12 * part);   // 16-byte aligned
 #pragma unroll
-          for (int k = 0; k < 9; ++k)
-            atomicAdd(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
+          for (int k = 0; k < 3; ++k)
+            atomicAdd(dst + k, make_float4(acc[2 * k].x, acc[2 * k].y, acc[2 * k + 1].x, acc[2 * k + 1].y));
           if (t == t1) break;
 #pragma unroll
-          for (int k = 0; k < 36; ++k) acc[k] = 0.f;
+          for (int k = 0; k < 6; ++k) acc[k] = make_float2(0.f, 0.f);
           cur = st_;
           slot = checked(__ldg(d.set_slots + (size_t)cur * 14 + item), d.nnzb, d.status);
         }
         const float* Jt = sJ + t * kJS;
-        float ja[6], jb[6];
+        const float2 j0 = make_float2(Jt[ra], Jt[ra]), j1 = make_float2(Jt[ra + 1], Jt[ra + 1]);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) { ja[k] = Jt[6 * a + k]; jb[k] = Jt[6 * bb + k]; }
-#pragma unroll
-        for (int p = 0; p < 6; ++p)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) acc[p * 6 + q] += ja[p] * jb[q];
+        for (int j = 0; j < 3; ++j) {
+          const float2 jb = make_float2(Jt[6 * bb + 2 * j], Jt[6 * bb + 2 * j + 1]);
+          acc[j] = __ffma2_rn(j0, jb, acc[j]);
+          acc[3 + j] = __ffma2_rn(j1, jb, acc[3 + j]);
+        }
       }
     } else {
       const int a = item - 10;
-      float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float2 acc = make_float2(0.f, 0.f);   // values 2 part and 2 part + 1 of the segment
       int cur = sset[t0];
       int node = checked(__ldg(d.set_slots + (size_t)cur * 14 + 10 + a), d.n_n, d.status);
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
-          float2* dst = reinterpret_cast<float2*>(d.g + (size_t)node * 6);   // 8-byte aligned
-#pragma unroll
-          for (int k = 0; k < 3; ++k) atomicAdd(dst + k, make_float2(acc[2 * k], acc[2 * k + 1]));
+          atomicAdd(reinterpret_cast<float2*>(d.g + (size_t)node * 6 + 2 * part), acc);   // 8-byte aligned
           if (t == t1) break;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc[k] = 0.f;
+          acc = make_float2(0.f, 0.f);
           cur = st_;
           node = checked(__ldg(d.set_slots + (size_t)cur * 14 + 10 + a), d.n_n, d.status);
         }
         const float* Jt = sJ + t * kJS;
         const float rr = Jt[24];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] += Jt[6 * a + k] * rr;
+        acc = __ffma2_rn(make_float2(Jt[6 * a + 2 * part], Jt[6 * a + 2 * part + 1]), make_float2(rr, rr), acc);
       }
     }
   }

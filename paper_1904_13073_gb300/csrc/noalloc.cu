@@ -102,14 +102,29 @@ sw_status sw_fusion_targets_static(const float* v_live4, const float* n_live4, i
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     set_process_error(std::string("sw_fusion_targets_static: cudaGetDevice: ") + cudaGetErrorString(e));
+    return SW_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_process_error("sw_fusion_targets_static: device ordinal " + std::to_string(dev) + " is beyond the " +
+                      std::to_string(kMaxDevices) + " this entry point supports");
+    return SW_ERR_CUDA;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) {
+    set_process_error(std::string("sw_fusion_targets_static: cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     return SW_ERR_CUDA;
   }
   unsigned long long* imap = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
+      // outside capture: the address in the current context (it changes
+      // after a device reset or in another context), remembered for
+      // captured calls
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_index_map);
       if (e != cudaSuccess) {
@@ -117,10 +132,12 @@ sw_status sw_fusion_targets_static(const float* v_live4, const float* n_live4, i
         return SW_ERR_CUDA;
       }
       g_addr[dev] = static_cast<unsigned long long*>(p);
+    } else if (!g_addr[dev]) {
+      set_process_error("sw_fusion_targets_static: the first call on a device must not be under stream capture");
+      return SW_ERR_CUDA;
     }
     imap = g_addr[dev];
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t entries = size_t(16) * width * height;
   k_clear<<<(unsigned)std::min<size_t>((entries + 255) / 256, 4096), 256, 0, st>>>(imap, entries);
   if (n_surfels > 0)

@@ -9,6 +9,10 @@ compiled into the library.  This test calls it twice in a row, on different
 inputs, through the C ABI and checks each result against the allocating
 stream path (sw_debug_fusion_targets) on the same inputs, bit for bit, which
 also shows that the second call does not see the first call's index map.
+Then it captures a call into a CUDA graph in PyTorch's global capture mode,
+where any device allocation (or other unsafe call) in the capturing thread
+fails the capture, replays the graph and compares again; and a call with no
+surfels must leave every pixel without a target.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.
@@ -74,6 +78,22 @@ def test_static_fusion_targets_match_stream_path_twice():
             assert (want >= 0).sum() > 100, call
             results.append(got)
         assert not np.array_equal(results[0], results[1])
+        # the last inputs again, captured into a graph: nothing may allocate
+        out.fill_(-7)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="global"):
+            sw.sw_fusion_targets_static(dv, dn, dV, dN, c.width, c.height, c.fx, c.fy, c.cx, c.cy,
+                                        1e-3, 0.85, out, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert np.all(out.cpu().numpy() == -7)   # captured, not run
+        graph.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        # no surfels: the index map stays empty and no pixel has a target
+        sw.sw_fusion_targets_static(None, None, dV, dN, c.width, c.height, c.fx, c.fy, c.cx, c.cy,
+                                    1e-3, 0.85, out, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert np.all(out.cpu().numpy() == -1)
     finally:
         sw.sw_destroy_stream(h)
 
