@@ -1592,6 +1592,7 @@ sw_status ensure_append_bufs(sw_stream* s) {
   a.scan_bytes = append_scan_bytes((int)np, (int)nmax);
   unsigned char* tmp = nullptr;
   SW_TRY(A(s, &tmp, std::max<size_t>(16, a.scan_bytes)));
+  SW_CUDA(s, cudaMemsetAsync(tmp, 0, 16, s->st));   // the scans' ticket counter (each scan leaves it 0)
   a.scan_tmp = tmp;
   s->app_ready = true;
   return SW_OK;

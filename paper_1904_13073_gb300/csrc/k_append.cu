@@ -243,7 +243,7 @@ inline int blocks(int n, int t) { return (n + t - 1) / t; }
 cudaError_t compact(const AppendBufs& a, const int* flag, int n, int* out, int* count, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
   if (e != cudaSuccess || n == 0) return e;
-  e = scan_sum(flag, a.pos, n, false, a.scan_tmp, a.scan_bytes, st);
+  e = scan_sum(flag, a.pos, n, false, a.scan_tmp, a.scan_bytes, st, true);   // cleared at allocation
   if (e != cudaSuccess) return e;
   k_scatter<<<blocks(n, 256), 256, 0, st>>>(flag, a.pos, n, out, count);
   return cudaGetLastError();

@@ -361,9 +361,11 @@ cudaError_t radix_sort(const K* kin, K* kout, const int* vin, int* vout, int n, 
 
 }  // namespace
 
-size_t scan_scratch_bytes(int n) { return n <= kTile ? 16 : align256((size_t)tiles_of(n) * 4) + 16; }
+// scratch: the ticket counter in its first 16 bytes, then the tile sums
+size_t scan_scratch_bytes(int n) { return n <= kTile ? 16 : 16 + (size_t)tiles_of(n) * 4; }
 
-cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, size_t tmp_bytes, cudaStream_t st) {
+cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, size_t tmp_bytes, cudaStream_t st,
+                     bool ticket_zero) {
   if (n < 0) return cudaErrorInvalidValue;
   if (n == 0) return cudaSuccess;
   const int n_tiles = tiles_of(n);
@@ -372,10 +374,12 @@ cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, 
     return cudaGetLastError();
   }
   if (tmp == nullptr || tmp_bytes < scan_scratch_bytes(n)) return cudaErrorInvalidValue;
-  int* tile_sum = static_cast<int*>(tmp);
-  unsigned* ticket = reinterpret_cast<unsigned*>(static_cast<char*>(tmp) + align256((size_t)n_tiles * 4));
-  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
+  unsigned* ticket = static_cast<unsigned*>(tmp);
+  int* tile_sum = reinterpret_cast<int*>(static_cast<char*>(tmp) + 16);
+  if (!ticket_zero) {   // (a completed scan leaves the counter at 0)
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
   k_scan_reduce<<<n_tiles, kThreads, 0, st>>>(in, n, tile_sum, ticket, n_tiles);
   k_scan_apply<<<n_tiles, kThreads, 0, st>>>(in, out, n, tile_sum, inclusive);
   return cudaGetLastError();

@@ -297,7 +297,11 @@ void launch_skin_merge(const SwDev& d, const float4* tv, int n, int n_old, int4*
 // sort's input is left untouched and must not alias its output.  Errors
 // (bad sizes, too little scratch) come back as cudaErrorInvalidValue.
 size_t scan_scratch_bytes(int n);
-cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, size_t tmp_bytes, cudaStream_t st);
+// ticket_zero: the scratch's first word is known to be 0 (a scratch kept
+// across calls and cleared once: every completed scan leaves it 0), so no
+// clearing is enqueued
+cudaError_t scan_sum(const int* in, int* out, int n, bool inclusive, void* tmp, size_t tmp_bytes, cudaStream_t st,
+                     bool ticket_zero = false);
 size_t sort_scratch_bytes_u32(int n, bool values);
 size_t sort_scratch_bytes_u64(int n, bool values);
 cudaError_t radix_sort_u32(const uint32_t* kin, uint32_t* kout, const int* vin, int* vout, int n, int begin_bit,
