@@ -142,7 +142,7 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
 # the preconditioner launch plus the cluster PCG launch);
 # profiles/k_pcg_cluster_plain_full_300k_2048.md and
 # profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": None, "data_assembly": None}
+PROFILED_TRAFFIC = {"pcg": 557824.0 + 3039232.0, "data_assembly": 25220864.0 + 5376.0}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
@@ -724,9 +724,8 @@ def main():
     nnzb = sw.sw_debug_assemble(h)[0]
     roof = roofline(stage_ms, stage_n, len(v4), len(node4), nnzb, n_corr, c.width * c.height, pcg)
     # the PCG is bound by synchronisation, not HBM: its latency bound is the
-    # hops it must take (cluster PCG: two waits per iteration for the peers'
-    # stores, one of them on every CTA's partials, and two cluster barriers
-    # per launch) times one hop, costed at a cluster barrier measured alone
+    # hops it must take (cluster PCG: two cluster barriers per iteration and
+    # two at set-up) times one hop measured alone
     if pcg_mode == 3:
         ctas = sw.sw_debug_pcg_cluster(h, 0, 16, 0)[0]
         hop_us = sw.sw_debug_cluster_barrier_us(ctas)
@@ -735,9 +734,8 @@ def main():
         roof["stages"]["pcg"]["latency_bound"] = {
             "hops_per_launch": hops, "hop_us": hop_us, "bound_us": hops * hop_us, "measured_us": meas,
             "frac": hops * hop_us / meas,
-            "note": "synchronisation hops of the cluster PCG (2 per iteration: the waits for the peers' stores, one "
-                    "of them on every CTA's partials; 2 cluster barriers per launch) x one cluster barrier of the "
-                    "same cluster measured alone; the stage also holds the preconditioner launch"}
+            "note": "cluster barriers of the cluster PCG (2 per iteration, 2 at set-up) x one barrier of the same "
+                    "cluster measured alone; the stage also holds the preconditioner launch"}
         if roof["dominant"]["kernel"] == "pcg":
             roof["dominant"]["latency_bound"] = roof["stages"]["pcg"]["latency_bound"]
 

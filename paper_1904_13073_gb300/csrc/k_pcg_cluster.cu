@@ -8,8 +8,10 @@
 // upper 6x6 blocks) and each iteration needs every CTA to agree on two inner
 // products, so it is bound by synchronisation, not by HBM.  Here the C CTAs
 // of a cluster (C = 16, one per SM, 768 threads each) keep the whole system
-// in their shared memory and exchange what they share through distributed
-// shared memory: nothing of the iteration goes through global memory.
+// in their shared memory, exchange what they share through distributed
+// shared memory, and synchronise with the hardware cluster barrier
+// (barrier.cluster arrive.release / wait.acquire): nothing of the iteration
+// goes through global memory and nothing polls.
 //
 // Work split.  The host partitions the nodes into C contiguous ranges of
 // their Morton order (a spatially compact share per CTA, balanced by shared
@@ -22,11 +24,9 @@
 // lanes take the rows' home blocks in turn, in the update phase lane c < 6
 // takes component c (r in a register; x, p, s in shared memory).
 //
-// Exchange, all by the producer into the consumer's shared memory, so that
-// every read on the critical path is a local one.  The stores are st.async:
-// each counts its bytes on an mbarrier of the receiving CTA, which waits
-// (bounded) on its own mbarrier for the bytes it expects, from whichever
-// CTAs send them, instead of on a cluster-wide barrier:
+// Exchange, all by the producer into the consumer's shared memory (remote
+// stores: st.shared::cluster), so that every read on the critical path is a
+// local one:
 //   u     each owner writes its rows' new u into the halo slots of the CTAs
 //         whose home blocks reference them (a push list per row);
 //   A_ijᵀ u_i  each home block writes its transposed product into a receive
@@ -35,26 +35,17 @@
 //   γ, δ  each CTA writes its two partial sums into slot `me` of every CTA.
 // One iteration (Chronopoulos-Gear: u = M⁻¹r and w = A u formed, γ = (r, u)
 // and δ = (w, u) from one reduction, p and s = A p by recurrence):
-//      -> wait: the halo's u (24 bytes per halo row, mbarrier U)
 //   A  w's home part from the local u and halo, the transposed products out,
 //      δ's share blockwise as uᵀA u (each off-diagonal block counts twice),
 //      γ's share from the previous step, the partials out;
-//      -> wait: every CTA's partials and this CTA's transposed products
-//         (16 bytes per CTA + 24 per receive slot, mbarrier B of the
-//         iteration's parity)
+//                                                   -> cluster barrier
 //   B  every CTA sums the C partials in the same order and takes the same
 //      step (α, β); own rows add their received products, then p = u + βp,
-//      s = w + βs, x += αp, r −= αs, u = M⁻¹r, u out, γ's next share.
-// Each mbarrier is re-armed for its next phase once its current one has
-// completed; no data of a later phase can arrive before that, because
-// every producer first needs data that this CTA sends only after its wait
-// (a CTA that sends transposed products to another also holds rows of it
-// in its halo, and every CTA needs every CTA's partials).  The partials are
-// double-buffered by iteration parity; a slot that is written once per
-// iteration is read before its next write for the same reason.  Every CTA
-// takes the same decisions from bit-identical totals, so all of them leave
-// the loop together; a last cluster barrier keeps every CTA's shared memory
-// alive until no other CTA can store into it.  The inner products are
+//      s = w + βs, x += αp, r −= αs, u = M⁻¹r, u out, γ's next share;
+//                                                   -> cluster barrier
+// Every CTA takes the same decisions from bit-identical totals, so all of
+// them pass the same barriers and leave the loop together; after the last
+// barrier no CTA touches another's shared memory.  The inner products are
 // accumulated in the accumulator type (double-float pairs or FP64) and
 // reduced by cascaded summation (sw_pcg.cuh).  The home blocks are staged
 // by bulk copies (cp.async.bulk, one per row, on an mbarrier whose wait is
@@ -128,8 +119,8 @@ struct SmemPlan {   // byte offsets
 __host__ __device__ constexpr unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, int NP) {
   SmemPlan L{};
-  L.part = 0;                                       // [iteration parity][sender CTA]: its two partial sums (16 bytes)
-  L.u = 2u * 16u * kMaxCluster;                     // u of the own rows, then the halo: 8 floats each
+  L.part = 0;                                       // per sender CTA, its two partial sums (16 bytes)
+  L.u = 16u * kMaxCluster;                          // u of the own rows, then the halo: 8 floats each
   L.recv = al16(L.u + 32u * (NR + NH));             // received A_ijᵀ u_i: 6 floats per slot
   L.a = al16(L.recv + 24u * NG);                    // home blocks, 36 floats each, row-major
   L.col = al16(L.a + 144u * NB);
@@ -141,8 +132,8 @@ __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, in
   L.po = al16(L.go + 4u * (NR + 1));
   L.push = al16(L.po + 4u * (NR + 1));
   L.rows = al16(L.push + 4u * NP);
-  L.bar = al16(L.rows + 4u * NR);                   // mbarriers: staging copies, halo u, B inputs (x2 parities)
-  L.total = L.bar + 32u;
+  L.bar = al16(L.rows + 4u * NR);                   // the staging copies' mbarrier
+  L.total = L.bar + 16u;
   return L;
 }
 
@@ -162,41 +153,15 @@ __device__ __forceinline__ unsigned at_rank(unsigned a, unsigned rank, unsigned 
   asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
-// Stores into a CTA's shared memory that count their bytes on that CTA's
-// mbarrier `bar` (a cluster address, like `a`): the receiver waits on its
-// own mbarrier for the bytes it expects instead of a cluster-wide barrier.
-__device__ __forceinline__ void sta_f4(unsigned a, float4 v, unsigned bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
-               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar)
+__device__ __forceinline__ void st_cl_f4(unsigned a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                : "memory");
 }
-__device__ __forceinline__ void sta_f2(unsigned a, float x, float y, unsigned bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(a), "f"(x),
-               "f"(y), "r"(bar)
-               : "memory");
+__device__ __forceinline__ void st_cl_f2(unsigned a, float x, float y) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
 }
-__device__ __forceinline__ void sta_u64x2(unsigned a, unsigned long long x, unsigned long long y, unsigned bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(a), "l"(x),
-               "l"(y), "r"(bar)
-               : "memory");
-}
-// arm one phase of a single-arrival mbarrier for `bytes` more bytes (the
-// arrival that lets the phase complete once they have landed)
-__device__ __forceinline__ void arm(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// bounded wait for the phase of parity `par` of an mbarrier that other CTAs'
-// stores complete; true if it completed
-__device__ __forceinline__ bool wait_cluster(unsigned bar, unsigned par) {
-  unsigned done = 0;
-  for (int spins = 0; spins < (1 << 20) && !done; ++spins) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(par)
-        : "memory");
-  }
-  return done != 0;
+__device__ __forceinline__ void st_cl_u64x2(unsigned a, unsigned long long x, unsigned long long y) {
+  asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
 }
 // one bulk copy global -> this CTA's shared memory, completing on an mbarrier
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
@@ -306,19 +271,13 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   const bool comp = gl < 6;                       // this lane holds component gl of its rows
   const unsigned uBase = smem_u32(sU), recvBase = smem_u32(sRecv), partBase = smem_u32(sPart);
   const unsigned bar = smem_u32(smem_raw + L.bar);
-  // the halo's u arrivals (one phase per iteration) and the B inputs
-  // (partials and transposed products; one mbarrier per iteration parity)
-  const unsigned barU = bar + 8u, barB0 = bar + 16u;
-  __shared__ int s_nh;   // this CTA's halo rows: the u pushes it receives per iteration
 
   // ---- set-up: the plan's tables and M⁻¹ by plain loads; the home blocks,
   // contiguous in A row by row, by one bulk copy per row on an mbarrier
   if (tid == 0) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar + 8u * m), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    s_nh = 0;
   }
   for (int a = tid; a <= nr; a += kCThreads) {
     if (a < nr) sRows[a] = checked(__ldg(P + off.rows + row0 + a), d.n_n, d.status);
@@ -327,13 +286,6 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     sPo[a] = checked_count(__ldg(P + off.po + row0 + me + a), np, d.status);
   }
   for (int x = tid; x < np; x += kCThreads) sPush[x] = checked_pair(__ldg(P + off.push + push0 + x), C, NR + NH, d.status);
-  __syncthreads();   // s_nh initialised
-  {
-    int nh = 0;   // pushes of every CTA that land here
-    for (int x = tid; x < n_push; x += kCThreads) nh += (__ldg(P + off.push + x) >> 16) == (int)me;
-    nh = __reduce_add_sync(0xffffffffu, nh);
-    if (lane == 0 && nh) atomicAdd(&s_nh, nh);
-  }
   for (int e = tid; e < nb; e += kCThreads) {
     sCol[e] = checked(__ldg(P + off.col + blk0 + e), NR + NH, d.status);
     const int o2t = __ldg(P + off.o2t + blk0 + e);
@@ -398,15 +350,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     }
   }
   __syncthreads();
-  // bytes each iteration brings: 24 per halo row (u), and 16 per CTA's
-  // partials plus 24 per receive slot (B)
-  const unsigned bytesU = 24u * (unsigned)s_nh, bytesB = 16u * (unsigned)C + 24u * (unsigned)sGo[nr];
-  if (tid == 0) {
-    if (K > 0) arm(barU, bytesU);        // u_0
-    if (K > 0) arm(barB0, bytesB);       // iteration 0
-    if (K > 1) arm(barB0 + 8u, bytesB);  // iteration 1
-  }
-  cluster_barrier();   // every CTA runs, its mbarriers armed: its shared memory may be written now
+  cluster_barrier();   // every CTA runs: its shared memory may be written now
 
   // u of the own rows out to the CTAs that hold them as halo (one lane per push)
   auto push_u = [&]() {
@@ -419,10 +363,9 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         const int tg = sPush[x];
         const float4 v = *reinterpret_cast<const float4*>(sU + 8 * a);
         const float2 w2 = *reinterpret_cast<const float2*>(sU + 8 * a + 4);
-        const unsigned peer = (unsigned)(tg >> 16);
-        const unsigned ta = at_rank(uBase + 32u * (unsigned)(tg & 0xffff), peer, me), tb = at_rank(barU, peer, me);
-        sta_f4(ta, v, tb);
-        sta_f2(ta + 16, w2.x, w2.y, tb);
+        const unsigned ta = at_rank(uBase + 32u * (unsigned)(tg & 0xffff), (unsigned)(tg >> 16), me);
+        st_cl_f4(ta, v);
+        st_cl_f2(ta + 16, w2.x, w2.y);
       }
     }
   };
@@ -430,20 +373,11 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   float a_prev = 1.f;     // warp 0, lane 0: the previous step's α and γ
   Acc g_prev = O::zero();
   int state = kGearOk;
+  cluster_barrier();   // every CTA's halo holds u₀
 
   // second rows exist only in the upper groups: whole warps without any skip them
   const int hmax = __any_sync(0xffffffffu, arow[1] < nr) ? 2 : 1;
   for (int k = 0; k < K; ++k) {
-    // the halo holds u_k once its pushes have landed; the own rows' u, which
-    // other groups wrote, after the CTA's barrier
-    const bool got_u = wait_cluster(barU, (unsigned)k & 1u);
-    if (!__syncthreads_and(got_u)) {
-      state = kGearLate;
-      break;
-    }
-    if (tid == 0 && k + 1 < K) arm(barU, bytesU);   // u_{k+1}
-    const unsigned barB = barB0 + 8u * ((unsigned)k & 1u);   // this iteration's B inputs
-
     // ---- A: w's home part, the transposed products out, δ's share
     Acc del = O::zero();
     float wh[2] = {0.f, 0.f};
@@ -495,15 +429,15 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         // δ's share: exact times 1 or 2, added by a cascaded (TwoSum) step
         del = acc_add_cascaded(del, acc_from<Acc>(tg < 0 ? dt : 2.f * dt));
         if (tg >= 0) {   // off the diagonal: A_ijᵀ u_i to its receive slot at the column's owner
-          const unsigned slot = (unsigned)(tg & 0xffff), peer = (unsigned)(tg >> 16);
-          const unsigned ta = at_rank(recvBase + 24u * slot, peer, me), tb = at_rank(barB, peer, me);
+          const unsigned slot = (unsigned)(tg & 0xffff);
+          const unsigned ta = at_rank(recvBase + 24u * slot, (unsigned)(tg >> 16), me);
           // a slot is 24 bytes: even slots start 16-byte aligned, odd ones 8 bytes past
           if (slot & 1u) {
-            sta_f2(ta, o2[0].x, o2[0].y, tb);
-            sta_f4(ta + 8, make_float4(o2[1].x, o2[1].y, o2[2].x, o2[2].y), tb);
+            st_cl_f2(ta, o2[0].x, o2[0].y);
+            st_cl_f4(ta + 8, make_float4(o2[1].x, o2[1].y, o2[2].x, o2[2].y));
           } else {
-            sta_f4(ta, make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y), tb);
-            sta_f2(ta + 16, o2[2].x, o2[2].y, tb);
+            st_cl_f4(ta, make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y));
+            st_cl_f2(ta + 16, o2[2].x, o2[2].y);
           }
         }
       }
@@ -511,18 +445,16 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     }
     Acc ga = gam, da = del;
     cta_sum2(ga, da, s_w);
-    if (warp == 0 && lane < C)   // the CTA's partials into slot `me` of every CTA (this iteration's parity)
-      sta_u64x2(at_rank(partBase + 256u * ((unsigned)k & 1u) + 16u * me, (unsigned)lane, me), O::bits(ga),
-                O::bits(da), at_rank(barB, (unsigned)lane, me));
+    if (warp == 0 && lane < C)   // the CTA's partials into slot `me` of every CTA
+      st_cl_u64x2(at_rank(partBase + 16u * me, (unsigned)lane, me), O::bits(ga), O::bits(da));
+    cluster_barrier();   // 1: partials and transposed products delivered
 
-    // ---- B: the step, the received products, the update, u out (once every
-    // CTA's partials and this CTA's transposed products have landed)
-    const bool got_b = wait_cluster(barB, ((unsigned)k >> 1) & 1u);
+    // ---- B: the step, the received products, the update, u out
     if (warp == 0) {
       Acc gs = O::zero(), ds = O::zero();
       if (lane < C) {
-        gs = sPart[32 * (k & 1) + 2 * lane];
-        ds = sPart[32 * (k & 1) + 2 * lane + 1];
+        gs = sPart[2 * lane];
+        ds = sPart[2 * lane + 1];
       }
       gs = acc_norm(warp_sum_cascaded(gs));
       ds = acc_norm(warp_sum_cascaded(ds));
@@ -548,9 +480,8 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
       for (int x = on ? sGo[a] : 0; x < x1; ++x) acc += sRecv[6 * x + gl];
       wt[h] = acc;
     }
-    const bool all_b = __syncthreads_and(got_b);
-    state = all_b ? s_state : kGearLate;
-    if (tid == 0 && k + 2 < K) arm(barB, bytesB);   // iteration k + 2's B inputs
+    __syncthreads();
+    state = s_state;
     if (state == kGearOk) {
       const float al = s_alpha, be = s_beta;
       gam = O::zero();
@@ -581,9 +512,10 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         }
       }
       __syncwarp();   // the group's six components of u written before its lanes push them
-      if (k + 1 < K) push_u();
+      push_u();
     }
-    if (state != kGearOk) break;   // the same in every CTA, except after a wait that ran out
+    cluster_barrier();   // 2: the new u delivered; partial and receive slots free again
+    if (state != kGearOk) break;
   }
 
   // ---- the final rᵀM⁻¹r (a statistic: one FP64 atomic per CTA, nobody waits)
@@ -591,12 +523,6 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     Acc ga = gam, zero = O::zero();
     cta_sum2(ga, zero, s_w);
     if (tid == 0) atomicAdd(d.pcg_rz + gn_it, O::value(ga));
-  }
-  // no CTA leaves while another may still store into its shared memory
-  cluster_barrier();
-  if (state == kGearLate) {   // a wait ran out: reported, and nothing moves
-    if (tid == 0) atomicOr(d.status, kStatusTimeout);
-    return;
   }
   if (state == kGearBreakdown) {
     if (tid == 0 && me == 0) atomicOr(d.status, kStatusBreakdown);
