@@ -988,6 +988,9 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
 // first entry, which the PCG turns into a breakdown of the whole solve.
 template <typename Real>
 __global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
+  // the cluster PCG launched after this one may start now: it stages its
+  // tables and matrix meanwhile and waits for this launch before reading M⁻¹
+  asm volatile("griddepcontrol.launch_dependents;");
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];

@@ -238,7 +238,10 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   using O = AccOps<Acc>;
   const unsigned me = cta_rank_in_cluster();
   const int s = __ldg(members + blockIdx.x / C);
-  if (!stream_active(bt, s)) return;   // the whole cluster leaves together
+  if (!stream_active(bt, s)) {   // the whole cluster leaves together, after the launch it may overlap
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    return;
+  }
   const SwDev d = bt.devs[s];
   const int* __restrict__ P = d.cplan;
   const int NR = __ldg(P + 1), NB = __ldg(P + 2), NG = __ldg(P + 3), NH = __ldg(P + 5), NP = __ldg(P + 6);
@@ -307,6 +310,11 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     const int b0 = checked(__ldg(P + off.blk + blk0 + e0), (long long)d.nnzb - len + 1, d.status);
     bulk_g2s(smem_u32(sA + 36 * (size_t)e0), Ag + 36 * (size_t)b0, 144u * (unsigned)len, bar);
   }
+  // M⁻¹ comes from the preconditioner launch just before this one, which
+  // lets this launch start early (programmatic dependent launch): everything
+  // above overlaps it, and this waits until it has completed and its writes
+  // are visible (a no-op when launched without the dependency)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int t = tid; t < nr * 21; t += kCThreads) {
     const int a = t / 21, q = t - 21 * a;
     sMi[t] = __ldg(d.minv + 21 * (size_t)sRows[a] + q);
@@ -824,13 +832,17 @@ cudaError_t launch_pcg_cluster(const BatchHost& b, int gn_it, int pcg_iters, cud
   cfg.blockDim = dim3(kCThreads);
   cfg.dynamicSmemBytes = b.cluster_smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // may start while the preconditioner launch before it runs (the kernel
+  // waits for it before reading M⁻¹)
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
