@@ -368,14 +368,17 @@ sw_status sw_debug_cluster_barrier_us(int ctas, double* us);
 sw_status sw_read_visibility(sw_handle h, int* visible, int cap, int* n_out);
 
 /* Test hook for the block-Jacobi preconditioner (Sec. 7): the inverse of
- * each of n symmetric 6x6 blocks (host, row-major, 36 values each; float, or
- * double when fp64 is nonzero) as the PCG forms it -- from its lower
- * triangle, by an LDLᵀ factorisation in FP64 -- written to inv21 (host,
- * 21 values per block, packed lower triangle row by row: (0,0) (1,0) (1,1)
- * (2,0) ...), same element type.  ok[i] (host) is 1, or 0 when block i is not
- * positive definite (its inv21 entries are then unspecified).  Needs a GPU;
+ * each of n symmetric 6x6 blocks (host, row-major, 36 values each) as the
+ * PCG forms it -- from its lower triangle, by an LDLᵀ factorisation --
+ * written to inv21 (host, 21 values per block, packed lower triangle row by
+ * row: (0,0) (1,0) (1,1) (2,0) ...), same element type as the blocks.
+ * mode 0: float blocks, the factorisation in double-float pairs (the
+ * default precision's); 1: double blocks, FP64 (SW_PRECISION_FP64); 2: float
+ * blocks, FP64 (SW_PRECISION_MIXED_F64DOTS).  ok[i] (host) is 1, or 0 when
+ * block i is not positive definite (its inv21 entries are then
+ * unspecified).  SW_ERR_INVALID_ARG for another mode.  Needs a GPU;
  * synchronous. */
-sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* inv21, int* ok);
+sw_status sw_debug_block_inverse(const void* blocks36, int n, int mode, void* inv21, int* ok);
 
 /* Test hooks for the library's own prefix sum and radix sort (k_sort.cu;
  * the model set-up sorts surfels by their 4-node set, the JᵀJ pattern

@@ -523,14 +523,17 @@ def sw_batch_read_profile(b):
     return _profile(lib().sw_batch_read_profile, b, None)
 
 
-def sw_debug_block_inverse(blocks, fp64=False):
-    """(inverses (n, 21) packed lower, ok (n,) bool) of the PCG's block inverse on (n, 6, 6) blocks."""
-    dt = np.float64 if fp64 else np.float32
+def sw_debug_block_inverse(blocks, fp64=False, mode=None):
+    """(inverses (n, 21) packed lower, ok (n,) bool) of the PCG's block inverse on (n, 6, 6) blocks.
+    mode 0: FP32 blocks, double-float arithmetic (the default precision); 1: FP64; 2: FP32 blocks,
+    FP64 arithmetic.  Without mode, fp64 picks 1 or 0."""
+    mode = (1 if fp64 else 0) if mode is None else int(mode)
+    dt = np.float64 if mode == 1 else np.float32
     b = np.ascontiguousarray(np.asarray(blocks, dt).reshape(-1, 36))
     n = b.shape[0]
     out = np.empty((max(1, n), 21), dt)
     ok = np.empty(max(1, n), np.int32)
-    _check(lib().sw_debug_block_inverse(b.ctypes.data_as(_P), n, int(bool(fp64)), out.ctypes.data_as(_P),
+    _check(lib().sw_debug_block_inverse(b.ctypes.data_as(_P), n, mode, out.ctypes.data_as(_P),
                                         ok.ctypes.data_as(_P)), None)
     return out[:n], ok[:n].astype(bool)
 

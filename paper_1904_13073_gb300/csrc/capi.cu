@@ -375,9 +375,12 @@ sw_status build_runner(Runner* r, sw_stream* err_to) {
         in_cluster[i] = 1;
       }
     // clusters only when they take the whole batch in one wave: members left
-    // to the cooperative kernel would run in a second launch after them, and
-    // clusters beyond those the device runs at once in further waves -- both
-    // slower than one cooperative launch over every member
+    // to the cooperative kernel run in a second launch after them, and
+    // clusters beyond those the device runs at once in further waves.  On
+    // the 16-stream uneven batch (7 clusters resident at once) one
+    // cooperative launch over every member took 407 us per Gauss-Newton
+    // iteration, one wave of clusters and the rest cooperative 407 us,
+    // clusters in waves 437 us.
     if (!cl.empty() && ((int)cl.size() != n || cluster_pcg_active(prec, cl_ctas, cl_smem) < (int)cl.size())) {
       cl.clear();
       cl_smem = 0;
@@ -2235,18 +2238,19 @@ sw_status sw_batch_read_profile(sw_batch_handle b, double* ms, int* launches) {
   return runner_profile(&b->run, nullptr, ms, launches);
 }
 
-sw_status sw_debug_block_inverse(const void* blocks36, int n, int fp64, void* inv21, int* ok) {
+sw_status sw_debug_block_inverse(const void* blocks36, int n, int mode, void* inv21, int* ok) {
   if (n < 0 || n > (1 << 24)) return fail(nullptr, SW_ERR_INVALID_ARG, "n out of range");
   if (n > 0 && (!blocks36 || !inv21 || !ok)) return fail(nullptr, SW_ERR_INVALID_ARG, "null array");
   if (n == 0) return SW_OK;
-  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  if (mode < 0 || mode > 2) return fail(nullptr, SW_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  const size_t es = mode == 1 ? sizeof(double) : sizeof(float);
   void *db = nullptr, *dout = nullptr;
   int* dok = nullptr;
   cudaError_t e = cudaMalloc(&db, (size_t)n * 36 * es);
   if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)n * 21 * es);
   if (e == cudaSuccess) e = cudaMalloc(&dok, (size_t)n * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(db, blocks36, (size_t)n * 36 * es, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = launch_debug_block_inverse(db, n, fp64, dout, dok, 0);
+  if (e == cudaSuccess) e = launch_debug_block_inverse(db, n, mode, dout, dok, 0);
   if (e == cudaSuccess) e = cudaMemcpy(inv21, dout, (size_t)n * 21 * es, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(ok, dok, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(db);

@@ -978,19 +978,94 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
   }
 }
 
+// The same factorisation and inverse for an FP32 block in double-float
+// pairs (sw_df.cuh, about 48 bits), all in the FP32 pipe: the default
+// precision's preconditioner (an FP64 instruction issues once per 64 cycles
+// per warp on this part, and the FP64 inverse is a chain of ~200 of them).
+// The block is first scaled by the power of two that brings its largest
+// diagonal entry to [0.5, 1) -- exact -- so that no pair's low part falls
+// below FP32's normal range; M⁻¹ is scaled back the same way.  False if the
+// block is not positive definite.
+__device__ bool block_inverse_df(const float* a, float* out) {
+  float amax = 0.f;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) amax = fmaxf(amax, fabsf(a[r * 7]));
+  if (!(amax > 0.f) || !(amax < 3.0e38f)) return false;
+  int ex;
+  frexpf(amax, &ex);
+  DF S[21], L[15], Di[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (c <= r) S[tri(r, c)] = DF{ldexpf(a[r * 6 + c], -ex), 0.f};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    DF dc = S[tri(c, c)];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < c) dc = df_fnma(L[sl(c, k)], S[tri(c, k)], dc);
+    if (!(dc.hi > 0.f)) return false;
+    Di[c] = df_recip(dc);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (r <= c) continue;
+      DF e = S[tri(r, c)];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < c) e = df_fnma(L[sl(r, k)], S[tri(c, k)], e);
+      S[tri(r, c)] = e;
+      L[sl(r, c)] = df_mul(e, Di[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (r <= c) continue;
+      DF x = df_neg(L[sl(r, c)]);
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k > c && k < r) x = df_fnma(L[sl(r, k)], L[sl(k, c)], x);
+      L[sl(r, c)] = x;
+    }
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (k == c) S[tri(c, c)] = Di[c];
+      if (k > c) S[tri(k, c)] = df_mul(Di[k], L[sl(k, c)]);
+    }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (c > r) continue;
+      DF m = S[tri(r, c)];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k > r) m = df_add(m, df_mul(L[sl(k, r)], S[tri(k, c)]));
+      out[tri(r, c)] = ldexpf(__fadd_rn(m.hi, m.lo), -ex);
+    }
+  return true;
+}
+
 // The block-Jacobi preconditioner, one thread per node of every active
 // stream, launched between the assembly and the PCG: its own launch gives the
 // FP64 inverse the registers that the 1024-thread PCG cannot, and spreads the
 // FP64 work (the slow pipe on this part) over many SMs, kPrecondTile nodes
 // per CTA.  M⁻¹_j, packed
-// lower, to minv (FP32 modes) or minv64 (FP64 mode).  A diagonal block that
-// is not positive definite sets kStatusBreakdown and leaves a NaN in its
-// first entry, which the PCG turns into a breakdown of the whole solve.
-template <typename Real>
+// lower, to minv (FP32 modes) or minv64 (FP64 mode); with kPairs the
+// double-float inverse (the default precision), else the FP64 one.  A
+// diagonal block that is not positive definite sets kStatusBreakdown and
+// leaves a NaN in its first entry, which the PCG turns into a breakdown of
+// the whole solve.
+template <typename Real, bool kPairs>
 __global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
-  // the cluster PCG launched after this one may start now: it stages its
-  // tables and matrix meanwhile and waits for this launch before reading M⁻¹
-  asm volatile("griddepcontrol.launch_dependents;");
+  // after the assembly's completion, the cluster PCG launched next may
+  // start: it stages its tables and matrix meanwhile and waits for this
+  // launch before reading M⁻¹
+  pdl_begin();
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -1003,17 +1078,24 @@ __global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
   } else {
     A = d.A; out = d.minv + 21 * (size_t)j;
   }
-  if (!block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, out)) {
+  bool ok;
+  if constexpr (kPairs) ok = block_inverse_df(A + (size_t)__ldg(d.row_ptr + j) * 36, out);
+  else ok = block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, out);
+  if (!ok) {
     atomicOr(d.status, kStatusBreakdown);
     out[0] = (Real)__longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
 // the preconditioner's block inverse alone, one thread per block (stage checks)
-template <typename Real>
+template <typename Real, bool kPairs>
 __global__ void k_debug_block_inverse(const Real* blocks, int n, Real* out, int* ok) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) ok[i] = block_inverse(blocks + (size_t)i * 36, out + (size_t)i * 21) ? 1 : 0;
+  if (i >= n) return;
+  bool good;
+  if constexpr (kPairs) good = block_inverse_df(blocks + (size_t)i * 36, out + (size_t)i * 21);
+  else good = block_inverse(blocks + (size_t)i * 36, out + (size_t)i * 21);
+  ok[i] = good ? 1 : 0;
 }
 
 template <typename Acc>
@@ -1100,17 +1182,26 @@ void launch_precond(const BatchHost& b, cudaStream_t st) {
   if (nb == 0) return;
   Batch bt = b.bt;
   bt.tile_base = b.tile_base_dev[kTilePrecond];
-  if (b.precision == SW_PRECISION_FP64) k_precond<double><<<nb, kPrecondTile, 0, st>>>(bt);
-  else k_precond<float><<<nb, kPrecondTile, 0, st>>>(bt);
+  // the default precision's double-float inverse may begin during the data
+  // assembly's tail (programmatic dependent launch); the FP64 one does not:
+  // overlapped with the assembly it cost the full-size frame 0.1 ms more
+  if (b.precision == SW_PRECISION_FP64) k_precond<double, false><<<nb, kPrecondTile, 0, st>>>(bt);
+  else if (b.precision == SW_PRECISION_MIXED_F64DOTS) k_precond<float, false><<<nb, kPrecondTile, 0, st>>>(bt);
+  else launch_overlapped(k_precond<float, true>, nb, kPrecondTile, st, bt);
 }
 
-cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void* out, int* ok, cudaStream_t st) {
+cudaError_t launch_debug_block_inverse(const void* blocks, int n, int mode, void* out, int* ok, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = (n + 127) / 128;
-  if (fp64)
-    k_debug_block_inverse<double><<<nb, 128, 0, st>>>(static_cast<const double*>(blocks), n, static_cast<double*>(out), ok);
+  if (mode == 1)
+    k_debug_block_inverse<double, false>
+        <<<nb, 128, 0, st>>>(static_cast<const double*>(blocks), n, static_cast<double*>(out), ok);
+  else if (mode == 2)
+    k_debug_block_inverse<float, false>
+        <<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
   else
-    k_debug_block_inverse<float><<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
+    k_debug_block_inverse<float, true>
+        <<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
   return cudaGetLastError();
 }
 

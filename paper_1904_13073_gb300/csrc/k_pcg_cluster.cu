@@ -526,6 +526,9 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     if (state != kGearOk) break;
   }
 
+  // the next launch (the next iteration's regulariser assembly) may begin;
+  // it waits for this launch's completion before reading anything
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // ---- the final rᵀM⁻¹r (a statistic: one FP64 atomic per CTA, nobody waits)
   if (state == kGearOk || state == kGearConverged) {
     Acc ga = gam, zero = O::zero();

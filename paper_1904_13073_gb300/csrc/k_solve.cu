@@ -110,6 +110,7 @@ __global__ void k_solve_begin(Batch bt) {
 // Threads [n8, n8 + nnzb): one per block; the off-diagonal ones write their
 // block (zero unless a graph edge joins its two nodes).
 __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) {
+  pdl_begin();
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -222,6 +223,7 @@ constexpr int kAsmChunks = 6;
 static_assert(3 * kAsmChunks * 14 <= kAsmTile, "one thread per (item, part, chunk)");
 
 __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_it, int write_live) {
+  pdl_begin();
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
@@ -407,11 +409,12 @@ void launch_solve_begin(const BatchHost& b, cudaStream_t st) {
 }
 void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileRegAssembly])
-    k_reg_assemble<<<b.total_tiles[kTileRegAssembly], kBlkTile, 0, st>>>(with_kind(b, kTileRegAssembly), gn_it);
+    launch_overlapped(k_reg_assemble, b.total_tiles[kTileRegAssembly], kBlkTile, st, with_kind(b, kTileRegAssembly), gn_it);
 }
 void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
   if (b.total_tiles[kTileSurfelsAssembly])
-    k_data_assemble<<<b.total_tiles[kTileSurfelsAssembly], kAsmTile, 0, st>>>(with_kind(b, kTileSurfelsAssembly), gn_it, 0);
+    launch_overlapped(k_data_assemble, b.total_tiles[kTileSurfelsAssembly], kAsmTile, st,
+                      with_kind(b, kTileSurfelsAssembly), gn_it, 0);
 }
 void launch_associate_only(const BatchHost& b, cudaStream_t st) {
   if (b.total_tiles[kTileSurfels]) k_associate_only<<<b.total_tiles[kTileSurfels], kSurfTile, 0, st>>>(with_kind(b, kTileSurfels));

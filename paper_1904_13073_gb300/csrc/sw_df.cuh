@@ -45,6 +45,32 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   return DF{s, e};
 }
 
+// a * b for pairs: the high parts' exact product (TwoProduct) plus the two
+// cross terms, renormalised (the lo * lo term is below the pair's precision)
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  fast_two_sum(p, e, s, t);
+  return DF{s, t};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// c - a * b
+__device__ __forceinline__ DF df_fnma(DF a, DF b, DF c) { return df_add(c, df_neg(df_mul(a, b))); }
+
+// 1 / x for a positive pair of normal magnitude: the FP32 reciprocal of the
+// high part, refined by one Newton-Raphson step r + r (1 - x r) evaluated in
+// pairs (about 24 -> 48 correct bits)
+__device__ __forceinline__ DF df_recip(DF x) {
+  const DF r = DF{__frcp_rn(x.hi), 0.f};
+  const DF q = df_add(DF{1.f, 0.f}, df_neg(df_mul(x, r)));
+  return df_add(r, df_mul(r, q));
+}
+
 // the pair's value, exactly (hi + lo fits an FP64 mantissa)
 __device__ __forceinline__ double df_value(DF v) { return (double)v.hi + (double)v.lo; }
 

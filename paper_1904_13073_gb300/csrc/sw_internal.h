@@ -152,6 +152,32 @@ __device__ __forceinline__ int find_stream(const Batch& bt, int b) {
 
 __device__ __forceinline__ bool stream_active(const Batch& bt, int s) { return !bt.active || __ldg(bt.active + s); }
 
+// Programmatic dependent launch along the Gauss-Newton loop: a kernel
+// launched by launch_overlapped may begin while the previous launch on the
+// stream still runs.  Such a kernel calls pdl_begin first: it waits until
+// that launch has completed and its writes are visible (so everything it
+// reads is current, and its own completion implies the previous one's),
+// then lets the next launch begin.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_overlapped(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------------ launchers
 
 enum TileKind { kTilePixels = 0, kTileSurfels, kTileSurfelsAssembly, kTileBlocks, kTilePcg, kTileNodes, kTilePrecond,
@@ -216,7 +242,9 @@ size_t pcg_smem_bytes(int rows_cap, int ent_cap, int precision, int mode);
 // its sw_status (SW_OK for inactive members); `status` has one entry per member.
 sw_status batch_member_status(sw_batch_handle b, int* status);
 // the PCG's 6x6 block inverse on n row-major blocks (float, or double with fp64), packed lower out
-cudaError_t launch_debug_block_inverse(const void* blocks, int n, int fp64, void* out, int* ok, cudaStream_t st);
+// mode 0: FP32 blocks, double-float inverse (the default precision's); 1: FP64
+// blocks, FP64 inverse; 2: FP32 blocks, FP64 inverse (SW_PRECISION_MIXED_F64DOTS)
+cudaError_t launch_debug_block_inverse(const void* blocks, int n, int mode, void* out, int* ok, cudaStream_t st);
 
 // ------------------------------------------------------------------ appending
 // Per-candidate records and scratch of the appending step (k_append.cu),

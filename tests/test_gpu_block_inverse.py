@@ -1,6 +1,8 @@
 """The block-Jacobi preconditioner's 6x6 inverse (Sec. 7) as the PCG forms
-it on the device -- from the block's lower triangle, LDLᵀ in FP64 with
-Newton-refined pivot reciprocals -- against the FP64 inverse from LAPACK,
+it on the device -- from the block's lower triangle, LDLᵀ with
+Newton-refined pivot reciprocals, in double-float pairs (mode 0, the
+default precision), in FP64 (mode 1, the FP64 variant) or in FP64 on FP32
+blocks (mode 2) -- against the FP64 inverse from LAPACK,
 over conditioning from 1 to 1e6, magnitudes from 1e-33 to 1e6 (the smallest
 below the range where the reciprocal's FP32 seed is used), an upper triangle
 that differs from the lower one, and blocks that are not positive
@@ -43,15 +45,16 @@ def _packed(m):
     return np.array([m[r, c] for r, c in TRI])
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_block_inverse_matches_lapack(fp64):
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_block_inverse_matches_lapack(mode):
+    fp64 = mode == 1
     rng = np.random.default_rng(5)
     B, conds = _blocks(rng)
     dt = np.float64 if fp64 else np.float32
     Bd = B.astype(dt)
     # the upper triangle off by a few ulps: the device reads the lower one
     Bd[::3, 1, 4] = np.nextafter(np.nextafter(Bd[::3, 1, 4], np.inf), np.inf)
-    inv, ok = sw.sw_debug_block_inverse(Bd, fp64=fp64)
+    inv, ok = sw.sw_debug_block_inverse(Bd, mode=mode)
     assert ok.all()
     for k in range(len(Bd)):
         S = np.tril(Bd[k].astype(np.float64))
@@ -61,7 +64,7 @@ def test_block_inverse_matches_lapack(fp64):
         big = np.abs(want).max()
         if fp64:
             tol = 1e-13 * conds[k] * big
-        else:   # the FP32 result: one rounding, plus an error far below it (46-bit reciprocals)
+        else:   # the FP32 result: one rounding, plus an error far below it (46-48-bit arithmetic)
             tol = np.spacing(np.abs(want).astype(np.float32)).astype(np.float64) + 1e-12 * conds[k] * big
         assert np.all(np.abs(got - want) <= tol), (k, conds[k], np.abs(got - want).max(), big)
 
@@ -76,8 +79,8 @@ def test_block_inverse_flags_blocks_that_are_not_positive_definite():
     zero = np.zeros((6, 6))
     semi = np.diag([1.0, 1.0, 1.0, 1.0, 1.0, 0.0])   # singular: a zero pivot
     B = np.array([good, neg, indef, zero, semi])
-    for fp64 in (False, True):
-        _, ok = sw.sw_debug_block_inverse(B, fp64=fp64)
+    for mode in (0, 1, 2):
+        _, ok = sw.sw_debug_block_inverse(B, mode=mode)
         assert ok.tolist() == [True, False, False, False, False]
 
 
@@ -90,6 +93,8 @@ def test_block_inverse_of_a_diagonal_block_is_exact_reciprocals():
     diag = inv[0][[0, 2, 5, 9, 14, 20]]
     assert np.all(np.abs(diag - 1.0 / d) <= np.spacing(1.0 / d))
     assert np.all(inv[0][[1, 3, 4, 6, 7, 8]] == 0.0)
-    inv32, ok = sw.sw_debug_block_inverse(np.diag(d).astype(np.float32)[None], fp64=False)
     want = (1.0 / d.astype(np.float32).astype(np.float64)).astype(np.float32)
-    np.testing.assert_array_equal(inv32[0][[0, 2, 5, 9, 14, 20]], want)
+    for mode in (0, 2):
+        inv32, ok = sw.sw_debug_block_inverse(np.diag(d).astype(np.float32)[None], mode=mode)
+        assert ok[0]
+        np.testing.assert_array_equal(inv32[0][[0, 2, 5, 9, 14, 20]], want)
