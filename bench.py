@@ -115,14 +115,17 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
+def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters, merged=True):
     """Algorithmic bytes per launch of each stage (what the stage must move at
     least, per unit of work):
       depth      4 B depth read + 32 B of V/N maps written per pixel
       reg        144 B per 6x6 block written + 80 B of node data per node
       data       64 B per surfel (v_ref, n_ref, 4-NN ids, weights)
                  + 32 B per association (V, N gathered) + 32 B per node (DQ)
-                 + 144 B per block and 24 B per node of JᵀJ / Jᵀe written
+                 + 144 B per block and 24 B per node of JᵀJ / Jᵀe written;
+                 with `merged` (the FP32 modes assemble both terms in one
+                 launch, timed as the data stage) + the regulariser's 80 B
+                 of node data per node, the system still written once
       pcg        per iteration 144 B per block (A read) + 192 B per node
                  (8 FP32 6-vectors), plus 252 B per node for the set-up
       fusion     96 B per surfel (warp: 64 read + 32 written) + 24 B per
@@ -131,7 +134,8 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
     return {
         "depth": 36.0 * n_pix,
         "reg_assembly": 144.0 * nnzb + 80.0 * n_n,
-        "data_assembly": 64.0 * n_s + 32.0 * n_corr + 32.0 * n_n + 144.0 * nnzb + 24.0 * n_n,
+        "data_assembly": 64.0 * n_s + 32.0 * n_corr + 32.0 * n_n + 144.0 * nnzb + 24.0 * n_n
+        + (80.0 * n_n if merged else 0.0),
         "pcg": pcg_iters * (144.0 * nnzb + 192.0 * n_n) + 252.0 * n_n,
         "fusion": 120.0 * n_s + 160.0 * n_pix,
     }
@@ -142,7 +146,7 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
 # the preconditioner launch plus the cluster PCG launch);
 # profiles/k_pcg_cluster_plain_full_300k_2048.md and
 # profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": 557824.0 + 3039232.0, "data_assembly": 25220864.0 + 5376.0}
+PROFILED_TRAFFIC = {"pcg": None, "data_assembly": None}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
@@ -922,9 +926,9 @@ def main():
                 "p50_ms": 1000.0 * float(np.percentile(e_lat, 50)), "p99_ms": 1000.0 * float(np.percentile(e_lat, 99))},
         "clocks": clocks,
         # kernels of this library per step: depth (frame id + maps), solve
-        # (stats reset + 4 per Gauss-Newton iteration: regulariser, data term,
-        # preconditioner, PCG), fusion (3)
-        "gpu_launches": args.steps * (2 + 1 + 4 * gn + 3),
+        # (stats reset, system clear, 3 per Gauss-Newton iteration: the
+        # assembly of both terms, preconditioner, PCG), fusion (3)
+        "gpu_launches": args.steps * (2 + 2 + 3 * gn + 3),
         "roofline": roof["dominant"],
         "stages_ms_per_step": {k: v / prof_steps for k, v in stage_ms.items()},
         "stage_roofline": roof["stages"],

@@ -44,12 +44,13 @@ extern "C" {
  *                              FP32; PCG inner products accumulated in
  *                              double-float pairs (about 48 significant bits);
  *                              6x6 block inverses (the block-Jacobi
- *                              preconditioner) by LDLᵀ in FP64.
+ *                              preconditioner) by Gauss-Jordan sweeps in
+ *                              double-float pairs.
  *   SW_PRECISION_FP64          the whole solve in FP64: node transforms, warp,
  *                              residuals, Jacobians, JᵀJ, PCG (the association
  *                              still decided in FP32 from the FP64 warp).
  *   SW_PRECISION_MIXED_F64DOTS as MIXED, with the inner products accumulated
- *                              in FP64.
+ *                              in FP64 and the block inverses by LDLᵀ in FP64.
  * Every member of one batch must use the same mode. */
 #define SW_PRECISION_MIXED 0
 #define SW_PRECISION_FP64 1
@@ -226,8 +227,9 @@ sw_status sw_debug_fusion_targets(sw_handle h, int* target, int* imap);
  * sw_params.visibility; the call synchronises. */
 sw_status sw_debug_visibility(sw_handle h, int* vis_map, int* visible);
 sw_status sw_debug_assemble(sw_handle h, int* nnzb_out, int* n_corr_out);
-/* Read the last assembled system: rows/cols [nnzb] block coordinates
- * (row <= col), vals [nnzb][36] row-major 6x6, g [6 n_nodes]. */
+/* Read the last assembled system (sw_debug_assemble's, or the last
+ * Gauss-Newton iteration's of the last solve): rows/cols [nnzb] block
+ * coordinates (row <= col), vals [nnzb][36] row-major 6x6, g [6 n_nodes]. */
 sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, float* g, int cap_blocks);
 
 /* ---------------------------------------------------------------------------
@@ -236,10 +238,11 @@ sw_status sw_debug_read_jtj(sw_handle h, int* rows, int* cols, float* vals, floa
  * one stream; Sec. 8 names stream-level parallelism as future work).
  *
  * A batch keeps per-stream state where it is (every member stays resident)
- * and runs on its own CUDA stream.  Each Gauss-Newton iteration is three
- * launches for the whole batch -- regulariser assembly, data-term assembly,
- * and one persistent cooperative kernel that runs the block-Jacobi PCG and
- * the update -- replayed from a captured CUDA graph.  Members whose active
+ * and runs on its own CUDA stream.  Each Gauss-Newton iteration is a few
+ * launches for the whole batch -- the assembly of both terms, the
+ * block-Jacobi preconditioner, and the PCG with the update (a thread-block
+ * cluster per member whose system fits on chip, one persistent cooperative
+ * kernel for the others) -- replayed from a captured CUDA graph.  Members whose active
  * flag is 0 are skipped by every launch (their state is untouched).
  * Results equal those of running each member alone up to floating-point
  * summation order.  Work that a member's own calls enqueued is ordered before
@@ -273,8 +276,9 @@ sw_status sw_batch_debug_pcg_mode(sw_batch_handle b, int* mode);
 /* ---------------------------------------------------------------------------
  * Stage timing (CUDA events recorded on the launching stream, inside the
  * captured solve graph).  Stages: 0 depth processing, 1 regulariser
- * assembly, 2 data-term assembly, 3 PCG + update, 4 fusion, 5 visibility
- * prediction (streams with sw_params.visibility).  Enabling or
+ * assembly (SW_PRECISION_FP64 only: the FP32 modes assemble both terms in
+ * one launch, timed as stage 2), 2 data-term assembly, 3 PCG + update, 4
+ * fusion, 5 visibility prediction (streams with sw_params.visibility).  Enabling or
  * disabling re-captures the solve graph.  sw_read_profile synchronises and
  * returns, per stage, the summed milliseconds and the number of launches of
  * the last upload, solve and fusion.
@@ -369,12 +373,12 @@ sw_status sw_read_visibility(sw_handle h, int* visible, int cap, int* n_out);
 
 /* Test hook for the block-Jacobi preconditioner (Sec. 7): the inverse of
  * each of n symmetric 6x6 blocks (host, row-major, 36 values each) as the
- * PCG forms it -- from its lower triangle, by an LDLᵀ factorisation --
- * written to inv21 (host, 21 values per block, packed lower triangle row by
- * row: (0,0) (1,0) (1,1) (2,0) ...), same element type as the blocks.
- * mode 0: float blocks, the factorisation in double-float pairs (the
- * default precision's); 1: double blocks, FP64 (SW_PRECISION_FP64); 2: float
- * blocks, FP64 (SW_PRECISION_MIXED_F64DOTS).  ok[i] (host) is 1, or 0 when
+ * PCG forms it -- from its lower triangle -- written to inv21 (host, 21
+ * values per block, packed lower triangle row by row: (0,0) (1,0) (1,1)
+ * (2,0) ...), same element type as the blocks.  mode 0: float blocks,
+ * Gauss-Jordan sweeps in double-float pairs on eight lanes per block (the
+ * default precision's); 1: double blocks, LDLᵀ in FP64 (SW_PRECISION_FP64);
+ * 2: float blocks, LDLᵀ in FP64 (SW_PRECISION_MIXED_F64DOTS).  ok[i] (host) is 1, or 0 when
  * block i is not positive definite (its inv21 entries are then
  * unspecified).  SW_ERR_INVALID_ARG for another mode.  Needs a GPU;
  * synchronous. */

@@ -111,6 +111,7 @@ struct sw_stream {
   Runner* run = nullptr;     // the stream's own one-stream runner
   std::vector<int> rl_ptr_host;   // per block row, the start of its SpMV entries (PCG work sizing)
   int cplan_ctas = 0;             // cluster size of the stream's cluster-PCG plan (0: none)
+  int last_sys = 0;               // the FP32 system buffer (0: A and g, 1: A2 and g2) assembled last
   int* corr_rec_buf = nullptr;    // sw_debug_record_correspondence: kMaxGn x max_surfels
   size_t cplan_smem = 0;          // shared memory per CTA that plan needs
   // ordering against batches this stream belongs to
@@ -535,14 +536,28 @@ void prof_mark(Runner* r, std::vector<ProfEvent>* list, int stage, bool begin, b
   }
 }
 
-// The two assembly stages of a Gauss-Newton iteration in the batch's precision.
-void launch_reg_stage(const BatchHost& b, int it, cudaStream_t st) {
-  if (b.precision == SW_PRECISION_FP64) launch_reg_assemble64(b, it, st);
-  else launch_reg_assemble(b, it, st);
-}
-void launch_data_stage(const BatchHost& b, int it, cudaStream_t st) {
-  if (b.precision == SW_PRECISION_FP64) launch_data_assemble64(b, it, st);
-  else launch_data_assemble(b, it, st);
+// A Gauss-Newton iteration's assembly in the batch's precision: FP64, the
+// regulariser's launch (plain stores, which also initialise the system),
+// then the data term's (profiled as two stages); FP32, one launch of both
+// into the iteration's system buffer, cleared by the previous iteration's
+// launch or, before the solve's first, by launch_system_clear (profiled as
+// the data stage).
+void launch_assembly_stage(Runner* r, int it, std::vector<ProfEvent>* prof) {
+  const BatchHost& b = r->bh;
+  cudaStream_t st = r->st;
+  if (b.precision == SW_PRECISION_FP64) {
+    prof_mark(r, prof, kProfReg, true, true);
+    launch_reg_assemble64(b, it, st);
+    prof_mark(r, prof, kProfReg, false, true);
+    prof_mark(r, prof, kProfData, true, true);
+    launch_data_assemble64(b, it, st);
+    prof_mark(r, prof, kProfData, false, true);
+  } else {
+    prof_mark(r, prof, kProfData, true, true);
+    if (it == 0) launch_system_clear(b, st);
+    launch_assemble(b, it, st);
+    prof_mark(r, prof, kProfData, false, true);
+  }
 }
 
 sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vector<ProfEvent>* prof) {
@@ -555,14 +570,9 @@ sw_status enqueue_solve(Runner* r, sw_stream* err_to, int gn, int pcg, std::vect
     prof_mark(r, prof, kProfVis, false, true);
   }
   for (int it = 0; it < gn; ++it) {
-    prof_mark(r, prof, kProfReg, true, true);
-    launch_reg_stage(r->bh, it, st);
-    prof_mark(r, prof, kProfReg, false, true);
-    prof_mark(r, prof, kProfData, true, true);
-    launch_data_stage(r->bh, it, st);
-    prof_mark(r, prof, kProfData, false, true);
+    launch_assembly_stage(r, it, prof);
     prof_mark(r, prof, kProfPcg, true, true);
-    launch_precond(r->bh, st);
+    launch_precond(r->bh, it, st);
     SW_CUDA(err_to, launch_pcg_cluster(r->bh, it, pcg, st));
     SW_CUDA(err_to, launch_pcg(r->bh, it, pcg, st));
     prof_mark(r, prof, kProfPcg, false, true);
@@ -591,6 +601,8 @@ sw_status runner_solve(Runner* r, sw_stream* err_to, int gn, int pcg) {
   }
   r->last_key = key;
   SW_CUDA(err_to, cudaGraphLaunch(itg->second, r->st));
+  for (size_t i = 0; i < r->members.size(); ++i)   // iteration gn - 1 assembled into buffer (gn - 1) mod 2
+    if (!r->active_host || r->active_host[i]) r->members[i]->last_sys = (gn - 1) & 1;
   return SW_OK;
 }
 
@@ -804,9 +816,8 @@ sw_status runner_autotune(Runner* r, sw_stream* err_to, int pcg, int* best_rows,
       launch_solve_begin(r->bh, st);
       bool ok = true;
       for (int rep = 0; rep <= kTimed && ok; ++rep) {
-        launch_reg_stage(r->bh, 0, st);
-        launch_data_stage(r->bh, 0, st);
-        launch_precond(r->bh, st);
+        launch_assembly_stage(r, 0, nullptr);
+        launch_precond(r->bh, 0, st);
         cudaEventRecord(e0, st);
         ok = launch_pcg_cluster(r->bh, 0, pcg, st) == cudaSuccess && launch_pcg(r->bh, 0, pcg, st) == cudaSuccess;
         cudaEventRecord(e1, st);
@@ -944,7 +955,7 @@ sw_status sw_create_stream(const sw_params* p, void* cuda_stream, sw_handle* out
   ALLOC(h.in_ptr, nn + 1); ALLOC(h.in_src, SW_K_GRAPH * nn);
   ALLOC(h.depth, np); ALLOC(h.vmap, np); ALLOC(h.nmap, np); ALLOC(h.imap, 16 * np); ALLOC(h.fuse_target, np);
   ALLOC(h.vis_map, np); ALLOC(h.visible, ns);
-  ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.minv, 21 * nn);
+  ALLOC(h.row_ptr, nn + 1); ALLOC(h.rl_ptr, nn + 1); ALLOC(h.g, 6 * nn); ALLOC(h.g2, 6 * nn); ALLOC(h.minv, 21 * nn);
   ALLOC(h.part, 4 * kMaxCtaPerStream); ALLOC(h.pcg_epoch, 1);
   ALLOC(h.xp, 12 * nn);
   ALLOC(h.rigid, kRigidSlots); ALLOC(h.rigid_stats, 2 * kMaxRigid);
@@ -1193,12 +1204,15 @@ sw_status install_pattern(sw_stream* s, const int4* sets, int n_sets, bool graph
   }
   SW_TRY(build_plan(s));
   SW_TRY(A(s, &h.A, (size_t)h.nnzb * 36, true));
+  SW_TRY(A(s, &h.A2, (size_t)h.nnzb * 36, true));
   SW_CUDA(s, cudaMemsetAsync(h.A, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
+  SW_CUDA(s, cudaMemsetAsync(h.A2, 0, (size_t)h.nnzb * 36 * sizeof(float), st));
   if (h.precision == SW_PRECISION_FP64) {
     SW_TRY(A(s, &h.A64, (size_t)h.nnzb * 36, true));
     SW_CUDA(s, cudaMemsetAsync(h.A64, 0, (size_t)h.nnzb * 36 * sizeof(double), st));
   }
   SW_CUDA(s, cudaMemsetAsync(h.g, 0, (size_t)n_n * 6 * sizeof(float), st));
+  SW_CUDA(s, cudaMemsetAsync(h.g2, 0, (size_t)n_n * 6 * sizeof(float), st));
   SW_CUDA(s, cudaMemsetAsync(h.corr_pix, 0xff, (size_t)std::max(1, n_s) * sizeof(int), st));
   SW_CUDA(s, cudaMemsetAsync(h.status, 0, sizeof(int), st));
   SW_TRY(sync_desc(s));
@@ -1774,7 +1788,7 @@ sw_status sw_append_frame(sw_handle s, sw_append_stats* stats) {
       launch_slot_sets(h.set_slots, n_sets_all, all_sets.as<int4>(), st);
       SW_CUDA(s, cudaGetLastError());
       const int sorted_sets = s->sorted_sets;
-      recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A64, h.cplan});
+      recycle_blocks(s, {h.col, h.blk_row, h.blk_edge, h.rl_ent, h.set_slots, h.A, h.A2, h.A64, h.cplan});
       SW_TRY(install_pattern(s, all_sets.as<int4>(), n_sets_all, false));
       s->sorted_sets = sorted_sets;
       return finish(2);
@@ -1855,8 +1869,9 @@ sw_status sw_debug_assemble(sw_handle s, int* nnzb_out, int* n_corr_out) {
     launch_reg_assemble64(s->run->bh, 0, s->st);
     launch_data_assemble64(s->run->bh, 0, s->st);
   } else {
-    launch_reg_assemble(s->run->bh, 0, s->st);
-    launch_data_assemble(s->run->bh, 0, s->st);
+    launch_system_clear(s->run->bh, s->st);
+    launch_assemble(s->run->bh, 0, s->st);
+    s->last_sys = 0;
   }
   SW_CUDA(s, cudaGetLastError());
   int nc = 0;
@@ -1883,8 +1898,10 @@ sw_status sw_debug_read_jtj(sw_handle s, int* rows, int* cols, float* vals, floa
     for (size_t k = 0; k < vg.size(); ++k) g[k] = (float)vg[k];
     return SW_OK;
   }
-  if (vals) SW_CUDA(s, cudaMemcpyAsync(vals, s->h.A, (size_t)nb * 36 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
-  if (g) SW_CUDA(s, cudaMemcpyAsync(g, s->h.g, (size_t)s->h.n_n * 6 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+  const float* sa = s->last_sys ? s->h.A2 : s->h.A;
+  const float* sg = s->last_sys ? s->h.g2 : s->h.g;
+  if (vals) SW_CUDA(s, cudaMemcpyAsync(vals, sa, (size_t)nb * 36 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
+  if (g) SW_CUDA(s, cudaMemcpyAsync(g, sg, (size_t)s->h.n_n * 6 * sizeof(float), cudaMemcpyDeviceToHost, s->st));
   SW_CUDA(s, cudaStreamSynchronize(s->st));
   return SW_OK;
 }

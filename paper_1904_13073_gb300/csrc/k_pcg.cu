@@ -751,7 +751,8 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
   const int n = d.n_n;
   const int nr = n > t ? (n - t + Gs - 1) / Gs : 0;   // own rows (<= rows_cap, checked on the host)
   const unsigned long long base = __ldcg(d.pcg_epoch) * 1024ull;
-  const float* __restrict__ A = d.A;
+  const float* __restrict__ A = sys_A(d, gn_it);
+  const float* __restrict__ gsys = sys_g(d, gn_it);
   unsigned long long* const ub[2] = {d.xp, d.xp + 6 * (size_t)n};   // u by iteration parity
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SmemLayout L = pcg_layout<Real>(rows_cap, ent_cap, kMode, kGearVecs);
@@ -789,7 +790,7 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
       }
       Real r[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) r[c] = -d.g[6 * j + c];
+      for (int c = 0; c < 6; ++c) r[c] = -gsys[6 * j + c];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         Real u = 0;
@@ -978,90 +979,75 @@ k_pcg_gear(Batch bt, int K, int gn_it, int spin_arg, int rows_cap, int ent_cap) 
   }
 }
 
-// The same factorisation and inverse for an FP32 block in double-float
-// pairs (sw_df.cuh, about 48 bits), all in the FP32 pipe: the default
-// precision's preconditioner (an FP64 instruction issues once per 64 cycles
-// per warp on this part, and the FP64 inverse is a chain of ~200 of them).
-// The block is first scaled by the power of two that brings its largest
-// diagonal entry to [0.5, 1) -- exact -- so that no pair's low part falls
-// below FP32's normal range; M⁻¹ is scaled back the same way.  False if the
-// block is not positive definite.
-__device__ bool block_inverse_df(const float* a, float* out) {
-  float amax = 0.f;
+// The inverse of an FP32 block in double-float pairs (sw_df.cuh, about 48
+// bits), all in the FP32 pipe: the default precision's preconditioner (an
+// FP64 instruction issues once per 64 cycles per warp on this part).  It
+// runs the sweep operator -- Gauss-Jordan elimination in place on the
+// symmetric block, pivots in order without exchanges -- on eight lanes per
+// block: lane c < 6 holds column c, every step sends the pivot column to the
+// segment by shuffles, and each lane updates its own column (the pivot lane:
+// −v/d off the pivot, 1/d on it; another lane j: t = a_kj/d, then
+// a_ij −= a_ik t off the pivot row, a_kj = t).  After the six steps the block
+// holds its inverse.  The pivots are the LDLᵀ pivots (Schur complements), so
+// the block is positive definite exactly when every one is positive.  One
+// thread per block ran this as a serial LDLᵀ chain of ~3,800 instructions;
+// here a lane's chain is six steps of five independent updates.  The block
+// (its lower triangle: element (r, c) is read at (max, min)) is first scaled
+// by the power of two that brings its largest diagonal entry to [0.5, 1) --
+// exact -- so that no pair's low part falls below FP32's normal range; M⁻¹
+// is scaled back the same way.  Every lane of the 8-lane segment calls it
+// (`on` false where the segment has no block); every lane gets whether the
+// block is positive definite.
+__device__ bool block_inverse_df8(const float* a, float* out, int c, bool on) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int cc = c < 6 ? c : 0;
+  float col0[6];
 #pragma unroll
-  for (int r = 0; r < 6; ++r) amax = fmaxf(amax, fabsf(a[r * 7]));
-  if (!(amax > 0.f) || !(amax < 3.0e38f)) return false;
-  int ex;
-  frexpf(amax, &ex);
-  DF S[21], L[15], Di[6];
+  for (int r = 0; r < 6; ++r) col0[r] = on ? a[(r > cc ? r : cc) * 6 + (r > cc ? cc : r)] : 0.f;
+  float amax = (on && c < 6) ? fabsf(a[7 * cc]) : 0.f;
 #pragma unroll
-  for (int r = 0; r < 6; ++r)
+  for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kAll, amax, o, 8));
+  bool good = on && amax > 0.f && amax < 3.0e38f;
+  int ex = 0;
+  if (good) frexpf(amax, &ex);
+  DF col[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
-      if (c <= r) S[tri(r, c)] = DF{ldexpf(a[r * 6 + c], -ex), 0.f};
+  for (int r = 0; r < 6; ++r) col[r] = DF{good ? ldexpf(col0[r], -ex) : 0.f, 0.f};
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    DF dc = S[tri(c, c)];
+  for (int k = 0; k < 6; ++k) {
+    DF v[6];   // the pivot column, from lane k
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (k < c) dc = df_fnma(L[sl(c, k)], S[tri(c, k)], dc);
-    if (!(dc.hi > 0.f)) return false;
-    Di[c] = df_recip(dc);
+    for (int i = 0; i < 6; ++i)
+      v[i] = DF{__shfl_sync(kAll, col[i].hi, k, 8), __shfl_sync(kAll, col[i].lo, k, 8)};
+    good = good && v[k].hi > 0.f;
+    const DF inv = df_recip(good ? v[k] : DF{1.f, 0.f});
+    const bool piv = c == k;
+    const DF t = piv ? inv : df_mul(col[k], inv);
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
-      if (r <= c) continue;
-      DF e = S[tri(r, c)];
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k < c) e = df_fnma(L[sl(r, k)], S[tri(c, k)], e);
-      S[tri(r, c)] = e;
-      L[sl(r, c)] = df_mul(e, Di[c]);
-    }
+    for (int i = 0; i < 6; ++i)
+      if (i != k) col[i] = df_fnma(v[i], t, piv ? DF{0.f, 0.f} : col[i]);
+    col[k] = t;
   }
+  if (on && good && c < 6) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c)
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-      if (r <= c) continue;
-      DF x = df_neg(L[sl(r, c)]);
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k > c && k < r) x = df_fnma(L[sl(r, k)], L[sl(k, c)], x);
-      L[sl(r, c)] = x;
-    }
-#pragma unroll
-  for (int c = 0; c < 6; ++c)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      if (k == c) S[tri(c, c)] = Di[c];
-      if (k > c) S[tri(k, c)] = df_mul(Di[k], L[sl(k, c)]);
-    }
-#pragma unroll
-  for (int r = 0; r < 6; ++r)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      if (c > r) continue;
-      DF m = S[tri(r, c)];
-#pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (k > r) m = df_add(m, df_mul(L[sl(k, r)], S[tri(k, c)]));
-      out[tri(r, c)] = ldexpf(__fadd_rn(m.hi, m.lo), -ex);
-    }
-  return true;
+    for (int r = 0; r < 6; ++r)
+      if (r >= c) out[tri(r, c)] = ldexpf(__fadd_rn(col[r].hi, col[r].lo), -ex);
+  }
+  return good;
 }
 
-// The block-Jacobi preconditioner, one thread per node of every active
-// stream, launched between the assembly and the PCG: its own launch gives the
-// FP64 inverse the registers that the 1024-thread PCG cannot, and spreads the
-// FP64 work (the slow pipe on this part) over many SMs, kPrecondTile nodes
-// per CTA.  M⁻¹_j, packed
-// lower, to minv (FP32 modes) or minv64 (FP64 mode); with kPairs the
-// double-float inverse (the default precision), else the FP64 one.  A
+// The block-Jacobi preconditioner for every active stream, launched between
+// the assembly and the PCG: its own launch spreads the inversions over many
+// SMs, kPrecondTile nodes per CTA.  M⁻¹_j, packed lower, to minv (FP32
+// modes) or minv64 (FP64 mode); with kPairs the double-float sweep on eight
+// lanes per node (the default precision), else the FP64 LDLᵀ, one thread
+// per node (its own launch gives it the registers that the 1024-thread PCG
+// cannot).  A
 // diagonal block that is not positive definite sets kStatusBreakdown and
 // leaves a NaN in its first entry, which the PCG turns into a breakdown of
 // the whole solve.
 template <typename Real, bool kPairs>
-__global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
+__global__ void __launch_bounds__(8 * kPrecondTile) k_precond(Batch bt, int gn_it) {
   // after the assembly's completion, the cluster PCG launched next may
   // start: it stages its tables and matrix meanwhile and waits for this
   // launch before reading M⁻¹
@@ -1069,6 +1055,18 @@ __global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
   const int s = find_stream(bt, blockIdx.x);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
+  if constexpr (kPairs) {   // eight lanes per node
+    const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kPrecondTile + (threadIdx.x >> 3);
+    const bool on = j < d.n_n;
+    const float* blk = sys_A(d, gn_it) + (on ? (size_t)checked(__ldg(d.row_ptr + j), d.nnzb, d.status) * 36 : 0);
+    float* out = d.minv + 21 * (size_t)(on ? j : 0);
+    const bool ok = block_inverse_df8(blk, out, threadIdx.x & 7, on);
+    if (on && !ok && (threadIdx.x & 7) == 0) {
+      atomicOr(d.status, kStatusBreakdown);
+      out[0] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
   const int j = (blockIdx.x - __ldg(bt.tile_base + s)) * kPrecondTile + threadIdx.x;
   if (j >= d.n_n) return;
   const Real* A;
@@ -1076,26 +1074,29 @@ __global__ void __launch_bounds__(kPrecondTile) k_precond(Batch bt) {
   if constexpr (std::is_same<Real, double>::value) {
     A = d.A64; out = d.minv64 + 21 * (size_t)j;
   } else {
-    A = d.A; out = d.minv + 21 * (size_t)j;
+    A = sys_A(d, gn_it); out = d.minv + 21 * (size_t)j;
   }
-  bool ok;
-  if constexpr (kPairs) ok = block_inverse_df(A + (size_t)__ldg(d.row_ptr + j) * 36, out);
-  else ok = block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, out);
+  const bool ok = block_inverse(A + (size_t)__ldg(d.row_ptr + j) * 36, out);
   if (!ok) {
     atomicOr(d.status, kStatusBreakdown);
     out[0] = (Real)__longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
-// the preconditioner's block inverse alone, one thread per block (stage checks)
+// the preconditioner's block inverse alone (stage checks)
 template <typename Real, bool kPairs>
 __global__ void k_debug_block_inverse(const Real* blocks, int n, Real* out, int* ok) {
+  if constexpr (kPairs) {   // eight lanes per block, as in k_precond
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool on = i < n;
+    const bool good = block_inverse_df8(blocks + 36 * (size_t)(on ? i : 0), out + 21 * (size_t)(on ? i : 0),
+                                        threadIdx.x & 7, on);
+    if (on && (threadIdx.x & 7) == 0) ok[i] = good ? 1 : 0;
+    return;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  bool good;
-  if constexpr (kPairs) good = block_inverse_df(blocks + (size_t)i * 36, out + (size_t)i * 21);
-  else good = block_inverse(blocks + (size_t)i * 36, out + (size_t)i * 21);
-  ok[i] = good ? 1 : 0;
+  ok[i] = block_inverse(blocks + (size_t)i * 36, out + (size_t)i * 21) ? 1 : 0;
 }
 
 template <typename Acc>
@@ -1177,7 +1178,7 @@ cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-void launch_precond(const BatchHost& b, cudaStream_t st) {
+void launch_precond(const BatchHost& b, int gn_it, cudaStream_t st) {
   const int nb = b.total_tiles[kTilePrecond];
   if (nb == 0) return;
   Batch bt = b.bt;
@@ -1185,9 +1186,9 @@ void launch_precond(const BatchHost& b, cudaStream_t st) {
   // the default precision's double-float inverse may begin during the data
   // assembly's tail (programmatic dependent launch); the FP64 one does not:
   // overlapped with the assembly it cost the full-size frame 0.1 ms more
-  if (b.precision == SW_PRECISION_FP64) k_precond<double, false><<<nb, kPrecondTile, 0, st>>>(bt);
-  else if (b.precision == SW_PRECISION_MIXED_F64DOTS) k_precond<float, false><<<nb, kPrecondTile, 0, st>>>(bt);
-  else launch_overlapped(k_precond<float, true>, nb, kPrecondTile, st, bt);
+  if (b.precision == SW_PRECISION_FP64) k_precond<double, false><<<nb, kPrecondTile, 0, st>>>(bt, gn_it);
+  else if (b.precision == SW_PRECISION_MIXED_F64DOTS) k_precond<float, false><<<nb, kPrecondTile, 0, st>>>(bt, gn_it);
+  else launch_overlapped(k_precond<float, true>, nb, 8 * kPrecondTile, st, bt, gn_it);
 }
 
 cudaError_t launch_debug_block_inverse(const void* blocks, int n, int mode, void* out, int* ok, cudaStream_t st) {
@@ -1200,8 +1201,8 @@ cudaError_t launch_debug_block_inverse(const void* blocks, int n, int mode, void
     k_debug_block_inverse<float, false>
         <<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
   else
-    k_debug_block_inverse<float, true>
-        <<<nb, 128, 0, st>>>(static_cast<const float*>(blocks), n, static_cast<float*>(out), ok);
+    k_debug_block_inverse<float, true><<<(n + 15) / 16, 128, 0, st>>>(static_cast<const float*>(blocks), n,
+                                                                       static_cast<float*>(out), ok);
   return cudaGetLastError();
 }
 

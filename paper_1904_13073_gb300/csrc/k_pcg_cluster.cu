@@ -303,7 +303,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     (void)st;
   }
   __syncthreads();
-  const float* __restrict__ Ag = d.A;
+  const float* __restrict__ Ag = sys_A(d, gn_it);
   for (int a = tid; a < nr; a += kCThreads) {
     const int e0 = sHb[a], len = checked_count(sHb[a + 1] - e0, nb - e0, d.status);
     // the row's first block; its others follow it in A
@@ -342,7 +342,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     const int a = arow[h];
     const bool on = a < nr;
     const float* mi = sMi + 21 * (on ? a : 0);
-    const float r = (on && comp) ? -__ldg(d.g + 6 * (size_t)sRows[a] + gl) : 0.f;
+    const float r = (on && comp) ? -__ldg(sys_g(d, gn_it) + 6 * (size_t)sRows[a] + gl) : 0.f;
     float u = 0.f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {

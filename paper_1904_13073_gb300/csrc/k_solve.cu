@@ -1,12 +1,13 @@
 // K4-K6: the assembly half of one Gauss-Newton iteration of the non-rigid
-// solve (Sec. 7-8).
+// solve (Sec. 7-8), one launch (k_assemble) of two kinds of CTA:
 //
-//   K6 k_reg_assemble   the as-rigid-as-possible part (Eq. 11) of every
-//                       upper 6x6 block of JᵀJ and of Jᵀe, with plain stores:
-//                       8 lanes per node for the diagonal blocks and Jᵀe, one
-//                       thread per off-diagonal block.  It runs first and so
-//                       also initialises the whole system.
-//   K4+K5 k_data_assemble  one thread per surfel: dual-quaternion blend and
+//   K6 regulariser tiles  the as-rigid-as-possible part (Eq. 11) of every
+//                       upper 6x6 block of JᵀJ and of Jᵀe, added by vector
+//                       atomics: 8 lanes per node for the diagonal blocks and
+//                       Jᵀe, one thread per block for the others.  They also
+//                       clear the other of the two system buffers, which the
+//                       next iteration assembles into.
+//   K4+K5 data tiles    one thread per surfel: dual-quaternion blend and
 //                       forward warp (Eq. 1-2), projective association,
 //                       point-to-plane residual (Eq. 10) and its 1x24
 //                       Jacobian; the CTA then reduces JᵀJ and Jᵀe over runs
@@ -14,6 +15,11 @@
 //                       stored sorted by that set) and adds each run's ten
 //                       6x6 blocks and four 6-vectors to the system with
 //                       atomics.
+//
+// The two kinds run side by side, so the system they add to must be zero
+// before the launch: iteration k assembles into buffer k mod 2 (sys_A,
+// sys_g), cleared by iteration k - 1's launch or, for the solve's first
+// iteration, by k_system_clear.
 //   (K7+K8, the PCG and the node update, are in k_pcg.cu.)
 #include "sw_internal.h"
 #include "sw_check.cuh"
@@ -107,16 +113,16 @@ __global__ void k_solve_begin(Batch bt) {
 // [−[y]×, I]], so the block needs only the edges' count, Σy and Σ y yᵀ; the
 // out-edges all share y = T_j p_j.  Lane q of the group takes out-edge q and
 // the in-edges q, q + 8, ...; the group sums its lanes' shares by shuffles.
-// Threads [n8, n8 + nnzb): one per block; the off-diagonal ones write their
-// block (zero unless a graph edge joins its two nodes).
-__global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) {
-  pdl_begin();
-  const int s = find_stream(bt, blockIdx.x);
-  if (!stream_active(bt, s)) return;
-  const SwDev d = bt.devs[s];
-  const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
+// Threads [n8, n8 + nnzb): one per block; an off-diagonal one adds its
+// block when a graph edge joins its two nodes.  Thread b of the stream's
+// n8 + nnzb; returns its share of E_reg.  The system buffer of iteration
+// gn_it gets the terms; the other buffer's entries that the thread owns
+// (block b - n8, the Jᵀe segment of node j) are cleared for the next.
+__device__ __forceinline__ float reg_assemble_thread(const SwDev& d, int b, int gn_it) {
   // a new epoch for the generation stamps of the PCG launch that follows
   if (b == 0) *d.pcg_epoch += 1;
+  float* __restrict__ A = sys_A(d, gn_it);
+  float* __restrict__ g = sys_g(d, gn_it);
   const float sl = d.sqrt_lambda, l = sl * sl;
   const int n8 = reg_diag_threads(d.n_n);   // a multiple of 32: no warp straddles the two parts
   float ereg = 0.f;
@@ -181,20 +187,29 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
           acc[(3 + p) * 6 + c] = -l * ax[p * 3 + c];
           acc[(3 + p) * 6 + 3 + c] = p == c ? l * cnt : 0.f;
         }
-      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)checked(d.row_ptr[j], d.nnzb, d.status) * 36);
+      float4* dst = reinterpret_cast<float4*>(A + (size_t)checked(d.row_ptr[j], d.nnzb, d.status) * 36);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+      for (int k = 0; k < 9; ++k)
+        atomicAdd(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
+      float2* gj = reinterpret_cast<float2*>(g + 6 * (size_t)j);   // 8-byte aligned
+      float2* gn = reinterpret_cast<float2*>(sys_g(d, gn_it + 1) + 6 * (size_t)j);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) d.g[6 * j + k] = v[k];
+      for (int k = 0; k < 3; ++k) {
+        atomicAdd(gj + k, make_float2(v[2 * k], v[2 * k + 1]));
+        gn[k] = make_float2(0.f, 0.f);
+      }
     }
   } else if (b - n8 < d.nnzb) {
     const int bi = b - n8;
+    float4* nxt = reinterpret_cast<float4*>(sys_A(d, gn_it + 1) + (size_t)bi * 36);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nxt[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int i = checked(d.blk_row[bi], d.n_n, d.status), j = checked(d.col[bi], d.n_n, d.status);
-    if (i != j) {
+    const int fl = i != j ? d.blk_edge[bi] : 0;
+    if (fl) {
       float acc[36];
 #pragma unroll
       for (int k = 0; k < 36; ++k) acc[k] = 0.f;
-      const int fl = d.blk_edge[bi];
       if (fl & 1) {   // edge i -> j: J_i = sl[−[T_i p_i]×|I], J_j = −sl[−[T_j p_i]×|I]
         const float3 pi = f3(d.node_p[i]);
         add_reg_pair(acc, -l, node_apply(d, i, pi), node_apply(d, j, pi));
@@ -203,12 +218,13 @@ __global__ void __launch_bounds__(kBlkTile) k_reg_assemble(Batch bt, int gn_it) 
         const float3 pj = f3(d.node_p[j]);
         add_reg_pair(acc, -l, node_apply(d, i, pj), node_apply(d, j, pj));
       }
-      float4* dst = reinterpret_cast<float4*>(d.A + (size_t)bi * 36);
+      float4* dst = reinterpret_cast<float4*>(A + (size_t)bi * 36);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) dst[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+      for (int k = 0; k < 9; ++k)
+        atomicAdd(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
     }
   }
-  block_atomic_sum<double>((double)ereg, d.e_reg + gn_it);
+  return ereg;
 }
 
 // ------------------------------------------------------------------ K4+K5: data term
@@ -222,14 +238,16 @@ constexpr int kJS = 25;   // 24 Jacobian entries + residual per term
 constexpr int kAsmChunks = 6;
 static_assert(3 * kAsmChunks * 14 <= kAsmTile, "one thread per (item, part, chunk)");
 
-__global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_it, int write_live) {
-  pdl_begin();
-  const int s = find_stream(bt, blockIdx.x);
+// data tile `tile` of the batch (bt.tile_base: the data tiles' table)
+__device__ __forceinline__ void data_assemble_tile(const Batch& bt, int tile, int gn_it, int write_live) {
+  const int s = find_stream(bt, tile);
   if (!stream_active(bt, s)) return;
   const SwDev d = bt.devs[s];
+  float* __restrict__ A = sys_A(d, gn_it);
+  float* __restrict__ g = sys_g(d, gn_it);
   const int t_now = *d.t_now;
   const int tid = threadIdx.x;
-  const int i = (blockIdx.x - __ldg(bt.tile_base + s)) * kAsmTile + tid;
+  const int i = (tile - __ldg(bt.tile_base + s)) * kAsmTile + tid;
 
   __shared__ float sJ[kAsmTile * kJS];
   __shared__ int sset[kAsmTile];
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
-          float4* dst = reinterpret_cast<float4*>(d.A + (size_t)slot * 36 + 12 * part);   // 16-byte aligned
+          float4* dst = reinterpret_cast<float4*>(A + (size_t)slot * 36 + 12 * part);   // 16-byte aligned
 #pragma unroll
           for (int k = 0; k < 3; ++k)
             atomicAdd(dst + k, make_float4(acc[2 * k].x, acc[2 * k].y, acc[2 * k + 1].x, acc[2 * k + 1].y));
@@ -369,7 +387,7 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
       for (int t = t0; t <= t1; ++t) {
         const int st_ = t < t1 ? sset[t] : -1;
         if (st_ != cur) {
-          atomicAdd(reinterpret_cast<float2*>(d.g + (size_t)node * 6 + 2 * part), acc);   // 8-byte aligned
+          atomicAdd(reinterpret_cast<float2*>(g + (size_t)node * 6 + 2 * part), acc);   // 8-byte aligned
           if (t == t1) break;
           acc = make_float2(0.f, 0.f);
           cur = st_;
@@ -380,6 +398,47 @@ __global__ void __launch_bounds__(kAsmTile, 4) k_data_assemble(Batch bt, int gn_
         acc = __ffma2_rn(make_float2(Jt[6 * a + 2 * part], Jt[6 * a + 2 * part + 1]), make_float2(rr, rr), acc);
       }
     }
+  }
+}
+
+// One Gauss-Newton iteration's assembly: CTAs [0, reg_tiles) are the
+// regulariser's tiles (reg_base: their table, kAsmTile threads of a
+// stream's n8 + nnzb each), the rest the data tiles (bt.tile_base).  Both
+// add to the system buffer of gn_it, cleared before the launch.
+__global__ void __launch_bounds__(kAsmTile, 4)
+k_assemble(Batch bt, const int* __restrict__ reg_base, int reg_tiles, int gn_it, int write_live) {
+  pdl_begin();
+  if ((int)blockIdx.x < reg_tiles) {
+    Batch rb = bt;
+    rb.tile_base = reg_base;
+    const int s = find_stream(rb, blockIdx.x);
+    if (!stream_active(rb, s)) return;   // CTA-uniform
+    const SwDev d = bt.devs[s];
+    const int b = (blockIdx.x - __ldg(reg_base + s)) * kAsmTile + threadIdx.x;
+    const float ereg = reg_assemble_thread(d, b, gn_it);
+    block_atomic_sum<double>((double)ereg, d.e_reg + gn_it);
+    return;
+  }
+  data_assemble_tile(bt, blockIdx.x - reg_tiles, gn_it, write_live);
+}
+
+// Zeroes system buffer 0 of every active stream (the solve's first
+// iteration assembles into it): one thread per upper block, and the first
+// n_n threads the Jᵀe segments.
+__global__ void __launch_bounds__(kBlkTile) k_system_clear(Batch bt) {
+  const int s = find_stream(bt, blockIdx.x);
+  if (!stream_active(bt, s)) return;
+  const SwDev d = bt.devs[s];
+  const int b = (blockIdx.x - __ldg(bt.tile_base + s)) * kBlkTile + threadIdx.x;
+  if (b < d.nnzb) {
+    float4* blk = reinterpret_cast<float4*>(d.A + (size_t)b * 36);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) blk[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (b < d.n_n) {
+    float2* gj = reinterpret_cast<float2*>(d.g + 6 * (size_t)b);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gj[k] = make_float2(0.f, 0.f);
   }
 }
 
@@ -407,14 +466,14 @@ inline Batch with_kind(const BatchHost& b, int kind) {
 void launch_solve_begin(const BatchHost& b, cudaStream_t st) {
   if (b.bt.n_streams) k_solve_begin<<<b.bt.n_streams, 32, 0, st>>>(b.bt);
 }
-void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
-  if (b.total_tiles[kTileRegAssembly])
-    launch_overlapped(k_reg_assemble, b.total_tiles[kTileRegAssembly], kBlkTile, st, with_kind(b, kTileRegAssembly), gn_it);
+void launch_system_clear(const BatchHost& b, cudaStream_t st) {
+  if (b.total_tiles[kTileBlocks]) k_system_clear<<<b.total_tiles[kTileBlocks], kBlkTile, 0, st>>>(with_kind(b, kTileBlocks));
 }
-void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
-  if (b.total_tiles[kTileSurfelsAssembly])
-    launch_overlapped(k_data_assemble, b.total_tiles[kTileSurfelsAssembly], kAsmTile, st,
-                      with_kind(b, kTileSurfelsAssembly), gn_it, 0);
+void launch_assemble(const BatchHost& b, int gn_it, cudaStream_t st) {
+  const int nr = b.total_tiles[kTileRegAssembly], nd = b.total_tiles[kTileSurfelsAssembly];
+  if (nr + nd)
+    launch_overlapped(k_assemble, nr + nd, kAsmTile, st, with_kind(b, kTileSurfelsAssembly),
+                      (const int*)b.tile_base_dev[kTileRegAssembly], nr, gn_it, 0);
 }
 void launch_associate_only(const BatchHost& b, cudaStream_t st) {
   if (b.total_tiles[kTileSurfels]) k_associate_only<<<b.total_tiles[kTileSurfels], kSurfTile, 0, st>>>(with_kind(b, kTileSurfels));

@@ -104,8 +104,13 @@ struct SwDev {
   int* rl_ptr;        // n_n + 1: per block row, every block that multiplies into it
   int2* rl_ent;       //   (block | transposed << 31, neighbour node)
   int* set_slots;     // 14 per set: 10 upper blocks of (a<=b), then 4 node ids
-  float* A;           // nnzb * 36
-  float* g;           // 6 n_n
+  // the system JᵀJ (upper blocks) and Jᵀe in two buffers: Gauss-Newton
+  // iteration k assembles into buffer k mod 2 (sys_A, sys_g) while
+  // clearing the other for iteration k + 1
+  float* A;           // nnzb * 36, buffer 0
+  float* g;           // 6 n_n, buffer 0
+  float* A2;          // buffer 1
+  float* g2;
   // PCG
   float* minv;        // n_n * 21: block-Jacobi preconditioner, inverse of each diagonal block, packed lower
   struct PartSlot* part;   // 4 * kMaxCtaPerStream slots for the per-CTA partials of the PCG's reductions
@@ -151,6 +156,10 @@ __device__ __forceinline__ int find_stream(const Batch& bt, int b) {
 }
 
 __device__ __forceinline__ bool stream_active(const Batch& bt, int s) { return !bt.active || __ldg(bt.active + s); }
+
+// the system buffers that Gauss-Newton iteration gn_it assembles into and solves
+__device__ __forceinline__ float* sys_A(const SwDev& d, int gn_it) { return (gn_it & 1) ? d.A2 : d.A; }
+__device__ __forceinline__ float* sys_g(const SwDev& d, int gn_it) { return (gn_it & 1) ? d.g2 : d.g; }
 
 // Programmatic dependent launch along the Gauss-Newton loop: a kernel
 // launched by launch_overlapped may begin while the previous launch on the
@@ -206,10 +215,14 @@ void launch_knn_skin(const SwDev& d, const float4* v_orig, int n_s, int* ids_tmp
                      float4* w_out, cudaStream_t st);
 void launch_node_graph(const SwDev& d, cudaStream_t st);
 void launch_solve_begin(const BatchHost& b, cudaStream_t st);
-void launch_reg_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
-void launch_data_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
-// the block-Jacobi preconditioner of every active stream (inverse of each diagonal block)
-void launch_precond(const BatchHost& b, cudaStream_t st);
+// zeroes system buffer 0 of every active stream (before a solve's first assembly)
+void launch_system_clear(const BatchHost& b, cudaStream_t st);
+// Gauss-Newton iteration gn_it's assembly (FP32 modes): regulariser and data
+// terms into system buffer gn_it mod 2, which must be zero; clears the other
+void launch_assemble(const BatchHost& b, int gn_it, cudaStream_t st);
+// the block-Jacobi preconditioner of every active stream (inverse of each
+// diagonal block of the system iteration gn_it assembled)
+void launch_precond(const BatchHost& b, int gn_it, cudaStream_t st);
 cudaError_t launch_pcg(const BatchHost& b, int gn_it, int pcg_iters, cudaStream_t st);
 void launch_reg_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
 void launch_data_assemble64(const BatchHost& b, int gn_it, cudaStream_t st);
@@ -378,7 +391,7 @@ inline int tiles_for(int kind, const SwDev& d) {
     case kTilePcg: return 0;   // assigned by the runner (share of the persistent grid)
     case kTileNodes: return (d.n_n + kBlkTile - 1) / kBlkTile;
     case kTilePrecond: return (d.n_n + kPrecondTile - 1) / kPrecondTile;
-    case kTileRegAssembly: return (reg_diag_threads(d.n_n) + d.nnzb + kBlkTile - 1) / kBlkTile;   // 8 lanes per node, then a thread per block
+    case kTileRegAssembly: return (reg_diag_threads(d.n_n) + d.nnzb + kAsmTile - 1) / kAsmTile;   // 8 lanes per node, then a thread per block
   }
   return 0;
 }

@@ -19,6 +19,8 @@ def test_stage_bytes_follow_the_per_unit_figures():
     b = bench.stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, k)
     assert b["depth"] == 4800 * (4 + 32)
     assert b["reg_assembly"] == 150 * 144 + 20 * 80
+    assert b["data_assembly"] == 1000 * 64 + 300 * 32 + 20 * 32 + 150 * 144 + 20 * 24 + 20 * 80
+    b = bench.stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, k, merged=False)
     assert b["data_assembly"] == 1000 * 64 + 300 * 32 + 20 * 32 + 150 * 144 + 20 * 24
     assert b["pcg"] == 7 * (150 * 144 + 20 * 192) + 20 * 252
     assert b["fusion"] == 1000 * (64 + 32 + 24) + 4800 * 160

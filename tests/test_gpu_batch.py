@@ -85,9 +85,11 @@ def test_inactive_members_are_untouched_and_profile_counts_stages():
         np.testing.assert_array_equal(sw.sw_read_nodes(hs[1])[1], before_q)
         np.testing.assert_array_equal(sw.sw_read_surfels(hs[1])[0], before_v)
         assert stats[0]["n_corr"][0] > 0 and stats[2]["n_corr"][0] > 0
-        assert prof["reg_assembly"][1] == 2 and prof["data_assembly"][1] == 2 and prof["pcg"][1] == 2
+        # FP32 modes: one assembly launch of both terms, timed as the data stage
+        assert prof["reg_assembly"] == (0.0, 0)
+        assert prof["data_assembly"][1] == 2 and prof["pcg"][1] == 2
         assert prof["fusion"][1] == 1
-        assert all(prof[k][0] > 0 for k in ("reg_assembly", "data_assembly", "pcg", "fusion"))
+        assert all(prof[k][0] > 0 for k in ("data_assembly", "pcg", "fusion"))
         # a member's model is replaced: the batch rebuilds its tables at its
         # next call and keeps the active flags
         v4, n4, t2, node4 = sw.model_arrays(scenes[0])
@@ -111,9 +113,10 @@ def test_stream_profile_reports_each_stage():
         sw.sw_fuse_frame(h)
         prof = sw.sw_read_profile(h)
         assert prof["depth"][1] == 1 and prof["fusion"][1] == 1
-        assert prof["reg_assembly"][1] == 3 and prof["data_assembly"][1] == 3 and prof["pcg"][1] == 3
+        assert prof["reg_assembly"] == (0.0, 0)   # with the data term in one launch
+        assert prof["data_assembly"][1] == 3 and prof["pcg"][1] == 3
         assert prof["visibility"] == (0.0, 0)   # visibility prediction is off by default
-        assert all(v[0] > 0 for k, v in prof.items() if k != "visibility")
+        assert all(v[0] > 0 for k, v in prof.items() if k not in ("visibility", "reg_assembly"))
     finally:
         sw.sw_destroy_stream(h)
 
