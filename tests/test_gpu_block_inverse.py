@@ -1,8 +1,9 @@
 """The block-Jacobi preconditioner's 6x6 inverse (Sec. 7) as the PCG forms
-it on the device -- from the block's lower triangle, LDLᵀ with
-Newton-refined pivot reciprocals, in double-float pairs (mode 0, the
-default precision), in FP64 (mode 1, the FP64 variant) or in FP64 on FP32
-blocks (mode 2) -- against the FP64 inverse from LAPACK,
+it on the device -- from the block's lower triangle, with Newton-refined
+pivot reciprocals: Gauss-Jordan sweeps in double-float pairs on eight lanes
+per block (mode 0, the default precision), LDLᵀ in FP64 (mode 1, the FP64
+variant) or LDLᵀ in FP64 on FP32 blocks (mode 2) -- against the FP64
+inverse from LAPACK,
 over conditioning from 1 to 1e6, magnitudes from 1e-33 to 1e6 (the smallest
 below the range where the reciprocal's FP32 seed is used), an upper triangle
 that differs from the lower one, and blocks that are not positive
