@@ -141,12 +141,13 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters, merged=True):
     }
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# ncu capture of this workload's kernels as they are now (the "pcg" stage is
-# the preconditioner launch plus the cluster PCG launch);
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of
+# the two launches of one ncu capture) of this workload's kernels as they are
+# now (the "pcg" stage is the preconditioner launch plus the cluster PCG
+# launch; "data_assembly" is k_assemble, both terms);
 # profiles/k_pcg_cluster_plain_full_300k_2048.md and
-# profiles/k_data_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": None, "data_assembly": None}
+# profiles/k_assemble_plain_full_300k_2048.md give the commands.
+PROFILED_TRAFFIC = {"pcg": 562688.0 + 3039488.0, "data_assembly": 26726144.0 + 31104.0}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
