@@ -544,10 +544,12 @@ sw_status sw_server_set_appending(sw_server_handle s, int enable);
  * frame into one step. */
 sw_status sw_server_set_plain(sw_server_handle s, int enable);
 /* Adaptive steps (1, the default): every step runs its frames either as one
- * batch or one by one through their streams' own calls, whichever the
- * server's measured times say is cheaper (a batch step is shaped for all
- * admitted streams, so under light load a few frames finish sooner alone).
- * 0 batches every step.  Ignored in the plain mode. */
+ * batch or, when the server's measured times say that serving them one by
+ * one through their streams' own calls takes less time, only the oldest
+ * queued frame alone (as the plain mode does), deciding again at the next
+ * step (a batch step is shaped for all admitted streams, so under light load
+ * a few frames finish sooner alone).  0 batches every step.  Ignored in the
+ * plain mode. */
 sw_status sw_server_set_adaptive(sw_server_handle s, int enable);
 sw_status sw_server_read_stats(sw_server_handle s, sw_server_stats* out);
 

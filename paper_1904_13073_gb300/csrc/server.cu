@@ -30,7 +30,9 @@
 // changes) against the sum of the queued streams' own frame times (a
 // per-stream average; a stream not yet measured counts at the average of the
 // measured ones, and while none is measured a step of one or two frames runs
-// them one by one, which measures them).
+// alone, which measures them).  A step that runs alone serves only the oldest
+// queued frame, as the plain mode does, and the next step decides again; the
+// batch is first tried only on a long queue (kExploreBatch frames).
 //
 // In the plain mode (sw_server_set_plain) each step instead takes the single
 // oldest queued frame and runs it through its stream's own calls, one stream
@@ -92,7 +94,7 @@ struct sw_server {
   double window_ms = 0.0;        // how long a step may wait for more streams' frames
   bool appending = false;        // sw_append_frame after every served frame
   bool plain = false;            // one frame per step through its stream's own calls (no batching)
-  bool adaptive = true;          // per step, the batch or the streams' own calls, whichever is cheaper
+  bool adaptive = true;          // per step, the batch or the oldest frame alone, by measured times
   // measured costs for the adaptive policy (worker thread only), in ms
   static constexpr int kSizeClasses = 8;   // step sizes 1, 2, 3-4, 5-8, ..., 65+
   double tb[kSizeClasses] = {};  // batch step time by size class (0: not measured)
@@ -122,8 +124,13 @@ int size_class(int k) {
 
 double ema(double old, double x) { return old > 0.0 ? 0.7 * old + 0.3 * x : x; }
 
-// The adaptive policy's choice for a step of these streams' frames: true to
-// run them one by one through their own calls.
+// The adaptive policy's choice for a step of these streams' frames: true
+// when serving them one by one through their own calls takes less time than
+// one batch step.  Until the batch has been measured, a step batches only
+// from kExploreBatch queued frames on: a batch step lasts about as long as
+// the batch's largest member's solve whatever the share of active members,
+// so trying it on a short queue costs every frame in it that time.
+constexpr int kExploreBatch = 16;
 bool cheaper_alone(const sw_server* S, const std::vector<int>& ids) {
   const int k = (int)ids.size();
   double alone = 0.0;
@@ -142,7 +149,7 @@ bool cheaper_alone(const sw_server* S, const std::vector<int>& ids) {
     if (c - d >= 0 && S->tb[c - d] > 0.0) batch = S->tb[c - d];
     else if (c + d < sw_server::kSizeClasses && S->tb[c + d] > 0.0) batch = S->tb[c + d];
   }
-  if (batch == 0.0) return k <= 2;   // the batch not measured yet
+  if (batch == 0.0) return k < kExploreBatch;   // the batch not measured yet
   return alone < batch;
 }
 
@@ -282,18 +289,29 @@ void worker_main(sw_server* S) {
       members = S->order;
     }
     std::lock_guard<std::mutex> g(S->gpu);
+    // alone, the frames run oldest first
+    std::vector<size_t> by_age(taken.size());
+    for (size_t k = 0; k < taken.size(); ++k) by_age[k] = k;
+    std::sort(by_age.begin(), by_age.end(),
+              [&](size_t a, size_t b) { return taken[a].submit_ms < taken[b].submit_ms; });
+    bool alone = S->plain;
+    if (!alone && S->adaptive) {
+      alone = cheaper_alone(S, taken_ids);
+      if (alone && taken.size() > 1) {   // the oldest frame now; the others are decided again next step
+        const size_t o = by_age[0];
+        taken = {taken[o]};
+        taken_ids = {taken_ids[o]};
+        taken_ptrs = {taken_ptrs[o]};
+        by_age = {0};
+      }
+    }
     sw_status status = SW_OK;
     std::vector<sw_status> fstat(taken.size(), SW_OK);   // per taken frame
     std::vector<sw_append_stats> app(taken.size());
     std::vector<sw_status> app_status(taken.size(), SW_OK);
     std::vector<double> f_start(taken.size(), 0.0), f_done(taken.size(), 0.0);
-    const bool alone = S->plain || (S->adaptive && cheaper_alone(S, taken_ids));
     if (alone) {
       // each frame's stream alone, through its own calls, oldest frame first
-      std::vector<size_t> by_age(taken.size());
-      for (size_t k = 0; k < taken.size(); ++k) by_age[k] = k;
-      std::sort(by_age.begin(), by_age.end(),
-                [&](size_t a, size_t b) { return taken[a].submit_ms < taken[b].submit_ms; });
       for (size_t k : by_age) {
         SrvStream* s = taken_ptrs[k];
         f_start[k] = now_ms(S->t0);
