@@ -61,49 +61,101 @@ def render_frames(seed, ts, procs):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region.  Each sample carries
+    nvidia-smi's own timestamp; `__enter__` returns once the first sample
+    is written (so that the sampler is running before the region starts),
+    `region()` marks the timed region's start and end on the host clock, and
+    `summary()` keeps the samples taken inside it (the nearest one on each
+    side when the region is shorter than the sampling interval)."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 10
 
     def __init__(self, path):
         self.path = path
         self.proc = None
+        self.t0 = self.t1 = None
+
+    def _launch(self, interval_ms):
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                      "-lms", str(interval_ms)], stdout=self.f, stderr=subprocess.DEVNULL)
+        deadline = time.time() + 5.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                return True
+            time.sleep(0.01)
+        return os.path.getsize(self.path) > 0 and self.proc.poll() is None
 
     def __enter__(self):
         try:
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            if not self._launch(self.INTERVAL_MS):   # a sampler that refuses the short interval: 100 ms
+                if self.proc.poll() is None:
+                    self.proc.terminate()
+                self.proc.wait()
+                self.f.close()
+                self.INTERVAL_MS = 100
+                self._launch(self.INTERVAL_MS)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(2.5 * self.INTERVAL_MS / 1000.0)   # the sample after the region
             self.proc.terminate()
             self.proc.wait()
             self.f.close()
 
-    def summary(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def parse(lines):
+        """(epoch seconds, fields after the timestamp) per well-formed line."""
+        import datetime
+        out = []
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9 and parts[1].isdigit():
-                rows.append(parts)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = sorted(int(r[1]) for r in rows)
+            if len(parts) < 10 or not parts[2].isdigit():
+                continue
+            try:
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            out.append((t, parts[1:]))
+        return out
+
+    @staticmethod
+    def summarise(samples, t0, t1):
+        if not samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["no samples"]}
+        inside = [r for t, r in samples if t0 is not None and t1 is not None and t0 <= t <= t1]
+        n_inside = len(inside)
+        if not inside:   # a region shorter than the interval: the samples just before and after it
+            before = [r for t, r in samples if t0 is not None and t < t0]
+            after = [r for t, r in samples if t1 is not None and t > t1]
+            inside = before[-1:] + after[:1] or [samples[-1][1]]
+        sm = sorted(int(r[1]) for r in inside)
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for r in inside:
             for k, nm in enumerate(names):
                 if r[5 + k].lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": int(rows[0][2]), "samples": len(rows),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": int(inside[0][2]), "samples": n_inside,
+                "samples_used": len(inside), "interval_ms": Clocks.INTERVAL_MS, "reasons": sorted(reasons)}
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        with open(self.path) as f:
+            return self.summarise(self.parse(f), self.t0, self.t1)
 
 
 def measured_hbm_peak():
@@ -147,7 +199,7 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters, merged=True):
 # launch; "data_assembly" is k_assemble, both terms);
 # profiles/k_pcg_cluster_plain_full_300k_2048.md and
 # profiles/k_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": 562688.0 + 3039488.0, "data_assembly": 26726144.0 + 31104.0}
+PROFILED_TRAFFIC = {"pcg": 563968.0 + 3040000.0, "data_assembly": 26723840.0 + 29056.0}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):
@@ -693,6 +745,8 @@ def main():
     clocks_csv = args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else os.path.join(
         tempfile.gettempdir(), f"sw_clocks_rank{rank}.csv")
     with Clocks(clocks_csv) as clk:
+        torch.cuda.synchronize()
+        clk.start()
         for k in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xff)
@@ -700,6 +754,7 @@ def main():
             step(args.warmup + k, False)
             ends[k].record(stream)
         torch.cuda.synchronize()
+        clk.stop()
     if dist:
         dist.barrier()
     lat = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])

@@ -114,7 +114,7 @@ __host__ __device__ inline PlanOff plan_off(int C, int n_n, int nnzb, int n_push
 // the remotely written sections (partials, u, receive slots) sit at the same
 // offsets in every CTA
 struct SmemPlan {   // byte offsets
-  unsigned part, u, recv, a, col, o2t, mi, xps, hb, go, po, push, rows, bar, total;
+  unsigned part, u, recv, a, col, mi, xps, hb, go, po, push, rows, bar, total;
 };
 __host__ __device__ constexpr unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, int NP) {
@@ -123,9 +123,8 @@ __host__ __device__ inline SmemPlan smem_plan(int NR, int NB, int NG, int NH, in
   L.u = 16u * kMaxCluster;                          // u of the own rows, then the halo: 8 floats each
   L.recv = al16(L.u + 32u * (NR + NH));             // received A_ijᵀ u_i: 6 floats per slot
   L.a = al16(L.recv + 24u * NG);                    // home blocks, 36 floats each, row-major
-  L.col = al16(L.a + 144u * NB);
-  L.o2t = al16(L.col + 4u * NB);
-  L.mi = al16(L.o2t + 4u * NB);                     // M⁻¹ of each row, packed lower (21 floats)
+  L.col = al16(L.a + 144u * NB);                    // per home block {column's u slot, transposed target}
+  L.mi = al16(L.col + 8u * NB);                     // M⁻¹ of each row, packed lower (21 floats)
   L.xps = al16(L.mi + 84u * NR);                    // x, p, s of each row (3 x 6 floats)
   L.hb = al16(L.xps + 72u * NR);
   L.go = al16(L.hb + 4u * (NR + 1));
@@ -256,8 +255,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   float* sU = reinterpret_cast<float*>(smem_raw + L.u);
   float* sRecv = reinterpret_cast<float*>(smem_raw + L.recv);
   float* sA = reinterpret_cast<float*>(smem_raw + L.a);
-  int* sCol = reinterpret_cast<int*>(smem_raw + L.col);
-  int* sO2t = reinterpret_cast<int*>(smem_raw + L.o2t);
+  int2* sCol = reinterpret_cast<int2*>(smem_raw + L.col);
   float* sMi = reinterpret_cast<float*>(smem_raw + L.mi);
   float* sXps = reinterpret_cast<float*>(smem_raw + L.xps);   // row a: x at 18a, p at 18a + 6, s at 18a + 12
   int* sHb = reinterpret_cast<int*>(smem_raw + L.hb);
@@ -272,6 +270,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   const int g = tid >> 3, gl = tid & 7;           // row group, lane in the group
   const int gbase = lane & ~7;                    // the group's first lane in the warp
   const bool comp = gl < 6;                       // this lane holds component gl of its rows
+  const unsigned symoff = sym_offsets(comp ? gl : 0);   // row gl of a packed M⁻¹ block
   const unsigned uBase = smem_u32(sU), recvBase = smem_u32(sRecv), partBase = smem_u32(sPart);
   const unsigned bar = smem_u32(smem_raw + L.bar);
 
@@ -290,9 +289,9 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   }
   for (int x = tid; x < np; x += kCThreads) sPush[x] = checked_pair(__ldg(P + off.push + push0 + x), C, NR + NH, d.status);
   for (int e = tid; e < nb; e += kCThreads) {
-    sCol[e] = checked(__ldg(P + off.col + blk0 + e), NR + NH, d.status);
     const int o2t = __ldg(P + off.o2t + blk0 + e);
-    sO2t[e] = o2t == -1 ? -1 : checked_pair(o2t, C, NG, d.status);
+    sCol[e] = make_int2(checked(__ldg(P + off.col + blk0 + e), NR + NH, d.status),
+                        o2t == -1 ? -1 : checked_pair(o2t, C, NG, d.status));
   }
   for (int t = tid; t < 18 * nr; t += kCThreads) sXps[t] = 0.f;
   __syncthreads();
@@ -347,7 +346,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const float rk = __shfl_sync(0xffffffffu, r, gbase + k);
-      if (comp) u += mi[sym(gl, k)] * rk;
+      if (comp) u += mi[sym_at(symoff, k)] * rk;
     }
     if (on && comp) {
       rr[h] = r;
@@ -404,7 +403,8 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
 #pragma unroll
       for (int b = 0; b < 6; ++b) o1[b] = 0.f;
       for (int e = e0 + gl; e < e1; e += kGroup) {
-        const int ci = sCol[e];
+        const int2 co = sCol[e];   // one 8-byte load: the column's u slot and the transposed target
+        const int ci = co.x;
         const float4 u4 = *reinterpret_cast<const float4*>(sU + 8 * ci);
         const float2 u2 = *reinterpret_cast<const float2*>(sU + 8 * ci + 4);
         // u_j in component pairs; the products run on packed FP32 pairs
@@ -433,20 +433,16 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
           o1[2 * bp + 1] += sb;
           dt += ui[2 * bp] * sa + ui[2 * bp + 1] * sb;
         }
-        const int tg = sO2t[e];
+        const int tg = co.y;
         // δ's share: exact times 1 or 2, added by a cascaded (TwoSum) step
         del = acc_add_cascaded(del, acc_from<Acc>(tg < 0 ? dt : 2.f * dt));
         if (tg >= 0) {   // off the diagonal: A_ijᵀ u_i to its receive slot at the column's owner
           const unsigned slot = (unsigned)(tg & 0xffff);
           const unsigned ta = at_rank(recvBase + 24u * slot, (unsigned)(tg >> 16), me);
-          // a slot is 24 bytes: even slots start 16-byte aligned, odd ones 8 bytes past
-          if (slot & 1u) {
-            st_cl_f2(ta, o2[0].x, o2[0].y);
-            st_cl_f4(ta + 8, make_float4(o2[1].x, o2[1].y, o2[2].x, o2[2].y));
-          } else {
-            st_cl_f4(ta, make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y));
-            st_cl_f2(ta + 16, o2[2].x, o2[2].y);
-          }
+          // a slot is 24 bytes, 8-byte aligned: three pair stores, the same for every slot
+          st_cl_f2(ta, o2[0].x, o2[0].y);
+          st_cl_f2(ta + 8, o2[1].x, o2[1].y);
+          st_cl_f2(ta + 16, o2[2].x, o2[2].y);
         }
       }
       wh[h] = group_reduce_scatter6(o1, gl);
@@ -464,8 +460,14 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         gs = sPart[2 * lane];
         ds = sPart[2 * lane + 1];
       }
-      gs = acc_norm(warp_sum_cascaded(gs));
-      ds = acc_norm(warp_sum_cascaded(ds));
+      // lanes C..31 hold zeros: the butterfly over lanes 0..15 gives the same sums
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        gs = acc_add_cascaded(gs, O::shfl_xor(gs, o));
+        ds = acc_add_cascaded(ds, O::shfl_xor(ds, o));
+      }
+      gs = acc_norm(gs);
+      ds = acc_norm(ds);
       if (lane == 0) {
         float al, be;
         const int st = gear_step(k, gs, ds, g_prev, a_prev, &al, &be);
@@ -485,7 +487,9 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
       const bool on = a < nr && comp;
       float acc = wh[h];
       const int x1 = on ? sGo[a + 1] : 0;
-      for (int x = on ? sGo[a] : 0; x < x1; ++x) acc += sRecv[6 * x + gl];
+      int x = on ? sGo[a] : 0;
+      for (; x + 1 < x1; x += 2) acc = (acc + sRecv[6 * x + gl]) + sRecv[6 * x + 6 + gl];
+      if (x < x1) acc += sRecv[6 * x + gl];
       wt[h] = acc;
     }
     __syncthreads();
@@ -512,7 +516,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
 #pragma unroll
         for (int kk = 0; kk < 6; ++kk) {
           const float rk = __shfl_sync(0xffffffffu, rr[h], gbase + kk);
-          if (comp) u += mi[sym(gl, kk)] * rk;
+          if (comp) u += mi[sym_at(symoff, kk)] * rk;
         }
         if (on && comp) {
           sU[8 * a + gl] = u;

@@ -108,6 +108,17 @@ __device__ __forceinline__ float ratio_f32(double a, double b) {
 
 __device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }   // packed, r >= c
 __device__ __forceinline__ int sym(int r, int c) { return r >= c ? tri(r, c) : tri(c, r); }
+// the packed-lower offsets of row r (0..5) of a symmetric 6x6 block, 5 bits
+// each: computed once for a lane-dependent row, then read by sym_at with a
+// constant column in an unrolled loop (no per-column index arithmetic; one
+// register, which the 64-register cooperative kernels cannot spare)
+__device__ __forceinline__ unsigned sym_offsets(int r) {
+  unsigned o = 0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) o |= (unsigned)sym(r, c) << (5 * c);
+  return o;
+}
+__device__ __forceinline__ int sym_at(unsigned offsets, int c) { return (int)((offsets >> (5 * c)) & 31u); }
 
 template <typename Acc>
 __device__ __forceinline__ Acc acc_nan() {

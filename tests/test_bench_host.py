@@ -58,3 +58,24 @@ def test_peak_is_the_measured_copy_bandwidth_or_the_fallback():
 def test_whole_job_throughput_counts_every_replica():
     assert bench.job_frames_per_s(2.0, 1) == pytest.approx(500.0)
     assert bench.job_frames_per_s(4.0, 8) == pytest.approx(2000.0)
+
+
+def test_clock_summary_keeps_the_samples_inside_the_timed_region():
+    import datetime
+
+    def line(t, mhz, power_cap="Not Active", thermal="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.00, 0x0, Not Active, Not Active, {thermal}, {power_cap}"
+
+    t0 = 1_800_000_000.0
+    lines = [line(t0 - 0.05, 1200), line(t0 + 0.01, 2070), line(t0 + 0.02, 2055, power_cap="Active"),
+             line(t0 + 0.03, 2070), line(t0 + 0.2, 1000, thermal="Active")]
+    samples = bench.Clocks.parse(lines + ["garbage, line", ""])
+    assert len(samples) == 5
+    s = bench.Clocks.summarise(samples, t0, t0 + 0.04)
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]   # the thermal sample lies after the region
+    # a region between two samples: the nearest one on each side
+    s = bench.Clocks.summarise(samples, t0 + 0.1, t0 + 0.15)
+    assert s["samples"] == 0 and s["samples_used"] == 2 and s["reasons"] == ["sw_thermal_slowdown"]
+    assert bench.Clocks.summarise([], t0, t0 + 1)["reasons"] == ["no samples"]
