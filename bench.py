@@ -199,7 +199,7 @@ def stage_bytes(n_s, n_n, nnzb, n_corr, n_pix, pcg_iters, merged=True):
 # launch; "data_assembly" is k_assemble, both terms);
 # profiles/k_pcg_cluster_plain_full_300k_2048.md and
 # profiles/k_assemble_plain_full_300k_2048.md give the commands.
-PROFILED_TRAFFIC = {"pcg": 563968.0 + 3040000.0, "data_assembly": 26723840.0 + 29056.0}
+PROFILED_TRAFFIC = {"pcg": 563968.0 + 3055872.0, "data_assembly": 26728960.0 + 26496.0}
 
 
 def roofline(stage_ms, stage_n, n_s, n_n, nnzb, n_corr, n_pix, pcg_iters):

@@ -335,6 +335,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
   arow[0] = g;
   arow[1] = 2 * kGroups - 1 - g;
   float rr[2] = {0.f, 0.f};   // component gl of the rows' r
+  float uc[2] = {0.f, 0.f};   // component gl of the rows' u (also in sU for the group's loads)
   Acc gam = O::zero();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -350,6 +351,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
     }
     if (on && comp) {
       rr[h] = r;
+      uc[h] = u;
       sU[8 * a + gl] = u;
       // a diagonal block that is not positive definite (its inverse's first
       // entry is a NaN) reaches every CTA through the first reduction
@@ -505,7 +507,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
         const float* mi = sMi + 21 * (on ? a : 0);
         if (on && comp) {
           float* xps = sXps + 18 * a + gl;
-          const float pc = sU[8 * a + gl] + be * xps[6];
+          const float pc = uc[h] + be * xps[6];
           const float sc = wt[h] + be * xps[12];
           xps[6] = pc;
           xps[12] = sc;
@@ -519,6 +521,7 @@ k_pcg_cluster(Batch bt, const int* __restrict__ members, int C, int K, int gn_it
           if (comp) u += mi[sym_at(symoff, kk)] * rk;
         }
         if (on && comp) {
+          uc[h] = u;
           sU[8 * a + gl] = u;
           gam = acc_add_cascaded(gam, O::prod(rr[h], u));
         }
