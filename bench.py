@@ -601,9 +601,9 @@ def run_batched(sw, torch, members, rounds, warmup, flush, stream):
             sw.sw_solve_frame(hd, gn, pcg, want_stats=False)
             sw.sw_fuse_frame(hd)
 
-    # frame round 0 (one frame of every stream) is played untimed by both
-    # runs (the batched run tunes its PCG on it; the autotune leaves the
-    # state as it found it); frame rounds 1.. are timed
+    # the first pass over the streams (one frame of every stream) is played
+    # untimed by both runs (the batched run tunes its PCG on it; the
+    # autotune leaves the state as it found it); the later passes are timed
     reset_models()
     plain_round(0)
     lat_plain = timed(lambda r: plain_round(r + 1), rounds, warmup)
